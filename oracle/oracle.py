@@ -1,0 +1,347 @@
+"""Python face of the CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by `__graft_entry__.smoke()`
+and by the CPU-baseline leg of `bench.py`.  The product library never
+imports, links or executes anything in `oracle/`.
+
+The render itself lives in `rxgs_oracle.c` (plain C, float64 values with a
+float32 decision shadow); this module compiles it with gcc, loads it with
+ctypes and adds the float64 conditioning MLP (Sec. 3.3.2) in numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rxgs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -ffp-contract=off, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("theta0_deg", ctypes.c_double),
+                ("step_deg", ctypes.c_double), ("TH", ctypes.c_int), ("TW", ctypes.c_int),
+                ("eps_T", ctypes.c_float), ("q_max", ctypes.c_float), ("r_near", ctypes.c_float)]
+
+
+def make_grid(g) -> Grid:
+    """Accepts any object with the fields of `synthetic.Grid`."""
+    return Grid(int(g.H), int(g.W), float(g.theta0_deg), float(g.step_deg), int(g.tile_h),
+                int(g.tile_w), float(g.eps_T), float(g.q_max), float(g.r_near))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            _lib.or_exp32.restype = ctypes.c_float
+            _lib.or_exp32.argtypes = [ctypes.c_float]
+            _lib.or_atan2_32.restype = ctypes.c_float
+            _lib.or_atan2_32.argtypes = [ctypes.c_float, ctypes.c_float]
+            _lib.or_cov32.argtypes = [P, P, P]
+            _lib.or_cov64.argtypes = [P, P, P]
+            _lib.or_sigma2d64.argtypes = [P, P, P, P, P]
+            _lib.or_project_view32.restype = ctypes.c_int
+            _lib.or_project_view32.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
+            _lib.or_tile_lists.restype = ctypes.c_long
+            _lib.or_tile_lists.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_long, P]
+            _lib.or_render_view.restype = ctypes.c_int
+            _lib.or_render_view.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                            ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_int]
+            _lib.or_render_pixels.restype = ctypes.c_int
+            _lib.or_render_pixels.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                              ctypes.c_int, P, ctypes.c_int, P, P, P, P, P]
+            _lib.or_backward_view.restype = ctypes.c_int
+            _lib.or_backward_view.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                              ctypes.c_int, P, P, P, P, ctypes.c_int]
+            _lib.or_omp_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def threads() -> int:
+    return int(lib().or_omp_threads())
+
+
+def exp32(x: float) -> np.float32:
+    return np.float32(lib().or_exp32(ctypes.c_float(x)))
+
+
+def atan2_32(y: float, x: float) -> np.float32:
+    return np.float32(lib().or_atan2_32(ctypes.c_float(y), ctypes.c_float(x)))
+
+
+def cov32(log_scales, quats):
+    s, q = _c32(log_scales), _c32(quats)
+    out = np.zeros((s.shape[0], 6), np.float32)
+    L = lib()
+    for k in range(s.shape[0]):
+        L.or_cov32(_p(s[k]), _p(q[k]), _p(out[k]))
+    return out
+
+
+def cov64(log_scales, quats):
+    s, q = _c32(log_scales), _c32(quats)
+    out = np.zeros((s.shape[0], 6), np.float64)
+    L = lib()
+    for k in range(s.shape[0]):
+        L.or_cov64(_p(s[k]), _p(q[k]), _p(out[k]))
+    return out
+
+
+def sigma2d64(grid, mean, S6, centre):
+    g = make_grid(grid)
+    out = np.zeros(3, np.float64)
+    lib().or_sigma2d64(ctypes.byref(g), _p(_c32(mean)), _p(_c64(S6)), _p(_c32(centre)), _p(out))
+    return out
+
+
+def project_view32(grid, scene, centre):
+    """float32 shadow of the projection: (Sigma[K,6], rec[K,8], box[K,4])."""
+    g = make_grid(grid)
+    K = scene.K
+    S6 = np.zeros((K, 6), np.float32)
+    rec = np.zeros((K, 8), np.float32)
+    box = np.zeros((K, 4), np.int32)
+    lib().or_project_view32(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                            _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                            _p(S6), _p(rec), _p(box))
+    return S6, rec, box
+
+
+def tile_lists(grid, scene, centre, cap=None):
+    """Per-tile depth-sorted lists: (counts[tiles], lists[total], ntiles[K])."""
+    g = make_grid(grid)
+    K = scene.K
+    T = ((grid.H + grid.tile_h - 1) // grid.tile_h) * ((grid.W + grid.tile_w - 1) // grid.tile_w)
+    counts = np.zeros(T, np.int32)
+    ntiles = np.zeros(K, np.int32)
+    cap = cap or max(1, K * 8)
+    while True:
+        lists = np.zeros(cap, np.int32)
+        n = lib().or_tile_lists(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                                _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                                _p(counts), _p(lists), cap, _p(ntiles))
+        if n == -1:
+            cap *= 4
+            continue
+        if n < 0:
+            raise MemoryError("oracle tile_lists failed")
+        return counts, lists[:n].copy(), ntiles
+
+
+def render_view(grid, scene, centre, radiance, use_eps=True, want_abs=True, want_w=False,
+                want_spectra=True):
+    """Render one view for all receivers of `radiance` [N,K,C,2].
+
+    Returns dict(spectra[N,H,W,C,2] f64, absacc[N,H,W,C] f64,
+    ncontrib[H,W] i32, Tfinal[H,W] f32, T64[H,W] f64, Wvis[K] f64 or None)."""
+    g = make_grid(grid)
+    rad = _c64(radiance)
+    N, K, C = rad.shape[0], rad.shape[1], rad.shape[2]
+    assert K == scene.K
+    H, W = grid.H, grid.W
+    spec = np.zeros((N, H, W, C, 2), np.float64) if want_spectra else None
+    aab = np.zeros((N, H, W, C), np.float64) if want_abs else None
+    ncon = np.zeros((H, W), np.int32)
+    Tf = np.zeros((H, W), np.float32)
+    T64 = np.zeros((H, W), np.float64)
+    Wv = np.zeros(K, np.float64) if want_w else None
+    rc = lib().or_render_view(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                              _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                              N, C, _p(rad), _p(spec), _p(aab), _p(ncon), _p(Tf), _p(T64), _p(Wv),
+                              1 if use_eps else 0)
+    if rc != 0:
+        raise MemoryError("oracle render failed")
+    return dict(spectra=spec, absacc=aab, ncontrib=ncon, Tfinal=Tf, T64=T64, Wvis=Wv)
+
+
+def render_pixels(grid, scene, centre, radiance, pix):
+    """Render only the pixels pix[np] (= i*W + jj).  Returns
+    (values[np,N,C,2], absacc[np,N,C], ncontrib[np], Tfinal[np])."""
+    g = make_grid(grid)
+    rad = _c64(radiance)
+    N, K, C = rad.shape[0], rad.shape[1], rad.shape[2]
+    pix = np.ascontiguousarray(pix, dtype=np.int32)
+    npx = pix.shape[0]
+    out = np.zeros((npx, N, C, 2), np.float64)
+    aab = np.zeros((npx, N, C), np.float64)
+    ncon = np.zeros(npx, np.int32)
+    Tf = np.zeros(npx, np.float32)
+    rc = lib().or_render_pixels(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                                _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                                N, C, _p(rad), npx, _p(pix), _p(out), _p(aab), _p(ncon), _p(Tf))
+    if rc != 0:
+        raise MemoryError("oracle render failed")
+    return out, aab, ncon, Tf
+
+
+def backward_view(grid, scene, centre, radiance, gspec, use_eps=True):
+    """dL/d radiance [N,K,C,2] and dL/d opacity [K] for cotangent gspec
+    [N,H,W,C,2] on the spectra of one view."""
+    g = make_grid(grid)
+    rad = _c64(radiance)
+    N, K, C = rad.shape[0], rad.shape[1], rad.shape[2]
+    gr = np.zeros_like(rad)
+    gt = np.zeros(K, np.float64)
+    rc = lib().or_backward_view(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                                _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                                N, C, _p(rad), _p(_c64(gspec)), _p(gr), _p(gt), 1 if use_eps else 0)
+    if rc != 0:
+        raise MemoryError("oracle backward failed")
+    return gr, gt
+
+
+# ------------------------------------------------------------- reductions
+
+def amplitude(spec):
+    """|R| = sqrt(Re^2 + Im^2 + 1e-8)   (App. E.2)."""
+    return np.sqrt(spec[..., 0] ** 2 + spec[..., 1] ** 2 + 1e-8)
+
+
+def csi(spec):
+    """Coherent sum over all directions: [N,H,W,C,2] -> [N,C,2] (Def. 2)."""
+    return spec.sum(axis=(1, 2))
+
+
+def rssi(spec):
+    """|sum over directions| of the single channel: [N,H,W,1,2] -> [N]."""
+    s = csi(spec)[:, 0, :]
+    return np.sqrt(s[:, 0] ** 2 + s[:, 1] ** 2)
+
+
+# ------------------------------------------------- conditioning MLP (f64)
+
+def _bf16(a):
+    """Round float64 -> float32 -> bfloat16 (nearest even), back to float64."""
+    x = np.ascontiguousarray(a, dtype=np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    b = ((b + 0x7FFF + lsb) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _cmul(a, b):
+    return np.stack([a[..., 0] * b[..., 0] - a[..., 1] * b[..., 1],
+                     a[..., 0] * b[..., 1] + a[..., 1] * b[..., 0]], axis=-1)
+
+
+def _mlp(x, w1, b1, w2, b2, bf16):
+    if bf16:
+        x, w1, w2 = _bf16(x), _bf16(w1), _bf16(w2)
+    h = np.maximum(x @ w1.T + b1, 0.0)
+    if bf16:
+        h = _bf16(h)
+    return h @ w2.T + b2, h
+
+
+def local_features(rx, means):
+    """[v_hat (3), d, T=1, rho_bar=0] per (receiver, Gaussian): v_hat points
+    from the Gaussian to the receiver (Eq. local); occlusion features are
+    held at 'clear' (T = 1, rho_bar = 0)."""
+    r = np.asarray(rx, np.float64)[:, None, :]
+    p = np.asarray(means, np.float64)[None, :, :]
+    v = r - p
+    d = np.sqrt((v ** 2).sum(-1, keepdims=True))
+    vh = v / d
+    one = np.ones_like(d)
+    zero = np.zeros_like(d)
+    return np.concatenate([vh, d, one, zero], axis=-1)
+
+
+def mlp_radiance(params, rx, means, base, bf16=False):
+    """Receiver-conditioned radiance [N,K,C,2] (Eq. film, film_apply, local,
+    combined_local): s = (1 + a_l) * ((1 + a_g) * phi_base + b_g) + b_l with
+    complex products; each branch is Linear -> ReLU -> Linear with outputs
+    (a.re, a.im, b.re, b.im) per channel."""
+    P = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    base = np.asarray(base, np.float64)
+    K, C = base.shape[0], base.shape[1]
+    rx = np.asarray(rx, np.float64)
+    og, _ = _mlp(rx, P["g_w1"], P["g_b1"], P["g_w2"], P["g_b2"], bf16)        # [N,4C]
+    ol, _ = _mlp(local_features(rx, means), P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], bf16)
+    og = og.reshape(-1, 1, C, 4)
+    ol = ol.reshape(rx.shape[0], K, C, 4)
+    one = np.array([1.0, 0.0])
+    u = _cmul(one + og[..., 0:2], base[None]) + og[..., 2:4]
+    return _cmul(one + ol[..., 0:2], u) + ol[..., 2:4]
+
+
+def mlp_backward(params, rx, means, base, grad_s):
+    """Gradients of sum(grad_s * s) w.r.t. phi_base [K,C,2] and every MLP
+    parameter (float64, same names as `params`).
+
+    With complex products z = a b, dL/da = g conj(b) and dL/db = g conj(a)."""
+    P = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    base = np.asarray(base, np.float64)
+    rx = np.asarray(rx, np.float64)
+    g = np.asarray(grad_s, np.float64)                       # [N,K,C,2]
+    N, K, C = g.shape[0], g.shape[1], g.shape[2]
+    xg = rx
+    og, hg = _mlp(xg, P["g_w1"], P["g_b1"], P["g_w2"], P["g_b2"], False)
+    xl = local_features(rx, means)
+    ol, hl = _mlp(xl, P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], False)
+    og4 = og.reshape(N, 1, C, 4)
+    ol4 = ol.reshape(N, K, C, 4)
+    one = np.array([1.0, 0.0])
+
+    def conj(a):
+        return np.stack([a[..., 0], -a[..., 1]], axis=-1)
+
+    ag = one + og4[..., 0:2]
+    al = one + ol4[..., 0:2]
+    u = _cmul(ag, base[None]) + og4[..., 2:4]
+    d_al = _cmul(g, conj(u))                  # dL/d a_l
+    d_bl = g                                  # dL/d b_l
+    d_u = _cmul(g, conj(al))
+    d_ag = _cmul(d_u, conj(np.broadcast_to(base[None], d_u.shape))).sum(axis=1)   # [N,C,2]
+    d_bg = d_u.sum(axis=1)
+    d_base = _cmul(d_u, conj(np.broadcast_to(ag, d_u.shape))).sum(axis=0)         # [K,C,2]
+    d_ol = np.concatenate([d_al, d_bl], axis=-1).reshape(N, K, 4 * C)
+    d_og = np.concatenate([d_ag, d_bg], axis=-1).reshape(N, 4 * C)
+    out = {"base": d_base}
+    # local branch
+    out["l_w2"] = np.einsum("nko,nkh->oh", d_ol, hl)
+    out["l_b2"] = d_ol.sum(axis=(0, 1))
+    d_hl = (d_ol @ P["l_w2"]) * (hl > 0)
+    out["l_w1"] = np.einsum("nkh,nki->hi", d_hl, xl)
+    out["l_b1"] = d_hl.sum(axis=(0, 1))
+    # global branch
+    out["g_w2"] = d_og.T @ hg
+    out["g_b2"] = d_og.sum(axis=0)
+    d_hg = (d_og @ P["g_w2"]) * (hg > 0)
+    out["g_w1"] = d_hg.T @ xg
+    out["g_b1"] = d_hg.sum(axis=0)
+    return out

@@ -1,0 +1,483 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a library routine (scipy rotations, torch autograd, numpy complex
+arithmetic), brute force, an identity of the method, or finite differences.
+None needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2605_24290_gb300 import synthetic as S
+
+
+def tiny_scene(seed=1, K=48, pole=True, seam=True):
+    """K Gaussians around a transmitter at (5,4,1), including some near the
+    azimuth seam (phi ~ 0 / 360 deg) and some near the zenith."""
+    rng = np.random.default_rng(seed)
+    tx = np.array([5.0, 4.0, 1.0])
+    d = rng.uniform(1.0, 4.0, size=K)
+    az = rng.uniform(0, 2 * math.pi, size=K)
+    el = rng.uniform(-0.2, 1.4, size=K)
+    if seam:
+        az[:6] = rng.uniform(-0.15, 0.15, size=6)
+    if pole:
+        el[6:10] = rng.uniform(1.45, 1.56, size=4)
+    p = tx + np.stack([d * np.cos(el) * np.cos(az), d * np.cos(el) * np.sin(az), d * np.sin(el)], -1)
+    sc = S.Scene(S.f32(p), S.f32(rng.normal(-1.6, 0.4, size=(K, 3))), S.f32(rng.normal(size=(K, 4))),
+                 S.f32(1 / (1 + np.exp(-rng.normal(size=K)))))
+    return sc, S.f32(tx)
+
+
+def tiny_grid(**kw):
+    g = S.Grid(H=18, W=36, theta0_deg=-10.0, step_deg=10.0, tile_h=6, tile_w=6)
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+# ------------------------------------------------------ float32 exp / atan2
+
+def test_exp32_within_one_ulp(oracle):
+    xs = np.concatenate([np.linspace(-86.9, 88.0, 40001),
+                         np.random.default_rng(0).uniform(-4.5, 0.0, 40000)]).astype(np.float32)
+    got = np.array([oracle.exp32(float(x)) for x in xs], np.float64)
+    ref = np.exp(xs.astype(np.float64))
+    ulp = np.abs(got - ref) / np.spacing(ref.astype(np.float32)).astype(np.float64)
+    assert ulp.max() <= 1.0
+    assert oracle.exp32(0.0) == 1.0
+
+
+def test_atan2_32_within_four_ulp(oracle):
+    rng = np.random.default_rng(2)
+    ys = rng.normal(size=(20000, 2)).astype(np.float32)
+    axes = np.array([[0, 1], [1, 0], [0, -1], [-1, 0], [1, 1], [-1, -1], [1, -1], [-1, 1],
+                     [1e-7, 1], [1, 1e-7], [-1e-7, -1]], np.float32)
+    ys = np.concatenate([ys, axes])
+    got = np.array([oracle.atan2_32(float(y), float(x)) for y, x in ys], np.float64)
+    ref = np.arctan2(ys[:, 0].astype(np.float64), ys[:, 1].astype(np.float64))
+    ulp = np.abs(got - ref) / np.spacing(np.maximum(np.abs(ref), 1e-30).astype(np.float32))
+    assert ulp.max() <= 4.0
+
+
+# ------------------------------------------------------------- covariance
+
+def test_covariance_matches_rotation_library(oracle):
+    """Sigma = R S S^T R^T (App. E.1) against scipy's quaternion rotation."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(3)
+    s = S.f32(rng.normal(-2, 0.5, size=(50, 3)))
+    q = S.f32(rng.normal(size=(50, 4)))
+    c64 = oracle.cov64(s, q)
+    c32 = oracle.cov32(s, q)
+    for k in range(50):
+        R = Rotation.from_quat(q[k].astype(np.float64), scalar_first=True).as_matrix()
+        Sig = R @ np.diag(np.exp(2 * s[k].astype(np.float64))) @ R.T
+        ref = Sig[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+        scale = np.abs(Sig).max()
+        assert np.abs(c64[k] - ref).max() <= 1e-13 * scale
+        assert np.abs(c32[k] - ref).max() <= 2e-6 * scale
+
+
+# ------------------------------------------------------------- projection
+
+def _angles(u):
+    h = math.hypot(u[0], u[1])
+    return np.array([math.atan2(u[2], h), math.atan2(u[1], u[0])])
+
+
+def test_projection_isotropic_closed_form(oracle):
+    """An isotropic Gaussian of std sigma at distance rho projects to
+    Sigma2D = diag((sigma/(rho D))^2, (sigma/(h D))^2) in pixel units,
+    h = horizontal distance: the elevation and azimuth axes are orthogonal
+    with arc lengths rho*dtheta and h*dphi."""
+    g = S.Grid(step_deg=1.0)
+    D = math.radians(1.0)
+    for u, sig in [((3.0, 0.0, 0.0), 0.2), ((1.0, -2.0, 1.5), 0.1), ((-0.5, 0.3, 2.0), 0.05)]:
+        S6 = np.array([sig * sig, 0, 0, sig * sig, 0, sig * sig])
+        out = oracle.sigma2d64(g, np.array(u, np.float32), S6, np.zeros(3, np.float32))
+        uu = np.array(u, np.float32).astype(np.float64)
+        rho, h = np.linalg.norm(uu), math.hypot(uu[0], uu[1])
+        assert out[0] == pytest.approx((sig / (rho * D)) ** 2, rel=1e-12)
+        assert out[2] == pytest.approx((sig / (h * D)) ** 2, rel=1e-12)
+        assert abs(out[1]) <= 1e-12 * out[0]
+
+
+def test_projection_matches_finite_difference_jacobian(oracle):
+    """J Sigma J^T with J from central differences of the angle map."""
+    g = S.Grid(step_deg=1.0)
+    D = math.radians(1.0)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        u = rng.normal(size=3) * 3
+        u32 = u.astype(np.float32)
+        uu = u32.astype(np.float64)
+        A = rng.normal(size=(3, 3)) * 0.2
+        Sig = A @ A.T + 1e-3 * np.eye(3)
+        J = np.zeros((2, 3))
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = 1e-6
+            J[:, i] = (_angles(uu + e) - _angles(uu - e)) / 2e-6
+        J /= D
+        ref = J @ Sig @ J.T
+        S6 = Sig[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+        out = oracle.sigma2d64(g, u32, S6, np.zeros(3, np.float32))
+        np.testing.assert_allclose(out, [ref[0, 0], ref[0, 1], ref[1, 1]], rtol=1e-6,
+                                   atol=1e-7 * abs(ref).max())
+
+
+def test_projection_matches_monte_carlo(oracle):
+    """A small Gaussian's samples, mapped to angles, have the projected
+    covariance (the local linearisation the projection takes)."""
+    g = S.Grid(step_deg=1.0)
+    D = math.radians(1.0)
+    rng = np.random.default_rng(5)
+    u = np.array([2.0, 1.0, 0.7], np.float32)
+    A = rng.normal(size=(3, 3)) * 0.02
+    Sig = A @ A.T
+    X = rng.multivariate_normal(u.astype(np.float64), Sig, size=200000)
+    h = np.hypot(X[:, 0], X[:, 1])
+    ang = np.stack([np.arctan2(X[:, 2], h), np.arctan2(X[:, 1], X[:, 0])], -1) / D
+    emp = np.cov(ang.T)
+    S6 = Sig[[0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+    out = oracle.sigma2d64(g, u, S6, np.zeros(3, np.float32))
+    np.testing.assert_allclose([emp[0, 0], emp[0, 1], emp[1, 1]], out, rtol=0.03,
+                               atol=0.03 * max(out[0], out[2]))
+
+
+# ------------------------------------------------------------- compositing
+
+def _unit_radiance(N, K, C=1):
+    r = np.zeros((N, K, C, 2))
+    r[..., 0] = 1.0
+    return r
+
+
+def test_single_gaussian_closed_form(oracle):
+    """One Gaussian: spectrum = tau exp(-q/2) s on the pixels it covers, q
+    from the inverse of the finite-difference Sigma2D; zero elsewhere."""
+    g = S.Grid(H=90, W=360)
+    D = math.radians(1.0)
+    tx = np.array([0.0, 0.0, 0.0], np.float32)
+    p = np.array([[2.0, 1.0, 1.2]], np.float32)
+    sc = S.Scene(p, S.f32([[-1.5, -1.9, -1.7]]), S.f32([[0.9, 0.2, -0.3, 0.1]]), S.f32([0.7]))
+    s = np.array([[[[0.3, -1.1]]]])
+    out = oracle.render_view(g, sc, tx, s)
+    spec = out["spectra"][0, :, :, 0, :]
+    Sig = oracle.cov64(sc.log_scales, sc.quats)[0]
+    Sg = np.array([[Sig[0], Sig[1], Sig[2]], [Sig[1], Sig[3], Sig[4]], [Sig[2], Sig[4], Sig[5]]])
+    uu = p[0].astype(np.float64)
+    J = np.zeros((2, 3))
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1e-6
+        J[:, i] = (_angles(uu + e) - _angles(uu - e)) / 2e-6
+    J /= D
+    conic = np.linalg.inv(J @ Sg @ J.T)
+    c_ang = _angles(uu) / D
+    ii, jj = np.meshgrid(np.arange(90), np.arange(360), indexing="ij")
+    dth = ii - c_ang[0]
+    dph = (jj - c_ang[1] + 180) % 360 - 180
+    q = conic[0, 0] * dth ** 2 + 2 * conic[0, 1] * dth * dph + conic[1, 1] * dph ** 2
+    w = 0.7 * np.exp(-0.5 * q)
+    covered = out["ncontrib"] == 1
+    assert out["ncontrib"].max() == 1
+    # the pixels the oracle composites are exactly those with q <= 9 (away from the edge)
+    assert np.all(covered[q < 9 - 1e-4])
+    assert not np.any(covered[q > 9 + 1e-4])
+    ref = np.where(covered, w, 0.0)
+    np.testing.assert_allclose(spec[..., 0], ref * 0.3, rtol=1e-7, atol=1e-12)
+    np.testing.assert_allclose(spec[..., 1], ref * -1.1, rtol=1e-7, atol=1e-12)
+
+
+def test_transmittance_telescoping_identity(oracle):
+    """With s = 1 for every Gaussian, sum_k T_k w_k = 1 - prod_k (1 - w_k):
+    the composited signal plus the final transmittance is exactly 1."""
+    sc, tx = tiny_scene(7, K=64)
+    g = tiny_grid(eps_T=0.0)
+    out = oracle.render_view(g, sc, tx, _unit_radiance(1, sc.K), use_eps=False)
+    tot = out["spectra"][0, :, :, 0, 0] + out["T64"]
+    np.testing.assert_allclose(tot, 1.0, rtol=0, atol=1e-13)
+    assert np.all(out["spectra"][0, :, :, 0, 1] == 0.0)
+    # with the stop on, the final shadow transmittance is below eps exactly
+    # where the loop stopped early
+    g2 = tiny_grid(eps_T=0.5)
+    o2 = oracle.render_view(g2, sc, tx, _unit_radiance(1, sc.K))
+    stopped = o2["Tfinal"] < np.float32(0.5)
+    assert stopped.any() and (~stopped).any()
+    np.testing.assert_allclose(o2["spectra"][0, :, :, 0, 0] + o2["T64"], 1.0, atol=1e-13)
+
+
+def test_linearity_in_radiance(oracle):
+    sc, tx = tiny_scene(8)
+    g = tiny_grid()
+    rng = np.random.default_rng(9)
+    r1 = rng.normal(size=(2, sc.K, 2, 2))
+    r2 = rng.normal(size=(2, sc.K, 2, 2))
+    a = oracle.render_view(g, sc, tx, r1)["spectra"]
+    b = oracle.render_view(g, sc, tx, r2)["spectra"]
+    c = oracle.render_view(g, sc, tx, 2.0 * r1 - 0.5 * r2)["spectra"]
+    np.testing.assert_allclose(c, 2.0 * a - 0.5 * b, rtol=1e-12, atol=1e-12)
+
+
+def test_two_gaussians_front_to_back_and_stop(oracle):
+    """Two Gaussians on the same ray at q = 0: C = tau1 s1 + (1-tau1) tau2 s2;
+    the stop comes after the contribution that crosses eps (Algorithm 1)."""
+    tx = np.zeros(3, np.float32)
+    p = S.f32([[4.0, 0.0, 0.0], [2.0, 0.0, 0.0]])     # index 1 is nearer
+    sc = S.Scene(p, S.f32([[-2.0] * 3, [-2.0] * 3]), S.f32([[1, 0, 0, 0], [1, 0, 0, 0]]),
+                 S.f32([0.6, 0.5]))
+    rad = np.array([[[[1.0, 2.0]], [[-3.0, 0.5]]]])    # s_far, s_near
+    g = S.Grid(H=90, W=360)
+    out = oracle.render_view(g, sc, tx, rad)
+    got = out["spectra"][0, 0, 0, 0]
+    t_far, t_near = float(np.float32(0.6)), float(np.float32(0.5))
+    ref = t_near * np.array([-3.0, 0.5]) + (1 - t_near) * t_far * np.array([1.0, 2.0])
+    np.testing.assert_allclose(got, ref, rtol=1e-15)
+    assert out["ncontrib"][0, 0] == 2
+    g.eps_T = 0.6        # T after the near one is 0.5 < 0.6: stop there
+    out = oracle.render_view(g, sc, tx, rad)
+    np.testing.assert_allclose(out["spectra"][0, 0, 0, 0], t_near * np.array([-3.0, 0.5]), rtol=1e-15)
+    assert out["ncontrib"][0, 0] == 1
+
+
+def test_golden_two_gaussian_fixture(oracle):
+    """tests/golden/two_gaussians.txt: hand-derived values of the case above
+    (Algorithm 1, Stage 3)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "two_gaussians.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    tx = np.zeros(3, np.float32)
+    p = S.f32([[4.0, 0.0, 0.0], [2.0, 0.0, 0.0]])
+    sc = S.Scene(p, S.f32([[-2.0] * 3, [-2.0] * 3]), S.f32([[1, 0, 0, 0], [1, 0, 0, 0]]),
+                 S.f32([0.75, 0.5]))
+    rad = np.array([[[[1.0, 2.0]], [[-3.0, 0.5]]]])
+    out = oracle.render_view(S.Grid(H=90, W=360), sc, tx, rad)
+    assert out["spectra"][0, 0, 0, 0, 0] == pytest.approx(vals["re"], abs=1e-15)
+    assert out["spectra"][0, 0, 0, 0, 1] == pytest.approx(vals["im"], abs=1e-15)
+    assert out["T64"][0, 0] == pytest.approx(vals["T"], abs=1e-15)
+
+
+def test_tiled_lists_equal_brute_force(oracle):
+    """Per-tile lists hold exactly the Gaussians whose footprint meets the
+    tile, in ascending (depth, index); walking a pixel's tile list gives the
+    same sequence as walking all Gaussians in global depth order."""
+    for seed in range(3):
+        sc, tx = tiny_scene(10 + seed, K=64)
+        g = tiny_grid()
+        S6, rec, box = oracle.project_view32(g, sc, tx)
+        counts, lists, ntiles = oracle.tile_lists(g, sc, tx)
+        th, tw = 3, 6
+        vis = rec[:, 7] > 0
+        assert vis.sum() > 20
+
+        def inside(k, i, j):
+            if i < box[k, 0] or i > box[k, 1]:
+                return False
+            return (j - box[k, 2]) % g.W <= box[k, 3]
+
+        # independent tile sets by enumeration
+        sets = [set() for _ in range(th * tw)]
+        for k in np.nonzero(vis)[0]:
+            for i in range(g.H):
+                for j in range(g.W):
+                    if inside(k, i, j):
+                        sets[(i // g.tile_h) * tw + j // g.tile_w].add(int(k))
+        off = np.concatenate([[0], np.cumsum(counts)])
+        for t in range(th * tw):
+            lt = list(lists[off[t]:off[t + 1]])
+            assert set(lt) == sets[t]
+            assert lt == sorted(lt, key=lambda k: (rec[k, 6], k))
+        for k in range(sc.K):
+            assert ntiles[k] == sum(k in s_ for s_ in sets)
+        glob = sorted(np.nonzero(vis)[0], key=lambda k: (rec[k, 6], k))
+        for i in range(g.H):
+            for j in range(g.W):
+                t = (i // g.tile_h) * tw + j // g.tile_w
+                a = [k for k in lists[off[t]:off[t + 1]] if inside(k, i, j)]
+                b = [k for k in glob if inside(k, i, j)]
+                assert a == b
+        # wrap and pole cases were exercised
+        assert (box[vis, 3] == g.W - 1).any()
+        assert ((box[vis, 2] + box[vis, 3]) >= g.W).any()
+
+
+def test_render_reorder_identity(oracle):
+    """Eq. render_reorder: sum over directions of C^(j) = sum_k W_k s_kj with
+    receiver-independent W_k = sum_omega T_k w_k."""
+    sc, tx = tiny_scene(14, K=64)
+    g = tiny_grid()
+    rng = np.random.default_rng(15)
+    rad = rng.normal(size=(3, sc.K, 2, 2))
+    out = oracle.render_view(g, sc, tx, rad, want_w=True)
+    lhs = oracle.csi(out["spectra"])
+    rhs = np.einsum("k,nkcr->ncr", out["Wvis"], rad)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+
+
+def test_amplitude_and_reductions(oracle):
+    spec = np.zeros((1, 2, 2, 1, 2))
+    spec[0, 0, 0, 0] = [3.0, 4.0]
+    spec[0, 1, 1, 0] = [-1.0, 0.0]
+    assert oracle.amplitude(spec)[0, 0, 0, 0] == pytest.approx(math.sqrt(25 + 1e-8))
+    assert oracle.amplitude(spec)[0, 0, 1, 0] == pytest.approx(1e-4)
+    assert oracle.rssi(spec)[0] == pytest.approx(math.sqrt(4 + 16))
+
+
+# ------------------------------------------------------------------- MLP
+
+def _torch_mlp(params, rx, means, base):
+    torch = pytest.importorskip("torch")
+    P = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in params.items()}
+    rx_t = torch.tensor(np.asarray(rx, np.float64))
+    p_t = torch.tensor(np.asarray(means, np.float64))
+    b = torch.tensor(np.asarray(base, np.float64), requires_grad=True)
+    C = base.shape[1]
+
+    def mlp(x, pre):
+        h = torch.relu(torch.nn.functional.linear(x, P[pre + "_w1"], P[pre + "_b1"]))
+        return torch.nn.functional.linear(h, P[pre + "_w2"], P[pre + "_b2"])
+
+    og = mlp(rx_t, "g").reshape(-1, 1, C, 4)
+    v = rx_t[:, None, :] - p_t[None]
+    d = torch.linalg.norm(v, dim=-1, keepdim=True)
+    feat = torch.cat([v / d, d, torch.ones_like(d), torch.zeros_like(d)], -1)
+    ol = mlp(feat, "l").reshape(rx_t.shape[0], -1, C, 4)
+    cz = lambda a: torch.complex(a[..., 0], a[..., 1])
+    phi = cz(b)[None]
+    s = (1 + cz(ol[..., 0:2])) * ((1 + cz(og[..., 0:2])) * phi + cz(og[..., 2:4])) + cz(ol[..., 2:4])
+    return torch.stack([s.real, s.imag], -1), P, b
+
+
+def test_mlp_zero_init_is_identity(oracle):
+    """Both branches zero-initialised: s = phi_base (Sec. 3.3.2)."""
+    rng = np.random.default_rng(20)
+    C = 3
+    params = {k: np.zeros(v.shape) for k, v in S.draw_mlp(rng, C).items()}
+    base = rng.normal(size=(10, C, 2))
+    s = oracle.mlp_radiance(params, rng.normal(size=(4, 3)), rng.normal(size=(10, 3)), base)
+    np.testing.assert_array_equal(s, np.broadcast_to(base[None], s.shape))
+
+
+def test_mlp_affine_reproduces_propagation_factor(oracle):
+    """Corollary 2: with alpha = eta_eff - 1 and beta = 0 the affine
+    modulation is the complex product eta_eff * phi_base.  The MLP outputs
+    are made constant (zero hidden weights, set biases) and compared with
+    numpy complex arithmetic."""
+    rng = np.random.default_rng(21)
+    C = 2
+    params = {k: np.zeros(v.shape) for k, v in S.draw_mlp(rng, C).items()}
+    lam, d = 0.125, 3.7
+    eta = lam / (4 * math.pi * d) * np.exp(-2j * math.pi / lam * d)
+    params["l_b2"] = np.tile([eta.real - 1.0, eta.imag, 0.0, 0.0], C)
+    base = rng.normal(size=(5, C, 2))
+    s = oracle.mlp_radiance(params, rng.normal(size=(2, 3)), rng.normal(size=(5, 3)), base)
+    ref = eta * (base[..., 0] + 1j * base[..., 1])
+    np.testing.assert_allclose(s[..., 0], np.broadcast_to(ref.real, s.shape[:-1]), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(s[..., 1], np.broadcast_to(ref.imag, s.shape[:-1]), rtol=1e-13, atol=1e-15)
+    # global branch alone: (1 + a_g) phi + b_g
+    params = {k: np.zeros(v.shape) for k, v in S.draw_mlp(rng, C).items()}
+    params["g_b2"] = np.tile([0.2, -0.3, 0.05, 0.4], C)
+    s = oracle.mlp_radiance(params, rng.normal(size=(2, 3)), rng.normal(size=(5, 3)), base)
+    ref = (1.2 - 0.3j) * (base[..., 0] + 1j * base[..., 1]) + (0.05 + 0.4j)
+    np.testing.assert_allclose(s[0, ..., 0], ref.real, rtol=1e-13)
+    np.testing.assert_allclose(s[0, ..., 1], ref.imag, rtol=1e-13)
+
+
+def test_mlp_matches_torch(oracle):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(22)
+    C = 3
+    params = S.draw_mlp(rng, C, final_scale=1.0)
+    rx, means, base = rng.normal(size=(4, 3)) * 3, rng.normal(size=(7, 3)) * 3, rng.normal(size=(7, C, 2))
+    s = oracle.mlp_radiance(params, rx, means, base)
+    st, _, _ = _torch_mlp(params, rx, means, base)
+    np.testing.assert_allclose(s, st.detach().numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_backward_matches_torch_autograd(oracle):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(23)
+    C = 2
+    params = S.draw_mlp(rng, C, final_scale=1.0)
+    rx, means, base = rng.normal(size=(3, 3)) * 3, rng.normal(size=(6, 3)) * 3, rng.normal(size=(6, C, 2))
+    g = rng.normal(size=(3, 6, C, 2))
+    st, P, b = _torch_mlp(params, rx, means, base)
+    (st * torch.tensor(g)).sum().backward()
+    got = oracle.mlp_backward(params, rx, means, base, g)
+    np.testing.assert_allclose(got["base"], b.grad.numpy(), rtol=1e-11, atol=1e-12)
+    for k in params:
+        np.testing.assert_allclose(got[k], P[k].grad.numpy(), rtol=1e-11, atol=1e-12)
+
+
+def test_mlp_bf16_rounding_matches_torch(oracle):
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(24).normal(size=1000) * 10
+    got = oracle._bf16(x)
+    ref = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+# -------------------------------------------------------------- backward
+
+def test_render_backward_matches_finite_differences(oracle):
+    """The oracle's analytic gradients against central differences of its
+    own forward, with the early stop off so no decision can flip; q and the
+    footprint do not depend on radiance or opacity."""
+    sc, tx = tiny_scene(30, K=40)
+    g = tiny_grid()
+    rng = np.random.default_rng(31)
+    N, C = 2, 2
+    rad = rng.normal(size=(N, sc.K, C, 2))
+    gs = rng.normal(size=(N, g.H, g.W, C, 2))
+    gr, gt = oracle.backward_view(g, sc, tx, rad, gs, use_eps=False)
+
+    def loss(scene, r):
+        return float((oracle.render_view(g, scene, tx, r, use_eps=False, want_abs=False)["spectra"]
+                      * gs).sum())
+
+    # radiance: linear, so a unit step is exact
+    for _ in range(12):
+        idx = tuple(rng.integers(0, s_) for s_ in rad.shape)
+        rp, rm = rad.copy(), rad.copy()
+        rp[idx] += 0.5
+        rm[idx] -= 0.5
+        fd = loss(sc, rp) - loss(sc, rm)
+        assert fd == pytest.approx(gr[idx], rel=1e-9, abs=1e-9)
+    # opacity (float32 input): central difference over exactly representable steps
+    vis = np.nonzero(np.abs(gt) > 0)[0]
+    assert len(vis) > 10
+    for k in vis[:15]:
+        tp, tm = sc.opacity.copy(), sc.opacity.copy()
+        tp[k] = np.float32(tp[k] + 1e-3)
+        tm[k] = np.float32(tm[k] - 1e-3)
+        sp = S.Scene(sc.means, sc.log_scales, sc.quats, tp)
+        sm = S.Scene(sc.means, sc.log_scales, sc.quats, tm)
+        fd = (loss(sp, rad) - loss(sm, rad)) / (float(tp[k]) - float(tm[k]))
+        assert fd == pytest.approx(gt[k], rel=2e-5, abs=1e-7)
+
+
+def test_render_backward_with_stop_matches_fd_of_fixed_sequence(oracle):
+    """With the stop on, the gradient w.r.t. radiance is still exact (the
+    sequence does not depend on radiance)."""
+    sc, tx = tiny_scene(32, K=40)
+    g = tiny_grid(eps_T=0.02)
+    rng = np.random.default_rng(33)
+    rad = rng.normal(size=(1, sc.K, 1, 2))
+    gs = rng.normal(size=(1, g.H, g.W, 1, 2))
+    gr, _ = oracle.backward_view(g, sc, tx, rad, gs, use_eps=True)
+    base = oracle.render_view(g, sc, tx, rad)["spectra"]
+    for _ in range(8):
+        idx = tuple(rng.integers(0, s_) for s_ in rad.shape)
+        rp = rad.copy()
+        rp[idx] += 1.0
+        d = ((oracle.render_view(g, sc, tx, rp)["spectra"] - base) * gs).sum()
+        assert d == pytest.approx(gr[idx], rel=1e-9, abs=1e-9)
