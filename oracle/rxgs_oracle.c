@@ -236,6 +236,7 @@ void or_project32(const or_grid* g, const float p[3], float tau, const float S[6
   if (hi > (float)(g->H - 1)) hi = (float)(g->H - 1);
   if (!(lo <= hi)) return;
   float clo = ceilf(phi_px - ep), chi = floorf(phi_px + ep);
+  if (!(clo <= chi)) return;   /* no column centre inside the footprint */
   int j_lo, span;
   if (chi - clo >= Wf - 1.0f) {
     j_lo = 0; span = g->W - 1;

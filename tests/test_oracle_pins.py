@@ -298,6 +298,8 @@ def test_tiled_lists_equal_brute_force(oracle):
             assert lt == sorted(lt, key=lambda k: (rec[k, 6], k))
         for k in range(sc.K):
             assert ntiles[k] == sum(k in s_ for s_ in sets)
+        # a Gaussian is kept only if its footprint holds at least one pixel
+        assert np.all(ntiles[vis] >= 1)
         glob = sorted(np.nonzero(vis)[0], key=lambda k: (rec[k, 6], k))
         for i in range(g.H):
             for j in range(g.W):
