@@ -1,0 +1,227 @@
+/*
+ * rxgs.h -- C ABI of the GB300 multi-receiver RF Gaussian renderer.
+ *
+ * The library renders a frozen set of 3D Gaussians, as seen from one or
+ * more transmitters, at many receivers at once.  For every transmitter it
+ * projects the Gaussians onto an elevation x azimuth grid centred at the
+ * transmitter, bins them into tiles and depth-sorts each tile once; all
+ * receivers of that transmitter share this work and differ only in their
+ * radiance, which is alpha-composited front to back into a complex spectrum
+ * per receiver and optionally reduced to RSSI or per-subcarrier CSI.
+ *
+ *   Problem statement  S(t, r) = f(t, r; Theta)           (Sec. 3, Eq. 3)
+ *   Transmitter side   projection, tiles, depth sort       (Algorithm 1, Stage 1)
+ *   Receiver side      per-receiver radiance s_k^(j)       (Algorithm 1, Stage 2;
+ *                      Sec. 3.3.2, Eq. film, local, combined_local)
+ *   Compositing        w = tau exp(-q/2), C += T w s,
+ *                      T *= (1 - w), stop when T < eps     (Algorithm 1, Stage 3)
+ *   Amplitude          |R| = sqrt(Re^2 + Im^2 + 1e-8)      (App. E.2)
+ *   RSSI / CSI         coherent sum over directions        (Def. 2, Eq. render)
+ *   Backward           dL/d radiance, dL/d opacity         (App. D)
+ *
+ * Conventions shared by every call.
+ *   - Grid: row i has elevation theta0 + i*step, column j has azimuth j*step
+ *     (degrees); W*step must equal 360.  Pixels are the left/bottom grid
+ *     points.
+ *   - Complex numbers are two consecutive float32 (real, imaginary).
+ *   - Unless a field says otherwise, pointers are DEVICE pointers on the
+ *     current CUDA device, owned by the caller, and must stay valid until
+ *     the work on `stream` has finished.  `stream` is a cudaStream_t (NULL =
+ *     legacy default stream).  Calls enqueue work and return; device-side
+ *     problems surface as RXGS_E_DEVICE from the next call that
+ *     synchronises (rxgs_prepare, rxgs_sync, the serving calls).
+ *   - A status other than RXGS_OK means nothing was enqueued, except for
+ *     RXGS_E_CUDA / RXGS_E_DEVICE, which report an error of the CUDA
+ *     context; rxgs_last_error() gives a message.
+ *   - All reductions are deterministic: the same inputs give bit-identical
+ *     outputs, whatever the batch they are rendered in.
+ */
+#ifndef RXGS_H
+#define RXGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rxgs_ctx rxgs_ctx;
+typedef uint64_t rxgs_scene_t;   /* handle to a device-resident scene         */
+typedef uint64_t rxgs_views_t;   /* handle to transmitter-side (shared) state */
+typedef uint64_t rxgs_ticket_t;  /* handle to a serving request               */
+
+typedef enum {
+  RXGS_OK = 0,
+  RXGS_E_INVALID = 1,    /* bad argument; nothing enqueued                  */
+  RXGS_E_OOM = 2,        /* device allocation failed                        */
+  RXGS_E_CUDA = 3,       /* a CUDA call failed                              */
+  RXGS_E_ADMISSION = 4,  /* serving: request larger than the memory budget  */
+  RXGS_E_NOT_READY = 5,  /* serving: result not ready yet                   */
+  RXGS_E_TIMEOUT = 6,    /* serving: poll timed out                         */
+  RXGS_E_DEVICE = 7,     /* a kernel reported an error (capacity, bounds)   */
+  RXGS_E_CANCELLED = 8   /* serving: request cancelled                      */
+} rxgs_status;
+
+enum { RXGS_OUT_SPECTRA = 1, RXGS_OUT_RSSI = 2, RXGS_OUT_CSI = 4 };
+
+/* Grid and numerical options (Table 5 grids; Algorithm 1 constants). */
+typedef struct {
+  int H, W;            /* grid rows (elevation) x columns (azimuth)          */
+  float theta0_deg;    /* elevation of row 0 in degrees (0 or -90)           */
+  float step_deg;      /* angular step in degrees; W*step_deg == 360         */
+  int tile_h, tile_w;  /* tile shape; tile_h*tile_w == 256                   */
+  float eps_T;         /* stop threshold on transmittance (1e-4)             */
+  float q_max;         /* Mahalanobis cut-off q <= q_max (9 = 3 sigma)       */
+  float r_near;        /* Gaussians nearer than this to the transmitter are
+                          culled (0.05 m)                                    */
+  int cols_per_cta;    /* receiver*channel*2 columns per render CTA:
+                          16, 32, 64 or 128; 0 = chosen by the autotuner     */
+  int deterministic;   /* 1 (default): no float atomics in the forward and
+                          backward opacity gradient reductions               */
+  size_t mem_budget;   /* serving admission budget in bytes; 0 = 8 GiB      */
+} rxgs_options;
+
+/* Fills `o` with the defaults: 90x360 grid from 0 deg at 1 deg, 16x16
+ * tiles, eps 1e-4, q_max 9, r_near 0.05, autotuned columns. */
+void rxgs_default_options(rxgs_options* o);
+
+/* Creates a context on CUDA device `device`.  The context owns the scenes,
+ * views and serving state created through it.  Not thread-safe except for
+ * the serving calls.  Returns RXGS_E_INVALID for a bad option set. */
+rxgs_status rxgs_create(const rxgs_options* opts, int device, rxgs_ctx** out);
+rxgs_status rxgs_destroy(rxgs_ctx* ctx);
+const char* rxgs_last_error(rxgs_ctx* ctx);
+
+/* Scene upload (App. E.1 state: mean p, log-scale s, quaternion q = (w,x,y,z)
+ * not necessarily normalised, opacity tau in (0,1)).  The library copies the
+ * arrays into memory it owns and builds Sigma = R S S^T R^T once.
+ *   means[K,3], log_scales[K,3], quats[K,4], opacity[K]          float32
+ *   base_radiance[K,C,2]  phi_base, required when mlp_params != NULL
+ *   mlp_params            flat float32 parameters of the two conditioning
+ *                         MLPs (global: Linear(3,h) ReLU Linear(h,4C);
+ *                         local: Linear(6,h) ReLU Linear(h,4C)), in the order
+ *                         g_w1[h,3] g_b1[h] g_w2[4C,h] g_b2[4C] l_w1[h,6]
+ *                         l_b1[h] l_w2[4C,h] l_b2[4C]; NULL = no MLP
+ *   mlp_hidden            h (64)
+ *   mlp_bf16              1: matmul operands rounded to bf16, fp32 accumulate
+ *   on_device             1: pointers are device pointers; 0: host pointers */
+typedef struct {
+  int64_t K;
+  int C;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity;
+  const float* base_radiance;
+  const float* mlp_params;
+  int mlp_hidden;
+  int mlp_bf16;
+  int on_device;
+} rxgs_scene_desc;
+
+rxgs_status rxgs_upload_scene(rxgs_ctx* ctx, const rxgs_scene_desc* desc, rxgs_scene_t* out);
+rxgs_status rxgs_release_scene(rxgs_ctx* ctx, rxgs_scene_t scene);
+/* Replaces the opacity and/or phi_base / MLP parameters of a scene in place
+ * (device pointers, same shapes; NULL = keep).  Geometry stays frozen. */
+rxgs_status rxgs_update_scene(rxgs_ctx* ctx, rxgs_scene_t scene, const float* opacity,
+                              const float* base_radiance, const float* mlp_params, void* stream);
+
+/* Transmitter-side state (Algorithm 1, Stage 1): projection of every
+ * Gaussian for each of the M transmitters tx[M,3], the per-tile lists sorted
+ * by (transmitter, tile, depth) and the tile ranges.  It is shared by every
+ * receiver rendered against it.  This call reads back one integer (the
+ * instance count) and so synchronises `stream` once. */
+rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int M,
+                         rxgs_views_t* out, void* stream);
+rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream);
+
+/* What to render.
+ *   kind       RXGS_OUT_* bitmask
+ *   radiance   [N,K,C,2] receiver-major float32 (the paper's (N, K, 2)
+ *              signal tensor), shared by all transmitters; NULL = evaluate
+ *              the scene's conditioning MLP for the receivers
+ *   reduce_path for RSSI/CSI without spectra: 0 = per-pixel compositing then
+ *              a sum over pixels; 1 = visibility weights W_k (Eq.
+ *              render_reorder) then sum_k W_k s_kj.  Both give the same
+ *              value up to rounding order. */
+typedef struct {
+  int kind;
+  const float* radiance;
+  int reduce_path;
+} rxgs_render_desc;
+
+/* Outputs, all optional except those `kind` asks for:
+ *   spectra  [M,N,H,W,C,2]
+ *   rssi     [M,N]          |sum over pixels| (C must be 1)
+ *   csi      [M,N,C,2]      sum over pixels
+ *   ncontrib [M,H,W] int32  number of Gaussians composited per pixel
+ *   tfinal   [M,H,W]        transmittance after compositing */
+typedef struct {
+  float* spectra;
+  float* rssi;
+  float* csi;
+  int32_t* ncontrib;
+  float* tfinal;
+} rxgs_outputs;
+
+/* Renders every (transmitter, receiver) pair of `views` x rx[N,3]. */
+rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,
+                              const rxgs_render_desc* desc, rxgs_outputs* out, void* stream);
+
+/* rxgs_prepare + rxgs_render_views + rxgs_release_views in one call. */
+rxgs_status rxgs_render(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int M,
+                        const float* rx, int N, const rxgs_render_desc* desc,
+                        rxgs_outputs* out, void* stream);
+
+/* Backward (App. D): gradients of a loss L given dL/d(outputs).
+ *   grad_spectra [M,N,H,W,C,2] or NULL
+ *   grad_csi     [M,N,C,2] or NULL   (uniform over pixels)
+ *   grad_rssi    [M,N] or NULL       (needs fwd_csi)
+ *   fwd_spectra  the forward spectra, or NULL (then the kernel makes one
+ *                extra pass over each tile)
+ *   fwd_csi      the forward CSI [M,N,1,2] when grad_rssi is given
+ * Outputs (accumulated: caller zero-fills):
+ *   grad_radiance [N,K,C,2]  when desc->radiance != NULL
+ *   grad_opacity  [K]
+ *   grad_base     [K,C,2] and grad_mlp (flat) when the scene MLP is used
+ * Geometry (means, scales, rotations) is frozen and gets no gradient. */
+typedef struct {
+  const float* grad_spectra;
+  const float* grad_csi;
+  const float* grad_rssi;
+  const float* fwd_spectra;
+  const float* fwd_csi;
+} rxgs_cotangents;
+
+typedef struct {
+  float* grad_radiance;
+  float* grad_opacity;
+  float* grad_base;
+  float* grad_mlp;
+} rxgs_grads;
+
+rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,
+                                 const rxgs_render_desc* desc, const rxgs_cotangents* cot,
+                                 rxgs_grads* grads, void* stream);
+
+/* Inspection of transmitter-side state (for tests and tools).
+ *   n_inst   receives the number of (Gaussian, tile) instances
+ * rxgs_views_export copies (device pointers, any may be NULL):
+ *   rec[M,K,8]   float32 {theta_px, phi_px, conic_a, 2*conic_b, conic_c, tau,
+ *                rows, cols}; rows/cols are int32 bit patterns
+ *                i_lo | i_hi << 16 and j_lo | span << 16
+ *   counts[M,K]  tiles per Gaussian (0 = culled)
+ *   keys[I], vals[I]  sorted (view | tile | depth) keys and Gaussian indices
+ *   ranges[M,T,2]     [start, end) of each tile's list in keys/vals */
+rxgs_status rxgs_views_info(rxgs_ctx* ctx, rxgs_views_t views, int64_t* n_inst);
+rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uint32_t* counts,
+                              uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* stream);
+
+/* Waits for `stream` and converts a recorded device error into a status. */
+rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RXGS_H */

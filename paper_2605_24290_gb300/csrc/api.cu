@@ -1,0 +1,583 @@
+// api.cu -- the C ABI (include/rxgs.h): contexts, scenes, transmitter-side
+// views, forward and backward renders.  Device memory comes from CUDA's
+// stream-ordered pool (cudaMallocAsync / cudaFreeAsync on the caller's
+// stream); nothing here synchronises except rxgs_prepare (one readback of
+// the instance count) and rxgs_sync.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/rxgs.h"
+#include "rxgs_internal.h"
+
+using namespace rxgs;
+
+namespace {
+
+struct SceneState {
+  int K = 0, C = 0;
+  float4* geom = nullptr;   // [K][3]
+  float* base = nullptr;    // [K][C][2]
+  float* mlp = nullptr;     // flat
+  size_t mlp_floats = 0;
+  int hidden = 0, bf16 = 0;
+};
+
+struct ViewsState {
+  rxgs_scene_t scene = 0;
+  int M = 0, K = 0;
+  float* tx = nullptr;        // [M][3]
+  float4* rec = nullptr;      // [M][K][2]
+  uint32_t* depth = nullptr;  // [M][K]
+  uint32_t* counts = nullptr; // [M*K]
+  uint32_t* offsets = nullptr;// [M*K+1]
+  uint64_t* keys = nullptr;   // [I]
+  uint32_t* vals = nullptr;   // [I]
+  uint2* ranges = nullptr;    // [M][T]
+  uint32_t n_inst = 0;
+  int tile_bits = 0, view_bits = 0;
+};
+
+}  // namespace
+
+struct rxgs_ctx {
+  int device = 0;
+  rxgs_options opts{};
+  GridConst g{};
+  std::mutex mu;
+  std::string err;
+  uint64_t next_id = 1;
+  std::map<uint64_t, SceneState*> scenes;
+  std::map<uint64_t, ViewsState*> views;
+  unsigned* d_err = nullptr;      // device error word
+  uint32_t* h_pinned = nullptr;   // pinned readback slot
+};
+
+namespace {
+
+rxgs_status fail(rxgs_ctx* c, rxgs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? RXGS_E_OOM : RXGS_E_CUDA,      \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
+  if (n == 0) n = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+int bits_for(uint64_t n) {  // bits to hold values 0..n-1
+  int b = 0;
+  while ((1ull << b) < n) ++b;
+  return b;
+}
+
+rxgs_status check_last(rxgs_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, RXGS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return RXGS_OK;
+}
+
+bool make_grid(const rxgs_options& o, GridConst* g, std::string* why) {
+  if (o.H <= 0 || o.W <= 0 || o.H > 32767 || o.W > 32767) return *why = "H, W out of range", false;
+  if (!(o.step_deg > 0.0f) || std::fabs(o.W * static_cast<double>(o.step_deg) - 360.0) > 1e-3)
+    return *why = "W * step_deg must be 360", false;
+  if (o.H * static_cast<double>(o.step_deg) > 180.0 + 1e-3) return *why = "H * step_deg > 180", false;
+  if (o.tile_h <= 0 || o.tile_w <= 0 || o.tile_h * o.tile_w != 256)
+    return *why = "tile_h * tile_w must be 256", false;
+  if (!(o.q_max > 0.0f) || !(o.eps_T >= 0.0f) || !(o.r_near > 0.0f))
+    return *why = "q_max, eps_T, r_near out of range", false;
+  if (o.cols_per_cta != 0 && o.cols_per_cta != 16 && o.cols_per_cta != 32 &&
+      o.cols_per_cta != 64 && o.cols_per_cta != 128)
+    return *why = "cols_per_cta must be 0, 16, 32, 64 or 128", false;
+  g->H = o.H;
+  g->W = o.W;
+  g->TH = o.tile_h;
+  g->TW = o.tile_w;
+  g->tiles_h = (o.H + o.tile_h - 1) / o.tile_h;
+  g->tiles_w = (o.W + o.tile_w - 1) / o.tile_w;
+  g->T = g->tiles_h * g->tiles_w;
+  g->inv_step = static_cast<float>(180.0 / (3.14159265358979323846 * static_cast<double>(o.step_deg)));
+  g->theta0_px = static_cast<float>(static_cast<double>(o.theta0_deg) / static_cast<double>(o.step_deg));
+  g->Wf = static_cast<float>(o.W);
+  g->halfW = 0.5f * static_cast<float>(o.W);
+  g->Hm1f = static_cast<float>(o.H - 1);
+  g->eps_T = o.eps_T;
+  g->q_max = o.q_max;
+  g->ksig = sqrtf(o.q_max);
+  g->r_near = o.r_near;
+  return true;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+int pick_cols(const rxgs_ctx* ctx, int ncols) {
+  if (ctx->opts.cols_per_cta) return ctx->opts.cols_per_cta;
+  if (ncols <= 16) return 16;
+  if (ncols <= 32) return 32;
+  return 64;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void rxgs_default_options(rxgs_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->H = 90;
+  o->W = 360;
+  o->theta0_deg = 0.0f;
+  o->step_deg = 1.0f;
+  o->tile_h = 16;
+  o->tile_w = 16;
+  o->eps_T = 1e-4f;
+  o->q_max = 9.0f;
+  o->r_near = 0.05f;
+  o->cols_per_cta = 0;
+  o->deterministic = 1;
+  o->mem_budget = 0;
+}
+
+rxgs_status rxgs_create(const rxgs_options* opts, int device, rxgs_ctx** out) {
+  rxgs_ctx* ctx = nullptr;
+  if (!out) return RXGS_E_INVALID;
+  *out = nullptr;
+  ctx = new rxgs_ctx();
+  if (opts)
+    ctx->opts = *opts;
+  else
+    rxgs_default_options(&ctx->opts);
+  std::string why;
+  if (!make_grid(ctx->opts, &ctx->g, &why)) {
+    delete ctx;
+    return RXGS_E_INVALID;
+  }
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t thr = ~0ull;  // keep freed blocks cached in the pool
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  if (e != cudaSuccess) {
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? RXGS_E_OOM : RXGS_E_CUDA;
+  }
+  *out = ctx;
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
+  if (!ctx) return RXGS_E_INVALID;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->views) {
+    ViewsState* v = kv.second;
+    cudaFree(v->tx); cudaFree(v->rec); cudaFree(v->depth); cudaFree(v->counts);
+    cudaFree(v->offsets); cudaFree(v->keys); cudaFree(v->vals); cudaFree(v->ranges);
+    delete v;
+  }
+  for (auto& kv : ctx->scenes) {
+    SceneState* s = kv.second;
+    cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
+    delete s;
+  }
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return RXGS_OK;
+}
+
+const char* rxgs_last_error(rxgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+rxgs_status rxgs_upload_scene(rxgs_ctx* ctx, const rxgs_scene_desc* d, rxgs_scene_t* out) {
+  if (!ctx || !d || !out) return fail(ctx, RXGS_E_INVALID, "null argument");
+  if (d->K <= 0 || d->K > (1ll << 30)) return fail(ctx, RXGS_E_INVALID, "K out of range");
+  if (d->C <= 0 || d->C > 512) return fail(ctx, RXGS_E_INVALID, "C out of range");
+  if (!d->means || !d->log_scales || !d->quats || !d->opacity)
+    return fail(ctx, RXGS_E_INVALID, "missing scene array");
+  if (d->mlp_params && (!d->base_radiance || d->mlp_hidden != 64))
+    return fail(ctx, RXGS_E_INVALID, "the MLP needs base_radiance and hidden == 64");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  const int K = static_cast<int>(d->K), C = d->C;
+  const cudaMemcpyKind kind = d->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!d->on_device) {
+    // host-side validation: finite positions and opacity in (0, 1)
+    for (int k = 0; k < K; ++k) {
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->means[3 * k + a]) || !std::isfinite(d->log_scales[3 * k + a]))
+          return fail(ctx, RXGS_E_INVALID, "non-finite mean or scale at %d", k);
+      if (!(d->opacity[k] > 0.0f && d->opacity[k] < 1.0f))
+        return fail(ctx, RXGS_E_INVALID, "opacity out of (0,1) at %d", k);
+    }
+  }
+  SceneState* s = new SceneState();
+  s->K = K;
+  s->C = C;
+  float *m = nullptr, *ls = nullptr, *q = nullptr, *op = nullptr;
+  cudaStream_t st = 0;
+  cudaError_t e = cudaSuccess;
+  auto alloc_copy = [&](float** dst, const float* src, size_t n) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(dst, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*dst, src, n * sizeof(float), kind, st);
+  };
+  alloc_copy(&m, d->means, 3ull * K);
+  alloc_copy(&ls, d->log_scales, 3ull * K);
+  alloc_copy(&q, d->quats, 4ull * K);
+  alloc_copy(&op, d->opacity, static_cast<size_t>(K));
+  if (e == cudaSuccess) e = cudaMalloc(&s->geom, sizeof(float4) * 3ull * K);
+  if (e == cudaSuccess) {
+    launch_scene_upload(m, ls, q, op, K, s->geom, st);
+    e = cudaGetLastError();
+  }
+  if (d->base_radiance) alloc_copy(&s->base, d->base_radiance, 2ull * K * C);
+  if (d->mlp_params) {
+    const size_t h = static_cast<size_t>(d->mlp_hidden);
+    s->mlp_floats = h * 3 + h + 4 * C * h + 4 * C + h * 6 + h + 4 * C * h + 4 * C;
+    s->hidden = d->mlp_hidden;
+    s->bf16 = d->mlp_bf16;
+    alloc_copy(&s->mlp, d->mlp_params, s->mlp_floats);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(m);
+  cudaFree(ls);
+  cudaFree(q);
+  cudaFree(op);
+  if (e != cudaSuccess) {
+    cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
+    delete s;
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RXGS_E_OOM : RXGS_E_CUDA, "upload: %s",
+                cudaGetErrorString(e));
+  }
+  const uint64_t id = ctx->next_id++;
+  ctx->scenes[id] = s;
+  *out = id;
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_release_scene(rxgs_ctx* ctx, rxgs_scene_t scene) {
+  if (!ctx) return RXGS_E_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->scenes.find(scene);
+  if (it == ctx->scenes.end()) return fail(ctx, RXGS_E_INVALID, "unknown scene");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  SceneState* s = it->second;
+  cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
+  delete s;
+  ctx->scenes.erase(it);
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_update_scene(rxgs_ctx* ctx, rxgs_scene_t scene, const float* opacity,
+                              const float* base_radiance, const float* mlp_params,
+                              void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->scenes.find(scene);
+  if (it == ctx->scenes.end()) return fail(ctx, RXGS_E_INVALID, "unknown scene");
+  SceneState* s = it->second;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  if (opacity) launch_set_opacity(opacity, s->K, s->geom, st);
+  if (base_radiance) {
+    if (!s->base) return fail(ctx, RXGS_E_INVALID, "scene has no base radiance");
+    CK(cudaMemcpyAsync(s->base, base_radiance, sizeof(float) * 2ull * s->K * s->C,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  if (mlp_params) {
+    if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "scene has no MLP");
+    CK(cudaMemcpyAsync(s->mlp, mlp_params, sizeof(float) * s->mlp_floats,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  return check_last(ctx, "update_scene");
+}
+
+rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int M,
+                         rxgs_views_t* out, void* stream) {
+  if (!ctx || !tx || !out) return fail(ctx, RXGS_E_INVALID, "null argument");
+  if (M <= 0 || M > (1 << 16)) return fail(ctx, RXGS_E_INVALID, "M out of range");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->scenes.find(scene);
+  if (it == ctx->scenes.end()) return fail(ctx, RXGS_E_INVALID, "unknown scene");
+  const SceneState* s = it->second;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const GridConst& g = ctx->g;
+  ViewsState* v = new ViewsState();
+  v->scene = scene;
+  v->M = M;
+  v->K = s->K;
+  v->tile_bits = bits_for(static_cast<uint64_t>(g.T));
+  v->view_bits = bits_for(static_cast<uint64_t>(M));
+  if (31 + v->tile_bits + v->view_bits > 64) {
+    delete v;
+    return fail(ctx, RXGS_E_INVALID, "too many views x tiles for a 64-bit key");
+  }
+  const size_t MK = static_cast<size_t>(M) * s->K;
+  uint32_t* scan_tmp = nullptr;
+  auto cleanup = [&]() {
+    dfree(v->tx, st); dfree(v->rec, st); dfree(v->depth, st); dfree(v->counts, st);
+    dfree(v->offsets, st); dfree(v->keys, st); dfree(v->vals, st); dfree(v->ranges, st);
+    dfree(scan_tmp, st);
+    delete v;
+  };
+  cudaError_t e = dalloc(&v->tx, 3ull * M, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v->tx, tx, sizeof(float) * 3 * M, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = dalloc(&v->rec, 2 * MK, st);
+  if (e == cudaSuccess) e = dalloc(&v->depth, MK, st);
+  if (e == cudaSuccess) e = dalloc(&v->counts, MK, st);
+  if (e == cudaSuccess) e = dalloc(&v->offsets, MK + 1, st);
+  if (e == cudaSuccess) e = dalloc(&scan_tmp, scan_tmp_words(MK), st);
+  if (e == cudaSuccess) e = dalloc(&v->ranges, static_cast<size_t>(M) * g.T, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, RXGS_E_OOM, "prepare: %s", cudaGetErrorString(e));
+  }
+  launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st);
+  launch_exclusive_scan(v->counts, v->offsets, MK, scan_tmp, st);
+  e = cudaMemcpyAsync(ctx->h_pinned, v->offsets + MK, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(scan_tmp, st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, RXGS_E_CUDA, "prepare: %s", cudaGetErrorString(e));
+  }
+  const uint32_t I = ctx->h_pinned[0];
+  if (I > 0x7fffffffu) {
+    cleanup();
+    return fail(ctx, RXGS_E_INVALID, "instance count overflow");
+  }
+  v->n_inst = I;
+  uint64_t* keys_alt = nullptr;
+  uint32_t* vals_alt = nullptr;
+  uint32_t* sort_tmp = nullptr;
+  e = dalloc(&v->keys, I, st);
+  if (e == cudaSuccess) e = dalloc(&v->vals, I, st);
+  if (e == cudaSuccess) e = dalloc(&keys_alt, I, st);
+  if (e == cudaSuccess) e = dalloc(&vals_alt, I, st);
+  if (e == cudaSuccess) e = dalloc(&sort_tmp, radix_tmp_words(I), st);
+  if (e != cudaSuccess) {
+    dfree(keys_alt, st); dfree(vals_alt, st); dfree(sort_tmp, st);
+    cleanup();
+    return fail(ctx, RXGS_E_OOM, "prepare (sort buffers): %s", cudaGetErrorString(e));
+  }
+  launch_emit(g, v->rec, v->depth, v->offsets, s->K, M, v->tile_bits, v->keys, v->vals, st);
+  bool in_alt = false;
+  radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, 31 + v->tile_bits + v->view_bits,
+                   sort_tmp, &in_alt, st);
+  if (in_alt) {
+    std::swap(v->keys, keys_alt);
+    std::swap(v->vals, vals_alt);
+  }
+  dfree(keys_alt, st);
+  dfree(vals_alt, st);
+  dfree(sort_tmp, st);
+  launch_tile_ranges(v->keys, I, v->tile_bits, g.T, v->ranges, M, st);
+  rxgs_status rs = check_last(ctx, "prepare kernels");
+  if (rs != RXGS_OK) {
+    cleanup();
+    return rs;
+  }
+  const uint64_t id = ctx->next_id++;
+  ctx->views[id] = v;
+  *out = id;
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ViewsState* v = it->second;
+  dfree(v->tx, st); dfree(v->rec, st); dfree(v->depth, st); dfree(v->counts, st);
+  dfree(v->offsets, st); dfree(v->keys, st); dfree(v->vals, st); dfree(v->ranges, st);
+  delete v;
+  ctx->views.erase(it);
+  return RXGS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ render
+namespace {
+
+// Produces the Gaussian-major radiance [K][stride] for receivers rx[N].
+rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const float* rx, int N,
+                          const rxgs_render_desc* d, int stride, float* rad, float* glob,
+                          cudaStream_t st) {
+  if (d->radiance) {
+    launch_radiance_transpose(d->radiance, N, s->K, s->C, stride, rad, st);
+  } else {
+    if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
+    MlpParams m{s->mlp, s->hidden, s->C, s->bf16};
+    launch_mlp_radiance(m, rx, N, s->geom, s->base, s->K, stride, rad, glob, st);
+  }
+  return check_last(ctx, "radiance");
+}
+
+}  // namespace
+
+extern "C" {
+
+rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,
+                              const rxgs_render_desc* d, rxgs_outputs* out, void* stream) {
+  if (!ctx || !d || !out) return fail(ctx, RXGS_E_INVALID, "null argument");
+  if (N <= 0 || N > (1 << 20)) return fail(ctx, RXGS_E_INVALID, "N out of range");
+  const int kind = d->kind;
+  if (!kind) return fail(ctx, RXGS_E_INVALID, "empty output kind");
+  if ((kind & RXGS_OUT_SPECTRA) && !out->spectra) return fail(ctx, RXGS_E_INVALID, "spectra == NULL");
+  if ((kind & RXGS_OUT_RSSI) && !out->rssi) return fail(ctx, RXGS_E_INVALID, "rssi == NULL");
+  if ((kind & RXGS_OUT_CSI) && !out->csi) return fail(ctx, RXGS_E_INVALID, "csi == NULL");
+  if (!d->radiance && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
+  const ViewsState* v = it->second;
+  const SceneState* s = ctx->scenes.at(v->scene);
+  if ((kind & RXGS_OUT_RSSI) && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const GridConst& g = ctx->g;
+  const int ncols = 2 * N * s->C;
+  const int stride = round_up(ncols, 128);
+  float* rad = nullptr;
+  float* partial = nullptr;
+  float* glob = nullptr;
+  CK(dalloc(&rad, static_cast<size_t>(s->K) * stride, st));
+  const bool reduce = (kind & (RXGS_OUT_RSSI | RXGS_OUT_CSI)) != 0;
+  cudaError_t e = cudaSuccess;
+  if (reduce) e = dalloc(&partial, static_cast<size_t>(v->M) * g.T * ncols, st);
+  if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * s->C, st);
+  if (e != cudaSuccess) {
+    dfree(rad, st); dfree(partial, st);
+    return fail(ctx, RXGS_E_OOM, "render: %s", cudaGetErrorString(e));
+  }
+  rxgs_status rs = make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
+  if (rs == RXGS_OK) {
+    RenderArgs a{};
+    a.g = g;
+    a.rec = v->rec;
+    a.vals = v->vals;
+    a.ranges = v->ranges;
+    a.rad = rad;
+    a.K = s->K;
+    a.M = v->M;
+    a.N = N;
+    a.C = s->C;
+    a.stride = stride;
+    a.ncols = ncols;
+    a.spectra = (kind & RXGS_OUT_SPECTRA) ? out->spectra : nullptr;
+    a.partial = partial;
+    a.ncontrib = out->ncontrib;
+    a.tfinal = out->tfinal;
+    launch_render_fwd(a, pick_cols(ctx, ncols), st);
+    if (reduce)
+      launch_reduce_tiles(partial, v->M, g.T, N, s->C, (kind & RXGS_OUT_CSI) ? out->csi : nullptr,
+                          (kind & RXGS_OUT_RSSI) ? out->rssi : nullptr, st);
+    rs = check_last(ctx, "render");
+  }
+  dfree(rad, st);
+  dfree(partial, st);
+  dfree(glob, st);
+  return rs;
+}
+
+rxgs_status rxgs_render(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int M,
+                        const float* rx, int N, const rxgs_render_desc* d, rxgs_outputs* out,
+                        void* stream) {
+  rxgs_views_t v = 0;
+  rxgs_status st = rxgs_prepare(ctx, scene, tx, M, &v, stream);
+  if (st != RXGS_OK) return st;
+  st = rxgs_render_views(ctx, v, rx, N, d, out, stream);
+  rxgs_status st2 = rxgs_release_views(ctx, v, stream);
+  return st != RXGS_OK ? st : st2;
+}
+
+rxgs_status rxgs_views_info(rxgs_ctx* ctx, rxgs_views_t views, int64_t* n_inst) {
+  if (!ctx || !n_inst) return fail(ctx, RXGS_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
+  *n_inst = it->second->n_inst;
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uint32_t* counts,
+                              uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
+  const ViewsState* v = it->second;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(ctx->device));
+  const size_t MK = static_cast<size_t>(v->M) * v->K;
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  if (rec) CK(cudaMemcpyAsync(rec, v->rec, sizeof(float4) * 2 * MK, dd, st));
+  if (counts) CK(cudaMemcpyAsync(counts, v->counts, sizeof(uint32_t) * MK, dd, st));
+  if (keys && v->n_inst) CK(cudaMemcpyAsync(keys, v->keys, sizeof(uint64_t) * v->n_inst, dd, st));
+  if (vals && v->n_inst) CK(cudaMemcpyAsync(vals, v->vals, sizeof(uint32_t) * v->n_inst, dd, st));
+  if (ranges)
+    CK(cudaMemcpyAsync(ranges, v->ranges, sizeof(uint2) * static_cast<size_t>(v->M) * ctx->g.T, dd,
+                       st));
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t, const float*, int,
+                                 const rxgs_render_desc*, const rxgs_cotangents*, rxgs_grads*,
+                                 void*) {
+  return fail(ctx, RXGS_E_INVALID, "backward not available in this build");
+}
+
+rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned h = 0;
+  CK(cudaMemcpy(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost));
+  if (h) {
+    cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+    return fail(ctx, RXGS_E_DEVICE, "device error word 0x%x", h);
+  }
+  return RXGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// rxgs_internal.h -- shared declarations of the CUDA library (not part of the
+// C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace rxgs {
+
+// Grid constants as the kernels see them (all float32 values derived once on
+// the host).
+struct GridConst {
+  int H, W, TH, TW;
+  int tiles_h, tiles_w, T;  // T = tiles_h * tiles_w
+  float inv_step;           // 1 / step in radians, rounded to float32
+  float theta0_px;          // theta0 / step
+  float Wf, halfW, Hm1f;    // W, W/2, H-1 as floats
+  float eps_T, q_max, ksig, r_near;  // ksig = sqrt(q_max)
+};
+
+// Device error word bits (written by kernels, read by the host at syncs).
+enum : unsigned {
+  kErrCapacity = 1u,   // an instance list was larger than its buffer
+  kErrBounds = 2u,     // an index left its buffer (checked builds)
+  kErrArgument = 4u,   // a device-side argument check failed
+};
+
+// ----------------------------------------------------------- geometry (a0-a3)
+// Packed scene record: 3 x float4 = {p.xyz, tau}, {S00,S01,S02,S11},
+// {S12,S22,0,0}.
+void launch_scene_upload(const float* means, const float* log_scales, const float* quats,
+                         const float* opacity, int K, float4* geom, cudaStream_t s);
+void launch_set_opacity(const float* opacity, int K, float4* geom, cudaStream_t s);
+
+// Projection of K Gaussians for M views.  rec[M][K][2] float4, depth[M][K]
+// (float bits of rho), count[M*K] tile counts (0 = culled).
+void launch_preprocess(const GridConst& g, const float4* geom, int K, const float* tx, int M,
+                       float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s);
+
+// Exclusive scan of n uint32 values; out has n+1 entries (out[n] = total).
+// tmp must hold scan_tmp_words(n) uint32.
+size_t scan_tmp_words(size_t n);
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp,
+                           cudaStream_t s);
+
+// Writes the (view | tile | depth) keys and Gaussian-index values.
+void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
+                 const uint32_t* offsets, int K, int M, int tile_bits, uint64_t* keys,
+                 uint32_t* vals, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Returns, through *result_in_alt, whether the sorted data ended in the alt
+// buffers.  tmp must hold radix_tmp_words(n) uint32.
+size_t radix_tmp_words(size_t n);
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s);
+
+// ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
+void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
+                        int M, cudaStream_t s);
+
+// ------------------------------------------------------------- radiance (a4)
+// receiver-major [N][K][C][2] -> Gaussian-major [K][stride] (columns
+// j*2C + 2c + {0,1}; pad columns are zero).
+void launch_radiance_transpose(const float* rad, int N, int K, int C, int stride, float* out,
+                               cudaStream_t s);
+// Gaussian-major [K][stride] -> receiver-major [N][K][C][2] (accumulates).
+void launch_radiance_untranspose_add(const float* in, int N, int K, int C, int stride,
+                                     float* out, cudaStream_t s);
+
+struct MlpParams {
+  const float* p;  // flat parameters (fp32)
+  int hidden, C, bf16;
+};
+// Radiance from the conditioning MLP: out[K][stride] Gaussian-major.
+void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float4* geom,
+                         const float* base, int K, int stride, float* out, float* glob_out,
+                         cudaStream_t s);
+// Backward of the MLP: dS[K][stride] -> grad_base[K][C][2], grad_mlp (flat).
+size_t mlp_backward_tmp_floats(const MlpParams& m, int N, int K);
+void launch_mlp_backward(const MlpParams& m, const float* rx, int N, const float4* geom,
+                         const float* base, int K, int stride, const float* dS,
+                         const float* glob, float* grad_base, float* grad_mlp, float* tmp,
+                         cudaStream_t s);
+
+// ------------------------------------------------------------ render (a5-a7)
+struct RenderArgs {
+  GridConst g;
+  const float4* rec;       // [M][K][2]
+  const uint32_t* vals;    // sorted Gaussian ids
+  const uint2* ranges;     // [M][T]
+  const float* rad;        // [K][stride]
+  int K, M, N, C;
+  int stride;              // floats per radiance row
+  int ncols;               // N*2C valid columns
+  float* spectra;          // [M][N][H][W][C][2] or null
+  float* partial;          // [M][T][ncols] per-tile column sums or null
+  int32_t* ncontrib;       // [M][H][W] or null
+  float* tfinal;           // [M][H][W] or null
+};
+void launch_render_fwd(const RenderArgs& a, int cols_per_cta, cudaStream_t s);
+
+// Sums partial[M][T][ncols] over tiles -> csi[M][N][C][2], rssi[M][N].
+void launch_reduce_tiles(const float* partial, int M, int T, int N, int C, float* csi,
+                         float* rssi, cudaStream_t s);
+
+struct BackwardArgs {
+  RenderArgs f;               // forward arguments (spectra = fwd spectra or null)
+  const float* g_spec;        // [M][N][H][W][C][2] or null
+  const float* g_uniform;     // [M][ncols] cotangent uniform over pixels, or null
+  float* d_rad;               // [K][stride] dL/ds accumulated (atomics)
+  float* d_tau;               // [K] accumulated
+  float* d_tau_partial;       // deterministic: [I][colblocks] or null
+  uint32_t n_inst;
+};
+void launch_render_bwd(const BackwardArgs& a, int cols_per_cta, cudaStream_t s);
+
+}  // namespace rxgs

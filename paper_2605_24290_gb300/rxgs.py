@@ -1,0 +1,249 @@
+"""Python binding of librxgs (include/rxgs.h): argument marshalling only.
+
+Every step of the renderer runs in the CUDA library; this module turns torch
+tensors into device pointers and the current torch stream into the call's
+stream.  There is no CPU path: without the compiled library (or without a
+GPU) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librxgs.so")
+
+OUT_SPECTRA, OUT_RSSI, OUT_CSI = 1, 2, 4
+STATUS = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_ADMISSION", 5: "E_NOT_READY",
+          6: "E_TIMEOUT", 7: "E_DEVICE", 8: "E_CANCELLED"}
+OK, E_INVALID, E_OOM, E_CUDA, E_ADMISSION, E_NOT_READY, E_TIMEOUT, E_DEVICE, E_CANCELLED = range(9)
+
+
+class RxgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rxgs {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("theta0_deg", ctypes.c_float),
+                ("step_deg", ctypes.c_float), ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
+                ("eps_T", ctypes.c_float), ("q_max", ctypes.c_float), ("r_near", ctypes.c_float),
+                ("cols_per_cta", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("mem_budget", ctypes.c_size_t)]
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("C", ctypes.c_int), ("means", ctypes.c_void_p),
+                ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("base_radiance", ctypes.c_void_p),
+                ("mlp_params", ctypes.c_void_p), ("mlp_hidden", ctypes.c_int),
+                ("mlp_bf16", ctypes.c_int), ("on_device", ctypes.c_int)]
+
+
+class RenderDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("radiance", ctypes.c_void_p), ("reduce_path", ctypes.c_int)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("spectra", ctypes.c_void_p), ("rssi", ctypes.c_void_p), ("csi", ctypes.c_void_p),
+                ("ncontrib", ctypes.c_void_p), ("tfinal", ctypes.c_void_p)]
+
+
+class Cotangents(ctypes.Structure):
+    _fields_ = [("grad_spectra", ctypes.c_void_p), ("grad_csi", ctypes.c_void_p),
+                ("grad_rssi", ctypes.c_void_p), ("fwd_spectra", ctypes.c_void_p),
+                ("fwd_csi", ctypes.c_void_p)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("grad_radiance", ctypes.c_void_p), ("grad_opacity", ctypes.c_void_p),
+                ("grad_base", ctypes.c_void_p), ("grad_mlp", ctypes.c_void_p)]
+
+
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+I = ctypes.c_int
+# name -> (restype, argtypes); the exported symbols of include/rxgs.h
+SIGNATURES = {
+    "rxgs_default_options": (None, [P]),
+    "rxgs_create": (I, [P, I, P]),
+    "rxgs_destroy": (I, [P]),
+    "rxgs_last_error": (ctypes.c_char_p, [P]),
+    "rxgs_upload_scene": (I, [P, P, P]),
+    "rxgs_release_scene": (I, [P, U64]),
+    "rxgs_update_scene": (I, [P, U64, P, P, P, P]),
+    "rxgs_prepare": (I, [P, U64, P, I, P, P]),
+    "rxgs_release_views": (I, [P, U64, P]),
+    "rxgs_render_views": (I, [P, U64, P, I, P, P, P]),
+    "rxgs_render": (I, [P, U64, P, I, P, I, P, P, P]),
+    "rxgs_render_backward": (I, [P, U64, P, I, P, P, P, P]),
+    "rxgs_views_info": (I, [P, U64, P]),
+    "rxgs_views_export": (I, [P, U64, P, P, P, P, P, P]),
+    "rxgs_sync": (I, [P, P]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Loads librxgs.so (building it first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                from . import build as _b
+                _b.build()
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t):
+    import torch
+    if t is not None and t.dtype != torch.float32:
+        raise TypeError("expected float32")
+    return _ptr(t)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One rxgs context on one CUDA device (argument marshalling only)."""
+
+    def __init__(self, H=90, W=360, theta0_deg=0.0, step_deg=1.0, tile_h=16, tile_w=16,
+                 eps_T=1e-4, q_max=9.0, r_near=0.05, cols_per_cta=0, deterministic=1,
+                 mem_budget=0, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("rxgs needs a CUDA device; there is no CPU fallback")
+        self.lib = load()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        o = Options(H, W, theta0_deg, step_deg, tile_h, tile_w, eps_T, q_max, r_near, cols_per_cta,
+                    deterministic, mem_budget)
+        self.opts = o
+        h = ctypes.c_void_p()
+        st = self.lib.rxgs_create(ctypes.byref(o), self.device, ctypes.byref(h))
+        if st != OK:
+            raise RxgsError(st, "rxgs_create failed (bad options or CUDA error)")
+        self.h = h
+        self.H, self.W = H, W
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rxgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise RxgsError(st, self.lib.rxgs_last_error(self.h).decode())
+
+    # --------------------------------------------------------------- scene
+    def upload_scene(self, means, log_scales, quats, opacity, base=None, mlp=None, C=1,
+                     hidden=64, bf16=False):
+        """Device tensors (float32).  Returns a scene handle."""
+        d = SceneDesc(int(means.shape[0]), int(C), _f32(means), _f32(log_scales), _f32(quats),
+                      _f32(opacity), _f32(base), _f32(mlp), int(hidden), int(bool(bf16)), 1)
+        out = ctypes.c_uint64()
+        import torch
+        torch.cuda.synchronize()
+        self._check(self.lib.rxgs_upload_scene(self.h, ctypes.byref(d), ctypes.byref(out)))
+        return out.value
+
+    def release_scene(self, scene):
+        self._check(self.lib.rxgs_release_scene(self.h, U64(scene)))
+
+    def update_scene(self, scene, opacity=None, base=None, mlp=None, stream=None):
+        self._check(self.lib.rxgs_update_scene(self.h, U64(scene), _f32(opacity), _f32(base),
+                                               _f32(mlp), _stream(stream)))
+
+    # --------------------------------------------------------------- views
+    def prepare(self, scene, tx, stream=None):
+        out = ctypes.c_uint64()
+        self._check(self.lib.rxgs_prepare(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
+                                          ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def release_views(self, views, stream=None):
+        self._check(self.lib.rxgs_release_views(self.h, U64(views), _stream(stream)))
+
+    def render_views(self, views, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
+                     ncontrib=None, tfinal=None, reduce_path=0, stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path))
+        o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
+        self._check(self.lib.rxgs_render_views(self.h, U64(views), _f32(rx), int(N),
+                                               ctypes.byref(d), ctypes.byref(o), _stream(stream)))
+
+    def render(self, scene, tx, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
+               ncontrib=None, tfinal=None, reduce_path=0, stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path))
+        o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
+        self._check(self.lib.rxgs_render(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
+                                         _f32(rx), int(N), ctypes.byref(d), ctypes.byref(o),
+                                         _stream(stream)))
+
+    def render_backward(self, views, rx, N, kind, radiance=None, grad_spectra=None,
+                        grad_csi=None, grad_rssi=None, fwd_spectra=None, fwd_csi=None,
+                        grad_radiance=None, grad_opacity=None, grad_base=None, grad_mlp=None,
+                        stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), 0)
+        c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_spectra),
+                       _f32(fwd_csi))
+        g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp))
+        self._check(self.lib.rxgs_render_backward(self.h, U64(views), _f32(rx), int(N),
+                                                  ctypes.byref(d), ctypes.byref(c),
+                                                  ctypes.byref(g), _stream(stream)))
+
+    def views_info(self, views):
+        n = ctypes.c_int64()
+        self._check(self.lib.rxgs_views_info(self.h, U64(views), ctypes.byref(n)))
+        return n.value
+
+    def views_export(self, views, M, K, T, stream=None):
+        """Copies the transmitter-side state into new tensors:
+        (rec[M,K,8] f32, counts[M,K] i32, keys[I] i64, vals[I] i32, ranges[M,T,2] i32)."""
+        import torch
+        n = self.views_info(views)
+        dev = torch.device("cuda", self.device)
+        rec = torch.empty((M, K, 8), dtype=torch.float32, device=dev)
+        counts = torch.empty((M, K), dtype=torch.int32, device=dev)
+        keys = torch.empty((max(n, 1),), dtype=torch.int64, device=dev)
+        vals = torch.empty((max(n, 1),), dtype=torch.int32, device=dev)
+        ranges = torch.empty((M, T, 2), dtype=torch.int32, device=dev)
+        self._check(self.lib.rxgs_views_export(self.h, U64(views), _ptr(rec), _ptr(counts),
+                                               _ptr(keys), _ptr(vals), _ptr(ranges),
+                                               _stream(stream)))
+        return rec, counts, keys[:n], vals[:n], ranges
+
+    def sync(self, stream=None):
+        self._check(self.lib.rxgs_sync(self.h, _stream(stream)))
