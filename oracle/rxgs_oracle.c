@@ -243,7 +243,7 @@ void or_project32(const or_grid* g, const float p[3], float tau, const float S[6
   } else {
     int jl = (int)clo, jh = (int)chi;
     span = jh - jl;
-    j_lo = jl < 0 ? jl + g->W : jl;
+    j_lo = jl < 0 ? jl + g->W : (jl >= g->W ? jl - g->W : jl);   /* into [0, W) */
   }
   o->vis = 1;
   o->theta_px = theta_px; o->phi_px = phi_px;

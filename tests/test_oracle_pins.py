@@ -300,6 +300,7 @@ def test_tiled_lists_equal_brute_force(oracle):
             assert ntiles[k] == sum(k in s_ for s_ in sets)
         # a Gaussian is kept only if its footprint holds at least one pixel
         assert np.all(ntiles[vis] >= 1)
+        assert np.all((box[vis, 2] >= 0) & (box[vis, 2] < g.W))
         glob = sorted(np.nonzero(vis)[0], key=lambda k: (rec[k, 6], k))
         for i in range(g.H):
             for j in range(g.W):
@@ -310,6 +311,21 @@ def test_tiled_lists_equal_brute_force(oracle):
         # wrap and pole cases were exercised
         assert (box[vis, 3] == g.W - 1).any()
         assert ((box[vis, 2] + box[vis, 3]) >= g.W).any()
+
+
+def test_footprint_column_start_wraps_into_grid(oracle):
+    """A small Gaussian just below azimuth 360 deg whose only covered column
+    is 0: its column range starts inside [0, W) and its tile is tile 0."""
+    g = S.Grid(H=9, W=36, step_deg=10.0)
+    rng = np.random.default_rng(102)
+    sc = S.draw_scene(rng, 2000)
+    tx = S.draw_points(rng, 1)
+    _, rec, box = oracle.project_view32(g, sc, tx[0])
+    counts, lists, ntiles = oracle.tile_lists(g, sc, tx[0])
+    k = 6                                   # phi_px = 35.94, one column
+    assert rec[k, 7] == 1 and rec[k, 1] > 35.5
+    assert box[k, 2] == 0 and box[k, 3] == 0 and ntiles[k] == 1
+    assert k in lists[:counts[0]]
 
 
 def test_render_reorder_identity(oracle):
