@@ -135,7 +135,7 @@ __device__ __forceinline__ Footprint project_one(const GridConst& g, const float
   } else {
     const int jl = static_cast<int>(clo), jh = static_cast<int>(chi);
     o.span = jh - jl;
-    o.j_lo = jl < 0 ? jl + g.W : jl;
+    o.j_lo = jl < 0 ? jl + g.W : (jl >= g.W ? jl - g.W : jl);  // into [0, W)
   }
   o.vis = true;
   o.theta_px = theta_px;
