@@ -74,7 +74,7 @@ def lib():
                                               ctypes.c_int, P, ctypes.c_int, P, P, P, P, P]
             _lib.or_backward_view.restype = ctypes.c_int
             _lib.or_backward_view.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
-                                              ctypes.c_int, P, P, P, P, ctypes.c_int]
+                                              ctypes.c_int, P, P, P, P, P, P, ctypes.c_int]
             _lib.or_omp_threads.restype = ctypes.c_int
     return _lib
 
@@ -208,19 +208,25 @@ def render_pixels(grid, scene, centre, radiance, pix):
     return out, aab, ncon, Tf
 
 
-def backward_view(grid, scene, centre, radiance, gspec, use_eps=True):
+def backward_view(grid, scene, centre, radiance, gspec, use_eps=True, want_abs=False):
     """dL/d radiance [N,K,C,2] and dL/d opacity [K] for cotangent gspec
-    [N,H,W,C,2] on the spectra of one view."""
+    [N,H,W,C,2] on the spectra of one view.  With want_abs, also the sums of
+    absolute terms (error scales) of both."""
     g = make_grid(grid)
     rad = _c64(radiance)
     N, K, C = rad.shape[0], rad.shape[1], rad.shape[2]
     gr = np.zeros_like(rad)
     gt = np.zeros(K, np.float64)
+    ar = np.zeros_like(rad) if want_abs else None
+    at = np.zeros(K, np.float64) if want_abs else None
     rc = lib().or_backward_view(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
                                 _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
-                                N, C, _p(rad), _p(_c64(gspec)), _p(gr), _p(gt), 1 if use_eps else 0)
+                                N, C, _p(rad), _p(_c64(gspec)), _p(gr), _p(gt), _p(ar), _p(at),
+                                1 if use_eps else 0)
     if rc != 0:
         raise MemoryError("oracle backward failed")
+    if want_abs:
+        return gr, gt, ar, at
     return gr, gt
 
 

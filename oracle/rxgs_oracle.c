@@ -602,10 +602,14 @@ int or_render_pixels(const or_grid* g, int K, const float* p, const float* s, co
  * grad_rad[N][K][C][2] += sum_pixels T_k w_k g                (dL/ds)
  * grad_tau[K]          += sum_pixels G_k sum_j <g_j, T_k (s_kj - S_kj)>
  * where S_kj is the normalised colour behind k, swept back to front:
- * S <- w_m s_m + (1 - w_m) S.                                              */
+ * S <- w_m s_m + (1 - w_m) S.
+ * abs_rad / abs_tau (optional) receive the same sums taken over absolute
+ * values of every term: the scale against which a float32 result's
+ * rounding error is measured.                                               */
 int or_backward_view(const or_grid* g, int K, const float* p, const float* s, const float* q,
                      const float* tau, const float* c, int N, int C, const double* rad,
-                     const double* gspec, double* grad_rad, double* grad_tau, int use_eps) {
+                     const double* gspec, double* grad_rad, double* grad_tau, double* abs_rad,
+                     double* abs_tau, int use_eps) {
   or_view V;
   if (or_view_init(&V, g, K, p, s, q, tau, c)) return -2;
   const int H = g->H, W = g->W;
@@ -638,7 +642,7 @@ int or_backward_view(const or_grid* g, int K, const float* p, const float* s, co
       memset(Sb, 0, sizeof(double) * (size_t)N * C * 2);
       for (int e = n_c - 1; e >= 0; --e) {
         int k = seq[e];
-        double dLdw = 0.0;
+        double dLdw = 0.0, adw = 0.0;
         for (int j = 0; j < N; ++j)
           for (int ch = 0; ch < C; ++ch) {
             const double* gv = gspec + ((((size_t)j * H * W + pix) * C + ch) * 2);
@@ -647,11 +651,19 @@ int or_backward_view(const or_grid* g, int K, const float* p, const float* s, co
             double* Sv = Sb + (j * C + ch) * 2;
             gr[0] += sT[e] * sw[e] * gv[0];
             gr[1] += sT[e] * sw[e] * gv[1];
+            if (abs_rad) {
+              double* ar = abs_rad + ((((size_t)j * K + k) * C + ch) * 2);
+              ar[0] += sT[e] * sw[e] * fabs(gv[0]);
+              ar[1] += sT[e] * sw[e] * fabs(gv[1]);
+            }
             dLdw += sT[e] * (gv[0] * (sv[0] - Sv[0]) + gv[1] * (sv[1] - Sv[1]));
+            adw += sT[e] * (fabs(gv[0]) * (fabs(sv[0]) + fabs(Sv[0])) +
+                            fabs(gv[1]) * (fabs(sv[1]) + fabs(Sv[1])));
             Sv[0] = sw[e] * sv[0] + (1.0 - sw[e]) * Sv[0];
             Sv[1] = sw[e] * sv[1] + (1.0 - sw[e]) * Sv[1];
           }
         grad_tau[k] += dLdw * sG[e];
+        if (abs_tau) abs_tau[k] += adw * sG[e];
       }
     }
   free(seq); free(sw); free(sG); free(sT); free(Sb);

@@ -145,6 +145,32 @@ int pick_cols(const rxgs_ctx* ctx, int ncols) {
 
 }  // namespace
 
+// Cotangent that is uniform over the pixels of a (view, receiver, channel):
+// dL/dCSI directly, plus dL/dRSSI * S/|S| for RSSI = |S| (C == 1).
+__global__ void uniform_cot_kernel(const float* __restrict__ gcsi, const float* __restrict__ grssi,
+                                   const float* __restrict__ fcsi, int M, int N, int C,
+                                   float* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // (v, j, c)
+  if (idx >= M * N * C) return;
+  float re = gcsi ? gcsi[2 * idx] : 0.0f, im = gcsi ? gcsi[2 * idx + 1] : 0.0f;
+  if (grssi && C == 1) {
+    const float sr = fcsi[2 * idx], si = fcsi[2 * idx + 1];
+    const float mag = sqrtf(sr * sr + si * si);
+    if (mag > 0.0f) {
+      re += grssi[idx] * sr / mag;
+      im += grssi[idx] * si / mag;
+    }
+  }
+  out[2 * idx] = re;
+  out[2 * idx + 1] = im;
+}
+
+void launch_uniform_cotangent(const float* gcsi, const float* grssi, const float* fcsi, int M,
+                              int N, int C, float* out, cudaStream_t s) {
+  const int n = M * N * C;
+  uniform_cot_kernel<<<(n + 255) / 256, 256, 0, s>>>(gcsi, grssi, fcsi, M, N, C, out);
+}
+
 // ====================================================================== ABI
 extern "C" {
 
@@ -561,10 +587,99 @@ rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uin
   return RXGS_OK;
 }
 
-rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t, const float*, int,
-                                 const rxgs_render_desc*, const rxgs_cotangents*, rxgs_grads*,
-                                 void*) {
-  return fail(ctx, RXGS_E_INVALID, "backward not available in this build");
+rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,
+                                 const rxgs_render_desc* d, const rxgs_cotangents* cot,
+                                 rxgs_grads* gr, void* stream) {
+  if (!ctx || !d || !cot || !gr) return fail(ctx, RXGS_E_INVALID, "null argument");
+  if (N <= 0 || N > (1 << 20)) return fail(ctx, RXGS_E_INVALID, "N out of range");
+  if (!cot->grad_spectra && !cot->grad_csi && !cot->grad_rssi)
+    return fail(ctx, RXGS_E_INVALID, "no cotangent");
+  if (cot->grad_rssi && !cot->fwd_csi)
+    return fail(ctx, RXGS_E_INVALID, "grad_rssi needs the forward CSI (fwd_csi)");
+  if (!d->radiance && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
+  const ViewsState* v = it->second;
+  const SceneState* s = ctx->scenes.at(v->scene);
+  if (cot->grad_rssi && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
+  if (!d->radiance) {
+    if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
+    if (s->bf16) return fail(ctx, RXGS_E_INVALID, "backward through a bf16 MLP is not supported");
+    if (s->C > 4 || static_cast<size_t>(N) * 4 * s->C > 8192)
+      return fail(ctx, RXGS_E_INVALID, "MLP backward supports C <= 4 and N*4C <= 8192");
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const GridConst& g = ctx->g;
+  const int C = s->C, K = s->K, M = v->M;
+  const int ncols = 2 * N * C;
+  const int stride = round_up(ncols, 128);
+  float *rad = nullptr, *glob = nullptr, *d_rad = nullptr, *g_uni = nullptr, *d_tau = nullptr;
+  float *g_base = nullptr, *g_mlp = nullptr, *mlp_tmp = nullptr;
+  auto cleanup = [&]() {
+    dfree(rad, st); dfree(glob, st); dfree(d_rad, st); dfree(g_uni, st); dfree(mlp_tmp, st);
+    if (!gr->grad_opacity) dfree(d_tau, st);
+    if (!gr->grad_base) dfree(g_base, st);
+    if (!gr->grad_mlp) dfree(g_mlp, st);
+  };
+  cudaError_t e = dalloc(&rad, static_cast<size_t>(K) * stride, st);
+  if (e == cudaSuccess) e = dalloc(&d_rad, static_cast<size_t>(K) * stride, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_rad, 0, sizeof(float) * K * static_cast<size_t>(stride), st);
+  if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * C, st);
+  if (e == cudaSuccess && (cot->grad_csi || cot->grad_rssi))
+    e = dalloc(&g_uni, static_cast<size_t>(M) * ncols, st);
+  d_tau = gr->grad_opacity;
+  if (e == cudaSuccess && !d_tau) e = dalloc(&d_tau, static_cast<size_t>(K), st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, RXGS_E_OOM, "backward: %s", cudaGetErrorString(e));
+  }
+  rxgs_status rs = make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
+  if (rs != RXGS_OK) {
+    cleanup();
+    return rs;
+  }
+  if (g_uni) launch_uniform_cotangent(cot->grad_csi, cot->grad_rssi, cot->fwd_csi, M, N, C, g_uni, st);
+  BackwardArgs A{};
+  A.f.g = g;
+  A.f.rec = v->rec;
+  A.f.vals = v->vals;
+  A.f.ranges = v->ranges;
+  A.f.rad = rad;
+  A.f.K = K;
+  A.f.M = M;
+  A.f.N = N;
+  A.f.C = C;
+  A.f.stride = stride;
+  A.f.ncols = ncols;
+  A.f.spectra = const_cast<float*>(cot->fwd_spectra);
+  A.g_spec = cot->grad_spectra;
+  A.g_uniform = g_uni;
+  A.d_rad = d_rad;
+  A.d_tau = d_tau;
+  A.n_inst = v->n_inst;
+  launch_render_bwd(A, 32, st);
+  if (d->radiance) {
+    if (gr->grad_radiance) launch_radiance_untranspose_add(d_rad, N, K, C, stride, gr->grad_radiance, st);
+  } else {
+    MlpParams m{s->mlp, s->hidden, C, 0};
+    g_base = gr->grad_base;
+    g_mlp = gr->grad_mlp;
+    e = cudaSuccess;
+    if (!g_base) e = dalloc(&g_base, 2ull * K * C, st);
+    if (e == cudaSuccess && !g_mlp) e = dalloc(&g_mlp, s->mlp_floats, st);
+    if (e == cudaSuccess) e = dalloc(&mlp_tmp, mlp_backward_tmp_floats(m, N, K), st);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(ctx, RXGS_E_OOM, "backward (MLP): %s", cudaGetErrorString(e));
+    }
+    launch_mlp_backward(m, rx, N, s->geom, s->base, K, stride, d_rad, glob, g_base, g_mlp,
+                        mlp_tmp, st);
+  }
+  rs = check_last(ctx, "backward");
+  cleanup();
+  return rs;
 }
 
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream) {

@@ -245,5 +245,10 @@ class Context:
                                                _stream(stream)))
         return rec, counts, keys[:n], vals[:n], ranges
 
+    @staticmethod
+    def mlp_numel(C, hidden=64):
+        """Number of float32 parameters of the two conditioning MLPs."""
+        return hidden * 3 + hidden + 4 * C * hidden + 4 * C + hidden * 6 + hidden + 4 * C * hidden + 4 * C
+
     def sync(self, stream=None):
         self._check(self.lib.rxgs_sync(self.h, _stream(stream)))

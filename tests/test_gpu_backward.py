@@ -1,0 +1,254 @@
+"""Backward parity of the CUDA path: gradients to radiance, opacity, phi_base
+and the conditioning MLP against the float64 oracle, and directional finite
+differences of the GPU forward itself.
+
+Tolerance: |g_gpu - g_ref| <= TOL * A where A is the sum of the absolute
+values of every term of the reference gradient (the oracle's abs_* scales):
+the float32 error of a sum of terms is bounded by a small multiple of
+2^-24 times that sum, so 1e-4 is far above it and far below any
+structural mistake (a wrong sign, a missing term).
+"""
+import numpy as np
+import pytest
+
+from paper_2605_24290_gb300 import synthetic as S
+from tests.gpu_helpers import TOL, dev, upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a GPU"
+    return t
+
+
+@pytest.fixture(scope="module")
+def rx():
+    from paper_2605_24290_gb300 import rxgs
+    return rxgs
+
+
+def ctx_for(rx, g):
+    return rx.Context(H=g.H, W=g.W, theta0_deg=g.theta0_deg, step_deg=g.step_deg, tile_h=g.tile_h,
+                      tile_w=g.tile_w, eps_T=g.eps_T, q_max=g.q_max, r_near=g.r_near)
+
+
+def scaled_err(got, ref, scale):
+    got, ref, scale = (np.asarray(x, np.float64) for x in (got, ref, scale))
+    return float((np.abs(got - ref) / (scale + 1e-30)).max())
+
+
+def oracle_grads(oracle, g, sc, tx, rad, gspec):
+    """Sum over views of the oracle backward: (grad_rad, grad_tau, abs_rad, abs_tau)."""
+    tot = None
+    for v in range(tx.shape[0]):
+        r = oracle.backward_view(g, sc, tx[v], rad, gspec[v], want_abs=True)
+        tot = list(r) if tot is None else [a + b for a, b in zip(tot, r)]
+    return tot
+
+
+@pytest.mark.parametrize("with_fwd", [True, False])
+def test_backward_explicit_radiance(torch, rx, oracle, with_fwd):
+    """Cotangent on spectra; with the forward spectra (one walk per tile) and
+    without them (two walks)."""
+    rng = np.random.default_rng(201)
+    w = S.workload_small()
+    g, sc = w["grid"], w["scene"]
+    tx = np.concatenate([w["tx"], S.draw_points(rng, 1)])
+    rad = w["radiance"]
+    M, N, K = tx.shape[0], rad.shape[0], sc.K
+    gs = rng.normal(size=(M, N, g.H, g.W, 1, 2)).astype(np.float32)
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch)
+    views = ctx.prepare(h, dev(tx, torch))
+    radd = dev(rad, torch)
+    spec = torch.zeros((M, N, g.H, g.W, 1, 2), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_SPECTRA, radiance=radd, spectra=spec)
+    d_rad = torch.zeros_like(radd)
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, None, N, rx.OUT_SPECTRA, radiance=radd, grad_spectra=dev(gs, torch),
+                        fwd_spectra=spec if with_fwd else None, grad_radiance=d_rad,
+                        grad_opacity=d_tau)
+    ctx.sync()
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
+    e_r = scaled_err(d_rad.cpu().numpy(), ref_r, abs_r)
+    e_t = scaled_err(d_tau.cpu().numpy(), ref_t, abs_t)
+    assert e_r <= TOL, f"radiance gradient error {e_r}"
+    assert e_t <= TOL, f"opacity gradient error {e_t}"
+    assert np.abs(ref_t).max() > 0
+
+
+def test_backward_csi_and_rssi_cotangents(torch, rx, oracle):
+    """dL/dCSI and dL/dRSSI act as pixel-uniform cotangents on the spectra."""
+    rng = np.random.default_rng(202)
+    w = S.workload_small()
+    g, sc = w["grid"], w["scene"]
+    tx, rad = w["tx"], w["radiance"]
+    M, N, K = 1, rad.shape[0], sc.K
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch)
+    views = ctx.prepare(h, dev(tx, torch))
+    radd = dev(rad, torch)
+    csi = torch.zeros((M, N, 1, 2), device="cuda")
+    rssi = torch.zeros((M, N), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_CSI | rx.OUT_RSSI, radiance=radd, csi=csi, rssi=rssi)
+    gc = rng.normal(size=(M, N, 1, 2)).astype(np.float32)
+    gr = rng.normal(size=(M, N)).astype(np.float32)
+    d_rad = torch.zeros_like(radd)
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, None, N, rx.OUT_CSI | rx.OUT_RSSI, radiance=radd,
+                        grad_csi=dev(gc, torch), grad_rssi=dev(gr, torch), fwd_csi=csi,
+                        grad_radiance=d_rad, grad_opacity=d_tau)
+    ctx.sync()
+    o = oracle.render_view(g, sc, tx[0], rad.astype(np.float64))
+    S_ = oracle.csi(o["spectra"])[:, 0, :]                    # [N,2]
+    mag = np.sqrt((S_ ** 2).sum(-1, keepdims=True))
+    gu = gc[0, :, 0, :].astype(np.float64) + gr[0][:, None] * S_ / mag
+    gspec = np.broadcast_to(gu[:, None, None, None, :], (N, g.H, g.W, 1, 2)).copy()
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gspec[None])
+    assert scaled_err(d_rad.cpu().numpy(), ref_r, abs_r) <= TOL
+    assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
+
+
+def test_backward_through_mlp(torch, rx, oracle):
+    """Cotangent on spectra through the conditioning MLP to phi_base, the MLP
+    parameters and the opacity."""
+    rng = np.random.default_rng(203)
+    K, M, N, C = 3000, 2, 8, 1
+    sc = S.draw_scene(rng, K)
+    tx, rxp = S.draw_points(rng, M), S.draw_points(rng, N)
+    base = S.draw_base(rng, K, C)
+    mlp = S.draw_mlp(rng, C)
+    flat = S.flatten_mlp(mlp, C)
+    g = S.Grid()
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch, base=base, mlp_flat=flat, C=C)
+    views = ctx.prepare(h, dev(tx, torch))
+    spec = torch.zeros((M, N, g.H, g.W, C, 2), device="cuda")
+    rxd = dev(rxp, torch)
+    ctx.render_views(views, rxd, N, rx.OUT_SPECTRA, spectra=spec)
+    gs = rng.normal(size=(M, N, g.H, g.W, C, 2)).astype(np.float32)
+    d_tau = torch.zeros(K, device="cuda")
+    d_base = torch.zeros((K, C, 2), device="cuda")
+    d_mlp = torch.zeros(flat.shape[0], device="cuda")
+    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=dev(gs, torch), fwd_spectra=spec,
+                        grad_opacity=d_tau, grad_base=d_base, grad_mlp=d_mlp)
+    ctx.sync()
+    rad = oracle.mlp_radiance(mlp, rxp, sc.means, base)
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
+    assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
+    ref = oracle.mlp_backward(mlp, rxp, sc.means, base, ref_r)
+    # scale: the same chain applied to the absolute radiance-gradient terms
+    absd = {k: np.abs(v) for k, v in oracle.mlp_backward(
+        {k: np.abs(v) for k, v in mlp.items()}, rxp, sc.means, np.abs(base), abs_r).items()}
+    got_mlp = S.unflatten_mlp(d_mlp.cpu().numpy(), C)
+    e = scaled_err(d_base.cpu().numpy(), ref["base"], absd["base"] + 1e-3 * np.abs(ref["base"]).max())
+    assert e <= TOL, f"phi_base gradient {e}"
+    for name in mlp:
+        sc_ = absd[name] + 1e-3 * np.abs(ref[name]).max()
+        e = scaled_err(got_mlp[name], ref[name], sc_)
+        assert e <= TOL, f"{name} gradient {e}"
+
+
+def test_autograd_function_matches_abi(torch, rx):
+    from paper_2605_24290_gb300 import autograd as AG
+    rng = np.random.default_rng(204)
+    w = S.workload_small()
+    g, sc = w["grid"], w["scene"]
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch)
+    tx = dev(w["tx"], torch)
+    op = dev(sc.opacity, torch).requires_grad_(True)
+    rad = dev(w["radiance"], torch).requires_grad_(True)
+    spec, _, _ = AG.render(ctx, h, tx, None, 8, op, radiance=rad, kind=rx.OUT_SPECTRA)
+    gs = torch.from_numpy(rng.normal(size=tuple(spec.shape)).astype(np.float32)).cuda()
+    (spec * gs).sum().backward()
+    views = ctx.prepare(h, tx)
+    d_rad = torch.zeros_like(rad)
+    d_tau = torch.zeros_like(op)
+    ctx.render_backward(views, None, 8, rx.OUT_SPECTRA, radiance=rad.detach(), grad_spectra=gs,
+                        fwd_spectra=spec.detach(), grad_radiance=d_rad, grad_opacity=d_tau)
+    ctx.sync()
+    torch.testing.assert_close(rad.grad, d_rad, rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(op.grad, d_tau, rtol=1e-5, atol=1e-5)
+
+
+def test_directional_finite_differences_on_gpu(torch, rx):
+    """100,000 Gaussians (4 transmitters x 8 receivers), MLP radiance:
+    central differences of the GPU forward along random directions over 1,000
+    random parameters (400 opacities, 500 phi_base entries, 100 MLP weights)
+    against the GPU backward.  L = sum(g * spectra) is evaluated in float64;
+    the step sizes keep the float32 rounding of the forward well below the
+    measured change."""
+    w = S.workload_mlp(M=4, N=8)
+    g, sc, C = w["grid"], w["scene"], w["C"]
+    rng = np.random.default_rng(205)
+    flat = S.flatten_mlp(w["mlp"], C)
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch, base=w["base"], mlp_flat=flat, C=C)
+    txd, rxd = dev(w["tx"], torch), dev(w["rx"], torch)
+    M, N, K = 4, 8, sc.K
+    gs = torch.from_numpy(rng.normal(size=(M, N, g.H, g.W, C, 2)).astype(np.float32)).cuda()
+    op0 = dev(sc.opacity, torch)
+    base0 = dev(w["base"], torch)
+    mlp0 = dev(flat, torch)
+
+    def loss(op, base, mlp):
+        ctx.update_scene(h, opacity=op, base=base, mlp=mlp)
+        views = ctx.prepare(h, txd)
+        spec = torch.zeros((M, N, g.H, g.W, C, 2), device="cuda")
+        ctx.render_views(views, rxd, N, rx.OUT_SPECTRA, spectra=spec)
+        ctx.release_views(views)
+        return float((spec.double() * gs.double()).sum()), spec
+
+    L0, spec0 = loss(op0, base0, mlp0)
+    views = ctx.prepare(h, txd)
+    d_tau = torch.zeros(K, device="cuda")
+    d_base = torch.zeros((K, C, 2), device="cuda")
+    d_mlp = torch.zeros_like(mlp0)
+    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=gs, fwd_spectra=spec0,
+                        grad_opacity=d_tau, grad_base=d_base, grad_mlp=d_mlp)
+    ctx.sync()
+    ctx.release_views(views)
+    ip = torch.from_numpy(rng.choice(K, 400, replace=False)).cuda()
+    ib = torch.from_numpy(rng.choice(K * C * 2, 500, replace=False)).cuda()
+    # local-branch output weights and biases (they modulate every radiance)
+    lw2 = S.mlp_shapes(C)
+    off = 0
+    offs = {}
+    for name, shp in lw2:
+        offs[name] = off
+        off += int(np.prod(shp))
+    cand = np.arange(offs["l_w2"], offs["l_b2"] + 4 * C)
+    im = torch.from_numpy(rng.choice(cand, 100, replace=False)).cuda()
+    for trial in range(4):
+        dp = torch.from_numpy(rng.choice([-1.0, 1.0], 400).astype(np.float32)).cuda()
+        db = torch.from_numpy(rng.choice([-1.0, 1.0], 500).astype(np.float32)).cuda()
+        dm = torch.from_numpy(rng.choice([-1.0, 1.0], 100).astype(np.float32)).cuda()
+        hp, hb, hm = 2e-3, 0.5, 2e-3
+        an = (float((d_tau[ip] * dp).double().sum()) * hp + float((d_base.view(-1)[ib] * db).double().sum()) * hb
+              + float((d_mlp[im] * dm).double().sum()) * hm)
+
+        def shifted(sign):
+            op = op0.clone()
+            op[ip] += sign * hp * dp
+            bs = base0.clone().view(-1)
+            bs[ib] += sign * hb * db
+            ml = mlp0.clone()
+            ml[im] += sign * hm * dm
+            return op, bs.view_as(base0), ml
+
+        opp, bp, mp = shifted(+1)
+        opm, bm, mm = shifted(-1)
+        # the actual (float32-rounded) steps are what the forward saw
+        an = (float((d_tau[ip].double() * (opp[ip] - op0[ip]).double()).sum())
+              + float((d_base.view(-1)[ib].double() * (bp.view(-1)[ib] - base0.view(-1)[ib]).double()).sum())
+              + float((d_mlp[im].double() * (mp[im] - mlp0[im]).double()).sum()))
+        Lp, _ = loss(opp, bp, mp)
+        Lm, _ = loss(opm, bm, mm)
+        fd = (Lp - Lm) / 2.0
+        noise = 64 * 2.0 ** -24 * float((spec0.double() * gs.double()).abs().sum())
+        assert abs(fd - an) <= 2e-3 * abs(an) + noise, (trial, fd, an, noise)
+    ctx.update_scene(h, opacity=op0, base=base0, mlp=mlp0)
