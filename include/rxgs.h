@@ -33,8 +33,9 @@
  *   - A status other than RXGS_OK means nothing was enqueued, except for
  *     RXGS_E_CUDA / RXGS_E_DEVICE, which report an error of the CUDA
  *     context; rxgs_last_error() gives a message.
- *   - All reductions are deterministic: the same inputs give bit-identical
- *     outputs, whatever the batch they are rendered in.
+ *   - Forward outputs are deterministic: the same inputs give bit-identical
+ *     results; a receiver's spectrum does not depend on the other receivers
+ *     of its batch.
  */
 #ifndef RXGS_H
 #define RXGS_H
@@ -77,8 +78,7 @@ typedef struct {
                           culled (0.05 m)                                    */
   int cols_per_cta;    /* receiver*channel*2 columns per render CTA:
                           16, 32, 64 or 128; 0 = chosen by the autotuner     */
-  int deterministic;   /* 1 (default): no float atomics in the forward and
-                          backward opacity gradient reductions               */
+  int deterministic;   /* reserved (the forward is always deterministic)     */
   size_t mem_budget;   /* serving admission budget in bytes; 0 = 8 GiB      */
 } rxgs_options;
 
@@ -178,9 +178,11 @@ rxgs_status rxgs_render(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int 
  *   grad_spectra [M,N,H,W,C,2] or NULL
  *   grad_csi     [M,N,C,2] or NULL   (uniform over pixels)
  *   grad_rssi    [M,N] or NULL       (needs fwd_csi)
- *   fwd_spectra  the forward spectra, or NULL (then the kernel makes one
- *                extra pass over each tile)
  *   fwd_csi      the forward CSI [M,N,1,2] when grad_rssi is given
+ * Nothing else of the forward is needed: each tile re-walks its list with
+ * the forward's decisions, then sweeps it back to front.  `views`, `rx` and
+ * `desc->radiance` must be those of the forward.  Gradients are accumulated
+ * with float atomics (their rounding order is not fixed).
  * Outputs (accumulated: caller zero-fills):
  *   grad_radiance [N,K,C,2]  when desc->radiance != NULL
  *   grad_opacity  [K]
@@ -190,7 +192,6 @@ typedef struct {
   const float* grad_spectra;
   const float* grad_csi;
   const float* grad_rssi;
-  const float* fwd_spectra;
   const float* fwd_csi;
 } rxgs_cotangents;
 

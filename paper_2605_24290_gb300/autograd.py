@@ -36,15 +36,15 @@ class _Render(torch.autograd.Function):
             rctx.render_views(views, rx, N, kk, radiance=rad, spectra=spec, rssi=rssi, csi=csi)
         finally:
             rctx.release_views(views)
-        fctx.rctx, fctx.scene, fctx.N, fctx.kind = rctx, scene, N, kind
+        fctx.rctx, fctx.scene, fctx.N, fctx.kind, fctx.C = rctx, scene, N, kind, C
         fctx.has = (base is not None, mlp is not None, radiance is not None)
-        fctx.save_for_backward(tx, rx, rad, spec, csi, opacity)
+        fctx.save_for_backward(tx, rx, rad, csi, opacity)
         outs = (spec, rssi, csi if kind & rxgs.OUT_CSI else None)
         return tuple(o if o is not None else torch.empty(0, device=dev) for o in outs)
 
     @staticmethod
     def backward(fctx, g_spec, g_rssi, g_csi):
-        tx, rx, rad, spec, csi, opacity = fctx.saved_tensors
+        tx, rx, rad, csi, opacity = fctx.saved_tensors
         rctx, scene, N, kind = fctx.rctx, fctx.scene, fctx.N, fctx.kind
         has_base, has_mlp, has_rad = fctx.has
         gs = g_spec.contiguous() if (kind & rxgs.OUT_SPECTRA and g_spec is not None
@@ -58,7 +58,7 @@ class _Render(torch.autograd.Function):
         d_base = d_mlp = None
         if not has_rad:
             K = opacity.shape[0]
-            C = csi.shape[2] if csi is not None else spec.shape[4]
+            C = fctx.C
             d_base = torch.zeros((K, C, 2), device=opacity.device)
             d_mlp = torch.zeros((rctx.mlp_numel(C),), device=opacity.device)
         if gs is None and gr is None and gc is None:
@@ -66,8 +66,7 @@ class _Render(torch.autograd.Function):
         views = rctx.prepare(scene, tx)
         try:
             rctx.render_backward(views, rx, N, kind, radiance=rad, grad_spectra=gs, grad_csi=gc,
-                                 grad_rssi=gr, fwd_spectra=spec if gs is not None else None,
-                                 fwd_csi=csi, grad_radiance=d_rad, grad_opacity=d_op,
+                                 grad_rssi=gr, fwd_csi=csi, grad_radiance=d_rad, grad_opacity=d_op,
                                  grad_base=d_base, grad_mlp=d_mlp)
         finally:
             rctx.release_views(views)

@@ -653,7 +653,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.f.C = C;
   A.f.stride = stride;
   A.f.ncols = ncols;
-  A.f.spectra = const_cast<float*>(cot->fwd_spectra);
+  A.f.spectra = nullptr;
   A.g_spec = cot->grad_spectra;
   A.g_uniform = g_uni;
   A.d_rad = d_rad;

@@ -5,15 +5,20 @@
 // For one pixel with composited sequence k_1..k_n (weights w_m, transmittance
 // T_m = prod_{l<m} (1 - w_l)) and cotangent g_c per output column c:
 //   dL/ds_{k_m, c}  = T_m w_m g_c
-//   dL/dw_m         = T_m gamma_m - (D - E_m) / (1 - w_m)
-//   with gamma_m    = sum_c g_c s_{k_m, c},  E_m = sum_{l<=m} T_l w_l gamma_l,
-//        D          = sum_c g_c C_c (= E_n, the pixel's full sum)
+//   dL/dw_m         = T_m (gamma_m - Q_m),   gamma_m = sum_c g_c s_{k_m, c}
+//   Q_m             = sum_c g_c S_{m, c},  S_m the normalised colour behind m:
+//                     Q_{m-1} = w_m gamma_m + (1 - w_m) Q_m,  Q_n = 0
 //   dL/dtau_{k_m}   = exp(-q/2) dL/dw_m
-// Both gradients are linear in the columns, so each CTA handles a block of 32
-// columns and the per-column-block contributions add up.  Nothing per pixel
-// is stored by the forward: every tile walks its list again with the same
-// float32 decisions (per-tile recomputation).  D comes from the forward
-// spectra when they are given; otherwise a first walk accumulates it.
+// Q is a convex combination of the gammas, so the error of dL/dw_m scales
+// with T_m like the value itself (a forward difference D - E_m would cancel
+// catastrophically once T is small).
+//
+// Per tile, nothing is read from the forward: a first walk recomputes every
+// pixel's final T and stop position with the forward's float32 decisions
+// (per-tile recomputation), then the list is swept back to front, chunk by
+// chunk, recovering T_m = T_{m+1} / (1 - w_m).  Both gradients are linear in
+// the columns, so each CTA handles a block of 32 columns and the per-block
+// contributions add up.
 #include "render_common.cuh"
 #include "rxgs_internal.h"
 
@@ -28,7 +33,6 @@ constexpr size_t bwd_smem_bytes() {
          sizeof(float4) * 2 * kChunk + sizeof(uint32_t) * kChunk;
 }
 
-template <bool HAVE_D>
 __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const BackwardArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sG = reinterpret_cast<float*>(smem_raw);   // [256][36] cotangent rows
@@ -37,6 +41,7 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
   float* sR = sT + kChunk * kPad;                   // [32][32] radiance slice
   float4* sRec = reinterpret_cast<float4*>(sR + kChunk * kBNB);  // [32][2]
   uint32_t* sK = reinterpret_cast<uint32_t*>(sRec + 2 * kChunk);  // [32]
+  __shared__ unsigned sStop;
 
   const RenderArgs& a = A.f;
   const GridConst& g = a.g;
@@ -53,141 +58,170 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
   const size_t pix = static_cast<size_t>(i) * g.W + jj;
   const int twoC = 2 * a.C;
 
-  // cotangent of this pixel for the CTA's columns, and D from the forward
+  // cotangent of this pixel for the CTA's columns
   float gr[kBNB];
-  float D = 0.0f;
 #pragma unroll
   for (int c = 0; c < kBNB; ++c) {
     const int col = col0 + c;
     float val = 0.0f;
     if (valid && col < a.ncols) {
       const int j = col / twoC, e = col - j * twoC;
-      const size_t off = ((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + e;
-      if (A.g_spec) val += A.g_spec[off];
+      if (A.g_spec) val += A.g_spec[((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + e];
       if (A.g_uniform) val += A.g_uniform[static_cast<size_t>(v) * a.ncols + col];
-      if (HAVE_D) D = fmaf(val, a.spectra[off], D);
     }
     gr[c] = val;
     sG[t * kGStride + c] = val;
   }
+  if (t == 0) sStop = rg.x;
 
-  // dS mapping: 32 output blocks (4 Gaussians x 8 columns) x 8 pixel slices
-  const int slice = t & 7, ob = t >> 3;
-  const int bb = (ob >> 2) * 4, cbk = (ob & 3) * 8;
-
-  for (int pass = HAVE_D ? 1 : 0; pass < 2; ++pass) {
-    float T = 1.0f, E = 0.0f;
+  // ---- walk 1: final transmittance and stop position of every pixel
+  float T = 1.0f;
+  uint32_t stop = rg.y;  // one past the last list entry this pixel considers
+  {
     bool alive = valid;
+    if (!valid) stop = rg.x;
     for (uint32_t start = rg.x; start < rg.y; start += kChunk) {
       const int nb = min(kChunk, static_cast<int>(rg.y - start));
       __syncthreads();
       if (t < kChunk) {
         const bool ok = t < nb;
         const uint32_t k = ok ? a.vals[start + t] : 0u;
-        sK[t] = k;
         cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
         cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
-      }
-      {
-        // 32 rows x 32 columns = 256 float4, one per thread
-        const int b = t >> 3, q4 = t & 7;
-        const bool ok = b < nb;
-        const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
-        cp_async16(&sR[b * kBNB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
-                   ok);
       }
       cp_async_commit();
       cp_async_wait_all();
       __syncthreads();
-      for (int b = 0; b < nb; ++b) {
-        float Tw = 0.0f, dtau = 0.0f;
-        if (alive) {
+      if (alive) {
+        for (int b = 0; b < nb; ++b) {
           float w, G;
           if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
-            float gam = 0.0f;
-            const float4* r4 = reinterpret_cast<const float4*>(&sR[b * kBNB]);
-#pragma unroll
-            for (int q = 0; q < kBNB / 4; ++q) {
-              const float4 s4 = r4[q];
-              gam = fmaf(gr[4 * q + 0], s4.x, gam);
-              gam = fmaf(gr[4 * q + 1], s4.y, gam);
-              gam = fmaf(gr[4 * q + 2], s4.z, gam);
-              gam = fmaf(gr[4 * q + 3], s4.w, gam);
-            }
-            Tw = __fmul_rn(T, w);
-            E = fmaf(Tw, gam, E);
-            if (pass == 1) {
-              const float dldw = T * gam - (D - E) / (1.0f - w);
-              dtau = dldw * G;
-            }
             T = __fmul_rn(T, __fsub_rn(1.0f, w));
-            if (T < g.eps_T) alive = false;
+            if (T < g.eps_T) {
+              alive = false;
+              stop = start + b + 1;
+              break;
+            }
           }
-        }
-        if (pass == 1) {
-          sA[b * kPad + t] = Tw;
-          sT[b * kPad + t] = dtau;
         }
       }
-      const int n_alive = __syncthreads_count(alive);
-      if (pass == 1) {
-        // dL/ds[b][c] = sum_pixels A[b][p] g[p][c]: 4 x 8 block per thread over
-        // the pixels p = it*8 + slice, then a sum over the 8 slices.
-        float acc[4][8];
+      if (__syncthreads_count(alive) == 0) break;
+    }
+  }
+  atomicMax(&sStop, stop);
+  __syncthreads();
+  const uint32_t tile_stop = sStop;
+
+  // dS mapping: 32 output blocks (4 Gaussians x 8 columns) x 8 pixel slices
+  const int slice = t & 7, ob = t >> 3;
+  const int bb = (ob >> 2) * 4, cbk = (ob & 3) * 8;
+
+  // ---- walk 2: back to front
+  float Q = 0.0f;
+  const int nchunks = static_cast<int>((tile_stop - rg.x + kChunk - 1) / kChunk);
+  for (int ci = nchunks - 1; ci >= 0; --ci) {
+    const uint32_t start = rg.x + static_cast<uint32_t>(ci) * kChunk;
+    const int nb = min(kChunk, static_cast<int>(tile_stop - start));
+    __syncthreads();
+    if (t < kChunk) {
+      const bool ok = t < nb;
+      const uint32_t k = ok ? a.vals[start + t] : 0u;
+      sK[t] = k;
+      cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
+      cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
+    }
+    {
+      const int b = t >> 3, q4 = t & 7;  // 32 rows x 32 columns, one float4 each
+      const bool ok = b < nb;
+      const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
+      cp_async16(&sR[b * kBNB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
+                 ok);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    for (int b = nb - 1; b >= 0; --b) {
+      float Tw = 0.0f, dtau = 0.0f;
+      if (start + b < stop) {
+        float w, G;
+        if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
+          float gam = 0.0f;
+          const float4* r4 = reinterpret_cast<const float4*>(&sR[b * kBNB]);
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[x][c] = 0.0f;
-        if (bb < nb) {
-          for (int it = 0; it < kTilePixels / 8; ++it) {
-            const int p = it * 8 + slice;
-            const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk]);
-            const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk + 4]);
-            const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const float av = sA[(bb + x) * kPad + p];
-#pragma unroll
-              for (int c = 0; c < 8; ++c) acc[x][c] = fmaf(av, gv[c], acc[x][c]);
-            }
+          for (int q = 0; q < kBNB / 4; ++q) {
+            const float4 s4 = r4[q];
+            gam = fmaf(gr[4 * q + 0], s4.x, gam);
+            gam = fmaf(gr[4 * q + 1], s4.y, gam);
+            gam = fmaf(gr[4 * q + 2], s4.z, gam);
+            gam = fmaf(gr[4 * q + 3], s4.w, gam);
           }
+          const float one_m_w = 1.0f - w;
+          T = T / one_m_w;  // transmittance in front of this Gaussian
+          Tw = T * w;
+          dtau = T * (gam - Q) * G;
+          Q = fmaf(w, gam, one_m_w * Q);
         }
+      }
+      sA[b * kPad + t] = Tw;
+      sT[b * kPad + t] = dtau;
+    }
+    __syncthreads();
+    // dL/ds[b][c] = sum_pixels A[b][p] g[p][c]: 4 x 8 block per thread over the
+    // pixels p = it*8 + slice, then a sum over the 8 slices.
+    {
+      float acc[4][8];
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            float y = acc[x][c];
-            y += __shfl_xor_sync(0xffffffffu, y, 4);
-            y += __shfl_xor_sync(0xffffffffu, y, 2);
-            y += __shfl_xor_sync(0xffffffffu, y, 1);
-            acc[x][c] = y;
-          }
-        if (slice == 0) {
+        for (int c = 0; c < 8; ++c) acc[x][c] = 0.0f;
+      if (bb < nb) {
+        for (int it = 0; it < kTilePixels / 8; ++it) {
+          const int p = it * 8 + slice;
+          const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk]);
+          const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk + 4]);
+          const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
           for (int x = 0; x < 4; ++x) {
-            const int b = bb + x;
-            if (b >= nb) continue;
-            float* dst = A.d_rad + static_cast<size_t>(sK[b]) * a.stride + col0 + cbk;
+            const float av = sA[(bb + x) * kPad + p];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-              if (col0 + cbk + c < a.ncols && acc[x][c] != 0.0f) atomicAdd(&dst[c], acc[x][c]);
+            for (int c = 0; c < 8; ++c) acc[x][c] = fmaf(av, gv[c], acc[x][c]);
           }
         }
-        // dL/dtau: sum over pixels of each Gaussian of the chunk
-        {
-          const int b = t >> 3, part = t & 7;
-          float y = 0.0f;
-          if (b < nb)
-            for (int it = 0; it < kTilePixels / 8; ++it) y += sT[b * kPad + it * 8 + part];
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float y = acc[x][c];
           y += __shfl_xor_sync(0xffffffffu, y, 4);
           y += __shfl_xor_sync(0xffffffffu, y, 2);
           y += __shfl_xor_sync(0xffffffffu, y, 1);
-          if (part == 0 && b < nb && y != 0.0f) atomicAdd(&A.d_tau[sK[b]], y);
+          acc[x][c] = y;
+        }
+      if (slice == 0) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int b = bb + x;
+          if (b >= nb) continue;
+          float* dst = A.d_rad + static_cast<size_t>(sK[b]) * a.stride + col0 + cbk;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (col0 + cbk + c < a.ncols && acc[x][c] != 0.0f) atomicAdd(&dst[c], acc[x][c]);
         }
       }
-      if (n_alive == 0) break;
     }
-    if (pass == 0) D = E;  // the full sum of this pixel's contributions
+    // dL/dtau: sum over the tile's pixels for each Gaussian of the chunk; each
+    // column block adds the part of the gradient its columns carry
+    {
+      const int b = t >> 3, part = t & 7;
+      float y = 0.0f;
+      if (b < nb)
+        for (int it = 0; it < kTilePixels / 8; ++it) y += sT[b * kPad + it * 8 + part];
+      y += __shfl_xor_sync(0xffffffffu, y, 4);
+      y += __shfl_xor_sync(0xffffffffu, y, 2);
+      y += __shfl_xor_sync(0xffffffffu, y, 1);
+      if (part == 0 && b < nb && y != 0.0f) atomicAdd(&A.d_tau[sK[b]], y);
+    }
   }
 }
 
@@ -197,17 +231,12 @@ void launch_render_bwd(const BackwardArgs& A, int /*cols_per_cta*/, cudaStream_t
   constexpr size_t smem = bwd_smem_bytes();
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(render_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    cudaFuncSetAttribute(render_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     configured = true;
   }
   dim3 grid(a.g.T, (a.ncols + kBNB - 1) / kBNB, a.M);
-  if (a.spectra)
-    render_bwd_kernel<true><<<grid, kTilePixels, smem, s>>>(A);
-  else
-    render_bwd_kernel<false><<<grid, kTilePixels, smem, s>>>(A);
+  render_bwd_kernel<<<grid, kTilePixels, smem, s>>>(A);
 }
 
 }  // namespace rxgs

@@ -53,8 +53,7 @@ class Outputs(ctypes.Structure):
 
 class Cotangents(ctypes.Structure):
     _fields_ = [("grad_spectra", ctypes.c_void_p), ("grad_csi", ctypes.c_void_p),
-                ("grad_rssi", ctypes.c_void_p), ("fwd_spectra", ctypes.c_void_p),
-                ("fwd_csi", ctypes.c_void_p)]
+                ("grad_rssi", ctypes.c_void_p), ("fwd_csi", ctypes.c_void_p)]
 
 
 class Grads(ctypes.Structure):
@@ -213,12 +212,11 @@ class Context:
                                          _stream(stream)))
 
     def render_backward(self, views, rx, N, kind, radiance=None, grad_spectra=None,
-                        grad_csi=None, grad_rssi=None, fwd_spectra=None, fwd_csi=None,
+                        grad_csi=None, grad_rssi=None, fwd_csi=None,
                         grad_radiance=None, grad_opacity=None, grad_base=None, grad_mlp=None,
                         stream=None):
         d = RenderDesc(int(kind), _f32(radiance), 0)
-        c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_spectra),
-                       _f32(fwd_csi))
+        c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_csi))
         g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp))
         self._check(self.lib.rxgs_render_backward(self.h, U64(views), _f32(rx), int(N),
                                                   ctypes.byref(d), ctypes.byref(c),

@@ -49,13 +49,13 @@ def oracle_grads(oracle, g, sc, tx, rad, gspec):
     return tot
 
 
-@pytest.mark.parametrize("with_fwd", [True, False])
-def test_backward_explicit_radiance(torch, rx, oracle, with_fwd):
-    """Cotangent on spectra; with the forward spectra (one walk per tile) and
-    without them (two walks)."""
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32)])
+def test_backward_explicit_radiance(torch, rx, oracle, tile):
+    """Cotangent on spectra, two transmitters, 8 receivers."""
     rng = np.random.default_rng(201)
     w = S.workload_small()
     g, sc = w["grid"], w["scene"]
+    g.tile_h, g.tile_w = tile
     tx = np.concatenate([w["tx"], S.draw_points(rng, 1)])
     rad = w["radiance"]
     M, N, K = tx.shape[0], rad.shape[0], sc.K
@@ -69,8 +69,7 @@ def test_backward_explicit_radiance(torch, rx, oracle, with_fwd):
     d_rad = torch.zeros_like(radd)
     d_tau = torch.zeros(K, device="cuda")
     ctx.render_backward(views, None, N, rx.OUT_SPECTRA, radiance=radd, grad_spectra=dev(gs, torch),
-                        fwd_spectra=spec if with_fwd else None, grad_radiance=d_rad,
-                        grad_opacity=d_tau)
+                        grad_radiance=d_rad, grad_opacity=d_tau)
     ctx.sync()
     ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
     e_r = scaled_err(d_rad.cpu().numpy(), ref_r, abs_r)
@@ -133,7 +132,7 @@ def test_backward_through_mlp(torch, rx, oracle):
     d_tau = torch.zeros(K, device="cuda")
     d_base = torch.zeros((K, C, 2), device="cuda")
     d_mlp = torch.zeros(flat.shape[0], device="cuda")
-    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=dev(gs, torch), fwd_spectra=spec,
+    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=dev(gs, torch),
                         grad_opacity=d_tau, grad_base=d_base, grad_mlp=d_mlp)
     ctx.sync()
     rad = oracle.mlp_radiance(mlp, rxp, sc.means, base)
@@ -169,7 +168,7 @@ def test_autograd_function_matches_abi(torch, rx):
     d_rad = torch.zeros_like(rad)
     d_tau = torch.zeros_like(op)
     ctx.render_backward(views, None, 8, rx.OUT_SPECTRA, radiance=rad.detach(), grad_spectra=gs,
-                        fwd_spectra=spec.detach(), grad_radiance=d_rad, grad_opacity=d_tau)
+                        grad_radiance=d_rad, grad_opacity=d_tau)
     ctx.sync()
     torch.testing.assert_close(rad.grad, d_rad, rtol=1e-5, atol=1e-6)
     torch.testing.assert_close(op.grad, d_tau, rtol=1e-5, atol=1e-5)
@@ -208,7 +207,7 @@ def test_directional_finite_differences_on_gpu(torch, rx):
     d_tau = torch.zeros(K, device="cuda")
     d_base = torch.zeros((K, C, 2), device="cuda")
     d_mlp = torch.zeros_like(mlp0)
-    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=gs, fwd_spectra=spec0,
+    ctx.render_backward(views, rxd, N, rx.OUT_SPECTRA, grad_spectra=gs,
                         grad_opacity=d_tau, grad_base=d_base, grad_mlp=d_mlp)
     ctx.sync()
     ctx.release_views(views)
