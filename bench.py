@@ -1,0 +1,429 @@
+"""Benchmark: receiver spectra per second, batched vs a per-receiver loop.
+
+Workload (one step = the whole hot path over one batch):
+  100,000 Gaussians in a 10x8x3 m box, 32 transmitters x 64 receivers,
+  radiance from the 2-layer 64-wide conditioning MLP, 90x360 grid, 16x16
+  tiles.  A step = transmitter-side preparation (projection, key emission,
+  radix sort, tile ranges), MLP radiance, compositing into 2,048 spectra plus
+  their CSI/RSSI reduction, and the backward pass to opacity, phi_base and
+  the MLP weights for an N(0,1) cotangent on the spectra.
+  value = spectra per second = 2,048 / step time (inputs resident in HBM).
+
+Also reported: the per-receiver loop (the same kernels, one (tx, rx) pair per
+call, the full pipeline per pair), the end-to-end figure through the C ABI
+with host buffers (pinned H2D of the step's inputs, D2H of its gradients and
+RSSI), the roofline of the dominant kernel, clocks during the timed region
+and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs the same workload on its own GPU (independent
+transmitter batches; no collective on the data path) and rank 0 prints the
+whole-job throughput.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "receiver spectra/sec batched vs per-rx loop, same GB300; p50/p99 serve ms"
+UNIT = "spectra/s"
+WORKLOAD = "100k Gaussians, 32 tx x 64 rx, MLP radiance (2-layer, 64 wide), 90x360 grid, fwd+bwd"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.idx = gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- the step
+class Workload:
+    def __init__(self, torch, rxgs, S, device):
+        self.torch = torch
+        w = S.workload_mlp()
+        self.w = w
+        g, sc, C = w["grid"], w["scene"], w["C"]
+        self.g, self.C = g, C
+        self.M, self.N, self.K = w["tx"].shape[0], w["rx"].shape[0], sc.K
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.ctx = rxgs.Context(H=g.H, W=g.W)
+        self.rxgs = rxgs
+        flat = S.flatten_mlp(w["mlp"], C)
+        self.nmlp = flat.shape[0]
+        self.scene = self.ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats),
+                                           d(sc.opacity), d(w["base"]), d(flat), C=C)
+        self.tx, self.rx = d(w["tx"]), d(w["rx"])
+        M, N, K = self.M, self.N, self.K
+        self.spec = torch.empty((M, N, g.H, g.W, C, 2), device=device)
+        self.csi = torch.empty((M, N, C, 2), device=device)
+        self.rssi = torch.empty((M, N), device=device)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(S.SEED_BASE + 1)
+        self.gspec = torch.randn((M, N, g.H, g.W, C, 2), device=device, generator=gen)
+        self.d_tau = torch.zeros(K, device=device)
+        self.d_base = torch.zeros((K, C, 2), device=device)
+        self.d_mlp = torch.zeros(self.nmlp, device=device)
+        self.kind = rxgs.OUT_SPECTRA | rxgs.OUT_CSI | rxgs.OUT_RSSI
+
+    def step(self, tx=None, rx=None, gspec=None):
+        c, rx_ = self.ctx, self.rxgs
+        tx = self.tx if tx is None else tx
+        rx = self.rx if rx is None else rx
+        gspec = self.gspec if gspec is None else gspec
+        views = c.prepare(self.scene, tx)
+        c.render_views(views, rx, self.N, self.kind, spectra=self.spec, csi=self.csi, rssi=self.rssi)
+        self.d_tau.zero_()
+        self.d_base.zero_()
+        self.d_mlp.zero_()
+        c.render_backward(views, rx, self.N, rx_.OUT_SPECTRA, grad_spectra=gspec,
+                          grad_opacity=self.d_tau, grad_base=self.d_base, grad_mlp=self.d_mlp)
+        c.release_views(views)
+
+    def loop_pair(self, i, j, spec1, g1):
+        """One (tx, rx) pair through the full pipeline, forward + backward."""
+        c, rx_ = self.ctx, self.rxgs
+        views = c.prepare(self.scene, self.tx[i:i + 1])
+        c.render_views(views, self.rx[j:j + 1], 1, rx_.OUT_SPECTRA, spectra=spec1)
+        c.render_backward(views, self.rx[j:j + 1], 1, rx_.OUT_SPECTRA, grad_spectra=g1,
+                          grad_opacity=self.d_tau, grad_base=self.d_base, grad_mlp=self.d_mlp)
+        c.release_views(views)
+
+    def composited_pairs(self):
+        """Number of (pixel, Gaussian) pairs composited per step (each
+        transmitter's pixels x the Gaussians each pixel composites)."""
+        t = self.torch
+        ncon = t.zeros((self.M, self.g.H, self.g.W), dtype=t.int32, device=self.tx.device)
+        views = self.ctx.prepare(self.scene, self.tx)
+        self.ctx.render_views(views, self.rx, self.N, self.rxgs.OUT_SPECTRA, spectra=self.spec,
+                              ncontrib=ncon)
+        self.ctx.release_views(views)
+        return int(ncon.sum().item())
+
+
+def l2_flush(torch, buf):
+    buf.add_(1.0)
+
+
+def gpu_bench(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_24290_gb300 import rxgs
+    from paper_2605_24290_gb300 import synthetic as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = Workload(torch, rxgs, S, dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        W.step()
+    barrier()
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed between steps
+    stream = torch.cuda.current_stream()
+    W.ctx.profile(True)
+    W.ctx.profile_read(reset=True)
+    launches0 = W.ctx.profile_read(reset=False)["kernel_launches"]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            l2_flush(torch, flush)
+            evs[k][0].record(stream)
+            W.step()
+            evs[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    prof = W.ctx.profile_read(reset=True)
+    W.ctx.profile(False)
+    launches = prof["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    spectra_per_step = W.M * W.N
+    value = world * spectra_per_step / (ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel
+    stages = prof["stages"]
+    calls = max(1, stages.get("render_fwd", {}).get("calls", 1))
+    dom = max(stages.items(), key=lambda kv: kv[1]["ms"])[0] if stages else "render_fwd"
+    P = W.composited_pairs()
+    pk, src = peaks()
+    roof = None
+    if "render_fwd" in stages:
+        fwd_ms = stages["render_fwd"]["ms"] / stages["render_fwd"]["calls"]
+        flops = P * (16 + 4 * W.N * W.C)
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = fp32_alu_peak_tflops(sm_mhz)
+        ach = flops / (fwd_ms / 1e3) / 1e12
+        roof = {"kernel": "render_fwd", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
+                "units": f"{P} composited (pixel, Gaussian) pairs x (16 + 4*N*C) flops",
+                "launch_ms": round(fwd_ms, 4)}
+
+    # ---- per-receiver loop on a bounded sample of pairs (same kernels)
+    loop = None
+    if rank == 0 and not args.no_loop:
+        spec1 = torch.empty((1, 1, W.g.H, W.g.W, W.C, 2), device=dev)
+        g1 = W.gspec[0:1, 0:1].contiguous()
+        pairs = [(i % W.M, (7 * i) % W.N) for i in range(args.loop_pairs)]
+        for (i, j) in pairs[:3]:
+            W.loop_pair(i, j, spec1, g1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for (i, j) in pairs:
+            W.loop_pair(i, j, spec1, g1)
+        b.record()
+        torch.cuda.synchronize()
+        lms = a.elapsed_time(b)
+        loop = {"value": round(len(pairs) / (lms / 1e3), 2), "unit": UNIT,
+                "sample": f"{len(pairs)} (tx, rx) pairs, each prepare + MLP + forward + backward",
+                "ms_per_pair": round(lms / len(pairs), 4),
+                "batched_over_loop": round((spectra_per_step / (ms_max / 1e3)) / (len(pairs) / (lms / 1e3)), 2)}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_tx = torch.from_numpy(W.w["tx"]).pin_memory()
+        h_rx = torch.from_numpy(W.w["rx"]).pin_memory()
+        h_g = torch.empty(W.gspec.shape, dtype=torch.float32).pin_memory()
+        h_g.copy_(W.gspec.cpu())
+        d_tx, d_rx = torch.empty_like(W.tx), torch.empty_like(W.rx)
+        d_g = torch.empty_like(W.gspec)
+        o_tau = torch.empty(W.K).pin_memory()
+        o_base = torch.empty((W.K, W.C, 2)).pin_memory()
+        o_mlp = torch.empty(W.nmlp).pin_memory()
+        o_rssi = torch.empty((W.M, W.N)).pin_memory()
+        h2d = h_tx.numel() * 4 + h_rx.numel() * 4 + h_g.numel() * 4
+        d2h = (o_tau.numel() + o_base.numel() + o_mlp.numel() + o_rssi.numel()) * 4
+
+        def e2e_step():
+            d_tx.copy_(h_tx, non_blocking=True)
+            d_rx.copy_(h_rx, non_blocking=True)
+            d_g.copy_(h_g, non_blocking=True)
+            W.step(d_tx, d_rx, d_g)
+            o_tau.copy_(W.d_tau, non_blocking=True)
+            o_base.copy_(W.d_base, non_blocking=True)
+            o_mlp.copy_(W.d_mlp, non_blocking=True)
+            o_rssi.copy_(W.rssi, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        n_e = max(3, args.steps // 2)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e):
+            e2e_step()
+        barrier()
+        e_ms = (time.perf_counter() - t0) * 1e3 / n_e
+        te = torch.tensor([e_ms], device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e_ms = float(te.item())
+        e2e = {"value": round(world * spectra_per_step / (e_ms / 1e3), 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(e_ms, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_sample(args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; indoor-room scene recipe)",
+            "config": {"workload": WORKLOAD, "gaussians": W.K, "transmitters": W.M,
+                       "receivers": W.N, "grid": [W.g.H, W.g.W], "tile": [16, 16],
+                       "spectra_per_step": spectra_per_step,
+                       "step": "prepare + MLP + forward (spectra, CSI, RSSI) + backward",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "wall_s": round(wall, 3),
+            "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
+            "dominant_stage": dom,
+            "roofline": roof,
+            "per_rx_loop": loop,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_sample(budget_s=15.0, steps=1, npx=16384):
+    """The oracle on a bounded sample of the same workload: one transmitter,
+    one receiver, the forward and backward over a random pixel subset (plus
+    the MLP radiance and its backward for that receiver); scaled to spectra
+    per second by the sampled fraction of the grid."""
+    from oracle import oracle as O
+    from paper_2605_24290_gb300 import synthetic as S
+    O.build()
+    w = S.workload_mlp()
+    g, sc = w["grid"], w["scene"]
+    rng = np.random.default_rng(1)
+    HW = g.H * g.W
+    t_tot, frac_tot = 0.0, 0.0
+    for s in range(steps):
+        pix = rng.choice(HW, size=npx, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        rad = O.mlp_radiance(w["mlp"], w["rx"][s:s + 1], sc.means, w["base"])
+        O.render_pixels(g, sc, w["tx"][s], rad, pix)
+        gsp = rng.normal(size=(npx, 1, 1, 2))
+        gr, gt = O.backward_pixels(g, sc, w["tx"][s], rad, pix, gsp)
+        O.mlp_backward(w["mlp"], w["rx"][s:s + 1], sc.means, w["base"], gr)
+        t_tot += time.perf_counter() - t0
+        frac_tot += npx / HW
+    return {"value": round(frac_tot / t_tot, 4), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{steps} x (1 tx, 1 rx, {npx} of {HW} pixels) forward+backward incl. MLP; "
+                      f"scaled by the pixel fraction",
+            "seconds": round(t_tot, 2)}
+
+
+def reference_bench(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    npx = 4096
+    for _ in range(args.warmup):
+        cpu_sample(steps=1, npx=npx)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        r = cpu_sample(steps=1, npx=npx)
+        vals.append(r)
+    wall = time.perf_counter() - t0
+    frac = len(vals) * (npx / (90 * 360))
+    value = frac / sum(r["seconds"] for r in vals)
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sum(r["seconds"] for r in vals) / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded; indoor-room scene recipe)",
+            "config": {"workload": WORKLOAD, "step": vals[0]["sample"]},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 2)}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rxgs", choices=["rxgs", "reference"])
+    ap.add_argument("--loop-pairs", type=int, default=64)
+    ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_bench(args)
+    else:
+        gpu_bench(args)
+
+
+if __name__ == "__main__":
+    main()

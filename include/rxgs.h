@@ -219,6 +219,18 @@ rxgs_status rxgs_views_info(rxgs_ctx* ctx, rxgs_views_t views, int64_t* n_inst);
 rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uint32_t* counts,
                               uint64_t* keys, uint32_t* vals, uint32_t* ranges, void* stream);
 
+/* Stage profiler (tracing).  While enabled, every call records a CUDA event
+ * pair on its stream around each stage (preprocess, scan, emit, sort, ranges,
+ * mlp / radiance_transpose, render_fwd, reduce, render_bwd, mlp_bwd,
+ * radiance_grad).  rxgs_profile_read waits for the recorded events, folds
+ * them into per-stage totals and writes
+ *   {"kernel_launches": L, "stages": {"<stage>": {"ms": t, "calls": n}, ...}}
+ * into json[cap] (RXGS_E_INVALID if cap is too small); reset = 1 clears the
+ * totals afterwards.  kernel_launches counts every kernel the library has
+ * launched in this process. */
+rxgs_status rxgs_profile(rxgs_ctx* ctx, int enable);
+rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset);
+
 /* Waits for `stream` and converts a recorded device error into a status. */
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream);
 

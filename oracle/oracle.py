@@ -75,6 +75,9 @@ def lib():
             _lib.or_backward_view.restype = ctypes.c_int
             _lib.or_backward_view.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
                                               ctypes.c_int, P, P, P, P, P, P, ctypes.c_int]
+            _lib.or_backward_pixels.restype = ctypes.c_int
+            _lib.or_backward_pixels.argtypes = [P, ctypes.c_int, P, P, P, P, P, ctypes.c_int,
+                                                ctypes.c_int, P, ctypes.c_int, P, P, P, P]
             _lib.or_omp_threads.restype = ctypes.c_int
     return _lib
 
@@ -227,6 +230,24 @@ def backward_view(grid, scene, centre, radiance, gspec, use_eps=True, want_abs=F
         raise MemoryError("oracle backward failed")
     if want_abs:
         return gr, gt, ar, at
+    return gr, gt
+
+
+def backward_pixels(grid, scene, centre, radiance, pix, gpix):
+    """Backward restricted to pixels pix[np] with cotangent gpix[np,N,C,2]:
+    (dL/d radiance [N,K,C,2], dL/d opacity [K])."""
+    g = make_grid(grid)
+    rad = _c64(radiance)
+    N, K, C = rad.shape[0], rad.shape[1], rad.shape[2]
+    pix = np.ascontiguousarray(pix, dtype=np.int32)
+    gr = np.zeros_like(rad)
+    gt = np.zeros(K, np.float64)
+    rc = lib().or_backward_pixels(ctypes.byref(g), K, _p(_c32(scene.means)), _p(_c32(scene.log_scales)),
+                                  _p(_c32(scene.quats)), _p(_c32(scene.opacity)), _p(_c32(centre)),
+                                  N, C, _p(rad), int(pix.shape[0]), _p(pix), _p(_c64(gpix)), _p(gr),
+                                  _p(gt))
+    if rc != 0:
+        raise MemoryError("oracle backward failed")
     return gr, gt
 
 

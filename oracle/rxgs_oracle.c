@@ -596,6 +596,80 @@ int or_render_pixels(const or_grid* g, int K, const float* p, const float* s, co
   return 0;
 }
 
+
+/* Backward of one pixel (i, jj).  gv(j, ch) points at dL/d(Re, Im) of
+ * receiver j, channel ch of this pixel.                                     */
+typedef struct {
+  int* seq;
+  double *sw, *sG, *sT, *Sb;
+} or_bwd_scratch;
+
+static void or_backward_pixel(const or_grid* g, const or_view* V, const float* tau, int i, int jj,
+                              int N, int C, const double* rad, const double* gpix,
+                              size_t gstride_j, double* grad_rad, double* grad_tau,
+                              double* abs_rad, double* abs_tau, int use_eps,
+                              or_bwd_scratch* sc) {
+  const int K = V->K;
+  float T32 = 1.0f;
+  double T64 = 1.0;
+  int n_c = 0;
+  for (int n = 0; n < V->nvis; ++n) {
+    int k = V->order[n];
+    const or_p32* P = V->P32 + k;
+    if (!or_in_footprint(g, P, i, jj)) continue;
+    float w32;
+    int m;
+    if (!or_weight32(g, P, tau[k], i, jj, &w32, &m)) continue;
+    double G;
+    double w64 = or_weight64(g, V->P64 + k, (double)tau[k], i, jj, m, &G);
+    sc->seq[n_c] = k; sc->sw[n_c] = w64; sc->sG[n_c] = G; sc->sT[n_c] = T64;
+    T32 = T32 * (1.0f - w32);
+    T64 = T64 * (1.0 - w64);
+    n_c++;
+    if (use_eps && T32 < g->eps_T) break;
+  }
+  memset(sc->Sb, 0, sizeof(double) * (size_t)N * C * 2);
+  for (int e = n_c - 1; e >= 0; --e) {
+    int k = sc->seq[e];
+    double dLdw = 0.0, adw = 0.0;
+    for (int j = 0; j < N; ++j)
+      for (int ch = 0; ch < C; ++ch) {
+        const double* gv = gpix + j * gstride_j + (size_t)ch * 2;
+        const double* sv = rad + ((((size_t)j * K + k) * C + ch) * 2);
+        double* gr = grad_rad + ((((size_t)j * K + k) * C + ch) * 2);
+        double* Sv = sc->Sb + (j * C + ch) * 2;
+        gr[0] += sc->sT[e] * sc->sw[e] * gv[0];
+        gr[1] += sc->sT[e] * sc->sw[e] * gv[1];
+        if (abs_rad) {
+          double* ar = abs_rad + ((((size_t)j * K + k) * C + ch) * 2);
+          ar[0] += sc->sT[e] * sc->sw[e] * fabs(gv[0]);
+          ar[1] += sc->sT[e] * sc->sw[e] * fabs(gv[1]);
+        }
+        dLdw += sc->sT[e] * (gv[0] * (sv[0] - Sv[0]) + gv[1] * (sv[1] - Sv[1]));
+        adw += sc->sT[e] * (fabs(gv[0]) * (fabs(sv[0]) + fabs(Sv[0])) +
+                            fabs(gv[1]) * (fabs(sv[1]) + fabs(Sv[1])));
+        Sv[0] = sc->sw[e] * sv[0] + (1.0 - sc->sw[e]) * Sv[0];
+        Sv[1] = sc->sw[e] * sv[1] + (1.0 - sc->sw[e]) * Sv[1];
+      }
+    grad_tau[k] += dLdw * sc->sG[e];
+    if (abs_tau) abs_tau[k] += adw * sc->sG[e];
+  }
+}
+
+static int or_scratch_init(or_bwd_scratch* sc, int nvis, int N, int C) {
+  size_t n = (size_t)(nvis > 0 ? nvis : 1);
+  sc->seq = (int*)malloc(sizeof(int) * n);
+  sc->sw = (double*)malloc(sizeof(double) * n);
+  sc->sG = (double*)malloc(sizeof(double) * n);
+  sc->sT = (double*)malloc(sizeof(double) * n);
+  sc->Sb = (double*)malloc(sizeof(double) * (size_t)N * C * 2);
+  return (sc->seq && sc->sw && sc->sG && sc->sT && sc->Sb) ? 0 : -1;
+}
+
+static void or_scratch_free(or_bwd_scratch* sc) {
+  free(sc->seq); free(sc->sw); free(sc->sG); free(sc->sT); free(sc->Sb);
+}
+
 /* ---------------------------------------------------------------- backward
  * Exact derivative of the render for fixed decisions (App. D backward).
  * gspec[N][H][W][C][2] = dL/d(Re, Im) of each spectrum pixel.
@@ -612,61 +686,36 @@ int or_backward_view(const or_grid* g, int K, const float* p, const float* s, co
                      double* abs_tau, int use_eps) {
   or_view V;
   if (or_view_init(&V, g, K, p, s, q, tau, c)) return -2;
+  or_bwd_scratch sc;
+  if (or_scratch_init(&sc, V.nvis, N, C)) return -2;
   const int H = g->H, W = g->W;
-  int* seq = (int*)malloc(sizeof(int) * (size_t)(V.nvis > 0 ? V.nvis : 1));
-  double* sw = (double*)malloc(sizeof(double) * (size_t)(V.nvis > 0 ? V.nvis : 1));
-  double* sG = (double*)malloc(sizeof(double) * (size_t)(V.nvis > 0 ? V.nvis : 1));
-  double* sT = (double*)malloc(sizeof(double) * (size_t)(V.nvis > 0 ? V.nvis : 1));
-  double* Sb = (double*)malloc(sizeof(double) * (size_t)N * C * 2);
+  const size_t gstride_j = (size_t)H * W * C * 2;
   for (int i = 0; i < H; ++i)
     for (int jj = 0; jj < W; ++jj) {
-      float T32 = 1.0f;
-      double T64 = 1.0;
-      int n_c = 0;
-      for (int n = 0; n < V.nvis; ++n) {
-        int k = V.order[n];
-        const or_p32* P = V.P32 + k;
-        if (!or_in_footprint(g, P, i, jj)) continue;
-        float w32;
-        int m;
-        if (!or_weight32(g, P, tau[k], i, jj, &w32, &m)) continue;
-        double G;
-        double w64 = or_weight64(g, V.P64 + k, (double)tau[k], i, jj, m, &G);
-        seq[n_c] = k; sw[n_c] = w64; sG[n_c] = G; sT[n_c] = T64;
-        T32 = T32 * (1.0f - w32);
-        T64 = T64 * (1.0 - w64);
-        n_c++;
-        if (use_eps && T32 < g->eps_T) break;
-      }
       size_t pix = (size_t)i * W + jj;
-      memset(Sb, 0, sizeof(double) * (size_t)N * C * 2);
-      for (int e = n_c - 1; e >= 0; --e) {
-        int k = seq[e];
-        double dLdw = 0.0, adw = 0.0;
-        for (int j = 0; j < N; ++j)
-          for (int ch = 0; ch < C; ++ch) {
-            const double* gv = gspec + ((((size_t)j * H * W + pix) * C + ch) * 2);
-            const double* sv = rad + ((((size_t)j * K + k) * C + ch) * 2);
-            double* gr = grad_rad + ((((size_t)j * K + k) * C + ch) * 2);
-            double* Sv = Sb + (j * C + ch) * 2;
-            gr[0] += sT[e] * sw[e] * gv[0];
-            gr[1] += sT[e] * sw[e] * gv[1];
-            if (abs_rad) {
-              double* ar = abs_rad + ((((size_t)j * K + k) * C + ch) * 2);
-              ar[0] += sT[e] * sw[e] * fabs(gv[0]);
-              ar[1] += sT[e] * sw[e] * fabs(gv[1]);
-            }
-            dLdw += sT[e] * (gv[0] * (sv[0] - Sv[0]) + gv[1] * (sv[1] - Sv[1]));
-            adw += sT[e] * (fabs(gv[0]) * (fabs(sv[0]) + fabs(Sv[0])) +
-                            fabs(gv[1]) * (fabs(sv[1]) + fabs(Sv[1])));
-            Sv[0] = sw[e] * sv[0] + (1.0 - sw[e]) * Sv[0];
-            Sv[1] = sw[e] * sv[1] + (1.0 - sw[e]) * Sv[1];
-          }
-        grad_tau[k] += dLdw * sG[e];
-        if (abs_tau) abs_tau[k] += adw * sG[e];
-      }
+      or_backward_pixel(g, &V, tau, i, jj, N, C, rad, gspec + pix * C * 2, gstride_j, grad_rad,
+                        grad_tau, abs_rad, abs_tau, use_eps, &sc);
     }
-  free(seq); free(sw); free(sG); free(sT); free(Sb);
+  or_scratch_free(&sc);
+  or_view_free(&V);
+  return 0;
+}
+
+/* The backward restricted to a pixel list pix[np] (= i*W + jj), with the
+ * cotangent of those pixels gpix[np][N][C][2]; the early stop is on.       */
+int or_backward_pixels(const or_grid* g, int K, const float* p, const float* s, const float* q,
+                       const float* tau, const float* c, int N, int C, const double* rad,
+                       int np, const int* pix, const double* gpix, double* grad_rad,
+                       double* grad_tau) {
+  or_view V;
+  if (or_view_init(&V, g, K, p, s, q, tau, c)) return -2;
+  or_bwd_scratch sc;
+  if (or_scratch_init(&sc, V.nvis, N, C)) return -2;
+  for (int e = 0; e < np; ++e)
+    or_backward_pixel(g, &V, tau, pix[e] / g->W, pix[e] % g->W, N, C, rad,
+                      gpix + (size_t)e * N * C * 2, (size_t)C * 2, grad_rad, grad_tau, NULL, NULL,
+                      1, &sc);
+  or_scratch_free(&sc);
   or_view_free(&V);
   return 0;
 }

@@ -9,12 +9,20 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/rxgs.h"
 #include "rxgs_internal.h"
+
+namespace rxgs {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace rxgs
 
 using namespace rxgs;
 
@@ -57,6 +65,16 @@ struct rxgs_ctx {
   std::map<uint64_t, ViewsState*> views;
   unsigned* d_err = nullptr;      // device error word
   uint32_t* h_pinned = nullptr;   // pinned readback slot
+  // stage profiler: CUDA events recorded on the call's stream around each
+  // stage while enabled, folded into per-stage totals by rxgs_profile_read
+  bool prof = false;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, std::pair<double, long>> stage_ms;
 };
 
 namespace {
@@ -136,6 +154,38 @@ bool make_grid(const rxgs_options& o, GridConst* g, std::string* why) {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+cudaEvent_t take_event(rxgs_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Times one stage of a call on `stream` when the profiler is on.
+struct Stage {
+  rxgs_ctx* c;
+  cudaStream_t s;
+  std::string name;
+  cudaEvent_t a = nullptr;
+  Stage(rxgs_ctx* ctx, const char* n, cudaStream_t st) : c(ctx), s(st), name(n) {
+    if (c->prof) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Stage() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back({name, a, b});
+    }
+  }
+};
+
 int pick_cols(const rxgs_ctx* ctx, int ncols) {
   if (ctx->opts.cols_per_cta) return ctx->opts.cols_per_cta;
   if (ncols <= 16) return 16;
@@ -169,6 +219,7 @@ void launch_uniform_cotangent(const float* gcsi, const float* grssi, const float
                               int N, int C, float* out, cudaStream_t s) {
   const int n = M * N * C;
   uniform_cot_kernel<<<(n + 255) / 256, 256, 0, s>>>(gcsi, grssi, fcsi, M, N, C, out);
+  note_launches(1);
 }
 
 // ====================================================================== ABI
@@ -242,6 +293,11 @@ rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
   }
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_pinned);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   delete ctx;
   return RXGS_OK;
 }
@@ -394,8 +450,14 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     cleanup();
     return fail(ctx, RXGS_E_OOM, "prepare: %s", cudaGetErrorString(e));
   }
-  launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st);
-  launch_exclusive_scan(v->counts, v->offsets, MK, scan_tmp, st);
+  {
+    Stage sg(ctx, "preprocess", st);
+    launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st);
+  }
+  {
+    Stage sg(ctx, "scan", st);
+    launch_exclusive_scan(v->counts, v->offsets, MK, scan_tmp, st);
+  }
   e = cudaMemcpyAsync(ctx->h_pinned, v->offsets + MK, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(scan_tmp, st);
@@ -422,10 +484,16 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     cleanup();
     return fail(ctx, RXGS_E_OOM, "prepare (sort buffers): %s", cudaGetErrorString(e));
   }
-  launch_emit(g, v->rec, v->depth, v->offsets, s->K, M, v->tile_bits, v->keys, v->vals, st);
+  {
+    Stage sg(ctx, "emit", st);
+    launch_emit(g, v->rec, v->depth, v->offsets, s->K, M, v->tile_bits, v->keys, v->vals, st);
+  }
   bool in_alt = false;
-  radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, 31 + v->tile_bits + v->view_bits,
-                   sort_tmp, &in_alt, st);
+  {
+    Stage sg(ctx, "sort", st);
+    radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, 31 + v->tile_bits + v->view_bits,
+                     sort_tmp, &in_alt, st);
+  }
   if (in_alt) {
     std::swap(v->keys, keys_alt);
     std::swap(v->vals, vals_alt);
@@ -433,7 +501,10 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   dfree(keys_alt, st);
   dfree(vals_alt, st);
   dfree(sort_tmp, st);
-  launch_tile_ranges(v->keys, I, v->tile_bits, g.T, v->ranges, M, st);
+  {
+    Stage sg(ctx, "ranges", st);
+    launch_tile_ranges(v->keys, I, v->tile_bits, g.T, v->ranges, M, st);
+  }
   rxgs_status rs = check_last(ctx, "prepare kernels");
   if (rs != RXGS_OK) {
     cleanup();
@@ -469,6 +540,7 @@ namespace {
 rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const float* rx, int N,
                           const rxgs_render_desc* d, int stride, float* rad, float* glob,
                           cudaStream_t st) {
+  Stage sg(ctx, d->radiance ? "radiance_transpose" : "mlp", st);
   if (d->radiance) {
     launch_radiance_transpose(d->radiance, N, s->K, s->C, stride, rad, st);
   } else {
@@ -534,10 +606,15 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     a.partial = partial;
     a.ncontrib = out->ncontrib;
     a.tfinal = out->tfinal;
-    launch_render_fwd(a, pick_cols(ctx, ncols), st);
-    if (reduce)
+    {
+      Stage sg(ctx, "render_fwd", st);
+      launch_render_fwd(a, pick_cols(ctx, ncols), st);
+    }
+    if (reduce) {
+      Stage sg(ctx, "reduce", st);
       launch_reduce_tiles(partial, v->M, g.T, N, s->C, (kind & RXGS_OUT_CSI) ? out->csi : nullptr,
                           (kind & RXGS_OUT_RSSI) ? out->rssi : nullptr, st);
+    }
     rs = check_last(ctx, "render");
   }
   dfree(rad, st);
@@ -659,8 +736,12 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.d_rad = d_rad;
   A.d_tau = d_tau;
   A.n_inst = v->n_inst;
-  launch_render_bwd(A, 32, st);
+  {
+    Stage sg(ctx, "render_bwd", st);
+    launch_render_bwd(A, 32, st);
+  }
   if (d->radiance) {
+    Stage sg(ctx, "radiance_grad", st);
     if (gr->grad_radiance) launch_radiance_untranspose_add(d_rad, N, K, C, stride, gr->grad_radiance, st);
   } else {
     MlpParams m{s->mlp, s->hidden, C, 0};
@@ -674,12 +755,51 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
       cleanup();
       return fail(ctx, RXGS_E_OOM, "backward (MLP): %s", cudaGetErrorString(e));
     }
+    Stage sg(ctx, "mlp_bwd", st);
     launch_mlp_backward(m, rx, N, s->geom, s->base, K, stride, d_rad, glob, g_base, g_mlp,
                         mlp_tmp, st);
   }
   rs = check_last(ctx, "backward");
   cleanup();
   return rs;
+}
+
+rxgs_status rxgs_profile(rxgs_ctx* ctx, int enable) {
+  if (!ctx) return RXGS_E_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->prof = enable != 0;
+  return RXGS_OK;
+}
+
+rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset) {
+  if (!ctx || !json || cap == 0) return fail(ctx, RXGS_E_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  for (auto& p : ctx->pending) {
+    CK(cudaEventSynchronize(p.b));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    auto& e = ctx->stage_ms[p.name];
+    e.first += ms;
+    e.second += 1;
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  std::string out = "{\"kernel_launches\": " + std::to_string(launch_count()) + ", \"stages\": {";
+  bool first = true;
+  for (auto& kv : ctx->stage_ms) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s\"%s\": {\"ms\": %.6f, \"calls\": %ld}", first ? "" : ", ",
+             kv.first.c_str(), kv.second.first, kv.second.second);
+    out += buf;
+    first = false;
+  }
+  out += "}}";
+  if (reset) ctx->stage_ms.clear();
+  if (out.size() + 1 > cap) return fail(ctx, RXGS_E_INVALID, "buffer too small (%zu)", out.size() + 1);
+  std::memcpy(json, out.c_str(), out.size() + 1);
+  return RXGS_OK;
 }
 
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream) {

@@ -60,6 +60,7 @@ void launch_scene_upload(const float* means, const float* log_scales, const floa
                          const float* opacity, int K, float4* geom, cudaStream_t s) {
   if (K <= 0) return;
   scene_upload_kernel<<<(K + 255) / 256, 256, 0, s>>>(means, log_scales, quats, opacity, K, geom);
+  note_launches(1);
 }
 
 __global__ void set_opacity_kernel(const float* __restrict__ opacity, int K, float4* geom) {
@@ -70,6 +71,7 @@ __global__ void set_opacity_kernel(const float* __restrict__ opacity, int K, flo
 void launch_set_opacity(const float* opacity, int K, float4* geom, cudaStream_t s) {
   if (K <= 0) return;
   set_opacity_kernel<<<(K + 255) / 256, 256, 0, s>>>(opacity, K, geom);
+  note_launches(1);
 }
 
 // -------------------------------------------------------------- projection
@@ -213,6 +215,7 @@ void launch_preprocess(const GridConst& g, const float4* geom, int K, const floa
   if (K <= 0 || M <= 0) return;
   dim3 grid((K + 255) / 256, M);
   preprocess_kernel<<<grid, 256, 0, s>>>(g, geom, K, tx, rec, depth, count);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------- emission
@@ -254,6 +257,7 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
   if (K <= 0 || M <= 0) return;
   dim3 grid((K + 255) / 256, M);
   emit_kernel<<<grid, 256, 0, s>>>(g, rec, depth, offsets, K, tile_bits, keys, vals);
+  note_launches(1);
 }
 
 // -------------------------------------------------------------- tile ranges
@@ -277,6 +281,7 @@ void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, ui
   if (n == 0) return;
   tile_ranges_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(keys, n, tile_bits,
                                                                             T, ranges);
+  note_launches(1);
 }
 
 // -------------------------------------------------------------------- scan
@@ -371,8 +376,11 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t
   }
   const int nb = static_cast<int>((n + kScanTile - 1) / kScanTile);
   scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, n, tmp);
+  note_launches(1);
   scan_sums_kernel<<<1, kScanThreads, 0, s>>>(tmp, nb);
+  note_launches(1);
   scan_apply_kernel<<<nb, kScanThreads, 0, s>>>(in, n, tmp, out);
+  note_launches(1);
 }
 
 // ---------------------------------------------------------------- radiance
@@ -399,6 +407,7 @@ void launch_radiance_transpose(const float* rad, int N, int K, int C, int stride
   if (total == 0) return;
   radiance_transpose_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
       rad, N, K, C, stride, out);
+  note_launches(1);
 }
 
 __global__ void radiance_untranspose_add_kernel(const float* __restrict__ in, int N, int K,
@@ -420,6 +429,7 @@ void launch_radiance_untranspose_add(const float* in, int N, int K, int C, int s
   if (total == 0) return;
   radiance_untranspose_add_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
       in, N, K, C, stride, out);
+  note_launches(1);
 }
 
 }  // namespace rxgs

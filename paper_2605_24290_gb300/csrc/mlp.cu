@@ -135,6 +135,7 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
   // pad columns of every row stay zero
   cudaMemsetAsync(out, 0, sizeof(float) * static_cast<size_t>(K) * stride, s);
   mlp_global_kernel<<<N, 128, 0, s>>>(m.p, m.C, m.bf16, rx, glob);
+  note_launches(1);
   const size_t pairs = static_cast<size_t>(N) * K;
   const size_t smem = sizeof(float) * (kHidden * 7 + 4 * m.C * kHidden + 4 * m.C);
   if (smem > 48 * 1024)
@@ -142,6 +143,7 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
                          static_cast<int>(smem));
   mlp_local_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, smem, s>>>(
       m.p, m.C, m.bf16, rx, N, geom, base, K, stride, glob, out);
+  note_launches(1);
 }
 
 
@@ -420,11 +422,14 @@ void launch_mlp_backward(const MlpParams& m, const float* rx, int N, const float
   float* dog = tmp + static_cast<size_t>(blocks) * (nloc + static_cast<size_t>(N) * n4);
   mlp_local_bwd_kernel<<<blocks, kBwdPairs, smem, s>>>(m.p, C, rx, N, geom, base, K, stride, dS,
                                                        glob, grad_base, part);
+  note_launches(1);
   const int tot = nloc + N * n4;
   const MlpOffsets o = mlp_offsets(kHidden, C);
   mlp_partial_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(part, blocks, nloc, N * n4, o.l_w1,
                                                               grad_mlp, dog);
+  note_launches(1);
   mlp_global_bwd_kernel<<<1, 256, 0, s>>>(m.p, C, rx, N, dog, grad_mlp);
+  note_launches(1);
 }
 
 }  // namespace rxgs

@@ -160,8 +160,11 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32
   for (int shift = 0; shift < bits; shift += 8) {
     cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kDigits, s);
     radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(kin, n, shift, hist, totals, nb);
+    note_launches(1);
     radix_offsets_kernel<<<kDigits, kSortThreads, 0, s>>>(hist, totals, nb);
+    note_launches(1);
     radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(kin, vin, n, shift, hist, nb, kout, vout);
+    note_launches(1);
     uint64_t* tk = kin;
     kin = kout;
     kout = tk;

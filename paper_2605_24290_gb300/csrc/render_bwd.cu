@@ -237,6 +237,7 @@ void launch_render_bwd(const BackwardArgs& A, int /*cols_per_cta*/, cudaStream_t
   }
   dim3 grid(a.g.T, (a.ncols + kBNB - 1) / kBNB, a.M);
   render_bwd_kernel<<<grid, kTilePixels, smem, s>>>(A);
+  note_launches(1);
 }
 
 }  // namespace rxgs

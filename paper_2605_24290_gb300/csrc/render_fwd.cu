@@ -196,6 +196,7 @@ static void launch_fwd_nb(const RenderArgs& a, cudaStream_t s) {
   }
   dim3 grid(a.g.T, (a.ncols + NB - 1) / NB, a.M);
   render_fwd_kernel<NB><<<grid, kTilePixels, S::smem, s>>>(a);
+  note_launches(1);
 }
 
 void launch_render_fwd(const RenderArgs& a, int cols_per_cta, cudaStream_t s) {
@@ -234,6 +235,7 @@ void launch_reduce_tiles(const float* partial, int M, int T, int N, int C, float
   const int n = M * N * C;
   if (n <= 0) return;
   reduce_tiles_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, M, T, 2 * N * C, C, csi, rssi);
+  note_launches(1);
 }
 
 }  // namespace rxgs

@@ -18,6 +18,11 @@ struct GridConst {
   float eps_T, q_max, ksig, r_near;  // ksig = sqrt(q_max)
 };
 
+// Number of kernel launches issued by the library (all threads, all
+// contexts); each launch_* function adds the kernels it launched.
+void note_launches(unsigned n);
+unsigned long long launch_count();
+
 // Device error word bits (written by kernels, read by the host at syncs).
 enum : unsigned {
   kErrCapacity = 1u,   // an instance list was larger than its buffer

@@ -80,6 +80,8 @@ SIGNATURES = {
     "rxgs_render_backward": (I, [P, U64, P, I, P, P, P, P]),
     "rxgs_views_info": (I, [P, U64, P]),
     "rxgs_views_export": (I, [P, U64, P, P, P, P, P, P]),
+    "rxgs_profile": (I, [P, I]),
+    "rxgs_profile_read": (I, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
     "rxgs_sync": (I, [P, P]),
 }
 
@@ -242,6 +244,16 @@ class Context:
                                                _ptr(keys), _ptr(vals), _ptr(ranges),
                                                _stream(stream)))
         return rec, counts, keys[:n], vals[:n], ranges
+
+    def profile(self, enable=True):
+        self._check(self.lib.rxgs_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        """Per-stage CUDA-event totals and the library's kernel launch count."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.lib.rxgs_profile_read(self.h, buf, len(buf), 1 if reset else 0))
+        return json.loads(buf.value.decode())
 
     @staticmethod
     def mlp_numel(C, hidden=64):

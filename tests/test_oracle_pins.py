@@ -499,3 +499,23 @@ def test_render_backward_with_stop_matches_fd_of_fixed_sequence(oracle):
         rp[idx] += 1.0
         d = ((oracle.render_view(g, sc, tx, rp)["spectra"] - base) * gs).sum()
         assert d == pytest.approx(gr[idx], rel=1e-9, abs=1e-9)
+
+
+def test_backward_on_pixel_subsets_adds_up(oracle):
+    """The pixel-list backward over a partition of the grid sums to the
+    full-view backward (same per-pixel arithmetic, any pixel order)."""
+    sc, tx = tiny_scene(40, K=40)
+    g = tiny_grid(eps_T=0.02)
+    rng = np.random.default_rng(41)
+    rad = rng.normal(size=(2, sc.K, 1, 2))
+    gs = rng.normal(size=(2, g.H, g.W, 1, 2))
+    gr, gt = oracle.backward_view(g, sc, tx, rad, gs)
+    perm = rng.permutation(g.H * g.W).astype(np.int32)
+    acc_r, acc_t = np.zeros_like(gr), np.zeros_like(gt)
+    for part in np.array_split(perm, 3):
+        gp = gs.reshape(2, -1, 1, 2)[:, part].transpose(1, 0, 2, 3)
+        r, t = oracle.backward_pixels(g, sc, tx, rad, part, gp)
+        acc_r += r
+        acc_t += t
+    np.testing.assert_allclose(acc_r, gr, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(acc_t, gt, rtol=1e-10, atol=1e-12)
