@@ -181,8 +181,11 @@ rxgs_status rxgs_render(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int 
  *   fwd_csi      the forward CSI [M,N,1,2] when grad_rssi is given
  * Nothing else of the forward is needed: each tile re-walks its list with
  * the forward's decisions, then sweeps it back to front.  `views`, `rx` and
- * `desc->radiance` must be those of the forward.  Gradients are accumulated
- * with float atomics (their rounding order is not fixed).
+ * `desc->radiance` must be those of the forward.  The radiance the last
+ * rxgs_render_views computed on `views` is reused when rx, N, radiance and
+ * the scene (rxgs_update_scene) are unchanged; otherwise it is recomputed.
+ * Gradients are accumulated with float atomics (their rounding order is not
+ * fixed).
  * Outputs (accumulated: caller zero-fills):
  *   grad_radiance [N,K,C,2]  when desc->radiance != NULL
  *   grad_opacity  [K]

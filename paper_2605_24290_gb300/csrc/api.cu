@@ -30,6 +30,7 @@ namespace {
 
 struct SceneState {
   int K = 0, C = 0;
+  uint64_t generation = 0;  // bumped by rxgs_update_scene
   float4* geom = nullptr;   // [K][3]
   float* base = nullptr;    // [K][C][2]
   float* mlp = nullptr;     // flat
@@ -50,6 +51,15 @@ struct ViewsState {
   uint2* ranges = nullptr;    // [M][T]
   uint32_t n_inst = 0;
   int tile_bits = 0, view_bits = 0;
+  // radiance of the last rxgs_render_views on these views, kept for the
+  // backward: valid for the same rx pointer, N, radiance pointer and scene
+  // generation
+  float* rad = nullptr;
+  float* glob = nullptr;
+  const float* key_rx = nullptr;
+  const float* key_radiance = nullptr;
+  int key_N = 0, key_stride = 0;
+  uint64_t key_gen = ~0ull;
 };
 
 }  // namespace
@@ -284,6 +294,7 @@ rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
     ViewsState* v = kv.second;
     cudaFree(v->tx); cudaFree(v->rec); cudaFree(v->depth); cudaFree(v->counts);
     cudaFree(v->offsets); cudaFree(v->keys); cudaFree(v->vals); cudaFree(v->ranges);
+    cudaFree(v->rad); cudaFree(v->glob);
     delete v;
   }
   for (auto& kv : ctx->scenes) {
@@ -395,6 +406,7 @@ rxgs_status rxgs_update_scene(rxgs_ctx* ctx, rxgs_scene_t scene, const float* op
   SceneState* s = it->second;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(ctx->device));
+  s->generation++;
   if (opacity) launch_set_opacity(opacity, s->K, s->geom, st);
   if (base_radiance) {
     if (!s->base) return fail(ctx, RXGS_E_INVALID, "scene has no base radiance");
@@ -526,6 +538,7 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream) 
   ViewsState* v = it->second;
   dfree(v->tx, st); dfree(v->rec, st); dfree(v->depth, st); dfree(v->counts, st);
   dfree(v->offsets, st); dfree(v->keys, st); dfree(v->vals, st); dfree(v->ranges, st);
+  dfree(v->rad, st); dfree(v->glob, st);
   delete v;
   ctx->views.erase(it);
   return RXGS_OK;
@@ -568,7 +581,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->views.find(views);
   if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
-  const ViewsState* v = it->second;
+  ViewsState* v = it->second;
   const SceneState* s = ctx->scenes.at(v->scene);
   if ((kind & RXGS_OUT_RSSI) && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
   CK(cudaSetDevice(ctx->device));
@@ -590,12 +603,24 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   }
   rxgs_status rs = make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
   if (rs == RXGS_OK) {
+    // keep this radiance for a backward on the same views
+    dfree(v->rad, st);
+    dfree(v->glob, st);
+    v->rad = rad;
+    v->glob = glob;
+    v->key_rx = rx;
+    v->key_radiance = d->radiance;
+    v->key_N = N;
+    v->key_stride = stride;
+    v->key_gen = s->generation;
+    rad = nullptr;
+    glob = nullptr;
     RenderArgs a{};
     a.g = g;
     a.rec = v->rec;
     a.vals = v->vals;
     a.ranges = v->ranges;
-    a.rad = rad;
+    a.rad = v->rad;
     a.K = s->K;
     a.M = v->M;
     a.N = N;
@@ -693,17 +718,35 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   const int ncols = 2 * N * C;
   const int stride = round_up(ncols, 128);
   float *rad = nullptr, *glob = nullptr, *d_rad = nullptr, *g_uni = nullptr, *d_tau = nullptr;
-  float *g_base = nullptr, *g_mlp = nullptr, *mlp_tmp = nullptr;
+  float *g_base = nullptr, *g_mlp = nullptr, *mlp_tmp = nullptr, *tfin = nullptr;
+  uint32_t *stops = nullptr, *tstop = nullptr;
+  const bool cached = v->rad && v->key_rx == rx && v->key_radiance == d->radiance &&
+                      v->key_N == N && v->key_stride == stride && v->key_gen == s->generation;
   auto cleanup = [&]() {
+    if (cached) {
+      rad = nullptr;
+      glob = nullptr;
+    }
     dfree(rad, st); dfree(glob, st); dfree(d_rad, st); dfree(g_uni, st); dfree(mlp_tmp, st);
+    dfree(tfin, st); dfree(stops, st); dfree(tstop, st);
     if (!gr->grad_opacity) dfree(d_tau, st);
     if (!gr->grad_base) dfree(g_base, st);
     if (!gr->grad_mlp) dfree(g_mlp, st);
   };
-  cudaError_t e = dalloc(&rad, static_cast<size_t>(K) * stride, st);
+  cudaError_t e = cudaSuccess;
+  if (cached) {
+    rad = v->rad;
+    glob = v->glob;
+  } else {
+    e = dalloc(&rad, static_cast<size_t>(K) * stride, st);
+    if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * C, st);
+  }
   if (e == cudaSuccess) e = dalloc(&d_rad, static_cast<size_t>(K) * stride, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_rad, 0, sizeof(float) * K * static_cast<size_t>(stride), st);
-  if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * C, st);
+  const size_t MHW = static_cast<size_t>(M) * g.H * g.W;
+  if (e == cudaSuccess) e = dalloc(&tfin, MHW, st);
+  if (e == cudaSuccess) e = dalloc(&stops, MHW, st);
+  if (e == cudaSuccess) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
   if (e == cudaSuccess && (cot->grad_csi || cot->grad_rssi))
     e = dalloc(&g_uni, static_cast<size_t>(M) * ncols, st);
   d_tau = gr->grad_opacity;
@@ -712,7 +755,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     cleanup();
     return fail(ctx, RXGS_E_OOM, "backward: %s", cudaGetErrorString(e));
   }
-  rxgs_status rs = make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
+  rxgs_status rs = cached ? RXGS_OK : make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
   if (rs != RXGS_OK) {
     cleanup();
     return rs;
@@ -735,6 +778,9 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.g_uniform = g_uni;
   A.d_rad = d_rad;
   A.d_tau = d_tau;
+  A.tfin = tfin;
+  A.stops = stops;
+  A.tile_stop = tstop;
   A.n_inst = v->n_inst;
   {
     Stage sg(ctx, "render_bwd", st);

@@ -156,14 +156,15 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
 //   dL/da_l = g conj(u), dL/db_l = g, dL/du = g conj(1 + a_l)
 //   dL/da_g = sum_k dL/du conj(phi), dL/db_g = sum_k dL/du,
 //   dL/dphi = sum_j dL/du conj(1 + a_g)
-// The local-branch weight gradients are sums over all (j, k) pairs: each
-// persistent block accumulates its pairs in registers (one parameter per
-// thread), writes one partial, and a second kernel adds the partials in a
-// fixed order.
-constexpr int kBwdPairs = 256;  // pairs per tile (one per thread)
-constexpr int kMaxBwdC = 4;     // MLP backward supports C <= 4
+// One thread per (j, k) pair, grid-stride with a stride that is a multiple
+// of N so each thread keeps one receiver j.  The local-branch weight
+// gradients are sums of per-pair outer products (dol x h, dh x x): every warp
+// reduce-scatters each 32-wide slice over its lanes with shuffles (lane l
+// ends up owning hidden unit l of the slice) and keeps the result in
+// registers; at the end warps and blocks are combined in a fixed order.
+constexpr int kBwdThreads = 256;
 
-static int mlp_bwd_blocks() {
+static int mlp_bwd_blocks(int N) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -171,184 +172,232 @@ static int mlp_bwd_blocks() {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
       sms = 152;
   }
-  return sms;  // one resident block per SM (the tile buffers take ~150 KB)
+  int gcd = kBwdThreads, b = N;
+  while (b) {
+    const int t = gcd % b;
+    gcd = b;
+    b = t;
+  }
+  const int m = N / gcd;  // blocks * 256 must be a multiple of N
+  int blocks = 2 * sms;
+  blocks = blocks < m ? m : (blocks / m) * m;
+  return blocks;
 }
 
 size_t mlp_backward_tmp_floats(const MlpParams& m, int N, int /*K*/) {
   const int nloc = kHidden * 6 + kHidden + 4 * m.C * kHidden + 4 * m.C;
-  const int blocks = mlp_bwd_blocks();
+  const int blocks = mlp_bwd_blocks(N);
   return static_cast<size_t>(blocks) * (nloc + static_cast<size_t>(N) * 4 * m.C) +
          static_cast<size_t>(N) * 4 * m.C;
 }
 
-__global__ void __launch_bounds__(kBwdPairs) mlp_local_bwd_kernel(
-    const float* __restrict__ P, int C, const float* __restrict__ rx, int N,
+// Reduce-scatter of a 32-value per-lane vector over the warp: returns the
+// warp sum of entry `lane`.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int e = 0; e < off; ++e) {
+      const float send = hi ? v[e] : v[e + off];
+      const float keep = hi ? v[e + off] : v[e];
+      v[e] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+template <int CC>
+__global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
+    const float* __restrict__ P, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
     const float* __restrict__ dS, const float* __restrict__ glob, float* __restrict__ grad_base,
     float* __restrict__ part) {
-  extern __shared__ float sm[];
-  const MlpOffsets o = mlp_offsets(kHidden, C);
-  const int n4 = 4 * C;
-  float* W1 = sm;                          // [64][6]
-  float* B1 = W1 + kHidden * 6;            // [64]
-  float* W2 = B1 + kHidden;                // [4C][64]
-  float* sX = W2 + n4 * kHidden;           // [256][6]
-  float* sH = sX + kBwdPairs * 6;          // [256][65]  post-ReLU hidden (padded)
-  float* sDol = sH + kBwdPairs * 65;       // [256][4C]
-  float* sDh = sDol + kBwdPairs * n4;      // [256][65]
-  float* sDB = sDh + kBwdPairs * 65;       // [256][2C]  dL/dphi contributions
-  float* sOG = sDB + kBwdPairs * 2 * C;    // [256][4C]  dL/d(a_g, b_g) contributions
-  float* accOG = sOG + kBwdPairs * n4;     // [N][4C]    block accumulator
-  const int t = threadIdx.x;
-  for (int e = t; e < kHidden * 6; e += kBwdPairs) W1[e] = P[o.l_w1 + e];
-  for (int e = t; e < kHidden; e += kBwdPairs) B1[e] = P[o.l_b1 + e];
-  for (int e = t; e < n4 * kHidden; e += kBwdPairs) W2[e] = P[o.l_w2 + e];
-  for (int e = t; e < N * n4; e += kBwdPairs) accOG[e] = 0.0f;
-  // owned parameter accumulators
-  float aW2 = 0.0f, aW1a = 0.0f, aW1b = 0.0f, aB1 = 0.0f, aB2 = 0.0f;
-  const size_t pairs = static_cast<size_t>(N) * K;
-  const size_t ntiles = (pairs + kBwdPairs - 1) / kBwdPairs;
+  constexpr int n4 = 4 * CC;
+  constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
+  constexpr int kWarps = kBwdThreads / 32;
+  __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
+  extern __shared__ float sdyn[];  // [kWarps][nloc] warp partials, then [256][4C]
+  const MlpOffsets o = mlp_offsets(kHidden, CC);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int e = t; e < kHidden * 6; e += kBwdThreads) W1[e] = P[o.l_w1 + e];
+  for (int e = t; e < kHidden; e += kBwdThreads) B1[e] = P[o.l_b1 + e];
+  for (int e = t; e < n4 * kHidden; e += kBwdThreads) W2[e] = P[o.l_w2 + e];
+  for (int e = t; e < n4; e += kBwdThreads) B2[e] = P[o.l_b2 + e];
   __syncthreads();
-  for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const size_t p0 = tile * kBwdPairs;
-    const size_t pair = p0 + t;
+
+  float aw2[n4][2], aw1[4][2], ab1[2], ab2[n4], aog[n4];
+#pragma unroll
+  for (int q = 0; q < n4; ++q) aw2[q][0] = aw2[q][1] = ab2[q] = aog[q] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) aw1[i][0] = aw1[i][1] = 0.0f;
+  ab1[0] = ab1[1] = 0.0f;
+
+  const size_t pairs = static_cast<size_t>(N) * K;
+  const size_t gstride = static_cast<size_t>(gridDim.x) * kBwdThreads;
+  const size_t first = static_cast<size_t>(blockIdx.x) * kBwdThreads + t;
+  const int j = static_cast<int>(first % N);  // fixed: gstride is a multiple of N
+  const float rxj = rx[3 * j + 0], ryj = rx[3 * j + 1], rzj = rx[3 * j + 2];
+  float gj[n4];
+#pragma unroll
+  for (int q = 0; q < n4; ++q) gj[q] = glob[static_cast<size_t>(j) * n4 + q];
+
+  const size_t rounds = (pairs + gstride - 1) / gstride;
+  for (size_t r = 0; r < rounds; ++r) {
+    const size_t pair = first + r * gstride;
     const bool ok = pair < pairs;
-    // ---- phase 1: forward recompute and the complex-affine backward
-    {
-      float x[6] = {0, 0, 0, 0, 0, 0};
-      float dol[4 * kMaxBwdC], db[2 * kMaxBwdC], dog[4 * kMaxBwdC];
+    const int k = ok ? static_cast<int>(pair / N) : 0;
+    float x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float h[kHidden], dol[n4], db[2 * CC];
 #pragma unroll
-      for (int q = 0; q < 4 * kMaxBwdC; ++q) dol[q] = dog[q] = 0.0f;
+    for (int q = 0; q < n4; ++q) dol[q] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 2 * kMaxBwdC; ++q) db[q] = 0.0f;
-      if (ok) {
-        const int j = static_cast<int>(pair % N), k = static_cast<int>(pair / N);
-        const float4 p = geom[3 * k];
-        const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
-        const float d = sqrtf(vx * vx + vy * vy + vz * vz);
-        const float inv = 1.0f / d;
-        x[0] = vx * inv; x[1] = vy * inv; x[2] = vz * inv; x[3] = d; x[4] = 1.0f; x[5] = 0.0f;
-        float h[kHidden];
-#pragma unroll
-        for (int u = 0; u < kHidden; ++u) {
-          float a = B1[u];
-#pragma unroll
-          for (int i = 0; i < 6; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
-          h[u] = fmaxf(a, 0.0f);
-          sH[t * 65 + u] = h[u];
-        }
-        const float* gj = glob + static_cast<size_t>(j) * n4;
-        const float* gs = dS + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * C;
-        for (int c = 0; c < C; ++c) {
-          float ol[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float* w = W2 + (4 * c + q) * kHidden;
-            float a = P[o.l_b2 + 4 * c + q];
-#pragma unroll
-            for (int u = 0; u < kHidden; ++u) a = fmaf(w[u], h[u], a);
-            ol[q] = a;
-          }
-          const float pr = base[(static_cast<size_t>(k) * C + c) * 2 + 0];
-          const float pi = base[(static_cast<size_t>(k) * C + c) * 2 + 1];
-          const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
-          const float ur = agr * pr - agi * pi + gj[4 * c + 2];
-          const float ui = agr * pi + agi * pr + gj[4 * c + 3];
-          const float alr = 1.0f + ol[0], ali = ol[1];
-          const float gr = gs[2 * c], gi = gs[2 * c + 1];
-          // dL/da_l = g conj(u); dL/db_l = g
-          dol[4 * c + 0] = gr * ur + gi * ui;
-          dol[4 * c + 1] = gi * ur - gr * ui;
-          dol[4 * c + 2] = gr;
-          dol[4 * c + 3] = gi;
-          // dL/du = g conj(1 + a_l)
-          const float dur = gr * alr + gi * ali, dui = gi * alr - gr * ali;
-          // dL/da_g = du conj(phi); dL/db_g = du; dL/dphi = du conj(1 + a_g)
-          dog[4 * c + 0] = dur * pr + dui * pi;
-          dog[4 * c + 1] = dui * pr - dur * pi;
-          dog[4 * c + 2] = dur;
-          dog[4 * c + 3] = dui;
-          db[2 * c + 0] = dur * agr + dui * agi;
-          db[2 * c + 1] = dui * agr - dur * agi;
-        }
-      } else {
-        for (int u = 0; u < kHidden; ++u) sH[t * 65 + u] = 0.0f;
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i) sX[t * 6 + i] = x[i];
-      for (int q = 0; q < n4; ++q) {
-        sDol[t * n4 + q] = dol[q];
-        sOG[t * n4 + q] = dog[q];
-      }
-      for (int q = 0; q < 2 * C; ++q) sDB[t * 2 * C + q] = db[q];
+    for (int q = 0; q < 2 * CC; ++q) db[q] = 0.0f;
+    if (ok) {
+      const float4 p = geom[3 * k];
+      const float vx = rxj - p.x, vy = ryj - p.y, vz = rzj - p.z;
+      const float d = sqrtf(vx * vx + vy * vy + vz * vz);
+      const float inv = 1.0f / d;
+      x[0] = vx * inv;
+      x[1] = vy * inv;
+      x[2] = vz * inv;
+      x[3] = d;
     }
-    __syncthreads();
-    // ---- phase 2: dL/dh = W2^T dol masked by ReLU
+#pragma unroll
+    for (int u = 0; u < kHidden; ++u) {
+      float a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
+      h[u] = ok ? fmaxf(a, 0.0f) : 0.0f;
+    }
+    if (ok) {
+      const float* gs = dS + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * CC;
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        float ol[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float a = B2[4 * c + q];
+#pragma unroll
+          for (int u = 0; u < kHidden; ++u) a = fmaf(W2[(4 * c + q) * kHidden + u], h[u], a);
+          ol[q] = a;
+        }
+        const float pr = base[(static_cast<size_t>(k) * CC + c) * 2 + 0];
+        const float pi = base[(static_cast<size_t>(k) * CC + c) * 2 + 1];
+        const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
+        const float ur = agr * pr - agi * pi + gj[4 * c + 2];
+        const float ui = agr * pi + agi * pr + gj[4 * c + 3];
+        const float alr = 1.0f + ol[0], ali = ol[1];
+        const float gr = gs[2 * c], gi = gs[2 * c + 1];
+        dol[4 * c + 0] = gr * ur + gi * ui;  // dL/da_l = g conj(u)
+        dol[4 * c + 1] = gi * ur - gr * ui;
+        dol[4 * c + 2] = gr;                 // dL/db_l = g
+        dol[4 * c + 3] = gi;
+        const float dur = gr * alr + gi * ali, dui = gi * alr - gr * ali;  // g conj(1 + a_l)
+        aog[4 * c + 0] += dur * pr + dui * pi;  // dL/da_g = du conj(phi)
+        aog[4 * c + 1] += dui * pr - dur * pi;
+        aog[4 * c + 2] += dur;                  // dL/db_g = du
+        aog[4 * c + 3] += dui;
+        db[2 * c + 0] = dur * agr + dui * agi;  // dL/dphi = du conj(1 + a_g)
+        db[2 * c + 1] = dui * agr - dur * agi;
+      }
+    }
+    // dL/dphi: one atomic per warp when the warp's pairs share k
+    {
+      const int k0 = __shfl_sync(0xffffffffu, k, 0);
+      const bool same = __all_sync(0xffffffffu, !ok || k == k0) &&
+                        __shfl_sync(0xffffffffu, static_cast<int>(ok), 0);
+      if (same) {
+#pragma unroll
+        for (int q = 0; q < 2 * CC; ++q) {
+          float y = db[q];
+#pragma unroll
+          for (int off = 16; off >= 1; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+          if (lane == 0) atomicAdd(&grad_base[static_cast<size_t>(k0) * 2 * CC + q], y);
+        }
+      } else if (ok) {
+#pragma unroll
+        for (int q = 0; q < 2 * CC; ++q)
+          atomicAdd(&grad_base[static_cast<size_t>(k) * 2 * CC + q], db[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < n4; ++q) ab2[q] += dol[q];
+    // dL/dW2 = dol x h, reduce-scattered per 32-wide slice
+#pragma unroll
+    for (int q = 0; q < n4; ++q)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = dol[q] * h[hf * 32 + e];
+        aw2[q][hf] += warp_reduce_scatter32(v);
+      }
+    // dL/dh = W2^T dol on active units
+    float dh[kHidden];
+#pragma unroll
     for (int u = 0; u < kHidden; ++u) {
       float a = 0.0f;
-      for (int q = 0; q < n4; ++q) a = fmaf(W2[q * kHidden + u], sDol[t * n4 + q], a);
-      sDh[t * 65 + u] = sH[t * 65 + u] > 0.0f ? a : 0.0f;
+#pragma unroll
+      for (int q = 0; q < n4; ++q) a = fmaf(W2[q * kHidden + u], dol[q], a);
+      dh[u] = h[u] > 0.0f ? a : 0.0f;
     }
-    __syncthreads();
-    // ---- phase 3: owned parameter sums over the tile's pairs
-    if (t < n4 * kHidden) {
-      const int q = t / kHidden, u = t % kHidden;
-      float a = 0.0f;
-      for (int pp = 0; pp < kBwdPairs; ++pp) a = fmaf(sDol[pp * n4 + q], sH[pp * 65 + u], a);
-      aW2 += a;
-    }
-    {
-      const int e0 = t, e1 = t + kBwdPairs;  // dW1 entries u*6 + i
-      float a0 = 0.0f, a1 = 0.0f;
-      for (int pp = 0; pp < kBwdPairs; ++pp) {
-        a0 = fmaf(sDh[pp * 65 + e0 / 6], sX[pp * 6 + e0 % 6], a0);
-        if (e1 < kHidden * 6) a1 = fmaf(sDh[pp * 65 + e1 / 6], sX[pp * 6 + e1 % 6], a1);
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = dh[hf * 32 + e];
+        ab1[hf] += warp_reduce_scatter32(v);
       }
-      aW1a += a0;
-      aW1b += a1;
-    }
-    if (t < kHidden) {
-      float a = 0.0f;
-      for (int pp = 0; pp < kBwdPairs; ++pp) a += sDh[pp * 65 + t];
-      aB1 += a;
-    }
-    if (t < n4) {
-      float a = 0.0f;
-      for (int pp = 0; pp < kBwdPairs; ++pp) a += sDol[pp * n4 + t];
-      aB2 += a;
-    }
-    // ---- phase 4: dL/dphi per Gaussian (atomics: a Gaussian's pairs may span
-    // tiles), dL/d(a_g, b_g) per receiver into the block accumulator
-    {
-      const size_t kfirst = p0 / N;
-      const size_t plast = min(p0 + kBwdPairs, pairs) - 1;
-      const size_t klast = plast / N;
-      const size_t nk = klast - kfirst + 1;
-      for (size_t kk = t; kk < nk; kk += kBwdPairs) {
-        const size_t k = kfirst + kk;
-        const size_t a0 = max(k * N, p0) - p0, a1 = min((k + 1) * N, plast + 1) - p0;
-        for (int q = 0; q < 2 * C; ++q) {
-          float s = 0.0f;
-          for (size_t pp = a0; pp < a1; ++pp) s += sDB[pp * 2 * C + q];
-          atomicAdd(&grad_base[k * 2 * C + q], s);
-        }
-      }
-      for (int j = t; j < N; j += kBwdPairs) {
-        for (size_t pp = (j + N - p0 % N) % N; pp < kBwdPairs && p0 + pp < pairs; pp += N)
-          for (int q = 0; q < n4; ++q) accOG[j * n4 + q] += sOG[pp * n4 + q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = dh[hf * 32 + e] * x[i];
+        aw1[i][hf] += warp_reduce_scatter32(v);
       }
     }
-    __syncthreads();
   }
-  // ---- block partial: [local params (flat order l_w1 l_b1 l_w2 l_b2)] [N][4C]
-  const int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
+
+  // ---- warp partials -> shared, then a fixed-order sum over warps
+  float* wp = sdyn + warp * nloc;
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    const int u = hf * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) wp[u * 6 + i] = aw1[i][hf];
+    wp[u * 6 + 4] = ab1[hf];  // input 4 is constant 1: same gradient as the bias
+    wp[u * 6 + 5] = 0.0f;     // input 5 is constant 0
+    wp[kHidden * 6 + u] = ab1[hf];
+#pragma unroll
+    for (int q = 0; q < n4; ++q) wp[kHidden * 7 + q * kHidden + u] = aw2[q][hf];
+  }
+#pragma unroll
+  for (int q = 0; q < n4; ++q) {
+    float y = ab2[q];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+    if (lane == 0) wp[kHidden * 7 + n4 * kHidden + q] = y;
+  }
+  float* og = sdyn + kWarps * nloc;  // [256][4C]
+#pragma unroll
+  for (int q = 0; q < n4; ++q) og[t * n4 + q] = aog[q];
+  __syncthreads();
   float* dst = part + static_cast<size_t>(blockIdx.x) * (nloc + static_cast<size_t>(N) * n4);
-  dst[t] = aW1a;
-  if (t + kBwdPairs < kHidden * 6) dst[t + kBwdPairs] = aW1b;
-  if (t < kHidden) dst[kHidden * 6 + t] = aB1;
-  if (t < n4 * kHidden) dst[kHidden * 7 + t] = aW2;
-  if (t < n4) dst[kHidden * 7 + n4 * kHidden + t] = aB2;
-  for (int e = t; e < N * n4; e += kBwdPairs) dst[nloc + e] = accOG[e];
+  for (int e = t; e < nloc; e += kBwdThreads) {
+    float y = 0.0f;
+    for (int w = 0; w < kWarps; ++w) y += sdyn[w * nloc + e];
+    dst[e] = y;
+  }
+  const int shift = static_cast<int>((static_cast<size_t>(blockIdx.x) * kBwdThreads) % N);
+  for (int e = t; e < N * n4; e += kBwdThreads) {
+    const int jj = e / n4, q = e % n4;
+    float y = 0.0f;
+    for (int tt = (jj - shift + N) % N; tt < kBwdThreads; tt += N) y += og[tt * n4 + q];
+    dst[nloc + e] = y;
+  }
 }
 
 // Sums the block partials in block order: local parameters go into
@@ -406,23 +455,36 @@ __global__ void mlp_global_bwd_kernel(const float* __restrict__ P, int C,
   }
 }
 
+template <int CC>
+static void launch_mlp_local_bwd(int blocks, const MlpParams& m, const float* rx, int N,
+                                 const float4* geom, const float* base, int K, int stride,
+                                 const float* dS, const float* glob, float* grad_base, float* part,
+                                 cudaStream_t s) {
+  constexpr int n4 = 4 * CC;
+  constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
+  const size_t smem = sizeof(float) * ((kBwdThreads / 32) * nloc + kBwdThreads * n4);
+  cudaFuncSetAttribute(mlp_local_bwd_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  mlp_local_bwd_kernel<CC><<<blocks, kBwdThreads, smem, s>>>(m.p, rx, N, geom, base, K, stride, dS,
+                                                             glob, grad_base, part);
+  note_launches(1);
+}
+
 void launch_mlp_backward(const MlpParams& m, const float* rx, int N, const float4* geom,
                          const float* base, int K, int stride, const float* dS,
                          const float* glob, float* grad_base, float* grad_mlp, float* tmp,
                          cudaStream_t s) {
   const int C = m.C, n4 = 4 * C;
   const int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
-  const int blocks = mlp_bwd_blocks();
-  const size_t smem = sizeof(float) * (kHidden * 7 + n4 * kHidden + kBwdPairs * 6 +
-                                       kBwdPairs * 65 * 2 + kBwdPairs * n4 * 2 +
-                                       kBwdPairs * 2 * C + static_cast<size_t>(N) * n4);
-  cudaFuncSetAttribute(mlp_local_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
+  const int blocks = mlp_bwd_blocks(N);
   float* part = tmp;
   float* dog = tmp + static_cast<size_t>(blocks) * (nloc + static_cast<size_t>(N) * n4);
-  mlp_local_bwd_kernel<<<blocks, kBwdPairs, smem, s>>>(m.p, C, rx, N, geom, base, K, stride, dS,
-                                                       glob, grad_base, part);
-  note_launches(1);
+  switch (C) {
+    case 1: launch_mlp_local_bwd<1>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
+    case 2: launch_mlp_local_bwd<2>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
+    case 3: launch_mlp_local_bwd<3>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
+    default: launch_mlp_local_bwd<4>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
+  }
   const int tot = nloc + N * n4;
   const MlpOffsets o = mlp_offsets(kHidden, C);
   mlp_partial_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(part, blocks, nloc, N * n4, o.l_w1,

@@ -13,10 +13,11 @@
 // with T_m like the value itself (a forward difference D - E_m would cancel
 // catastrophically once T is small).
 //
-// Per tile, nothing is read from the forward: a first walk recomputes every
-// pixel's final T and stop position with the forward's float32 decisions
-// (per-tile recomputation), then the list is swept back to front, chunk by
-// chunk, recovering T_m = T_{m+1} / (1 - w_m).  Both gradients are linear in
+// Nothing is read from the forward: a pre-pass walks each tile's list once
+// and recomputes every pixel's final T and stop position with the forward's
+// float32 decisions (per-tile recomputation); then each (tile, column block)
+// sweeps the list back to front, chunk by chunk, recovering
+// T_m = T_{m+1} / (1 - w_m).  Both gradients are linear in
 // the columns, so each CTA handles a block of 32 columns and the per-block
 // contributions add up.
 #include "render_common.cuh"
@@ -33,6 +34,65 @@ constexpr size_t bwd_smem_bytes() {
          sizeof(float4) * 2 * kChunk + sizeof(uint32_t) * kChunk;
 }
 
+// Walk 1, once per (view, tile): every pixel's final transmittance and the
+// list position one past its last composited Gaussian (its stop), with the
+// forward's float32 decisions; tile_stop = the largest stop of the tile.
+__global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderArgs a,
+                                                                  float* __restrict__ tfin,
+                                                                  uint32_t* __restrict__ stops,
+                                                                  uint32_t* __restrict__ tile_stop) {
+  __shared__ float4 sRec[2 * kChunk];
+  __shared__ unsigned sStop;
+  const GridConst& g = a.g;
+  const int t = threadIdx.x;
+  const int tile = blockIdx.x, v = blockIdx.z;
+  const int tr = tile / g.tiles_w, tc = tile % g.tiles_w;
+  const int i = tr * g.TH + t / g.TW, jj = tc * g.TW + t % g.TW;
+  const bool valid = i < g.H && jj < g.W;
+  const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
+  const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
+  const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
+  if (t == 0) sStop = rg.x;
+  float T = 1.0f;
+  uint32_t stop = valid ? rg.y : rg.x;
+  bool alive = valid;
+  for (uint32_t start = rg.x; start < rg.y; start += kChunk) {
+    const int nb = min(kChunk, static_cast<int>(rg.y - start));
+    __syncthreads();
+    if (t < kChunk) {
+      const bool ok = t < nb;
+      const uint32_t k = ok ? a.vals[start + t] : 0u;
+      cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
+      cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (alive) {
+      for (int b = 0; b < nb; ++b) {
+        float w, G;
+        if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
+          T = __fmul_rn(T, __fsub_rn(1.0f, w));
+          if (T < g.eps_T) {
+            alive = false;
+            stop = start + b + 1;
+            break;
+          }
+        }
+      }
+    }
+    if (__syncthreads_count(alive) == 0) break;
+  }
+  atomicMax(&sStop, stop);
+  if (valid) {
+    const size_t o = static_cast<size_t>(v) * g.H * g.W + static_cast<size_t>(i) * g.W + jj;
+    tfin[o] = T;
+    stops[o] = stop;
+  }
+  __syncthreads();
+  if (t == 0) tile_stop[static_cast<size_t>(v) * g.T + tile] = sStop;
+}
+
 __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const BackwardArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sG = reinterpret_cast<float*>(smem_raw);   // [256][36] cotangent rows
@@ -41,7 +101,6 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
   float* sR = sT + kChunk * kPad;                   // [32][32] radiance slice
   float4* sRec = reinterpret_cast<float4*>(sR + kChunk * kBNB);  // [32][2]
   uint32_t* sK = reinterpret_cast<uint32_t*>(sRec + 2 * kChunk);  // [32]
-  __shared__ unsigned sStop;
 
   const RenderArgs& a = A.f;
   const GridConst& g = a.g;
@@ -72,45 +131,15 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
     gr[c] = val;
     sG[t * kGStride + c] = val;
   }
-  if (t == 0) sStop = rg.x;
-
-  // ---- walk 1: final transmittance and stop position of every pixel
+  // final transmittance and stop position from the per-tile pre-pass
   float T = 1.0f;
-  uint32_t stop = rg.y;  // one past the last list entry this pixel considers
-  {
-    bool alive = valid;
-    if (!valid) stop = rg.x;
-    for (uint32_t start = rg.x; start < rg.y; start += kChunk) {
-      const int nb = min(kChunk, static_cast<int>(rg.y - start));
-      __syncthreads();
-      if (t < kChunk) {
-        const bool ok = t < nb;
-        const uint32_t k = ok ? a.vals[start + t] : 0u;
-        cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
-        cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
-      }
-      cp_async_commit();
-      cp_async_wait_all();
-      __syncthreads();
-      if (alive) {
-        for (int b = 0; b < nb; ++b) {
-          float w, G;
-          if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
-            T = __fmul_rn(T, __fsub_rn(1.0f, w));
-            if (T < g.eps_T) {
-              alive = false;
-              stop = start + b + 1;
-              break;
-            }
-          }
-        }
-      }
-      if (__syncthreads_count(alive) == 0) break;
-    }
+  uint32_t stop = rg.x;
+  if (valid) {
+    const size_t o = static_cast<size_t>(v) * HW + pix;
+    T = A.tfin[o];
+    stop = A.stops[o];
   }
-  atomicMax(&sStop, stop);
-  __syncthreads();
-  const uint32_t tile_stop = sStop;
+  const uint32_t tile_stop = A.tile_stop[static_cast<size_t>(v) * g.T + tile];
 
   // dS mapping: 32 output blocks (4 Gaussians x 8 columns) x 8 pixel slices
   const int slice = t & 7, ob = t >> 3;
@@ -156,7 +185,7 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
             gam = fmaf(gr[4 * q + 3], s4.w, gam);
           }
           const float one_m_w = 1.0f - w;
-          T = T / one_m_w;  // transmittance in front of this Gaussian
+          T = __fdividef(T, one_m_w);  // transmittance in front of this Gaussian
           Tw = T * w;
           dtau = T * (gam - Q) * G;
           Q = fmaf(w, gam, one_m_w * Q);
@@ -235,6 +264,8 @@ void launch_render_bwd(const BackwardArgs& A, int /*cols_per_cta*/, cudaStream_t
                          static_cast<int>(smem));
     configured = true;
   }
+  bwd_prepass_kernel<<<dim3(a.g.T, 1, a.M), kTilePixels, 0, s>>>(a, A.tfin, A.stops, A.tile_stop);
+  note_launches(1);
   dim3 grid(a.g.T, (a.ncols + kBNB - 1) / kBNB, a.M);
   render_bwd_kernel<<<grid, kTilePixels, smem, s>>>(A);
   note_launches(1);

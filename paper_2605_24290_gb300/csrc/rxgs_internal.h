@@ -115,7 +115,9 @@ struct BackwardArgs {
   const float* g_uniform;     // [M][ncols] cotangent uniform over pixels, or null
   float* d_rad;               // [K][stride] dL/ds accumulated (atomics)
   float* d_tau;               // [K] accumulated
-  float* d_tau_partial;       // deterministic: [I][colblocks] or null
+  float* tfin;                // scratch [M][H][W]: final transmittance per pixel
+  uint32_t* stops;            // scratch [M][H][W]: stop position per pixel
+  uint32_t* tile_stop;        // scratch [M][T]: largest stop of each tile
   uint32_t n_inst;
 };
 void launch_render_bwd(const BackwardArgs& a, int cols_per_cta, cudaStream_t s);
