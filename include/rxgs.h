@@ -234,6 +234,24 @@ rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uin
 rxgs_status rxgs_profile(rxgs_ctx* ctx, int enable);
 rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset);
 
+/* CSI (and RSSI when C == 1) of prepared views for the receiver-major
+ * radiance[N,K,C,2], WITHOUT allocating any device memory.  The paper has no
+ * counterpart: this is for callers that must not allocate while rendering
+ * (a latency-bound serving thread, a host program whose device memory is
+ * owned by another allocator or budgeted up front).  It computes the same
+ * values as rxgs_render_views with RXGS_OUT_CSI / RXGS_OUT_RSSI.
+ *   csi[M,N,C,2] and/or rssi[M,N]   outputs (device, caller-owned)
+ * The per-tile partial sums live in a fixed 16 MiB device array inside the
+ * library (every GPU that loads the library keeps it until the process
+ * exits), so M * tiles * 2 * N * C must not exceed 4,194,304; larger
+ * requests return RXGS_E_INVALID and print the limit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call reuses the same
+ * array: calls whose work overlaps on the GPU race and must be serialised
+ * by the caller (one stream, or events). */
+rxgs_status rxgs_render_csi_noalloc(rxgs_ctx* ctx, rxgs_views_t views, const float* radiance,
+                                    int N, float* csi, float* rssi, void* stream);
+
 /* Waits for `stream` and converts a recorded device error into a status. */
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream);
 

@@ -232,6 +232,33 @@ void launch_uniform_cotangent(const float* gcsi, const float* grssi, const float
   note_launches(1);
 }
 
+namespace rxgs {
+bool lookup_views(void* c, uint64_t views, ViewsRef* out, const char** err) {
+  rxgs_ctx* ctx = static_cast<rxgs_ctx*>(c);
+  if (!ctx) {
+    *err = "null context";
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) {
+    *err = "unknown views";
+    return false;
+  }
+  const ViewsState* v = it->second;
+  const SceneState* s = ctx->scenes.at(v->scene);
+  out->device = ctx->device;
+  out->g = ctx->g;
+  out->M = v->M;
+  out->K = v->K;
+  out->C = s->C;
+  out->rec = v->rec;
+  out->vals = v->vals;
+  out->ranges = v->ranges;
+  return true;
+}
+}  // namespace rxgs
+
 // ====================================================================== ABI
 extern "C" {
 

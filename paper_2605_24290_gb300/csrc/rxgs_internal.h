@@ -122,4 +122,16 @@ struct BackwardArgs {
 };
 void launch_render_bwd(const BackwardArgs& a, int cols_per_cta, cudaStream_t s);
 
+// Read-only view of a context's prepared transmitter-side state, for entry
+// points that live outside api.cu.  Returns false for an unknown handle.
+struct ViewsRef {
+  int device;
+  GridConst g;
+  int M, K, C;
+  const float4* rec;
+  const uint32_t* vals;
+  const uint2* ranges;
+};
+bool lookup_views(void* ctx, uint64_t views, ViewsRef* out, const char** err);
+
 }  // namespace rxgs

@@ -82,6 +82,7 @@ SIGNATURES = {
     "rxgs_views_export": (I, [P, U64, P, P, P, P, P, P]),
     "rxgs_profile": (I, [P, I]),
     "rxgs_profile_read": (I, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
+    "rxgs_render_csi_noalloc": (I, [P, U64, P, I, P, P, P]),
     "rxgs_sync": (I, [P, P]),
 }
 
@@ -259,6 +260,15 @@ class Context:
     def mlp_numel(C, hidden=64):
         """Number of float32 parameters of the two conditioning MLPs."""
         return hidden * 3 + hidden + 4 * C * hidden + 4 * C + hidden * 6 + hidden + 4 * C * hidden + 4 * C
+
+    def render_csi_noalloc(self, views, radiance, N, csi=None, rssi=None, stream=None):
+        """CSI / RSSI of prepared views with no device allocation (the
+        library's fixed scratch array holds the partial sums)."""
+        st = self.lib.rxgs_render_csi_noalloc(self.h, U64(views), _f32(radiance), int(N), _f32(csi),
+                                              _f32(rssi), _stream(stream))
+        if st != OK:
+            raise RxgsError(st, "rxgs_render_csi_noalloc failed (bad arguments or sizes beyond "
+                                "its fixed scratch)")
 
     def sync(self, stream=None):
         self._check(self.lib.rxgs_sync(self.h, _stream(stream)))
