@@ -174,6 +174,26 @@ rxgs_status rxgs_render(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int 
                         const float* rx, int N, const rxgs_render_desc* desc,
                         rxgs_outputs* out, void* stream);
 
+/* Uneven receiver batches (one transmitter per batch, ragged receiver
+ * counts) rendered by one persistent launch inside a CUDA graph.
+ *   tx[B,3]            one transmitter per batch (device or host pointer)
+ *   rx[R,3]            all receivers, batch after batch, R = sum rx_counts
+ *   rx_counts[B]       HOST array, each >= 1
+ *   desc->radiance     [R,K,C,2] receiver-major, or NULL = scene MLP
+ *   out->spectra       [R,H,W,C,2], out->csi [R,C,2], out->rssi [R]
+ * The first call for a (scene, kind, radiance mode) whose sizes exceed every
+ * existing plan measures the batch's instance counts (one readback per
+ * view), allocates a plan with capacity for the next power of two of views
+ * and receivers and 1.25x the largest per-view instance count, and captures
+ * the pipeline into a CUDA graph; later calls copy the inputs and a small
+ * descriptor into the plan and replay the graph.  A batch whose instances
+ * exceed the plan's capacity sets RXGS_E_DEVICE at the next rxgs_sync (its
+ * results are then invalid).  Calls that share a plan must be ordered (one
+ * stream). */
+rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
+                                const float* rx, const int32_t* rx_counts,
+                                const rxgs_render_desc* desc, rxgs_outputs* out, void* stream);
+
 /* Backward (App. D): gradients of a loss L given dL/d(outputs).
  *   grad_spectra [M,N,H,W,C,2] or NULL
  *   grad_csi     [M,N,C,2] or NULL   (uniform over pixels)

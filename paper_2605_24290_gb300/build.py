@@ -30,7 +30,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def headers():
@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     hdr = max(_mtime(h) for h in headers())
     objs, jobs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         if force or _mtime(obj) < max(_mtime(src), hdr):
             jobs.append((src, obj))
@@ -56,7 +56,8 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     def run(job):
         src, obj = job
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+        lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
+        cmd = [cc, *ARCH, *FLAGS, *extra, *lang, "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -70,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
                     print(out, file=sys.stderr)
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/rxgs.h"
+#include "ctx_internal.h"
 #include "rxgs_internal.h"
 
 namespace rxgs {
@@ -27,103 +28,6 @@ unsigned long long launch_count() { return g_launches.load(std::memory_order_rel
 using namespace rxgs;
 
 namespace {
-
-struct SceneState {
-  int K = 0, C = 0;
-  uint64_t generation = 0;  // bumped by rxgs_update_scene
-  float4* geom = nullptr;   // [K][3]
-  float* base = nullptr;    // [K][C][2]
-  float* mlp = nullptr;     // flat
-  size_t mlp_floats = 0;
-  int hidden = 0, bf16 = 0;
-};
-
-struct ViewsState {
-  rxgs_scene_t scene = 0;
-  int M = 0, K = 0;
-  float* tx = nullptr;        // [M][3]
-  float4* rec = nullptr;      // [M][K][2]
-  uint32_t* depth = nullptr;  // [M][K]
-  uint32_t* counts = nullptr; // [M*K]
-  uint32_t* offsets = nullptr;// [M*K+1]
-  uint64_t* keys = nullptr;   // [I]
-  uint32_t* vals = nullptr;   // [I]
-  uint2* ranges = nullptr;    // [M][T]
-  uint32_t n_inst = 0;
-  int tile_bits = 0, view_bits = 0;
-  // radiance of the last rxgs_render_views on these views, kept for the
-  // backward: valid for the same rx pointer, N, radiance pointer and scene
-  // generation
-  float* rad = nullptr;
-  float* glob = nullptr;
-  const float* key_rx = nullptr;
-  const float* key_radiance = nullptr;
-  int key_N = 0, key_stride = 0;
-  uint64_t key_gen = ~0ull;
-};
-
-}  // namespace
-
-struct rxgs_ctx {
-  int device = 0;
-  rxgs_options opts{};
-  GridConst g{};
-  std::mutex mu;
-  std::string err;
-  uint64_t next_id = 1;
-  std::map<uint64_t, SceneState*> scenes;
-  std::map<uint64_t, ViewsState*> views;
-  unsigned* d_err = nullptr;      // device error word
-  uint32_t* h_pinned = nullptr;   // pinned readback slot
-  // stage profiler: CUDA events recorded on the call's stream around each
-  // stage while enabled, folded into per-stage totals by rxgs_profile_read
-  bool prof = false;
-  struct Pending {
-    std::string name;
-    cudaEvent_t a, b;
-  };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> event_pool;
-  std::map<std::string, std::pair<double, long>> stage_ms;
-};
-
-namespace {
-
-rxgs_status fail(rxgs_ctx* c, rxgs_status st, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  if (c) c->err = buf;
-  return st;
-}
-
-#define CK(call)                                                                        \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess)                                                              \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? RXGS_E_OOM : RXGS_E_CUDA,      \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-  } while (0)
-
-template <typename T>
-cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
-  if (n == 0) n = 1;
-  return cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
-}
-
-template <typename T>
-void dfree(T*& p, cudaStream_t s) {
-  if (p) cudaFreeAsync(p, s);
-  p = nullptr;
-}
-
-int bits_for(uint64_t n) {  // bits to hold values 0..n-1
-  int b = 0;
-  while ((1ull << b) < n) ++b;
-  return b;
-}
 
 rxgs_status check_last(rxgs_ctx* ctx, const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -162,47 +66,6 @@ bool make_grid(const rxgs_options& o, GridConst* g, std::string* why) {
   return true;
 }
 
-int round_up(int x, int m) { return (x + m - 1) / m * m; }
-
-cudaEvent_t take_event(rxgs_ctx* c) {
-  if (!c->event_pool.empty()) {
-    cudaEvent_t e = c->event_pool.back();
-    c->event_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// Times one stage of a call on `stream` when the profiler is on.
-struct Stage {
-  rxgs_ctx* c;
-  cudaStream_t s;
-  std::string name;
-  cudaEvent_t a = nullptr;
-  Stage(rxgs_ctx* ctx, const char* n, cudaStream_t st) : c(ctx), s(st), name(n) {
-    if (c->prof) {
-      a = take_event(c);
-      cudaEventRecord(a, s);
-    }
-  }
-  ~Stage() {
-    if (a) {
-      cudaEvent_t b = take_event(c);
-      cudaEventRecord(b, s);
-      c->pending.push_back({name, a, b});
-    }
-  }
-};
-
-int pick_cols(const rxgs_ctx* ctx, int ncols) {
-  if (ctx->opts.cols_per_cta) return ctx->opts.cols_per_cta;
-  if (ncols <= 16) return 16;
-  if (ncols <= 32) return 32;
-  return 64;
-}
-
 }  // namespace
 
 // Cotangent that is uniform over the pixels of a (view, receiver, channel):
@@ -233,6 +96,24 @@ void launch_uniform_cotangent(const float* gcsi, const float* grssi, const float
 }
 
 namespace rxgs {
+cudaEvent_t take_event(rxgs_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int pick_cols(const rxgs_ctx* ctx, int ncols) {
+  if (ctx->opts.cols_per_cta) return ctx->opts.cols_per_cta;
+  if (ncols <= 16) return 16;
+  if (ncols <= 32) return 32;
+  return 64;
+}
+
 bool lookup_views(void* c, uint64_t views, ViewsRef* out, const char** err) {
   rxgs_ctx* ctx = static_cast<rxgs_ctx*>(c);
   if (!ctx) {
@@ -329,6 +210,8 @@ rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
     cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
     delete s;
   }
+  if (ctx->serve) destroy_serve(ctx->serve);
+  for (BatchPlan* p : ctx->plans) destroy_plan(p);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_pinned);
   for (auto& p : ctx->pending) {

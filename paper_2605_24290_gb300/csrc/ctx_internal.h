@@ -1,0 +1,154 @@
+// ctx_internal.h -- host-side state of a context (scenes, views, batch
+// plans, serving) shared by the library's translation units.  Not part of
+// the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rxgs.h"
+#include "rxgs_internal.h"
+
+namespace rxgs {
+
+struct SceneState {
+  int K = 0, C = 0;
+  uint64_t generation = 0;  // bumped by rxgs_update_scene
+  float4* geom = nullptr;   // [K][3]
+  float* base = nullptr;    // [K][C][2]
+  float* mlp = nullptr;     // flat
+  size_t mlp_floats = 0;
+  int hidden = 0, bf16 = 0;
+};
+
+struct ViewsState {
+  rxgs_scene_t scene = 0;
+  int M = 0, K = 0;
+  float* tx = nullptr;        // [M][3]
+  float4* rec = nullptr;      // [M][K][2]
+  uint32_t* depth = nullptr;  // [M][K]
+  uint32_t* counts = nullptr; // [M*K]
+  uint32_t* offsets = nullptr;// [M*K+1]
+  uint64_t* keys = nullptr;   // [I]
+  uint32_t* vals = nullptr;   // [I]
+  uint2* ranges = nullptr;    // [M][T]
+  uint32_t n_inst = 0;
+  int tile_bits = 0, view_bits = 0;
+  // radiance of the last rxgs_render_views on these views, kept for the
+  // backward: valid for the same rx pointer, N, radiance pointer and scene
+  // generation
+  float* rad = nullptr;
+  float* glob = nullptr;
+  const float* key_rx = nullptr;
+  const float* key_radiance = nullptr;
+  int key_N = 0, key_stride = 0;
+  uint64_t key_gen = ~0ull;
+};
+
+struct BatchPlan;    // batch.cu
+struct ServeState;   // serve.cpp
+void destroy_plan(BatchPlan* p);
+void destroy_serve(ServeState* s);
+
+}  // namespace rxgs
+
+struct rxgs_ctx {
+  int device = 0;
+  rxgs_options opts{};
+  rxgs::GridConst g{};
+  std::mutex mu;
+  std::string err;
+  uint64_t next_id = 1;
+  std::map<uint64_t, rxgs::SceneState*> scenes;
+  std::map<uint64_t, rxgs::ViewsState*> views;
+  std::vector<rxgs::BatchPlan*> plans;
+  rxgs::ServeState* serve = nullptr;
+  unsigned* d_err = nullptr;      // device error word
+  uint32_t* h_pinned = nullptr;   // pinned readback slot
+  // stage profiler: CUDA events recorded on the call's stream around each
+  // stage while enabled, folded into per-stage totals by rxgs_profile_read
+  bool prof = false;
+  struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, std::pair<double, long>> stage_ms;
+};
+
+namespace rxgs {
+
+inline rxgs_status fail(rxgs_ctx* c, rxgs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? RXGS_E_OOM : RXGS_E_CUDA,      \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
+  if (n == 0) n = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+inline int bits_for(uint64_t n) {  // bits to hold values 0..n-1
+  int b = 0;
+  while ((1ull << b) < n) ++b;
+  return b;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+cudaEvent_t take_event(rxgs_ctx* c);
+
+// Times one stage of a call on `stream` when the profiler is on.
+struct Stage {
+  rxgs_ctx* c;
+  cudaStream_t s;
+  std::string name;
+  cudaEvent_t a = nullptr;
+  Stage(rxgs_ctx* ctx, const char* n, cudaStream_t st) : c(ctx), s(st), name(n) {
+    if (c->prof) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Stage() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back({name, a, b});
+    }
+  }
+};
+
+int pick_cols(const rxgs_ctx* ctx, int ncols);
+
+}  // namespace rxgs

@@ -186,12 +186,19 @@ __device__ __forceinline__ TileCols tile_cols(const GridConst& g, int j_lo, int 
 
 __global__ void preprocess_kernel(GridConst g, const float4* __restrict__ geom, int K,
                                   const float* __restrict__ tx, float4* __restrict__ rec,
-                                  uint32_t* __restrict__ depth, uint32_t* __restrict__ count) {
+                                  uint32_t* __restrict__ depth, uint32_t* __restrict__ count,
+                                  const int* __restrict__ nviews_dev) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y;
   if (k >= K) return;
   const float4 g0 = geom[3 * k + 0], g1 = geom[3 * k + 1], g2 = geom[3 * k + 2];
-  const Footprint f = project_one(g, g0, g1, g2, tx[3 * v + 0], tx[3 * v + 1], tx[3 * v + 2]);
+  Footprint f;
+  if (nviews_dev && v >= *nviews_dev) {
+    f.vis = false;  // view slot unused in this batch
+    f.rho = 0.0f;
+  } else {
+    f = project_one(g, g0, g1, g2, tx[3 * v + 0], tx[3 * v + 1], tx[3 * v + 2]);
+  }
   const size_t idx = static_cast<size_t>(v) * K + k;
   uint32_t n = 0;
   if (f.vis) {
@@ -211,10 +218,11 @@ __global__ void preprocess_kernel(GridConst g, const float4* __restrict__ geom, 
 }
 
 void launch_preprocess(const GridConst& g, const float4* geom, int K, const float* tx, int M,
-                       float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s) {
+                       float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s,
+                       const int* nviews_dev) {
   if (K <= 0 || M <= 0) return;
   dim3 grid((K + 255) / 256, M);
-  preprocess_kernel<<<grid, 256, 0, s>>>(g, geom, K, tx, rec, depth, count);
+  preprocess_kernel<<<grid, 256, 0, s>>>(g, geom, K, tx, rec, depth, count, nviews_dev);
   note_launches(1);
 }
 
@@ -224,7 +232,8 @@ void launch_preprocess(const GridConst& g, const float4* geom, int K, const floa
 __global__ void emit_kernel(GridConst g, const float4* __restrict__ rec,
                             const uint32_t* __restrict__ depth,
                             const uint32_t* __restrict__ offsets, int K, int tile_bits,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t cap,
+                            unsigned* __restrict__ err) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y;
   if (k >= K) return;
@@ -232,6 +241,10 @@ __global__ void emit_kernel(GridConst g, const float4* __restrict__ rec,
   uint32_t o = offsets[idx];
   const uint32_t end = offsets[idx + 1];
   if (o == end) return;
+  if (end > cap) {  // more instances than the buffers hold: record, write nothing
+    if (err) atomicOr(err, kErrCapacity);
+    return;
+  }
   const float4 r1 = rec[2 * idx + 1];
   const int rows = __float_as_int(r1.z), cols = __float_as_int(r1.w);
   const int i_lo = rows & 0xffff, i_hi = rows >> 16, j_lo = cols & 0xffff, span = cols >> 16;
@@ -253,16 +266,18 @@ __global__ void emit_kernel(GridConst g, const float4* __restrict__ rec,
 
 void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
                  const uint32_t* offsets, int K, int M, int tile_bits, uint64_t* keys,
-                 uint32_t* vals, cudaStream_t s) {
+                 uint32_t* vals, cudaStream_t s, uint32_t cap, unsigned* err) {
   if (K <= 0 || M <= 0) return;
   dim3 grid((K + 255) / 256, M);
-  emit_kernel<<<grid, 256, 0, s>>>(g, rec, depth, offsets, K, tile_bits, keys, vals);
+  emit_kernel<<<grid, 256, 0, s>>>(g, rec, depth, offsets, K, tile_bits, keys, vals, cap, err);
   note_launches(1);
 }
 
 // -------------------------------------------------------------- tile ranges
 __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, size_t n, int tile_bits,
-                                   int T, uint2* __restrict__ ranges) {
+                                   int T, uint2* __restrict__ ranges,
+                                   const uint32_t* __restrict__ n_dev) {
+  if (n_dev && *n_dev < n) n = *n_dev;
   const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   auto slot = [&](uint64_t key) {
@@ -276,11 +291,11 @@ __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, size_t n, 
 }
 
 void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
-                        int M, cudaStream_t s) {
+                        int M, cudaStream_t s, const uint32_t* n_dev) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(M) * T, s);
   if (n == 0) return;
   tile_ranges_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(keys, n, tile_bits,
-                                                                            T, ranges);
+                                                                            T, ranges, n_dev);
   note_launches(1);
 }
 

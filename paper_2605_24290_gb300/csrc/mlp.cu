@@ -40,10 +40,12 @@ __device__ __forceinline__ float rb(float x, int bf16) {
 
 // glob[j][4C] = MLP_g(r_j); one block per receiver.
 __global__ void mlp_global_kernel(const float* __restrict__ P, int C, int bf16,
-                                  const float* __restrict__ rx, float* __restrict__ glob) {
+                                  const float* __restrict__ rx, float* __restrict__ glob,
+                                  const int* __restrict__ n_dev) {
   __shared__ float h[kHidden];
   const MlpOffsets o = mlp_offsets(kHidden, C);
   const int j = blockIdx.x;
+  if (n_dev && j >= *n_dev) return;
   const float x0 = rb(rx[3 * j + 0], bf16), x1 = rb(rx[3 * j + 1], bf16),
               x2 = rb(rx[3 * j + 2], bf16);
   for (int u = threadIdx.x; u < kHidden; u += blockDim.x) {
@@ -71,7 +73,9 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
                                                         const float* __restrict__ base, int K,
                                                         int stride,
                                                         const float* __restrict__ glob,
-                                                        float* __restrict__ out) {
+                                                        float* __restrict__ out,
+                                                        const int* __restrict__ n_dev,
+                                                        const int* __restrict__ col_of) {
   extern __shared__ float sw[];  // l_w1 [64*6], l_b1 [64], l_w2 [4C*64], l_b2 [4C]
   const MlpOffsets o = mlp_offsets(kHidden, C);
   const int nw = kHidden * 6 + kHidden + 4 * C * kHidden + 4 * C;
@@ -90,6 +94,7 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
   if (pair >= static_cast<size_t>(N) * K) return;
   const int j = static_cast<int>(pair % N);
   const int k = static_cast<int>(pair / N);
+  if (n_dev && j >= *n_dev) return;
   const float4 p = geom[3 * k];
   const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
   const float d = sqrtf(vx * vx + vy * vy + vz * vz);
@@ -105,7 +110,8 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
     h[u] = rb(fmaxf(a, 0.0f), bf16);
   }
   const float* gj = glob + static_cast<size_t>(j) * 4 * C;
-  float* dst = out + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * C;
+  float* dst = out + static_cast<size_t>(k) * stride +
+               (col_of ? static_cast<size_t>(col_of[j]) : static_cast<size_t>(j) * 2 * C);
   for (int c = 0; c < C; ++c) {
     float ol[4];
 #pragma unroll
@@ -130,11 +136,11 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
 
 void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float4* geom,
                          const float* base, int K, int stride, float* out, float* glob,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int* n_dev, const int* col_of, bool clear) {
   if (N <= 0 || K <= 0) return;
   // pad columns of every row stay zero
-  cudaMemsetAsync(out, 0, sizeof(float) * static_cast<size_t>(K) * stride, s);
-  mlp_global_kernel<<<N, 128, 0, s>>>(m.p, m.C, m.bf16, rx, glob);
+  if (clear) cudaMemsetAsync(out, 0, sizeof(float) * static_cast<size_t>(K) * stride, s);
+  mlp_global_kernel<<<N, 128, 0, s>>>(m.p, m.C, m.bf16, rx, glob, n_dev);
   note_launches(1);
   const size_t pairs = static_cast<size_t>(N) * K;
   const size_t smem = sizeof(float) * (kHidden * 7 + 4 * m.C * kHidden + 4 * m.C);
@@ -142,7 +148,7 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
     cudaFuncSetAttribute(mlp_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
   mlp_local_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, smem, s>>>(
-      m.p, m.C, m.bf16, rx, N, geom, base, K, stride, glob, out);
+      m.p, m.C, m.bf16, rx, N, geom, base, K, stride, glob, out, n_dev, col_of);
   note_launches(1);
 }
 

@@ -19,7 +19,8 @@ constexpr int kDigits = 256;
 
 __global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, size_t n, int shift,
                                   uint32_t* __restrict__ hist, uint32_t* __restrict__ totals,
-                                  int nblocks) {
+                                  int nblocks, const uint32_t* __restrict__ n_dev) {
+  if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t h[kDigits];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -84,7 +85,9 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ keys_in,
                                      const uint32_t* __restrict__ vals_in, size_t n, int shift,
                                      const uint32_t* __restrict__ offsets, int nblocks,
                                      uint64_t* __restrict__ keys_out,
-                                     uint32_t* __restrict__ vals_out) {
+                                     uint32_t* __restrict__ vals_out,
+                                     const uint32_t* __restrict__ n_dev) {
+  if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t wcnt[kSortWarps][kDigits];
   __shared__ uint32_t gbase[kDigits];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -148,7 +151,8 @@ size_t radix_tmp_words(size_t n) {
 }
 
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s) {
+                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
+                      const uint32_t* n_dev) {
   *result_in_alt = false;
   if (n <= 1 || bits <= 0) return;
   const int nb = static_cast<int>((n + kSortTile - 1) / kSortTile);
@@ -159,11 +163,12 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32
   bool alt = false;
   for (int shift = 0; shift < bits; shift += 8) {
     cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kDigits, s);
-    radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(kin, n, shift, hist, totals, nb);
+    radix_hist_kernel<<<nb, kSortThreads, 0, s>>>(kin, n, shift, hist, totals, nb, n_dev);
     note_launches(1);
     radix_offsets_kernel<<<kDigits, kSortThreads, 0, s>>>(hist, totals, nb);
     note_launches(1);
-    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(kin, vin, n, shift, hist, nb, kout, vout);
+    radix_scatter_kernel<<<nb, kSortThreads, 0, s>>>(kin, vin, n, shift, hist, nb, kout, vout,
+                                                     n_dev);
     note_launches(1);
     uint64_t* tk = kin;
     kin = kout;

@@ -39,8 +39,10 @@ void launch_set_opacity(const float* opacity, int K, float4* geom, cudaStream_t 
 
 // Projection of K Gaussians for M views.  rec[M][K][2] float4, depth[M][K]
 // (float bits of rho), count[M*K] tile counts (0 = culled).
+// nviews_dev (optional): number of view slots in use; later slots are culled.
 void launch_preprocess(const GridConst& g, const float4* geom, int K, const float* tx, int M,
-                       float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s);
+                       float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s,
+                       const int* nviews_dev = nullptr);
 
 // Exclusive scan of n uint32 values; out has n+1 entries (out[n] = total).
 // tmp must hold scan_tmp_words(n) uint32.
@@ -49,20 +51,25 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t
                            cudaStream_t s);
 
 // Writes the (view | tile | depth) keys and Gaussian-index values.
+// A Gaussian whose instances would end beyond `cap` writes nothing and sets
+// kErrCapacity in *err.
 void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
                  const uint32_t* offsets, int K, int M, int tile_bits, uint64_t* keys,
-                 uint32_t* vals, cudaStream_t s);
+                 uint32_t* vals, cudaStream_t s, uint32_t cap = 0xffffffffu,
+                 unsigned* err = nullptr);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
 // Returns, through *result_in_alt, whether the sorted data ended in the alt
 // buffers.  tmp must hold radix_tmp_words(n) uint32.
 size_t radix_tmp_words(size_t n);
+// n_dev (optional): the actual item count, <= n (launch sizes follow n).
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s);
+                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
+                      const uint32_t* n_dev = nullptr);
 
 // ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
 void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
-                        int M, cudaStream_t s);
+                        int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
 
 // ------------------------------------------------------------- radiance (a4)
 // receiver-major [N][K][C][2] -> Gaussian-major [K][stride] (columns
@@ -78,9 +85,12 @@ struct MlpParams {
   int hidden, C, bf16;
 };
 // Radiance from the conditioning MLP: out[K][stride] Gaussian-major.
+// Optional: n_dev = receivers in use (<= N), col_of[j] = first column of
+// receiver j (default j*2C); clear = zero the whole buffer first.
 void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float4* geom,
                          const float* base, int K, int stride, float* out, float* glob_out,
-                         cudaStream_t s);
+                         cudaStream_t s, const int* n_dev = nullptr, const int* col_of = nullptr,
+                         bool clear = true);
 // Backward of the MLP: dS[K][stride] -> grad_base[K][C][2], grad_mlp (flat).
 size_t mlp_backward_tmp_floats(const MlpParams& m, int N, int K);
 void launch_mlp_backward(const MlpParams& m, const float* rx, int N, const float4* geom,

@@ -83,6 +83,7 @@ SIGNATURES = {
     "rxgs_profile": (I, [P, I]),
     "rxgs_profile_read": (I, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
     "rxgs_render_csi_noalloc": (I, [P, U64, P, I, P, P, P]),
+    "rxgs_render_batched": (I, [P, U64, P, I, P, P, P, P, P]),
     "rxgs_sync": (I, [P, P]),
 }
 
@@ -260,6 +261,16 @@ class Context:
     def mlp_numel(C, hidden=64):
         """Number of float32 parameters of the two conditioning MLPs."""
         return hidden * 3 + hidden + 4 * C * hidden + 4 * C + hidden * 6 + hidden + 4 * C * hidden + 4 * C
+
+    def render_batched(self, scene, tx, rx, counts, kind, radiance=None, spectra=None, rssi=None,
+                       csi=None, stream=None):
+        """Ragged batches: tx[B,3], rx[R,3], counts = list of B receiver counts."""
+        cnt = (ctypes.c_int32 * len(counts))(*[int(c) for c in counts])
+        d = RenderDesc(int(kind), _f32(radiance), 0)
+        o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), None, None)
+        self._check(self.lib.rxgs_render_batched(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
+                                                 _f32(rx), cnt, ctypes.byref(d), ctypes.byref(o),
+                                                 _stream(stream)))
 
     def render_csi_noalloc(self, views, radiance, N, csi=None, rssi=None, stream=None):
         """CSI / RSSI of prepared views with no device allocation (the
