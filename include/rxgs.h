@@ -194,6 +194,56 @@ rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, const float* 
                                 const float* rx, const int32_t* rx_counts,
                                 const rxgs_render_desc* desc, rxgs_outputs* out, void* stream);
 
+/* Serving: a request loop that batches (transmitter, receiver set) queries of
+ * different sizes against a device-resident scene (continuous batching).  A
+ * scheduler thread owned by the context admits queued requests in arrival
+ * order into the next free slot while the batch fits the slot's capacity
+ * and the memory budget has room next to the batches already on the GPU,
+ * renders the batch with the batched pipeline on the slot's stream, and
+ * picks the next batch without waiting: with `slots` > 1, batches overlap on
+ * the device.  A request's result does not depend on the batch it lands in
+ * (see rxgs_render_batched).  The scene needs a conditioning MLP.
+ *   kind                 RXGS_OUT_RSSI (C == 1) or RXGS_OUT_CSI
+ *   max_batch_receivers  receivers per batch (a larger request is refused
+ *                        with RXGS_E_ADMISSION at submit)
+ *   max_batch_views      requests per batch
+ *   mem_budget           bytes of estimated device memory all batches in
+ *                        flight may use (a request estimated above it alone
+ *                        is refused with RXGS_E_ADMISSION)
+ *   slots                batches that may be in flight at once (1..8) */
+typedef struct {
+  int kind;
+  int max_batch_receivers;
+  int max_batch_views;
+  size_t mem_budget;
+  int slots;
+} rxgs_serve_options;
+
+void rxgs_serve_default_options(rxgs_serve_options* o);
+rxgs_status rxgs_serve_start(rxgs_ctx* ctx, rxgs_scene_t scene, const rxgs_serve_options* opts);
+/* tx[3] and rx[n,3] are HOST pointers, copied before the call returns. */
+rxgs_status rxgs_serve_submit(rxgs_ctx* ctx, const float* tx, const float* rx, int n,
+                              rxgs_ticket_t* ticket);
+/* Waits up to timeout_us (0 = do not wait, < 0 = forever) for the request;
+ * on RXGS_OK copies its result to the HOST buffer out (n floats for RSSI,
+ * n*C*2 for CSI) and retires the ticket.  RXGS_E_NOT_READY (timeout_us == 0)
+ * and RXGS_E_TIMEOUT keep the ticket; RXGS_E_CANCELLED and RXGS_E_DEVICE
+ * retire it. */
+rxgs_status rxgs_serve_poll(rxgs_ctx* ctx, rxgs_ticket_t ticket, float* out, int timeout_us);
+/* Removes a request that is still queued (RXGS_E_NOT_READY once it is on
+ * the GPU); a later poll returns RXGS_E_CANCELLED. */
+rxgs_status rxgs_serve_cancel(rxgs_ctx* ctx, rxgs_ticket_t ticket);
+/* {"completed", "failed", "retried", "cancelled", "batches",
+ *  "mean_batch_receivers", "p50_ms", "p90_ms", "p99_ms", "max_ms", "mean_ms",
+ *  "queued", "inflight_bytes", "elapsed_s"}; latency = submit to completion. */
+rxgs_status rxgs_serve_stats(rxgs_ctx* ctx, char* json, size_t cap);
+rxgs_status rxgs_serve_reset_stats(rxgs_ctx* ctx);
+/* Failure injection on the host: the next `batches` batches fail before
+ * launch and their requests complete with RXGS_E_DEVICE (no GPU fault). */
+rxgs_status rxgs_serve_inject_fault(rxgs_ctx* ctx, int batches);
+/* Drains the batches in flight, stops the scheduler and frees its state. */
+rxgs_status rxgs_serve_stop(rxgs_ctx* ctx);
+
 /* Backward (App. D): gradients of a loss L given dL/d(outputs).
  *   grad_spectra [M,N,H,W,C,2] or NULL
  *   grad_csi     [M,N,C,2] or NULL   (uniform over pixels)

@@ -39,6 +39,7 @@ struct DescLayout {
 
 struct BatchPlan {
   rxgs_scene_t scene = 0;
+  int tag = 0;  // owner (0 = rxgs_render_batched, >0 = a serving slot)
   int B_max = 0, R_max = 0, C = 0, NB = 64, kind = 0;
   bool mlp = false;
   uint32_t I_cap = 0;
@@ -262,7 +263,8 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   uint64_t* keys = in_alt ? p->keys_alt : p->keys;
   uint32_t* vals = in_alt ? p->vals_alt : p->vals;
   launch_tile_ranges(keys, p->I_cap, p->tile_bits, g.T, p->ranges, p->B_max, st, n_dev);
-  cudaMemsetAsync(p->rad, 0, sizeof(float) * static_cast<size_t>(K) * p->stride, st);
+  // no clearing of the radiance: a column block may read columns past its
+  // view's last one, but those only feed accumulators that are never stored
   if (p->mlp) {
     MlpParams m{s->mlp, s->hidden, C, s->bf16};
     launch_mlp_radiance(m, p->rx, p->R_max, s->geom, s->base, K, p->stride, p->rad, p->glob, st,
@@ -349,9 +351,10 @@ using namespace rxgs;
 // Builds a plan for (scene, kind, radiance mode) holding B views, R
 // receivers and inst_need instances.
 static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState* s, int kind,
-                            bool mlp, int B, int R, uint32_t inst_need, BatchPlan** out) {
+                            bool mlp, int B, int R, uint32_t inst_need, int tag, BatchPlan** out) {
   BatchPlan* p = new BatchPlan();
   p->scene = scene;
+  p->tag = tag;
   p->kind = kind;
   p->mlp = mlp;
   p->C = s->C;
@@ -370,13 +373,36 @@ static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState*
   return RXGS_OK;
 }
 
-static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, int B, int R) {
+// The smallest existing plan that fits, so launch sizes stay within 2x of
+// the batch (plans come in power-of-two size classes of views and receivers).
+static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, int B, int R,
+                            int tag) {
   const int NB = ctx->opts.cols_per_cta ? ctx->opts.cols_per_cta : 64;
+  const int Bc = next_pow2(B, 4), Rc = next_pow2(R, 32);
+  BatchPlan* best = nullptr;
   for (BatchPlan* q : ctx->plans)
-    if (q->scene == scene && q->kind == kind && q->mlp == mlp && q->B_max >= B && q->R_max >= R &&
-        q->g.TH == ctx->g.TH && q->g.TW == ctx->g.TW && q->NB == NB)
-      return q;
-  return nullptr;
+    if (q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp && q->B_max >= B &&
+        q->R_max >= R && q->B_max <= 2 * Bc && q->R_max <= 2 * Rc && q->g.TH == ctx->g.TH &&
+        q->g.TW == ctx->g.TW && q->NB == NB &&
+        (!best || static_cast<size_t>(q->B_max) * q->R_max <
+                      static_cast<size_t>(best->B_max) * best->R_max))
+      best = q;
+  return best;
+}
+
+// Drops the plans of one owner (after a capacity overflow, to grow them).
+void rxgs::drop_plans(rxgs_ctx* ctx, int tag) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::vector<BatchPlan*> keep;
+  for (BatchPlan* q : ctx->plans) {
+    if (q->tag == tag) {
+      cudaDeviceSynchronize();
+      destroy_plan(q);
+    } else {
+      keep.push_back(q);
+    }
+  }
+  ctx->plans.swap(keep);
 }
 
 // Exact instance count of a batch's views (one synchronising readback);
@@ -384,10 +410,11 @@ static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool ml
 static rxgs_status count_instances(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
                                    uint32_t* max_per_view, cudaStream_t st);
 
-extern "C" rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx,
-                                           int B, const float* rx, const int32_t* rx_counts,
-                                           const rxgs_render_desc* d, rxgs_outputs* out,
-                                           void* stream) {
+namespace rxgs {
+rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
+                                  const float* rx, const int32_t* rx_counts,
+                                  const rxgs_render_desc* d, rxgs_outputs* out, void* stream,
+                                  int tag, double inst_margin) {
   if (!ctx || !tx || !rx_counts || !d || !out) return fail(ctx, RXGS_E_INVALID, "null argument");
   if (B <= 0 || B > 4096) return fail(ctx, RXGS_E_INVALID, "B out of range");
   int R = 0;
@@ -418,16 +445,16 @@ extern "C" rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, co
   BatchPlan* p = nullptr;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    p = find_plan(ctx, scene, kind, mlp, B, R);
+    p = find_plan(ctx, scene, kind, mlp, B, R, tag);
   }
   if (!p) {
     uint32_t per_view = 0;
     rxgs_status rs = count_instances(ctx, scene, tx, B, &per_view, st);
     if (rs != RXGS_OK) return rs;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    const uint64_t need = static_cast<uint64_t>(per_view) * next_pow2(B, 4) * 5 / 4 + 4096;
-    if (need > 0x7fffffffull) return fail(ctx, RXGS_E_INVALID, "instance capacity overflow");
-    rs = new_plan(ctx, scene, s, kind, mlp, B, R, static_cast<uint32_t>(need), &p);
+    const double need_d = static_cast<double>(per_view) * next_pow2(B, 4) * inst_margin + 4096.0;
+    if (need_d > 2147483647.0) return fail(ctx, RXGS_E_INVALID, "instance capacity overflow");
+    rs = new_plan(ctx, scene, s, kind, mlp, B, R, static_cast<uint32_t>(need_d), tag, &p);
     if (rs != RXGS_OK) return rs;
   }
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -453,6 +480,14 @@ extern "C" rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, co
   if (kind & RXGS_OUT_RSSI)
     CK(cudaMemcpyAsync(out->rssi, p->rssi, sizeof(float) * R, cudaMemcpyDeviceToDevice, st));
   return RXGS_OK;
+}
+}  // namespace rxgs
+
+extern "C" rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx,
+                                           int B, const float* rx, const int32_t* rx_counts,
+                                           const rxgs_render_desc* d, rxgs_outputs* out,
+                                           void* stream) {
+  return render_batched_tagged(ctx, scene, tx, B, rx, rx_counts, d, out, stream, 0, 1.25);
 }
 
 static rxgs_status count_instances(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,

@@ -151,4 +151,12 @@ struct Stage {
 
 int pick_cols(const rxgs_ctx* ctx, int ncols);
 
+// rxgs_render_batched with a plan owner tag (serving slots own their plans)
+// and the instance-capacity margin over the measured batch.
+rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
+                                  const float* rx, const int32_t* rx_counts,
+                                  const rxgs_render_desc* d, rxgs_outputs* out, void* stream,
+                                  int tag, double inst_margin);
+void drop_plans(rxgs_ctx* ctx, int tag);
+
 }  // namespace rxgs

@@ -51,6 +51,12 @@ class Outputs(ctypes.Structure):
                 ("ncontrib", ctypes.c_void_p), ("tfinal", ctypes.c_void_p)]
 
 
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("max_batch_receivers", ctypes.c_int),
+                ("max_batch_views", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
+                ("slots", ctypes.c_int)]
+
+
 class Cotangents(ctypes.Structure):
     _fields_ = [("grad_spectra", ctypes.c_void_p), ("grad_csi", ctypes.c_void_p),
                 ("grad_rssi", ctypes.c_void_p), ("fwd_csi", ctypes.c_void_p)]
@@ -84,6 +90,15 @@ SIGNATURES = {
     "rxgs_profile_read": (I, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
     "rxgs_render_csi_noalloc": (I, [P, U64, P, I, P, P, P]),
     "rxgs_render_batched": (I, [P, U64, P, I, P, P, P, P, P]),
+    "rxgs_serve_default_options": (None, [P]),
+    "rxgs_serve_start": (I, [P, U64, P]),
+    "rxgs_serve_submit": (I, [P, P, P, I, P]),
+    "rxgs_serve_poll": (I, [P, U64, P, I]),
+    "rxgs_serve_cancel": (I, [P, U64]),
+    "rxgs_serve_stats": (I, [P, ctypes.c_char_p, ctypes.c_size_t]),
+    "rxgs_serve_reset_stats": (I, [P]),
+    "rxgs_serve_inject_fault": (I, [P, I]),
+    "rxgs_serve_stop": (I, [P]),
     "rxgs_sync": (I, [P, P]),
 }
 
@@ -271,6 +286,51 @@ class Context:
         self._check(self.lib.rxgs_render_batched(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                                  _f32(rx), cnt, ctypes.byref(d), ctypes.byref(o),
                                                  _stream(stream)))
+
+    # ------------------------------------------------------------- serving
+    def serve_start(self, scene, kind=OUT_RSSI, max_batch_receivers=4096, max_batch_views=64,
+                    mem_budget=16 << 30, slots=2):
+        o = ServeOptions(int(kind), int(max_batch_receivers), int(max_batch_views),
+                         int(mem_budget), int(slots))
+        self._check(self.lib.rxgs_serve_start(self.h, U64(scene), ctypes.byref(o)))
+
+    def serve_submit(self, tx, rx):
+        """tx: 3 floats, rx: [n,3] float32 numpy array (host).  Returns a ticket."""
+        import numpy as np
+        t = np.ascontiguousarray(tx, dtype=np.float32)
+        r = np.ascontiguousarray(rx, dtype=np.float32).reshape(-1, 3)
+        out = ctypes.c_uint64()
+        self._check(self.lib.rxgs_serve_submit(self.h, t.ctypes.data_as(P), r.ctypes.data_as(P),
+                                               int(r.shape[0]), ctypes.byref(out)))
+        return out.value
+
+    def serve_poll(self, ticket, n_out, timeout_us=-1):
+        """Returns the result (numpy float32, n_out values) or raises RxgsError
+        (E_NOT_READY / E_TIMEOUT keep the ticket)."""
+        import numpy as np
+        out = np.empty(int(n_out), np.float32)
+        st = self.lib.rxgs_serve_poll(self.h, U64(ticket), out.ctypes.data_as(P), int(timeout_us))
+        if st != OK:
+            raise RxgsError(st, self.lib.rxgs_last_error(self.h).decode())
+        return out
+
+    def serve_cancel(self, ticket):
+        self._check(self.lib.rxgs_serve_cancel(self.h, U64(ticket)))
+
+    def serve_stats(self):
+        import json
+        buf = ctypes.create_string_buffer(1024)
+        self._check(self.lib.rxgs_serve_stats(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def serve_reset_stats(self):
+        self._check(self.lib.rxgs_serve_reset_stats(self.h))
+
+    def serve_inject_fault(self, batches=1):
+        self._check(self.lib.rxgs_serve_inject_fault(self.h, int(batches)))
+
+    def serve_stop(self):
+        self._check(self.lib.rxgs_serve_stop(self.h))
 
     def render_csi_noalloc(self, views, radiance, N, csi=None, rssi=None, stream=None):
         """CSI / RSSI of prepared views with no device allocation (the
