@@ -313,6 +313,13 @@ def gpu_bench(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e_ms, 4)}
 
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = serve_bench(torch, rxgs, S, seconds=args.serve_seconds)
+    bcsi = None
+    if rank == 0 and not args.no_batched:
+        bcsi = batched_csi_bench(torch, rxgs, S)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_sample(args.cpu_seconds)
@@ -334,6 +341,8 @@ def gpu_bench(args):
             "dominant_stage": dom,
             "roofline": roof,
             "per_rx_loop": loop,
+            "serve": serve,
+            "batched_csi": bcsi,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -344,8 +353,106 @@ def gpu_bench(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving
+def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=1.5):
+    """300,000 resident Gaussians (MLP radiance), Poisson requests at `rate`
+    per second, each 1 transmitter and n = floor(exp(U(0, ln 1025))) receivers,
+    RSSI out; latency = submit to completion (library-side)."""
+    import threading
+    rng = np.random.default_rng(S.SEED_BASE + 3)
+    sc = S.draw_scene(rng, 300_000)
+    base = S.draw_base(rng, sc.K, 1)
+    mlp = S.draw_mlp(rng, 1)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = rxgs.Context()
+    h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), d(base),
+                         d(S.flatten_mlp(mlp, 1)), C=1)
+    budget = 16 << 30
+    ctx.serve_start(h, kind=rxgs.OUT_RSSI, max_batch_receivers=2048, max_batch_views=16,
+                    mem_budget=budget, slots=2)
+
+    def run(dur, rate_hz):
+        reqs = S.serve_requests(rng, max(1, int(dur * rate_hz)), rate_hz)
+        done = []
+        tickets = []
+        lock = threading.Lock()
+
+        def poller():
+            i = 0
+            while True:
+                with lock:
+                    if i < len(tickets):
+                        tk, n = tickets[i]
+                    elif len(tickets) == len(reqs):
+                        return
+                    else:
+                        tk = None
+                if tk is None:
+                    time.sleep(0.0005)
+                    continue
+                ctx.serve_poll(tk, n, timeout_us=-1)
+                done.append(time.perf_counter())
+                i += 1
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if r["t"] > now:
+                time.sleep(r["t"] - now)
+            tk = ctx.serve_submit(r["tx"], r["rx"])
+            with lock:
+                tickets.append((tk, r["rx"].shape[0]))
+        th.join()
+        wall = time.perf_counter() - t0
+        return len(reqs), sum(r["rx"].shape[0] for r in reqs), wall
+
+    run(warm, rate)                      # plans and graphs for the size classes
+    ctx.serve_reset_stats()
+    nreq, nrx, wall = run(seconds, rate)
+    st = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    return {"offered_rps": rate, "achieved_rps": round(nreq / wall, 2),
+            "receivers_per_s": round(nrx / wall, 1), "requests": nreq,
+            "p50_ms": st["p50_ms"], "p90_ms": st["p90_ms"], "p99_ms": st["p99_ms"],
+            "max_ms": st["max_ms"], "batches": st["batches"],
+            "mean_batch_receivers": st["mean_batch_receivers"], "failed": st["failed"],
+            "mem_budget_bytes": budget, "slots": 2,
+            "workload": "300k Gaussians, MLP radiance, RSSI, Poisson arrivals, n log-uniform 1..1024"}
+
+
+def batched_csi_bench(torch, rxgs, S, reps=3):
+    """300,000 Gaussians, 256 receivers in batches of U{1..64} (one
+    transmitter each), CSI over 52 subcarriers from the bf16 MLP, one
+    persistent render launch per batch set under a CUDA graph."""
+    w = S.workload_csi()
+    sc, C = w["scene"], w["C"]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = rxgs.Context()
+    h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), d(w["base"]),
+                         d(S.flatten_mlp(w["mlp"], C)), C=C, bf16=True)
+    R = int(sum(w["sizes"]))
+    csi = torch.empty((R, C, 2), device="cuda")
+    tx, rx = d(w["tx"]), d(w["rx"])
+    ctx.render_batched(h, tx, rx, w["sizes"], rxgs.OUT_CSI, csi=csi)   # plan + graph capture
+    ctx.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ctx.render_batched(h, tx, rx, w["sizes"], rxgs.OUT_CSI, csi=csi)
+    b.record()
+    ctx.sync()
+    ms = a.elapsed_time(b) / reps
+    ctx.close()
+    return {"receivers": R, "batches": len(w["sizes"]), "subcarriers": C,
+            "ms_per_call": round(ms, 3), "csi_per_s": round(R / (ms / 1e3), 1),
+            "workload": "300k Gaussians, 256 rx in U{1..64} batches, C=52, bf16 MLP, CSI"}
+
+
 # ------------------------------------------------------------ CPU oracle
-def cpu_sample(budget_s=15.0, steps=1, npx=16384):
+def cpu_sample(budget_s=15.0, steps=None, npx=16384):
     """The oracle on a bounded sample of the same workload: one transmitter,
     one receiver, the forward and backward over a random pixel subset (plus
     the MLP radiance and its backward for that receiver); scaled to spectra
@@ -358,18 +465,23 @@ def cpu_sample(budget_s=15.0, steps=1, npx=16384):
     rng = np.random.default_rng(1)
     HW = g.H * g.W
     t_tot, frac_tot = 0.0, 0.0
-    for s in range(steps):
+    n_done = 0
+    for s in range(10_000):
+        if (steps is not None and s >= steps) or (steps is None and t_tot >= budget_s):
+            break
+        n_done += 1
         pix = rng.choice(HW, size=npx, replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        rad = O.mlp_radiance(w["mlp"], w["rx"][s:s + 1], sc.means, w["base"])
-        O.render_pixels(g, sc, w["tx"][s], rad, pix)
+        ti, rj = s % w["tx"].shape[0], s % w["rx"].shape[0]
+        rad = O.mlp_radiance(w["mlp"], w["rx"][rj:rj + 1], sc.means, w["base"])
+        O.render_pixels(g, sc, w["tx"][ti], rad, pix)
         gsp = rng.normal(size=(npx, 1, 1, 2))
-        gr, gt = O.backward_pixels(g, sc, w["tx"][s], rad, pix, gsp)
-        O.mlp_backward(w["mlp"], w["rx"][s:s + 1], sc.means, w["base"], gr)
+        gr, gt = O.backward_pixels(g, sc, w["tx"][ti], rad, pix, gsp)
+        O.mlp_backward(w["mlp"], w["rx"][rj:rj + 1], sc.means, w["base"], gr)
         t_tot += time.perf_counter() - t0
         frac_tot += npx / HW
     return {"value": round(frac_tot / t_tot, 4), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{steps} x (1 tx, 1 rx, {npx} of {HW} pixels) forward+backward incl. MLP; "
+            "sample": f"{n_done} x (1 tx, 1 rx, {npx} of {HW} pixels) forward+backward incl. MLP; "
                       f"scaled by the pixel fraction",
             "seconds": round(t_tot, 2)}
 
@@ -416,6 +528,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -194,6 +194,18 @@ rxgs_status rxgs_render_batched(rxgs_ctx* ctx, rxgs_scene_t scene, const float* 
                                 const float* rx, const int32_t* rx_counts,
                                 const rxgs_render_desc* desc, rxgs_outputs* out, void* stream);
 
+/* Autotuner: renders the given workload (M transmitters x N receivers, as
+ * rxgs_render) with every tile shape in {16x16, 8x32, 32x8} and every
+ * column block in {16, 32, 64, 128} not wider than the work, `iters` times
+ * each after one warm-up, and keeps the fastest pair in the context's
+ * options (used by later calls, including new batch plans).  Writes
+ *   {"candidates": [{"tile": [h, w], "cols": c, "ms": t}, ...],
+ *    "chosen": {...}}
+ * into json[cap] when json != NULL.  Spectra do not depend on the choice. */
+rxgs_status rxgs_autotune(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int M,
+                          const float* rx, int N, const rxgs_render_desc* desc, int iters,
+                          char* json, size_t cap);
+
 /* Serving: a request loop that batches (transmitter, receiver set) queries of
  * different sizes against a device-resident scene (continuous batching).  A
  * scheduler thread owned by the context admits queued requests in arrival

@@ -96,6 +96,11 @@ void launch_uniform_cotangent(const float* gcsi, const float* grssi, const float
 }
 
 namespace rxgs {
+bool make_grid_options(const rxgs_options& o, GridConst* g) {
+  std::string why;
+  return make_grid(o, g, &why);
+}
+
 cudaEvent_t take_event(rxgs_ctx* c) {
   if (!c->event_pool.empty()) {
     cudaEvent_t e = c->event_pool.back();

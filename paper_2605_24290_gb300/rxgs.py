@@ -90,6 +90,7 @@ SIGNATURES = {
     "rxgs_profile_read": (I, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
     "rxgs_render_csi_noalloc": (I, [P, U64, P, I, P, P, P]),
     "rxgs_render_batched": (I, [P, U64, P, I, P, P, P, P, P]),
+    "rxgs_autotune": (I, [P, U64, P, I, P, I, P, I, ctypes.c_char_p, ctypes.c_size_t]),
     "rxgs_serve_default_options": (None, [P]),
     "rxgs_serve_start": (I, [P, U64, P]),
     "rxgs_serve_submit": (I, [P, P, P, I, P]),
@@ -286,6 +287,17 @@ class Context:
         self._check(self.lib.rxgs_render_batched(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                                  _f32(rx), cnt, ctypes.byref(d), ctypes.byref(o),
                                                  _stream(stream)))
+
+    def autotune(self, scene, tx, rx, N, kind, radiance=None, iters=3):
+        """Times tile shapes x column blocks on this workload and keeps the
+        fastest in the context; returns the timings."""
+        import json
+        d = RenderDesc(int(kind), _f32(radiance), 0)
+        buf = ctypes.create_string_buffer(8192)
+        self._check(self.lib.rxgs_autotune(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
+                                           _f32(rx), int(N), ctypes.byref(d), int(iters), buf,
+                                           len(buf)))
+        return json.loads(buf.value.decode())
 
     # ------------------------------------------------------------- serving
     def serve_start(self, scene, kind=OUT_RSSI, max_batch_receivers=4096, max_batch_views=64,

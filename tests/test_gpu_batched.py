@@ -92,3 +92,26 @@ def test_batched_mlp_matches_single_batches_and_oracle(torch, rx, oracle):
         a = o["absacc"].sum(axis=(1, 2))
         assert norm_err(csi[off:off + n].cpu().numpy(), ref, a) <= TOL
         off += n
+
+
+def test_autotune_keeps_spectra(torch, rx):
+    """The autotuner only moves work between CTAs: spectra after tuning are
+    bit-identical to those before."""
+    rng = np.random.default_rng(403)
+    sc = S.draw_scene(rng, 3000)
+    g = S.Grid()
+    ctx = rx.Context(H=g.H, W=g.W)
+    h = upload(ctx, sc, torch)
+    tx = dev(S.draw_points(rng, 2), torch)
+    rad = dev(S.draw_radiance(rng, 6, sc.K, 1), torch)
+    before = torch.zeros((2, 6, g.H, g.W, 1, 2), device="cuda")
+    ctx.render(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, spectra=before)
+    res = ctx.autotune(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, iters=2)
+    assert len(res["candidates"]) >= 6
+    ch = res["chosen"]
+    assert any(c["tile"] == ch["tile"] and c["cols"] == ch["cols"] for c in res["candidates"])
+    after = torch.zeros_like(before)
+    ctx.render(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, spectra=after)
+    ctx.sync()
+    np.testing.assert_array_equal(before.cpu().numpy().view(np.uint32),
+                                  after.cpu().numpy().view(np.uint32))
