@@ -206,15 +206,20 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
       if (bb < nb) {
         for (int it = 0; it < kTilePixels / 8; ++it) {
           const int p = it * 8 + slice;
+          float av[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) av[x] = sA[(bb + x) * kPad + p];
+          // skip 8-pixel groups where these 4 Gaussians weigh nothing
+          if (!__any_sync(0xffffffffu, av[0] != 0.0f || av[1] != 0.0f || av[2] != 0.0f ||
+                                           av[3] != 0.0f))
+            continue;
           const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk]);
           const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk + 4]);
           const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            const float av = sA[(bb + x) * kPad + p];
+          for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[x][c] = fmaf(av, gv[c], acc[x][c]);
-          }
+            for (int c = 0; c < 8; ++c) acc[x][c] = fmaf(av[x], gv[c], acc[x][c]);
         }
       }
 #pragma unroll

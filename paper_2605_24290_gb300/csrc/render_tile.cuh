@@ -104,18 +104,27 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
     }
     cp_async_wait_all();
     const int n_alive = __syncthreads_count(alive);
-    // ---- phase B: acc[p][c] += A[b][p] * s[b][c]
+    // ---- phase B: acc[p][c] += A[b][p] * s[b][c], skipping (Gaussian,
+    // pixel strip) pairs that are zero for the whole warp: most list entries
+    // cover only part of a tile, and stopped pixels contribute nothing.
     for (int b = 0; b < nb; ++b) {
       float av[S::PX];
+      unsigned act = 0;  // warp-uniform: strips with a non-zero weight
 #pragma unroll
-      for (int p = 0; p < S::PX; ++p) av[p] = sA[b * kTilePixels + p * S::PG + pg];
+      for (int p = 0; p < S::PX; ++p) {
+        av[p] = sA[b * kTilePixels + p * S::PG + pg];
+        act |= __any_sync(0xffffffffu, av[p] != 0.0f) ? (1u << p) : 0u;
+      }
+      if (act == 0) continue;
       const float4 b0 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8]);
       const float4 b1 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8 + 4]);
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int p = 0; p < S::PX; ++p)
+        if (act & (1u << p)) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av[p], bv[c], acc[p][c]);
+          for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av[p], bv[c], acc[p][c]);
+        }
     }
     if (n_alive == 0) break;
   }

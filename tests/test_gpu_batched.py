@@ -103,15 +103,15 @@ def test_autotune_keeps_spectra(torch, rx):
     ctx = rx.Context(H=g.H, W=g.W)
     h = upload(ctx, sc, torch)
     tx = dev(S.draw_points(rng, 2), torch)
-    rad = dev(S.draw_radiance(rng, 6, sc.K, 1), torch)
-    before = torch.zeros((2, 6, g.H, g.W, 1, 2), device="cuda")
-    ctx.render(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, spectra=before)
-    res = ctx.autotune(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, iters=2)
+    rad = dev(S.draw_radiance(rng, 24, sc.K, 1), torch)
+    before = torch.zeros((2, 24, g.H, g.W, 1, 2), device="cuda")
+    ctx.render(h, tx, None, 24, rx.OUT_SPECTRA, radiance=rad, spectra=before)
+    res = ctx.autotune(h, tx, None, 24, rx.OUT_SPECTRA, radiance=rad, iters=2)
     assert len(res["candidates"]) >= 6
     ch = res["chosen"]
     assert any(c["tile"] == ch["tile"] and c["cols"] == ch["cols"] for c in res["candidates"])
     after = torch.zeros_like(before)
-    ctx.render(h, tx, None, 6, rx.OUT_SPECTRA, radiance=rad, spectra=after)
+    ctx.render(h, tx, None, 24, rx.OUT_SPECTRA, radiance=rad, spectra=after)
     ctx.sync()
     np.testing.assert_array_equal(before.cpu().numpy().view(np.uint32),
                                   after.cpu().numpy().view(np.uint32))
