@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
   const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
   const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
   if (t == 0) sStop = rg.x;
+  const Strip strip = warp_strip(g, tr, tc, t >> 5);
   float T = 1.0f;
   uint32_t stop = valid ? rg.y : rg.x;
   bool alive = valid;
@@ -68,15 +69,19 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    if (alive) {
-      for (int b = 0; b < nb; ++b) {
+    {
+      const int lane = t & 31;
+      const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
+      unsigned m = __ballot_sync(0xffffffffu, rel);
+      while (alive && m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
         float w, G;
         if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
           T = __fmul_rn(T, __fsub_rn(1.0f, w));
           if (T < g.eps_T) {
             alive = false;
             stop = start + b + 1;
-            break;
           }
         }
       }
@@ -101,6 +106,7 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
   float* sR = sT + kChunk * kPad;                   // [32][32] radiance slice
   float4* sRec = reinterpret_cast<float4*>(sR + kChunk * kBNB);  // [32][2]
   uint32_t* sK = reinterpret_cast<uint32_t*>(sRec + 2 * kChunk);  // [32]
+  __shared__ unsigned sMask[kTilePixels / 32];  // per warp: chunk entries meeting its strip
 
   const RenderArgs& a = A.f;
   const GridConst& g = a.g;
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
   const size_t HW = static_cast<size_t>(g.H) * g.W;
   const size_t pix = static_cast<size_t>(i) * g.W + jj;
   const int twoC = 2 * a.C;
+  const Strip strip = warp_strip(g, tr, tc, t >> 5);
 
   // cotangent of this pixel for the CTA's columns
   float gr[kBNB];
@@ -169,30 +176,39 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    for (int b = nb - 1; b >= 0; --b) {
-      float Tw = 0.0f, dtau = 0.0f;
-      if (start + b < stop) {
-        float w, G;
-        if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
-          float gam = 0.0f;
-          const float4* r4 = reinterpret_cast<const float4*>(&sR[b * kBNB]);
+    {
+      // entries meeting this warp's strip, swept from the back
+      const int lane = t & 31;
+      const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
+      unsigned m = __ballot_sync(0xffffffffu, rel);
+      if (lane == 0) sMask[t >> 5] = m;
+      while (m) {
+        const int b = 31 - __clz(m);
+        m &= ~(1u << b);
+        float Tw = 0.0f, dtau = 0.0f;
+        if (start + b < stop) {
+          float w, G;
+          if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
+            float gam = 0.0f;
+            const float4* r4 = reinterpret_cast<const float4*>(&sR[b * kBNB]);
 #pragma unroll
-          for (int q = 0; q < kBNB / 4; ++q) {
-            const float4 s4 = r4[q];
-            gam = fmaf(gr[4 * q + 0], s4.x, gam);
-            gam = fmaf(gr[4 * q + 1], s4.y, gam);
-            gam = fmaf(gr[4 * q + 2], s4.z, gam);
-            gam = fmaf(gr[4 * q + 3], s4.w, gam);
+            for (int q = 0; q < kBNB / 4; ++q) {
+              const float4 s4 = r4[q];
+              gam = fmaf(gr[4 * q + 0], s4.x, gam);
+              gam = fmaf(gr[4 * q + 1], s4.y, gam);
+              gam = fmaf(gr[4 * q + 2], s4.z, gam);
+              gam = fmaf(gr[4 * q + 3], s4.w, gam);
+            }
+            const float one_m_w = 1.0f - w;
+            T = __fdividef(T, one_m_w);  // transmittance in front of this Gaussian
+            Tw = T * w;
+            dtau = T * (gam - Q) * G;
+            Q = fmaf(w, gam, one_m_w * Q);
           }
-          const float one_m_w = 1.0f - w;
-          T = __fdividef(T, one_m_w);  // transmittance in front of this Gaussian
-          Tw = T * w;
-          dtau = T * (gam - Q) * G;
-          Q = fmaf(w, gam, one_m_w * Q);
         }
+        sA[b * kPad + t] = Tw;
+        sT[b * kPad + t] = dtau;
       }
-      sA[b * kPad + t] = Tw;
-      sT[b * kPad + t] = dtau;
     }
     __syncthreads();
     // dL/ds[b][c] = sum_pixels A[b][p] g[p][c]: 4 x 8 block per thread over the
@@ -205,14 +221,14 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
         for (int c = 0; c < 8; ++c) acc[x][c] = 0.0f;
       if (bb < nb) {
         for (int it = 0; it < kTilePixels / 8; ++it) {
+          // pixels it*8 .. it*8+7 belong to warp it/4, which wrote only the
+          // entries of its mask: skip the group when none of b..b+3 is there
+          const unsigned wm = (sMask[it >> 2] >> bb) & 0xfu;
+          if (!wm) continue;
           const int p = it * 8 + slice;
           float av[4];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) av[x] = sA[(bb + x) * kPad + p];
-          // skip 8-pixel groups where these 4 Gaussians weigh nothing
-          if (!__any_sync(0xffffffffu, av[0] != 0.0f || av[1] != 0.0f || av[2] != 0.0f ||
-                                           av[3] != 0.0f))
-            continue;
+          for (int x = 0; x < 4; ++x) av[x] = (wm >> x) & 1u ? sA[(bb + x) * kPad + p] : 0.0f;
           const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk]);
           const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk + 4]);
           const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
@@ -250,7 +266,8 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
       const int b = t >> 3, part = t & 7;
       float y = 0.0f;
       if (b < nb)
-        for (int it = 0; it < kTilePixels / 8; ++it) y += sT[b * kPad + it * 8 + part];
+        for (int it = 0; it < kTilePixels / 8; ++it)
+          if ((sMask[it >> 2] >> b) & 1u) y += sT[b * kPad + it * 8 + part];
       y += __shfl_xor_sync(0xffffffffu, y, 4);
       y += __shfl_xor_sync(0xffffffffu, y, 2);
       y += __shfl_xor_sync(0xffffffffu, y, 1);

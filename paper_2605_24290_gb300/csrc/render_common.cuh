@@ -49,4 +49,43 @@ __device__ __forceinline__ bool pixel_weight(const GridConst& g, const float4 r0
   return true;
 }
 
+// The pixels of warp `w` of a tile (threads 32w .. 32w+31, row-major over the
+// TH x TW tile) lie in grid rows [r0, r1] and columns [c0, c1].
+struct Strip {
+  int r0, r1, c0, c1;
+};
+
+__device__ __forceinline__ Strip warp_strip(const GridConst& g, int tr, int tc, int w) {
+  Strip s;
+  const int t0 = 32 * w, t1 = t0 + 31;
+  s.r0 = tr * g.TH + t0 / g.TW;
+  s.r1 = tr * g.TH + t1 / g.TW;
+  if (g.TW >= 32) {
+    s.c0 = tc * g.TW + t0 % g.TW;
+    s.c1 = s.c0 + 31;
+  } else {
+    s.c0 = tc * g.TW;
+    s.c1 = s.c0 + g.TW - 1;
+  }
+  if (s.r1 > g.H - 1) s.r1 = g.H - 1;
+  if (s.c1 > g.W - 1) s.c1 = g.W - 1;
+  return s;
+}
+
+// Does a footprint (record word r1: rows i_lo..i_hi, columns j_lo..j_lo+span
+// modulo W) meet the strip?  A superset test: every pixel of the strip that
+// lies in the footprint makes it true.
+__device__ __forceinline__ bool touches_strip(const GridConst& g, const float4 r1, const Strip& s) {
+  if (s.r0 > s.r1 || s.c0 > s.c1) return false;
+  const int rows = __float_as_int(r1.z), cols = __float_as_int(r1.w);
+  const int i_lo = rows & 0xffff, i_hi = rows >> 16, j_lo = cols & 0xffff, span = cols >> 16;
+  if (i_hi < s.r0 || i_lo > s.r1) return false;
+  int a = s.c0 - j_lo;
+  if (a < 0) a += g.W;
+  if (a <= span) return true;
+  int b = j_lo - s.c0;
+  if (b < 0) b += g.W;
+  return b <= s.c1 - s.c0;
+}
+
 }  // namespace rxgs

@@ -53,6 +53,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
   const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
   const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
   const float* radv = a.rad + job.col_base;
+  __shared__ unsigned sMask[kTilePixels / 32];  // per warp: chunk entries meeting its strip
 
   const int pg = t % S::PG, cg = t / S::PG;
   float acc[S::PX][8];
@@ -88,43 +89,94 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
     cp_async_commit();
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // records landed
     __syncthreads();
-    // ---- phase A: transmittance-weighted alphas, one pixel per thread
-    for (int b = 0; b < nb; ++b) {
-      float Tw = 0.0f;
-      if (alive) {
-        float w, G;
-        if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
-          Tw = __fmul_rn(T, w);
-          T = __fmul_rn(T, __fsub_rn(1.0f, w));
+    // ---- phase A: transmittance-weighted alphas, one pixel per thread.
+    // Each warp first marks the chunk's Gaussians whose footprint meets its
+    // pixel strip (one Gaussian per lane, then a ballot) and walks only
+    // those, two at a time: their weights are independent, only the T
+    // updates are sequential, in list order.
+    {
+      const Strip strip = warp_strip(g, tr, tc, t >> 5);
+      const int lane = t & 31;
+      const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
+      const unsigned mask = __ballot_sync(0xffffffffu, rel);
+      if (lane == 0) sMask[t >> 5] = mask;
+      unsigned m = __any_sync(0xffffffffu, alive) ? mask : 0u;
+      // Gaussians of the mask that this warp skips (no pixel alive) still
+      // need a zero weight for phase B
+      if (!m) {
+        unsigned z = mask;
+        while (z) {
+          const int b = __ffs(z) - 1;
+          z &= z - 1;
+          sA[b * kTilePixels + t] = 0.0f;
+        }
+      }
+      while (m) {
+        const int b0 = __ffs(m) - 1;
+        m &= m - 1;
+        const int b1 = m ? __ffs(m) - 1 : -1;
+        if (b1 >= 0) m &= m - 1;
+        float w0 = 0.0f, w1 = 0.0f, G;
+        bool c0 = false, c1 = false;
+        if (alive) {
+          c0 = pixel_weight(g, sRec[2 * b0], sRec[2 * b0 + 1], i, jj, fi, fj, &w0, &G);
+          if (b1 >= 0) c1 = pixel_weight(g, sRec[2 * b1], sRec[2 * b1 + 1], i, jj, fi, fj, &w1, &G);
+        }
+        float Tw0 = 0.0f, Tw1 = 0.0f;
+        if (alive && c0) {
+          Tw0 = __fmul_rn(T, w0);
+          T = __fmul_rn(T, __fsub_rn(1.0f, w0));
           ++ncon;
           if (T < g.eps_T) alive = false;
         }
+        if (alive && c1) {
+          Tw1 = __fmul_rn(T, w1);
+          T = __fmul_rn(T, __fsub_rn(1.0f, w1));
+          ++ncon;
+          if (T < g.eps_T) alive = false;
+        }
+        sA[b0 * kTilePixels + t] = Tw0;
+        if (b1 >= 0) sA[b1 * kTilePixels + t] = Tw1;
       }
-      sA[b * kTilePixels + t] = Tw;
     }
     cp_async_wait_all();
     const int n_alive = __syncthreads_count(alive);
-    // ---- phase B: acc[p][c] += A[b][p] * s[b][c], skipping (Gaussian,
-    // pixel strip) pairs that are zero for the whole warp: most list entries
-    // cover only part of a tile, and stopped pixels contribute nothing.
-    for (int b = 0; b < nb; ++b) {
-      float av[S::PX];
-      unsigned act = 0;  // warp-uniform: strips with a non-zero weight
+    // ---- phase B: acc[p][c] += A[b][p] * s[b][c] over the (Gaussian, pixel
+    // strip) pairs marked in phase A; pixel group p of this thread lies in
+    // the strip(s) of warps [p*PG/32, (p+1)*PG/32).
+    {
+      // pmask: union over the warps of group p (uniform, for skipping);
+      // own: the mask of the warp that wrote this thread's pixel of group p
+      // (entries outside it were not written this chunk and weigh zero)
+      unsigned pmask[S::PX], own[S::PX];
+      unsigned any = 0;
 #pragma unroll
       for (int p = 0; p < S::PX; ++p) {
-        av[p] = sA[b * kTilePixels + p * S::PG + pg];
-        act |= __any_sync(0xffffffffu, av[p] != 0.0f) ? (1u << p) : 0u;
-      }
-      if (act == 0) continue;
-      const float4 b0 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8 + 4]);
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        unsigned mm = 0;
+        if (S::PG >= 32) {
 #pragma unroll
-      for (int p = 0; p < S::PX; ++p)
-        if (act & (1u << p)) {
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av[p], bv[c], acc[p][c]);
+          for (int q = 0; q < S::PG / 32; ++q) mm |= sMask[p * (S::PG / 32) + q];
+        } else {
+          mm = sMask[(p * S::PG) / 32];
         }
+        pmask[p] = mm;
+        own[p] = sMask[(p * S::PG + pg) >> 5];
+        any |= mm;
+      }
+      while (any) {
+        const int b = __ffs(any) - 1;
+        any &= any - 1;
+        const float4 b0 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8 + 4]);
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int p = 0; p < S::PX; ++p)
+          if (pmask[p] & (1u << b)) {
+            const float av = (own[p] & (1u << b)) ? sA[b * kTilePixels + p * S::PG + pg] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av, bv[c], acc[p][c]);
+          }
+      }
     }
     if (n_alive == 0) break;
   }
