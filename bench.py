@@ -191,6 +191,11 @@ def gpu_bench(args):
     dev = torch.device("cuda", local)
     W = Workload(torch, rxgs, S, dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    tune = None
+    if not args.no_tune:
+        # the project's autotuner picks tile shape and columns per CTA on
+        # this workload (forward pass); the choice stays in the context
+        tune = W.ctx.autotune(W.scene, W.tx, W.rx, W.N, W.kind, iters=2)
 
     def barrier():
         if world > 1:
@@ -331,14 +336,16 @@ def gpu_bench(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; indoor-room scene recipe)",
             "config": {"workload": WORKLOAD, "gaussians": W.K, "transmitters": W.M,
-                       "receivers": W.N, "grid": [W.g.H, W.g.W], "tile": [16, 16],
+                       "receivers": W.N, "grid": [W.g.H, W.g.W],
                        "spectra_per_step": spectra_per_step,
+                       "tile_autotuned": tune["chosen"] if tune else None,
                        "step": "prepare + MLP + forward (spectra, CSI, RSSI) + backward",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "wall_s": round(wall, 3),
             "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
             "dominant_stage": dom,
+            "autotune": tune,
             "roofline": roof,
             "per_rx_loop": loop,
             "serve": serve,
@@ -529,6 +536,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()

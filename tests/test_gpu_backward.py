@@ -170,8 +170,9 @@ def test_autograd_function_matches_abi(torch, rx):
     ctx.render_backward(views, None, 8, rx.OUT_SPECTRA, radiance=rad.detach(), grad_spectra=gs,
                         grad_radiance=d_rad, grad_opacity=d_tau)
     ctx.sync()
-    torch.testing.assert_close(rad.grad, d_rad, rtol=1e-5, atol=1e-6)
-    torch.testing.assert_close(op.grad, d_tau, rtol=1e-5, atol=1e-5)
+    # both runs accumulate with float atomics, so only the rounding order differs
+    torch.testing.assert_close(rad.grad, d_rad, rtol=1e-4, atol=1e-5)
+    torch.testing.assert_close(op.grad, d_tau, rtol=1e-4, atol=1e-4)
 
 
 def test_directional_finite_differences_on_gpu(torch, rx):
