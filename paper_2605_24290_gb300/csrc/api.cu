@@ -502,6 +502,54 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const GridConst& g = ctx->g;
+  if (d->reduce_path == 1) {
+    // CSI / RSSI through visibility weights (Eq. render_reorder)
+    if (kind & RXGS_OUT_SPECTRA)
+      return fail(ctx, RXGS_E_INVALID, "reduce_path 1 gives CSI / RSSI only, not spectra");
+    if (d->radiance && !weighted_sum_supported(s->C))
+      return fail(ctx, RXGS_E_INVALID, "reduce_path 1 with explicit radiance needs 2C to divide 256");
+    if (!d->radiance && !s->mlp)
+      return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
+    if (!d->radiance && s->C > 52) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 supports C <= 52");
+    float *W = nullptr, *tmp = nullptr, *glob = nullptr, *csi_t = nullptr;
+    const size_t ntmp = d->radiance ? weighted_sum_tmp_floats(v->M, s->K, N, s->C)
+                                    : mlp_weighted_tmp_floats(v->M, s->K, N, s->C);
+    cudaError_t e = dalloc(&W, static_cast<size_t>(v->M) * s->K, st);
+    if (e == cudaSuccess) e = dalloc(&tmp, ntmp, st);
+    if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * s->C, st);
+    float* csi = (kind & RXGS_OUT_CSI) ? out->csi : nullptr;
+    if (e == cudaSuccess && !csi) e = dalloc(&csi_t, static_cast<size_t>(v->M) * N * 2 * s->C, st);
+    if (e != cudaSuccess) {
+      dfree(W, st); dfree(tmp, st); dfree(glob, st); dfree(csi_t, st);
+      return fail(ctx, RXGS_E_OOM, "render (visibility): %s", cudaGetErrorString(e));
+    }
+    if (!csi) csi = csi_t;
+    RenderArgs a{};
+    a.g = g;
+    a.rec = v->rec;
+    a.vals = v->vals;
+    a.ranges = v->ranges;
+    a.K = s->K;
+    a.M = v->M;
+    {
+      Stage sg(ctx, "visibility", st);
+      launch_visibility(a, W, st);
+    }
+    float* rssi = (kind & RXGS_OUT_RSSI) ? out->rssi : nullptr;
+    if (d->radiance) {
+      Stage sg(ctx, "weighted_sum", st);
+      launch_weighted_sum(d->radiance, N, s->K, s->C, W, v->M, tmp, csi, rssi, st);
+    } else {
+      Stage sg(ctx, "mlp_weighted", st);
+      MlpParams m{s->mlp, s->hidden, s->C, s->bf16};
+      launch_mlp_global(m, rx, N, glob, st);
+      launch_mlp_weighted(m, rx, N, s->geom, s->base, s->K, W, v->M, nullptr, glob, tmp, csi, rssi,
+                          nullptr, st);
+    }
+    rxgs_status rs = check_last(ctx, "render (visibility)");
+    dfree(W, st); dfree(tmp, st); dfree(glob, st); dfree(csi_t, st);
+    return rs;
+  }
   const int ncols = 2 * N * s->C;
   const int stride = round_up(ncols, 128);
   float* rad = nullptr;

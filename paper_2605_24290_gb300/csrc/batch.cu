@@ -42,6 +42,9 @@ struct BatchPlan {
   int tag = 0;  // owner (0 = rxgs_render_batched, >0 = a serving slot)
   int B_max = 0, R_max = 0, C = 0, NB = 64, kind = 0;
   bool mlp = false;
+  bool vis = false;  // CSI / RSSI through visibility weights (MLP radiance)
+  float* W = nullptr;       // [B_max][K]
+  float* wtmp = nullptr;    // chunk partial sums
   uint32_t I_cap = 0;
   int cols_cap = 0, stride = 0;
   int tile_bits = 0, view_bits = 0;
@@ -74,7 +77,7 @@ void destroy_plan(BatchPlan* p) {
   void* bufs[] = {p->tx, p->rx, p->rad_in, p->rad, p->glob, p->desc, p->rec, p->depth,
                   p->counts, p->offsets, p->scan_tmp, p->keys, p->keys_alt, p->vals,
                   p->vals_alt, p->sort_tmp, p->ranges, p->partial, p->spectra, p->csi,
-                  p->rssi, p->counter};
+                  p->rssi, p->counter, p->W, p->wtmp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_desc) cudaFreeHost(p->h_desc);
@@ -228,8 +231,13 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   A(&p->vals_alt, p->I_cap);
   A(&p->sort_tmp, radix_tmp_words(p->I_cap));
   A(&p->ranges, static_cast<size_t>(p->B_max) * g.T);
-  A(&p->rad, static_cast<size_t>(K) * p->stride);
-  A(&p->partial, static_cast<size_t>(g.T) * p->cols_cap);
+  if (p->vis) {
+    A(&p->W, static_cast<size_t>(p->B_max) * K);
+    A(&p->wtmp, mlp_weighted_tmp_floats(1, K, p->R_max, C));
+  } else {
+    A(&p->rad, static_cast<size_t>(K) * p->stride);
+    A(&p->partial, static_cast<size_t>(g.T) * p->cols_cap);
+  }
   A(&p->counter, 1);
   if (p->mlp)
     A(&p->glob, static_cast<size_t>(p->R_max) * 4 * C);
@@ -263,6 +271,28 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   uint64_t* keys = in_alt ? p->keys_alt : p->keys;
   uint32_t* vals = in_alt ? p->vals_alt : p->vals;
   launch_tile_ranges(keys, p->I_cap, p->tile_bits, g.T, p->ranges, p->B_max, st, n_dev);
+  if (p->vis) {
+    // CSI / RSSI = sum_k W[v(j)][k] s(j, k): one receiver-independent pass
+    // per view, then the MLP evaluated only where the weight is non-zero
+    RenderArgs va{};
+    va.g = g;
+    va.rec = p->rec;
+    va.vals = in_alt ? p->vals_alt : p->vals;
+    va.ranges = p->ranges;
+    va.K = K;
+    va.M = p->B_max;
+    launch_visibility(va, p->W, st);
+    MlpParams m{s->mlp, s->hidden, C, s->bf16};
+    launch_mlp_global(m, p->rx, p->R_max, p->glob, st, p->desc + 1);
+    launch_mlp_weighted(m, p->rx, p->R_max, s->geom, s->base, K, p->W, p->B_max,
+                        p->desc + p->L.rx_view(), p->glob, p->wtmp, p->csi,
+                        C == 1 ? p->rssi : nullptr, p->desc + 1, st);
+    e = cudaStreamEndCapture(st, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, RXGS_E_CUDA, "graph: %s", cudaGetErrorString(e));
+    return RXGS_OK;
+  }
   // no clearing of the radiance: a column block may read columns past its
   // view's last one, but those only feed accumulators that are never stored
   if (p->mlp) {
@@ -351,10 +381,12 @@ using namespace rxgs;
 // Builds a plan for (scene, kind, radiance mode) holding B views, R
 // receivers and inst_need instances.
 static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState* s, int kind,
-                            bool mlp, int B, int R, uint32_t inst_need, int tag, BatchPlan** out) {
+                            bool mlp, bool vis, int B, int R, uint32_t inst_need, int tag,
+                            BatchPlan** out) {
   BatchPlan* p = new BatchPlan();
   p->scene = scene;
   p->tag = tag;
+  p->vis = vis;
   p->kind = kind;
   p->mlp = mlp;
   p->C = s->C;
@@ -375,14 +407,15 @@ static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState*
 
 // The smallest existing plan that fits, so launch sizes stay within 2x of
 // the batch (plans come in power-of-two size classes of views and receivers).
-static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, int B, int R,
-                            int tag) {
+static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, bool vis, int B,
+                            int R, int tag) {
   const int NB = ctx->opts.cols_per_cta ? ctx->opts.cols_per_cta : 64;
   const int Bc = next_pow2(B, 4), Rc = next_pow2(R, 32);
   BatchPlan* best = nullptr;
   for (BatchPlan* q : ctx->plans)
-    if (q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp && q->B_max >= B &&
-        q->R_max >= R && q->B_max <= 2 * Bc && q->R_max <= 2 * Rc && q->g.TH == ctx->g.TH &&
+    if (q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp && q->vis == vis &&
+        q->B_max >= B && q->R_max >= R && q->B_max <= 2 * Bc && q->R_max <= 2 * Rc &&
+        q->g.TH == ctx->g.TH &&
         q->g.TW == ctx->g.TW && q->NB == NB &&
         (!best || static_cast<size_t>(q->B_max) * q->R_max <
                       static_cast<size_t>(best->B_max) * best->R_max))
@@ -442,10 +475,14 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
   CK(cudaSetDevice(ctx->device));
   // size a plan: reuse one that fits, else measure this batch's instances
   const bool mlp = d->radiance == nullptr;
+  const bool vis = d->reduce_path == 1;
+  if (vis && (!mlp || (kind & RXGS_OUT_SPECTRA) || s->C > 52))
+    return fail(ctx, RXGS_E_INVALID,
+                "batched reduce_path 1 needs MLP radiance, CSI/RSSI only and C <= 52");
   BatchPlan* p = nullptr;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    p = find_plan(ctx, scene, kind, mlp, B, R, tag);
+    p = find_plan(ctx, scene, kind, mlp, vis, B, R, tag);
   }
   if (!p) {
     uint32_t per_view = 0;
@@ -454,7 +491,7 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
     std::lock_guard<std::mutex> lk(ctx->mu);
     const double need_d = static_cast<double>(per_view) * next_pow2(B, 4) * inst_margin + 4096.0;
     if (need_d > 2147483647.0) return fail(ctx, RXGS_E_INVALID, "instance capacity overflow");
-    rs = new_plan(ctx, scene, s, kind, mlp, B, R, static_cast<uint32_t>(need_d), tag, &p);
+    rs = new_plan(ctx, scene, s, kind, mlp, vis, B, R, static_cast<uint32_t>(need_d), tag, &p);
     if (rs != RXGS_OK) return rs;
   }
   std::lock_guard<std::mutex> lk(ctx->mu);

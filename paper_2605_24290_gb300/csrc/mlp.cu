@@ -134,6 +134,13 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
   }
 }
 
+void launch_mlp_global(const MlpParams& m, const float* rx, int N, float* glob, cudaStream_t s,
+                       const int* n_dev) {
+  if (N <= 0) return;
+  mlp_global_kernel<<<N, 128, 0, s>>>(m.p, m.C, m.bf16, rx, glob, n_dev);
+  note_launches(1);
+}
+
 void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float4* geom,
                          const float* base, int K, int stride, float* out, float* glob,
                          cudaStream_t s, const int* n_dev, const int* col_of, bool clear) {

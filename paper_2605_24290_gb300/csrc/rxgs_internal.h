@@ -132,6 +132,28 @@ struct BackwardArgs {
 };
 void launch_render_bwd(const BackwardArgs& a, int cols_per_cta, cudaStream_t s);
 
+// ------------------------------------------ visibility weights (Eq. render_reorder)
+// W[M][K] = sum over each view's pixels of T_k w_k (zeroed first).
+void launch_visibility(const RenderArgs& a, float* W, cudaStream_t s);
+// csi[M][N][C][2] (and rssi[M][N] when C == 1) = sum_k W[v][k] rad[j][k][:],
+// rad receiver-major [N][K][C][2].  Needs 256 % (2C) == 0.
+bool weighted_sum_supported(int C);
+size_t weighted_sum_tmp_floats(int M, int K, int N, int C);
+void launch_weighted_sum(const float* rad, int N, int K, int C, const float* W, int M, float* tmp,
+                         float* csi, float* rssi, cudaStream_t s);
+// The same with the radiance from the conditioning MLP, evaluated on the fly
+// (never stored) and only where the weight is non-zero.  rx_view == NULL:
+// every receiver with every view, outputs [M][N][C][2]; otherwise receiver j
+// with view rx_view[j] only, outputs [N][C][2].  C <= 52.
+size_t mlp_weighted_tmp_floats(int M, int K, int N, int C);
+void launch_mlp_weighted(const MlpParams& m, const float* rx, int N, const float4* geom,
+                         const float* base, int K, const float* W, int M, const int* rx_view,
+                         const float* glob, float* tmp, float* csi, float* rssi,
+                         const int* n_dev, cudaStream_t s);
+// glob[N][4C] = global MLP branch of every receiver (n_dev optional).
+void launch_mlp_global(const MlpParams& m, const float* rx, int N, float* glob, cudaStream_t s,
+                       const int* n_dev = nullptr);
+
 // Read-only view of a context's prepared transmitter-side state, for entry
 // points that live outside api.cu.  Returns false for an unknown handle.
 struct ViewsRef {

@@ -71,10 +71,12 @@ struct ServeState {
 };
 
 static size_t estimate_bytes(const ServeState& s, int n) {
-  // radiance columns + per-tile partial sums per receiver, plus a view's
-  // projected records and (Gaussian, tile) instances
-  const size_t per_rx = static_cast<size_t>(s.K) * 2 * s.C * 4 + 138ull * 2 * s.C * 4;
-  const size_t per_view = static_cast<size_t>(s.K) * (32 + 12 + 3 * 2 * 12);
+  // batches run the visibility path: per receiver its position, output and
+  // per-chunk partial sums; per request (view) its projected records, tile
+  // counts and offsets, (Gaussian, tile) instances with sort buffers (about
+  // four tiles per Gaussian, keys and values twice) and its weights W
+  const size_t per_rx = (static_cast<size_t>(s.K) / 4096 + 2) * 2 * s.C * 4 + 64;
+  const size_t per_view = static_cast<size_t>(s.K) * (32 + 12 + 4 + 4 * 2 * 12);
   return static_cast<size_t>(n) * per_rx + per_view;
 }
 
@@ -189,6 +191,7 @@ static void worker_main(ServeState* S) {
     if (!inject) {
       rxgs_render_desc d{};
       d.kind = S->o.kind;
+      d.reduce_path = 1;  // CSI / RSSI through visibility weights
       rxgs_outputs out{};
       if (S->o.kind == RXGS_OUT_RSSI)
         out.rssi = sl.d_out;

@@ -279,10 +279,13 @@ class Context:
         return hidden * 3 + hidden + 4 * C * hidden + 4 * C + hidden * 6 + hidden + 4 * C * hidden + 4 * C
 
     def render_batched(self, scene, tx, rx, counts, kind, radiance=None, spectra=None, rssi=None,
-                       csi=None, stream=None):
-        """Ragged batches: tx[B,3], rx[R,3], counts = list of B receiver counts."""
+                       csi=None, reduce_path=None, stream=None):
+        """Ragged batches: tx[B,3], rx[R,3], counts = list of B receiver counts.
+        reduce_path defaults to the visibility path for CSI/RSSI-only MLP renders."""
         cnt = (ctypes.c_int32 * len(counts))(*[int(c) for c in counts])
-        d = RenderDesc(int(kind), _f32(radiance), 0)
+        if reduce_path is None:
+            reduce_path = 1 if (radiance is None and not (kind & OUT_SPECTRA)) else 0
+        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path))
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), None, None)
         self._check(self.lib.rxgs_render_batched(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                                  _f32(rx), cnt, ctypes.byref(d), ctypes.byref(o),

@@ -78,7 +78,8 @@ def test_batched_mlp_matches_single_batches_and_oracle(torch, rx, oracle):
     kind = rx.OUT_CSI | rx.OUT_RSSI
     csi = torch.zeros((R, C, 2), device="cuda")
     rssi = torch.zeros((R,), device="cuda")
-    ctx.render_batched(h, dev(tx, torch), dev(rxp, torch), counts, kind, csi=csi, rssi=rssi)
+    ctx.render_batched(h, dev(tx, torch), dev(rxp, torch), counts, kind, csi=csi, rssi=rssi,
+                       reduce_path=0)
     ctx.sync()
     off = 0
     for b, n in enumerate(counts):

@@ -38,12 +38,14 @@ def make_server(torch, rx, K=3000, C=1, seed=501):
 
 
 def alone(ctx, rx, torch, h, tx, rxp, kind, C):
+    """The request rendered on its own through per-pixel compositing."""
     n = rxp.shape[0]
     csi = torch.zeros((1, n, C, 2), device="cuda")
     rssi = torch.zeros((1, n), device="cuda") if C == 1 else None
-    ctx.render(h, dev(tx[None], torch), dev(rxp, torch), n, kind, csi=csi, rssi=rssi)
+    ctx.render(h, dev(tx[None], torch), dev(rxp, torch), n, kind | rx.OUT_CSI, csi=csi, rssi=rssi)
     ctx.sync()
-    return (rssi[0] if kind == rx.OUT_RSSI else csi[0]).cpu().numpy().reshape(-1)
+    out = (rssi[0] if kind == rx.OUT_RSSI else csi[0]).cpu().numpy().reshape(-1)
+    return out
 
 
 @pytest.mark.parametrize("C,kind_name", [(1, "OUT_RSSI"), (2, "OUT_CSI")])
@@ -71,9 +73,13 @@ def test_each_result_equals_the_request_alone(torch, rx, C, kind_name):
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["batches"] < len(reqs)            # requests were batched together
     ctx.serve_stop()
+    # batches go through the visibility path (W accumulated with atomics),
+    # the reference through per-pixel compositing: equal within a relative
+    # 1e-4 of the request's largest output magnitude
     for (tx, rxp), got in zip(reqs, results):
         ref = alone(ctx, rx, torch, h, tx, rxp, kind, C)
-        np.testing.assert_array_equal(got, ref)
+        scale = np.abs(ref).max() + 1e-30
+        assert float(np.abs(got - ref).max()) <= 1e-4 * scale
 
 
 def test_admission_cancel_timeout_and_fault(torch, rx):
