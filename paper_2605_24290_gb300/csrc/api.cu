@@ -15,7 +15,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rxgs.h"
+#include "rxgs.h"
 #include "ctx_internal.h"
 #include "rxgs_internal.h"
 

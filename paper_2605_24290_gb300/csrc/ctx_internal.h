@@ -15,7 +15,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/rxgs.h"
+#include "rxgs.h"
 #include "rxgs_internal.h"
 
 namespace rxgs {

@@ -19,7 +19,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/rxgs.h"
+#include "rxgs.h"
 #include "render_common.cuh"
 #include "rxgs_internal.h"
 
