@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kTilePixels, NB >= 128 ? 1 : 2)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sA = reinterpret_cast<float*>(smem_raw);
   float* sR = sA + kChunk * kTilePixels;
-  float4* sRec = reinterpret_cast<float4*>(sR + kChunk * NB);
+  float4* sRec = reinterpret_cast<float4*>(sR + 2 * kChunk * NB);
   __shared__ float sRed[kTilePixels / 32][8];
   __shared__ int sJob;
   const int nviews = desc[0];
@@ -172,8 +172,7 @@ __global__ void batch_reduce_kernel(const float* __restrict__ partial, int T, in
 template <int NB>
 static void launch_batch_render(const RenderArgs& a, const int* desc, const DescLayout& L,
                                 unsigned* counter, int cols_cap, cudaStream_t s) {
-  constexpr size_t smem = sizeof(float) * (kChunk * kTilePixels + kChunk * NB) +
-                          sizeof(float4) * 2 * kChunk;
+  constexpr size_t smem = FwdShape<NB>::smem;
   cudaFuncSetAttribute(batch_render_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(smem));
   int dev = 0, sms = 152, per_sm = 1;

@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
       const int lane = t & 31;
       const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
-      if (lane == 0) sMask[t >> 5] = m;
+      // no pixel of the strip reaches this chunk: nothing to do here
+      if (!__any_sync(0xffffffffu, start < stop)) m = 0;
+      unsigned used = 0;  // entries with a non-zero weight somewhere in the strip
       while (m) {
         const int b = 31 - __clz(m);
         m &= ~(1u << b);
@@ -208,7 +210,9 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
         }
         sA[b * kPad + t] = Tw;
         sT[b * kPad + t] = dtau;
+        if (__any_sync(0xffffffffu, Tw != 0.0f)) used |= 1u << b;
       }
+      if (lane == 0) sMask[t >> 5] = used;
     }
     __syncthreads();
     // dL/ds[b][c] = sum_pixels A[b][p] g[p][c]: 4 x 8 block per thread over the

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(kTilePixels, NB >= 128 ? 1 : 2)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sA = reinterpret_cast<float*>(smem_raw);              // [kChunk][256]
   float* sR = sA + kChunk * kTilePixels;                        // [kChunk][NB]
-  float4* sRec = reinterpret_cast<float4*>(sR + kChunk * NB);   // [kChunk][2]
+  float4* sRec = reinterpret_cast<float4*>(sR + 2 * kChunk * NB);  // [2][kChunk][2]
   __shared__ float sRed[kTilePixels / 32][8];
   TileJob job;
   job.v = blockIdx.z;

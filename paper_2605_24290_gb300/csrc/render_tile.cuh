@@ -25,8 +25,8 @@ struct FwdShape {
   static constexpr int CG = NB / 8;               // column groups (8 columns each)
   static constexpr int PG = kTilePixels / CG;     // pixel groups
   static constexpr int PX = kTilePixels / PG;     // pixels per thread (= NB/8)
-  static constexpr size_t smem = sizeof(float) * (kChunk * kTilePixels + kChunk * NB) +
-                                 sizeof(float4) * 2 * kChunk;
+  static constexpr size_t smem = sizeof(float) * (kChunk * kTilePixels + 2 * kChunk * NB) +
+                                 sizeof(float4) * 2 * 2 * kChunk;
 };
 
 // One (view, tile, column block) of the compositing.  The column block
@@ -65,30 +65,43 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
   float T = 1.0f;
   bool alive = valid;
   int ncon = 0;
-  for (uint32_t start = rg.x; start < rg.y; start += kChunk) {
+  // Chunks are double-buffered: while chunk c is composited, the records
+  // and radiance rows of chunk c + 1 are already in flight (cp.async).
+  auto stage = [&](uint32_t start, int buf) {
     const int nb = min(kChunk, static_cast<int>(rg.y - start));
-    __syncthreads();
+    float4* rb = sRec + buf * 2 * kChunk;
+    float* rr = sR + buf * kChunk * NB;
     if (t < kChunk) {
       const bool ok = t < nb;
       const uint32_t k = ok ? a.vals[start + t] : 0u;
       // geometry record (2 x 16 B) and the NB-column radiance slice of row k
-      cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
-      cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
+      cp_async16(&rb[2 * t + 0], &rec[2 * k + 0], ok);
+      cp_async16(&rb[2 * t + 1], &rec[2 * k + 1], ok);
+    }
+    constexpr int Q = NB / 4;  // float4 per row slice
+    for (int e = t; e < kChunk * Q; e += kTilePixels) {
+      const int b = e / Q, q4 = e % Q;
+      const bool ok = b < nb;
+      const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
+      cp_async16(&rr[b * NB + 4 * q4], radv + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
+                 ok);
     }
     cp_async_commit();
-    {
-      constexpr int Q = NB / 4;  // float4 per row slice
-      for (int e = t; e < kChunk * Q; e += kTilePixels) {
-        const int b = e / Q, q4 = e % Q;
-        const bool ok = b < nb;
-        const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
-        cp_async16(&sR[b * NB + 4 * q4], radv + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
-                   ok);
-      }
+  };
+  if (rg.x < rg.y) stage(rg.x, 0);
+  int buf = 0;
+  for (uint32_t start = rg.x; start < rg.y; start += kChunk, buf ^= 1) {
+    const int nb = min(kChunk, static_cast<int>(rg.y - start));
+    __syncthreads();  // everyone is done with the buffer the prefetch overwrites
+    if (start + kChunk < rg.y) {
+      stage(start + kChunk, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this chunk landed
+    } else {
+      cp_async_wait_all();
     }
-    cp_async_commit();
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // records landed
     __syncthreads();
+    const float4* sRecC = sRec + buf * 2 * kChunk;
+    const float* sRC = sR + buf * kChunk * NB;
     // ---- phase A: transmittance-weighted alphas, one pixel per thread.
     // Each warp first marks the chunk's Gaussians whose footprint meets its
     // pixel strip (one Gaussian per lane, then a ballot) and walks only
@@ -97,20 +110,13 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
     {
       const Strip strip = warp_strip(g, tr, tc, t >> 5);
       const int lane = t & 31;
-      const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
+      const bool rel = lane < nb && touches_strip(g, sRecC[2 * lane + 1], strip);
       const unsigned mask = __ballot_sync(0xffffffffu, rel);
-      if (lane == 0) sMask[t >> 5] = mask;
+      // walk the marked entries while some pixel of the strip is alive; the
+      // stored mask keeps only entries that gave some pixel of the strip a
+      // non-zero weight (phase B reads nothing else)
       unsigned m = __any_sync(0xffffffffu, alive) ? mask : 0u;
-      // Gaussians of the mask that this warp skips (no pixel alive) still
-      // need a zero weight for phase B
-      if (!m) {
-        unsigned z = mask;
-        while (z) {
-          const int b = __ffs(z) - 1;
-          z &= z - 1;
-          sA[b * kTilePixels + t] = 0.0f;
-        }
-      }
+      unsigned used = 0;
       while (m) {
         const int b0 = __ffs(m) - 1;
         m &= m - 1;
@@ -119,8 +125,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
         float w0 = 0.0f, w1 = 0.0f, G;
         bool c0 = false, c1 = false;
         if (alive) {
-          c0 = pixel_weight(g, sRec[2 * b0], sRec[2 * b0 + 1], i, jj, fi, fj, &w0, &G);
-          if (b1 >= 0) c1 = pixel_weight(g, sRec[2 * b1], sRec[2 * b1 + 1], i, jj, fi, fj, &w1, &G);
+          c0 = pixel_weight(g, sRecC[2 * b0], sRecC[2 * b0 + 1], i, jj, fi, fj, &w0, &G);
+          if (b1 >= 0) c1 = pixel_weight(g, sRecC[2 * b1], sRecC[2 * b1 + 1], i, jj, fi, fj, &w1, &G);
         }
         float Tw0 = 0.0f, Tw1 = 0.0f;
         if (alive && c0) {
@@ -137,9 +143,11 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
         }
         sA[b0 * kTilePixels + t] = Tw0;
         if (b1 >= 0) sA[b1 * kTilePixels + t] = Tw1;
+        if (__any_sync(0xffffffffu, Tw0 != 0.0f)) used |= 1u << b0;
+        if (b1 >= 0 && __any_sync(0xffffffffu, Tw1 != 0.0f)) used |= 1u << b1;
       }
+      if (lane == 0) sMask[t >> 5] = used;
     }
-    cp_async_wait_all();
     const int n_alive = __syncthreads_count(alive);
     // ---- phase B: acc[p][c] += A[b][p] * s[b][c] over the (Gaussian, pixel
     // strip) pairs marked in phase A; pixel group p of this thread lies in
@@ -166,19 +174,25 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
       while (any) {
         const int b = __ffs(any) - 1;
         any &= any - 1;
-        const float4 b0 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&sR[b * NB + cg * 8 + 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&sRC[b * NB + cg * 8]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&sRC[b * NB + cg * 8 + 4]);
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float av[S::PX];
+#pragma unroll
+        for (int p = 0; p < S::PX; ++p)
+          av[p] = (own[p] & (1u << b)) ? sA[b * kTilePixels + p * S::PG + pg] : 0.0f;
 #pragma unroll
         for (int p = 0; p < S::PX; ++p)
           if (pmask[p] & (1u << b)) {
-            const float av = (own[p] & (1u << b)) ? sA[b * kTilePixels + p * S::PG + pg] : 0.0f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av, bv[c], acc[p][c]);
+            for (int c = 0; c < 8; ++c) acc[p][c] = fmaf(av[p], bv[c], acc[p][c]);
           }
       }
     }
-    if (n_alive == 0) break;
+    if (n_alive == 0) {
+      cp_async_wait_all();  // a prefetch may still be in flight
+      break;
+    }
   }
 
   // ---- epilogue
