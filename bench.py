@@ -52,6 +52,31 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# from the committed ncu capture (profiles/render_kernels_*_full.md), valid
+# only while the kernel sources hash to the value recorded at capture time.
+NCU_TRAFFIC = {
+    "render_fwd": {"bytes": 26_906_880 + 476_077_568, "tile": [16, 16],
+                   "files": ["render_fwd.cu", "render_tile.cuh", "render_common.cuh", "rxgs_math.cuh"],
+                   "sha1": "7b00d89e342f7dd3"},
+    "render_bwd": {"bytes": 568_947_456 + 8_235_776, "tile": [16, 16],
+                   "files": ["render_bwd.cu", "render_common.cuh", "rxgs_math.cuh"],
+                   "sha1": "cc8d90c17f2a61fa"},
+}
+
+
+def ncu_traffic(kernel, tile):
+    import hashlib
+    e = NCU_TRAFFIC.get(kernel)
+    if not e or list(tile) != e["tile"]:
+        return None
+    m = hashlib.sha1()
+    for f in e["files"]:
+        with open(os.path.join(ROOT, "paper_2605_24290_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return e["bytes"] if m.hexdigest()[:16] == e["sha1"] else None
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -240,18 +265,24 @@ def gpu_bench(args):
     dom = max(stages.items(), key=lambda kv: kv[1]["ms"])[0] if stages else "render_fwd"
     P = W.composited_pairs()
     pk, src = peaks()
-    roof = None
-    if "render_fwd" in stages:
-        fwd_ms = stages["render_fwd"]["ms"] / stages["render_fwd"]["calls"]
-        flops = P * (16 + 4 * W.N * W.C)
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = fp32_alu_peak_tflops(sm_mhz)
-        ach = flops / (fwd_ms / 1e3) / 1e12
-        roof = {"kernel": "render_fwd", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak = fp32_alu_peak_tflops(sm_mhz)
+    tile = tune["chosen"]["tile"] if tune else [16, 16]
+
+    def roofline(kernel, flops_per_pair, what):
+        if kernel not in stages:
+            return None
+        kms = stages[kernel]["ms"] / stages[kernel]["calls"]
+        ach = P * flops_per_pair / (kms / 1e3) / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(kernel, tile),
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
-                "units": f"{P} composited (pixel, Gaussian) pairs x (16 + 4*N*C) flops",
-                "launch_ms": round(fwd_ms, 4)}
+                "units": f"{P} composited (pixel, Gaussian) pairs x {what} flops",
+                "launch_ms": round(kms, 4)}
+
+    # dominant kernel: the backward (weight 16 + gamma 4NC + dL/ds 4NC per pair)
+    roof = roofline("render_bwd", 16 + 8 * W.N * W.C, "(16 + 8*N*C)")
+    roof_fwd = roofline("render_fwd", 16 + 4 * W.N * W.C, "(16 + 4*N*C)")
 
     # ---- per-receiver loop on a bounded sample of pairs (same kernels)
     loop = None
@@ -347,6 +378,7 @@ def gpu_bench(args):
             "dominant_stage": dom,
             "autotune": tune,
             "roofline": roof,
+            "roofline_fwd": roof_fwd,
             "per_rx_loop": loop,
             "serve": serve,
             "batched_csi": bcsi,
