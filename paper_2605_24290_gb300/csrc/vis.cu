@@ -318,10 +318,18 @@ static void launch_mw(const MlpParams& m, const float* rx, int N, const float4* 
 // M views) or one view per receiver (rx_view[j]); then the chunk sums are
 // added in order into csi[Mpart][N][C][2] / rssi (Mpart = M, or 1 per
 // receiver in the ragged case, laid out as [N][C][2]).
+bool launch_mlp_weighted_tc(const MlpParams& m, const float* rx, int N, const float4* geom,
+                            const float* base, int K, const float* W, int M, const int* rx_view,
+                            const float* glob, float* tmp, float* csi, float* rssi,
+                            const int* n_dev, cudaStream_t s);
+
 void launch_mlp_weighted(const MlpParams& m, const float* rx, int N, const float4* geom,
                          const float* base, int K, const float* W, int M, const int* rx_view,
                          const float* glob, float* tmp, float* csi, float* rssi,
                          const int* n_dev, cudaStream_t s) {
+  // bf16 MLPs: output layer on tensor cores
+  if (launch_mlp_weighted_tc(m, rx, N, geom, base, K, W, M, rx_view, glob, tmp, csi, rssi, n_dev, s))
+    return;
   const int Mpart = rx_view ? 1 : M;
   const int C2 = 2 * m.C;
   // views per pass: up to 8 for C <= 4, one at a time for wider channels
@@ -342,6 +350,261 @@ void launch_mlp_weighted(const MlpParams& m, const float* rx, int N, const float
   weighted_sum_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, nchunks, N, Mpart, m.C, csi,
                                                              rssi);
   note_launches(1);
+}
+
+}  // namespace rxgs
+
+namespace rxgs {
+
+// --------------------------- bf16 MLP on tensor cores, fused with the sum
+// Same result as mlp_weighted in bf16 mode (inputs, weights and hidden
+// activations rounded to bf16, float32 accumulation), with the output layer
+// [16 pairs x 64] x [64 x 4C] on warp-level tensor-core MMAs
+// (mma.sync m16n8k16 bf16 -> f32).  Block (chunk of Gaussians, receiver j):
+//   1. the chunk's Gaussians with W[v][k] != 0 are compacted into a list;
+//   2. each warp takes 16 listed Gaussians at a time: lanes compute the
+//      hidden layer (bf16) into shared memory, then the MMAs produce the
+//      local (alpha, beta) of every channel, and lanes holding alpha combine
+//      them with beta (from the neighbour lane), phi_base and the global
+//      branch into s, accumulating W s per channel;
+//   3. lanes, then warps, are summed in a fixed order into part[chunk][j].
+constexpr int kTcMaxNT = 26;  // 8-wide output tiles: 4C <= 208, C <= 52
+constexpr int kTcHStride = 72;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
+    const float* __restrict__ P, int C, const float* __restrict__ rx,
+    const float4* __restrict__ geom, const float* __restrict__ base, int K,
+    const float* __restrict__ W, int v0, const int* __restrict__ rx_view,
+    const float* __restrict__ glob, int Mpart, const int* __restrict__ n_dev,
+    float* __restrict__ part) {
+  constexpr int H = 64;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n4 = 4 * C, NT = (n4 + 7) / 8;
+  uint32_t* sBf = reinterpret_cast<uint32_t*>(smem_raw);               // [NT][4][32][2]
+  float* sW1 = reinterpret_cast<float*>(sBf + NT * 4 * 32 * 2);         // [64][6] bf16-rounded
+  float* sB1 = sW1 + H * 6;                                             // [64]
+  float* sB2 = sB1 + H;                                                 // [NT*8]
+  float* sG = sB2 + NT * 8;                                             // [4C] global branch
+  __nv_bfloat16* sH = reinterpret_cast<__nv_bfloat16*>(sG + n4);         // [8 warps][16][72]
+  int* sList = reinterpret_cast<int*>(sH + 8 * 16 * kTcHStride);         // [kMwChunk]
+  __shared__ int sCount;
+  __shared__ int sWarpOff[8];
+  __shared__ float sRed[8][2 * 52];
+  const int j = blockIdx.y, chunk = blockIdx.x;
+  if (n_dev && j >= *n_dev) return;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int off_l = H * 3 + H + n4 * H + n4;  // l_w1 in the flat parameters
+  const float* W2 = P + off_l + H * 7;
+  // B fragments of W2^T: element (k, n) = W2[n][k]
+  for (int e = t; e < NT * 4 * 32; e += 256) {
+    const int nt = e / 128, ks = (e / 32) % 4, l = e % 32;
+    const int n = nt * 8 + (l >> 2), k0 = ks * 16 + (l & 3) * 2;
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n < n4) {
+      w[0] = W2[n * H + k0];
+      w[1] = W2[n * H + k0 + 1];
+      w[2] = W2[n * H + k0 + 8];
+      w[3] = W2[n * H + k0 + 9];
+    }
+    sBf[2 * e + 0] = pack_bf16(w[0], w[1]);
+    sBf[2 * e + 1] = pack_bf16(w[2], w[3]);
+  }
+  for (int e = t; e < H * 6; e += 256) sW1[e] = __bfloat162float(__float2bfloat16_rn(P[off_l + e]));
+  for (int e = t; e < H; e += 256) sB1[e] = P[off_l + H * 6 + e];
+  for (int e = t; e < NT * 8; e += 256) sB2[e] = e < n4 ? P[off_l + H * 7 + n4 * H + e] : 0.0f;
+  for (int e = t; e < n4; e += 256) sG[e] = glob[static_cast<size_t>(j) * n4 + e];
+  const int vj = rx_view ? rx_view[j] : v0;
+  const float* Wv = W + static_cast<size_t>(vj) * K;
+  // ---- compaction of the chunk's non-zero weights (ordered)
+  const int k0 = chunk * kMwChunk, k1 = min(K, k0 + kMwChunk);
+  constexpr int kPer = kMwChunk / 256;
+  int cnt = 0;
+  for (int q = 0; q < kPer; ++q) {
+    const int k = k0 + t * kPer + q;
+    cnt += (k < k1 && Wv[k] != 0.0f);
+  }
+  int inc = cnt;  // inclusive scan over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) sWarpOff[warp] = inc;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int w = 0; w < 8; ++w) {
+      const int c = sWarpOff[w];
+      sWarpOff[w] = run;
+      run += c;
+    }
+    sCount = run;
+  }
+  __syncthreads();
+  int pos = sWarpOff[warp] + inc - cnt;
+  for (int q = 0; q < kPer; ++q) {
+    const int k = k0 + t * kPer + q;
+    if (k < k1 && Wv[k] != 0.0f) sList[pos++] = k;
+  }
+  __syncthreads();
+  const int nact = sCount;
+  // ---- 16-Gaussian tiles per warp
+  const float rxj = rx[3 * j], ryj = rx[3 * j + 1], rzj = rx[3 * j + 2];
+  const int g = lane >> 2, tig = lane & 3;
+  float acc[kTcMaxNT][2];
+#pragma unroll
+  for (int nt = 0; nt < kTcMaxNT; ++nt) acc[nt][0] = acc[nt][1] = 0.0f;
+  __nv_bfloat16* hW = sH + warp * 16 * kTcHStride;
+  for (int tile = warp; tile * 16 < nact; tile += 8) {
+    // hidden layer: lane computes units [32*half, 32*half + 32) of row r
+    {
+      const int r = lane & 15, half = lane >> 4;
+      const int li = tile * 16 + r;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      const bool ok = li < nact;
+      if (ok) {
+        const float4 p = geom[3 * sList[li]];
+        const float vx = rxj - p.x, vy = ryj - p.y, vz = rzj - p.z;
+        const float d = sqrtf(vx * vx + vy * vy + vz * vz);
+        const float inv = 1.0f / d;
+        x[0] = __bfloat162float(__float2bfloat16_rn(vx * inv));
+        x[1] = __bfloat162float(__float2bfloat16_rn(vy * inv));
+        x[2] = __bfloat162float(__float2bfloat16_rn(vz * inv));
+        x[3] = __bfloat162float(__float2bfloat16_rn(d));
+      }
+#pragma unroll 8
+      for (int uu = 0; uu < 32; ++uu) {
+        const int u = half * 32 + uu;
+        float a = sB1[u];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a = fmaf(sW1[u * 6 + i], x[i], a);
+        a += sW1[u * 6 + 4];  // inputs 4 and 5 are the constants 1 and 0
+        hW[r * kTcHStride + u] = __float2bfloat16_rn(ok ? fmaxf(a, 0.0f) : 0.0f);
+      }
+    }
+    __syncwarp();
+    // A fragments of the 16 x 64 hidden tile
+    uint32_t af[4][4];
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int c0 = ks * 16 + tig * 2;
+      af[ks][0] = *reinterpret_cast<const uint32_t*>(&hW[g * kTcHStride + c0]);
+      af[ks][1] = *reinterpret_cast<const uint32_t*>(&hW[(g + 8) * kTcHStride + c0]);
+      af[ks][2] = *reinterpret_cast<const uint32_t*>(&hW[g * kTcHStride + c0 + 8]);
+      af[ks][3] = *reinterpret_cast<const uint32_t*>(&hW[(g + 8) * kTcHStride + c0 + 8]);
+    }
+    __syncwarp();  // hW is rewritten by the next tile
+    const int la = tile * 16 + g, lb = la + 8;
+    const int ka = la < nact ? sList[la] : -1, kb = lb < nact ? sList[lb] : -1;
+    const float wa = ka >= 0 ? Wv[ka] : 0.0f, wb = kb >= 0 ? Wv[kb] : 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < kTcMaxNT; ++nt) {
+      if (nt >= NT) break;
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t* bp = sBf + ((nt * 4 + ks) * 32 + lane) * 2;
+        mma_bf16_16816(d, af[ks], bp[0], bp[1]);
+      }
+      const int col = nt * 8 + tig * 2;
+      d[0] += sB2[col];
+      d[1] += sB2[col + 1];
+      d[2] += sB2[col];
+      d[3] += sB2[col + 1];
+      // beta of the same channel sits in the neighbouring lane (tig + 1)
+      const float b0 = __shfl_xor_sync(0xffffffffu, d[0], 1);
+      const float b1 = __shfl_xor_sync(0xffffffffu, d[1], 1);
+      const float b2 = __shfl_xor_sync(0xffffffffu, d[2], 1);
+      const float b3 = __shfl_xor_sync(0xffffffffu, d[3], 1);
+      const int ch = 2 * nt + (tig >> 1);
+      if ((tig & 1) == 0 && ch < C) {
+        const float agr = 1.0f + sG[4 * ch + 0], agi = sG[4 * ch + 1];
+        const float bgr = sG[4 * ch + 2], bgi = sG[4 * ch + 3];
+        if (ka >= 0) {
+          const float pr = base[(static_cast<size_t>(ka) * C + ch) * 2 + 0];
+          const float pi = base[(static_cast<size_t>(ka) * C + ch) * 2 + 1];
+          const float ur = agr * pr - agi * pi + bgr, ui = agr * pi + agi * pr + bgi;
+          const float alr = 1.0f + d[0], ali = d[1];
+          acc[nt][0] = fmaf(wa, alr * ur - ali * ui + b0, acc[nt][0]);
+          acc[nt][1] = fmaf(wa, alr * ui + ali * ur + b1, acc[nt][1]);
+        }
+        if (kb >= 0) {
+          const float pr = base[(static_cast<size_t>(kb) * C + ch) * 2 + 0];
+          const float pi = base[(static_cast<size_t>(kb) * C + ch) * 2 + 1];
+          const float ur = agr * pr - agi * pi + bgr, ui = agr * pi + agi * pr + bgi;
+          const float alr = 1.0f + d[2], ali = d[3];
+          acc[nt][0] = fmaf(wb, alr * ur - ali * ui + b2, acc[nt][0]);
+          acc[nt][1] = fmaf(wb, alr * ui + ali * ur + b3, acc[nt][1]);
+        }
+      }
+    }
+  }
+  // ---- lanes with the same tig (rows g = 0..7), then warps, in fixed order
+#pragma unroll
+  for (int nt = 0; nt < kTcMaxNT; ++nt) {
+    if (nt >= NT) break;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float y = acc[nt][e];
+      y += __shfl_xor_sync(0xffffffffu, y, 4);
+      y += __shfl_xor_sync(0xffffffffu, y, 8);
+      y += __shfl_xor_sync(0xffffffffu, y, 16);
+      acc[nt][e] = y;
+    }
+    const int ch = 2 * nt + (tig >> 1);
+    if (g == 0 && (tig & 1) == 0 && ch < C) {
+      sRed[warp][2 * ch] = acc[nt][0];
+      sRed[warp][2 * ch + 1] = acc[nt][1];
+    }
+  }
+  __syncthreads();
+  if (t < 2 * C) {
+    float y = 0.0f;
+    for (int w = 0; w < 8; ++w) y += sRed[w][t];
+    part[((static_cast<size_t>(chunk) * gridDim.y + j) * Mpart + (rx_view ? 0 : v0)) * 2 * C + t] = y;
+  }
+}
+
+size_t mlp_weighted_tc_smem(int C) {
+  const int n4 = 4 * C, NT = (n4 + 7) / 8;
+  return sizeof(uint32_t) * NT * 4 * 32 * 2 + sizeof(float) * (64 * 6 + 64 + NT * 8 + n4) +
+         sizeof(__nv_bfloat16) * 8 * 16 * kTcHStride + sizeof(int) * kMwChunk;
+}
+
+bool launch_mlp_weighted_tc(const MlpParams& m, const float* rx, int N, const float4* geom,
+                            const float* base, int K, const float* W, int M, const int* rx_view,
+                            const float* glob, float* tmp, float* csi, float* rssi,
+                            const int* n_dev, cudaStream_t s) {
+  if (!m.bf16 || m.C <= 4 || m.C > 52) return false;  // narrow spectra: multi-view SIMT kernel
+  const int Mpart = rx_view ? 1 : M;
+  const int nchunks = (K + kMwChunk - 1) / kMwChunk;
+  const size_t smem = mlp_weighted_tc_smem(m.C);
+  cudaFuncSetAttribute(mlp_weighted_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+  for (int v0 = 0; v0 < (rx_view ? 1 : M); ++v0) {
+    mlp_weighted_tc_kernel<<<dim3(nchunks, N), 256, smem, s>>>(m.p, m.C, rx, geom, base, K, W, v0,
+                                                               rx_view, glob, Mpart, n_dev, tmp);
+    note_launches(1);
+  }
+  const int n = Mpart * N * m.C;
+  weighted_sum_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, nchunks, N, Mpart, m.C, csi,
+                                                             rssi);
+  note_launches(1);
+  return true;
 }
 
 }  // namespace rxgs

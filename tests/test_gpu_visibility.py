@@ -79,3 +79,43 @@ def test_mlp_visibility_equals_oracle_and_batched(torch, rx, oracle, C):
     ref = np.concatenate([csi[0, :4].cpu().numpy(), csi[1, 4:].cpu().numpy()])
     a = np.concatenate([scales[0][:4], scales[1][4:]])
     assert norm_err(bc.cpu().numpy(), ref, a) <= TOL
+
+
+@pytest.mark.parametrize("C", [3, 8, 52])
+def test_mlp_bf16_visibility_pixel_and_batched(torch, rx, oracle, C):
+    """bf16 conditioning MLP: the per-pixel path, the visibility path (tensor
+    cores for C > 4) and uneven batches, against the oracle's bf16 MLP."""
+    rng = np.random.default_rng(640 + C)
+    K = 3000
+    sc = S.draw_scene(rng, K)
+    base = S.draw_base(rng, K, C)
+    mlp = S.draw_mlp(rng, C)
+    g = S.Grid()
+    ctx = rx.Context(H=g.H, W=g.W)
+    h = upload(ctx, sc, torch, base=base, mlp_flat=S.flatten_mlp(mlp, C), C=C, bf16=True)
+    tx = S.draw_points(rng, 2)
+    rxp = S.draw_points(rng, 9)
+    views = ctx.prepare(h, dev(tx, torch))
+    csi_v = torch.zeros((2, 9, C, 2), device="cuda")
+    csi_p = torch.zeros((2, 9, C, 2), device="cuda")
+    ctx.render_views(views, dev(rxp, torch), 9, rx.OUT_CSI, csi=csi_v, reduce_path=1)
+    ctx.render_views(views, dev(rxp, torch), 9, rx.OUT_CSI, csi=csi_p, reduce_path=0)
+    ctx.sync()
+    rad = oracle.mlp_radiance(mlp, rxp, sc.means, base, bf16=True)
+    scales = []
+    for v in range(2):
+        o = oracle.render_view(g, sc, tx[v], rad)
+        a = o["absacc"].sum(axis=(1, 2))
+        scales.append(a)
+        ref = oracle.csi(o["spectra"])
+        ev = norm_err(csi_v[v].cpu().numpy(), ref, a)
+        ep = norm_err(csi_p[v].cpu().numpy(), ref, a)
+        print(f"C={C} view {v}: visibility {ev:.3e}  per-pixel {ep:.3e}")
+        assert ev <= TOL and ep <= TOL
+    counts = [4, 5]
+    bc = torch.zeros((9, C, 2), device="cuda")
+    ctx.render_batched(h, dev(tx, torch), dev(rxp, torch), counts, rx.OUT_CSI, csi=bc)
+    ctx.sync()
+    ref = np.concatenate([csi_v[0, :4].cpu().numpy(), csi_v[1, 4:].cpu().numpy()])
+    a = np.concatenate([scales[0][:4], scales[1][4:]])
+    assert norm_err(bc.cpu().numpy(), ref, a) <= TOL
