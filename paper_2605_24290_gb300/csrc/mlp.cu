@@ -170,11 +170,13 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
 //   dL/da_g = sum_k dL/du conj(phi), dL/db_g = sum_k dL/du,
 //   dL/dphi = sum_j dL/du conj(1 + a_g)
 // One thread per (j, k) pair, grid-stride with a stride that is a multiple
-// of N so each thread keeps one receiver j.  The local-branch weight
-// gradients are sums of per-pair outer products (dol x h, dh x x): every warp
-// reduce-scatters each 32-wide slice over its lanes with shuffles (lane l
-// ends up owning hidden unit l of the slice) and keeps the result in
-// registers; at the end warps and blocks are combined in a fixed order.
+// of N so each thread keeps one receiver j (phase 1: features, hidden
+// layer, outputs, the combination's gradients).  The local-branch weight
+// gradients are sums over pairs of outer products (dol x h, dh x x); they
+// are accumulated with the warp transposed (phase 2): lane l owns hidden
+// units l and l + 32, walks the warp's 32 pairs (features and dol staged in
+// shared memory), recomputes h for its units and accumulates in registers.
+// At the end warps and blocks are combined in a fixed order.
 constexpr int kBwdThreads = 256;
 
 static int mlp_bwd_blocks(int N) {
@@ -204,23 +206,6 @@ size_t mlp_backward_tmp_floats(const MlpParams& m, int N, int /*K*/) {
          static_cast<size_t>(N) * 4 * m.C;
 }
 
-// Reduce-scatter of a 32-value per-lane vector over the warp: returns the
-// warp sum of entry `lane`.
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const bool hi = (lane & off) != 0;
-#pragma unroll
-    for (int e = 0; e < off; ++e) {
-      const float send = hi ? v[e] : v[e + off];
-      const float keep = hi ? v[e + off] : v[e];
-      v[e] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-    }
-  }
-  return v[0];
-}
-
 template <int CC>
 __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const float* __restrict__ P, const float* __restrict__ rx, int N,
@@ -231,6 +216,8 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   constexpr int kWarps = kBwdThreads / 32;
   __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
+  __shared__ float4 sX[kBwdThreads];            // features of each thread's pair
+  __shared__ float4 sD[kBwdThreads * CC];       // dol of each thread's pair
   extern __shared__ float sdyn[];  // [kWarps][nloc] warp partials, then [256][4C]
   const MlpOffsets o = mlp_offsets(kHidden, CC);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -239,6 +226,18 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   for (int e = t; e < n4 * kHidden; e += kBwdThreads) W2[e] = P[o.l_w2 + e];
   for (int e = t; e < n4; e += kBwdThreads) B2[e] = P[o.l_b2 + e];
   __syncthreads();
+
+  // phase-2 operands of this lane's hidden units u = lane, lane + 32
+  float w1u[2][5], w2u[2][n4];
+#pragma unroll
+  for (int hf = 0; hf < 2; ++hf) {
+    const int u = hf * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) w1u[hf][i] = W1[u * 6 + i];
+#pragma unroll
+    for (int q = 0; q < n4; ++q) w2u[hf][q] = W2[q * kHidden + u];
+  }
+  float b1u[2] = {B1[lane], B1[32 + lane]};
 
   float aw2[n4][2], aw1[4][2], ab1[2], ab2[n4], aog[n4];
 #pragma unroll
@@ -262,7 +261,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const bool ok = pair < pairs;
     const int k = ok ? static_cast<int>(pair / N) : 0;
     float x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float h[kHidden], dol[n4], db[2 * CC];
+    float dol[n4], db[2 * CC];
 #pragma unroll
     for (int q = 0; q < n4; ++q) dol[q] = 0.0f;
 #pragma unroll
@@ -276,26 +275,24 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
       x[1] = vy * inv;
       x[2] = vz * inv;
       x[3] = d;
-    }
+      // hidden units streamed into the outputs (same summation order as
+      // the forward: bias first, then units in ascending order)
+      float oall[n4];
 #pragma unroll
-    for (int u = 0; u < kHidden; ++u) {
-      float a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
+      for (int q = 0; q < n4; ++q) oall[q] = B2[q];
+#pragma unroll 8
+      for (int u = 0; u < kHidden; ++u) {
+        float a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
-      h[u] = ok ? fmaxf(a, 0.0f) : 0.0f;
-    }
-    if (ok) {
+        for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
+        const float hu = fmaxf(a, 0.0f);
+#pragma unroll
+        for (int q = 0; q < n4; ++q) oall[q] = fmaf(W2[q * kHidden + u], hu, oall[q]);
+      }
       const float* gs = dS + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * CC;
 #pragma unroll
       for (int c = 0; c < CC; ++c) {
-        float ol[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float a = B2[4 * c + q];
-#pragma unroll
-          for (int u = 0; u < kHidden; ++u) a = fmaf(W2[(4 * c + q) * kHidden + u], h[u], a);
-          ol[q] = a;
-        }
+        const float ol[4] = {oall[4 * c], oall[4 * c + 1], oall[4 * c + 2], oall[4 * c + 3]};
         const float pr = base[(static_cast<size_t>(k) * CC + c) * 2 + 0];
         const float pi = base[(static_cast<size_t>(k) * CC + c) * 2 + 1];
         const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
@@ -337,41 +334,47 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     }
 #pragma unroll
     for (int q = 0; q < n4; ++q) ab2[q] += dol[q];
-    // dL/dW2 = dol x h, reduce-scattered per 32-wide slice
+    // ---- phase 2: the warp's 32 pairs, lane = hidden units lane, lane + 32
+    sX[t] = make_float4(x[0], x[1], x[2], x[3]);
 #pragma unroll
-    for (int q = 0; q < n4; ++q)
+    for (int c = 0; c < CC; ++c)
+      sD[t * CC + c] = make_float4(dol[4 * c], dol[4 * c + 1], dol[4 * c + 2], dol[4 * c + 3]);
+    __syncwarp();
+#pragma unroll 4
+    for (int pp = 0; pp < 32; ++pp) {
+      const int p = warp * 32 + pp;
+      const float4 xp = sX[p];
+      float dv[n4];
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        const float4 d4 = sD[p * CC + c];
+        dv[4 * c + 0] = d4.x;
+        dv[4 * c + 1] = d4.y;
+        dv[4 * c + 2] = d4.z;
+        dv[4 * c + 3] = d4.w;
+      }
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
-        float v[32];
+        float a = b1u[hf] + w1u[hf][4];
+        a = fmaf(w1u[hf][0], xp.x, a);
+        a = fmaf(w1u[hf][1], xp.y, a);
+        a = fmaf(w1u[hf][2], xp.z, a);
+        a = fmaf(w1u[hf][3], xp.w, a);
+        const float hv = fmaxf(a, 0.0f);
+        float g = 0.0f;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = dol[q] * h[hf * 32 + e];
-        aw2[q][hf] += warp_reduce_scatter32(v);
-      }
-    // dL/dh = W2^T dol on active units
-    float dh[kHidden];
+        for (int q = 0; q < n4; ++q) g = fmaf(w2u[hf][q], dv[q], g);
+        const float dh = hv > 0.0f ? g : 0.0f;  // dL/dh = W2^T dol on active units
+        ab1[hf] += dh;
+        aw1[0][hf] = fmaf(dh, xp.x, aw1[0][hf]);
+        aw1[1][hf] = fmaf(dh, xp.y, aw1[1][hf]);
+        aw1[2][hf] = fmaf(dh, xp.z, aw1[2][hf]);
+        aw1[3][hf] = fmaf(dh, xp.w, aw1[3][hf]);
 #pragma unroll
-    for (int u = 0; u < kHidden; ++u) {
-      float a = 0.0f;
-#pragma unroll
-      for (int q = 0; q < n4; ++q) a = fmaf(W2[q * kHidden + u], dol[q], a);
-      dh[u] = h[u] > 0.0f ? a : 0.0f;
-    }
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      {
-        float v[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = dh[hf * 32 + e];
-        ab1[hf] += warp_reduce_scatter32(v);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        float v[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = dh[hf * 32 + e] * x[i];
-        aw1[i][hf] += warp_reduce_scatter32(v);
+        for (int q = 0; q < n4; ++q) aw2[q][hf] = fmaf(dv[q], hv, aw2[q][hf]);
       }
     }
+    __syncwarp();  // sX / sD are rewritten in the next round
   }
 
   // ---- warp partials -> shared, then a fixed-order sum over warps

@@ -25,15 +25,6 @@
 
 namespace rxgs {
 
-constexpr int kBNB = 32;      // columns per backward CTA
-constexpr int kPad = 257;     // padded per-pixel row (bank spread)
-constexpr int kGStride = 36;  // padded cotangent row (float4 aligned)
-
-constexpr size_t bwd_smem_bytes() {
-  return sizeof(float) * (kTilePixels * kGStride + 2 * kChunk * kPad + kChunk * kBNB) +
-         sizeof(float4) * 2 * kChunk + sizeof(uint32_t) * kChunk;
-}
-
 // Walk 1, once per (view, tile): every pixel's final transmittance and the
 // list position one past its last composited Gaussian (its stop), with the
 // forward's float32 decisions; tile_stop = the largest stop of the tile.
@@ -98,125 +89,239 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
   if (t == 0) tile_stop[static_cast<size_t>(v) * g.T + tile] = sStop;
 }
 
-__global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const BackwardArgs A) {
+// Walk 2, one CTA of 512 threads per (view, tile, block of NB columns): two
+// threads per pixel (lanes l and l + 16 of a warp; a warp covers 16 pixels).
+// Per chunk of the list, back to front over the entries that meet the
+// warp's 16-pixel strip, two entries b0 > b1 at a time:
+//   - the lower half of the warp evaluates the weight of b0 and the upper
+//     half that of b1 (exchanged by shuffles), so each (pixel, entry) weight
+//     is computed once per NB columns;
+//   - each half dots the pixel's cotangent with the radiance over its NB/2
+//     columns for both entries; a shuffle adds the halves into gamma;
+//   - both halves then run the same recurrence (T recovery, Q suffix);
+//   - dL/dtau is summed over the warp's pixels by shuffles.
+// Then dL/ds[b][c] = sum_p (T w)[b][p] g[p][c] is register-tiled over all
+// 512 threads (4 entries x 8 columns per thread over a slice of the pixels).
+template <int NB>
+struct BwdShape {
+  static constexpr int kThreads = 2 * kTilePixels;
+  static constexpr int HC = NB / 2;                 // gamma columns per thread
+  static constexpr int GS = NB + 4;                 // padded cotangent row (float4 aligned)
+  static constexpr int CB = NB / 8;                 // 8-column groups in the product
+  static constexpr int SL = kThreads / (8 * CB);    // pixel slices in the product
+  static constexpr int kWarps = kThreads / 32;
+  // cotangent rows, T w, two radiance / record / index buffers, dtau sums
+  static constexpr size_t smem =
+      sizeof(float) * (kTilePixels * GS + kChunk * kTilePixels + 2 * kChunk * NB + kWarps * kChunk) +
+      sizeof(float4) * 2 * 2 * kChunk + sizeof(uint32_t) * 2 * kChunk;
+};
+
+template <int NB>
+__global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const BackwardArgs A) {
+  using S = BwdShape<NB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sG = reinterpret_cast<float*>(smem_raw);   // [256][36] cotangent rows
-  float* sA = sG + kTilePixels * kGStride;          // [32][257] T w
-  float* sT = sA + kChunk * kPad;                   // [32][257] dL/dtau per pixel
-  float* sR = sT + kChunk * kPad;                   // [32][32] radiance slice
-  float4* sRec = reinterpret_cast<float4*>(sR + kChunk * kBNB);  // [32][2]
-  uint32_t* sK = reinterpret_cast<uint32_t*>(sRec + 2 * kChunk);  // [32]
-  __shared__ unsigned sMask[kTilePixels / 32];  // per warp: chunk entries meeting its strip
+  float* sG = reinterpret_cast<float*>(smem_raw);          // [256][GS] cotangent rows
+  float* sA = sG + kTilePixels * S::GS;                     // [32][256] T w
+  float* sR0 = sA + kChunk * kTilePixels;                   // [2][32][NB] radiance slices
+  float* sTau = sR0 + 2 * kChunk * NB;                      // [16 warps][32] dL/dtau sums
+  float4* sRec0 = reinterpret_cast<float4*>(sTau + S::kWarps * kChunk);  // [2][32][2]
+  uint32_t* sK0 = reinterpret_cast<uint32_t*>(sRec0 + 2 * 2 * kChunk);    // [2][32]
+  __shared__ unsigned sMask[S::kWarps];  // per warp: entries with a non-zero weight
 
   const RenderArgs& a = A.f;
   const GridConst& g = a.g;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5, h = lane >> 4;
+  const int px = wp * 16 + (lane & 15);
   const int tile = blockIdx.x, v = blockIdx.z;
-  const int col0 = blockIdx.y * kBNB;
+  const int col0 = blockIdx.y * NB;
   const int tr = tile / g.tiles_w, tc = tile % g.tiles_w;
-  const int i = tr * g.TH + t / g.TW, jj = tc * g.TW + t % g.TW;
+  const int i = tr * g.TH + px / g.TW, jj = tc * g.TW + px % g.TW;
   const bool valid = i < g.H && jj < g.W;
   const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
   const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
   const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
   const size_t HW = static_cast<size_t>(g.H) * g.W;
-  const size_t pix = static_cast<size_t>(i) * g.W + jj;
   const int twoC = 2 * a.C;
-  const Strip strip = warp_strip(g, tr, tc, t >> 5);
+  const Strip strip = pixel_strip(g, tr, tc, wp * 16, 16);
 
-  // cotangent of this pixel for the CTA's columns
-  float gr[kBNB];
-#pragma unroll
-  for (int c = 0; c < kBNB; ++c) {
-    const int col = col0 + c;
-    float val = 0.0f;
-    if (valid && col < a.ncols) {
-      const int j = col / twoC, e = col - j * twoC;
-      if (A.g_spec) val += A.g_spec[((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + e];
-      if (A.g_uniform) val += A.g_uniform[static_cast<size_t>(v) * a.ncols + col];
+  // cotangent rows of the tile for the CTA's columns (consecutive threads
+  // take consecutive pixels of one column): asynchronous copies when the
+  // cotangent is per pixel only, so that all of them are in flight at once
+  if (A.g_spec && !A.g_uniform) {
+    for (int e = t; e < kTilePixels * NB; e += S::kThreads) {
+      const int p = e % kTilePixels, c = e / kTilePixels;
+      const int pi = tr * g.TH + p / g.TW, pj = tc * g.TW + p % g.TW;
+      const int col = col0 + c;
+      const bool ok = pi < g.H && pj < g.W && col < a.ncols;
+      const float* src = A.g_spec;
+      if (ok) {
+        const int j = col / twoC, ec = col - j * twoC;
+        const size_t pix = static_cast<size_t>(pi) * g.W + pj;
+        src += ((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + ec;
+      }
+      cp_async4(&sG[p * S::GS + c], src, ok);
     }
-    gr[c] = val;
-    sG[t * kGStride + c] = val;
+    cp_async_commit();
+  } else {
+#pragma unroll 8
+    for (int e = t; e < kTilePixels * NB; e += S::kThreads) {
+      const int p = e % kTilePixels, c = e / kTilePixels;
+      const int pi = tr * g.TH + p / g.TW, pj = tc * g.TW + p % g.TW;
+      const int col = col0 + c;
+      float val = 0.0f;
+      if (pi < g.H && pj < g.W && col < a.ncols) {
+        const int j = col / twoC, ec = col - j * twoC;
+        const size_t pix = static_cast<size_t>(pi) * g.W + pj;
+        if (A.g_spec) val += A.g_spec[((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + ec];
+        if (A.g_uniform) val += A.g_uniform[static_cast<size_t>(v) * a.ncols + col];
+      }
+      sG[p * S::GS + c] = val;
+    }
   }
   // final transmittance and stop position from the per-tile pre-pass
   float T = 1.0f;
   uint32_t stop = rg.x;
   if (valid) {
-    const size_t o = static_cast<size_t>(v) * HW + pix;
+    const size_t o = static_cast<size_t>(v) * HW + static_cast<size_t>(i) * g.W + jj;
     T = A.tfin[o];
     stop = A.stops[o];
   }
   const uint32_t tile_stop = A.tile_stop[static_cast<size_t>(v) * g.T + tile];
 
-  // dS mapping: 32 output blocks (4 Gaussians x 8 columns) x 8 pixel slices
-  const int slice = t & 7, ob = t >> 3;
-  const int bb = (ob >> 2) * 4, cbk = (ob & 3) * 8;
+  // product mapping: 8 groups of 4 entries x CB groups of 8 columns, SL
+  // pixel slices
+  const int slice = t % S::SL, ob = t / S::SL;
+  const int bb = (ob / S::CB) * 4, cbk = (ob % S::CB) * 8;
 
-  // ---- walk 2: back to front
   float Q = 0.0f;
+  const float* gRow = sG + px * S::GS + h * S::HC;
   const int nchunks = static_cast<int>((tile_stop - rg.x + kChunk - 1) / kChunk);
-  for (int ci = nchunks - 1; ci >= 0; --ci) {
-    const uint32_t start = rg.x + static_cast<uint32_t>(ci) * kChunk;
+  // Chunks are double-buffered: while chunk ci is swept, the records,
+  // indices and radiance rows of chunk ci - 1 are in flight (cp.async).
+  auto stage = [&](int cs, int buf) {
+    const uint32_t start = rg.x + static_cast<uint32_t>(cs) * kChunk;
     const int nb = min(kChunk, static_cast<int>(tile_stop - start));
-    __syncthreads();
+    float4* rb = sRec0 + buf * 2 * kChunk;
+    float* rr = sR0 + buf * kChunk * NB;
     if (t < kChunk) {
       const bool ok = t < nb;
       const uint32_t k = ok ? a.vals[start + t] : 0u;
-      sK[t] = k;
-      cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
-      cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
+      sK0[buf * kChunk + t] = k;
+      cp_async16(&rb[2 * t + 0], &rec[2 * k + 0], ok);
+      cp_async16(&rb[2 * t + 1], &rec[2 * k + 1], ok);
     }
-    {
-      const int b = t >> 3, q4 = t & 7;  // 32 rows x 32 columns, one float4 each
+    constexpr int Q4 = NB / 4;  // float4 per radiance row slice
+    for (int e = t; e < kChunk * Q4; e += S::kThreads) {
+      const int b = e / Q4, q4 = e % Q4;
       const bool ok = b < nb;
       const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
-      cp_async16(&sR[b * kBNB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
+      cp_async16(&rr[b * NB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
                  ok);
     }
     cp_async_commit();
-    cp_async_wait_all();
+  };
+  if (nchunks > 0) stage(nchunks - 1, 0);
+  int buf = 0;
+  for (int ci = nchunks - 1; ci >= 0; --ci, buf ^= 1) {
+    const uint32_t start = rg.x + static_cast<uint32_t>(ci) * kChunk;
+    const int nb = min(kChunk, static_cast<int>(tile_stop - start));
+    __syncthreads();  // everyone is done with the buffer the prefetch overwrites
+    if (ci > 0) {
+      stage(ci - 1, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this chunk landed
+    } else {
+      cp_async_wait_all();
+    }
+    sTau[t] = 0.0f;  // 512 threads, 16 x 32 entries
     __syncthreads();
+    const float4* sRec = sRec0 + buf * 2 * kChunk;
+    const float* sR = sR0 + buf * kChunk * NB;
+    const uint32_t* sK = sK0 + buf * kChunk;
     {
-      // entries meeting this warp's strip, swept from the back
-      const int lane = t & 31;
       const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
       // no pixel of the strip reaches this chunk: nothing to do here
       if (!__any_sync(0xffffffffu, start < stop)) m = 0;
-      unsigned used = 0;  // entries with a non-zero weight somewhere in the strip
+      unsigned used = 0;
+      const int src0 = lane & 15, src1 = src0 | 16;
       while (m) {
-        const int b = 31 - __clz(m);
-        m &= ~(1u << b);
-        float Tw = 0.0f, dtau = 0.0f;
-        if (start + b < stop) {
+        const int b0 = 31 - __clz(m);
+        m &= ~(1u << b0);
+        const int b1 = m ? 31 - __clz(m) : -1;
+        if (b1 >= 0) m &= ~(1u << b1);
+        // weights: lower half b0, upper half b1; G = 0 marks "not composited"
+        const int bm = h ? b1 : b0;
+        float wm = 0.0f, Gm = 0.0f;
+        if (bm >= 0 && start + bm < stop) {
           float w, G;
-          if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
-            float gam = 0.0f;
-            const float4* r4 = reinterpret_cast<const float4*>(&sR[b * kBNB]);
-#pragma unroll
-            for (int q = 0; q < kBNB / 4; ++q) {
-              const float4 s4 = r4[q];
-              gam = fmaf(gr[4 * q + 0], s4.x, gam);
-              gam = fmaf(gr[4 * q + 1], s4.y, gam);
-              gam = fmaf(gr[4 * q + 2], s4.z, gam);
-              gam = fmaf(gr[4 * q + 3], s4.w, gam);
-            }
-            const float one_m_w = 1.0f - w;
-            T = __fdividef(T, one_m_w);  // transmittance in front of this Gaussian
-            Tw = T * w;
-            dtau = T * (gam - Q) * G;
-            Q = fmaf(w, gam, one_m_w * Q);
+          if (pixel_weight(g, sRec[2 * bm], sRec[2 * bm + 1], i, jj, fi, fj, &w, &G)) {
+            wm = w;
+            Gm = G;
           }
         }
-        sA[b * kPad + t] = Tw;
-        sT[b * kPad + t] = dtau;
-        if (__any_sync(0xffffffffu, Tw != 0.0f)) used |= 1u << b;
+        const float w0 = __shfl_sync(0xffffffffu, wm, src0);
+        const float G0 = __shfl_sync(0xffffffffu, Gm, src0);
+        const float w1 = __shfl_sync(0xffffffffu, wm, src1);
+        const float G1 = __shfl_sync(0xffffffffu, Gm, src1);
+        // gamma over this half's columns, both entries
+        float p0 = 0.0f, p1 = 0.0f;
+        const bool c0 = G0 != 0.0f, c1 = G1 != 0.0f;
+        if (c0 || c1) {
+          const float4* r0 = reinterpret_cast<const float4*>(&sR[b0 * NB + h * S::HC]);
+          const float4* r1 = reinterpret_cast<const float4*>(&sR[(b1 >= 0 ? b1 : b0) * NB + h * S::HC]);
+          const float4* g4 = reinterpret_cast<const float4*>(gRow);
+#pragma unroll
+          for (int q = 0; q < S::HC / 4; ++q) {
+            const float4 gv = g4[q], a0 = r0[q], a1 = r1[q];
+            p0 = fmaf(gv.x, a0.x, p0);
+            p0 = fmaf(gv.y, a0.y, p0);
+            p0 = fmaf(gv.z, a0.z, p0);
+            p0 = fmaf(gv.w, a0.w, p0);
+            p1 = fmaf(gv.x, a1.x, p1);
+            p1 = fmaf(gv.y, a1.y, p1);
+            p1 = fmaf(gv.z, a1.z, p1);
+            p1 = fmaf(gv.w, a1.w, p1);
+          }
+        }
+        const float gam0 = p0 + __shfl_xor_sync(0xffffffffu, p0, 16);
+        const float gam1 = p1 + __shfl_xor_sync(0xffffffffu, p1, 16);
+        float Tw0 = 0.0f, Tw1 = 0.0f, dt0 = 0.0f, dt1 = 0.0f;
+        if (c0) {
+          const float one_m_w = 1.0f - w0;
+          T = __fdividef(T, one_m_w);  // transmittance in front of this Gaussian
+          Tw0 = T * w0;
+          dt0 = T * (gam0 - Q) * G0;
+          Q = fmaf(w0, gam0, one_m_w * Q);
+        }
+        if (c1) {
+          const float one_m_w = 1.0f - w1;
+          T = __fdividef(T, one_m_w);
+          Tw1 = T * w1;
+          dt1 = T * (gam1 - Q) * G1;
+          Q = fmaf(w1, gam1, one_m_w * Q);
+        }
+        if (h == 0)
+          sA[b0 * kTilePixels + px] = Tw0;
+        else if (b1 >= 0)
+          sA[b1 * kTilePixels + px] = Tw1;
+        if (__any_sync(0xffffffffu, Tw0 != 0.0f)) used |= 1u << b0;
+        if (b1 >= 0 && __any_sync(0xffffffffu, Tw1 != 0.0f)) used |= 1u << b1;
+        // dL/dtau over the warp's 16 pixels: each half sums its own entry
+        float dv = h ? dt1 : dt0;
+        if (__any_sync(0xffffffffu, dv != 0.0f)) {
+          dv += __shfl_xor_sync(0xffffffffu, dv, 1);
+          dv += __shfl_xor_sync(0xffffffffu, dv, 2);
+          dv += __shfl_xor_sync(0xffffffffu, dv, 4);
+          dv += __shfl_xor_sync(0xffffffffu, dv, 8);
+          if (lane == 0) sTau[wp * kChunk + b0] = dv;
+          if (lane == 16 && b1 >= 0) sTau[wp * kChunk + b1] = dv;
+        }
       }
-      if (lane == 0) sMask[t >> 5] = used;
+      if (lane == 0) sMask[wp] = used;
     }
     __syncthreads();
-    // dL/ds[b][c] = sum_pixels A[b][p] g[p][c]: 4 x 8 block per thread over the
-    // pixels p = it*8 + slice, then a sum over the 8 slices.
+    // dL/ds[b][c] = sum_p A[b][p] g[p][c]: 4 x 8 block per thread over the
+    // pixels p = it*SL + slice, then a sum over the SL slices.
     {
       float acc[4][8];
 #pragma unroll
@@ -224,17 +329,18 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[x][c] = 0.0f;
       if (bb < nb) {
-        for (int it = 0; it < kTilePixels / 8; ++it) {
-          // pixels it*8 .. it*8+7 belong to warp it/4, which wrote only the
-          // entries of its mask: skip the group when none of b..b+3 is there
-          const unsigned wm = (sMask[it >> 2] >> bb) & 0xfu;
+        for (int it = 0; it < kTilePixels / S::SL; ++it) {
+          // pixels it*SL .. it*SL+SL-1 belong to warp (it*SL)/16, which wrote
+          // only the entries of its mask: skip the group when none of
+          // b..b+3 is there
+          const unsigned wm = (sMask[(it * S::SL) >> 4] >> bb) & 0xfu;
           if (!wm) continue;
-          const int p = it * 8 + slice;
+          const int p = it * S::SL + slice;
           float av[4];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) av[x] = (wm >> x) & 1u ? sA[(bb + x) * kPad + p] : 0.0f;
-          const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk]);
-          const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * kGStride + cbk + 4]);
+          for (int x = 0; x < 4; ++x) av[x] = (wm >> x) & 1u ? sA[(bb + x) * kTilePixels + p] : 0.0f;
+          const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * S::GS + cbk]);
+          const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * S::GS + cbk + 4]);
           const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
           for (int x = 0; x < 4; ++x)
@@ -247,9 +353,8 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           float y = acc[x][c];
-          y += __shfl_xor_sync(0xffffffffu, y, 4);
-          y += __shfl_xor_sync(0xffffffffu, y, 2);
-          y += __shfl_xor_sync(0xffffffffu, y, 1);
+#pragma unroll
+          for (int o = S::SL / 2; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
           acc[x][c] = y;
         }
       if (slice == 0) {
@@ -264,37 +369,44 @@ __global__ void __launch_bounds__(kTilePixels, 2) render_bwd_kernel(const Backwa
         }
       }
     }
-    // dL/dtau: sum over the tile's pixels for each Gaussian of the chunk; each
-    // column block adds the part of the gradient its columns carry
-    {
-      const int b = t >> 3, part = t & 7;
+    // dL/dtau: the warps' sums in order; each column block adds the part of
+    // the gradient its columns carry
+    if (t < nb) {
       float y = 0.0f;
-      if (b < nb)
-        for (int it = 0; it < kTilePixels / 8; ++it)
-          if ((sMask[it >> 2] >> b) & 1u) y += sT[b * kPad + it * 8 + part];
-      y += __shfl_xor_sync(0xffffffffu, y, 4);
-      y += __shfl_xor_sync(0xffffffffu, y, 2);
-      y += __shfl_xor_sync(0xffffffffu, y, 1);
-      if (part == 0 && b < nb && y != 0.0f) atomicAdd(&A.d_tau[sK[b]], y);
+#pragma unroll
+      for (int w = 0; w < S::kWarps; ++w) y += sTau[w * kChunk + t];
+      if (y != 0.0f) atomicAdd(&A.d_tau[sK[t]], y);
     }
   }
+  cp_async_wait_all();  // the cotangent copies when the tile has no chunk
+}
+
+template <int NB>
+static void launch_bwd_nb(const BackwardArgs& A, cudaStream_t s) {
+  const RenderArgs& a = A.f;
+  constexpr size_t smem = BwdShape<NB>::smem;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(render_bwd_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    configured = true;
+  }
+  dim3 grid(a.g.T, (a.ncols + NB - 1) / NB, a.M);
+  render_bwd_kernel<NB><<<grid, BwdShape<NB>::kThreads, smem, s>>>(A);
+  note_launches(1);
 }
 
 void launch_render_bwd(const BackwardArgs& A, int /*cols_per_cta*/, cudaStream_t s) {
   const RenderArgs& a = A.f;
   if (a.M <= 0 || a.ncols <= 0) return;
-  constexpr size_t smem = bwd_smem_bytes();
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(render_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    configured = true;
-  }
   bwd_prepass_kernel<<<dim3(a.g.T, 1, a.M), kTilePixels, 0, s>>>(a, A.tfin, A.stops, A.tile_stop);
   note_launches(1);
-  dim3 grid(a.g.T, (a.ncols + kBNB - 1) / kBNB, a.M);
-  render_bwd_kernel<<<grid, kTilePixels, smem, s>>>(A);
-  note_launches(1);
+  // radiance rows are padded to a multiple of 128 columns, so every block
+  // of 64 or 128 columns lies inside its row
+  if (a.ncols <= 64)
+    launch_bwd_nb<64>(A, s);
+  else
+    launch_bwd_nb<128>(A, s);
 }
 
 }  // namespace rxgs

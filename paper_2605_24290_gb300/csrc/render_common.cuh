@@ -15,6 +15,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
   const int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -55,14 +60,16 @@ struct Strip {
   int r0, r1, c0, c1;
 };
 
-__device__ __forceinline__ Strip warp_strip(const GridConst& g, int tr, int tc, int w) {
+// Pixels p0 .. p0+np-1 of a tile (row-major over TH x TW; np is 16 or 32
+// and divides or is a multiple of TW, which is 8, 16 or 32).
+__device__ __forceinline__ Strip pixel_strip(const GridConst& g, int tr, int tc, int p0, int np) {
   Strip s;
-  const int t0 = 32 * w, t1 = t0 + 31;
-  s.r0 = tr * g.TH + t0 / g.TW;
+  const int t1 = p0 + np - 1;
+  s.r0 = tr * g.TH + p0 / g.TW;
   s.r1 = tr * g.TH + t1 / g.TW;
-  if (g.TW >= 32) {
-    s.c0 = tc * g.TW + t0 % g.TW;
-    s.c1 = s.c0 + 31;
+  if (g.TW >= np) {
+    s.c0 = tc * g.TW + p0 % g.TW;
+    s.c1 = s.c0 + np - 1;
   } else {
     s.c0 = tc * g.TW;
     s.c1 = s.c0 + g.TW - 1;
@@ -70,6 +77,10 @@ __device__ __forceinline__ Strip warp_strip(const GridConst& g, int tr, int tc, 
   if (s.r1 > g.H - 1) s.r1 = g.H - 1;
   if (s.c1 > g.W - 1) s.c1 = g.W - 1;
   return s;
+}
+
+__device__ __forceinline__ Strip warp_strip(const GridConst& g, int tr, int tc, int w) {
+  return pixel_strip(g, tr, tc, 32 * w, 32);
 }
 
 // Does a footprint (record word r1: rows i_lo..i_hi, columns j_lo..j_lo+span

@@ -111,11 +111,12 @@ def test_backward_csi_and_rssi_cotangents(torch, rx, oracle):
     assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
 
 
-def test_backward_through_mlp(torch, rx, oracle):
+@pytest.mark.parametrize("N,C", [(8, 1), (8, 3), (40, 2), (6, 4)])
+def test_backward_through_mlp(torch, rx, oracle, N, C):
     """Cotangent on spectra through the conditioning MLP to phi_base, the MLP
-    parameters and the opacity."""
-    rng = np.random.default_rng(203)
-    K, M, N, C = 3000, 2, 8, 1
+    parameters and the opacity (N * 2C columns: one or two column blocks)."""
+    rng = np.random.default_rng(203 + 10 * C + N)
+    K, M = 3000, 2
     sc = S.draw_scene(rng, K)
     tx, rxp = S.draw_points(rng, M), S.draw_points(rng, N)
     base = S.draw_base(rng, K, C)
