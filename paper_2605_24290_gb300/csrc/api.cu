@@ -116,7 +116,8 @@ int pick_cols(const rxgs_ctx* ctx, int ncols) {
   if (ctx->opts.cols_per_cta) return ctx->opts.cols_per_cta;
   if (ncols <= 16) return 16;
   if (ncols <= 32) return 32;
-  return 64;
+  if (ncols <= 64) return 64;
+  return 128;
 }
 
 bool lookup_views(void* c, uint64_t views, ViewsRef* out, const char** err) {

@@ -10,15 +10,21 @@
 
 namespace rxgs {
 
+// 128-column blocks run with two threads per pixel (512 threads).
 template <int NB>
-__global__ void __launch_bounds__(kTilePixels, NB >= 128 ? 1 : 2)
+constexpr int fwd_tpp() {
+  return NB >= 128 ? 2 : 1;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(fwd_tpp<NB>() * kTilePixels, NB >= 128 ? 1 : 2)
     render_fwd_kernel(const RenderArgs a) {
-  using S = FwdShape<NB>;
+  using S = FwdShape<NB, fwd_tpp<NB>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sA = reinterpret_cast<float*>(smem_raw);              // [kChunk][256]
   float* sR = sA + kChunk * kTilePixels;                        // [kChunk][NB]
   float4* sRec = reinterpret_cast<float4*>(sR + 2 * kChunk * NB);  // [2][kChunk][2]
-  __shared__ float sRed[kTilePixels / 32][8];
+  __shared__ float sRed[S::kThreads / 32][8];
   TileJob job;
   job.v = blockIdx.z;
   job.tile = blockIdx.x;
@@ -28,12 +34,12 @@ __global__ void __launch_bounds__(kTilePixels, NB >= 128 ? 1 : 2)
   job.out_rx0 = job.v * a.N;
   job.partial_row =
       a.partial ? a.partial + (static_cast<size_t>(job.v) * a.g.T + job.tile) * a.ncols : nullptr;
-  render_tile<NB>(a, job, sA, sR, sRec, sRed);
+  render_tile<NB, fwd_tpp<NB>()>(a, job, sA, sR, sRec, sRed);
 }
 
 template <int NB>
 static void launch_fwd_nb(const RenderArgs& a, cudaStream_t s) {
-  using S = FwdShape<NB>;
+  using S = FwdShape<NB, fwd_tpp<NB>()>;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(render_fwd_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -41,7 +47,7 @@ static void launch_fwd_nb(const RenderArgs& a, cudaStream_t s) {
     configured = true;
   }
   dim3 grid(a.g.T, (a.ncols + NB - 1) / NB, a.M);
-  render_fwd_kernel<NB><<<grid, kTilePixels, S::smem, s>>>(a);
+  render_fwd_kernel<NB><<<grid, S::kThreads, S::smem, s>>>(a);
   note_launches(1);
 }
 

@@ -14,17 +14,25 @@
 //            register-tiled (NB/8 pixels x 8 columns per thread).
 // The radiance rows of the chunk are copied with cp.async while phase A
 // runs.  The tile stops as soon as every pixel has T < eps.
+//
+// With TPP = 2 the CTA has 512 threads, two per pixel (lanes l and l + 16
+// of a warp; a warp covers a 16-pixel strip): in phase A the two threads of
+// a pixel evaluate the weights of alternate marked Gaussians, exchange them
+// by shuffles and both apply the (cheap, sequential) transmittance updates,
+// so a wide column block costs one weight evaluation per (pixel, Gaussian).
 #pragma once
 #include "render_common.cuh"
 #include "rxgs_internal.h"
 
 namespace rxgs {
 
-template <int NB>
+template <int NB, int TPP = 1>
 struct FwdShape {
+  static constexpr int kThreads = TPP * kTilePixels;
+  static constexpr int SP = 32 / TPP;             // pixels per warp strip
   static constexpr int CG = NB / 8;               // column groups (8 columns each)
-  static constexpr int PG = kTilePixels / CG;     // pixel groups
-  static constexpr int PX = kTilePixels / PG;     // pixels per thread (= NB/8)
+  static constexpr int PG = kThreads / CG;        // pixel groups
+  static constexpr int PX = kTilePixels / PG;     // pixels per thread
   static constexpr size_t smem = sizeof(float) * (kChunk * kTilePixels + 2 * kChunk * NB) +
                                  sizeof(float4) * 2 * 2 * kChunk;
 };
@@ -38,22 +46,25 @@ struct TileJob {
   float* partial_row;
 };
 
-template <int NB>
+template <int NB, int TPP = 1>
 __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& job, float* sA,
                                             float* sR, float4* sRec, float (*sRed)[8]) {
-  using S = FwdShape<NB>;
+  using S = FwdShape<NB, TPP>;
   const GridConst& g = a.g;
   const int t = threadIdx.x;
+  const int lane = t & 31, wp = t >> 5;
+  const int h = TPP == 2 ? lane >> 4 : 0;              // which thread of the pixel
+  const int px = TPP == 2 ? wp * 16 + (lane & 15) : t;  // this thread's pixel
   const int tile = job.tile, v = job.v;
   const int col0 = job.col0;
   const int tr = tile / g.tiles_w, tc = tile % g.tiles_w;
-  const int i = tr * g.TH + t / g.TW, jj = tc * g.TW + t % g.TW;
+  const int i = tr * g.TH + px / g.TW, jj = tc * g.TW + px % g.TW;
   const bool valid = i < g.H && jj < g.W;
   const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
   const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
   const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
   const float* radv = a.rad + job.col_base;
-  __shared__ unsigned sMask[kTilePixels / 32];  // per warp: chunk entries meeting its strip
+  __shared__ unsigned sMask[S::kThreads / 32];  // per warp: chunk entries meeting its strip
 
   const int pg = t % S::PG, cg = t / S::PG;
   float acc[S::PX][8];
@@ -79,7 +90,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
       cp_async16(&rb[2 * t + 1], &rec[2 * k + 1], ok);
     }
     constexpr int Q = NB / 4;  // float4 per row slice
-    for (int e = t; e < kChunk * Q; e += kTilePixels) {
+    for (int e = t; e < kChunk * Q; e += S::kThreads) {
       const int b = e / Q, q4 = e % Q;
       const bool ok = b < nb;
       const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
@@ -107,9 +118,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
     // pixel strip (one Gaussian per lane, then a ballot) and walks only
     // those, two at a time: their weights are independent, only the T
     // updates are sequential, in list order.
-    {
-      const Strip strip = warp_strip(g, tr, tc, t >> 5);
-      const int lane = t & 31;
+    if (TPP == 1) {
+      const Strip strip = warp_strip(g, tr, tc, wp);
       const bool rel = lane < nb && touches_strip(g, sRecC[2 * lane + 1], strip);
       const unsigned mask = __ballot_sync(0xffffffffu, rel);
       // walk the marked entries while some pixel of the strip is alive; the
@@ -146,12 +156,55 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
         if (__any_sync(0xffffffffu, Tw0 != 0.0f)) used |= 1u << b0;
         if (b1 >= 0 && __any_sync(0xffffffffu, Tw1 != 0.0f)) used |= 1u << b1;
       }
-      if (lane == 0) sMask[t >> 5] = used;
+      if (lane == 0) sMask[wp] = used;
+    } else {
+      // two threads per pixel: the lower half of the warp evaluates b0, the
+      // upper half b1; both apply the updates in list order
+      const Strip strip = pixel_strip(g, tr, tc, wp * 16, 16);
+      const bool rel = lane < nb && touches_strip(g, sRecC[2 * lane + 1], strip);
+      const unsigned mask = __ballot_sync(0xffffffffu, rel);
+      unsigned m = __any_sync(0xffffffffu, alive) ? mask : 0u;
+      unsigned used = 0;
+      const int src0 = lane & 15, src1 = src0 | 16;
+      while (m) {
+        const int b0 = __ffs(m) - 1;
+        m &= m - 1;
+        const int b1 = m ? __ffs(m) - 1 : -1;
+        if (b1 >= 0) m &= m - 1;
+        const int bm = h ? b1 : b0;
+        float wm = 0.0f, G;
+        bool cm = false;
+        if (alive && bm >= 0) cm = pixel_weight(g, sRecC[2 * bm], sRecC[2 * bm + 1], i, jj, fi, fj, &wm, &G);
+        const float w0 = __shfl_sync(0xffffffffu, wm, src0);
+        const float w1 = __shfl_sync(0xffffffffu, wm, src1);
+        const bool c0 = __shfl_sync(0xffffffffu, static_cast<int>(cm), src0) != 0;
+        const bool c1 = __shfl_sync(0xffffffffu, static_cast<int>(cm), src1) != 0;
+        float Tw0 = 0.0f, Tw1 = 0.0f;
+        if (alive && c0) {
+          Tw0 = __fmul_rn(T, w0);
+          T = __fmul_rn(T, __fsub_rn(1.0f, w0));
+          ++ncon;
+          if (T < g.eps_T) alive = false;
+        }
+        if (alive && c1) {
+          Tw1 = __fmul_rn(T, w1);
+          T = __fmul_rn(T, __fsub_rn(1.0f, w1));
+          ++ncon;
+          if (T < g.eps_T) alive = false;
+        }
+        if (h == 0)
+          sA[b0 * kTilePixels + px] = Tw0;
+        else if (b1 >= 0)
+          sA[b1 * kTilePixels + px] = Tw1;
+        if (__any_sync(0xffffffffu, Tw0 != 0.0f)) used |= 1u << b0;
+        if (b1 >= 0 && __any_sync(0xffffffffu, Tw1 != 0.0f)) used |= 1u << b1;
+      }
+      if (lane == 0) sMask[wp] = used;
     }
     const int n_alive = __syncthreads_count(alive);
     // ---- phase B: acc[p][c] += A[b][p] * s[b][c] over the (Gaussian, pixel
     // strip) pairs marked in phase A; pixel group p of this thread lies in
-    // the strip(s) of warps [p*PG/32, (p+1)*PG/32).
+    // the strip(s) of warps [p*PG/SP, (p+1)*PG/SP) (SP pixels per strip).
     {
       // pmask: union over the warps of group p (uniform, for skipping);
       // own: the mask of the warp that wrote this thread's pixel of group p
@@ -161,14 +214,14 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
 #pragma unroll
       for (int p = 0; p < S::PX; ++p) {
         unsigned mm = 0;
-        if (S::PG >= 32) {
+        if (S::PG >= S::SP) {
 #pragma unroll
-          for (int q = 0; q < S::PG / 32; ++q) mm |= sMask[p * (S::PG / 32) + q];
+          for (int q = 0; q < S::PG / S::SP; ++q) mm |= sMask[p * (S::PG / S::SP) + q];
         } else {
-          mm = sMask[(p * S::PG) / 32];
+          mm = sMask[(p * S::PG) / S::SP];
         }
         pmask[p] = mm;
-        own[p] = sMask[(p * S::PG + pg) >> 5];
+        own[p] = sMask[(p * S::PG + pg) / S::SP];
         any |= mm;
       }
       while (any) {
@@ -197,7 +250,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
 
   // ---- epilogue
   const size_t HW = static_cast<size_t>(g.H) * g.W;
-  if (col0 == 0 && valid) {
+  if (col0 == 0 && valid && h == 0) {
     const size_t o = static_cast<size_t>(v) * HW + static_cast<size_t>(i) * g.W + jj;
     if (a.ncontrib) a.ncontrib[o] = ncon;
     if (a.tfinal) a.tfinal[o] = T;
