@@ -295,9 +295,12 @@ __global__ void __launch_bounds__(256) mlp_weighted_kernel(
   }
 }
 
+size_t mlp_weighted_tc_extra_floats(int C);
+
 size_t mlp_weighted_tmp_floats(int M, int K, int N, int C) {
   const size_t nchunks = (K + kMwChunk - 1) / kMwChunk;
-  return nchunks * N * static_cast<size_t>(M) * 2 * C;
+  // chunk partials, plus room for packed tensor-core weight fragments
+  return nchunks * N * static_cast<size_t>(M) * 2 * C + mlp_weighted_tc_extra_floats(C);
 }
 
 template <int MAXC2, int MAXV>
@@ -359,17 +362,22 @@ namespace rxgs {
 // --------------------------- bf16 MLP on tensor cores, fused with the sum
 // Same result as mlp_weighted in bf16 mode (inputs, weights and hidden
 // activations rounded to bf16, float32 accumulation), with the output layer
-// [16 pairs x 64] x [64 x 4C] on warp-level tensor-core MMAs
-// (mma.sync m16n8k16 bf16 -> f32).  Block (chunk of Gaussians, receiver j):
-//   1. the chunk's Gaussians with W[v][k] != 0 are compacted into a list;
-//   2. each warp takes 16 listed Gaussians at a time: lanes compute the
-//      hidden layer (bf16) into shared memory, then the MMAs produce the
-//      local (alpha, beta) of every channel, and lanes holding alpha combine
-//      them with beta (from the neighbour lane), phi_base and the global
-//      branch into s, accumulating W s per channel;
+// [16 Gaussians x 64] x [64 x 4C] on warp-level tensor-core MMAs
+// (mma.sync m16n8k16 bf16 -> f32).  A pack kernel lays W2^T out once per
+// call as the MMA's B fragments (bf16 pairs); every block copies them to
+// shared memory.  Block (chunk of 4096 Gaussians, receiver j), each warp a
+// 512-Gaussian segment of the chunk:
+//   1. the warp compacts its segment's Gaussians with W[v][k] != 0 (ballots
+//      over coalesced reads, ascending k);
+//   2. 16 listed Gaussians at a time: lanes compute the hidden layer (bf16)
+//      into shared memory, the MMAs produce the local (alpha, beta) of every
+//      channel, and lanes holding alpha combine them with beta (from the
+//      neighbour lane), phi_base and the global branch into s, accumulating
+//      W s per channel;
 //   3. lanes, then warps, are summed in a fixed order into part[chunk][j].
 constexpr int kTcMaxNT = 26;  // 8-wide output tiles: 4C <= 208, C <= 52
 constexpr int kTcHStride = 72;
+constexpr int kTcSeg = kMwChunk / 8;  // Gaussians per warp segment
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -385,12 +393,35 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+static int tc_tiles(int C) { return (4 * C + 7) / 8; }
+static size_t tc_pack_words(int C) { return static_cast<size_t>(tc_tiles(C)) * 4 * 32 * 2; }
+
+// B fragments of W2^T (element (k, n) = W2[n][k]), [NT][4 k-steps][32 lanes][2]
+__global__ void mlp_pack_w2_kernel(const float* __restrict__ P, int C, uint32_t* __restrict__ out) {
+  constexpr int H = 64;
+  const int n4 = 4 * C, NT = (n4 + 7) / 8;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NT * 4 * 32) return;
+  const float* W2 = P + (H * 3 + H + n4 * H + n4) + H * 7;
+  const int nt = e / 128, ks = (e / 32) % 4, l = e % 32;
+  const int n = nt * 8 + (l >> 2), k0 = ks * 16 + (l & 3) * 2;
+  float w[4] = {0.f, 0.f, 0.f, 0.f};
+  if (n < n4) {
+    w[0] = W2[n * H + k0];
+    w[1] = W2[n * H + k0 + 1];
+    w[2] = W2[n * H + k0 + 8];
+    w[3] = W2[n * H + k0 + 9];
+  }
+  out[2 * e + 0] = pack_bf16(w[0], w[1]);
+  out[2 * e + 1] = pack_bf16(w[2], w[3]);
+}
+
 __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
-    const float* __restrict__ P, int C, const float* __restrict__ rx,
-    const float4* __restrict__ geom, const float* __restrict__ base, int K,
-    const float* __restrict__ W, int v0, const int* __restrict__ rx_view,
-    const float* __restrict__ glob, int Mpart, const int* __restrict__ n_dev,
-    float* __restrict__ part) {
+    const float* __restrict__ P, int C, const uint32_t* __restrict__ packed,
+    const float* __restrict__ rx, const float4* __restrict__ geom,
+    const float* __restrict__ base, int K, const float* __restrict__ W, int v0,
+    const int* __restrict__ rx_view, const float* __restrict__ glob, int Mpart,
+    const int* __restrict__ n_dev, float* __restrict__ part) {
   constexpr int H = 64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n4 = 4 * C, NT = (n4 + 7) / 8;
@@ -400,28 +431,16 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
   float* sB2 = sB1 + H;                                                 // [NT*8]
   float* sG = sB2 + NT * 8;                                             // [4C] global branch
   __nv_bfloat16* sH = reinterpret_cast<__nv_bfloat16*>(sG + n4);         // [8 warps][16][72]
-  int* sList = reinterpret_cast<int*>(sH + 8 * 16 * kTcHStride);         // [kMwChunk]
-  __shared__ int sCount;
-  __shared__ int sWarpOff[8];
+  int* sList = reinterpret_cast<int*>(sH + 8 * 16 * kTcHStride);         // [8 warps][512]
   __shared__ float sRed[8][2 * 52];
   const int j = blockIdx.y, chunk = blockIdx.x;
   if (n_dev && j >= *n_dev) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int off_l = H * 3 + H + n4 * H + n4;  // l_w1 in the flat parameters
-  const float* W2 = P + off_l + H * 7;
-  // B fragments of W2^T: element (k, n) = W2[n][k]
-  for (int e = t; e < NT * 4 * 32; e += 256) {
-    const int nt = e / 128, ks = (e / 32) % 4, l = e % 32;
-    const int n = nt * 8 + (l >> 2), k0 = ks * 16 + (l & 3) * 2;
-    float w[4] = {0.f, 0.f, 0.f, 0.f};
-    if (n < n4) {
-      w[0] = W2[n * H + k0];
-      w[1] = W2[n * H + k0 + 1];
-      w[2] = W2[n * H + k0 + 8];
-      w[3] = W2[n * H + k0 + 9];
-    }
-    sBf[2 * e + 0] = pack_bf16(w[0], w[1]);
-    sBf[2 * e + 1] = pack_bf16(w[2], w[3]);
+  {
+    const int n16 = NT * 4 * 32 * 2 / 4;  // 16-byte pieces of the packed fragments
+    for (int e = t; e < n16; e += 256) cp_async16(&sBf[4 * e], &packed[4 * e], true);
+    cp_async_commit();
   }
   for (int e = t; e < H * 6; e += 256) sW1[e] = __bfloat162float(__float2bfloat16_rn(P[off_l + e]));
   for (int e = t; e < H; e += 256) sB1[e] = P[off_l + H * 6 + e];
@@ -429,47 +448,28 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
   for (int e = t; e < n4; e += 256) sG[e] = glob[static_cast<size_t>(j) * n4 + e];
   const int vj = rx_view ? rx_view[j] : v0;
   const float* Wv = W + static_cast<size_t>(vj) * K;
-  // ---- compaction of the chunk's non-zero weights (ordered)
-  const int k0 = chunk * kMwChunk, k1 = min(K, k0 + kMwChunk);
-  constexpr int kPer = kMwChunk / 256;
-  int cnt = 0;
-  for (int q = 0; q < kPer; ++q) {
-    const int k = k0 + t * kPer + q;
-    cnt += (k < k1 && Wv[k] != 0.0f);
+  // ---- per-warp compaction of the segment's non-zero weights (ascending k)
+  int* wl = sList + warp * kTcSeg;
+  const int s0 = chunk * kMwChunk + warp * kTcSeg;
+  int nact = 0;
+#pragma unroll 4
+  for (int r = 0; r < kTcSeg / 32; ++r) {
+    const int k = s0 + r * 32 + lane;
+    const bool nz = k < K && Wv[k] != 0.0f;
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (nz) wl[nact + __popc(bal & ((1u << lane) - 1u))] = k;
+    nact += __popc(bal);
   }
-  int inc = cnt;  // inclusive scan over the warp
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) sWarpOff[warp] = inc;
+  cp_async_wait_all();
   __syncthreads();
-  if (t == 0) {
-    int run = 0;
-    for (int w = 0; w < 8; ++w) {
-      const int c = sWarpOff[w];
-      sWarpOff[w] = run;
-      run += c;
-    }
-    sCount = run;
-  }
-  __syncthreads();
-  int pos = sWarpOff[warp] + inc - cnt;
-  for (int q = 0; q < kPer; ++q) {
-    const int k = k0 + t * kPer + q;
-    if (k < k1 && Wv[k] != 0.0f) sList[pos++] = k;
-  }
-  __syncthreads();
-  const int nact = sCount;
-  // ---- 16-Gaussian tiles per warp
+  // ---- 16-Gaussian tiles of the warp's list
   const float rxj = rx[3 * j], ryj = rx[3 * j + 1], rzj = rx[3 * j + 2];
   const int g = lane >> 2, tig = lane & 3;
   float acc[kTcMaxNT][2];
 #pragma unroll
   for (int nt = 0; nt < kTcMaxNT; ++nt) acc[nt][0] = acc[nt][1] = 0.0f;
   __nv_bfloat16* hW = sH + warp * 16 * kTcHStride;
-  for (int tile = warp; tile * 16 < nact; tile += 8) {
+  for (int tile = 0; tile * 16 < nact; ++tile) {
     // hidden layer: lane computes units [32*half, 32*half + 32) of row r
     {
       const int r = lane & 15, half = lane >> 4;
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
       float x[4] = {0.f, 0.f, 0.f, 0.f};
       const bool ok = li < nact;
       if (ok) {
-        const float4 p = geom[3 * sList[li]];
+        const float4 p = geom[3 * wl[li]];
         const float vx = rxj - p.x, vy = ryj - p.y, vz = rzj - p.z;
         const float d = sqrtf(vx * vx + vy * vy + vz * vz);
         const float inv = 1.0f / d;
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
     }
     __syncwarp();  // hW is rewritten by the next tile
     const int la = tile * 16 + g, lb = la + 8;
-    const int ka = la < nact ? sList[la] : -1, kb = lb < nact ? sList[lb] : -1;
+    const int ka = la < nact ? wl[la] : -1, kb = lb < nact ? wl[lb] : -1;
     const float wa = ka >= 0 ? Wv[ka] : 0.0f, wb = kb >= 0 ? Wv[kb] : 0.0f;
 #pragma unroll
     for (int nt = 0; nt < kTcMaxNT; ++nt) {
@@ -517,8 +517,8 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
       float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t* bp = sBf + ((nt * 4 + ks) * 32 + lane) * 2;
-        mma_bf16_16816(d, af[ks], bp[0], bp[1]);
+        const uint2 bp = *reinterpret_cast<const uint2*>(&sBf[((nt * 4 + ks) * 32 + lane) * 2]);
+        mma_bf16_16816(d, af[ks], bp.x, bp.y);
       }
       const int col = nt * 8 + tig * 2;
       d[0] += sB2[col];
@@ -535,17 +535,15 @@ __global__ void __launch_bounds__(256, 2) mlp_weighted_tc_kernel(
         const float agr = 1.0f + sG[4 * ch + 0], agi = sG[4 * ch + 1];
         const float bgr = sG[4 * ch + 2], bgi = sG[4 * ch + 3];
         if (ka >= 0) {
-          const float pr = base[(static_cast<size_t>(ka) * C + ch) * 2 + 0];
-          const float pi = base[(static_cast<size_t>(ka) * C + ch) * 2 + 1];
-          const float ur = agr * pr - agi * pi + bgr, ui = agr * pi + agi * pr + bgi;
+          const float2 ph = *reinterpret_cast<const float2*>(&base[(static_cast<size_t>(ka) * C + ch) * 2]);
+          const float ur = agr * ph.x - agi * ph.y + bgr, ui = agr * ph.y + agi * ph.x + bgi;
           const float alr = 1.0f + d[0], ali = d[1];
           acc[nt][0] = fmaf(wa, alr * ur - ali * ui + b0, acc[nt][0]);
           acc[nt][1] = fmaf(wa, alr * ui + ali * ur + b1, acc[nt][1]);
         }
         if (kb >= 0) {
-          const float pr = base[(static_cast<size_t>(kb) * C + ch) * 2 + 0];
-          const float pi = base[(static_cast<size_t>(kb) * C + ch) * 2 + 1];
-          const float ur = agr * pr - agi * pi + bgr, ui = agr * pi + agi * pr + bgi;
+          const float2 ph = *reinterpret_cast<const float2*>(&base[(static_cast<size_t>(kb) * C + ch) * 2]);
+          const float ur = agr * ph.x - agi * ph.y + bgr, ui = agr * ph.y + agi * ph.x + bgi;
           const float alr = 1.0f + d[2], ali = d[3];
           acc[nt][0] = fmaf(wb, alr * ur - ali * ui + b2, acc[nt][0]);
           acc[nt][1] = fmaf(wb, alr * ui + ali * ur + b3, acc[nt][1]);
@@ -585,26 +583,37 @@ size_t mlp_weighted_tc_smem(int C) {
          sizeof(__nv_bfloat16) * 8 * 16 * kTcHStride + sizeof(int) * kMwChunk;
 }
 
+// Wide spectra through tensor cores (bf16 MLPs with 4 < C <= 52).  The
+// packed W2^T fragments sit at the start of tmp, the chunk partials after.
+bool mlp_weighted_uses_tc(const MlpParams& m) { return m.bf16 && m.C > 4 && m.C <= 52; }
+
 bool launch_mlp_weighted_tc(const MlpParams& m, const float* rx, int N, const float4* geom,
                             const float* base, int K, const float* W, int M, const int* rx_view,
                             const float* glob, float* tmp, float* csi, float* rssi,
                             const int* n_dev, cudaStream_t s) {
-  if (!m.bf16 || m.C <= 4 || m.C > 52) return false;  // narrow spectra: multi-view SIMT kernel
+  if (!mlp_weighted_uses_tc(m)) return false;
+  uint32_t* packed = reinterpret_cast<uint32_t*>(tmp);
+  float* part = tmp + tc_pack_words(m.C);
+  const int nfrag = tc_tiles(m.C) * 4 * 32;
+  mlp_pack_w2_kernel<<<(nfrag + 255) / 256, 256, 0, s>>>(m.p, m.C, packed);
+  note_launches(1);
   const int Mpart = rx_view ? 1 : M;
   const int nchunks = (K + kMwChunk - 1) / kMwChunk;
   const size_t smem = mlp_weighted_tc_smem(m.C);
   cudaFuncSetAttribute(mlp_weighted_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(smem));
   for (int v0 = 0; v0 < (rx_view ? 1 : M); ++v0) {
-    mlp_weighted_tc_kernel<<<dim3(nchunks, N), 256, smem, s>>>(m.p, m.C, rx, geom, base, K, W, v0,
-                                                               rx_view, glob, Mpart, n_dev, tmp);
+    mlp_weighted_tc_kernel<<<dim3(nchunks, N), 256, smem, s>>>(
+        m.p, m.C, packed, rx, geom, base, K, W, v0, rx_view, glob, Mpart, n_dev, part);
     note_launches(1);
   }
   const int n = Mpart * N * m.C;
-  weighted_sum_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(tmp, nchunks, N, Mpart, m.C, csi,
+  weighted_sum_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(part, nchunks, N, Mpart, m.C, csi,
                                                              rssi);
   note_launches(1);
   return true;
 }
+
+size_t mlp_weighted_tc_extra_floats(int C) { return tc_pack_words(C); }
 
 }  // namespace rxgs
