@@ -56,19 +56,19 @@ def peaks():
 # from the committed ncu capture (profiles/render_kernels_*_full.md), valid
 # only while the kernel sources hash to the value recorded at capture time.
 NCU_TRAFFIC = {
-    "render_fwd": {"bytes": 26_906_880 + 476_077_568, "tile": [16, 16],
-                   "files": ["render_fwd.cu", "render_tile.cuh", "render_common.cuh", "rxgs_math.cuh"],
-                   "sha1": "7b00d89e342f7dd3"},
-    "render_bwd": {"bytes": 568_947_456 + 8_235_776, "tile": [16, 16],
-                   "files": ["render_bwd.cu", "render_common.cuh", "rxgs_math.cuh"],
-                   "sha1": "cc8d90c17f2a61fa"},
+    "render_fwd": {"bytes": 26_776_064 + 476_146_176, "tile": [16, 16], "cols": 128,
+                   "files": ['render_fwd.cu', 'render_tile.cuh', 'render_common.cuh', 'rxgs_math.cuh'],
+                   "sha1": "f3977881eec78516"},
+    "render_bwd": {"bytes": 567_493_120 + 7_951_872, "tile": [16, 16], "cols": 128,
+                   "files": ['render_bwd.cu', 'render_common.cuh', 'rxgs_math.cuh'],
+                   "sha1": "b14af49ac801b8a1"},
 }
 
 
-def ncu_traffic(kernel, tile):
+def ncu_traffic(kernel, tile, cols):
     import hashlib
     e = NCU_TRAFFIC.get(kernel)
-    if not e or list(tile) != e["tile"]:
+    if not e or list(tile) != e["tile"] or cols != e["cols"]:
         return None
     m = hashlib.sha1()
     for f in e["files"]:
@@ -268,6 +268,8 @@ def gpu_bench(args):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak = fp32_alu_peak_tflops(sm_mhz)
     tile = tune["chosen"]["tile"] if tune else [16, 16]
+    # column block of the forward (the backward always takes 128 for 128 columns)
+    cols = tune["chosen"]["cols"] if tune else (128 if 2 * W.N * W.C > 64 else 64)
 
     def roofline(kernel, flops_per_pair, what):
         if kernel not in stages:
@@ -275,7 +277,7 @@ def gpu_bench(args):
         kms = stages[kernel]["ms"] / stages[kernel]["calls"]
         ach = P * flops_per_pair / (kms / 1e3) / 1e12
         return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(kernel, tile),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(kernel, tile, cols if kernel == "render_fwd" else 128),
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
                 "units": f"{P} composited (pixel, Gaussian) pairs x {what} flops",
                 "launch_ms": round(kms, 4)}

@@ -747,8 +747,12 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.tile_stop = tstop;
   A.n_inst = v->n_inst;
   {
+    Stage sg(ctx, "bwd_prepass", st);
+    launch_bwd_prepass(A, st);
+  }
+  {
     Stage sg(ctx, "render_bwd", st);
-    launch_render_bwd(A, 32, st);
+    launch_render_bwd(A, st);
   }
   if (d->radiance) {
     Stage sg(ctx, "radiance_grad", st);

@@ -396,11 +396,16 @@ static void launch_bwd_nb(const BackwardArgs& A, cudaStream_t s) {
   note_launches(1);
 }
 
-void launch_render_bwd(const BackwardArgs& A, int /*cols_per_cta*/, cudaStream_t s) {
+void launch_bwd_prepass(const BackwardArgs& A, cudaStream_t s) {
   const RenderArgs& a = A.f;
   if (a.M <= 0 || a.ncols <= 0) return;
   bwd_prepass_kernel<<<dim3(a.g.T, 1, a.M), kTilePixels, 0, s>>>(a, A.tfin, A.stops, A.tile_stop);
   note_launches(1);
+}
+
+void launch_render_bwd(const BackwardArgs& A, cudaStream_t s) {
+  const RenderArgs& a = A.f;
+  if (a.M <= 0 || a.ncols <= 0) return;
   // radiance rows are padded to a multiple of 128 columns, so every block
   // of 64 or 128 columns lies inside its row
   if (a.ncols <= 64)

@@ -130,7 +130,10 @@ struct BackwardArgs {
   uint32_t* tile_stop;        // scratch [M][T]: largest stop of each tile
   uint32_t n_inst;
 };
-void launch_render_bwd(const BackwardArgs& a, int cols_per_cta, cudaStream_t s);
+// Walk 1 of the backward (final T and stop per pixel, largest stop per tile)
+void launch_bwd_prepass(const BackwardArgs& a, cudaStream_t s);
+// Walk 2: the back-to-front sweep producing d_rad and d_tau
+void launch_render_bwd(const BackwardArgs& a, cudaStream_t s);
 
 // ------------------------------------------ visibility weights (Eq. render_reorder)
 // W[M][K] = sum over each view's pixels of T_k w_k (zeroed first).
