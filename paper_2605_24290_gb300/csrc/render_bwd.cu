@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
                                                                   float* __restrict__ tfin,
                                                                   uint32_t* __restrict__ stops,
                                                                   uint32_t* __restrict__ tile_stop) {
-  __shared__ float4 sRec[2 * kChunk];
+  __shared__ float4 sRec[2][2 * kChunk];
+  __shared__ uint32_t sIdx[3 * kChunk];
   __shared__ unsigned sStop;
   const GridConst& g = a.g;
   const int t = threadIdx.x;
@@ -48,27 +49,55 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
   float T = 1.0f;
   uint32_t stop = valid ? rg.y : rg.x;
   bool alive = valid;
-  for (uint32_t start = rg.x; start < rg.y; start += kChunk) {
-    const int nb = min(kChunk, static_cast<int>(rg.y - start));
-    __syncthreads();
+  // the same copy pipeline as the forward: records of chunk n + 1 and
+  // indices of chunk n + 2 in flight while chunk n is walked
+  const int nchunks = static_cast<int>((rg.y - rg.x + kChunk - 1) / kChunk);
+  auto chunk_len = [&](int n) {
+    return min(kChunk, static_cast<int>(rg.y - rg.x - static_cast<uint32_t>(n) * kChunk));
+  };
+  auto copy_indices = [&](int n) {
+    const bool ok = t < chunk_len(n);
+    if (t < kChunk)
+      cp_async4(&sIdx[(n % 3) * kChunk + t], ok ? &a.vals[rg.x + n * kChunk + t] : a.vals, ok);
+  };
+  auto gather = [&](int n) {
     if (t < kChunk) {
-      const bool ok = t < nb;
-      const uint32_t k = ok ? a.vals[start + t] : 0u;
-      cp_async16(&sRec[2 * t + 0], &rec[2 * k + 0], ok);
-      cp_async16(&sRec[2 * t + 1], &rec[2 * k + 1], ok);
+      const bool ok = t < chunk_len(n);
+      const uint32_t k = ok ? sIdx[(n % 3) * kChunk + t] : 0u;
+      cp_async16(&sRec[n & 1][2 * t + 0], &rec[2 * k + 0], ok);
+      cp_async16(&sRec[n & 1][2 * t + 1], &rec[2 * k + 1], ok);
     }
+  };
+  if (nchunks > 0) {
+    copy_indices(0);
     cp_async_commit();
+    if (nchunks > 1) copy_indices(1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    gather(0);
+    cp_async_commit();
+  }
+  for (int n = 0; n < nchunks; ++n) {
+    const uint32_t start = rg.x + static_cast<uint32_t>(n) * kChunk;
+    const int nb = chunk_len(n);
     cp_async_wait_all();
     __syncthreads();
+    if (n + 1 < nchunks) {
+      if (n + 2 < nchunks) copy_indices(n + 2);
+      gather(n + 1);
+    }
+    cp_async_commit();
+    const float4* sR = sRec[n & 1];
     {
       const int lane = t & 31;
-      const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
+      const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
       while (alive && m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
         float w, G;
-        if (pixel_weight(g, sRec[2 * b], sRec[2 * b + 1], i, jj, fi, fj, &w, &G)) {
+        if (pixel_weight(g, sR[2 * b], sR[2 * b + 1], i, jj, fi, fj, &w, &G)) {
           T = __fmul_rn(T, __fsub_rn(1.0f, w));
           if (T < g.eps_T) {
             alive = false;
@@ -79,6 +108,7 @@ __global__ void __launch_bounds__(kTilePixels) bwd_prepass_kernel(const RenderAr
     }
     if (__syncthreads_count(alive) == 0) break;
   }
+  cp_async_wait_all();  // a prefetch may still be in flight
   atomicMax(&sStop, stop);
   if (valid) {
     const size_t o = static_cast<size_t>(v) * g.H * g.W + static_cast<size_t>(i) * g.W + jj;
@@ -113,7 +143,7 @@ struct BwdShape {
   // cotangent rows, T w, two radiance / record / index buffers, dtau sums
   static constexpr size_t smem =
       sizeof(float) * (kTilePixels * GS + kChunk * kTilePixels + 2 * kChunk * NB + kWarps * kChunk) +
-      sizeof(float4) * 2 * 2 * kChunk + sizeof(uint32_t) * 2 * kChunk;
+      sizeof(float4) * 2 * 2 * kChunk + sizeof(uint32_t) * 3 * kChunk;
 };
 
 template <int NB>
@@ -125,7 +155,7 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
   float* sR0 = sA + kChunk * kTilePixels;                   // [2][32][NB] radiance slices
   float* sTau = sR0 + 2 * kChunk * NB;                      // [16 warps][32] dL/dtau sums
   float4* sRec0 = reinterpret_cast<float4*>(sTau + S::kWarps * kChunk);  // [2][32][2]
-  uint32_t* sK0 = reinterpret_cast<uint32_t*>(sRec0 + 2 * 2 * kChunk);    // [2][32]
+  uint32_t* sK0 = reinterpret_cast<uint32_t*>(sRec0 + 2 * 2 * kChunk);    // [3][32] indices
   __shared__ unsigned sMask[S::kWarps];  // per warp: entries with a non-zero weight
 
   const RenderArgs& a = A.f;
@@ -196,47 +226,62 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
   float Q = 0.0f;
   const float* gRow = sG + px * S::GS + h * S::HC;
   const int nchunks = static_cast<int>((tile_stop - rg.x + kChunk - 1) / kChunk);
-  // Chunks are double-buffered: while chunk ci is swept, the records,
-  // indices and radiance rows of chunk ci - 1 are in flight (cp.async).
-  auto stage = [&](int cs, int buf) {
-    const uint32_t start = rg.x + static_cast<uint32_t>(cs) * kChunk;
-    const int nb = min(kChunk, static_cast<int>(tile_stop - start));
-    float4* rb = sRec0 + buf * 2 * kChunk;
-    float* rr = sR0 + buf * kChunk * NB;
+  // Chunks are processed back to front (n-th processed = chunk nchunks-1-n)
+  // through a copy pipeline: while chunk n is swept, the records and
+  // radiance rows of chunk n + 1 (gathered with the indices already in
+  // shared memory) and the indices of chunk n + 2 are in flight (cp.async),
+  // so no thread waits on a global load at a chunk boundary.
+  auto chunk_start = [&](int n) { return rg.x + static_cast<uint32_t>(nchunks - 1 - n) * kChunk; };
+  auto chunk_len = [&](int n) { return min(kChunk, static_cast<int>(tile_stop - chunk_start(n))); };
+  auto copy_indices = [&](int n) {
+    const uint32_t st0 = chunk_start(n);
+    const bool ok = t < chunk_len(n);
+    if (t < kChunk) cp_async4(&sK0[(n % 3) * kChunk + t], ok ? &a.vals[st0 + t] : a.vals, ok);
+  };
+  auto gather = [&](int n) {
+    const int nbn = chunk_len(n);
+    const uint32_t* ks = sK0 + (n % 3) * kChunk;
+    float4* rb = sRec0 + (n & 1) * 2 * kChunk;
+    float* rr = sR0 + (n & 1) * kChunk * NB;
     if (t < kChunk) {
-      const bool ok = t < nb;
-      const uint32_t k = ok ? a.vals[start + t] : 0u;
-      sK0[buf * kChunk + t] = k;
+      const bool ok = t < nbn;
+      const uint32_t k = ok ? ks[t] : 0u;
       cp_async16(&rb[2 * t + 0], &rec[2 * k + 0], ok);
       cp_async16(&rb[2 * t + 1], &rec[2 * k + 1], ok);
     }
     constexpr int Q4 = NB / 4;  // float4 per radiance row slice
     for (int e = t; e < kChunk * Q4; e += S::kThreads) {
       const int b = e / Q4, q4 = e % Q4;
-      const bool ok = b < nb;
-      const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
+      const bool ok = b < nbn;
+      const uint32_t k = ok ? ks[b] : 0u;
       cp_async16(&rr[b * NB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
                  ok);
     }
-    cp_async_commit();
   };
-  if (nchunks > 0) stage(nchunks - 1, 0);
-  int buf = 0;
-  for (int ci = nchunks - 1; ci >= 0; --ci, buf ^= 1) {
-    const uint32_t start = rg.x + static_cast<uint32_t>(ci) * kChunk;
-    const int nb = min(kChunk, static_cast<int>(tile_stop - start));
-    __syncthreads();  // everyone is done with the buffer the prefetch overwrites
-    if (ci > 0) {
-      stage(ci - 1, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this chunk landed
-    } else {
-      cp_async_wait_all();
-    }
-    sTau[t] = 0.0f;  // 512 threads, 16 x 32 entries
+  sTau[t] = 0.0f;  // 512 threads, 16 x 32 entries; the dL/dtau step re-zeroes
+  if (nchunks > 0) {
+    copy_indices(0);
+    cp_async_commit();
+    if (nchunks > 1) copy_indices(1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // cotangent and indices of chunk 0
     __syncthreads();
-    const float4* sRec = sRec0 + buf * 2 * kChunk;
-    const float* sR = sR0 + buf * kChunk * NB;
-    const uint32_t* sK = sK0 + buf * kChunk;
+    gather(0);
+    cp_async_commit();
+  }
+  for (int n = 0; n < nchunks; ++n) {
+    const uint32_t start = chunk_start(n);
+    const int nb = chunk_len(n);
+    cp_async_wait_all();  // chunk n's records and rows, chunk n + 1's indices
+    __syncthreads();      // ... visible to all; everyone is done with chunk n - 1
+    if (n + 1 < nchunks) {
+      if (n + 2 < nchunks) copy_indices(n + 2);
+      gather(n + 1);
+    }
+    cp_async_commit();
+    const float4* sRec = sRec0 + (n & 1) * 2 * kChunk;
+    const float* sR = sR0 + (n & 1) * kChunk * NB;
+    const uint32_t* sK = sK0 + (n % 3) * kChunk;
     {
       const bool rel = lane < nb && touches_strip(g, sRec[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
@@ -370,12 +415,16 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
       }
     }
     // dL/dtau: the warps' sums in order; each column block adds the part of
-    // the gradient its columns carry
-    if (t < nb) {
+    // the gradient its columns carry.  Entry t's sums are re-zeroed by the
+    // thread that read them.
+    if (t < kChunk) {
       float y = 0.0f;
 #pragma unroll
-      for (int w = 0; w < S::kWarps; ++w) y += sTau[w * kChunk + t];
-      if (y != 0.0f) atomicAdd(&A.d_tau[sK[t]], y);
+      for (int w = 0; w < S::kWarps; ++w) {
+        y += sTau[w * kChunk + t];
+        sTau[w * kChunk + t] = 0.0f;
+      }
+      if (t < nb && y != 0.0f) atomicAdd(&A.d_tau[sK[t]], y);
     }
   }
   cp_async_wait_all();  // the cotangent copies when the tile has no chunk

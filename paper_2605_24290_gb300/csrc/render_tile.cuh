@@ -76,15 +76,28 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
   float T = 1.0f;
   bool alive = valid;
   int ncon = 0;
-  // Chunks are double-buffered: while chunk c is composited, the records
-  // and radiance rows of chunk c + 1 are already in flight (cp.async).
-  auto stage = [&](uint32_t start, int buf) {
-    const int nb = min(kChunk, static_cast<int>(rg.y - start));
-    float4* rb = sRec + buf * 2 * kChunk;
-    float* rr = sR + buf * kChunk * NB;
+  // Chunks go through a copy pipeline: while chunk n is composited, the
+  // records and radiance rows of chunk n + 1 (gathered with indices already
+  // in shared memory) and the list indices of chunk n + 2 are in flight
+  // (cp.async), so no thread waits on a global load at a chunk boundary.
+  __shared__ uint32_t sIdx[3 * kChunk];  // list indices of chunks n, n+1, n+2
+  const int nchunks = static_cast<int>((rg.y - rg.x + kChunk - 1) / kChunk);
+  auto chunk_len = [&](int n) {
+    return min(kChunk, static_cast<int>(rg.y - rg.x - static_cast<uint32_t>(n) * kChunk));
+  };
+  auto copy_indices = [&](int n) {
+    const bool ok = t < chunk_len(n);
+    if (t < kChunk)
+      cp_async4(&sIdx[(n % 3) * kChunk + t], ok ? &a.vals[rg.x + n * kChunk + t] : a.vals, ok);
+  };
+  auto gather = [&](int n) {
+    const int nbn = chunk_len(n);
+    const uint32_t* ks = sIdx + (n % 3) * kChunk;
+    float4* rb = sRec + (n & 1) * 2 * kChunk;
+    float* rr = sR + (n & 1) * kChunk * NB;
     if (t < kChunk) {
-      const bool ok = t < nb;
-      const uint32_t k = ok ? a.vals[start + t] : 0u;
+      const bool ok = t < nbn;
+      const uint32_t k = ok ? ks[t] : 0u;
       // geometry record (2 x 16 B) and the NB-column radiance slice of row k
       cp_async16(&rb[2 * t + 0], &rec[2 * k + 0], ok);
       cp_async16(&rb[2 * t + 1], &rec[2 * k + 1], ok);
@@ -92,27 +105,33 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
     constexpr int Q = NB / 4;  // float4 per row slice
     for (int e = t; e < kChunk * Q; e += S::kThreads) {
       const int b = e / Q, q4 = e % Q;
-      const bool ok = b < nb;
-      const uint32_t k = ok ? __ldg(&a.vals[start + b]) : 0u;
+      const bool ok = b < nbn;
+      const uint32_t k = ok ? ks[b] : 0u;
       cp_async16(&rr[b * NB + 4 * q4], radv + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
                  ok);
     }
-    cp_async_commit();
   };
-  if (rg.x < rg.y) stage(rg.x, 0);
-  int buf = 0;
-  for (uint32_t start = rg.x; start < rg.y; start += kChunk, buf ^= 1) {
-    const int nb = min(kChunk, static_cast<int>(rg.y - start));
-    __syncthreads();  // everyone is done with the buffer the prefetch overwrites
-    if (start + kChunk < rg.y) {
-      stage(start + kChunk, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this chunk landed
-    } else {
-      cp_async_wait_all();
-    }
+  if (nchunks > 0) {
+    copy_indices(0);
+    cp_async_commit();
+    if (nchunks > 1) copy_indices(1);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // indices of chunk 0
     __syncthreads();
-    const float4* sRecC = sRec + buf * 2 * kChunk;
-    const float* sRC = sR + buf * kChunk * NB;
+    gather(0);
+    cp_async_commit();
+  }
+  for (int n = 0; n < nchunks; ++n) {
+    const int nb = chunk_len(n);
+    cp_async_wait_all();  // chunk n's records and rows, chunk n + 1's indices
+    __syncthreads();      // ... visible to all; everyone is done with chunk n - 1
+    if (n + 1 < nchunks) {
+      if (n + 2 < nchunks) copy_indices(n + 2);
+      gather(n + 1);
+    }
+    cp_async_commit();
+    const float4* sRecC = sRec + (n & 1) * 2 * kChunk;
+    const float* sRC = sR + (n & 1) * kChunk * NB;
     // ---- phase A: transmittance-weighted alphas, one pixel per thread.
     // Each warp first marks the chunk's Gaussians whose footprint meets its
     // pixel strip (one Gaussian per lane, then a ballot) and walks only
