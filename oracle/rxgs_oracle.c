@@ -604,17 +604,21 @@ typedef struct {
   double *sw, *sG, *sT, *Sb;
 } or_bwd_scratch;
 
+/* cand[0..ncand) (optional): the Gaussians of V->order, in that order,
+ * whose footprint rows include row i -- the others fail the footprint test
+ * below anyway.                                                             */
 static void or_backward_pixel(const or_grid* g, const or_view* V, const float* tau, int i, int jj,
                               int N, int C, const double* rad, const double* gpix,
                               size_t gstride_j, double* grad_rad, double* grad_tau,
                               double* abs_rad, double* abs_tau, int use_eps,
-                              or_bwd_scratch* sc) {
+                              or_bwd_scratch* sc, const int* cand, int ncand) {
   const int K = V->K;
   float T32 = 1.0f;
   double T64 = 1.0;
   int n_c = 0;
-  for (int n = 0; n < V->nvis; ++n) {
-    int k = V->order[n];
+  const int nloop = cand ? ncand : V->nvis;
+  for (int n = 0; n < nloop; ++n) {
+    int k = cand ? cand[n] : V->order[n];
     const or_p32* P = V->P32 + k;
     if (!or_in_footprint(g, P, i, jj)) continue;
     float w32;
@@ -656,6 +660,9 @@ static void or_backward_pixel(const or_grid* g, const or_view* V, const float* t
   }
 }
 
+int or_omp_threads(void);
+static int or_thread_num(void);
+
 static int or_scratch_init(or_bwd_scratch* sc, int nvis, int N, int C) {
   size_t n = (size_t)(nvis > 0 ? nvis : 1);
   sc->seq = (int*)malloc(sizeof(int) * n);
@@ -686,19 +693,62 @@ int or_backward_view(const or_grid* g, int K, const float* p, const float* s, co
                      double* abs_tau, int use_eps) {
   or_view V;
   if (or_view_init(&V, g, K, p, s, q, tau, c)) return -2;
-  or_bwd_scratch sc;
-  if (or_scratch_init(&sc, V.nvis, N, C)) return -2;
   const int H = g->H, W = g->W;
   const size_t gstride_j = (size_t)H * W * C * 2;
-  for (int i = 0; i < H; ++i)
-    for (int jj = 0; jj < W; ++jj) {
-      size_t pix = (size_t)i * W + jj;
-      or_backward_pixel(g, &V, tau, i, jj, N, C, rad, gspec + pix * C * 2, gstride_j, grad_rad,
-                        grad_tau, abs_rad, abs_tau, use_eps, &sc);
+  const size_t nrad = (size_t)N * K * C * 2;
+  /* Rows are split over threads; each thread sums into its own arrays, which
+   * are added into the outputs in thread order at the end (a fixed order for
+   * a given thread count).                                                 */
+  const int nthr = or_omp_threads();
+  double** part = (double**)calloc((size_t)nthr * 4, sizeof(double*));
+  or_bwd_scratch* scs = (or_bwd_scratch*)calloc((size_t)nthr, sizeof(or_bwd_scratch));
+  int ok = part && scs;
+  for (int t = 0; ok && t < nthr; ++t) {
+    part[4 * t + 0] = (double*)calloc(nrad, sizeof(double));
+    part[4 * t + 1] = (double*)calloc((size_t)K, sizeof(double));
+    part[4 * t + 2] = abs_rad ? (double*)calloc(nrad, sizeof(double)) : NULL;
+    part[4 * t + 3] = abs_tau ? (double*)calloc((size_t)K, sizeof(double)) : NULL;
+    ok = part[4 * t] && part[4 * t + 1] && (!abs_rad || part[4 * t + 2]) &&
+         (!abs_tau || part[4 * t + 3]) && or_scratch_init(&scs[t], V.nvis, N, C) == 0;
+  }
+  int* cand = ok ? (int*)malloc(sizeof(int) * (size_t)nthr * (V.nvis > 0 ? V.nvis : 1)) : NULL;
+  ok = ok && cand;
+  if (ok) {
+#pragma omp parallel for schedule(static) num_threads(nthr)
+    for (int i = 0; i < H; ++i) {
+      const int t = or_thread_num();
+      /* the depth-ordered Gaussians whose footprint rows include row i */
+      int* ci = cand + (size_t)t * (V.nvis > 0 ? V.nvis : 1);
+      int nc = 0;
+      for (int n = 0; n < V.nvis; ++n) {
+        const or_p32* P = V.P32 + V.order[n];
+        if (i >= P->i_lo && i <= P->i_hi) ci[nc++] = V.order[n];
+      }
+      for (int jj = 0; jj < W; ++jj) {
+        size_t pix = (size_t)i * W + jj;
+        or_backward_pixel(g, &V, tau, i, jj, N, C, rad, gspec + pix * C * 2, gstride_j,
+                          part[4 * t + 0], part[4 * t + 1], part[4 * t + 2], part[4 * t + 3],
+                          use_eps, &scs[t], ci, nc);
+      }
     }
-  or_scratch_free(&sc);
+    for (int t = 0; t < nthr; ++t) {
+      for (size_t e = 0; e < nrad; ++e) grad_rad[e] += part[4 * t][e];
+      for (int k = 0; k < K; ++k) grad_tau[k] += part[4 * t + 1][k];
+      if (abs_rad)
+        for (size_t e = 0; e < nrad; ++e) abs_rad[e] += part[4 * t + 2][e];
+      if (abs_tau)
+        for (int k = 0; k < K; ++k) abs_tau[k] += part[4 * t + 3][k];
+    }
+  }
+  for (int t = 0; part && scs && t < nthr; ++t) {
+    for (int e = 0; e < 4; ++e) free(part[4 * t + e]);
+    if (scs[t].seq || scs[t].sw || scs[t].sG || scs[t].sT || scs[t].Sb) or_scratch_free(&scs[t]);
+  }
+  free(part);
+  free(scs);
+  free(cand);
   or_view_free(&V);
-  return 0;
+  return ok ? 0 : -2;
 }
 
 /* The backward restricted to a pixel list pix[np] (= i*W + jj), with the
@@ -714,7 +764,7 @@ int or_backward_pixels(const or_grid* g, int K, const float* p, const float* s, 
   for (int e = 0; e < np; ++e)
     or_backward_pixel(g, &V, tau, pix[e] / g->W, pix[e] % g->W, N, C, rad,
                       gpix + (size_t)e * N * C * 2, (size_t)C * 2, grad_rad, grad_tau, NULL, NULL,
-                      1, &sc);
+                      1, &sc, NULL, 0);
   or_scratch_free(&sc);
   or_view_free(&V);
   return 0;
@@ -726,5 +776,14 @@ int or_omp_threads(void) {
   return omp_get_max_threads();
 #else
   return 1;
+#endif
+}
+
+static int or_thread_num(void) {
+#ifdef _OPENMP
+  extern int omp_get_thread_num(void);
+  return omp_get_thread_num();
+#else
+  return 0;
 #endif
 }
