@@ -188,9 +188,13 @@ def serve_requests(rng: np.random.Generator, n_req: int, rate_hz: float, max_rx:
     return reqs
 
 
-def workload_coverage(seed: int = SEED_BASE + 4, K: int = 1_000_000, M: int = 16, side: int = 32):
+def workload_coverage(seed: int = SEED_BASE + 4, K: int = 1_000_000, M: int = 16, side: int = 32,
+                      with_radiance: bool = True):
     """1,000,000 Gaussians in a 40x30x4 m box, 16 transmitters, 1,024
-    receivers at floor-grid cell centres 1 m high, 180x360 grid."""
+    receivers at floor-grid cell centres 1 m high, 180x360 grid.  The
+    [1024, K, 1, 2] radiance (8.2 GB at full size) is drawn here only when
+    asked; `hashed_radiance_rows` / `hashed_radiance_torch` give a
+    counter-based stand-in that can be produced on either side."""
     rng = np.random.default_rng(seed)
     box = (40.0, 30.0, 4.0)
     scene = draw_scene(rng, K, box)
@@ -198,6 +202,68 @@ def workload_coverage(seed: int = SEED_BASE + 4, K: int = 1_000_000, M: int = 16
     a, b = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
     rx = f32(np.stack([(a.reshape(-1) + 0.5) * 40.0 / side, (b.reshape(-1) + 0.5) * 30.0 / side,
                        np.ones(side * side)], axis=-1))
-    rad = draw_radiance(rng, side * side, K, 1)
+    rad = draw_radiance(rng, side * side, K, 1) if with_radiance else None
     return dict(scene=scene, tx=tx, rx=rx, radiance=rad,
                 grid=Grid(H=180, W=360, theta0_deg=-90.0))
+
+
+# ---------------------------------------------- counter-based radiance
+# SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) applied to the counter
+# i = j*K + k + 1: z = i * 0x9E3779B97F4A7C15, then the three xor-shift /
+# multiply rounds.  The real part takes bits 40..63 and the imaginary part
+# bits 16..39 of z, each mapped to m / 2^23 - 1 in [-1, 1): exact in
+# float32, so the numpy and the torch versions agree bit for bit.
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+
+
+def _splitmix64_np(i: np.ndarray) -> np.ndarray:
+    z = i.astype(np.uint64) * np.uint64(_SM_GAMMA)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_M1)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_M2)
+    return z ^ (z >> np.uint64(31))
+
+
+def hashed_radiance_rows(js, K: int) -> np.ndarray:
+    """Rows js of the counter-based radiance, [len(js), K, 1, 2] float32."""
+    js = np.asarray(js, np.uint64)
+    out = np.empty((js.shape[0], K, 1, 2), np.float32)
+    k = np.arange(K, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        for r, j in enumerate(js):
+            z = _splitmix64_np(j * np.uint64(K) + k + np.uint64(1))
+            re = ((z >> np.uint64(40)) & np.uint64(0xFFFFFF)).astype(np.float64) / 8388608.0 - 1.0
+            im = ((z >> np.uint64(16)) & np.uint64(0xFFFFFF)).astype(np.float64) / 8388608.0 - 1.0
+            out[r, :, 0, 0] = re
+            out[r, :, 0, 1] = im
+    return out
+
+
+def _i64(c: int) -> int:
+    """The int64 with the bit pattern of the 64-bit constant c."""
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def hashed_radiance_torch(torch, N: int, K: int, device, rows_per_pass: int = 32):
+    """The same counter-based radiance for rows 0..N-1, [N, K, 1, 2] float32,
+    built on `device` with int64 arithmetic (wrapping products; logical
+    right shifts by masking)."""
+    out = torch.empty((N, K, 1, 2), dtype=torch.float32, device=device)
+    k = torch.arange(K, dtype=torch.int64, device=device)
+
+    def srl(z, s):
+        return (z >> s) & ((1 << (64 - s)) - 1)
+
+    for j0 in range(0, N, rows_per_pass):
+        j1 = min(N, j0 + rows_per_pass)
+        j = torch.arange(j0, j1, dtype=torch.int64, device=device)[:, None]
+        z = (j * K + k[None, :] + 1) * _i64(_SM_GAMMA)
+        z = (z ^ srl(z, 30)) * _i64(_SM_M1)
+        z = (z ^ srl(z, 27)) * _i64(_SM_M2)
+        z = z ^ srl(z, 31)
+        re = (srl(z, 40) & 0xFFFFFF).to(torch.float64) / 8388608.0 - 1.0
+        im = (srl(z, 16) & 0xFFFFFF).to(torch.float64) / 8388608.0 - 1.0
+        out[j0:j1, :, 0, 0] = re.to(torch.float32)
+        out[j0:j1, :, 0, 1] = im.to(torch.float32)
+    return out
