@@ -357,6 +357,9 @@ def gpu_bench(args):
     bcsi = None
     if rank == 0 and not args.no_batched:
         bcsi = batched_csi_bench(torch, rxgs, S)
+    cov = None
+    if rank == 0 and not args.no_coverage:
+        cov = coverage_bench(torch, rxgs, S)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -384,6 +387,7 @@ def gpu_bench(args):
             "per_rx_loop": loop,
             "serve": serve,
             "batched_csi": bcsi,
+            "coverage": cov,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -492,6 +496,58 @@ def batched_csi_bench(torch, rxgs, S, reps=3):
             "workload": "300k Gaussians, 256 rx in U{1..64} batches, C=52, bf16 MLP, CSI"}
 
 
+def coverage_bench(torch, rxgs, S, reps=3):
+    """Coverage map: 1,000,000 Gaussians, 16 transmitters x 1,024 receivers,
+    180x360 grid, explicit radiance [1024, 1M, 1, 2] (8.2 GB, resident):
+    RSSI through the visibility path, then the backward from an RSSI
+    cotangent to radiance and opacity (the radiance gradient is another
+    8.2 GB).  Views are prepared once; forward and backward are timed
+    separately with CUDA events."""
+    w = S.workload_coverage(with_radiance=False)
+    g, sc = w["grid"], w["scene"]
+    M, N, K = w["tx"].shape[0], w["rx"].shape[0], sc.K
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = rxgs.Context(H=g.H, W=g.W, theta0_deg=g.theta0_deg)
+    h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), None, None, C=1)
+    rad = S.hashed_radiance_torch(torch, N, K, "cuda")
+    views = ctx.prepare(h, d(w["tx"]))
+    rssi = torch.empty((M, N), device="cuda")
+    csi = torch.empty((M, N, 1, 2), device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(S.SEED_BASE + 41)
+    grssi = torch.randn((M, N), device="cuda", generator=gen)
+    d_rad = torch.zeros((N, K, 1, 2), device="cuda")
+    d_tau = torch.zeros(K, device="cuda")
+
+    def fwd():
+        ctx.render_views(views, None, N, rxgs.OUT_RSSI | rxgs.OUT_CSI, radiance=rad, rssi=rssi,
+                         csi=csi, reduce_path=1)
+
+    def bwd():
+        ctx.render_backward(views, None, N, rxgs.OUT_RSSI, radiance=rad, grad_rssi=grssi,
+                            fwd_csi=csi, grad_radiance=d_rad, grad_opacity=d_tau)
+
+    fwd()
+    bwd()
+    ctx.sync()
+    out = {}
+    for name, fn in (("fwd", fwd), ("bwd", bwd)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        ctx.sync()
+        out[name] = a.elapsed_time(b) / reps
+    ctx.release_views(views)
+    ctx.close()
+    return {"pairs": M * N, "forward_ms": round(out["fwd"], 3), "backward_ms": round(out["bwd"], 3),
+            "rssi_per_s": round(M * N / (out["fwd"] / 1e3), 1),
+            "note": "views prepared once outside the timed calls",
+            "workload": "1M Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance [1024,1M,1,2], "
+                        "RSSI (visibility path) + RSSI backward to radiance and opacity"}
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_sample(budget_s=15.0, steps=None, npx=16384):
     """The oracle on a bounded sample of the same workload: one transmitter,
@@ -572,6 +628,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-coverage", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":

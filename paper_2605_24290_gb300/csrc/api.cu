@@ -653,6 +653,66 @@ rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uin
   return RXGS_OK;
 }
 
+// CSI / RSSI cotangents with explicit radiance: the visibility-weight
+// backward (vis_bwd.cu) -- no Gaussian-major radiance copy and no
+// [K][N*2C] gradient buffer.
+static rxgs_status backward_visibility(rxgs_ctx* ctx, const SceneState* s, const ViewsState* v,
+                                       int N, const rxgs_render_desc* d,
+                                       const rxgs_cotangents* cot, rxgs_grads* gr,
+                                       cudaStream_t st) {
+  const GridConst& g = ctx->g;
+  const int C = s->C, K = s->K, M = v->M;
+  const size_t MK = static_cast<size_t>(M) * K;
+  const size_t MHW = static_cast<size_t>(M) * g.H * g.W;
+  float *g_uni = nullptr, *gamma = nullptr, *W = nullptr, *tfin = nullptr, *d_tau = nullptr;
+  uint32_t *stops = nullptr, *tstop = nullptr;
+  auto cleanup = [&]() {
+    dfree(g_uni, st); dfree(gamma, st); dfree(W, st); dfree(tfin, st); dfree(stops, st);
+    dfree(tstop, st);
+    if (!gr->grad_opacity) dfree(d_tau, st);
+  };
+  cudaError_t e = dalloc(&g_uni, static_cast<size_t>(M) * 2 * N * C, st);
+  if (e == cudaSuccess) e = dalloc(&gamma, MK, st);
+  if (e == cudaSuccess && gr->grad_radiance) e = dalloc(&W, MK, st);
+  if (e == cudaSuccess && W) e = cudaMemsetAsync(W, 0, sizeof(float) * MK, st);
+  if (e == cudaSuccess) e = dalloc(&tfin, MHW, st);
+  if (e == cudaSuccess) e = dalloc(&stops, MHW, st);
+  if (e == cudaSuccess) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
+  d_tau = gr->grad_opacity;
+  if (e == cudaSuccess && !d_tau) e = dalloc(&d_tau, static_cast<size_t>(K), st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, RXGS_E_OOM, "backward: %s", cudaGetErrorString(e));
+  }
+  launch_uniform_cotangent(cot->grad_csi, cot->grad_rssi, cot->fwd_csi, M, N, C, g_uni, st);
+  BackwardArgs A{};
+  A.f.g = g;
+  A.f.rec = v->rec;
+  A.f.vals = v->vals;
+  A.f.ranges = v->ranges;
+  A.f.K = K;
+  A.f.M = M;
+  A.f.N = N;
+  A.f.C = C;
+  A.f.ncols = 2 * N * C;
+  A.d_tau = d_tau;
+  A.tfin = tfin;
+  A.stops = stops;
+  A.tile_stop = tstop;
+  A.n_inst = v->n_inst;
+  {
+    Stage sg(ctx, "bwd_prepass", st);
+    launch_bwd_prepass(A, st);
+  }
+  {
+    Stage sg(ctx, "vis_bwd", st);
+    launch_vis_backward(A, d->radiance, g_uni, gamma, W, gr->grad_radiance, st);
+  }
+  rxgs_status rs = check_last(ctx, "backward");
+  cleanup();
+  return rs;
+}
+
 rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,
                                  const rxgs_render_desc* d, const rxgs_cotangents* cot,
                                  rxgs_grads* gr, void* stream) {
@@ -677,6 +737,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (d->radiance && !cot->grad_spectra) return backward_visibility(ctx, s, v, N, d, cot, gr, st);
   const GridConst& g = ctx->g;
   const int C = s->C, K = s->K, M = v->M;
   const int ncols = 2 * N * C;

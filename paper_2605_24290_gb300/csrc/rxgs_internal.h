@@ -134,6 +134,12 @@ struct BackwardArgs {
 void launch_bwd_prepass(const BackwardArgs& a, cudaStream_t s);
 // Walk 2: the back-to-front sweep producing d_rad and d_tau
 void launch_render_bwd(const BackwardArgs& a, cudaStream_t s);
+// CSI / RSSI cotangents with explicit receiver-major radiance rad_rm
+// [N][K][C][2]: gamma [M][K] and W [M][K] (zeroed by the caller) are
+// scratch; d_tau += ..., grad_radiance (or null) += sum_v W g.  Needs the
+// pre-pass outputs in A (tfin, stops, tile_stop).
+void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float* gu,
+                         float* gamma, float* W, float* grad_radiance, cudaStream_t s);
 
 // ------------------------------------------ visibility weights (Eq. render_reorder)
 // W[M][K] = sum over each view's pixels of T_k w_k (zeroed first).

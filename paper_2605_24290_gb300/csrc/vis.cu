@@ -89,46 +89,73 @@ void launch_visibility(const RenderArgs& a, float* W, cudaStream_t s) {
 // rad[j][k][e] W[v][k] for all views v; a second kernel adds the chunks in
 // order.  The radiance row is read once for all views.
 constexpr int kWsChunk = 4096;   // Gaussians per block
-constexpr int kWsMaxViews = 32;  // views handled per pass
+constexpr int kWsSub = 256;      // Gaussians per shared-memory stage
+constexpr int kWsMaxViews = 16;  // views handled per pass
 
-__global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restrict__ rad, int K,
-                                                           int C, const float* __restrict__ W,
-                                                           int M, int v0, int nv,
+// Block (chunk of 4096 Gaussians, 256 complex columns q = (j, c)): thread q
+// accumulates sum_k W[v][k] s[j][k][c] for up to 16 views in registers.  The
+// chunk's visibility weights are staged 256 Gaussians at a time in shared
+// memory as [k][16 views] (four 16-byte broadcasts per Gaussian); each
+// thread streams its own radiance column (one float2 per Gaussian; with
+// C = 1 the 32 lanes of a warp read 32 receivers' rows, whose 32-byte
+// sectors serve the next Gaussians from L1).
+__global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restrict__ rad, int N,
+                                                           int K, int C,
+                                                           const float* __restrict__ W, int M,
+                                                           int v0, int nv,
                                                            float* __restrict__ part) {
-  const int j = blockIdx.y, chunk = blockIdx.x;
-  const int twoC = 2 * C;
+  __shared__ __align__(16) float sW[kWsSub][kWsMaxViews];
+  const int chunk = blockIdx.x, t = threadIdx.x;
+  const int q = blockIdx.y * 256 + t;  // complex column (j, c)
+  const bool active = q < N * C;
+  const int j = active ? q / C : 0, c = active ? q - j * C : 0;
   const int k0 = chunk * kWsChunk, k1 = min(K, k0 + kWsChunk);
-  extern __shared__ float red[];  // [8 warps][nv][twoC]
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  // each thread owns (entry e = t % twoC slot) ... simple layout: loop over
-  // (k, e) pairs with e fastest; accumulate per (v, e) in registers for e
-  // fixed per thread when twoC divides 256
-  const int per = 256 / twoC;        // threads per e (twoC <= 256 and divides 256)
-  const int e = t % twoC, sub = t / twoC;
-  float acc[kWsMaxViews];
+  float acc[kWsMaxViews][2];
 #pragma unroll
-  for (int q = 0; q < kWsMaxViews; ++q) acc[q] = 0.0f;
-  const float* row = rad + static_cast<size_t>(j) * K * twoC;
-  if (sub < per) {
-    for (int k = k0 + sub; k < k1; k += per) {
-      const float x = row[static_cast<size_t>(k) * twoC + e];
+  for (int v = 0; v < kWsMaxViews; ++v) acc[v][0] = acc[v][1] = 0.0f;
+  const float2* col = reinterpret_cast<const float2*>(rad) + static_cast<size_t>(j) * K * C + c;
+  for (int ks = k0; ks < k1; ks += kWsSub) {
+    const int kn = min(kWsSub, k1 - ks);
+    __syncthreads();  // the previous stage is consumed
+    {
+      float wv[kWsMaxViews];
 #pragma unroll
-      for (int q = 0; q < kWsMaxViews; ++q)
-        if (q < nv) acc[q] = fmaf(x, W[static_cast<size_t>(v0 + q) * K + k], acc[q]);
+      for (int v = 0; v < kWsMaxViews; ++v)
+        wv[v] = (v < nv && t < kn) ? W[static_cast<size_t>(v0 + v) * K + ks + t] : 0.0f;
+#pragma unroll
+      for (int v4 = 0; v4 < kWsMaxViews / 4; ++v4)
+        *reinterpret_cast<float4*>(&sW[t][4 * v4]) =
+            make_float4(wv[4 * v4], wv[4 * v4 + 1], wv[4 * v4 + 2], wv[4 * v4 + 3]);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 4
+      for (int kk = 0; kk < kn; ++kk) {
+        const float2 sv = col[static_cast<size_t>(ks + kk) * C];
+#pragma unroll
+        for (int v4 = 0; v4 < kWsMaxViews / 4; ++v4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(&sW[kk][4 * v4]);
+          acc[4 * v4 + 0][0] = fmaf(w4.x, sv.x, acc[4 * v4 + 0][0]);
+          acc[4 * v4 + 0][1] = fmaf(w4.x, sv.y, acc[4 * v4 + 0][1]);
+          acc[4 * v4 + 1][0] = fmaf(w4.y, sv.x, acc[4 * v4 + 1][0]);
+          acc[4 * v4 + 1][1] = fmaf(w4.y, sv.y, acc[4 * v4 + 1][1]);
+          acc[4 * v4 + 2][0] = fmaf(w4.z, sv.x, acc[4 * v4 + 2][0]);
+          acc[4 * v4 + 2][1] = fmaf(w4.z, sv.y, acc[4 * v4 + 2][1]);
+          acc[4 * v4 + 3][0] = fmaf(w4.w, sv.x, acc[4 * v4 + 3][0]);
+          acc[4 * v4 + 3][1] = fmaf(w4.w, sv.y, acc[4 * v4 + 3][1]);
+        }
+      }
     }
   }
-  // reduce over the `per` threads sharing e (fixed order through shared memory)
-  float* r = red;  // [per][nv][twoC] reused per view group
-  for (int q = 0; q < nv; ++q) r[(sub * nv + q) * twoC + e] = acc[q];
-  __syncthreads();
-  for (int o = t; o < nv * twoC; o += 256) {
-    float y = 0.0f;
-    for (int s2 = 0; s2 < per; ++s2) y += r[s2 * nv * twoC + o];
-    const int q = o / twoC, ee = o % twoC;
-    part[((static_cast<size_t>(chunk) * gridDim.y + j) * M + v0 + q) * twoC + ee] = y;
+  if (!active) return;
+  const int twoC = 2 * C;
+#pragma unroll
+  for (int v = 0; v < kWsMaxViews; ++v) {
+    if (v >= nv) break;
+    float* dst = part + ((static_cast<size_t>(chunk) * N + j) * M + v0 + v) * twoC + 2 * c;
+    dst[0] = acc[v][0];
+    dst[1] = acc[v][1];
   }
-  (void)lane;
-  (void)warp;
 }
 
 __global__ void weighted_sum_finish_kernel(const float* __restrict__ part, int nchunks, int N,
@@ -156,16 +183,15 @@ size_t weighted_sum_tmp_floats(int M, int K, int N, int C) {
   return nchunks * N * M * 2ull * C;
 }
 
-bool weighted_sum_supported(int C) { return 256 % (2 * C) == 0; }
+bool weighted_sum_supported(int C) { return C >= 1; }
 
 void launch_weighted_sum(const float* rad, int N, int K, int C, const float* W, int M, float* tmp,
                          float* csi, float* rssi, cudaStream_t s) {
   const int nchunks = (K + kWsChunk - 1) / kWsChunk;
-  const int twoC = 2 * C;
+  const unsigned colblocks = static_cast<unsigned>((N * C + 255) / 256);
   for (int v0 = 0; v0 < M; v0 += kWsMaxViews) {
     const int nv = min(kWsMaxViews, M - v0);
-    const size_t smem = sizeof(float) * (256 / twoC) * nv * twoC;
-    weighted_sum_kernel<<<dim3(nchunks, N), 256, smem, s>>>(rad, K, C, W, M, v0, nv, tmp);
+    weighted_sum_kernel<<<dim3(nchunks, colblocks), 256, 0, s>>>(rad, N, K, C, W, M, v0, nv, tmp);
     note_launches(1);
   }
   const int n = M * N * C;
