@@ -137,8 +137,10 @@ struct BwdShape {
   static constexpr int kThreads = 2 * kTilePixels;
   static constexpr int HC = NB / 2;                 // gamma columns per thread
   static constexpr int GS = NB + 4;                 // padded cotangent row (float4 aligned)
-  static constexpr int CB = NB / 8;                 // 8-column groups in the product
-  static constexpr int SL = kThreads / (8 * CB);    // pixel slices in the product
+  static constexpr int PE = 2;                      // entries per product block
+  static constexpr int PC = 16;                     // columns per product block
+  static constexpr int CB = NB / PC;                // column groups in the product
+  static constexpr int SL = kThreads / ((kChunk / PE) * CB);  // pixel slices in the product
   static constexpr int kWarps = kThreads / 32;
   // cotangent rows, T w, two radiance / record / index buffers, dtau sums
   static constexpr size_t smem =
@@ -218,10 +220,10 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
   }
   const uint32_t tile_stop = A.tile_stop[static_cast<size_t>(v) * g.T + tile];
 
-  // product mapping: 8 groups of 4 entries x CB groups of 8 columns, SL
+  // product mapping: 16 groups of 2 entries x CB groups of 16 columns, SL
   // pixel slices
   const int slice = t % S::SL, ob = t / S::SL;
-  const int bb = (ob / S::CB) * 4, cbk = (ob % S::CB) * 8;
+  const int bb = (ob / S::CB) * S::PE, cbk = (ob % S::CB) * S::PC;
 
   float Q = 0.0f;
   const float* gRow = sG + px * S::GS + h * S::HC;
@@ -365,38 +367,45 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
       if (lane == 0) sMask[wp] = used;
     }
     __syncthreads();
-    // dL/ds[b][c] = sum_p A[b][p] g[p][c]: 4 x 8 block per thread over the
+    // dL/ds[b][c] = sum_p A[b][p] g[p][c]: 2 x 16 block per thread over the
     // pixels p = it*SL + slice, then a sum over the SL slices.
     {
-      float acc[4][8];
+      float acc[S::PE][S::PC];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < S::PE; ++x)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[x][c] = 0.0f;
+        for (int c = 0; c < S::PC; ++c) acc[x][c] = 0.0f;
       if (bb < nb) {
         for (int it = 0; it < kTilePixels / S::SL; ++it) {
           // pixels it*SL .. it*SL+SL-1 belong to warp (it*SL)/16, which wrote
-          // only the entries of its mask: skip the group when none of
-          // b..b+3 is there
-          const unsigned wm = (sMask[(it * S::SL) >> 4] >> bb) & 0xfu;
+          // only the entries of its mask: skip the group when neither of
+          // b, b+1 is there
+          const unsigned wm = (sMask[(it * S::SL) >> 4] >> bb) & ((1u << S::PE) - 1u);
           if (!wm) continue;
           const int p = it * S::SL + slice;
-          float av[4];
+          float av[S::PE];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) av[x] = (wm >> x) & 1u ? sA[(bb + x) * kTilePixels + p] : 0.0f;
-          const float4 g0 = *reinterpret_cast<const float4*>(&sG[p * S::GS + cbk]);
-          const float4 g1 = *reinterpret_cast<const float4*>(&sG[p * S::GS + cbk + 4]);
-          const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+          for (int x = 0; x < S::PE; ++x)
+            av[x] = (wm >> x) & 1u ? sA[(bb + x) * kTilePixels + p] : 0.0f;
+          float gv[S::PC];
 #pragma unroll
-          for (int x = 0; x < 4; ++x)
+          for (int q = 0; q < S::PC / 4; ++q) {
+            const float4 g4 = *reinterpret_cast<const float4*>(&sG[p * S::GS + cbk + 4 * q]);
+            gv[4 * q] = g4.x;
+            gv[4 * q + 1] = g4.y;
+            gv[4 * q + 2] = g4.z;
+            gv[4 * q + 3] = g4.w;
+          }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[x][c] = fmaf(av[x], gv[c], acc[x][c]);
+          for (int x = 0; x < S::PE; ++x)
+#pragma unroll
+            for (int c = 0; c < S::PC; ++c) acc[x][c] = fmaf(av[x], gv[c], acc[x][c]);
         }
       }
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < S::PE; ++x)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < S::PC; ++c) {
           float y = acc[x][c];
 #pragma unroll
           for (int o = S::SL / 2; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
@@ -404,12 +413,12 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
         }
       if (slice == 0) {
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < S::PE; ++x) {
           const int b = bb + x;
           if (b >= nb) continue;
           float* dst = A.d_rad + static_cast<size_t>(sK[b]) * a.stride + col0 + cbk;
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
+          for (int c = 0; c < S::PC; ++c)
             if (col0 + cbk + c < a.ncols && acc[x][c] != 0.0f) atomicAdd(&dst[c], acc[x][c]);
         }
       }
