@@ -136,8 +136,10 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
 
 // Narrow spectra (C <= 4): the same arithmetic with the hidden units
 // streamed into the 4C output accumulators (bias first, then units in
-// ascending order, as above), so no 64-entry hidden vector is kept.
-template <int CC>
+// ascending order, as above), so no 64-entry hidden vector is kept.  Each
+// thread evaluates PP pairs (block-strided, so every slice of a block stays
+// coalesced) and reuses each weight it reads from shared memory PP times.
+template <int CC, int PP>
 __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     const float* __restrict__ P, int bf16, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
@@ -151,43 +153,77 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
   for (int e = threadIdx.x; e < n4 * kHidden; e += blockDim.x) W2[e] = rb(P[o.l_w2 + e], bf16);
   for (int e = threadIdx.x; e < n4; e += blockDim.x) B2[e] = P[o.l_b2 + e];
   __syncthreads();
-  const size_t pair = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (pair >= static_cast<size_t>(N) * K) return;
-  const int j = static_cast<int>(pair % N);
-  const int k = static_cast<int>(pair / N);
-  if (n_dev && j >= *n_dev) return;
-  const float4 p = geom[3 * k];
-  const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
-  const float d = sqrtf(vx * vx + vy * vy + vz * vz);
-  const float inv = 1.0f / d;
-  const float x[6] = {rb(vx * inv, bf16), rb(vy * inv, bf16), rb(vz * inv, bf16), rb(d, bf16),
-                      1.0f, 0.0f};
-  float ol[n4];
+  const size_t npairs = static_cast<size_t>(N) * K;
+  const int nlim = n_dev ? *n_dev : N;
+  float x[PP][4];
+  bool ok[PP];
+  int jv[PP], kv[PP];
 #pragma unroll
-  for (int q = 0; q < n4; ++q) ol[q] = B2[q];
-#pragma unroll 8
-  for (int u = 0; u < kHidden; ++u) {
-    float a = B1[u];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
-    const float hu = rb(fmaxf(a, 0.0f), bf16);
-#pragma unroll
-    for (int q = 0; q < n4; ++q) ol[q] = fmaf(W2[q * kHidden + u], hu, ol[q]);
+  for (int r = 0; r < PP; ++r) {
+    const size_t pair = (static_cast<size_t>(blockIdx.x) * PP + r) * blockDim.x + threadIdx.x;
+    ok[r] = pair < npairs;
+    const int j = ok[r] ? static_cast<int>(pair % N) : 0;
+    const int k = ok[r] ? static_cast<int>(pair / N) : 0;
+    ok[r] = ok[r] && j < nlim;
+    jv[r] = j;
+    kv[r] = k;
+    x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0.0f;
+    if (ok[r]) {
+      const float4 p = geom[3 * k];
+      const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
+      const float d = sqrtf(vx * vx + vy * vy + vz * vz);
+      const float inv = 1.0f / d;
+      x[r][0] = rb(vx * inv, bf16);
+      x[r][1] = rb(vy * inv, bf16);
+      x[r][2] = rb(vz * inv, bf16);
+      x[r][3] = rb(d, bf16);
+    }
   }
-  const float* gj = glob + static_cast<size_t>(j) * n4;
-  float* dst = out + static_cast<size_t>(k) * stride +
-               (col_of ? static_cast<size_t>(col_of[j]) : static_cast<size_t>(j) * 2 * CC);
+  float ol[PP][n4];
 #pragma unroll
-  for (int c = 0; c < CC; ++c) {
-    const float pr = base[(static_cast<size_t>(k) * CC + c) * 2 + 0];
-    const float pi = base[(static_cast<size_t>(k) * CC + c) * 2 + 1];
-    const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
-    const float ur = agr * pr - agi * pi + gj[4 * c + 2];
-    const float ui = agr * pi + agi * pr + gj[4 * c + 3];
-    const float alr = 1.0f + ol[4 * c], ali = ol[4 * c + 1];
-    const float sr = alr * ur - ali * ui + ol[4 * c + 2];
-    const float si = alr * ui + ali * ur + ol[4 * c + 3];
-    *reinterpret_cast<float2*>(&dst[2 * c]) = make_float2(sr, si);
+  for (int r = 0; r < PP; ++r)
+#pragma unroll
+    for (int q = 0; q < n4; ++q) ol[r][q] = B2[q];
+#pragma unroll 4
+  for (int u = 0; u < kHidden; ++u) {
+    float w1[6], w2[n4];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) w1[i] = W1[u * 6 + i];
+#pragma unroll
+    for (int q = 0; q < n4; ++q) w2[q] = W2[q * kHidden + u];
+    const float b1 = B1[u];
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      // inputs 4 and 5 are the constants 1 and 0: the same fmaf chain as the
+      // general kernel (fmaf(w, 1, a) = a + w and fmaf(w, 0, a) = a)
+      float a = b1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a = fmaf(w1[i], x[r][i], a);
+      a = a + w1[4];
+      const float hu = rb(fmaxf(a, 0.0f), bf16);
+#pragma unroll
+      for (int q = 0; q < n4; ++q) ol[r][q] = fmaf(w2[q], hu, ol[r][q]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PP; ++r) {
+    if (!ok[r]) continue;
+    const int j = jv[r], k = kv[r];
+    const float* gj = glob + static_cast<size_t>(j) * n4;
+    float* dst = out + static_cast<size_t>(k) * stride +
+                 (col_of ? static_cast<size_t>(col_of[j]) : static_cast<size_t>(j) * 2 * CC);
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      const float pr = base[(static_cast<size_t>(k) * CC + c) * 2 + 0];
+      const float pi = base[(static_cast<size_t>(k) * CC + c) * 2 + 1];
+      const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
+      const float ur = agr * pr - agi * pi + gj[4 * c + 2];
+      const float ui = agr * pi + agi * pr + gj[4 * c + 3];
+      const float alr = 1.0f + ol[r][4 * c], ali = ol[r][4 * c + 1];
+      const float sr = alr * ur - ali * ui + ol[r][4 * c + 2];
+      const float si = alr * ui + ali * ur + ol[r][4 * c + 3];
+      *reinterpret_cast<float2*>(&dst[2 * c]) = make_float2(sr, si);
+    }
   }
 }
 
@@ -207,18 +243,19 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
   mlp_global_kernel<<<N, 128, 0, s>>>(m.p, m.C, m.bf16, rx, glob, n_dev);
   note_launches(1);
   const size_t pairs = static_cast<size_t>(N) * K;
-  const unsigned nblk = static_cast<unsigned>((pairs + 255) / 256);
   switch (m.C) {
-#define RXGS_NARROW(CCV)                                                                        \
-  case CCV:                                                                                   \
-    mlp_local_narrow_kernel<CCV><<<nblk, 256, 0, s>>>(m.p, m.bf16, rx, N, geom, base, K, stride, \
-                                                       glob, out, n_dev, col_of);             \
+#define RXGS_NARROW(CCV, PPV)                                                                  \
+  case CCV: {                                                                                 \
+    const unsigned nblk = static_cast<unsigned>((pairs + 256 * PPV - 1) / (256 * PPV));       \
+    mlp_local_narrow_kernel<CCV, PPV><<<nblk, 256, 0, s>>>(m.p, m.bf16, rx, N, geom, base, K,  \
+                                                            stride, glob, out, n_dev, col_of); \
     note_launches(1);                                                                         \
-    return;
-    RXGS_NARROW(1)
-    RXGS_NARROW(2)
-    RXGS_NARROW(3)
-    RXGS_NARROW(4)
+    return;                                                                                   \
+  }
+    RXGS_NARROW(1, 4)
+    RXGS_NARROW(2, 4)
+    RXGS_NARROW(3, 2)
+    RXGS_NARROW(4, 2)
 #undef RXGS_NARROW
     default:
       break;
