@@ -88,71 +88,91 @@ void launch_visibility(const RenderArgs& a, float* W, cudaStream_t s) {
 // Block (j, chunk of K): out_part[chunk][j][v][e] = sum_{k in chunk}
 // rad[j][k][e] W[v][k] for all views v; a second kernel adds the chunks in
 // order.  The radiance row is read once for all views.
-constexpr int kWsChunk = 4096;   // Gaussians per block
+constexpr int kWsChunk = 1024;   // Gaussians per block
 constexpr int kWsSub = 256;      // Gaussians per shared-memory stage
 constexpr int kWsMaxViews = 16;  // views handled per pass
 
-// Block (chunk of 4096 Gaussians, 256 complex columns q = (j, c)): thread q
-// accumulates sum_k W[v][k] s[j][k][c] for up to 16 views in registers.  The
-// chunk's visibility weights are staged 256 Gaussians at a time in shared
-// memory as [k][16 views] (four 16-byte broadcasts per Gaussian); each
-// thread streams its own radiance column (one float2 per Gaussian; with
-// C = 1 the 32 lanes of a warp read 32 receivers' rows, whose 32-byte
-// sectors serve the next Gaussians from L1).
+// Block (chunk of 1024 Gaussians, 256 complex columns q = (j, c)): thread t
+// accumulates sum_k W[v][k] s[j][k][c] for its column and up to 16 views in
+// registers, four Gaussians per step, with the next step's radiance already
+// loading while the current one is multiplied (register double buffer: the
+// kernel is bound by the bytes in flight).  The chunk's visibility weights
+// are staged 256 Gaussians at a time in shared memory as [view][k] and read
+// as 16-byte broadcasts.  With C = 1 (K even) a column's four Gaussians are
+// 32 contiguous bytes, read as two 16-byte loads, so each warp load uses
+// whole sectors.
+template <bool kVec>
+__device__ __forceinline__ void ws_load4(const float2* col, int k, int kk, int kn, int C,
+                                         bool act, float2 (&sv)[4]) {
+  if (kVec && act && kk + 4 <= kn) {
+    const float4 a4 = *reinterpret_cast<const float4*>(col + k);
+    const float4 b4 = *reinterpret_cast<const float4*>(col + k + 2);
+    sv[0] = make_float2(a4.x, a4.y);
+    sv[1] = make_float2(a4.z, a4.w);
+    sv[2] = make_float2(b4.x, b4.y);
+    sv[3] = make_float2(b4.z, b4.w);
+  } else {
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      sv[x] = (act && kk + x < kn) ? col[static_cast<size_t>(k + x) * C] : make_float2(0.f, 0.f);
+  }
+}
+
+template <bool kVec>
 __global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restrict__ rad, int N,
                                                            int K, int C,
                                                            const float* __restrict__ W, int M,
                                                            int v0, int nv,
                                                            float* __restrict__ part) {
-  __shared__ __align__(16) float sW[kWsSub][kWsMaxViews];
+  __shared__ __align__(16) float sW[kWsMaxViews][kWsSub];
   const int chunk = blockIdx.x, t = threadIdx.x;
-  const int q = blockIdx.y * 256 + t;  // complex column (j, c)
-  const bool active = q < N * C;
-  const int j = active ? q / C : 0, c = active ? q - j * C : 0;
+  const int ncq = N * C;
+  const int qcol = blockIdx.y * 256 + t;
+  const bool act = qcol < ncq;
+  const int jq = act ? qcol / C : 0, cq = act ? qcol - jq * C : 0;
+  const float2* col = reinterpret_cast<const float2*>(rad) + static_cast<size_t>(jq) * K * C + cq;
   const int k0 = chunk * kWsChunk, k1 = min(K, k0 + kWsChunk);
   float acc[kWsMaxViews][2];
 #pragma unroll
   for (int v = 0; v < kWsMaxViews; ++v) acc[v][0] = acc[v][1] = 0.0f;
-  const float2* col = reinterpret_cast<const float2*>(rad) + static_cast<size_t>(j) * K * C + c;
   for (int ks = k0; ks < k1; ks += kWsSub) {
     const int kn = min(kWsSub, k1 - ks);
     __syncthreads();  // the previous stage is consumed
-    {
-      float wv[kWsMaxViews];
 #pragma unroll
-      for (int v = 0; v < kWsMaxViews; ++v)
-        wv[v] = (v < nv && t < kn) ? W[static_cast<size_t>(v0 + v) * K + ks + t] : 0.0f;
-#pragma unroll
-      for (int v4 = 0; v4 < kWsMaxViews / 4; ++v4)
-        *reinterpret_cast<float4*>(&sW[t][4 * v4]) =
-            make_float4(wv[4 * v4], wv[4 * v4 + 1], wv[4 * v4 + 2], wv[4 * v4 + 3]);
-    }
+    for (int v = 0; v < kWsMaxViews; ++v)
+      sW[v][t] = (v < nv && t < kn) ? W[static_cast<size_t>(v0 + v) * K + ks + t] : 0.0f;
     __syncthreads();
-    if (active) {
-#pragma unroll 4
-      for (int kk = 0; kk < kn; ++kk) {
-        const float2 sv = col[static_cast<size_t>(ks + kk) * C];
+    // four Gaussians per step; sW is zero past kn, and the loads of
+    // Gaussians past kn are skipped
+    float2 cur[4], nxt[4];
+    ws_load4<kVec>(col, ks, 0, kn, C, act, cur);
+    for (int kk = 0; kk < kn; kk += 4) {
+      if (kk + 4 < kn) ws_load4<kVec>(col, ks + kk + 4, kk + 4, kn, C, act, nxt);
 #pragma unroll
-        for (int v4 = 0; v4 < kWsMaxViews / 4; ++v4) {
-          const float4 w4 = *reinterpret_cast<const float4*>(&sW[kk][4 * v4]);
-          acc[4 * v4 + 0][0] = fmaf(w4.x, sv.x, acc[4 * v4 + 0][0]);
-          acc[4 * v4 + 0][1] = fmaf(w4.x, sv.y, acc[4 * v4 + 0][1]);
-          acc[4 * v4 + 1][0] = fmaf(w4.y, sv.x, acc[4 * v4 + 1][0]);
-          acc[4 * v4 + 1][1] = fmaf(w4.y, sv.y, acc[4 * v4 + 1][1]);
-          acc[4 * v4 + 2][0] = fmaf(w4.z, sv.x, acc[4 * v4 + 2][0]);
-          acc[4 * v4 + 2][1] = fmaf(w4.z, sv.y, acc[4 * v4 + 2][1]);
-          acc[4 * v4 + 3][0] = fmaf(w4.w, sv.x, acc[4 * v4 + 3][0]);
-          acc[4 * v4 + 3][1] = fmaf(w4.w, sv.y, acc[4 * v4 + 3][1]);
-        }
+      for (int v = 0; v < kWsMaxViews; ++v) {
+        const float4 w4 = *reinterpret_cast<const float4*>(&sW[v][kk]);
+        float re = acc[v][0], im = acc[v][1];
+        re = fmaf(w4.x, cur[0].x, re);
+        im = fmaf(w4.x, cur[0].y, im);
+        re = fmaf(w4.y, cur[1].x, re);
+        im = fmaf(w4.y, cur[1].y, im);
+        re = fmaf(w4.z, cur[2].x, re);
+        im = fmaf(w4.z, cur[2].y, im);
+        re = fmaf(w4.w, cur[3].x, re);
+        im = fmaf(w4.w, cur[3].y, im);
+        acc[v][0] = re;
+        acc[v][1] = im;
       }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) cur[x] = nxt[x];
     }
   }
-  if (!active) return;
+  if (!act) return;
   const int twoC = 2 * C;
 #pragma unroll
   for (int v = 0; v < kWsMaxViews; ++v) {
     if (v >= nv) break;
-    float* dst = part + ((static_cast<size_t>(chunk) * N + j) * M + v0 + v) * twoC + 2 * c;
+    float* dst = part + ((static_cast<size_t>(chunk) * N + jq) * M + v0 + v) * twoC + 2 * cq;
     dst[0] = acc[v][0];
     dst[1] = acc[v][1];
   }
@@ -189,9 +209,16 @@ void launch_weighted_sum(const float* rad, int N, int K, int C, const float* W, 
                          float* csi, float* rssi, cudaStream_t s) {
   const int nchunks = (K + kWsChunk - 1) / kWsChunk;
   const unsigned colblocks = static_cast<unsigned>((N * C + 255) / 256);
+  // 16-byte loads need each receiver row of a single channel to start on 16 B
+  const bool vec = C == 1 && K % 2 == 0 && (reinterpret_cast<uintptr_t>(rad) & 15) == 0;
   for (int v0 = 0; v0 < M; v0 += kWsMaxViews) {
     const int nv = min(kWsMaxViews, M - v0);
-    weighted_sum_kernel<<<dim3(nchunks, colblocks), 256, 0, s>>>(rad, N, K, C, W, M, v0, nv, tmp);
+    if (vec)
+      weighted_sum_kernel<true><<<dim3(nchunks, colblocks), 256, 0, s>>>(rad, N, K, C, W, M, v0,
+                                                                          nv, tmp);
+    else
+      weighted_sum_kernel<false><<<dim3(nchunks, colblocks), 256, 0, s>>>(rad, N, K, C, W, M, v0,
+                                                                           nv, tmp);
     note_launches(1);
   }
   const int n = M * N * C;

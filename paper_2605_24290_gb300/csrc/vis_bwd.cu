@@ -24,20 +24,27 @@ namespace rxgs {
 constexpr int kVbViews = 16;   // views per pass of the column kernels
 constexpr int kGamCols = 128;  // complex columns staged per step in gamma_kernel
 
-// gamma[v][k] for v in [v0, v0 + nv): thread k (256 per block) walks all
+// gamma[v][k] for v in [v0, v0 + nv): thread = 4 consecutive Gaussians
+// (1,024 per block), 16 views x 4 Gaussians in registers, walking all
 // complex columns q = (j, c); the cotangents of 128 columns for the pass's
-// views are staged in shared memory as [q][view] (re, im).
+// views are staged in shared memory as [q][view] (re, im) and read as
+// 16-byte broadcasts.  With C = 1 (K even) the four Gaussians of a column
+// are 32 contiguous bytes (two 16-byte loads).
+template <bool kVec>
 __global__ void __launch_bounds__(256) gamma_kernel(const float* __restrict__ rad, int N, int K,
                                                     int C, const float* __restrict__ gu, int M,
                                                     int v0, int nv, float* __restrict__ gamma) {
   __shared__ __align__(16) float sg[kGamCols][kVbViews][2];
   const int t = threadIdx.x;
-  const int k = blockIdx.x * 256 + t;
+  const int k0 = (blockIdx.x * 256 + t) * 4;
   const int ncq = N * C;
-  float acc[kVbViews];
+  float acc[kVbViews][4];
 #pragma unroll
-  for (int v = 0; v < kVbViews; ++v) acc[v] = 0.0f;
+  for (int v = 0; v < kVbViews; ++v)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) acc[v][x] = 0.0f;
   const float2* r2 = reinterpret_cast<const float2*>(rad);
+  const bool full = k0 + 4 <= K;
   for (int q0 = 0; q0 < ncq; q0 += kGamCols) {
     const int nq = min(kGamCols, ncq - q0);
     __syncthreads();
@@ -50,23 +57,43 @@ __global__ void __launch_bounds__(256) gamma_kernel(const float* __restrict__ ra
       sg[qq][v][1] = x.y;
     }
     __syncthreads();
-    if (k < K) {
+    if (k0 < K) {
       for (int qq = 0; qq < nq; ++qq) {
         const int q = q0 + qq, j = q / C, c = q - j * C;
-        const float2 s = r2[(static_cast<size_t>(j) * K + k) * C + c];
+        const float2* cp = r2 + (static_cast<size_t>(j) * K + k0) * C + c;
+        float2 sv[4];
+        if (kVec && full) {
+          const float4 a4 = *reinterpret_cast<const float4*>(cp);
+          const float4 b4 = *reinterpret_cast<const float4*>(cp + 2);
+          sv[0] = make_float2(a4.x, a4.y);
+          sv[1] = make_float2(a4.z, a4.w);
+          sv[2] = make_float2(b4.x, b4.y);
+          sv[3] = make_float2(b4.z, b4.w);
+        } else {
 #pragma unroll
-        for (int v4 = 0; v4 < kVbViews / 2; ++v4) {
-          const float4 g4 = *reinterpret_cast<const float4*>(&sg[qq][2 * v4][0]);
-          acc[2 * v4] = fmaf(g4.x, s.x, fmaf(g4.y, s.y, acc[2 * v4]));
-          acc[2 * v4 + 1] = fmaf(g4.z, s.x, fmaf(g4.w, s.y, acc[2 * v4 + 1]));
+          for (int x = 0; x < 4; ++x)
+            sv[x] = k0 + x < K ? cp[static_cast<size_t>(x) * C] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int v2 = 0; v2 < kVbViews / 2; ++v2) {
+          const float4 g4 = *reinterpret_cast<const float4*>(&sg[qq][2 * v2][0]);
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            acc[2 * v2][x] = fmaf(g4.x, sv[x].x, fmaf(g4.y, sv[x].y, acc[2 * v2][x]));
+            acc[2 * v2 + 1][x] = fmaf(g4.z, sv[x].x, fmaf(g4.w, sv[x].y, acc[2 * v2 + 1][x]));
+          }
         }
       }
     }
   }
-  if (k >= K) return;
+  if (k0 >= K) return;
 #pragma unroll
-  for (int v = 0; v < kVbViews; ++v)
-    if (v < nv) gamma[static_cast<size_t>(v0 + v) * K + k] = acc[v];
+  for (int v = 0; v < kVbViews; ++v) {
+    if (v >= nv) break;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      if (k0 + x < K) gamma[static_cast<size_t>(v0 + v) * K + k0 + x] = acc[v][x];
+  }
 }
 
 // Back-to-front sweep of one (view, tile) with the scalar gamma: one thread
@@ -199,6 +226,7 @@ __global__ void __launch_bounds__(kTilePixels) bwd_uniform_kernel(
 // in shared memory.
 constexpr int kOutCols = 64;
 
+template <bool kVec>
 __global__ void __launch_bounds__(256) outer_kernel(const float* __restrict__ W, int K,
                                                     const float* __restrict__ gu, int N, int C,
                                                     int v0, int nv, float* __restrict__ grad) {
@@ -236,13 +264,28 @@ __global__ void __launch_bounds__(256) outer_kernel(const float* __restrict__ W,
       }
     }
     float2* dst = reinterpret_cast<float2*>(grad) + (static_cast<size_t>(j) * K + k0) * C + c;
+    if (kVec && k0 + 4 <= K) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      float4 a4 = d4[0], b4 = d4[1];
+      a4.x += re[0];
+      a4.y += im[0];
+      a4.z += re[1];
+      a4.w += im[1];
+      b4.x += re[2];
+      b4.y += im[2];
+      b4.z += re[3];
+      b4.w += im[3];
+      d4[0] = a4;
+      d4[1] = b4;
+    } else {
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      if (k0 + x >= K) break;
-      float2 o = dst[static_cast<size_t>(x) * C];
-      o.x += re[x];
-      o.y += im[x];
-      dst[static_cast<size_t>(x) * C] = o;
+      for (int x = 0; x < 4; ++x) {
+        if (k0 + x >= K) break;
+        float2 o = dst[static_cast<size_t>(x) * C];
+        o.x += re[x];
+        o.y += im[x];
+        dst[static_cast<size_t>(x) * C] = o;
+      }
     }
   }
 }
@@ -252,9 +295,15 @@ void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float
   const RenderArgs& a = A.f;
   const int M = a.M, K = a.K, N = a.N, C = a.C;
   if (M <= 0 || K <= 0) return;
+  // 16-byte access to a single channel's rows needs K even and 16-byte bases
+  const bool vec_r = C == 1 && K % 2 == 0 && (reinterpret_cast<uintptr_t>(rad_rm) & 15) == 0;
+  const unsigned kb = static_cast<unsigned>((K + 1023) / 1024);
   for (int v0 = 0; v0 < M; v0 += kVbViews) {
     const int nv = min(kVbViews, M - v0);
-    gamma_kernel<<<(K + 255) / 256, 256, 0, s>>>(rad_rm, N, K, C, gu, M, v0, nv, gamma);
+    if (vec_r)
+      gamma_kernel<true><<<kb, 256, 0, s>>>(rad_rm, N, K, C, gu, M, v0, nv, gamma);
+    else
+      gamma_kernel<false><<<kb, 256, 0, s>>>(rad_rm, N, K, C, gu, M, v0, nv, gamma);
     note_launches(1);
   }
   bwd_uniform_kernel<<<dim3(a.g.T, 1, M), kTilePixels, 0, s>>>(a, gamma, A.tfin, A.stops,
@@ -262,11 +311,14 @@ void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float
                                                                A.d_tau);
   note_launches(1);
   if (!grad_radiance) return;
-  const unsigned kb = static_cast<unsigned>((K + 1023) / 1024);
+  const bool vec_g = C == 1 && K % 2 == 0 && (reinterpret_cast<uintptr_t>(grad_radiance) & 15) == 0;
   const unsigned qb = static_cast<unsigned>((N * C + kOutCols - 1) / kOutCols);
   for (int v0 = 0; v0 < M; v0 += kVbViews) {
     const int nv = min(kVbViews, M - v0);
-    outer_kernel<<<dim3(kb, qb), 256, 0, s>>>(W, K, gu, N, C, v0, nv, grad_radiance);
+    if (vec_g)
+      outer_kernel<true><<<dim3(kb, qb), 256, 0, s>>>(W, K, gu, N, C, v0, nv, grad_radiance);
+    else
+      outer_kernel<false><<<dim3(kb, qb), 256, 0, s>>>(W, K, gu, N, C, v0, nv, grad_radiance);
     note_launches(1);
   }
 }

@@ -111,6 +111,39 @@ def test_backward_csi_and_rssi_cotangents(torch, rx, oracle):
     assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
 
 
+def test_backward_csi_wide_channels_odd_k(torch, rx, oracle):
+    """CSI cotangent with C = 2 and an odd Gaussian count (the
+    visibility-weight backward's scalar loads), two views."""
+    rng = np.random.default_rng(205)
+    K, N, C = 3001, 5, 2
+    sc = S.draw_scene(rng, K)
+    tx = S.draw_points(rng, 2)
+    rad = S.draw_radiance(rng, N, K, C)
+    g = S.Grid()
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch, C=C)
+    views = ctx.prepare(h, dev(tx, torch))
+    radd = dev(rad, torch)
+    csi = torch.zeros((2, N, C, 2), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_CSI, radiance=radd, csi=csi, reduce_path=1)
+    gc = rng.normal(size=(2, N, C, 2)).astype(np.float32)
+    d_rad = torch.zeros_like(radd)
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, None, N, rx.OUT_CSI, radiance=radd, grad_csi=dev(gc, torch),
+                        grad_radiance=d_rad, grad_opacity=d_tau)
+    ctx.sync()
+    gspec = np.broadcast_to(gc.astype(np.float64)[:, :, None, None, :, :],
+                            (2, N, g.H, g.W, C, 2)).copy()
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gspec)
+    assert scaled_err(d_rad.cpu().numpy(), ref_r, abs_r) <= TOL
+    assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
+    for v in range(2):
+        o = oracle.render_view(g, sc, tx[v], rad.astype(np.float64))
+        a = o["absacc"].sum(axis=(1, 2))
+        e = np.abs(csi[v].cpu().numpy() - oracle.csi(o["spectra"])) / (a[..., None] + 1e-30)
+        assert float(e.max()) <= TOL
+
+
 @pytest.mark.parametrize("N,C", [(8, 1), (8, 3), (40, 2), (6, 4)])
 def test_backward_through_mlp(torch, rx, oracle, N, C):
     """Cotangent on spectra through the conditioning MLP to phi_base, the MLP
