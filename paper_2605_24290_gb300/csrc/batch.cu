@@ -400,6 +400,7 @@ static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState*
     return st;
   }
   ctx->plans.push_back(p);
+  ctx->plans_built++;
   *out = p;
   return RXGS_OK;
 }
@@ -407,18 +408,26 @@ static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState*
 // The smallest existing plan that fits, so launch sizes stay within 2x of
 // the batch (plans come in power-of-two size classes of views and receivers).
 static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, bool vis, int B,
-                            int R, int tag) {
+                            int R, int tag, bool allow_larger) {
   const int NB = ctx->opts.cols_per_cta ? ctx->opts.cols_per_cta : 64;
   const int Bc = next_pow2(B, 4), Rc = next_pow2(R, 32);
   BatchPlan* best = nullptr;
-  for (BatchPlan* q : ctx->plans)
-    if (q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp && q->vis == vis &&
-        q->B_max >= B && q->R_max >= R && q->B_max <= 2 * Bc && q->R_max <= 2 * Rc &&
-        q->g.TH == ctx->g.TH &&
-        q->g.TW == ctx->g.TW && q->NB == NB &&
-        (!best || static_cast<size_t>(q->B_max) * q->R_max <
-                      static_cast<size_t>(best->B_max) * best->R_max))
+  BatchPlan* any = nullptr;  // the smallest fitting plan of any size
+  for (BatchPlan* q : ctx->plans) {
+    if (!(q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp &&
+          q->vis == vis && q->B_max >= B && q->R_max >= R && q->g.TH == ctx->g.TH &&
+          q->g.TW == ctx->g.TW && q->NB == NB))
+      continue;
+    const size_t sz = static_cast<size_t>(q->B_max) * q->R_max;
+    if (!any || sz < static_cast<size_t>(any->B_max) * any->R_max) any = q;
+    if (q->B_max <= 2 * Bc && q->R_max <= 2 * Rc &&
+        (!best || sz < static_cast<size_t>(best->B_max) * best->R_max))
       best = q;
+  }
+  // with allow_larger, a batch whose size class has no plan yet runs in a
+  // larger one when there is one (its kernels read the real sizes from the
+  // descriptor) rather than waiting for a plan to be built and captured
+  if (!best && allow_larger) best = any;
   return best;
 }
 
@@ -437,6 +446,18 @@ void rxgs::drop_plans(rxgs_ctx* ctx, int tag) {
   ctx->plans.swap(keep);
 }
 
+void rxgs::drop_plan(rxgs_ctx* ctx, const void* plan) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::vector<BatchPlan*> keep;
+  for (BatchPlan* q : ctx->plans) {
+    if (q == plan)
+      destroy_plan(q);
+    else
+      keep.push_back(q);
+  }
+  ctx->plans.swap(keep);
+}
+
 // Exact instance count of a batch's views (one synchronising readback);
 // used to size a new plan.
 static rxgs_status count_instances(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
@@ -446,7 +467,7 @@ namespace rxgs {
 rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
                                   const float* rx, const int32_t* rx_counts,
                                   const rxgs_render_desc* d, rxgs_outputs* out, void* stream,
-                                  int tag, double inst_margin) {
+                                  int tag, double inst_margin, const void** plan_used) {
   if (!ctx || !tx || !rx_counts || !d || !out) return fail(ctx, RXGS_E_INVALID, "null argument");
   if (B <= 0 || B > 4096) return fail(ctx, RXGS_E_INVALID, "B out of range");
   int R = 0;
@@ -481,7 +502,7 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
   BatchPlan* p = nullptr;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    p = find_plan(ctx, scene, kind, mlp, vis, B, R, tag);
+    p = find_plan(ctx, scene, kind, mlp, vis, B, R, tag, false);
   }
   if (!p) {
     uint32_t per_view = 0;
@@ -508,6 +529,7 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
                        cudaMemcpyDefault, st));
   // the pinned descriptor is consumed by the copy above before we return
   CK(cudaGraphLaunch(p->exec, st));
+  if (plan_used) *plan_used = p;
   const size_t HW2C = static_cast<size_t>(p->g.H) * p->g.W * 2 * s->C;
   if (kind & RXGS_OUT_SPECTRA)
     CK(cudaMemcpyAsync(out->spectra, p->spectra, sizeof(float) * R * HW2C, cudaMemcpyDeviceToDevice, st));

@@ -71,6 +71,7 @@ struct rxgs_ctx {
   std::map<uint64_t, rxgs::SceneState*> scenes;
   std::map<uint64_t, rxgs::ViewsState*> views;
   std::vector<rxgs::BatchPlan*> plans;
+  long plans_built = 0;           // batch plans built (graph captures) so far
   rxgs::ServeState* serve = nullptr;
   unsigned* d_err = nullptr;      // device error word
   uint32_t* h_pinned = nullptr;   // pinned readback slot
@@ -156,7 +157,10 @@ int pick_cols(const rxgs_ctx* ctx, int ncols);
 rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int B,
                                   const float* rx, const int32_t* rx_counts,
                                   const rxgs_render_desc* d, rxgs_outputs* out, void* stream,
-                                  int tag, double inst_margin);
+                                  int tag, double inst_margin, const void** plan_used = nullptr);
 void drop_plans(rxgs_ctx* ctx, int tag);
+// Drops one plan (a batch overflowed its instance capacity); the caller has
+// synchronised the stream the plan ran on.
+void drop_plan(rxgs_ctx* ctx, const void* plan);
 
 }  // namespace rxgs

@@ -47,6 +47,7 @@ struct Slot {
   unsigned* h_err = nullptr;                                 // pinned
   float* d_out = nullptr;
   int cap_views = 0, cap_rx = 0, out_per_rx = 0;
+  const void* plan = nullptr;  // the batch plan of the batch in flight
 };
 
 struct ServeState {
@@ -67,6 +68,7 @@ struct ServeState {
   // statistics
   std::vector<double> lat_ms;
   long batches = 0, batch_rx = 0, failed = 0, retried = 0, cancelled = 0;
+  long plans_base = 0;  // ctx->plans_built at the last statistics reset
   Clock::time_point t_start;
 };
 
@@ -125,8 +127,9 @@ static void worker_main(ServeState* S) {
         cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), sl.st);
         cudaStreamSynchronize(sl.st);
         lk.unlock();
-        drop_plans(ctx, sl.tag);
+        drop_plan(ctx, sl.plan);  // only the plan that overflowed is rebuilt
         lk.lock();
+        sl.plan = nullptr;
         for (auto it = sl.reqs.rbegin(); it != sl.reqs.rend(); ++it) S->queue.push_front(*it);
         S->retried += static_cast<long>(sl.reqs.size());
         S->inflight_bytes -= sl.bytes;
@@ -198,7 +201,7 @@ static void worker_main(ServeState* S) {
       else
         out.csi = sl.d_out;
       st = render_batched_tagged(ctx, S->scene, sl.h_tx, static_cast<int>(sl.reqs.size()), sl.h_rx,
-                                 sl.counts.data(), &d, &out, sl.st, sl.tag, 2.0);
+                                 sl.counts.data(), &d, &out, sl.st, sl.tag, 2.0, &sl.plan);
       if (st == RXGS_OK) {
         cudaMemcpyAsync(sl.h_out, sl.d_out, sizeof(float) * static_cast<size_t>(nrx) * sl.out_per_rx,
                         cudaMemcpyDeviceToHost, sl.st);
@@ -402,13 +405,19 @@ rxgs_status rxgs_serve_stats(rxgs_ctx* ctx, char* json, size_t cap) {
   };
   const double el = std::chrono::duration<double>(Clock::now() - S->t_start).count();
   const double mean = v.empty() ? 0.0 : std::accumulate(v.begin(), v.end(), 0.0) / v.size();
-  char buf[768];
+  long built = 0;
+  {
+    std::lock_guard<std::mutex> lc(ctx->mu);
+    built = ctx->plans_built - S->plans_base;
+  }
+  char buf[800];
   snprintf(buf, sizeof buf,
            "{\"completed\": %zu, \"failed\": %ld, \"retried\": %ld, \"cancelled\": %ld, "
+           "\"plans_built\": %ld, "
            "\"batches\": %ld, \"mean_batch_receivers\": %.2f, \"p50_ms\": %.4f, \"p90_ms\": %.4f, "
            "\"p99_ms\": %.4f, \"max_ms\": %.4f, \"mean_ms\": %.4f, \"queued\": %zu, "
            "\"inflight_bytes\": %zu, \"elapsed_s\": %.3f}",
-           v.size(), S->failed, S->retried, S->cancelled, S->batches,
+           v.size(), S->failed, S->retried, S->cancelled, built, S->batches,
            S->batches ? static_cast<double>(S->batch_rx) / S->batches : 0.0, pct(0.5), pct(0.9),
            pct(0.99), v.empty() ? 0.0 : v.back(), mean, S->queue.size(), S->inflight_bytes, el);
   if (strlen(buf) + 1 > cap) return RXGS_E_INVALID;
@@ -422,6 +431,10 @@ rxgs_status rxgs_serve_reset_stats(rxgs_ctx* ctx) {
   std::lock_guard<std::mutex> lk(S->mu);
   S->lat_ms.clear();
   S->batches = S->batch_rx = S->failed = S->retried = S->cancelled = 0;
+  {
+    std::lock_guard<std::mutex> lc(ctx->mu);
+    S->plans_base = ctx->plans_built;
+  }
   S->t_start = Clock::now();
   return RXGS_OK;
 }
