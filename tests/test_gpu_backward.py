@@ -49,7 +49,7 @@ def oracle_grads(oracle, g, sc, tx, rad, gspec):
     return tot
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 32)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
 def test_backward_explicit_radiance(torch, rx, oracle, tile):
     """Cotangent on spectra, two transmitters, 8 receivers."""
     rng = np.random.default_rng(201)
