@@ -435,7 +435,8 @@ def gpu_bench(args):
 
 
 # ---------------------------------------------------------------- serving
-def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0):
+def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0, sweep_factors=(0.5, 2.0, 4.0),
+                sweep_seconds=3.0):
     """300,000 resident Gaussians (MLP radiance), Poisson requests at `rate`
     per second, each 1 transmitter and n = floor(exp(U(0, ln 1025))) receivers,
     RSSI out; latency = submit to completion (library-side)."""
@@ -493,6 +494,17 @@ def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0):
     ctx.serve_reset_stats()
     nreq, nrx, wall = run(seconds, rate)
     st = ctx.serve_stats()
+    # the same stream at 0.5x, 2x and 4x the rate (shorter runs)
+    sweep = []
+    for f in sweep_factors:
+        ctx.serve_reset_stats()
+        n2, r2, w2 = run(sweep_seconds, rate * f)
+        s2 = ctx.serve_stats()
+        sweep.append({"offered_rps": rate * f, "achieved_rps": round(n2 / w2, 2),
+                      "receivers_per_s": round(r2 / w2, 1), "requests": n2,
+                      "p50_ms": s2["p50_ms"], "p99_ms": s2["p99_ms"], "max_ms": s2["max_ms"],
+                      "mean_batch_receivers": s2["mean_batch_receivers"],
+                      "plans_built": s2["plans_built"]})
     ctx.serve_stop()
     ctx.close()
     return {"offered_rps": rate, "achieved_rps": round(nreq / wall, 2),
@@ -501,7 +513,7 @@ def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0):
             "max_ms": st["max_ms"], "batches": st["batches"],
             "mean_batch_receivers": st["mean_batch_receivers"], "failed": st["failed"],
             "retried": st["retried"], "plans_built": st["plans_built"],
-            "mem_budget_bytes": budget, "slots": 2,
+            "mem_budget_bytes": budget, "slots": 2, "rate_sweep": sweep,
             "workload": "300k Gaussians, MLP radiance, RSSI, Poisson arrivals, n log-uniform 1..1024"}
 
 
