@@ -372,3 +372,73 @@ def mlp_backward(params, rx, means, base, grad_s):
     out["g_w1"] = d_hg.T @ xg
     out["g_b1"] = d_hg.sum(axis=0)
     return out
+
+
+# --------------------------------- FLE directional radiance (App. E.2, Alg. 1)
+# For the direction from the transmitter to a Gaussian's centre, with polar
+# angle theta (cos theta = u_z / |u|) and azimuth phi = atan2(u_y, u_x):
+#   s = sum_{l <= lmax} sum_{|m| <= l} (a_lm + i b_lm) N_l|m| P_l^|m|(cos theta) e^{i m phi}
+# i.e. Re s = sum [a cos(m phi) - b sin(m phi)] N P,  Im s = sum [a sin + b cos] N P,
+# N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!), P_l^m without the
+# Condon-Shortley phase.  Component index of (l, m): l*l + l + m.
+
+def fle_count(lmax: int) -> int:
+    return (lmax + 1) ** 2
+
+
+def assoc_legendre(lmax: int, x):
+    """P_l^m(x), 0 <= m <= l <= lmax, no Condon-Shortley phase, by the
+    three-term recurrence: P_m^m = (2m-1)!! (1-x^2)^(m/2),
+    P_{m+1}^m = (2m+1) x P_m^m, (l-m) P_l^m = (2l-1) x P_{l-1}^m - (l+m-1) P_{l-2}^m.
+    Returns P[l, m, ...]."""
+    x = np.asarray(x, np.float64)
+    s = np.sqrt(np.maximum(0.0, 1.0 - x * x))
+    P = np.zeros((lmax + 1, lmax + 1) + x.shape, np.float64)
+    pmm = np.ones_like(x)
+    for m in range(lmax + 1):
+        if m > 0:
+            pmm = pmm * (2 * m - 1) * s
+        P[m, m] = pmm
+        if m + 1 <= lmax:
+            P[m + 1, m] = (2 * m + 1) * x * pmm
+        for l in range(m + 2, lmax + 1):
+            P[l, m] = ((2 * l - 1) * x * P[l - 1, m] - (l + m - 1) * P[l - 2, m]) / (l - m)
+    return P
+
+
+def fle_norm(l: int, m: int) -> float:
+    import math
+    m = abs(m)
+    return math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+
+
+def fle_basis(means, centre, lmax: int):
+    """Complex basis Y[K, L] of each Gaussian's direction from `centre`."""
+    u = np.asarray(means, np.float64) - np.asarray(centre, np.float64)[None, :]
+    rho = np.sqrt((u * u).sum(axis=1))
+    ct = u[:, 2] / rho
+    phi = np.arctan2(u[:, 1], u[:, 0])
+    P = assoc_legendre(lmax, ct)
+    Y = np.zeros((u.shape[0], fle_count(lmax)), np.complex128)
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            Y[:, l * l + l + m] = fle_norm(l, m) * P[l, abs(m)] * np.exp(1j * m * phi)
+    return Y
+
+
+def fle_radiance(coeffs, means, centre, lmax: int):
+    """Radiance [N,K,1,2] of one view from coefficients [N,K,2,L]."""
+    c = np.asarray(coeffs, np.float64)
+    Y = fle_basis(means, centre, lmax)                      # [K, L]
+    s = ((c[:, :, 0, :] + 1j * c[:, :, 1, :]) * Y[None]).sum(axis=-1)   # [N, K]
+    return np.stack([s.real, s.imag], axis=-1)[:, :, None, :]
+
+
+def fle_backward(grad_rad, means, centre, lmax: int):
+    """dL/dcoeffs [N,K,2,L] of one view from dL/dradiance [N,K,1,2]:
+    dL/da = g_re Re Y + g_im Im Y, dL/db = -g_re Im Y + g_im Re Y."""
+    g = np.asarray(grad_rad, np.float64)[:, :, 0, :]          # [N, K, 2]
+    Y = fle_basis(means, centre, lmax)[None]                  # [1, K, L]
+    da = g[..., 0:1] * Y.real + g[..., 1:2] * Y.imag
+    db = -g[..., 0:1] * Y.imag + g[..., 1:2] * Y.real
+    return np.stack([da, db], axis=2)

@@ -519,3 +519,86 @@ def test_backward_on_pixel_subsets_adds_up(oracle):
         acc_t += t
     np.testing.assert_allclose(acc_r, gr, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(acc_t, gt, rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------------ FLE basis pins
+def test_fle_legendre_closed_forms(oracle):
+    """P_l^m for l <= 2 against the closed forms (no Condon-Shortley phase)."""
+    x = np.linspace(-0.97, 0.97, 31)
+    P = oracle.assoc_legendre(2, x)
+    s = np.sqrt(1 - x * x)
+    np.testing.assert_allclose(P[0, 0], 1.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(P[1, 0], x, rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(P[1, 1], s, rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(P[2, 0], 0.5 * (3 * x * x - 1), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(P[2, 1], 3 * x * s, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(P[2, 2], 3 * (1 - x * x), rtol=1e-14, atol=1e-15)
+
+
+def test_fle_legendre_matches_scipy():
+    """scipy's lpmv carries the Condon-Shortley phase (-1)^m."""
+    sp = pytest.importorskip("scipy.special")
+    from oracle import oracle as O
+    x = np.linspace(-0.99, 0.99, 41)
+    P = O.assoc_legendre(9, x)
+    for l in range(10):
+        for m in range(l + 1):
+            np.testing.assert_allclose(P[l, m], (-1) ** m * sp.lpmv(m, l, x), rtol=1e-10,
+                                       atol=1e-10 * max(1.0, np.abs(P[l, m]).max()))
+
+
+def test_fle_basis_is_orthonormal_on_the_sphere(oracle):
+    """Gauss-Legendre in cos(theta) x uniform azimuth integrates Y_a conj(Y_b)
+    exactly for l <= 9: the Gram matrix is the identity."""
+    lmax = 9
+    xg, wg = np.polynomial.legendre.leggauss(24)
+    nphi = 32
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    ct = np.repeat(xg, nphi)
+    st = np.sqrt(1 - ct * ct)
+    ph = np.tile(phi, xg.size)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+    w = np.repeat(wg, nphi) * (2 * np.pi / nphi)
+    Y = oracle.fle_basis(dirs, np.zeros(3), lmax)            # centre at the origin
+    G = (Y * w[:, None]).T @ Y.conj()
+    np.testing.assert_allclose(G, np.eye(Y.shape[1]), atol=1e-12)
+
+
+def test_fle_radiance_special_cases(oracle):
+    """Only a_00: s = a / sqrt(4 pi) in every direction; only a_10:
+    s = sqrt(3 / (4 pi)) cos(theta); only b_11: s = i sqrt(3/(8 pi)) sin(theta) e^{i phi}."""
+    rng = np.random.default_rng(5)
+    means = rng.normal(size=(7, 3))
+    tx = rng.normal(size=3)
+    u = means - tx
+    rho = np.linalg.norm(u, axis=1)
+    L = oracle.fle_count(2)
+    c = np.zeros((1, 7, 2, L))
+    c[0, :, 0, 0] = 2.5
+    s = oracle.fle_radiance(c, means, tx, 2)[0, :, 0]
+    np.testing.assert_allclose(s[:, 0], 2.5 / np.sqrt(4 * np.pi), rtol=1e-14)
+    np.testing.assert_allclose(s[:, 1], 0.0, atol=1e-15)
+    c[:] = 0
+    c[0, :, 0, 2] = 1.0                                       # (l, m) = (1, 0)
+    s = oracle.fle_radiance(c, means, tx, 2)[0, :, 0]
+    np.testing.assert_allclose(s[:, 0], np.sqrt(3 / (4 * np.pi)) * u[:, 2] / rho, rtol=1e-13)
+    c[:] = 0
+    c[0, :, 1, 3] = 1.0                                       # b_11: i * N11 P11 e^{i phi}
+    s = oracle.fle_radiance(c, means, tx, 2)[0, :, 0]
+    h = np.hypot(u[:, 0], u[:, 1])
+    e = (u[:, 0] + 1j * u[:, 1]) / h
+    ref = 1j * np.sqrt(3 / (8 * np.pi)) * (h / rho) * e
+    np.testing.assert_allclose(s[:, 0], ref.real, atol=1e-14)
+    np.testing.assert_allclose(s[:, 1], ref.imag, atol=1e-14)
+
+
+def test_fle_backward_is_the_adjoint(oracle):
+    """<g, J c> = <J^T g, c> for the linear map coefficients -> radiance."""
+    rng = np.random.default_rng(6)
+    lmax, N, K = 4, 3, 11
+    means, tx = rng.normal(size=(K, 3)), rng.normal(size=3)
+    c = rng.normal(size=(N, K, 2, oracle.fle_count(lmax)))
+    g = rng.normal(size=(N, K, 1, 2))
+    lhs = (g * oracle.fle_radiance(c, means, tx, lmax)).sum()
+    rhs = (oracle.fle_backward(g, means, tx, lmax) * c).sum()
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
