@@ -140,15 +140,29 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream);
  *   kind       RXGS_OUT_* bitmask
  *   radiance   [N,K,C,2] receiver-major float32 (the paper's (N, K, 2)
  *              signal tensor), shared by all transmitters; NULL = evaluate
- *              the scene's conditioning MLP for the receivers
+ *              the scene's conditioning MLP for the receivers (unless
+ *              fle_coeffs is given)
  *   reduce_path for RSSI/CSI without spectra: 0 = per-pixel compositing then
  *              a sum over pixels; 1 = visibility weights W_k (Eq.
  *              render_reorder) then sum_k W_k s_kj.  Both give the same
- *              value up to rounding order. */
+ *              value up to rounding order.
+ *   fle_coeffs [N,K,2,L] float32, L = (fle_lmax + 1)^2, or NULL: the
+ *              per-receiver directional coefficients of the Fourier-Legendre
+ *              radiance (App. E.2, the tensor Algorithm 1 reduces against the
+ *              transmitter-side basis).  Component l*l + l + m holds a_lm
+ *              ([..][0][.]) and b_lm ([..][1][.]); for the direction from the
+ *              transmitter to Gaussian k (polar angle theta from +z, azimuth
+ *              phi) s = sum (a + i b) N_l|m| P_l^|m|(cos theta) e^{i m phi},
+ *              P without the Condon-Shortley phase.  Needs C == 1,
+ *              radiance == NULL, reduce_path == 0 and 0 <= fle_lmax <= 9; the
+ *              radiance then differs per transmitter.
+ *   fle_lmax   the degree of fle_coeffs */
 typedef struct {
   int kind;
   const float* radiance;
   int reduce_path;
+  const float* fle_coeffs;
+  int fle_lmax;
 } rxgs_render_desc;
 
 /* Outputs, all optional except those `kind` asks for:
@@ -285,6 +299,7 @@ typedef struct {
   float* grad_opacity;
   float* grad_base;
   float* grad_mlp;
+  float* grad_fle;       /* [N,K,2,L] += dL/dfle_coeffs (FLE radiance), or NULL */
 } rxgs_grads;
 
 rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,

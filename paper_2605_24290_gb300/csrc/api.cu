@@ -465,12 +465,18 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream) 
 // ------------------------------------------------------------------ render
 namespace {
 
-// Produces the Gaussian-major radiance [K][stride] for receivers rx[N].
-rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const float* rx, int N,
-                          const rxgs_render_desc* d, int stride, float* rad, float* glob,
-                          cudaStream_t st) {
-  Stage sg(ctx, d->radiance ? "radiance_transpose" : "mlp", st);
-  if (d->radiance) {
+// Produces the Gaussian-major radiance [K][stride] for receivers rx[N]; with
+// FLE coefficients, one such array per view of v ([M][K][stride]).
+rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* v,
+                          const float* rx, int N, const rxgs_render_desc* d, int stride,
+                          float* rad, float* glob, cudaStream_t st) {
+  Stage sg(ctx, d->radiance ? "radiance_transpose" : (d->fle_coeffs ? "fle" : "mlp"), st);
+  if (d->fle_coeffs) {
+    // pad columns of every row stay zero
+    cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
+    launch_fle_radiance(d->fle_coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+                        static_cast<size_t>(s->K) * stride, rad, st);
+  } else if (d->radiance) {
     launch_radiance_transpose(d->radiance, N, s->K, s->C, stride, rad, st);
   } else {
     if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
@@ -493,13 +499,19 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   if ((kind & RXGS_OUT_SPECTRA) && !out->spectra) return fail(ctx, RXGS_E_INVALID, "spectra == NULL");
   if ((kind & RXGS_OUT_RSSI) && !out->rssi) return fail(ctx, RXGS_E_INVALID, "rssi == NULL");
   if ((kind & RXGS_OUT_CSI) && !out->csi) return fail(ctx, RXGS_E_INVALID, "csi == NULL");
-  if (!d->radiance && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
+  if (!d->radiance && !d->fle_coeffs && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->views.find(views);
   if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
   ViewsState* v = it->second;
   const SceneState* s = ctx->scenes.at(v->scene);
   if ((kind & RXGS_OUT_RSSI) && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
+  if (d->fle_coeffs) {
+    if (d->radiance) return fail(ctx, RXGS_E_INVALID, "radiance and fle_coeffs exclude each other");
+    if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
+    if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
+    if (d->reduce_path == 1) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 does not take FLE radiance");
+  }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const GridConst& g = ctx->g;
@@ -553,19 +565,22 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   }
   const int ncols = 2 * N * s->C;
   const int stride = round_up(ncols, 128);
+  const bool fle = d->fle_coeffs != nullptr;
+  const size_t rad_view = fle ? static_cast<size_t>(s->K) * stride : 0;
   float* rad = nullptr;
   float* partial = nullptr;
   float* glob = nullptr;
-  CK(dalloc(&rad, static_cast<size_t>(s->K) * stride, st));
+  CK(dalloc(&rad, static_cast<size_t>(s->K) * stride * (fle ? v->M : 1), st));
   const bool reduce = (kind & (RXGS_OUT_RSSI | RXGS_OUT_CSI)) != 0;
   cudaError_t e = cudaSuccess;
   if (reduce) e = dalloc(&partial, static_cast<size_t>(v->M) * g.T * ncols, st);
-  if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * s->C, st);
+  if (e == cudaSuccess && !d->radiance && !fle)
+    e = dalloc(&glob, static_cast<size_t>(N) * 4 * s->C, st);
   if (e != cudaSuccess) {
     dfree(rad, st); dfree(partial, st);
     return fail(ctx, RXGS_E_OOM, "render: %s", cudaGetErrorString(e));
   }
-  rxgs_status rs = make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
+  rxgs_status rs = make_radiance(ctx, s, v, rx, N, d, stride, rad, glob, st);
   if (rs == RXGS_OK) {
     // keep this radiance for a backward on the same views
     dfree(v->rad, st);
@@ -574,6 +589,8 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     v->glob = glob;
     v->key_rx = rx;
     v->key_radiance = d->radiance;
+    v->key_fle = d->fle_coeffs;
+    v->key_lmax = fle ? d->fle_lmax : -1;
     v->key_N = N;
     v->key_stride = stride;
     v->key_gen = s->generation;
@@ -585,6 +602,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     a.vals = v->vals;
     a.ranges = v->ranges;
     a.rad = v->rad;
+    a.rad_view = rad_view;
     a.K = s->K;
     a.M = v->M;
     a.N = N;
@@ -722,14 +740,19 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     return fail(ctx, RXGS_E_INVALID, "no cotangent");
   if (cot->grad_rssi && !cot->fwd_csi)
     return fail(ctx, RXGS_E_INVALID, "grad_rssi needs the forward CSI (fwd_csi)");
-  if (!d->radiance && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
+  if (!d->radiance && !d->fle_coeffs && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->views.find(views);
   if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "unknown views");
   const ViewsState* v = it->second;
   const SceneState* s = ctx->scenes.at(v->scene);
   if (cot->grad_rssi && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
-  if (!d->radiance) {
+  if (d->fle_coeffs) {
+    if (d->radiance) return fail(ctx, RXGS_E_INVALID, "radiance and fle_coeffs exclude each other");
+    if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
+    if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
+  }
+  if (!d->radiance && !d->fle_coeffs) {
     if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
     if (s->bf16) return fail(ctx, RXGS_E_INVALID, "backward through a bf16 MLP is not supported");
     if (s->C > 4 || static_cast<size_t>(N) * 4 * s->C > 8192)
@@ -742,10 +765,14 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   const int C = s->C, K = s->K, M = v->M;
   const int ncols = 2 * N * C;
   const int stride = round_up(ncols, 128);
+  const bool fle = d->fle_coeffs != nullptr;
+  const size_t rad_view = fle ? static_cast<size_t>(K) * stride : 0;
+  const size_t nrad = static_cast<size_t>(K) * stride * (fle ? M : 1);
   float *rad = nullptr, *glob = nullptr, *d_rad = nullptr, *g_uni = nullptr, *d_tau = nullptr;
   float *g_base = nullptr, *g_mlp = nullptr, *mlp_tmp = nullptr, *tfin = nullptr;
   uint32_t *stops = nullptr, *tstop = nullptr;
   const bool cached = v->rad && v->key_rx == rx && v->key_radiance == d->radiance &&
+                      v->key_fle == d->fle_coeffs && v->key_lmax == (fle ? d->fle_lmax : -1) &&
                       v->key_N == N && v->key_stride == stride && v->key_gen == s->generation;
   auto cleanup = [&]() {
     if (cached) {
@@ -763,11 +790,12 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     rad = v->rad;
     glob = v->glob;
   } else {
-    e = dalloc(&rad, static_cast<size_t>(K) * stride, st);
-    if (e == cudaSuccess && !d->radiance) e = dalloc(&glob, static_cast<size_t>(N) * 4 * C, st);
+    e = dalloc(&rad, nrad, st);
+    if (e == cudaSuccess && !d->radiance && !fle)
+      e = dalloc(&glob, static_cast<size_t>(N) * 4 * C, st);
   }
-  if (e == cudaSuccess) e = dalloc(&d_rad, static_cast<size_t>(K) * stride, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_rad, 0, sizeof(float) * K * static_cast<size_t>(stride), st);
+  if (e == cudaSuccess) e = dalloc(&d_rad, nrad, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_rad, 0, sizeof(float) * nrad, st);
   const size_t MHW = static_cast<size_t>(M) * g.H * g.W;
   if (e == cudaSuccess) e = dalloc(&tfin, MHW, st);
   if (e == cudaSuccess) e = dalloc(&stops, MHW, st);
@@ -780,7 +808,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     cleanup();
     return fail(ctx, RXGS_E_OOM, "backward: %s", cudaGetErrorString(e));
   }
-  rxgs_status rs = cached ? RXGS_OK : make_radiance(ctx, s, rx, N, d, stride, rad, glob, st);
+  rxgs_status rs = cached ? RXGS_OK : make_radiance(ctx, s, v, rx, N, d, stride, rad, glob, st);
   if (rs != RXGS_OK) {
     cleanup();
     return rs;
@@ -792,6 +820,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.f.vals = v->vals;
   A.f.ranges = v->ranges;
   A.f.rad = rad;
+  A.f.rad_view = rad_view;
   A.f.K = K;
   A.f.M = M;
   A.f.N = N;
@@ -818,6 +847,11 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   if (d->radiance) {
     Stage sg(ctx, "radiance_grad", st);
     if (gr->grad_radiance) launch_radiance_untranspose_add(d_rad, N, K, C, stride, gr->grad_radiance, st);
+  } else if (fle) {
+    Stage sg(ctx, "fle_bwd", st);
+    if (gr->grad_fle)
+      launch_fle_backward(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
+                          gr->grad_fle, st);
   } else {
     MlpParams m{s->mlp, s->hidden, C, 0};
     g_base = gr->grad_base;

@@ -50,6 +50,8 @@ struct ViewsState {
   float* glob = nullptr;
   const float* key_rx = nullptr;
   const float* key_radiance = nullptr;
+  const float* key_fle = nullptr;
+  int key_lmax = -1;
   int key_N = 0, key_stride = 0;
   uint64_t key_gen = ~0ull;
 };

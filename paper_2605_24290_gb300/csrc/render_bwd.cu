@@ -256,7 +256,9 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
       const int b = e / Q4, q4 = e % Q4;
       const bool ok = b < nbn;
       const uint32_t k = ok ? ks[b] : 0u;
-      cp_async16(&rr[b * NB + 4 * q4], a.rad + static_cast<size_t>(k) * a.stride + col0 + 4 * q4,
+      cp_async16(&rr[b * NB + 4 * q4],
+                 a.rad + static_cast<size_t>(v) * a.rad_view + static_cast<size_t>(k) * a.stride +
+                     col0 + 4 * q4,
                  ok);
     }
   };
@@ -416,7 +418,8 @@ __global__ void __launch_bounds__(2 * kTilePixels, 1) render_bwd_kernel(const Ba
         for (int x = 0; x < S::PE; ++x) {
           const int b = bb + x;
           if (b >= nb) continue;
-          float* dst = A.d_rad + static_cast<size_t>(sK[b]) * a.stride + col0 + cbk;
+          float* dst = A.d_rad + static_cast<size_t>(v) * a.rad_view +
+                       static_cast<size_t>(sK[b]) * a.stride + col0 + cbk;
 #pragma unroll
           for (int c = 0; c < S::PC; ++c)
             if (col0 + cbk + c < a.ncols && acc[x][c] != 0.0f) atomicAdd(&dst[c], acc[x][c]);

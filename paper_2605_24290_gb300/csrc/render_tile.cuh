@@ -63,7 +63,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const TileJob& 
   const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
   const uint2 rg = a.ranges[static_cast<size_t>(v) * g.T + tile];
   const float4* rec = a.rec + static_cast<size_t>(v) * a.K * 2;
-  const float* radv = a.rad + job.col_base;
+  const float* radv = a.rad + job.col_base + static_cast<size_t>(v) * a.rad_view;
   __shared__ unsigned sMask[S::kThreads / 32];  // per warp: chunk entries meeting its strip
 
   const int pg = t % S::PG, cg = t / S::PG;

@@ -104,7 +104,8 @@ struct RenderArgs {
   const float4* rec;       // [M][K][2]
   const uint32_t* vals;    // sorted Gaussian ids
   const uint2* ranges;     // [M][T]
-  const float* rad;        // [K][stride]
+  const float* rad;        // [K][stride], or [M][K][stride] when rad_view != 0
+  size_t rad_view;         // floats between views' radiance (0: shared by all views)
   int K, M, N, C;
   int stride;              // floats per radiance row
   int ncols;               // N*2C valid columns
@@ -123,7 +124,7 @@ struct BackwardArgs {
   RenderArgs f;               // forward arguments (spectra = fwd spectra or null)
   const float* g_spec;        // [M][N][H][W][C][2] or null
   const float* g_uniform;     // [M][ncols] cotangent uniform over pixels, or null
-  float* d_rad;               // [K][stride] dL/ds accumulated (atomics)
+  float* d_rad;               // [K][stride] (per view [M][K][stride] when f.rad_view != 0) dL/ds, atomics
   float* d_tau;               // [K] accumulated
   float* tfin;                // scratch [M][H][W]: final transmittance per pixel
   uint32_t* stops;            // scratch [M][H][W]: stop position per pixel
@@ -140,6 +141,17 @@ void launch_render_bwd(const BackwardArgs& a, cudaStream_t s);
 // pre-pass outputs in A (tfin, stops, tile_stop).
 void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float* gu,
                          float* gamma, float* W, float* grad_radiance, cudaStream_t s);
+
+// ------------------------------------------ FLE directional radiance (App. E.2)
+// rad[v][k][stride] columns 2j, 2j+1 (v < M, rad_view floats per view) from
+// coefficients [N][K][2][(lmax+1)^2] and the transmitters tx[M][3].
+void launch_fle_radiance(const float* coeffs, int N, int K, int lmax, const float4* geom,
+                         const float* tx, int M, int stride, size_t rad_view, float* rad,
+                         cudaStream_t s);
+// grad[N][K][2][L] += sum_v d_rad[v][k][2j..] conj(Y_v,k)
+void launch_fle_backward(const float* d_rad, int N, int K, int lmax, const float4* geom,
+                         const float* tx, int M, int stride, size_t rad_view, float* grad,
+                         cudaStream_t s);
 
 // ------------------------------------------ visibility weights (Eq. render_reorder)
 // W[M][K] = sum over each view's pixels of T_k w_k (zeroed first).

@@ -43,7 +43,8 @@ class SceneDesc(ctypes.Structure):
 
 
 class RenderDesc(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("radiance", ctypes.c_void_p), ("reduce_path", ctypes.c_int)]
+    _fields_ = [("kind", ctypes.c_int), ("radiance", ctypes.c_void_p), ("reduce_path", ctypes.c_int),
+                ("fle_coeffs", ctypes.c_void_p), ("fle_lmax", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):
@@ -64,7 +65,8 @@ class Cotangents(ctypes.Structure):
 
 class Grads(ctypes.Structure):
     _fields_ = [("grad_radiance", ctypes.c_void_p), ("grad_opacity", ctypes.c_void_p),
-                ("grad_base", ctypes.c_void_p), ("grad_mlp", ctypes.c_void_p)]
+                ("grad_base", ctypes.c_void_p), ("grad_mlp", ctypes.c_void_p),
+                ("grad_fle", ctypes.c_void_p)]
 
 
 P = ctypes.c_void_p
@@ -217,15 +219,16 @@ class Context:
         self._check(self.lib.rxgs_release_views(self.h, U64(views), _stream(stream)))
 
     def render_views(self, views, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
-                     ncontrib=None, tfinal=None, reduce_path=0, stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path))
+                     ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0,
+                     stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs), int(fle_lmax))
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render_views(self.h, U64(views), _f32(rx), int(N),
                                                ctypes.byref(d), ctypes.byref(o), _stream(stream)))
 
     def render(self, scene, tx, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
-               ncontrib=None, tfinal=None, reduce_path=0, stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path))
+               ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0, stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs), int(fle_lmax))
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                          _f32(rx), int(N), ctypes.byref(d), ctypes.byref(o),
@@ -234,10 +237,11 @@ class Context:
     def render_backward(self, views, rx, N, kind, radiance=None, grad_spectra=None,
                         grad_csi=None, grad_rssi=None, fwd_csi=None,
                         grad_radiance=None, grad_opacity=None, grad_base=None, grad_mlp=None,
-                        stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), 0)
+                        fle_coeffs=None, fle_lmax=0, grad_fle=None, stream=None):
+        d = RenderDesc(int(kind), _f32(radiance), 0, _f32(fle_coeffs), int(fle_lmax))
         c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_csi))
-        g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp))
+        g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp),
+                  _f32(grad_fle))
         self._check(self.lib.rxgs_render_backward(self.h, U64(views), _f32(rx), int(N),
                                                   ctypes.byref(d), ctypes.byref(c),
                                                   ctypes.byref(g), _stream(stream)))
