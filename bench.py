@@ -396,6 +396,9 @@ def gpu_bench(args):
     cov = None
     if rank == 0 and not args.no_coverage:
         cov = coverage_bench(torch, rxgs, S)
+    fle = None
+    if rank == 0 and not args.no_fle:
+        fle = fle_bench(torch, rxgs, S)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -424,6 +427,7 @@ def gpu_bench(args):
             "serve": serve,
             "batched_csi": bcsi,
             "coverage": cov,
+            "fle": fle,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -597,6 +601,61 @@ def coverage_bench(torch, rxgs, S, reps=3):
                         "RSSI (visibility path) + RSSI backward to radiance and opacity"}
 
 
+def fle_bench(torch, rxgs, S, reps=3, lmax=9):
+    """FLE radiance (App. E.2) at the bench scene's size: 100,000 Gaussians,
+    32 transmitters x 64 receivers, degree 9 (L = 100 components; the
+    coefficient tensor [64, 100k, 2, 100] is 5.1 GB), 90x360 grid: forward
+    spectra, and forward + backward (spectra cotangent) to the coefficients
+    and the opacity.  Views prepared once outside the timing."""
+    w = S.workload_mlp()
+    g, sc = w["grid"], w["scene"]
+    M, N, K = w["tx"].shape[0], w["rx"].shape[0], sc.K
+    L = (lmax + 1) ** 2
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = rxgs.Context(H=g.H, W=g.W)
+    h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), None, None, C=1)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(S.SEED_BASE + 50)
+    coeffs = torch.randn((N, K, 2, L), device="cuda", generator=gen) * 0.1
+    gspec = torch.randn((M, N, g.H, g.W, 1, 2), device="cuda", generator=gen)
+    spec = torch.empty((M, N, g.H, g.W, 1, 2), device="cuda")
+    d_fle = torch.zeros_like(coeffs)
+    d_tau = torch.zeros(K, device="cuda")
+    views = ctx.prepare(h, d(w["tx"]))
+
+    def fwd():
+        ctx.render_views(views, None, N, rxgs.OUT_SPECTRA, spectra=spec, fle_coeffs=coeffs,
+                         fle_lmax=lmax)
+
+    def fwd_bwd():
+        fwd()
+        ctx.render_backward(views, None, N, rxgs.OUT_SPECTRA, grad_spectra=gspec,
+                            grad_opacity=d_tau, fle_coeffs=coeffs, fle_lmax=lmax, grad_fle=d_fle)
+
+    fwd_bwd()
+    ctx.sync()
+    out = {}
+    for name, fn in (("forward", fwd), ("forward_backward", fwd_bwd)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        ctx.sync()
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        out[name] = {"ms": round(a.elapsed_time(b) / reps, 3),
+                     "stages_ms": {k: round(v["ms"] / reps, 3) for k, v in prof["stages"].items()}}
+    ctx.release_views(views)
+    ctx.close()
+    ms = out["forward_backward"]["ms"]
+    return {"spectra_per_s_fwd_bwd": round(M * N / (ms / 1e3), 1), **out,
+            "workload": "100k Gaussians, 32 tx x 64 rx, FLE degree 9 (L = 100), 90x360, "
+                        "spectra; backward to coefficients and opacity"}
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_sample(budget_s=15.0, steps=None, npx=16384):
     """The oracle on a bounded sample of the same workload: one transmitter,
@@ -678,6 +737,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-coverage", action="store_true")
+    ap.add_argument("--no-fle", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":

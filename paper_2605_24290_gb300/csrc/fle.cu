@@ -149,7 +149,10 @@ __global__ void __launch_bounds__(256) fle_backward_kernel(
   const int k = blockIdx.x, t = threadIdx.x;
   const int L = (lmax + 1) * (lmax + 1);
   const float4 p = geom[3 * k];
-  const int jj = t % 16, ll = t / 16;  // receivers jj + 16 q, components ll + 16 r
+  // receivers jj + 16 q, components ll + 16 r: consecutive lanes take
+  // consecutive components of one receiver, so the gradient rows are
+  // updated in contiguous segments
+  const int ll = t % 16, jj = t / 16;
   constexpr int kR = (kFleMaxL + 15) / 16;
   for (int j0 = 0; j0 < N; j0 += kFleRx) {
     const int nr = min(kFleRx, N - j0);
