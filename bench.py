@@ -399,6 +399,9 @@ def gpu_bench(args):
     fle = None
     if rank == 0 and not args.no_fle:
         fle = fle_bench(torch, rxgs, S)
+    train = None
+    if rank == 0 and not args.no_train:
+        train = train_bench(torch, rxgs, S)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -428,6 +431,7 @@ def gpu_bench(args):
             "batched_csi": bcsi,
             "coverage": cov,
             "fle": fle,
+            "train_step": train,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -656,6 +660,39 @@ def fle_bench(torch, rxgs, S, reps=3, lmax=9):
                         "spectra; backward to coefficients and opacity"}
 
 
+def train_bench(torch, rxgs, S, reps=3):
+    """Stage II training step at the bench scene's size (100k Gaussians,
+    32 tx x 64 rx, MLP radiance, 90x360): render, L1 loss on the amplitude
+    spectra, backward to phi_base and the MLP, two Adam updates."""
+    from paper_2605_24290_gb300.train import Stage2Trainer
+    w = S.workload_mlp()
+    g, sc, C = w["grid"], w["scene"], w["C"]
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = rxgs.Context(H=g.H, W=g.W)
+    flat = d(S.flatten_mlp(w["mlp"], C))
+    h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), d(w["base"]),
+                         flat, C=C)
+    tx, rx = d(w["tx"]), d(w["rx"])
+    M, N = tx.shape[0], rx.shape[0]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(S.SEED_BASE + 60)
+    target = torch.rand((M, N, g.H, g.W, C), device="cuda", generator=gen)
+    tr = Stage2Trainer(ctx, h, d(sc.opacity), d(w["base"]), flat)
+    for _ in range(2):
+        tr.step(tx, rx, target)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    losses = [tr.step(tx, rx, target) for _ in range(reps)]
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    ctx.close()
+    return {"ms_per_step": round(ms, 3), "spectra_per_s": round(M * N / (ms / 1e3), 1),
+            "loss_first_last": [round(float(losses[0]), 6), round(float(losses[-1]), 6)],
+            "workload": "100k Gaussians, 32 tx x 64 rx, MLP radiance, L1 on |R| + Adam (phi_base, MLP)"}
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_sample(budget_s=15.0, steps=None, npx=16384):
     """The oracle on a bounded sample of the same workload: one transmitter,
@@ -738,6 +775,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-coverage", action="store_true")
     ap.add_argument("--no-fle", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
