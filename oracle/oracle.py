@@ -294,21 +294,95 @@ def _mlp(x, w1, b1, w2, b2, bf16):
     return h @ w2.T + b2, h
 
 
-def local_features(rx, means):
-    """[v_hat (3), d, T=1, rho_bar=0] per (receiver, Gaussian): v_hat points
-    from the Gaussian to the receiver (Eq. local); occlusion features are
-    held at 'clear' (T = 1, rho_bar = 0)."""
+def local_features(rx, means, occ=None):
+    """[v_hat (3), d, T, rho_bar] per (receiver, Gaussian): v_hat points from
+    the Gaussian to the receiver (Eq. local); T and rho_bar are the occlusion
+    probes of `occ` (occupancy_probes), or 'clear' (T = 1, rho_bar = 0)."""
     r = np.asarray(rx, np.float64)[:, None, :]
     p = np.asarray(means, np.float64)[None, :, :]
     v = r - p
     d = np.sqrt((v ** 2).sum(-1, keepdims=True))
     vh = v / d
-    one = np.ones_like(d)
-    zero = np.zeros_like(d)
-    return np.concatenate([vh, d, one, zero], axis=-1)
+    if occ is None:
+        T = np.ones_like(d)
+        rb = np.zeros_like(d)
+    else:
+        T, rb = occupancy_probes(occ, rx, means)
+        T, rb = T[..., None], rb[..., None]
+    return np.concatenate([vh, d, T, rb], axis=-1)
 
 
-def mlp_radiance(params, rx, means, base, bf16=False):
+# ------------------------- occupancy grid and occlusion probes (App. E.5)
+# Grid: res^3 voxels over the bounding box [lo, hi] of the Gaussian means,
+# voxel size D = (hi - lo) / res per axis (an axis of zero extent gets
+# 1e-3 m), voxel centre lo + (i + 0.5) D.  Splat: Gaussian k adds
+# tau_k exp(-1/2 sum_a ((c_a - p_a) / s_a)^2), s = exp(log-scale) (the
+# rotation is not used), to every voxel centre within 2 s_a of p_a on every
+# axis; densities are summed and clamped to [0, 1] when probed.  Probes:
+# for Gaussian k and receiver j, x_s = p + t_s (r - p) at
+# t_s = float32(0.05 + 0.06 s), s = 0..15; the voxel floor((x - lo) / D)
+# (density 0 outside the grid); T = prod (1 - rho_s), rho_bar = mean rho_s.
+# Every voxel range and index is decided in float32 with the written
+# operation order (p - 2s - lo) / D - 0.5 and (x - lo) / D.
+
+OCC_PROBES = 16
+
+
+def occupancy_grid(scene, res: int = 128):
+    """(grid [res,res,res] float64 densities, lo [3] f32, D [3] f32)."""
+    f = np.float32
+    p = np.asarray(scene.means, f)
+    s = np.exp(np.asarray(scene.log_scales, np.float64)).astype(f)
+    tau = np.asarray(scene.opacity, np.float64)
+    lo = p.min(axis=0).astype(f)
+    hi = p.max(axis=0).astype(f)
+    ext = (hi - lo).astype(f)
+    ext = np.where(ext > f(0), ext, f(1e-3)).astype(f)
+    D = (ext / f(res)).astype(f)
+    two_s = (f(2) * s).astype(f)
+    a_lo = ((p - two_s) - lo) / D - f(0.5)
+    a_hi = ((p + two_s) - lo) / D - f(0.5)
+    i_lo = np.maximum(np.ceil(a_lo).astype(np.int64), 0)
+    i_hi = np.minimum(np.floor(a_hi).astype(np.int64), res - 1)
+    grid = np.zeros((res, res, res), np.float64)
+    for k in range(p.shape[0]):
+        if np.any(i_lo[k] > i_hi[k]):
+            continue
+        axes = []
+        for a in range(3):
+            idx = np.arange(i_lo[k, a], i_hi[k, a] + 1)
+            c = lo[a].astype(np.float64) + (idx + 0.5) * D[a].astype(np.float64)
+            axes.append((idx, ((c - p[k, a]) / s[k, a]) ** 2))
+        q = axes[0][1][:, None, None] + axes[1][1][None, :, None] + axes[2][1][None, None, :]
+        grid[np.ix_(axes[0][0], axes[1][0], axes[2][0])] += tau[k] * np.exp(-0.5 * q)
+    return grid, lo, D
+
+
+def occupancy_probes(occ, rx, means):
+    """(T [N,K], rho_bar [N,K]) of the occlusion probes (float64 values,
+    float32 voxel decisions)."""
+    grid, lo, D = occ
+    f = np.float32
+    res = grid.shape[0]
+    p = np.asarray(means, f)[None, :, :]
+    r = np.asarray(rx, f)[:, None, :]
+    dvec = (r - p).astype(f)
+    T = np.ones(dvec.shape[:2])
+    acc = np.zeros(dvec.shape[:2])
+    for s_ in range(OCC_PROBES):
+        t = f(0.05 + 0.06 * s_)
+        x = (p + (t * dvec).astype(f)).astype(f)
+        u = (x - lo) / D
+        idx = np.floor(u).astype(np.int64)
+        inside = np.all((idx >= 0) & (idx < res), axis=-1)
+        ic = np.clip(idx, 0, res - 1)
+        rho = np.where(inside, np.minimum(grid[ic[..., 0], ic[..., 1], ic[..., 2]], 1.0), 0.0)
+        T *= 1.0 - rho
+        acc += rho
+    return T, acc / OCC_PROBES
+
+
+def mlp_radiance(params, rx, means, base, bf16=False, occ=None):
     """Receiver-conditioned radiance [N,K,C,2] (Eq. film, film_apply, local,
     combined_local): s = (1 + a_l) * ((1 + a_g) * phi_base + b_g) + b_l with
     complex products; each branch is Linear -> ReLU -> Linear with outputs
@@ -318,7 +392,7 @@ def mlp_radiance(params, rx, means, base, bf16=False):
     K, C = base.shape[0], base.shape[1]
     rx = np.asarray(rx, np.float64)
     og, _ = _mlp(rx, P["g_w1"], P["g_b1"], P["g_w2"], P["g_b2"], bf16)        # [N,4C]
-    ol, _ = _mlp(local_features(rx, means), P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], bf16)
+    ol, _ = _mlp(local_features(rx, means, occ), P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], bf16)
     og = og.reshape(-1, 1, C, 4)
     ol = ol.reshape(rx.shape[0], K, C, 4)
     one = np.array([1.0, 0.0])
@@ -326,7 +400,7 @@ def mlp_radiance(params, rx, means, base, bf16=False):
     return _cmul(one + ol[..., 0:2], u) + ol[..., 2:4]
 
 
-def mlp_backward(params, rx, means, base, grad_s):
+def mlp_backward(params, rx, means, base, grad_s, occ=None):
     """Gradients of sum(grad_s * s) w.r.t. phi_base [K,C,2] and every MLP
     parameter (float64, same names as `params`).
 
@@ -338,7 +412,7 @@ def mlp_backward(params, rx, means, base, grad_s):
     N, K, C = g.shape[0], g.shape[1], g.shape[2]
     xg = rx
     og, hg = _mlp(xg, P["g_w1"], P["g_b1"], P["g_w2"], P["g_b2"], False)
-    xl = local_features(rx, means)
+    xl = local_features(rx, means, occ)
     ol, hl = _mlp(xl, P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], False)
     og4 = og.reshape(N, 1, C, 4)
     ol4 = ol.reshape(N, K, C, 4)

@@ -602,3 +602,87 @@ def test_fle_backward_is_the_adjoint(oracle):
     lhs = (g * oracle.fle_radiance(c, means, tx, lmax)).sum()
     rhs = (oracle.fle_backward(g, means, tx, lmax) * c).sum()
     assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+# ---------------------------------------------- occupancy grid and probes
+class _Sc:
+    def __init__(self, means, log_scales, opacity):
+        self.means, self.log_scales, self.opacity = means, log_scales, opacity
+
+
+def test_occupancy_single_gaussian_closed_form(oracle):
+    """One isotropic Gaussian among two far corner anchors of zero opacity:
+    every voxel within 2 sigma holds tau exp(-|c - p|^2 / (2 sigma^2))."""
+    means = np.array([[0, 0, 0], [8, 8, 8], [4.01, 3.97, 4.02]], np.float32)
+    ls = np.log(np.array([[0.1] * 3, [0.1] * 3, [0.5] * 3], np.float32))
+    op = np.array([0.0, 0.0, 0.7], np.float32)
+    grid, lo, D = oracle.occupancy_grid(_Sc(means, ls, op), res=32)
+    idx = np.argwhere(grid > 0)
+    c = lo.astype(np.float64) + (idx + 0.5) * D.astype(np.float64)
+    r2 = ((c - means[2].astype(np.float64)) ** 2).sum(axis=1)
+    np.testing.assert_allclose(grid[tuple(idx.T)], 0.7 * np.exp(-r2 / (2 * 0.5 ** 2)), rtol=1e-6)
+    assert np.all(np.abs(c - means[2]) <= 2 * 0.5 + 1e-6)
+    assert idx.shape[0] > 100
+
+
+def test_occupancy_probes_clear_and_uniform_slab(oracle):
+    """An empty grid gives T = 1, rho_bar = 0 (the clear features); a grid of
+    uniform density rho0 gives T = (1 - rho0)^16 and rho_bar = rho0 for a
+    receiver-Gaussian segment inside it."""
+    rng = np.random.default_rng(3)
+    means = rng.uniform(0, 5, size=(6, 3)).astype(np.float32)
+    rx = rng.uniform(1, 4, size=(2, 3)).astype(np.float32)
+    lo = np.zeros(3, np.float32)
+    D = np.full(3, 5.0 / 16, np.float32)
+    T, rb = oracle.occupancy_probes((np.zeros((16, 16, 16)), lo, D), rx, means)
+    np.testing.assert_array_equal(T, 1.0)
+    np.testing.assert_array_equal(rb, 0.0)
+    T, rb = oracle.occupancy_probes((np.full((16, 16, 16), 0.2), lo, D), rx, means)
+    np.testing.assert_allclose(T, 0.8 ** 16, rtol=1e-12)
+    np.testing.assert_allclose(rb, 0.2, rtol=1e-12)
+    T, rb = oracle.occupancy_probes((np.full((16, 16, 16), 3.0), lo, D), rx, means)
+    np.testing.assert_array_equal(T, 0.0)        # densities clamp to 1
+    np.testing.assert_allclose(rb, 1.0)
+
+
+def test_mlp_with_empty_occupancy_equals_clear_features(oracle):
+    rng = np.random.default_rng(4)
+    from paper_2605_24290_gb300 import synthetic as S
+    sc = S.draw_scene(rng, 20)
+    mlp = S.draw_mlp(rng, 1)
+    base = S.draw_base(rng, 20, 1)
+    rx = S.draw_points(rng, 3)
+    grid, lo, D = oracle.occupancy_grid(sc, res=16)
+    a = oracle.mlp_radiance(mlp, rx, sc.means, base, occ=(np.zeros_like(grid), lo, D))
+    b = oracle.mlp_radiance(mlp, rx, sc.means, base)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_mlp_backward_with_occupancy_matches_finite_differences(oracle):
+    """The occlusion inputs enter dW1 through columns 4 and 5 (T, rho_bar)."""
+    rng = np.random.default_rng(8)
+    from paper_2605_24290_gb300 import synthetic as S
+    K, N = 40, 3
+    sc = S.draw_scene(rng, K, box=(3.0, 3.0, 2.0))
+    sc.log_scales[:] = np.log(0.4)
+    sc.opacity[:] = 0.5
+    mlp = S.draw_mlp(rng, 1)
+    base = S.draw_base(rng, K, 1)
+    rx = S.draw_points(rng, N, box=(3.0, 3.0, 2.0))
+    occ = oracle.occupancy_grid(sc, res=16)
+    T, rb = oracle.occupancy_probes(occ, rx, sc.means)
+    assert T.min() < 0.99 and rb.max() > 0.01          # the probes see occupancy
+    g = rng.normal(size=(N, K, 1, 2))
+    grads = oracle.mlp_backward(mlp, rx, sc.means, base, g, occ=occ)
+    for (u, i) in [(3, 4), (10, 5), (7, 4)]:
+        h = 1e-6
+        P1 = {k: v.copy() for k, v in mlp.items()}
+        P2 = {k: v.copy() for k, v in mlp.items()}
+        P1["l_w1"] = P1["l_w1"].astype(np.float64)
+        P2["l_w1"] = P2["l_w1"].astype(np.float64)
+        P1["l_w1"][u, i] += h
+        P2["l_w1"][u, i] -= h
+        f1 = (g * oracle.mlp_radiance(P1, rx, sc.means, base, occ=occ)).sum()
+        f2 = (g * oracle.mlp_radiance(P2, rx, sc.means, base, occ=occ)).sum()
+        fd = (f1 - f2) / (2 * h)
+        assert abs(fd - grads["l_w1"][u, i]) <= 1e-6 * (1 + abs(fd)), (u, i, fd, grads["l_w1"][u, i])
