@@ -316,9 +316,10 @@ def local_features(rx, means, occ=None):
 # Grid: res^3 voxels over the bounding box [lo, hi] of the Gaussian means,
 # voxel size D = (hi - lo) / res per axis (an axis of zero extent gets
 # 1e-3 m), voxel centre lo + (i + 0.5) D.  Splat: Gaussian k adds
-# tau_k exp(-1/2 sum_a ((c_a - p_a) / s_a)^2), s = exp(log-scale) (the
-# rotation is not used), to every voxel centre within 2 s_a of p_a on every
-# axis; densities are summed and clamped to [0, 1] when probed.  Probes:
+# tau_k exp(-1/2 sum_a ((c_a - p_a) / s_a)^2), s_a = sqrt(Sigma_aa) its
+# standard deviation along axis a (from the float32 covariance of the
+# decision specification), to every voxel centre within 2 s_a of p_a on
+# every axis; densities are summed and clamped to [0, 1] when probed.  Probes:
 # for Gaussian k and receiver j, x_s = p + t_s (r - p) at
 # t_s = float32(0.05 + 0.06 s), s = 0..15; the voxel floor((x - lo) / D)
 # (density 0 outside the grid); T = prod (1 - rho_s), rho_bar = mean rho_s.
@@ -332,7 +333,8 @@ def occupancy_grid(scene, res: int = 128):
     """(grid [res,res,res] float64 densities, lo [3] f32, D [3] f32)."""
     f = np.float32
     p = np.asarray(scene.means, f)
-    s = np.exp(np.asarray(scene.log_scales, np.float64)).astype(f)
+    S32 = cov32(scene.log_scales, scene.quats)                # [K][00 01 02 11 12 22]
+    s = np.sqrt(S32[:, [0, 3, 5]]).astype(f)
     tau = np.asarray(scene.opacity, np.float64)
     lo = p.min(axis=0).astype(f)
     hi = p.max(axis=0).astype(f)

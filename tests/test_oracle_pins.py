@@ -608,6 +608,7 @@ def test_fle_backward_is_the_adjoint(oracle):
 class _Sc:
     def __init__(self, means, log_scales, opacity):
         self.means, self.log_scales, self.opacity = means, log_scales, opacity
+        self.quats = np.tile(np.array([1, 0, 0, 0], np.float32), (means.shape[0], 1))
 
 
 def test_occupancy_single_gaussian_closed_form(oracle):
