@@ -122,6 +122,18 @@ typedef struct {
 
 rxgs_status rxgs_upload_scene(rxgs_ctx* ctx, const rxgs_scene_desc* desc, rxgs_scene_t* out);
 rxgs_status rxgs_release_scene(rxgs_ctx* ctx, rxgs_scene_t scene);
+
+/* Occlusion inputs of the local conditioning branch (App. E.5): splats the
+ * scene's Gaussians as they are now (positions, covariances, opacities)
+ * into a res^3 density grid over the bounding box of the means (Gaussian k
+ * adds tau_k exp(-1/2 sum_a ((c_a - p_a) / s_a)^2), s_a = sqrt(Sigma_aa), to
+ * voxel centres within 2 s_a on every axis; densities clamp to [0, 1]).
+ * Later MLP renders and backwards of the scene (per-pixel reduce path)
+ * feed the local MLP T_k = prod_s (1 - rho_s) and rho_bar_k = mean_s rho_s
+ * over 16 probes x = p + t (r - p), t = 0.05 + 0.06 s, instead of the clear
+ * (1, 0).  res = 0 removes the grid.  1 <= res <= 512.  Batched rendering,
+ * serving and reduce_path 1 refuse a scene with a grid. */
+rxgs_status rxgs_build_occupancy(rxgs_ctx* ctx, rxgs_scene_t scene, int res, void* stream);
 /* Replaces the opacity and/or phi_base / MLP parameters of a scene in place
  * (device pointers, same shapes; NULL = keep).  Geometry stays frozen. */
 rxgs_status rxgs_update_scene(rxgs_ctx* ctx, rxgs_scene_t scene, const float* opacity,

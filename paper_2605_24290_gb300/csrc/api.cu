@@ -214,6 +214,7 @@ rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
   for (auto& kv : ctx->scenes) {
     SceneState* s = kv.second;
     cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
+    cudaFree(s->occ); cudaFree(s->occ_box);
     delete s;
   }
   if (ctx->serve) destroy_serve(ctx->serve);
@@ -307,9 +308,41 @@ rxgs_status rxgs_release_scene(rxgs_ctx* ctx, rxgs_scene_t scene) {
   cudaDeviceSynchronize();
   SceneState* s = it->second;
   cudaFree(s->geom); cudaFree(s->base); cudaFree(s->mlp);
+  cudaFree(s->occ); cudaFree(s->occ_box);
   delete s;
   ctx->scenes.erase(it);
   return RXGS_OK;
+}
+
+rxgs_status rxgs_build_occupancy(rxgs_ctx* ctx, rxgs_scene_t scene, int res, void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  if (res < 0 || res > 512) return fail(ctx, RXGS_E_INVALID, "res must be 0..512");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->scenes.find(scene);
+  if (it == ctx->scenes.end()) return fail(ctx, RXGS_E_INVALID, "unknown scene");
+  SceneState* s = it->second;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->occ) {
+    CK(cudaStreamSynchronize(st));
+    cudaFree(s->occ);
+    cudaFree(s->occ_box);
+    s->occ = nullptr;
+    s->occ_box = nullptr;
+    s->occ_res = 0;
+  }
+  s->generation++;  // cached radiance of earlier renders is stale
+  if (res == 0) return RXGS_OK;
+  const size_t n = static_cast<size_t>(res) * res * res;
+  if (cudaMalloc(&s->occ, sizeof(float) * n) != cudaSuccess ||
+      cudaMalloc(&s->occ_box, sizeof(float) * 6) != cudaSuccess) {
+    cudaFree(s->occ);
+    s->occ = nullptr;
+    return fail(ctx, RXGS_E_OOM, "occupancy grid of %d^3", res);
+  }
+  s->occ_res = res;
+  launch_occ_build(s->geom, s->K, res, s->occ_box, s->occ, st);
+  return check_last(ctx, "build_occupancy");
 }
 
 rxgs_status rxgs_update_scene(rxgs_ctx* ctx, rxgs_scene_t scene, const float* opacity,
@@ -481,7 +514,15 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
   } else {
     if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
     MlpParams m{s->mlp, s->hidden, s->C, s->bf16};
+    float2* feat = nullptr;
+    if (s->occ) {
+      if (dalloc(&feat, static_cast<size_t>(N) * s->K, st) != cudaSuccess)
+        return fail(ctx, RXGS_E_OOM, "occlusion inputs");
+      launch_occ_probes(s->geom, s->K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
+      m.feat = feat;
+    }
     launch_mlp_radiance(m, rx, N, s->geom, s->base, s->K, stride, rad, glob, st);
+    dfree(feat, st);
   }
   return check_last(ctx, "radiance");
 }
@@ -524,6 +565,8 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     if (!d->radiance && !s->mlp)
       return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
     if (!d->radiance && s->C > 52) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 supports C <= 52");
+    if (!d->radiance && s->occ)
+      return fail(ctx, RXGS_E_INVALID, "reduce_path 1 does not take occlusion inputs (occupancy grid)");
     float *W = nullptr, *tmp = nullptr, *glob = nullptr, *csi_t = nullptr;
     const size_t ntmp = d->radiance ? weighted_sum_tmp_floats(v->M, s->K, N, s->C)
                                     : mlp_weighted_tmp_floats(v->M, s->K, N, s->C);
@@ -857,9 +900,17 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     g_base = gr->grad_base;
     g_mlp = gr->grad_mlp;
     e = cudaSuccess;
+    float2* feat = nullptr;
     if (!g_base) e = dalloc(&g_base, 2ull * K * C, st);
     if (e == cudaSuccess && !g_mlp) e = dalloc(&g_mlp, s->mlp_floats, st);
     if (e == cudaSuccess) e = dalloc(&mlp_tmp, mlp_backward_tmp_floats(m, N, K), st);
+    if (e == cudaSuccess && s->occ) {
+      e = dalloc(&feat, static_cast<size_t>(N) * K, st);
+      if (e == cudaSuccess) {
+        launch_occ_probes(s->geom, K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
+        m.feat = feat;
+      }
+    }
     if (e != cudaSuccess) {
       cleanup();
       return fail(ctx, RXGS_E_OOM, "backward (MLP): %s", cudaGetErrorString(e));
@@ -867,6 +918,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     Stage sg(ctx, "mlp_bwd", st);
     launch_mlp_backward(m, rx, N, s->geom, s->base, K, stride, d_rad, glob, g_base, g_mlp,
                         mlp_tmp, st);
+    dfree(feat, st);
   }
   rs = check_last(ctx, "backward");
   cleanup();

@@ -491,6 +491,8 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
     s = it->second;
   }
   if ((kind & RXGS_OUT_RSSI) && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
+  if (!d->radiance && s->occ)
+    return fail(ctx, RXGS_E_INVALID, "batched rendering does not take occlusion inputs (occupancy grid)");
   if (!d->radiance && !s->mlp)
     return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
   CK(cudaSetDevice(ctx->device));

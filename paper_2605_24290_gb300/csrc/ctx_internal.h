@@ -28,6 +28,10 @@ struct SceneState {
   float* mlp = nullptr;     // flat
   size_t mlp_floats = 0;
   int hidden = 0, bf16 = 0;
+  // occupancy grid of the local branch's occlusion inputs (null: clear)
+  float* occ = nullptr;      // [res^3]
+  float* occ_box = nullptr;  // lo[3], D[3]
+  int occ_res = 0;
 };
 
 struct ViewsState {

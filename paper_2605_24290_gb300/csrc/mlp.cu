@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
                                                         const float* __restrict__ glob,
                                                         float* __restrict__ out,
                                                         const int* __restrict__ n_dev,
-                                                        const int* __restrict__ col_of) {
+                                                        const int* __restrict__ col_of,
+                                                        const float2* __restrict__ feat) {
   extern __shared__ float sw[];  // l_w1 [64*6], l_b1 [64], l_w2 [4C*64], l_b2 [4C]
   const MlpOffsets o = mlp_offsets(kHidden, C);
   const int nw = kHidden * 6 + kHidden + 4 * C * kHidden + 4 * C;
@@ -99,8 +100,10 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
   const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
   const float d = sqrtf(vx * vx + vy * vy + vz * vz);
   const float inv = 1.0f / d;
+  float2 oc = make_float2(1.0f, 0.0f);  // occlusion inputs (T, rho_bar)
+  if (feat) oc = feat[static_cast<size_t>(j) * K + k];
   const float x[6] = {rb(vx * inv, bf16), rb(vy * inv, bf16), rb(vz * inv, bf16), rb(d, bf16),
-                      1.0f, 0.0f};
+                      rb(oc.x, bf16), rb(oc.y, bf16)};
   float h[kHidden];
 #pragma unroll
   for (int u = 0; u < kHidden; ++u) {
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     const float* __restrict__ P, int bf16, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
     const float* __restrict__ glob, float* __restrict__ out, const int* __restrict__ n_dev,
-    const int* __restrict__ col_of) {
+    const int* __restrict__ col_of, const float2* __restrict__ feat) {
   constexpr int n4 = 4 * CC;
   __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
   const MlpOffsets o = mlp_offsets(kHidden, CC);
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
   __syncthreads();
   const size_t npairs = static_cast<size_t>(N) * K;
   const int nlim = n_dev ? *n_dev : N;
-  float x[PP][4];
+  float x[PP][4], xo[PP][2];  // direction, distance; occlusion (T, rho_bar)
   bool ok[PP];
   int jv[PP], kv[PP];
 #pragma unroll
@@ -168,6 +171,13 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     jv[r] = j;
     kv[r] = k;
     x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0.0f;
+    xo[r][0] = 1.0f;
+    xo[r][1] = 0.0f;
+    if (ok[r] && feat) {
+      const float2 f = feat[static_cast<size_t>(j) * K + k];
+      xo[r][0] = rb(f.x, bf16);
+      xo[r][1] = rb(f.y, bf16);
+    }
     if (ok[r]) {
       const float4 p = geom[3 * k];
       const float vx = rx[3 * j + 0] - p.x, vy = rx[3 * j + 1] - p.y, vz = rx[3 * j + 2] - p.z;
@@ -199,7 +209,12 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
       float a = b1;
 #pragma unroll
       for (int i = 0; i < 4; ++i) a = fmaf(w1[i], x[r][i], a);
-      a = a + w1[4];
+      if (feat) {
+        a = fmaf(w1[4], xo[r][0], a);
+        a = fmaf(w1[5], xo[r][1], a);
+      } else {
+        a = a + w1[4];
+      }
       const float hu = rb(fmaxf(a, 0.0f), bf16);
 #pragma unroll
       for (int q = 0; q < n4; ++q) ol[r][q] = fmaf(w2[q], hu, ol[r][q]);
@@ -248,7 +263,8 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
   case CCV: {                                                                                 \
     const unsigned nblk = static_cast<unsigned>((pairs + 256 * PPV - 1) / (256 * PPV));       \
     mlp_local_narrow_kernel<CCV, PPV><<<nblk, 256, 0, s>>>(m.p, m.bf16, rx, N, geom, base, K,  \
-                                                            stride, glob, out, n_dev, col_of); \
+                                                            stride, glob, out, n_dev, col_of,  \
+                                                            m.feat);                           \
     note_launches(1);                                                                         \
     return;                                                                                   \
   }
@@ -265,7 +281,7 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
     cudaFuncSetAttribute(mlp_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
   mlp_local_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, smem, s>>>(
-      m.p, m.C, m.bf16, rx, N, geom, base, K, stride, glob, out, n_dev, col_of);
+      m.p, m.C, m.bf16, rx, N, geom, base, K, stride, glob, out, n_dev, col_of, m.feat);
   note_launches(1);
 }
 
@@ -321,12 +337,13 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const float* __restrict__ P, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
     const float* __restrict__ dS, const float* __restrict__ glob, float* __restrict__ grad_base,
-    float* __restrict__ part) {
+    float* __restrict__ part, const float2* __restrict__ feat) {
   constexpr int n4 = 4 * CC;
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   constexpr int kWarps = kBwdThreads / 32;
   __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
   __shared__ float4 sX[kBwdThreads];            // features of each thread's pair
+  __shared__ float2 sO[kBwdThreads];            // its occlusion inputs (T, rho_bar)
   __shared__ float4 sD[kBwdThreads * CC];       // dol of each thread's pair
   extern __shared__ float sdyn[];  // [kWarps][nloc] warp partials, then [256][4C]
   const MlpOffsets o = mlp_offsets(kHidden, CC);
@@ -338,22 +355,22 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   __syncthreads();
 
   // phase-2 operands of this lane's hidden units u = lane, lane + 32
-  float w1u[2][5], w2u[2][n4];
+  float w1u[2][6], w2u[2][n4];
 #pragma unroll
   for (int hf = 0; hf < 2; ++hf) {
     const int u = hf * 32 + lane;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) w1u[hf][i] = W1[u * 6 + i];
+    for (int i = 0; i < 6; ++i) w1u[hf][i] = W1[u * 6 + i];
 #pragma unroll
     for (int q = 0; q < n4; ++q) w2u[hf][q] = W2[q * kHidden + u];
   }
   float b1u[2] = {B1[lane], B1[32 + lane]};
 
-  float aw2[n4][2], aw1[4][2], ab1[2], ab2[n4], aog[n4];
+  float aw2[n4][2], aw1[6][2], ab1[2], ab2[n4], aog[n4];
 #pragma unroll
   for (int q = 0; q < n4; ++q) aw2[q][0] = aw2[q][1] = ab2[q] = aog[q] = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) aw1[i][0] = aw1[i][1] = 0.0f;
+  for (int i = 0; i < 6; ++i) aw1[i][0] = aw1[i][1] = 0.0f;
   ab1[0] = ab1[1] = 0.0f;
 
   const size_t pairs = static_cast<size_t>(N) * K;
@@ -371,6 +388,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const bool ok = pair < pairs;
     const int k = ok ? static_cast<int>(pair / N) : 0;
     float x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float2 oc = make_float2(1.0f, 0.0f);  // occlusion inputs (T, rho_bar)
     float dol[n4], db[2 * CC];
 #pragma unroll
     for (int q = 0; q < n4; ++q) dol[q] = 0.0f;
@@ -385,6 +403,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
       x[1] = vy * inv;
       x[2] = vz * inv;
       x[3] = d;
+      if (feat) oc = feat[static_cast<size_t>(j) * K + k];
       // hidden units streamed into the outputs (same summation order as
       // the forward: bias first, then units in ascending order)
       float oall[n4];
@@ -392,9 +411,18 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
       for (int q = 0; q < n4; ++q) oall[q] = B2[q];
 #pragma unroll 8
       for (int u = 0; u < kHidden; ++u) {
-        float a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
+        float a;
+        if (feat) {  // the forward's order: inputs 0..5
+          a = B1[u];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
+          for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
+          a = fmaf(W1[u * 6 + 4], oc.x, a);
+          a = fmaf(W1[u * 6 + 5], oc.y, a);
+        } else {
+          a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
+        }
         const float hu = fmaxf(a, 0.0f);
 #pragma unroll
         for (int q = 0; q < n4; ++q) oall[q] = fmaf(W2[q * kHidden + u], hu, oall[q]);
@@ -446,6 +474,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int q = 0; q < n4; ++q) ab2[q] += dol[q];
     // ---- phase 2: the warp's 32 pairs, lane = hidden units lane, lane + 32
     sX[t] = make_float4(x[0], x[1], x[2], x[3]);
+    sO[t] = oc;
 #pragma unroll
     for (int c = 0; c < CC; ++c)
       sD[t * CC + c] = make_float4(dol[4 * c], dol[4 * c + 1], dol[4 * c + 2], dol[4 * c + 3]);
@@ -454,6 +483,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int pp = 0; pp < 32; ++pp) {
       const int p = warp * 32 + pp;
       const float4 xp = sX[p];
+      const float2 op = sO[p];
       float dv[n4];
 #pragma unroll
       for (int c = 0; c < CC; ++c) {
@@ -465,11 +495,22 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
       }
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
-        float a = b1u[hf] + w1u[hf][4];
-        a = fmaf(w1u[hf][0], xp.x, a);
-        a = fmaf(w1u[hf][1], xp.y, a);
-        a = fmaf(w1u[hf][2], xp.z, a);
-        a = fmaf(w1u[hf][3], xp.w, a);
+        float a;
+        if (feat) {
+          a = b1u[hf];
+          a = fmaf(w1u[hf][0], xp.x, a);
+          a = fmaf(w1u[hf][1], xp.y, a);
+          a = fmaf(w1u[hf][2], xp.z, a);
+          a = fmaf(w1u[hf][3], xp.w, a);
+          a = fmaf(w1u[hf][4], op.x, a);
+          a = fmaf(w1u[hf][5], op.y, a);
+        } else {
+          a = b1u[hf] + w1u[hf][4];
+          a = fmaf(w1u[hf][0], xp.x, a);
+          a = fmaf(w1u[hf][1], xp.y, a);
+          a = fmaf(w1u[hf][2], xp.z, a);
+          a = fmaf(w1u[hf][3], xp.w, a);
+        }
         const float hv = fmaxf(a, 0.0f);
         float g = 0.0f;
 #pragma unroll
@@ -480,6 +521,8 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
         aw1[1][hf] = fmaf(dh, xp.y, aw1[1][hf]);
         aw1[2][hf] = fmaf(dh, xp.z, aw1[2][hf]);
         aw1[3][hf] = fmaf(dh, xp.w, aw1[3][hf]);
+        aw1[4][hf] = fmaf(dh, op.x, aw1[4][hf]);
+        aw1[5][hf] = fmaf(dh, op.y, aw1[5][hf]);
 #pragma unroll
         for (int q = 0; q < n4; ++q) aw2[q][hf] = fmaf(dv[q], hv, aw2[q][hf]);
       }
@@ -494,8 +537,10 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const int u = hf * 32 + lane;
 #pragma unroll
     for (int i = 0; i < 4; ++i) wp[u * 6 + i] = aw1[i][hf];
-    wp[u * 6 + 4] = ab1[hf];  // input 4 is constant 1: same gradient as the bias
-    wp[u * 6 + 5] = 0.0f;     // input 5 is constant 0
+    // inputs 4 and 5: the occlusion features, or the constants 1 and 0
+    // (the gradient of input 4 then equals the bias gradient)
+    wp[u * 6 + 4] = feat ? aw1[4][hf] : ab1[hf];
+    wp[u * 6 + 5] = feat ? aw1[5][hf] : 0.0f;
     wp[kHidden * 6 + u] = ab1[hf];
 #pragma unroll
     for (int q = 0; q < n4; ++q) wp[kHidden * 7 + q * kHidden + u] = aw2[q][hf];
@@ -592,7 +637,7 @@ static void launch_mlp_local_bwd(int blocks, const MlpParams& m, const float* rx
   cudaFuncSetAttribute(mlp_local_bwd_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(smem));
   mlp_local_bwd_kernel<CC><<<blocks, kBwdThreads, smem, s>>>(m.p, rx, N, geom, base, K, stride, dS,
-                                                             glob, grad_base, part);
+                                                             glob, grad_base, part, m.feat);
   note_launches(1);
 }
 

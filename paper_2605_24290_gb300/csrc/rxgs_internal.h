@@ -83,6 +83,9 @@ void launch_radiance_untranspose_add(const float* in, int N, int K, int C, int s
 struct MlpParams {
   const float* p;  // flat parameters (fp32)
   int hidden, C, bf16;
+  // occlusion inputs (T, rho_bar) of the local branch per (receiver,
+  // Gaussian) pair [N][K], or null: clear (1, 0)
+  const float2* feat = nullptr;
 };
 // Radiance from the conditioning MLP: out[K][stride] Gaussian-major.
 // Optional: n_dev = receivers in use (<= N), col_of[j] = first column of
@@ -141,6 +144,13 @@ void launch_render_bwd(const BackwardArgs& a, cudaStream_t s);
 // pre-pass outputs in A (tfin, stops, tile_stop).
 void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float* gu,
                          float* gamma, float* W, float* grad_radiance, cudaStream_t s);
+
+// ------------------------------------------ occupancy grid and probes (App. E.5)
+// box[6] = (lo, D) and grid[res^3] from the scene's Gaussians.
+void launch_occ_build(const float4* geom, int K, int res, float* box, float* grid, cudaStream_t s);
+// feat[N][K] = (T, rho_bar) along each (Gaussian, receiver) segment.
+void launch_occ_probes(const float4* geom, int K, const float* rx, int N, int res,
+                       const float* box, const float* grid, float2* feat, cudaStream_t s);
 
 // ------------------------------------------ FLE directional radiance (App. E.2)
 // rad[v][k][stride] columns 2j, 2j+1 (v < M, rad_view floats per view) from

@@ -279,6 +279,7 @@ rxgs_status rxgs_serve_start(rxgs_ctx* ctx, rxgs_scene_t scene, const rxgs_serve
     s = it->second;
   }
   if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "serving needs a scene with a conditioning MLP");
+  if (s->occ) return fail(ctx, RXGS_E_INVALID, "serving does not take occlusion inputs (occupancy grid)");
   if (o.kind == RXGS_OUT_RSSI && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
   CK(cudaSetDevice(ctx->device));
   ServeState* S = new ServeState();

@@ -81,6 +81,7 @@ SIGNATURES = {
     "rxgs_upload_scene": (I, [P, P, P]),
     "rxgs_release_scene": (I, [P, U64]),
     "rxgs_update_scene": (I, [P, U64, P, P, P, P]),
+    "rxgs_build_occupancy": (I, [P, U64, I, P]),
     "rxgs_prepare": (I, [P, U64, P, I, P, P]),
     "rxgs_release_views": (I, [P, U64, P]),
     "rxgs_render_views": (I, [P, U64, P, I, P, P, P]),
@@ -207,6 +208,11 @@ class Context:
     def update_scene(self, scene, opacity=None, base=None, mlp=None, stream=None):
         self._check(self.lib.rxgs_update_scene(self.h, U64(scene), _f32(opacity), _f32(base),
                                                _f32(mlp), _stream(stream)))
+
+    def build_occupancy(self, scene, res=128, stream=None):
+        """Occupancy grid for the local branch's occlusion inputs (res = 0
+        removes it)."""
+        self._check(self.lib.rxgs_build_occupancy(self.h, U64(scene), int(res), _stream(stream)))
 
     # --------------------------------------------------------------- views
     def prepare(self, scene, tx, stream=None):
