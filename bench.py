@@ -402,6 +402,9 @@ def gpu_bench(args):
     train = None
     if rank == 0 and not args.no_train:
         train = train_bench(torch, rxgs, S)
+    occ = None
+    if rank == 0 and not args.no_occupancy:
+        occ = occupancy_bench(torch, rxgs, S, W)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -432,6 +435,7 @@ def gpu_bench(args):
             "coverage": cov,
             "fle": fle,
             "train_step": train,
+            "occupancy": occ,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -693,6 +697,30 @@ def train_bench(torch, rxgs, S, reps=3):
             "workload": "100k Gaussians, 32 tx x 64 rx, MLP radiance, L1 on |R| + Adam (phi_base, MLP)"}
 
 
+def occupancy_bench(torch, rxgs, S, W, reps=3):
+    """Occlusion inputs (App. E.5) on the bench scene: building the 128^3
+    grid once, and the bench step (prepare + MLP + forward + backward) with
+    the 16 probes per (receiver, Gaussian) pair feeding the local MLP."""
+    c = W.ctx
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    c.build_occupancy(W.scene, 128)
+    b.record()
+    torch.cuda.synchronize()
+    build_ms = a.elapsed_time(b)
+    W.step()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        W.step()
+    b.record()
+    torch.cuda.synchronize()
+    step_ms = a.elapsed_time(b) / reps
+    c.build_occupancy(W.scene, 0)
+    return {"grid": 128, "build_ms": round(build_ms, 3), "step_ms": round(step_ms, 3),
+            "workload": "bench step with occlusion probes (16 per pair) in the local MLP"}
+
+
 # ------------------------------------------------------------ CPU oracle
 def cpu_sample(budget_s=15.0, steps=None, npx=16384):
     """The oracle on a bounded sample of the same workload: one transmitter,
@@ -776,6 +804,7 @@ def main():
     ap.add_argument("--no-coverage", action="store_true")
     ap.add_argument("--no-fle", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-occupancy", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":

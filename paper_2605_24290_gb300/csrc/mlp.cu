@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) mlp_local_kernel(const float* __restrict_
 // ascending order, as above), so no 64-entry hidden vector is kept.  Each
 // thread evaluates PP pairs (block-strided, so every slice of a block stays
 // coalesced) and reuses each weight it reads from shared memory PP times.
-template <int CC, int PP>
+template <int CC, int PP, bool OCC>
 __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     const float* __restrict__ P, int bf16, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     x[r][0] = x[r][1] = x[r][2] = x[r][3] = 0.0f;
     xo[r][0] = 1.0f;
     xo[r][1] = 0.0f;
-    if (ok[r] && feat) {
+    if (OCC && ok[r]) {
       const float2 f = feat[static_cast<size_t>(j) * K + k];
       xo[r][0] = rb(f.x, bf16);
       xo[r][1] = rb(f.y, bf16);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
       float a = b1;
 #pragma unroll
       for (int i = 0; i < 4; ++i) a = fmaf(w1[i], x[r][i], a);
-      if (feat) {
+      if (OCC) {
         a = fmaf(w1[4], xo[r][0], a);
         a = fmaf(w1[5], xo[r][1], a);
       } else {
@@ -262,9 +262,12 @@ void launch_mlp_radiance(const MlpParams& m, const float* rx, int N, const float
 #define RXGS_NARROW(CCV, PPV)                                                                  \
   case CCV: {                                                                                 \
     const unsigned nblk = static_cast<unsigned>((pairs + 256 * PPV - 1) / (256 * PPV));       \
-    mlp_local_narrow_kernel<CCV, PPV><<<nblk, 256, 0, s>>>(m.p, m.bf16, rx, N, geom, base, K,  \
-                                                            stride, glob, out, n_dev, col_of,  \
-                                                            m.feat);                           \
+    if (m.feat)                                                                               \
+      mlp_local_narrow_kernel<CCV, PPV, true><<<nblk, 256, 0, s>>>(                           \
+          m.p, m.bf16, rx, N, geom, base, K, stride, glob, out, n_dev, col_of, m.feat);       \
+    else                                                                                      \
+      mlp_local_narrow_kernel<CCV, PPV, false><<<nblk, 256, 0, s>>>(                          \
+          m.p, m.bf16, rx, N, geom, base, K, stride, glob, out, n_dev, col_of, nullptr);      \
     note_launches(1);                                                                         \
     return;                                                                                   \
   }
@@ -332,7 +335,7 @@ size_t mlp_backward_tmp_floats(const MlpParams& m, int N, int /*K*/) {
          static_cast<size_t>(N) * 4 * m.C;
 }
 
-template <int CC>
+template <int CC, bool OCC>
 __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const float* __restrict__ P, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
@@ -366,11 +369,12 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   }
   float b1u[2] = {B1[lane], B1[32 + lane]};
 
-  float aw2[n4][2], aw1[6][2], ab1[2], ab2[n4], aog[n4];
+  constexpr int NI = OCC ? 6 : 4;  // inputs with a weight gradient of their own
+  float aw2[n4][2], aw1[NI][2], ab1[2], ab2[n4], aog[n4];
 #pragma unroll
   for (int q = 0; q < n4; ++q) aw2[q][0] = aw2[q][1] = ab2[q] = aog[q] = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) aw1[i][0] = aw1[i][1] = 0.0f;
+  for (int i = 0; i < NI; ++i) aw1[i][0] = aw1[i][1] = 0.0f;
   ab1[0] = ab1[1] = 0.0f;
 
   const size_t pairs = static_cast<size_t>(N) * K;
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
       x[1] = vy * inv;
       x[2] = vz * inv;
       x[3] = d;
-      if (feat) oc = feat[static_cast<size_t>(j) * K + k];
+      if (OCC) oc = feat[static_cast<size_t>(j) * K + k];
       // hidden units streamed into the outputs (same summation order as
       // the forward: bias first, then units in ascending order)
       float oall[n4];
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
 #pragma unroll 8
       for (int u = 0; u < kHidden; ++u) {
         float a;
-        if (feat) {  // the forward's order: inputs 0..5
+        if (OCC) {  // the forward's order: inputs 0..5
           a = B1[u];
 #pragma unroll
           for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int q = 0; q < n4; ++q) ab2[q] += dol[q];
     // ---- phase 2: the warp's 32 pairs, lane = hidden units lane, lane + 32
     sX[t] = make_float4(x[0], x[1], x[2], x[3]);
-    sO[t] = oc;
+    if (OCC) sO[t] = oc;
 #pragma unroll
     for (int c = 0; c < CC; ++c)
       sD[t * CC + c] = make_float4(dol[4 * c], dol[4 * c + 1], dol[4 * c + 2], dol[4 * c + 3]);
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int pp = 0; pp < 32; ++pp) {
       const int p = warp * 32 + pp;
       const float4 xp = sX[p];
-      const float2 op = sO[p];
+      const float2 op = OCC ? sO[p] : make_float2(1.0f, 0.0f);
       float dv[n4];
 #pragma unroll
       for (int c = 0; c < CC; ++c) {
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
         float a;
-        if (feat) {
+        if (OCC) {
           a = b1u[hf];
           a = fmaf(w1u[hf][0], xp.x, a);
           a = fmaf(w1u[hf][1], xp.y, a);
@@ -521,8 +525,10 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
         aw1[1][hf] = fmaf(dh, xp.y, aw1[1][hf]);
         aw1[2][hf] = fmaf(dh, xp.z, aw1[2][hf]);
         aw1[3][hf] = fmaf(dh, xp.w, aw1[3][hf]);
-        aw1[4][hf] = fmaf(dh, op.x, aw1[4][hf]);
-        aw1[5][hf] = fmaf(dh, op.y, aw1[5][hf]);
+        if (OCC) {
+          aw1[NI - 2][hf] = fmaf(dh, op.x, aw1[NI - 2][hf]);
+          aw1[NI - 1][hf] = fmaf(dh, op.y, aw1[NI - 1][hf]);
+        }
 #pragma unroll
         for (int q = 0; q < n4; ++q) aw2[q][hf] = fmaf(dv[q], hv, aw2[q][hf]);
       }
@@ -539,8 +545,8 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int i = 0; i < 4; ++i) wp[u * 6 + i] = aw1[i][hf];
     // inputs 4 and 5: the occlusion features, or the constants 1 and 0
     // (the gradient of input 4 then equals the bias gradient)
-    wp[u * 6 + 4] = feat ? aw1[4][hf] : ab1[hf];
-    wp[u * 6 + 5] = feat ? aw1[5][hf] : 0.0f;
+    wp[u * 6 + 4] = OCC ? aw1[NI - 2][hf] : ab1[hf];
+    wp[u * 6 + 5] = OCC ? aw1[NI - 1][hf] : 0.0f;
     wp[kHidden * 6 + u] = ab1[hf];
 #pragma unroll
     for (int q = 0; q < n4; ++q) wp[kHidden * 7 + q * kHidden + u] = aw2[q][hf];
@@ -634,10 +640,17 @@ static void launch_mlp_local_bwd(int blocks, const MlpParams& m, const float* rx
   constexpr int n4 = 4 * CC;
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   const size_t smem = sizeof(float) * ((kBwdThreads / 32) * nloc + kBwdThreads * n4);
-  cudaFuncSetAttribute(mlp_local_bwd_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
-  mlp_local_bwd_kernel<CC><<<blocks, kBwdThreads, smem, s>>>(m.p, rx, N, geom, base, K, stride, dS,
-                                                             glob, grad_base, part, m.feat);
+  if (m.feat) {
+    cudaFuncSetAttribute(mlp_local_bwd_kernel<CC, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    mlp_local_bwd_kernel<CC, true><<<blocks, kBwdThreads, smem, s>>>(
+        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, m.feat);
+  } else {
+    cudaFuncSetAttribute(mlp_local_bwd_kernel<CC, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    mlp_local_bwd_kernel<CC, false><<<blocks, kBwdThreads, smem, s>>>(
+        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, nullptr);
+  }
   note_launches(1);
 }
 
