@@ -100,3 +100,45 @@ def test_fle_arguments_are_checked(torch, rx):
     ctx.render_views(views, None, 3, rx.OUT_RSSI, rssi=rssi, fle_coeffs=cd, fle_lmax=2)
     ctx.sync()
     assert bool(torch.isfinite(rssi).all())
+
+
+def test_fle_view_and_receiver_groups(torch, rx, oracle):
+    """33 transmitters and 65 receivers: the FLE kernels' second group of
+    views (32 per pass) and of receivers (64 per pass)."""
+    rng = np.random.default_rng(720)
+    K, M, N, lmax = 300, 33, 65, 3
+    sc = S.draw_scene(rng, K)
+    tx = S.draw_points(rng, M)
+    coeffs = draw_coeffs(rng, N, K, lmax)
+    g = S.Grid()
+    ctx = rx.Context(H=g.H, W=g.W)
+    h = upload(ctx, sc, torch)
+    views = ctx.prepare(h, dev(tx, torch))
+    cd = dev(coeffs, torch)
+    csi = torch.zeros((M, N, 1, 2), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_CSI, csi=csi, fle_coeffs=cd, fle_lmax=lmax)
+    gc = rng.normal(size=(M, N, 1, 2)).astype(np.float32)
+    d_fle = torch.zeros_like(cd)
+    ctx.render_backward(views, None, N, rx.OUT_CSI, grad_csi=dev(gc, torch), fle_coeffs=cd,
+                        fle_lmax=lmax, grad_fle=d_fle)
+    ctx.sync()
+    ref_c = np.zeros(coeffs.shape)
+    scale_c = np.zeros(coeffs.shape)
+    for v in [0, 31, 32]:
+        rad = oracle.fle_radiance(coeffs, sc.means, tx[v], lmax)
+        o = oracle.render_view(g, sc, tx[v], rad)
+        a = o["absacc"].sum(axis=(1, 2))
+        e = np.abs(csi[v].cpu().numpy() - oracle.csi(o["spectra"])) / (a[..., None] + 1e-30)
+        assert float(e.max()) <= TOL, v
+    # the coefficient gradient over all views (uniform cotangent per view)
+    for v in range(M):
+        rad = oracle.fle_radiance(coeffs, sc.means, tx[v], lmax)
+        gspec = np.broadcast_to(gc[v].astype(np.float64)[:, None, None, :, :],
+                                (N, g.H, g.W, 1, 2))
+        gr, _, ar, _ = oracle.backward_view(g, sc, tx[v], rad, gspec, want_abs=True)
+        ref_c += oracle.fle_backward(gr, sc.means, tx[v], lmax)
+        Ya = np.abs(oracle.fle_basis(sc.means, tx[v], lmax))
+        scale_c += (ar[:, :, 0, 0] + ar[:, :, 0, 1])[:, :, None, None] * Ya[None, :, None, :]
+    e_c = float((np.abs(d_fle.cpu().numpy() - ref_c) / (scale_c + 1e-30)).max())
+    assert e_c <= TOL, e_c
+    ctx.release_views(views)

@@ -119,3 +119,43 @@ def test_mlp_bf16_visibility_pixel_and_batched(torch, rx, oracle, C):
     ref = np.concatenate([csi_v[0, :4].cpu().numpy(), csi_v[1, 4:].cpu().numpy()])
     a = np.concatenate([scales[0][:4], scales[1][4:]])
     assert norm_err(bc.cpu().numpy(), ref, a) <= TOL
+
+
+def test_visibility_many_views_and_backward(torch, rx, oracle):
+    """18 transmitters (two passes of 16 views in the weighted sum, the gamma
+    and the outer-product kernels), C = 2, an odd Gaussian count."""
+    rng = np.random.default_rng(660)
+    K, M, N, C = 1501, 18, 5, 2
+    sc = S.draw_scene(rng, K)
+    g = S.Grid()
+    ctx = rx.Context(H=g.H, W=g.W)
+    h = upload(ctx, sc, torch, C=C)
+    tx = S.draw_points(rng, M)
+    rad = S.draw_radiance(rng, N, K, C)
+    views = ctx.prepare(h, dev(tx, torch))
+    radd = dev(rad, torch)
+    csi = torch.zeros((M, N, C, 2), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_CSI, radiance=radd, csi=csi, reduce_path=1)
+    gc = rng.normal(size=(M, N, C, 2)).astype(np.float32)
+    d_rad = torch.zeros_like(radd)
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, None, N, rx.OUT_CSI, radiance=radd, grad_csi=dev(gc, torch),
+                        grad_radiance=d_rad, grad_opacity=d_tau)
+    ctx.sync()
+    ref_r = np.zeros(rad.shape)
+    abs_r = np.zeros(rad.shape)
+    ref_t = np.zeros(K)
+    abs_t = np.zeros(K)
+    for v in range(M):
+        o = oracle.render_view(g, sc, tx[v], rad.astype(np.float64))
+        a = o["absacc"].sum(axis=(1, 2))
+        assert norm_err(csi[v].cpu().numpy(), oracle.csi(o["spectra"]), a) <= TOL, v
+        gspec = np.broadcast_to(gc[v].astype(np.float64)[:, None, None, :, :], (N, g.H, g.W, C, 2))
+        gr, gt, ar, at = oracle.backward_view(g, sc, tx[v], rad.astype(np.float64), gspec,
+                                              want_abs=True)
+        ref_r += gr
+        abs_r += ar
+        ref_t += gt
+        abs_t += at
+    assert float((np.abs(d_rad.cpu().numpy() - ref_r) / (abs_r + 1e-30)).max()) <= TOL
+    assert float((np.abs(d_tau.cpu().numpy() - ref_t) / (abs_t + 1e-30)).max()) <= TOL
