@@ -408,26 +408,17 @@ static rxgs_status new_plan(rxgs_ctx* ctx, rxgs_scene_t scene, const SceneState*
 // The smallest existing plan that fits, so launch sizes stay within 2x of
 // the batch (plans come in power-of-two size classes of views and receivers).
 static BatchPlan* find_plan(rxgs_ctx* ctx, rxgs_scene_t scene, int kind, bool mlp, bool vis, int B,
-                            int R, int tag, bool allow_larger) {
+                            int R, int tag) {
   const int NB = ctx->opts.cols_per_cta ? ctx->opts.cols_per_cta : 64;
   const int Bc = next_pow2(B, 4), Rc = next_pow2(R, 32);
   BatchPlan* best = nullptr;
-  BatchPlan* any = nullptr;  // the smallest fitting plan of any size
-  for (BatchPlan* q : ctx->plans) {
-    if (!(q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp &&
-          q->vis == vis && q->B_max >= B && q->R_max >= R && q->g.TH == ctx->g.TH &&
-          q->g.TW == ctx->g.TW && q->NB == NB))
-      continue;
-    const size_t sz = static_cast<size_t>(q->B_max) * q->R_max;
-    if (!any || sz < static_cast<size_t>(any->B_max) * any->R_max) any = q;
-    if (q->B_max <= 2 * Bc && q->R_max <= 2 * Rc &&
-        (!best || sz < static_cast<size_t>(best->B_max) * best->R_max))
+  for (BatchPlan* q : ctx->plans)
+    if (q->scene == scene && q->tag == tag && q->kind == kind && q->mlp == mlp && q->vis == vis &&
+        q->B_max >= B && q->R_max >= R && q->B_max <= 2 * Bc && q->R_max <= 2 * Rc &&
+        q->g.TH == ctx->g.TH && q->g.TW == ctx->g.TW && q->NB == NB &&
+        (!best || static_cast<size_t>(q->B_max) * q->R_max <
+                      static_cast<size_t>(best->B_max) * best->R_max))
       best = q;
-  }
-  // with allow_larger, a batch whose size class has no plan yet runs in a
-  // larger one when there is one (its kernels read the real sizes from the
-  // descriptor) rather than waiting for a plan to be built and captured
-  if (!best && allow_larger) best = any;
   return best;
 }
 
@@ -505,7 +496,7 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
   BatchPlan* p = nullptr;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    p = find_plan(ctx, scene, kind, mlp, vis, B, R, tag, false);
+    p = find_plan(ctx, scene, kind, mlp, vis, B, R, tag);
   }
   if (!p) {
     uint32_t per_view = 0;
