@@ -132,6 +132,20 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def whole_job_rate(torch, dist, ms_local, units_per_step, device):
+    """Replicas: every rank processes `units_per_step` per step in
+    `ms_local` ms; the job's step time is the slowest rank's (max over
+    ranks) and its rate counts the units of all ranks.  Returns
+    (ms_max, units per second of the whole job)."""
+    t = torch.tensor([float(ms_local)], device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return ms_max, world * units_per_step / (ms_max / 1e3)
+
+
 # --------------------------------------------------------------- the step
 class Workload:
     def __init__(self, torch, rxgs, S, device):
@@ -254,12 +268,8 @@ def gpu_bench(args):
     launches = prof["kernel_launches"] - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     spectra_per_step = W.M * W.N
-    value = world * spectra_per_step / (ms_max / 1e3)
+    ms_max, value = whole_job_rate(torch, dist if world > 1 else None, ms, spectra_per_step, dev)
 
     # ---- roofline of the dominant kernel
     stages = prof["stages"]
@@ -379,11 +389,9 @@ def gpu_bench(args):
             e2e_step()
         barrier()
         e_ms = (time.perf_counter() - t0) * 1e3 / n_e
-        te = torch.tensor([e_ms], device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e_ms = float(te.item())
-        e2e = {"value": round(world * spectra_per_step / (e_ms / 1e3), 2), "unit": UNIT,
+        e_ms, e_val = whole_job_rate(torch, dist if world > 1 else None, e_ms, spectra_per_step,
+                                     dev)
+        e2e = {"value": round(e_val, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e_ms, 4)}
 
