@@ -798,8 +798,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   if (!d->radiance && !d->fle_coeffs) {
     if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
     if (s->bf16) return fail(ctx, RXGS_E_INVALID, "backward through a bf16 MLP is not supported");
-    if (s->C > 4 || static_cast<size_t>(N) * 4 * s->C > 8192)
-      return fail(ctx, RXGS_E_INVALID, "MLP backward supports C <= 4 and N*4C <= 8192");
+
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);

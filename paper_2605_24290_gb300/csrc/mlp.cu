@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     const float* __restrict__ P, const float* __restrict__ rx, int N,
     const float4* __restrict__ geom, const float* __restrict__ base, int K, int stride,
     const float* __restrict__ dS, const float* __restrict__ glob, float* __restrict__ grad_base,
-    float* __restrict__ part, const float2* __restrict__ feat) {
+    float* __restrict__ part, const float2* __restrict__ feat, int c0, int Ct) {
+  // channels c0 .. c0 + CC - 1 of Ct (one group of a wide spectrum)
   constexpr int n4 = 4 * CC;
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   constexpr int kWarps = kBwdThreads / 32;
@@ -349,12 +350,12 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   __shared__ float2 sO[kBwdThreads];            // its occlusion inputs (T, rho_bar)
   __shared__ float4 sD[kBwdThreads * CC];       // dol of each thread's pair
   extern __shared__ float sdyn[];  // [kWarps][nloc] warp partials, then [256][4C]
-  const MlpOffsets o = mlp_offsets(kHidden, CC);
+  const MlpOffsets o = mlp_offsets(kHidden, Ct);
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int e = t; e < kHidden * 6; e += kBwdThreads) W1[e] = P[o.l_w1 + e];
   for (int e = t; e < kHidden; e += kBwdThreads) B1[e] = P[o.l_b1 + e];
-  for (int e = t; e < n4 * kHidden; e += kBwdThreads) W2[e] = P[o.l_w2 + e];
-  for (int e = t; e < n4; e += kBwdThreads) B2[e] = P[o.l_b2 + e];
+  for (int e = t; e < n4 * kHidden; e += kBwdThreads) W2[e] = P[o.l_w2 + 4 * c0 * kHidden + e];
+  for (int e = t; e < n4; e += kBwdThreads) B2[e] = P[o.l_b2 + 4 * c0 + e];
   __syncthreads();
 
   // phase-2 operands of this lane's hidden units u = lane, lane + 32
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   const float rxj = rx[3 * j + 0], ryj = rx[3 * j + 1], rzj = rx[3 * j + 2];
   float gj[n4];
 #pragma unroll
-  for (int q = 0; q < n4; ++q) gj[q] = glob[static_cast<size_t>(j) * n4 + q];
+  for (int q = 0; q < n4; ++q) gj[q] = glob[static_cast<size_t>(j) * 4 * Ct + 4 * c0 + q];
 
   const size_t rounds = (pairs + gstride - 1) / gstride;
   for (size_t r = 0; r < rounds; ++r) {
@@ -431,12 +432,12 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
 #pragma unroll
         for (int q = 0; q < n4; ++q) oall[q] = fmaf(W2[q * kHidden + u], hu, oall[q]);
       }
-      const float* gs = dS + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * CC;
+      const float* gs = dS + static_cast<size_t>(k) * stride + static_cast<size_t>(j) * 2 * Ct + 2 * c0;
 #pragma unroll
       for (int c = 0; c < CC; ++c) {
         const float ol[4] = {oall[4 * c], oall[4 * c + 1], oall[4 * c + 2], oall[4 * c + 3]};
-        const float pr = base[(static_cast<size_t>(k) * CC + c) * 2 + 0];
-        const float pi = base[(static_cast<size_t>(k) * CC + c) * 2 + 1];
+        const float pr = base[(static_cast<size_t>(k) * Ct + c0 + c) * 2 + 0];
+        const float pi = base[(static_cast<size_t>(k) * Ct + c0 + c) * 2 + 1];
         const float agr = 1.0f + gj[4 * c + 0], agi = gj[4 * c + 1];
         const float ur = agr * pr - agi * pi + gj[4 * c + 2];
         const float ui = agr * pi + agi * pr + gj[4 * c + 3];
@@ -466,12 +467,12 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
           float y = db[q];
 #pragma unroll
           for (int off = 16; off >= 1; off >>= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
-          if (lane == 0) atomicAdd(&grad_base[static_cast<size_t>(k0) * 2 * CC + q], y);
+          if (lane == 0) atomicAdd(&grad_base[(static_cast<size_t>(k0) * Ct + c0) * 2 + q], y);
         }
       } else if (ok) {
 #pragma unroll
         for (int q = 0; q < 2 * CC; ++q)
-          atomicAdd(&grad_base[static_cast<size_t>(k) * 2 * CC + q], db[q]);
+          atomicAdd(&grad_base[(static_cast<size_t>(k) * Ct + c0) * 2 + q], db[q]);
       }
     }
 #pragma unroll
@@ -579,17 +580,29 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
 
 // Sums the block partials in block order: local parameters go into
 // grad_mlp, the per-receiver (a_g, b_g) gradients into dog[N][4C].
+// Sums the block partials of one channel group (channels c0 .. c0 + cc - 1
+// of Ct) in block order: W1 and B1 add into grad_mlp (every group
+// contributes), the group's W2 rows and B2 entries go to their places, and
+// the per-receiver (a_g, b_g) gradients to dog[N][4 Ct].
 __global__ void mlp_partial_reduce_kernel(const float* __restrict__ part, int blocks, int nloc,
-                                          int nog, int l_off, float* __restrict__ grad_mlp,
-                                          float* __restrict__ dog) {
+                                          int nog, MlpOffsets o, int c0, int cc, int Ct,
+                                          float* __restrict__ grad_mlp, float* __restrict__ dog) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nloc + nog) return;
   float s = 0.0f;
   for (int b = 0; b < blocks; ++b) s += part[static_cast<size_t>(b) * (nloc + nog) + e];
-  if (e < nloc)
-    grad_mlp[l_off + e] += s;
-  else
-    dog[e - nloc] = s;
+  const int n4 = 4 * cc;
+  const int w1b1 = kHidden * 7, w2 = n4 * kHidden;
+  if (e < w1b1) {
+    grad_mlp[o.l_w1 + e] += s;
+  } else if (e < w1b1 + w2) {
+    grad_mlp[o.l_w2 + 4 * c0 * kHidden + (e - w1b1)] += s;
+  } else if (e < nloc) {
+    grad_mlp[o.l_b2 + 4 * c0 + (e - w1b1 - w2)] += s;
+  } else {
+    const int jq = e - nloc, jj = jq / n4, q = jq % n4;
+    dog[static_cast<size_t>(jj) * 4 * Ct + 4 * c0 + q] = s;
+  }
 }
 
 // Global branch backward for all receivers in one block (N is small).
@@ -636,7 +649,7 @@ template <int CC>
 static void launch_mlp_local_bwd(int blocks, const MlpParams& m, const float* rx, int N,
                                  const float4* geom, const float* base, int K, int stride,
                                  const float* dS, const float* glob, float* grad_base, float* part,
-                                 cudaStream_t s) {
+                                 int c0, cudaStream_t s) {
   constexpr int n4 = 4 * CC;
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   const size_t smem = sizeof(float) * ((kBwdThreads / 32) * nloc + kBwdThreads * n4);
@@ -644,12 +657,12 @@ static void launch_mlp_local_bwd(int blocks, const MlpParams& m, const float* rx
     cudaFuncSetAttribute(mlp_local_bwd_kernel<CC, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     mlp_local_bwd_kernel<CC, true><<<blocks, kBwdThreads, smem, s>>>(
-        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, m.feat);
+        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, m.feat, c0, m.C);
   } else {
     cudaFuncSetAttribute(mlp_local_bwd_kernel<CC, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     mlp_local_bwd_kernel<CC, false><<<blocks, kBwdThreads, smem, s>>>(
-        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, nullptr);
+        m.p, rx, N, geom, base, K, stride, dS, glob, grad_base, part, nullptr, c0, m.C);
   }
   note_launches(1);
 }
@@ -661,19 +674,24 @@ void launch_mlp_backward(const MlpParams& m, const float* rx, int N, const float
   const int C = m.C, n4 = 4 * C;
   const int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   const int blocks = mlp_bwd_blocks(N);
-  float* part = tmp;
+  float* part = tmp;  // one channel group's block partials at a time
   float* dog = tmp + static_cast<size_t>(blocks) * (nloc + static_cast<size_t>(N) * n4);
-  switch (C) {
-    case 1: launch_mlp_local_bwd<1>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
-    case 2: launch_mlp_local_bwd<2>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
-    case 3: launch_mlp_local_bwd<3>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
-    default: launch_mlp_local_bwd<4>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, s); break;
-  }
-  const int tot = nloc + N * n4;
   const MlpOffsets o = mlp_offsets(kHidden, C);
-  mlp_partial_reduce_kernel<<<(tot + 255) / 256, 256, 0, s>>>(part, blocks, nloc, N * n4, o.l_w1,
-                                                              grad_mlp, dog);
-  note_launches(1);
+  // channels in groups of up to 4: the hidden-layer gradient is a sum over
+  // output channels, so the groups' contributions to W1 and B1 add up
+  for (int c0 = 0; c0 < C; c0 += 4) {
+    const int cc = C - c0 < 4 ? C - c0 : 4;
+    switch (cc) {
+      case 1: launch_mlp_local_bwd<1>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, c0, s); break;
+      case 2: launch_mlp_local_bwd<2>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, c0, s); break;
+      case 3: launch_mlp_local_bwd<3>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, c0, s); break;
+      default: launch_mlp_local_bwd<4>(blocks, m, rx, N, geom, base, K, stride, dS, glob, grad_base, part, c0, s); break;
+    }
+    const int gl = kHidden * 7 + 4 * cc * kHidden + 4 * cc, gog = N * 4 * cc;
+    mlp_partial_reduce_kernel<<<(gl + gog + 255) / 256, 256, 0, s>>>(part, blocks, gl, gog, o, c0,
+                                                                     cc, C, grad_mlp, dog);
+    note_launches(1);
+  }
   mlp_global_bwd_kernel<<<1, 256, 0, s>>>(m.p, C, rx, N, dog, grad_mlp);
   note_launches(1);
 }
