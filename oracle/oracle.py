@@ -518,3 +518,106 @@ def fle_backward(grad_rad, means, centre, lmax: int):
     da = g[..., 0:1] * Y.real + g[..., 1:2] * Y.imag
     db = -g[..., 0:1] * Y.imag + g[..., 1:2] * Y.real
     return np.stack([da, db], axis=2)
+
+
+# ------------------ global branch over the FLE components (Eq. rx_enc, film, film_apply)
+# Parameters (a dict of arrays; float64 inside):
+#   omega [F, 3]   frequency vectors of the receiver encoding
+#   embed [L, dc]  learnable component embeddings e_l
+#   w1 [D, din], b1 [D], w2 [D, D], b2 [D], w3 [4, D], b3 [4],  din = 2F + 2 + dc
+# The global MLP has three linear layers with ReLU between them (App. E.4);
+# its four outputs per (receiver, component) are (a.re, a.im, b.re, b.im).
+# Component l*l + l + m carries the degree/order feature c_l = (l, m) / max(lmax, 1).
+
+
+def rx_encoding(rx, omega):
+    """gamma(r) of Eq. rx_enc: [sin(w_1.r), cos(w_1.r), ..., sin(w_F.r), cos(w_F.r)]."""
+    ph = np.asarray(rx, np.float64) @ np.asarray(omega, np.float64).T      # [N, F]
+    out = np.empty(ph.shape[:-1] + (2 * ph.shape[-1],), np.float64)
+    out[..., 0::2] = np.sin(ph)
+    out[..., 1::2] = np.cos(ph)
+    return out
+
+
+def film_component_features(lmax: int):
+    """c_l = (l, m) / max(lmax, 1) for component l*l + l + m: [L, 2]."""
+    L = fle_count(lmax)
+    c = np.zeros((L, 2), np.float64)
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            c[l * l + l + m] = (l, m)
+    return c / max(lmax, 1)
+
+
+def film_inputs(film, rx, lmax: int):
+    """x [N, L, din] = [gamma(r_j); c_l; e_l] (the input of Eq. film)."""
+    g = rx_encoding(rx, film["omega"])                                    # [N, 2F]
+    c = film_component_features(lmax)                                      # [L, 2]
+    e = np.asarray(film["embed"], np.float64)                              # [L, dc]
+    N, L = g.shape[0], c.shape[0]
+    return np.concatenate([np.broadcast_to(g[:, None, :], (N, L, g.shape[1])),
+                           np.broadcast_to(c[None], (N, L, 2)),
+                           np.broadcast_to(e[None], (N, L, e.shape[1]))], axis=-1)
+
+
+def _film_mlp(P, x):
+    h1 = np.maximum(x @ P["w1"].T + P["b1"], 0.0)
+    h2 = np.maximum(h1 @ P["w2"].T + P["b2"], 0.0)
+    return h2 @ P["w3"].T + P["b3"], h1, h2
+
+
+def film_global(film, rx, lmax: int):
+    """(a_l, b_l) per receiver and component (Eq. film): [N, L, 4] =
+    (a.re, a.im, b.re, b.im)."""
+    P = {k: np.asarray(v, np.float64) for k, v in film.items()}
+    out, _, _ = _film_mlp(P, film_inputs(P, rx, lmax))
+    return out
+
+
+def film_fle_coeffs(film, base, rx, lmax: int):
+    """Per-receiver FLE coefficients [N,K,2,L] from the base coefficients
+    base [K,2,L] (Eq. film_apply): (1 + a_l) phi_kl + b_l, complex, the same
+    modulation for every Gaussian."""
+    ab = film_global(film, rx, lmax)                                       # [N, L, 4]
+    a = (1.0 + ab[..., 0]) + 1j * ab[..., 1]
+    b = ab[..., 2] + 1j * ab[..., 3]
+    base = np.asarray(base, np.float64)
+    phi = base[:, 0, :] + 1j * base[:, 1, :]                               # [K, L]
+    c = a[:, None, :] * phi[None] + b[:, None, :]                         # [N, K, L]
+    return np.stack([c.real, c.imag], axis=2)
+
+
+def film_fle_backward(film, base, rx, lmax: int, grad_coeffs):
+    """Gradients of sum(grad_coeffs * coeffs) (coeffs = film_fle_coeffs)
+    w.r.t. base [K,2,L] and every FiLM parameter (float64, same names as
+    `film`).  With G = dL/dRe + i dL/dIm of a coefficient: dL/dphi = conj(1 + a) G,
+    dL/da = conj(phi) G, dL/db = G."""
+    P = {k: np.asarray(v, np.float64) for k, v in film.items()}
+    base = np.asarray(base, np.float64)
+    gc = np.asarray(grad_coeffs, np.float64)
+    G = gc[:, :, 0, :] + 1j * gc[:, :, 1, :]                               # [N, K, L]
+    x = film_inputs(P, rx, lmax)
+    ab, h1, h2 = _film_mlp(P, x)
+    a = (1.0 + ab[..., 0]) + 1j * ab[..., 1]                               # [N, L]
+    phi = base[:, 0, :] + 1j * base[:, 1, :]
+    d_phi = (np.conj(a)[:, None, :] * G).sum(axis=0)                        # [K, L]
+    d_a = (np.conj(phi)[None] * G).sum(axis=1)                              # [N, L]
+    d_b = G.sum(axis=1)
+    d_out = np.stack([d_a.real, d_a.imag, d_b.real, d_b.imag], axis=-1)     # [N, L, 4]
+    out = {"base": np.stack([d_phi.real, d_phi.imag], axis=1)}
+    out["w3"] = np.einsum("nlo,nlh->oh", d_out, h2)
+    out["b3"] = d_out.sum(axis=(0, 1))
+    d_h2 = (d_out @ P["w3"]) * (h2 > 0)
+    out["w2"] = np.einsum("nlo,nlh->oh", d_h2, h1)
+    out["b2"] = d_h2.sum(axis=(0, 1))
+    d_h1 = (d_h2 @ P["w2"]) * (h1 > 0)
+    out["w1"] = np.einsum("nlo,nli->oi", d_h1, x)
+    out["b1"] = d_h1.sum(axis=(0, 1))
+    d_x = d_h1 @ P["w1"]                                                    # [N, L, din]
+    F = P["omega"].shape[0]
+    out["embed"] = d_x[..., 2 * F + 2:].sum(axis=0)
+    d_g = d_x[..., :2 * F].sum(axis=1)                                      # [N, 2F]
+    ph = np.asarray(rx, np.float64) @ P["omega"].T
+    d_ph = d_g[:, 0::2] * np.cos(ph) - d_g[:, 1::2] * np.sin(ph)            # [N, F]
+    out["omega"] = d_ph.T @ np.asarray(rx, np.float64)
+    return out

@@ -267,3 +267,47 @@ def hashed_radiance_torch(torch, N: int, K: int, device, rows_per_pass: int = 32
         out[j0:j1, :, 0, 0] = re.to(torch.float32)
         out[j0:j1, :, 0, 1] = im.to(torch.float32)
     return out
+
+
+# --------------------------- global FiLM over FLE components (App. E.4 sizes)
+FILM_BANDS = 6      # Fourier bands per spatial dimension
+FILM_EMBED = 16     # component embedding width d_c
+FILM_HIDDEN = 64    # hidden width d of the 3-layer global MLP
+
+
+def film_frequencies(F: int = FILM_BANDS) -> np.ndarray:
+    """The receiver encoding's frequency vectors at their initial values:
+    2^f along each axis, f = 0 .. F-1 (3F vectors, x bands first)."""
+    w = np.zeros((3 * F, 3), np.float64)
+    for d in range(3):
+        for f in range(F):
+            w[d * F + f, d] = 2.0 ** f
+    return f32(w)
+
+
+def draw_film(rng: np.random.Generator, lmax: int, F: int = FILM_BANDS, dc: int = FILM_EMBED,
+              D: int = FILM_HIDDEN, out_scale: float = 0.3) -> dict:
+    """Parameters of the global FiLM MLP over L = (lmax+1)^2 components:
+    frequencies at their initial spacing, random embeddings and weights.
+    The final layer is drawn non-zero (a trained state, not the identity
+    of the zero initialisation)."""
+    L = (lmax + 1) ** 2
+    nw = 3 * F
+    din = 2 * nw + 2 + dc
+    return {
+        "omega": film_frequencies(F),
+        "embed": f32(0.5 * rng.normal(size=(L, dc))),
+        "w1": f32(rng.normal(size=(D, din)) * np.sqrt(2.0 / din)),
+        "b1": f32(0.1 * rng.normal(size=D)),
+        "w2": f32(rng.normal(size=(D, D)) * np.sqrt(2.0 / D)),
+        "b2": f32(0.1 * rng.normal(size=D)),
+        "w3": f32(rng.normal(size=(4, D)) * out_scale / np.sqrt(D)),
+        "b3": f32(0.1 * out_scale * rng.normal(size=4)),
+    }
+
+
+def draw_fle_base(rng: np.random.Generator, K: int, lmax: int) -> np.ndarray:
+    """Base FLE coefficients [K, 2, L], decaying with the degree l."""
+    L = (lmax + 1) ** 2
+    l_of = np.floor(np.sqrt(np.arange(L)))
+    return f32(rng.normal(size=(K, 2, L)) / (1.0 + l_of)[None, None, :])

@@ -687,3 +687,112 @@ def test_mlp_backward_with_occupancy_matches_finite_differences(oracle):
         f2 = (g * oracle.mlp_radiance(P2, rx, sc.means, base, occ=occ)).sum()
         fd = (f1 - f2) / (2 * h)
         assert abs(fd - grads["l_w1"][u, i]) <= 1e-6 * (1 + abs(fd)), (u, i, fd, grads["l_w1"][u, i])
+
+
+# ------------- global FiLM over FLE components (Eq. rx_enc, film, film_apply)
+def _tiny_film(lmax, nw, dc, D, w3, b3):
+    din = 2 * nw + 2 + dc
+    return {"omega": np.zeros((nw, 3)), "embed": np.zeros((oracle_L(lmax), dc)),
+            "w1": np.zeros((D, din)), "b1": np.zeros(D), "w2": np.zeros((D, D)),
+            "b2": np.zeros(D), "w3": np.asarray(w3, float), "b3": np.asarray(b3, float)}
+
+
+def oracle_L(lmax):
+    return (lmax + 1) ** 2
+
+
+def test_rx_encoding_hand_values(oracle):
+    """Interleaved [sin(w_1.r), cos(w_1.r), sin(w_2.r), cos(w_2.r)]."""
+    om = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    r = np.array([[np.pi / 2, np.pi / 8, 5.0]])
+    g = oracle.rx_encoding(r, om)[0]
+    h = np.sqrt(0.5)
+    np.testing.assert_allclose(g, [1.0, 0.0, h, h], atol=1e-15)
+
+
+def test_film_component_features_index_map(oracle):
+    """Component l*l + l + m carries (l, m) / lmax."""
+    c = oracle.film_component_features(2)
+    np.testing.assert_array_equal(c[0], [0.0, 0.0])
+    np.testing.assert_array_equal(c[3], [0.5, 0.5])       # (1, 1)
+    np.testing.assert_array_equal(c[5], [1.0, -0.5])      # (2, -1)
+    np.testing.assert_array_equal(c[8], [1.0, 1.0])       # (2, 2)
+    np.testing.assert_array_equal(oracle.film_component_features(0), [[0.0, 0.0]])
+
+
+def test_film_zero_final_layer_is_identity(oracle):
+    """Zero-initialised final layer (App. E.4): every receiver sees the base
+    coefficients unchanged."""
+    rng = np.random.default_rng(40)
+    lmax, K, N = 3, 6, 4
+    film = S.draw_film(rng, lmax, F=2, dc=3, D=8)
+    film["w3"][:] = 0.0
+    film["b3"][:] = 0.0
+    base = S.draw_fle_base(rng, K, lmax)
+    c = oracle.film_fle_coeffs(film, base, rng.normal(size=(N, 3)), lmax)
+    for j in range(N):
+        np.testing.assert_array_equal(c[j], base.astype(np.float64))
+
+
+def test_film_apply_complex_affine_hand_value(oracle):
+    """w3 = 0, b3 = (0.5, 0.25, 0.1, -0.2): (1.5 + 0.25i)(1 + 2i) + (0.1 - 0.2i)
+    = 1.1 + 3.05i."""
+    film = _tiny_film(0, 1, 1, 2, np.zeros((4, 2)), [0.5, 0.25, 0.1, -0.2])
+    base = np.zeros((1, 2, 1))
+    base[0, 0, 0], base[0, 1, 0] = 1.0, 2.0
+    c = oracle.film_fle_coeffs(film, base, np.zeros((1, 3)), 0)
+    np.testing.assert_allclose(c[0, 0, :, 0], [1.1, 3.05], rtol=1e-15)
+
+
+def test_film_mlp_hand_network(oracle):
+    """A hand-wired 3-layer network over x = [sin, cos, c_l, c_m, e_l]:
+    h1 = relu(s), relu(-s), relu(c_m + e); h2 = w2 h1 with w2 not
+    symmetric; outputs a.re = h2_0, a.im = h2_2, b.re = h2_1.  With
+    s = sin(w.r) = +-1/2 and embeddings (0.5, 0.25, -0.5, 2) over lmax = 1."""
+    w3 = np.zeros((4, 3))
+    w3[0, 0], w3[1, 2], w3[2, 1] = 1.0, 1.0, 1.0
+    film = _tiny_film(1, 1, 1, 3, w3, np.zeros(4))
+    film["omega"][0] = (1.0, 0.0, 0.0)
+    film["embed"][:, 0] = (0.5, 0.25, -0.5, 2.0)
+    film["w1"][0, 0], film["w1"][1, 0] = 1.0, -1.0
+    film["w1"][2, 3], film["w1"][2, 4] = 1.0, 1.0
+    film["w2"][:] = [[1.0, 2.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]
+    rx = np.array([[np.pi / 6, 0.0, 0.0], [-np.pi / 6, 0.0, 0.0]])
+    ab = oracle.film_global(film, rx, 1)                       # [2, 4, 4]
+    np.testing.assert_allclose(ab[0, :, 0], 0.5, rtol=1e-14)  # relu(s)
+    np.testing.assert_allclose(ab[1, :, 0], 1.0, rtol=1e-14)  # 2 relu(-s)
+    np.testing.assert_allclose(ab[0, :, 2], 0.0, atol=1e-15)
+    np.testing.assert_allclose(ab[1, :, 2], 0.5, rtol=1e-14)
+    for j in range(2):                                         # relu(m + e_l)
+        np.testing.assert_allclose(ab[j, :, 1], [0.5, 0.0, 0.0, 3.0], atol=1e-15)
+    np.testing.assert_array_equal(ab[..., 3], 0.0)
+
+
+def test_film_backward_matches_finite_differences(oracle):
+    """Every FiLM parameter and the base coefficients against central
+    differences of film_fle_coeffs."""
+    rng = np.random.default_rng(41)
+    lmax, K, N = 2, 3, 3
+    film = {k: v.astype(np.float64) for k, v in
+            S.draw_film(rng, lmax, F=2, dc=3, D=5, out_scale=1.0).items()}
+    base = S.draw_fle_base(rng, K, lmax).astype(np.float64)
+    rx = rng.uniform(-1.0, 1.0, size=(N, 3))
+    gc = rng.normal(size=(N, K, 2, oracle.fle_count(lmax)))
+    got = oracle.film_fle_backward(film, base, rx, lmax, gc)
+
+    def loss(f, b):
+        return float((gc * oracle.film_fle_coeffs(f, b, rx, lmax)).sum())
+
+    h = 1e-6
+    for name in ["omega", "embed", "w1", "b1", "w2", "b2", "w3", "b3", "base"]:
+        ref = np.zeros_like(got[name])
+        src = base if name == "base" else film[name]
+        for idx in np.ndindex(src.shape):
+            keep = src[idx]
+            src[idx] = keep + h
+            lp = loss(film, base)
+            src[idx] = keep - h
+            lm = loss(film, base)
+            src[idx] = keep
+            ref[idx] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(got[name], ref, rtol=1e-6, atol=1e-7, err_msg=name)
