@@ -648,10 +648,33 @@ def fle_bench(torch, rxgs, S, reps=3, lmax=9):
         ctx.render_backward(views, None, N, rxgs.OUT_SPECTRA, grad_spectra=gspec,
                             grad_opacity=d_tau, fle_coeffs=coeffs, fle_lmax=lmax, grad_fle=d_fle)
 
+    # the same with the coefficients conditioned by the global FiLM branch
+    # (Eq. film, film_apply; App. E.4 sizes: F = 6, d_c = 16, d = 64)
+    rng = np.random.default_rng(S.SEED_BASE + 51)
+    film_np = S.draw_film(rng, lmax)
+    dims = rxgs.film_sizes(film_np)
+    film = d(rxgs.pack_film(film_np))
+    base = d(S.draw_fle_base(rng, K, lmax))
+    rx_d = d(w["rx"])
+    d_base = torch.zeros_like(base)
+    d_film = torch.zeros_like(film)
+
+    def film_fwd():
+        ctx.render_views(views, rx_d, N, rxgs.OUT_SPECTRA, spectra=spec, fle_lmax=lmax,
+                         fle_base=base, film=film, film_dims=dims)
+
+    def film_fwd_bwd():
+        film_fwd()
+        ctx.render_backward(views, rx_d, N, rxgs.OUT_SPECTRA, grad_spectra=gspec,
+                            grad_opacity=d_tau, fle_lmax=lmax, fle_base=base, film=film,
+                            film_dims=dims, grad_fle_base=d_base, grad_film=d_film)
+
     fwd_bwd()
+    film_fwd_bwd()
     ctx.sync()
     out = {}
-    for name, fn in (("forward", fwd), ("forward_backward", fwd_bwd)):
+    for name, fn in (("forward", fwd), ("forward_backward", fwd_bwd),
+                     ("film_forward", film_fwd), ("film_forward_backward", film_fwd_bwd)):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ctx.profile(True)
         ctx.profile_read(reset=True)
@@ -667,9 +690,14 @@ def fle_bench(torch, rxgs, S, reps=3, lmax=9):
     ctx.release_views(views)
     ctx.close()
     ms = out["forward_backward"]["ms"]
-    return {"spectra_per_s_fwd_bwd": round(M * N / (ms / 1e3), 1), **out,
+    ms_f = out["film_forward_backward"]["ms"]
+    return {"spectra_per_s_fwd_bwd": round(M * N / (ms / 1e3), 1),
+            "film_spectra_per_s_fwd_bwd": round(M * N / (ms_f / 1e3), 1), **out,
             "workload": "100k Gaussians, 32 tx x 64 rx, FLE degree 9 (L = 100), 90x360, "
-                        "spectra; backward to coefficients and opacity"}
+                        "spectra; backward to coefficients and opacity; film_*: base "
+                        "coefficients [100k, 2, 100] conditioned by the global FiLM branch "
+                        "(18 frequency vectors, d_c = 16, d = 64), backward to the base, "
+                        "every FiLM parameter and the opacity"}
 
 
 def train_bench(torch, rxgs, S, reps=3):

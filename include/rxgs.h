@@ -168,14 +168,48 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream);
  *              P without the Condon-Shortley phase.  Needs C == 1,
  *              radiance == NULL, reduce_path == 0 and 0 <= fle_lmax <= 9; the
  *              radiance then differs per transmitter.
- *   fle_lmax   the degree of fle_coeffs */
+ *   fle_lmax   the degree of fle_coeffs (or of fle_base)
+ *   fle_base   [K,2,L] float32 or NULL: base FLE coefficients conditioned on
+ *              the receiver by the global FiLM branch (Eq. rx_enc, film,
+ *              film_apply): receiver j's coefficient l of Gaussian k is
+ *              (1 + a_jl) fle_base_kl + b_jl (complex), with (a_jl, b_jl) from
+ *              `film` (see rxgs_film_eval).  Excludes fle_coeffs and radiance;
+ *              needs `film`, rx, C == 1, reduce_path == 0, 0 <= fle_lmax <= 9.
+ *   film       packed FiLM parameters (rxgs_film_param_count floats, device),
+ *              read when fle_base != NULL
+ *   film_nfreq, film_embed, film_hidden   the FiLM sizes: frequency vectors
+ *              (1..32), embedding width (0..64), hidden width (1..256) */
 typedef struct {
   int kind;
   const float* radiance;
   int reduce_path;
   const float* fle_coeffs;
   int fle_lmax;
+  const float* fle_base;
+  const float* film;
+  int film_nfreq;
+  int film_embed;
+  int film_hidden;
 } rxgs_render_desc;
+
+/* The global FiLM branch over FLE components (Eq. rx_enc, film; App. E.4).
+ * Packed parameters, float32, in this order:
+ *   omega[nfreq][3]   frequency vectors of the receiver encoding
+ *                     gamma(r) = [sin(w_1.r), cos(w_1.r), ..., sin(w_F.r), cos(w_F.r)]
+ *   embed[L][embed]   component embeddings e_l, L = (lmax + 1)^2
+ *   w1[hidden][din], b1[hidden], w2[hidden][hidden], b2[hidden],
+ *   w3[4][hidden], b3[4]   three linear layers, ReLU between them,
+ *                     din = 2 nfreq + 2 + embed
+ * The input of component l*l + l + m for receiver r is
+ * [gamma(r); l / max(lmax, 1); m / max(lmax, 1); e_l]; the four outputs are
+ * (a.re, a.im, b.re, b.im).
+ * rxgs_film_param_count returns the packed length, or 0 for sizes out of range.
+ * rxgs_film_eval writes ab[N][L][4] for receivers rx[N][3] (device pointers
+ * on `stream`, caller-owned); RXGS_E_INVALID for sizes out of range or null
+ * pointers. */
+int64_t rxgs_film_param_count(int nfreq, int embed, int hidden, int lmax);
+rxgs_status rxgs_film_eval(rxgs_ctx* ctx, const float* film, int nfreq, int embed, int hidden,
+                           int lmax, const float* rx, int N, float* ab, void* stream);
 
 /* Outputs, all optional except those `kind` asks for:
  *   spectra  [M,N,H,W,C,2]
@@ -312,6 +346,10 @@ typedef struct {
   float* grad_base;
   float* grad_mlp;
   float* grad_fle;       /* [N,K,2,L] += dL/dfle_coeffs (FLE radiance), or NULL */
+  float* grad_fle_base;  /* [K,2,L] += dL/dfle_base (FiLM-conditioned FLE), or NULL */
+  float* grad_film;      /* packed like `film` += dL/dfilm, or NULL; the MLP's
+                            weight gradients are summed in a fixed order, the
+                            per-receiver (a, b) gradients with float atomics */
 } rxgs_grads;
 
 rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float* rx, int N,

@@ -498,13 +498,46 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream) 
 // ------------------------------------------------------------------ render
 namespace {
 
+// Checks of the FLE radiance arguments (explicit or FiLM-conditioned).
+rxgs_status check_fle(rxgs_ctx* ctx, const SceneState* s, const rxgs_render_desc* d) {
+  if (!d->fle_coeffs && !d->fle_base) return RXGS_OK;
+  if (d->fle_coeffs && d->fle_base)
+    return fail(ctx, RXGS_E_INVALID, "fle_coeffs and fle_base exclude each other");
+  if (d->radiance) return fail(ctx, RXGS_E_INVALID, "radiance and FLE coefficients exclude each other");
+  if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
+  if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
+  if (d->reduce_path == 1) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 does not take FLE radiance");
+  if (d->fle_base) {
+    if (!d->film) return fail(ctx, RXGS_E_INVALID, "fle_base needs the FiLM parameters (film)");
+    if (rxgs_film_param_count(d->film_nfreq, d->film_embed, d->film_hidden, d->fle_lmax) <= 0)
+      return fail(ctx, RXGS_E_INVALID, "FiLM sizes out of range (nfreq 1..%d, embed 0..%d, hidden 1..%d)",
+                  kFilmMaxFreq, kFilmMaxEmbed, kFilmMaxHidden);
+  }
+  return RXGS_OK;
+}
+
+FilmDims desc_film_dims(const rxgs_render_desc* d) {
+  return film_dims(d->film_nfreq, d->film_embed, d->film_hidden, d->fle_lmax);
+}
+
 // Produces the Gaussian-major radiance [K][stride] for receivers rx[N]; with
 // FLE coefficients, one such array per view of v ([M][K][stride]).
 rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* v,
                           const float* rx, int N, const rxgs_render_desc* d, int stride,
                           float* rad, float* glob, cudaStream_t st) {
-  Stage sg(ctx, d->radiance ? "radiance_transpose" : (d->fle_coeffs ? "fle" : "mlp"), st);
-  if (d->fle_coeffs) {
+  Stage sg(ctx, d->radiance ? "radiance_transpose"
+                            : (d->fle_coeffs ? "fle" : (d->fle_base ? "fle_film" : "mlp")), st);
+  if (d->fle_base) {
+    const FilmDims f = desc_film_dims(d);
+    float4* ab = nullptr;
+    if (dalloc(&ab, static_cast<size_t>(N) * f.L, st) != cudaSuccess)
+      return fail(ctx, RXGS_E_OOM, "FiLM outputs");
+    launch_film_global(d->film, f, rx, N, ab, st);
+    cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
+    launch_fle_radiance(nullptr, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+                        static_cast<size_t>(s->K) * stride, rad, st, d->fle_base, ab);
+    dfree(ab, st);
+  } else if (d->fle_coeffs) {
     // pad columns of every row stay zero
     cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
     launch_fle_radiance(d->fle_coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
@@ -547,12 +580,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   ViewsState* v = it->second;
   const SceneState* s = ctx->scenes.at(v->scene);
   if ((kind & RXGS_OUT_RSSI) && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
-  if (d->fle_coeffs) {
-    if (d->radiance) return fail(ctx, RXGS_E_INVALID, "radiance and fle_coeffs exclude each other");
-    if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
-    if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
-    if (d->reduce_path == 1) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 does not take FLE radiance");
-  }
+  if (rxgs_status fs = check_fle(ctx, s, d); fs != RXGS_OK) return fs;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const GridConst& g = ctx->g;
@@ -608,7 +636,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
   }
   const int ncols = 2 * N * s->C;
   const int stride = round_up(ncols, 128);
-  const bool fle = d->fle_coeffs != nullptr;
+  const bool fle = d->fle_coeffs != nullptr || d->fle_base != nullptr;
   const size_t rad_view = fle ? static_cast<size_t>(s->K) * stride : 0;
   float* rad = nullptr;
   float* partial = nullptr;
@@ -632,7 +660,11 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     v->glob = glob;
     v->key_rx = rx;
     v->key_radiance = d->radiance;
-    v->key_fle = d->fle_coeffs;
+    v->key_fle = d->fle_coeffs ? d->fle_coeffs : d->fle_base;
+    v->key_film = d->fle_base ? d->film : nullptr;
+    v->key_film_dims[0] = d->fle_base ? d->film_nfreq : 0;
+    v->key_film_dims[1] = d->fle_base ? d->film_embed : 0;
+    v->key_film_dims[2] = d->fle_base ? d->film_hidden : 0;
     v->key_lmax = fle ? d->fle_lmax : -1;
     v->key_N = N;
     v->key_stride = stride;
@@ -790,12 +822,8 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   const ViewsState* v = it->second;
   const SceneState* s = ctx->scenes.at(v->scene);
   if (cot->grad_rssi && s->C != 1) return fail(ctx, RXGS_E_INVALID, "RSSI needs C == 1");
-  if (d->fle_coeffs) {
-    if (d->radiance) return fail(ctx, RXGS_E_INVALID, "radiance and fle_coeffs exclude each other");
-    if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
-    if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
-  }
-  if (!d->radiance && !d->fle_coeffs) {
+  if (rxgs_status fs = check_fle(ctx, s, d); fs != RXGS_OK) return fs;
+  if (!d->radiance && !d->fle_coeffs && !d->fle_base) {
     if (!s->mlp) return fail(ctx, RXGS_E_INVALID, "no radiance given and the scene has no MLP");
     if (s->bf16) return fail(ctx, RXGS_E_INVALID, "backward through a bf16 MLP is not supported");
 
@@ -807,14 +835,20 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   const int C = s->C, K = s->K, M = v->M;
   const int ncols = 2 * N * C;
   const int stride = round_up(ncols, 128);
-  const bool fle = d->fle_coeffs != nullptr;
+  const bool film = d->fle_base != nullptr;
+  const bool fle = d->fle_coeffs != nullptr || film;
   const size_t rad_view = fle ? static_cast<size_t>(K) * stride : 0;
   const size_t nrad = static_cast<size_t>(K) * stride * (fle ? M : 1);
   float *rad = nullptr, *glob = nullptr, *d_rad = nullptr, *g_uni = nullptr, *d_tau = nullptr;
   float *g_base = nullptr, *g_mlp = nullptr, *mlp_tmp = nullptr, *tfin = nullptr;
   uint32_t *stops = nullptr, *tstop = nullptr;
   const bool cached = v->rad && v->key_rx == rx && v->key_radiance == d->radiance &&
-                      v->key_fle == d->fle_coeffs && v->key_lmax == (fle ? d->fle_lmax : -1) &&
+                      v->key_fle == (d->fle_coeffs ? d->fle_coeffs : d->fle_base) &&
+                      v->key_film == (film ? d->film : nullptr) &&
+                      v->key_film_dims[0] == (film ? d->film_nfreq : 0) &&
+                      v->key_film_dims[1] == (film ? d->film_embed : 0) &&
+                      v->key_film_dims[2] == (film ? d->film_hidden : 0) &&
+                      v->key_lmax == (fle ? d->fle_lmax : -1) &&
                       v->key_N == N && v->key_stride == stride && v->key_gen == s->generation;
   auto cleanup = [&]() {
     if (cached) {
@@ -889,6 +923,32 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   if (d->radiance) {
     Stage sg(ctx, "radiance_grad", st);
     if (gr->grad_radiance) launch_radiance_untranspose_add(d_rad, N, K, C, stride, gr->grad_radiance, st);
+  } else if (film) {
+    const FilmDims f = desc_film_dims(d);
+    float4 *ab = nullptr, *d_ab = nullptr;
+    float* ftmp = nullptr;
+    const size_t S = static_cast<size_t>(N) * f.L;
+    e = dalloc(&ab, S, st);
+    if (e == cudaSuccess) e = dalloc(&d_ab, S, st);
+    if (e == cudaSuccess && gr->grad_film) e = dalloc(&ftmp, film_backward_tmp_floats(f, N), st);
+    if (e != cudaSuccess) {
+      dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st);
+      cleanup();
+      return fail(ctx, RXGS_E_OOM, "backward (FiLM): %s", cudaGetErrorString(e));
+    }
+    {
+      Stage sg(ctx, "fle_film_bwd", st);
+      cudaMemsetAsync(d_ab, 0, sizeof(float4) * S, st);
+      launch_film_global(d->film, f, rx, N, ab, st);
+      launch_film_fle_backward(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
+                               d->fle_base, ab, gr->grad_fle_base, reinterpret_cast<float*>(d_ab),
+                               st);
+    }
+    if (gr->grad_film) {
+      Stage sg(ctx, "film_mlp_bwd", st);
+      launch_film_backward(d->film, f, rx, N, d_ab, ftmp, gr->grad_film, st);
+    }
+    dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st);
   } else if (fle) {
     Stage sg(ctx, "fle_bwd", st);
     if (gr->grad_fle)
@@ -922,6 +982,25 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   rs = check_last(ctx, "backward");
   cleanup();
   return rs;
+}
+
+int64_t rxgs_film_param_count(int nfreq, int embed, int hidden, int lmax) {
+  if (nfreq < 1 || nfreq > kFilmMaxFreq || embed < 0 || embed > kFilmMaxEmbed || hidden < 1 ||
+      hidden > kFilmMaxHidden || lmax < 0 || lmax > 9)
+    return 0;
+  return static_cast<int64_t>(film_dims(nfreq, embed, hidden, lmax).total);
+}
+
+rxgs_status rxgs_film_eval(rxgs_ctx* ctx, const float* film, int nfreq, int embed, int hidden,
+                           int lmax, const float* rx, int N, float* ab, void* stream) {
+  if (!ctx || !film || !rx || !ab) return fail(ctx, RXGS_E_INVALID, "null argument");
+  if (N <= 0 || N > (1 << 20)) return fail(ctx, RXGS_E_INVALID, "N out of range");
+  if (rxgs_film_param_count(nfreq, embed, hidden, lmax) <= 0)
+    return fail(ctx, RXGS_E_INVALID, "FiLM sizes out of range");
+  CK(cudaSetDevice(ctx->device));
+  launch_film_global(film, film_dims(nfreq, embed, hidden, lmax), rx, N,
+                     reinterpret_cast<float4*>(ab), static_cast<cudaStream_t>(stream));
+  return check_last(ctx, "film_eval");
 }
 
 rxgs_status rxgs_profile(rxgs_ctx* ctx, int enable) {

@@ -472,7 +472,8 @@ rxgs_status render_batched_tagged(rxgs_ctx* ctx, rxgs_scene_t scene, const float
   if ((kind & RXGS_OUT_RSSI) && !out->rssi) return fail(ctx, RXGS_E_INVALID, "rssi == NULL");
   if ((kind & RXGS_OUT_CSI) && !out->csi) return fail(ctx, RXGS_E_INVALID, "csi == NULL");
   if (!d->radiance && !rx) return fail(ctx, RXGS_E_INVALID, "rx == NULL");
-  if (d->fle_coeffs) return fail(ctx, RXGS_E_INVALID, "batched rendering does not take FLE radiance");
+  if (d->fle_coeffs || d->fle_base)
+    return fail(ctx, RXGS_E_INVALID, "batched rendering does not take FLE radiance");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SceneState* s = nullptr;
   {

@@ -54,7 +54,9 @@ struct ViewsState {
   float* glob = nullptr;
   const float* key_rx = nullptr;
   const float* key_radiance = nullptr;
-  const float* key_fle = nullptr;
+  const float* key_fle = nullptr;   // fle_coeffs, or fle_base with the FiLM below
+  const float* key_film = nullptr;
+  int key_film_dims[3] = {0, 0, 0};
   int key_lmax = -1;
   int key_N = 0, key_stride = 0;
   uint64_t key_gen = ~0ull;

@@ -154,10 +154,39 @@ void launch_occ_probes(const float4* geom, int K, const float* rx, int N, int re
 
 // ------------------------------------------ FLE directional radiance (App. E.2)
 // rad[v][k][stride] columns 2j, 2j+1 (v < M, rad_view floats per view) from
-// coefficients [N][K][2][(lmax+1)^2] and the transmitters tx[M][3].
+// coefficients [N][K][2][(lmax+1)^2] and the transmitters tx[M][3].  With
+// base != NULL the coefficients are not read: receiver j's coefficient l of
+// Gaussian k is (1 + a_jl) base_kl + b_jl (complex, Eq. film_apply), base
+// [K][2][L] and ab[N][L] = (a.re, a.im, b.re, b.im).
 void launch_fle_radiance(const float* coeffs, int N, int K, int lmax, const float4* geom,
                          const float* tx, int M, int stride, size_t rad_view, float* rad,
-                         cudaStream_t s);
+                         cudaStream_t s, const float* base = nullptr,
+                         const float4* ab = nullptr);
+// The backward of the FiLM form above: grad_base[K][2][L] += sum_j conj(1 + a_jl) G_jkl
+// (grad_base may be NULL) and d_ab[N][L] += (conj(base_kl) G_jkl, G_jkl) summed
+// over k with float atomics, where G_jkl = sum_v d_rad[v][k][2j..] conj(Y_v,k,l).
+void launch_film_fle_backward(const float* d_rad, int N, int K, int lmax, const float4* geom,
+                              const float* tx, int M, int stride, size_t rad_view,
+                              const float* base, const float4* ab, float* grad_base,
+                              float* d_ab, cudaStream_t s);
+
+// ------------------------------------------ global FiLM MLP over FLE components
+// Packed parameters (float32): omega[nw][3], embed[L][dc], w1[D][din], b1[D],
+// w2[D][D], b2[D], w3[4][D], b3[4] with din = 2 nw + 2 + dc (Eq. rx_enc, film).
+struct FilmDims {
+  int nw, dc, D, lmax, L, din;
+  size_t o_omega, o_embed, o_w1, o_b1, o_w2, o_b2, o_w3, o_b3, total;
+};
+constexpr int kFilmMaxFreq = 32, kFilmMaxEmbed = 64, kFilmMaxHidden = 256;
+FilmDims film_dims(int nw, int dc, int D, int lmax);
+// ab[N][L] = MLP_global([gamma(r_j); c_l; e_l]) for every receiver and component.
+void launch_film_global(const float* film, const FilmDims& f, const float* rx, int N, float4* ab,
+                        cudaStream_t s);
+// grad_film (packed as above) += the gradient of sum(d_ab * ab) over every
+// parameter; tmp holds film_backward_tmp_floats(f, N) floats.
+size_t film_backward_tmp_floats(const FilmDims& f, int N);
+void launch_film_backward(const float* film, const FilmDims& f, const float* rx, int N,
+                          const float4* d_ab, float* tmp, float* grad_film, cudaStream_t s);
 // grad[N][K][2][L] += sum_v d_rad[v][k][2j..] conj(Y_v,k)
 void launch_fle_backward(const float* d_rad, int N, int K, int lmax, const float4* geom,
                          const float* tx, int M, int stride, size_t rad_view, float* grad,

@@ -44,7 +44,10 @@ class SceneDesc(ctypes.Structure):
 
 class RenderDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("radiance", ctypes.c_void_p), ("reduce_path", ctypes.c_int),
-                ("fle_coeffs", ctypes.c_void_p), ("fle_lmax", ctypes.c_int)]
+                ("fle_coeffs", ctypes.c_void_p), ("fle_lmax", ctypes.c_int),
+                ("fle_base", ctypes.c_void_p), ("film", ctypes.c_void_p),
+                ("film_nfreq", ctypes.c_int), ("film_embed", ctypes.c_int),
+                ("film_hidden", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):
@@ -66,7 +69,8 @@ class Cotangents(ctypes.Structure):
 class Grads(ctypes.Structure):
     _fields_ = [("grad_radiance", ctypes.c_void_p), ("grad_opacity", ctypes.c_void_p),
                 ("grad_base", ctypes.c_void_p), ("grad_mlp", ctypes.c_void_p),
-                ("grad_fle", ctypes.c_void_p)]
+                ("grad_fle", ctypes.c_void_p), ("grad_fle_base", ctypes.c_void_p),
+                ("grad_film", ctypes.c_void_p)]
 
 
 P = ctypes.c_void_p
@@ -104,7 +108,48 @@ SIGNATURES = {
     "rxgs_serve_inject_fault": (I, [P, I]),
     "rxgs_serve_stop": (I, [P]),
     "rxgs_sync": (I, [P, P]),
+    "rxgs_film_param_count": (ctypes.c_int64, [I, I, I, I]),
+    "rxgs_film_eval": (I, [P, P, I, I, I, I, P, I, P, P]),
 }
+
+# Packed order of the global FiLM parameters (rxgs_film_eval).
+FILM_FIELDS = ("omega", "embed", "w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def film_shapes(nfreq: int, embed: int, hidden: int, lmax: int) -> dict:
+    L = (lmax + 1) ** 2
+    din = 2 * nfreq + 2 + embed
+    return {"omega": (nfreq, 3), "embed": (L, embed), "w1": (hidden, din), "b1": (hidden,),
+            "w2": (hidden, hidden), "b2": (hidden,), "w3": (4, hidden), "b3": (4,)}
+
+
+def film_sizes(params: dict):
+    """(nfreq, embed, hidden) of a FiLM parameter dict."""
+    return (int(params["omega"].shape[0]), int(params["embed"].shape[1]),
+            int(params["w1"].shape[0]))
+
+
+def pack_film(params: dict):
+    """Concatenates the FiLM parameters (numpy arrays or tensors) in the
+    packed order, flattened."""
+    parts = [params[k].reshape(-1) for k in FILM_FIELDS]
+    if hasattr(parts[0], "detach"):
+        import torch
+        return torch.cat(parts)
+    import numpy as np
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unpack_film(flat, nfreq: int, embed: int, hidden: int, lmax: int) -> dict:
+    """The inverse of pack_film (views into `flat`)."""
+    out, o = {}, 0
+    for k, shp in film_shapes(nfreq, embed, hidden, lmax).items():
+        n = 1
+        for d in shp:
+            n *= d
+        out[k] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
 
 _lib = None
 _lock = threading.Lock()
@@ -224,17 +269,31 @@ class Context:
     def release_views(self, views, stream=None):
         self._check(self.lib.rxgs_release_views(self.h, U64(views), _stream(stream)))
 
+    @staticmethod
+    def _desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims):
+        nf, ne, nh = film_dims if film_dims is not None else (0, 0, 0)
+        return RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs),
+                          int(fle_lmax), _f32(fle_base), _f32(film), int(nf), int(ne), int(nh))
+
+    def film_eval(self, film, film_dims, lmax, rx, N, ab, stream=None):
+        """ab[N, L, 4] = (a.re, a.im, b.re, b.im) of the global FiLM branch."""
+        nf, ne, nh = film_dims
+        self._check(self.lib.rxgs_film_eval(self.h, _f32(film), int(nf), int(ne), int(nh),
+                                            int(lmax), _f32(rx), int(N), _f32(ab),
+                                            _stream(stream)))
+
     def render_views(self, views, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
                      ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0,
-                     stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs), int(fle_lmax))
+                     fle_base=None, film=None, film_dims=None, stream=None):
+        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims)
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render_views(self.h, U64(views), _f32(rx), int(N),
                                                ctypes.byref(d), ctypes.byref(o), _stream(stream)))
 
     def render(self, scene, tx, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
-               ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0, stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs), int(fle_lmax))
+               ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0,
+               fle_base=None, film=None, film_dims=None, stream=None):
+        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims)
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                          _f32(rx), int(N), ctypes.byref(d), ctypes.byref(o),
@@ -243,11 +302,12 @@ class Context:
     def render_backward(self, views, rx, N, kind, radiance=None, grad_spectra=None,
                         grad_csi=None, grad_rssi=None, fwd_csi=None,
                         grad_radiance=None, grad_opacity=None, grad_base=None, grad_mlp=None,
-                        fle_coeffs=None, fle_lmax=0, grad_fle=None, stream=None):
-        d = RenderDesc(int(kind), _f32(radiance), 0, _f32(fle_coeffs), int(fle_lmax))
+                        fle_coeffs=None, fle_lmax=0, grad_fle=None, fle_base=None, film=None,
+                        film_dims=None, grad_fle_base=None, grad_film=None, stream=None):
+        d = self._desc(kind, radiance, 0, fle_coeffs, fle_lmax, fle_base, film, film_dims)
         c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_csi))
         g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp),
-                  _f32(grad_fle))
+                  _f32(grad_fle), _f32(grad_fle_base), _f32(grad_film))
         self._check(self.lib.rxgs_render_backward(self.h, U64(views), _f32(rx), int(N),
                                                   ctypes.byref(d), ctypes.byref(c),
                                                   ctypes.byref(g), _stream(stream)))

@@ -51,3 +51,25 @@ def test_context_refuses_without_gpu():
     from paper_2605_24290_gb300 import rxgs
     with pytest.raises(RuntimeError):
         rxgs.Context()
+
+
+def test_film_packed_length_matches_the_binding_layout():
+    """rxgs_film_param_count (host only) agrees with pack_film's layout and
+    refuses sizes out of range."""
+    import numpy as np
+    from paper_2605_24290_gb300 import build, rxgs
+    from paper_2605_24290_gb300 import synthetic as S
+    lib = ctypes.CDLL(build.build())
+    lib.rxgs_film_param_count.restype = ctypes.c_int64
+    lib.rxgs_film_param_count.argtypes = [ctypes.c_int] * 4
+    rng = np.random.default_rng(3)
+    for F, dc, D, lmax in [(6, 16, 64, 9), (5, 16, 256, 4), (1, 0, 1, 0)]:
+        p = S.draw_film(rng, lmax, F=F, dc=dc, D=D)
+        flat = rxgs.pack_film(p)
+        assert lib.rxgs_film_param_count(3 * F, dc, D, lmax) == flat.size
+        back = rxgs.unpack_film(flat, 3 * F, dc, D, lmax)
+        for k in rxgs.FILM_FIELDS:
+            np.testing.assert_array_equal(back[k], p[k])
+    for bad in [(0, 16, 64, 9), (33, 16, 64, 9), (18, 65, 64, 9), (18, 16, 257, 9),
+                (18, 16, 64, 10), (18, -1, 64, 2)]:
+        assert lib.rxgs_film_param_count(*bad) == 0
