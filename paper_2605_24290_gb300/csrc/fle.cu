@@ -12,7 +12,11 @@
 // products, [views x L] x [L x receivers] and [receivers x views] x
 // [views x L], so a block takes one Gaussian and stages its basis for 32
 // views and its coefficients (or gradients) for 64 receivers in shared
-// memory; the coefficient tensor is read once for all views.
+// memory; the coefficient tensor is read once for all views.  With the global
+// FiLM branch (Eq. film_apply) the coefficients are formed from the base
+// coefficients and the per-(receiver, component) modulation while staged,
+// and the backward folds the coefficient gradient into the base and
+// modulation gradients without storing it.
 #include <algorithm>
 #include <cmath>
 
