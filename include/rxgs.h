@@ -324,14 +324,18 @@ rxgs_status rxgs_serve_stop(rxgs_ctx* ctx);
  * Nothing else of the forward is needed: each tile re-walks its list with
  * the forward's decisions, then sweeps it back to front.  `views`, `rx` and
  * `desc->radiance` must be those of the forward.  The radiance the last
- * rxgs_render_views computed on `views` is reused when rx, N, radiance and
- * the scene (rxgs_update_scene) are unchanged; otherwise it is recomputed.
+ * rxgs_render_views computed on `views` is reused when rx, N, radiance (or
+ * fle_coeffs, or fle_base with film and its sizes) and the scene
+ * (rxgs_update_scene) are unchanged, compared by pointer; otherwise it is
+ * recomputed.
  * Gradients are accumulated with float atomics (their rounding order is not
  * fixed).
  * Outputs (accumulated: caller zero-fills):
  *   grad_radiance [N,K,C,2]  when desc->radiance != NULL
  *   grad_opacity  [K]
  *   grad_base     [K,C,2] and grad_mlp (flat) when the scene MLP is used
+ *   grad_fle      [N,K,2,L] when desc->fle_coeffs != NULL
+ *   grad_fle_base [K,2,L] and grad_film (packed) when desc->fle_base != NULL
  * Geometry (means, scales, rotations) is frozen and gets no gradient. */
 typedef struct {
   const float* grad_spectra;
