@@ -6,7 +6,10 @@ imports, links or executes anything in `oracle/`.
 
 The render itself lives in `rxgs_oracle.c` (plain C, float64 values with a
 float32 decision shadow); this module compiles it with gcc, loads it with
-ctypes and adds the float64 conditioning MLP (Sec. 3.3.2) in numpy.
+ctypes and adds, in float64 numpy, the conditioning MLP (Sec. 3.3.2), the
+FLE directional basis (App. E.2), the occupancy grid and its probes
+(App. E.5) and the global FiLM branch over FLE components (Eq. rx_enc, film,
+film_apply), each with its backward where the path has one.
 """
 from __future__ import annotations
 
