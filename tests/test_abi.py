@@ -73,3 +73,20 @@ def test_film_packed_length_matches_the_binding_layout():
     for bad in [(0, 16, 64, 9), (33, 16, 64, 9), (18, 65, 64, 9), (18, 16, 257, 9),
                 (18, 16, 64, 10), (18, -1, 64, 2)]:
         assert lib.rxgs_film_param_count(*bad) == 0
+
+
+def test_film_packing_round_trip_with_torch():
+    """pack_film / unpack_film keep every field, for numpy and torch."""
+    torch = pytest.importorskip("torch")
+    from paper_2605_24290_gb300 import rxgs
+    import numpy as np
+    from paper_2605_24290_gb300 import synthetic as S
+    rng = np.random.default_rng(43)
+    p = S.draw_film(rng, 3, F=2, dc=4, D=8)
+    flat_np = rxgs.pack_film(p)
+    flat_t = rxgs.pack_film({k: torch.from_numpy(v) for k, v in p.items()})
+    assert isinstance(flat_t, torch.Tensor)
+    np.testing.assert_array_equal(flat_t.numpy(), flat_np)
+    back = rxgs.unpack_film(flat_t, *rxgs.film_sizes(p), 3)
+    for k in rxgs.FILM_FIELDS:
+        np.testing.assert_array_equal(back[k].numpy(), p[k])

@@ -796,3 +796,24 @@ def test_film_backward_matches_finite_differences(oracle):
             src[idx] = keep
             ref[idx] = (lp - lm) / (2 * h)
         np.testing.assert_allclose(got[name], ref, rtol=1e-6, atol=1e-7, err_msg=name)
+
+
+def test_film_degree_zero_radiance_closed_form(oracle):
+    """lmax = 0: one component, Y_00 = 1/sqrt(4 pi) in every direction, so the
+    conditioned radiance is ((1 + a) phi + b) / sqrt(4 pi) for each receiver."""
+    rng = np.random.default_rng(42)
+    film = {k: v.astype(np.float64) for k, v in S.draw_film(rng, 0, F=2, dc=3, D=6,
+                                                             out_scale=1.0).items()}
+    K, N = 5, 3
+    base = S.draw_fle_base(rng, K, 0).astype(np.float64)
+    r = rng.uniform(-1.0, 1.0, size=(N, 3))
+    means, tx = rng.normal(size=(K, 3)), rng.normal(size=3)
+    s = oracle.fle_radiance(oracle.film_fle_coeffs(film, base, r, 0), means, tx, 0)[:, :, 0]
+    ab = oracle.film_global(film, r, 0)[:, 0]                         # [N, 4]
+    a = (1.0 + ab[:, 0]) + 1j * ab[:, 1]
+    b = ab[:, 2] + 1j * ab[:, 3]
+    phi = base[:, 0, 0] + 1j * base[:, 1, 0]
+    ref = (a[:, None] * phi[None] + b[:, None]) / np.sqrt(4 * np.pi)
+    np.testing.assert_allclose(s[..., 0], ref.real, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(s[..., 1], ref.imag, rtol=1e-13, atol=1e-15)
+
