@@ -123,6 +123,29 @@ def film_shapes(nfreq: int, embed: int, hidden: int, lmax: int) -> dict:
             "w2": (hidden, hidden), "b2": (hidden,), "w3": (4, hidden), "b3": (4,)}
 
 
+def film_param_count(nfreq: int, embed: int, hidden: int, lmax: int) -> int:
+    """Length of the packed FiLM parameters (rxgs_film_param_count)."""
+    n = 0
+    for shp in film_shapes(nfreq, embed, hidden, lmax).values():
+        k = 1
+        for d in shp:
+            k *= d
+        n += k
+    return n
+
+
+def check_film_length(numel: int, nfreq: int, embed: int, hidden: int, lmax: int) -> None:
+    """Raises ValueError when sizes the library accepts (nfreq 1..32, embed
+    0..64, hidden 1..256, lmax 0..9) do not match the packed length; sizes
+    out of range are left to the library, which refuses them."""
+    if not (1 <= nfreq <= 32 and 0 <= embed <= 64 and 1 <= hidden <= 256 and 0 <= lmax <= 9):
+        return
+    need = film_param_count(nfreq, embed, hidden, lmax)
+    if int(numel) != need:
+        raise ValueError(f"film holds {int(numel)} floats; sizes ({nfreq}, {embed}, {hidden}) "
+                         f"and lmax {lmax} need {need}")
+
+
 def film_sizes(params: dict):
     """(nfreq, embed, hidden) of a FiLM parameter dict."""
     return (int(params["omega"].shape[0]), int(params["embed"].shape[1]),
@@ -272,12 +295,18 @@ class Context:
     @staticmethod
     def _desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims):
         nf, ne, nh = film_dims if film_dims is not None else (0, 0, 0)
+        if film is not None and film_dims is not None:
+            check_film_length(film.numel(), int(nf), int(ne), int(nh), int(fle_lmax))
         return RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs),
                           int(fle_lmax), _f32(fle_base), _f32(film), int(nf), int(ne), int(nh))
 
     def film_eval(self, film, film_dims, lmax, rx, N, ab, stream=None):
         """ab[N, L, 4] = (a.re, a.im, b.re, b.im) of the global FiLM branch."""
         nf, ne, nh = film_dims
+        check_film_length(film.numel(), int(nf), int(ne), int(nh), int(lmax))
+        L = (int(lmax) + 1) ** 2
+        if ab.numel() != int(N) * L * 4 or rx.numel() != int(N) * 3:
+            raise ValueError("ab must hold [N, L, 4] and rx [N, 3] floats")
         self._check(self.lib.rxgs_film_eval(self.h, _f32(film), int(nf), int(ne), int(nh),
                                             int(lmax), _f32(rx), int(N), _f32(ab),
                                             _stream(stream)))

@@ -67,6 +67,7 @@ def test_film_packed_length_matches_the_binding_layout():
         p = S.draw_film(rng, lmax, F=F, dc=dc, D=D)
         flat = rxgs.pack_film(p)
         assert lib.rxgs_film_param_count(3 * F, dc, D, lmax) == flat.size
+        assert rxgs.film_param_count(3 * F, dc, D, lmax) == flat.size
         back = rxgs.unpack_film(flat, 3 * F, dc, D, lmax)
         for k in rxgs.FILM_FIELDS:
             np.testing.assert_array_equal(back[k], p[k])
@@ -90,3 +91,13 @@ def test_film_packing_round_trip_with_torch():
     back = rxgs.unpack_film(flat_t, *rxgs.film_sizes(p), 3)
     for k in rxgs.FILM_FIELDS:
         np.testing.assert_array_equal(back[k].numpy(), p[k])
+
+
+def test_film_length_check_leaves_out_of_range_sizes_to_the_library():
+    from paper_2605_24290_gb300 import rxgs
+    n = rxgs.film_param_count(18, 16, 64, 9)
+    rxgs.check_film_length(n, 18, 16, 64, 9)
+    with pytest.raises(ValueError):
+        rxgs.check_film_length(n - 1, 18, 16, 64, 9)
+    rxgs.check_film_length(n, 18, 16, 300, 9)     # the library refuses hidden = 300
+    rxgs.check_film_length(n, 18, 16, 64, 10)     # and lmax = 10
