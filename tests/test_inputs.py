@@ -24,3 +24,17 @@ def test_hashed_radiance_numpy_equals_torch():
     np.testing.assert_array_equal(a, b[rows].numpy())
     assert a.min() >= -1.0 and a.max() < 1.0
     assert abs(float(a.mean())) < 0.05
+
+
+def test_film_frequencies_start_at_powers_of_two():
+    """The receiver encoding's frequencies start at 2^f along each axis
+    (App. E.4), F bands per axis."""
+    import numpy as np
+    from paper_2605_24290_gb300 import synthetic as S
+    w = S.film_frequencies(6)
+    assert w.shape == (18, 3) and w.dtype == np.float32
+    for d in range(3):
+        for f in range(6):
+            row = np.zeros(3, np.float32)
+            row[d] = 2.0 ** f
+            np.testing.assert_array_equal(w[d * 6 + f], row)
