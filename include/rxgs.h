@@ -13,6 +13,9 @@
  *   Transmitter side   projection, tiles, depth sort       (Algorithm 1, Stage 1)
  *   Receiver side      per-receiver radiance s_k^(j)       (Algorithm 1, Stage 2;
  *                      Sec. 3.3.2, Eq. film, local, combined_local)
+ *                      or Fourier-Legendre coefficients,   (App. E.2)
+ *                      explicit or conditioned by the      (Eq. rx_enc, film,
+ *                      global FiLM branch                   film_apply; App. E.4)
  *   Compositing        w = tau exp(-q/2), C += T w s,
  *                      T *= (1 - w), stop when T < eps     (Algorithm 1, Stage 3)
  *   Amplitude          |R| = sqrt(Re^2 + Im^2 + 1e-8)      (App. E.2)
