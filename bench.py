@@ -52,9 +52,9 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
-# from the committed ncu capture (profiles/render_kernels_*_full.md), valid
-# only while the kernel sources hash to the value recorded at capture time.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch,
+# measured by one ncu capture of that kernel on this workload; valid only
+# while the kernel sources hash to the value recorded at capture time.
 NCU_TRAFFIC = {
     "render_fwd": {"bytes": 27_203_328 + 475_968_256, "tile": [16, 16], "cols": 128,
                    "files": ['render_fwd.cu', 'render_tile.cuh', 'render_common.cuh', 'rxgs_math.cuh'],
@@ -77,9 +77,9 @@ def ncu_traffic(kernel, tile, cols):
     return e["bytes"] if m.hexdigest()[:16] == e["sha1"] else None
 
 
-def fp32_alu_peak_tflops(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_alu_peak_tflops(sm_mhz, sms):
+    """SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ----------------------------------------------------------------- clocks
@@ -212,6 +212,15 @@ class Workload:
         return int(ncon.sum().item())
 
 
+def bench_config(world):
+    """The workload of one step, shared by both arms of the benchmark."""
+    return {"workload": WORKLOAD, "gaussians": 100_000, "transmitters": 32, "receivers": 64,
+            "grid": [90, 360], "spectra_per_step": 32 * 64,
+            "step": "prepare + MLP + forward (spectra, CSI, RSSI) + backward",
+            "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": f"replicas x{world}"}
+
+
 def l2_flush(torch, buf):
     buf.add_(1.0)
 
@@ -278,7 +287,8 @@ def gpu_bench(args):
     P = W.composited_pairs()
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak = fp32_alu_peak_tflops(sm_mhz)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_alu_peak_tflops(sm_mhz, sms)
     tile = tune["chosen"]["tile"] if tune else [16, 16]
     # column block of the forward (the backward always takes 128 for 128 columns)
     cols = tune["chosen"]["cols"] if tune else (128 if 2 * W.N * W.C > 64 else 64)
@@ -290,7 +300,7 @@ def gpu_bench(args):
         ach = P * flops_per_pair / (kms / 1e3) / 1e12
         return {"kernel": kernel, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(kernel, tile, cols if kernel == "render_fwd" else 128),
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
                 "units": f"{P} composited (pixel, Gaussian) pairs x {what} flops",
                 "launch_ms": round(kms, 4)}
 
@@ -358,8 +368,10 @@ def gpu_bench(args):
         o_base = torch.empty((W.K, W.C, 2)).pin_memory()
         o_mlp = torch.empty(W.nmlp).pin_memory()
         o_rssi = torch.empty((W.M, W.N)).pin_memory()
+        o_spec = torch.empty(W.spec.shape).pin_memory()
         h2d = h_tx.numel() * 4 + h_rx.numel() * 4 + h_g.numel() * 4
-        d2h = (o_tau.numel() + o_base.numel() + o_mlp.numel() + o_rssi.numel()) * 4
+        d2h = (o_tau.numel() + o_base.numel() + o_mlp.numel() + o_rssi.numel() +
+               o_spec.numel()) * 4
 
         # the cotangent (531 MB) is only needed by the backward: its copy runs
         # on a side stream, overlapped with prepare + forward
@@ -372,8 +384,21 @@ def gpu_bench(args):
                 d_g.copy_(h_g, non_blocking=True)
                 g_ready = torch.cuda.Event()
                 g_ready.record(copy_stream)
-            W.step(d_tx, d_rx, d_g,
-                   before_backward=lambda: torch.cuda.current_stream().wait_event(g_ready))
+            # the spectra (531 MB) go back to the host on the side stream while
+            # the backward runs
+            def before_backward():
+                cur = torch.cuda.current_stream()
+                cur.wait_event(g_ready)
+                f_done = torch.cuda.Event()
+                f_done.record(cur)
+                copy_stream.wait_event(f_done)
+                with torch.cuda.stream(copy_stream):
+                    o_spec.copy_(W.spec, non_blocking=True)
+                    s_done.record(copy_stream)
+
+            s_done = torch.cuda.Event()
+            W.step(d_tx, d_rx, d_g, before_backward=before_backward)
+            torch.cuda.current_stream().wait_event(s_done)
             o_tau.copy_(W.d_tau, non_blocking=True)
             o_base.copy_(W.d_base, non_blocking=True)
             o_mlp.copy_(W.d_mlp, non_blocking=True)
@@ -393,7 +418,9 @@ def gpu_bench(args):
                                      dev)
         e2e = {"value": round(e_val, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": round(e_ms, 4)}
+               "ms_per_step": round(e_ms, 4),
+               "copies": "H2D tx, rx and the spectra cotangent; D2H the spectra, RSSI and the "
+                         "opacity, phi_base and MLP gradients (pinned host buffers)"}
 
     serve = None
     if rank == 0 and not args.no_serve:
@@ -424,13 +451,7 @@ def gpu_bench(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; indoor-room scene recipe)",
-            "config": {"workload": WORKLOAD, "gaussians": W.K, "transmitters": W.M,
-                       "receivers": W.N, "grid": [W.g.H, W.g.W],
-                       "spectra_per_step": spectra_per_step,
-                       "tile_autotuned": tune["chosen"] if tune else None,
-                       "step": "prepare + MLP + forward (spectra, CSI, RSSI) + backward",
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(bench_config(world), tile_autotuned=tune["chosen"] if tune else None),
             "wall_s": round(wall, 3),
             "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
             "dominant_stage": dom,
@@ -455,7 +476,7 @@ def gpu_bench(args):
 
 
 # ---------------------------------------------------------------- serving
-def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0, sweep_factors=(0.5, 2.0, 4.0),
+def serve_bench(torch, rxgs, S, seconds=60.0, rate=200.0, warm=3.0, sweep_factors=(0.5, 2.0, 4.0),
                 sweep_seconds=3.0):
     """300,000 resident Gaussians (MLP radiance), Poisson requests at `rate`
     per second, each 1 transmitter and n = floor(exp(U(0, ln 1025))) receivers,
@@ -527,7 +548,7 @@ def serve_bench(torch, rxgs, S, seconds=8.0, rate=200.0, warm=3.0, sweep_factors
                       "plans_built": s2["plans_built"]})
     ctx.serve_stop()
     ctx.close()
-    return {"offered_rps": rate, "achieved_rps": round(nreq / wall, 2),
+    return {"seconds": seconds, "offered_rps": rate, "achieved_rps": round(nreq / wall, 2),
             "receivers_per_s": round(nrx / wall, 1), "requests": nreq,
             "p50_ms": st["p50_ms"], "p90_ms": st["p90_ms"], "p99_ms": st["p99_ms"],
             "max_ms": st["max_ms"], "batches": st["batches"],
@@ -567,11 +588,14 @@ def batched_csi_bench(torch, rxgs, S, reps=3):
 
 def coverage_bench(torch, rxgs, S, reps=3):
     """Coverage map: 1,000,000 Gaussians, 16 transmitters x 1,024 receivers,
-    180x360 grid, explicit radiance [1024, 1M, 1, 2] (8.2 GB, resident):
-    RSSI through the visibility path, then the backward from an RSSI
-    cotangent to radiance and opacity (the radiance gradient is another
-    8.2 GB).  Views are prepared once; forward and backward are timed
-    separately with CUDA events."""
+    180x360 grid, explicit radiance [1024, 1M, 1, 2] (8.2 GB, resident).
+    One step = the transmitter-side preparation of the 16 views (projection,
+    key emission, radix sort, tile ranges), RSSI through the visibility path,
+    and the backward from an RSSI cotangent to radiance and opacity (the
+    radiance gradient is another 8.2 GB), timed as a whole with CUDA events.
+    Roofline: HBM, for the weighted sum (the radiance read once for all 16
+    views) and the visibility backward (the radiance read once more, the
+    gradient read and written once)."""
     w = S.workload_coverage(with_radiance=False)
     g, sc = w["grid"], w["scene"]
     M, N, K = w["tx"].shape[0], w["rx"].shape[0], sc.K
@@ -579,7 +603,7 @@ def coverage_bench(torch, rxgs, S, reps=3):
     ctx = rxgs.Context(H=g.H, W=g.W, theta0_deg=g.theta0_deg)
     h = ctx.upload_scene(d(sc.means), d(sc.log_scales), d(sc.quats), d(sc.opacity), None, None, C=1)
     rad = S.hashed_radiance_torch(torch, N, K, "cuda")
-    views = ctx.prepare(h, d(w["tx"]))
+    txd = d(w["tx"])
     rssi = torch.empty((M, N), device="cuda")
     csi = torch.empty((M, N, 1, 2), device="cuda")
     gen = torch.Generator(device="cuda")
@@ -588,33 +612,50 @@ def coverage_bench(torch, rxgs, S, reps=3):
     d_rad = torch.zeros((N, K, 1, 2), device="cuda")
     d_tau = torch.zeros(K, device="cuda")
 
-    def fwd():
+    def step():
+        views = ctx.prepare(h, txd)
         ctx.render_views(views, None, N, rxgs.OUT_RSSI | rxgs.OUT_CSI, radiance=rad, rssi=rssi,
                          csi=csi, reduce_path=1)
-
-    def bwd():
         ctx.render_backward(views, None, N, rxgs.OUT_RSSI, radiance=rad, grad_rssi=grssi,
                             fwd_csi=csi, grad_radiance=d_rad, grad_opacity=d_tau)
+        ctx.release_views(views)
 
-    fwd()
-    bwd()
+    for _ in range(2):
+        step()
     ctx.sync()
-    out = {}
-    for name, fn in (("fwd", fwd), ("bwd", bwd)):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            fn()
-        b.record()
-        ctx.sync()
-        out[name] = a.elapsed_time(b) / reps
-    ctx.release_views(views)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    a.record()
+    for _ in range(reps):
+        step()
+    b.record()
+    ctx.sync()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
     ctx.close()
-    return {"pairs": M * N, "forward_ms": round(out["fwd"], 3), "backward_ms": round(out["bwd"], 3),
-            "rssi_per_s": round(M * N / (out["fwd"] / 1e3), 1),
-            "note": "views prepared once outside the timed calls",
-            "workload": "1M Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance [1024,1M,1,2], "
-                        "RSSI (visibility path) + RSSI backward to radiance and opacity"}
+    ms = a.elapsed_time(b) / reps
+    stages = {k: round(v["ms"] / reps, 3) for k, v in prof["stages"].items()}
+    pk, src = peaks()
+    rad_bytes = 8.0 * N * K
+
+    def hbm(stage, nbytes, what):
+        if stage not in prof["stages"]:
+            return None
+        kms = prof["stages"][stage]["ms"] / prof["stages"][stage]["calls"]
+        ach = nbytes / (kms / 1e3) / 1e9
+        return {"kernel": stage, "bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / pk["hbm_gbs"], 4), "launch_ms": round(kms, 4),
+                "units": what, "peak_source": f"hbm_gbs ({src})"}
+
+    return {"pairs": M * N, "ms_per_step": round(ms, 3), "rssi_per_s": round(M * N / (ms / 1e3), 1),
+            "stages_ms_per_step": stages,
+            "roofline": [hbm("weighted_sum", rad_bytes, "radiance [1024, 1M, 1, 2] read once"),
+                         hbm("vis_bwd", 3 * rad_bytes,
+                             "radiance read once, radiance gradient read and written once")],
+            "step": "prepare (16 views) + RSSI forward (visibility path) + RSSI backward to "
+                    "radiance and opacity",
+            "workload": "1M Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance [1024,1M,1,2]"}
 
 
 def fle_bench(torch, rxgs, S, reps=3, lmax=9):
@@ -813,7 +854,7 @@ def reference_bench(args):
             "ms_per_step": round(1e3 * sum(r["seconds"] for r in vals) / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded; indoor-room scene recipe)",
-            "config": {"workload": WORKLOAD, "step": vals[0]["sample"]},
+            "config": bench_config(world),
             "impl": "reference",
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": vals[0]["cores"],
                              "kind": "oracle", "sample": vals[0]["sample"]},
@@ -841,7 +882,7 @@ def main():
     ap.add_argument("--no-fle", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-occupancy", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -381,10 +381,14 @@ rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uin
  * mlp / radiance_transpose, render_fwd, reduce, render_bwd, mlp_bwd,
  * radiance_grad).  rxgs_profile_read waits for the recorded events, folds
  * them into per-stage totals and writes
- *   {"kernel_launches": L, "stages": {"<stage>": {"ms": t, "calls": n}, ...}}
+ *   {"kernel_launches": L, "device_allocs": A, "pool_used_bytes": U,
+ *    "pool_reserved_bytes": R, "stages": {"<stage>": {"ms": t, "calls": n}, ...}}
  * into json[cap] (RXGS_E_INVALID if cap is too small); reset = 1 clears the
  * totals afterwards.  kernel_launches counts every kernel the library has
- * launched in this process. */
+ * launched in this process, device_allocs every stream-ordered device
+ * allocation it has made; U and R are the current used and reserved bytes
+ * of the context device's default memory pool, which those allocations
+ * draw on. */
 rxgs_status rxgs_profile(rxgs_ctx* ctx, int enable);
 rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset);
 
@@ -396,13 +400,19 @@ rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset);
  * values as rxgs_render_views with RXGS_OUT_CSI / RXGS_OUT_RSSI.
  *   csi[M,N,C,2] and/or rssi[M,N]   outputs (device, caller-owned)
  * The per-tile partial sums live in a fixed 16 MiB device array inside the
- * library (every GPU that loads the library keeps it until the process
- * exits), so M * tiles * 2 * N * C must not exceed 4,194,304; larger
- * requests return RXGS_E_INVALID and print the limit.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call reuses the same
- * array: calls whose work overlaps on the GPU race and must be serialised
- * by the caller (one stream, or events). */
+ * library.  rxgs_create looks up its device address on the context's device
+ * (cudaGetSymbolAddress), which also brings the array into existence there:
+ * from the first rxgs_create on a GPU the array occupies 16 MiB of it until
+ * the process exits; the calls themselves allocate nothing.
+ * M * tiles * 2 * N * C must not exceed 4,194,304, and 2 * N * C / 64 column
+ * blocks must fit the launch grid (65,535); larger requests return
+ * RXGS_E_INVALID, with the reason in rxgs_last_error, before any launch.
+ * The call makes the context's device current for its launches and restores
+ * the caller's current device before it returns.  Every call reuses the same
+ * array and the last call's contents stay in it (each call writes every
+ * entry it reads, so nothing needs clearing): calls whose work overlaps on
+ * the GPU race and must be serialised by the caller (one stream, or
+ * events). */
 rxgs_status rxgs_render_csi_noalloc(rxgs_ctx* ctx, rxgs_views_t views, const float* radiance,
                                     int N, float* csi, float* rssi, void* stream);
 

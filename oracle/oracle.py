@@ -453,6 +453,168 @@ def mlp_backward(params, rx, means, base, grad_s, occ=None):
     return out
 
 
+def _cmul_abs(A, B):
+    """Bounds of |Re|, |Im| of a * b from bounds A, B of those of a and b."""
+    return np.stack([A[..., 0] * B[..., 0] + A[..., 1] * B[..., 1],
+                     A[..., 0] * B[..., 1] + A[..., 1] * B[..., 0]], axis=-1)
+
+
+def mlp_backward_chain(params, rx, means, base, abs_grad_s, occ=None, amb=1e-5):
+    """Error scales of `mlp_backward`: the same steps with every factor
+    replaced by a bound of its absolute value (the absolute chain), so each
+    returned entry bounds the sum of the absolute values of the terms that
+    make up that gradient entry.  `abs_grad_s` [N,K,C,2] bounds the incoming
+    gradient's terms.  ReLU units follow the forward's own activity.
+
+    A unit whose pre-activation lies within `amb` of zero, relative to its
+    own chain, is a decision float32 cannot settle: the GPU may take it either
+    way, which adds or removes its whole term d_h * x in the first layer's
+    gradients.  Such units count as active in the chain, and their first-layer
+    terms are also returned apart, as the second dict, so that a comparison
+    can admit both outcomes.  Returns (chain, ambiguous), keyed like
+    `mlp_backward`."""
+    P = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    A = {k: np.abs(v) for k, v in P.items()}
+    base = np.asarray(base, np.float64)
+    G = np.abs(np.asarray(abs_grad_s, np.float64))
+    N, K, C = G.shape[0], G.shape[1], G.shape[2]
+    xg = np.asarray(rx, np.float64)
+    xl = local_features(rx, means, occ)
+
+    def layer(x, w1, b1, w2, b2, aw1, ab1, aw2, ab2):
+        pre = x @ w1.T + b1
+        cpre = np.abs(x) @ aw1.T + ab1
+        amb_u = np.abs(pre) <= amb * cpre
+        act = (pre > 0) | amb_u
+        ch = cpre * act
+        return ch @ aw2.T + ab2, ch, act, amb_u
+
+    cog, chg, actg, ambg = layer(xg, P["g_w1"], P["g_b1"], P["g_w2"], P["g_b2"],
+                                 A["g_w1"], A["g_b1"], A["g_w2"], A["g_b2"])
+    col, chl, actl, ambl = layer(xl, P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"],
+                                 A["l_w1"], A["l_b1"], A["l_w2"], A["l_b2"])
+    cog4 = cog.reshape(N, 1, C, 4)
+    col4 = col.reshape(N, K, C, 4)
+    one = np.array([1.0, 0.0])
+    AG = one + cog4[..., 0:2]
+    AL = one + col4[..., 0:2]
+    B = np.abs(base)[None]
+    U = _cmul_abs(AG, B) + cog4[..., 2:4]
+    D_al = _cmul_abs(G, U)
+    D_u = _cmul_abs(G, AL)
+    D_ag = _cmul_abs(D_u, np.broadcast_to(B, D_u.shape)).sum(axis=1)
+    D_bg = D_u.sum(axis=1)
+    out = {"base": _cmul_abs(D_u, np.broadcast_to(AG, D_u.shape)).sum(axis=0)}
+    D_ol = np.concatenate([D_al, G], axis=-1).reshape(N, K, 4 * C)
+    D_og = np.concatenate([D_ag, D_bg], axis=-1).reshape(N, 4 * C)
+    amb_out = {k: np.zeros_like(v) for k, v in P.items()}
+    amb_out["base"] = np.zeros_like(base)
+    out["l_w2"] = np.einsum("nko,nkh->oh", D_ol, chl)
+    out["l_b2"] = D_ol.sum(axis=(0, 1))
+    D_hl = D_ol @ A["l_w2"]
+    out["l_w1"] = np.einsum("nkh,nki->hi", D_hl * actl, np.abs(xl))
+    out["l_b1"] = (D_hl * actl).sum(axis=(0, 1))
+    amb_out["l_w1"] = np.einsum("nkh,nki->hi", D_hl * ambl, np.abs(xl))
+    amb_out["l_b1"] = (D_hl * ambl).sum(axis=(0, 1))
+    out["g_w2"] = D_og.T @ chg
+    out["g_b2"] = D_og.sum(axis=0)
+    D_hg = D_og @ A["g_w2"]
+    out["g_w1"] = (D_hg * actg).T @ np.abs(xg)
+    out["g_b1"] = (D_hg * actg).sum(axis=0)
+    amb_out["g_w1"] = (D_hg * ambg).T @ np.abs(xg)
+    amb_out["g_b1"] = (D_hg * ambg).sum(axis=0)
+    return out, amb_out
+
+
+# ----------------------------- Stage II step (Sec. 3.1; App. E.3, App. E.5)
+# Geometry is frozen; phi_base and the conditioning MLP are trained against
+# the L1 term of the loss (App. E.3) on the amplitude |R| (App. E.2) or on
+# RSSI, each parameter group with its own Adam optimiser (App. E.5).  The
+# SSIM and FFT terms of App. E.3 are not part of the path.
+
+def l1_amplitude(spec, target):
+    """L = mean over elements of | |R| - y | with |R| = sqrt(Re^2 + Im^2 +
+    1e-8), spec [..., 2], target [...].  Returns (L, dL/dspec): the
+    derivative of |R| is R / |R|, so dL/dspec = sign(|R| - y) / n * R / |R|."""
+    spec = np.asarray(spec, np.float64)
+    amp = amplitude(spec)
+    diff = amp - np.asarray(target, np.float64)
+    n = diff.size
+    return float(np.abs(diff).mean()), (np.sign(diff) / n)[..., None] * spec / amp[..., None]
+
+
+def l1_rssi(csi1, target):
+    """L = mean | RSSI - y | with RSSI = |CSI| of a single channel, csi1
+    [..., 2], target [...]; returns (L, dL/dcsi1) = sign(RSSI - y) / n *
+    CSI / RSSI (zero where RSSI = 0)."""
+    c = np.asarray(csi1, np.float64)
+    r = np.sqrt(c[..., 0] ** 2 + c[..., 1] ** 2)
+    diff = r - np.asarray(target, np.float64)
+    n = diff.size
+    safe = np.where(r > 0, r, 1.0)
+    return float(np.abs(diff).mean()), ((np.sign(diff) / n) * (r > 0) / safe)[..., None] * c
+
+
+def adam(p, g, m, v, t, lr, betas=(0.9, 0.999), eps=1e-8):
+    """One update of Adam (Kingma & Ba, Algorithm 1), the optimiser App. E.5
+    names, with PyTorch's default hyperparameters and no weight decay.  t is
+    the 1-based step count.  Returns (p, m, v):
+        m <- b1 m + (1 - b1) g,   v <- b2 v + (1 - b2) g^2,
+        p <- p - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)."""
+    b1, b2 = betas
+    p, g, m, v = (np.asarray(x, np.float64) for x in (p, g, m, v))
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def stage2_step(grid, scene, tx, rx, base, params, target, state=None, lr_base=5e-3,
+                lr_mlp=1e-3, kind="spectra"):
+    """One Stage II iteration: the receiver-conditioned radiance of every
+    (receiver, Gaussian) pair (MLP), every transmitter's view rendered
+    (brute force), the L1 loss against `target` (amplitude spectra
+    [M,N,H,W,C] for kind "spectra", RSSI [M,N] for kind "rssi"), its
+    gradient through the render backward (summed over views) and the MLP
+    backward, then one Adam update of phi_base and one of the MLP parameters
+    with separate optimiser states (App. E.5).
+
+    `state` (None at the first step) is {"t": steps taken, name: (m, v)}.
+    Returns dict(loss, grad_base, grad_mlp, base, params, state, spectra)."""
+    M = tx.shape[0]
+    rad = mlp_radiance(params, rx, scene.means, base)
+    spec = np.stack([render_view(grid, scene, tx[v], rad, want_abs=False)["spectra"]
+                     for v in range(M)])                                  # [M,N,H,W,C,2]
+    if kind == "spectra":
+        loss, gspec = l1_amplitude(spec, target)
+    elif kind == "rssi":
+        loss, gcsi = l1_rssi(csi(spec.reshape((-1,) + spec.shape[2:]))[:, 0].reshape(M, -1, 2),
+                             target)
+        gspec = np.broadcast_to(gcsi[:, :, None, None, None, :], spec.shape)
+    else:
+        raise ValueError(kind)
+    grad_rad = None
+    for v in range(M):
+        gr, _ = backward_view(grid, scene, tx[v], rad, gspec[v])
+        grad_rad = gr if grad_rad is None else grad_rad + gr
+    grads = mlp_backward(params, rx, scene.means, base, grad_rad)
+    st = {"t": 0} if state is None else dict(state)
+    t = st["t"] + 1
+    new_base, *mv = adam(base, grads["base"],
+                         *st.get("base", (np.zeros_like(grads["base"]),) * 2), t, lr_base)
+    st["base"] = tuple(mv)
+    new_params = {}
+    for k in params:
+        new_params[k], *mv = adam(params[k], grads[k],
+                                  *st.get(k, (np.zeros_like(grads[k]),) * 2), t, lr_mlp)
+        st[k] = tuple(mv)
+    st["t"] = t
+    return dict(loss=loss, grad_base=grads["base"],
+                grad_mlp={k: grads[k] for k in params}, base=new_base, params=new_params,
+                state=st, spectra=spec)
+
+
 # --------------------------------- FLE directional radiance (App. E.2, Alg. 1)
 # For the direction from the transmitter to a Gaussian's centre, with polar
 # angle theta (cos theta = u_z / |u|) and azimuth phi = atan2(u_y, u_x):

@@ -23,6 +23,9 @@ namespace rxgs {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+static std::atomic<unsigned long long> g_dallocs{0};
+void note_dalloc() { g_dallocs.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long dalloc_count() { return g_dallocs.load(std::memory_order_relaxed); }
 }  // namespace rxgs
 
 using namespace rxgs;
@@ -191,6 +194,9 @@ rxgs_status rxgs_create(const rxgs_options* opts, int device, rxgs_ctx** out) {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   }
+  // the allocation-free entry point's scratch address on this device (this
+  // also loads the module that holds the array, so it exists from here on)
+  if (e == cudaSuccess) e = noalloc_scratch_address(device, &ctx->noalloc_partial);
   if (e != cudaSuccess) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
@@ -1025,7 +1031,20 @@ rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset) 
     ctx->event_pool.push_back(p.b);
   }
   ctx->pending.clear();
-  std::string out = "{\"kernel_launches\": " + std::to_string(launch_count()) + ", \"stages\": {";
+  // allocation evidence: the library's stream-ordered allocations so far and
+  // the device's default memory pool (which those allocations draw on)
+  size_t used = 0, reserved = 0;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+    uint64_t u = 0, r = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) == cudaSuccess) used = u;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) == cudaSuccess)
+      reserved = r;
+  }
+  std::string out = "{\"kernel_launches\": " + std::to_string(launch_count()) +
+                    ", \"device_allocs\": " + std::to_string(dalloc_count()) +
+                    ", \"pool_used_bytes\": " + std::to_string(used) +
+                    ", \"pool_reserved_bytes\": " + std::to_string(reserved) + ", \"stages\": {";
   bool first = true;
   for (auto& kv : ctx->stage_ms) {
     char buf[160];

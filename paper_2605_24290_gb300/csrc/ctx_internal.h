@@ -93,6 +93,9 @@ struct rxgs_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   std::map<std::string, std::pair<double, long>> stage_ms;
+  // device address of the allocation-free entry point's fixed scratch array
+  // on `device` (noalloc.cu), taken when the context is created
+  float* noalloc_partial = nullptr;
 };
 
 namespace rxgs {
@@ -115,11 +118,21 @@ inline rxgs_status fail(rxgs_ctx* c, rxgs_status st, const char* fmt, ...) {
                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
   } while (0)
 
+// Number of stream-ordered device allocations the library has made (all
+// render, backward and prepare scratch goes through dalloc).
+void note_dalloc();
+unsigned long long dalloc_count();
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t n, cudaStream_t s) {
   if (n == 0) n = 1;
+  note_dalloc();
   return cudaMallocAsync(reinterpret_cast<void**>(p), n * sizeof(T), s);
 }
+
+// Looks up (once per device, with that device current) the device address
+// of the allocation-free entry point's scratch array (noalloc.cu).
+cudaError_t noalloc_scratch_address(int device, float** out);
 
 template <typename T>
 void dfree(T*& p, cudaStream_t s) {

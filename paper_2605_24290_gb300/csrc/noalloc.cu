@@ -11,15 +11,19 @@
 // variant reads the caller's receiver-major radiance in place and keeps the
 // per-tile partial sums in one fixed, file-scope device array instead.
 //
-// The array holds kNoAllocFloats floats (16 MiB) on every GPU that loads the
-// library, for the life of the process, and is shared by every call: the
-// kernel writes every entry it later reads, so no clearing is needed, but
-// two calls whose work overlaps on the same GPU (for example on two
-// streams) race on it and give wrong results.
+// The array holds kNoAllocFloats floats (16 MiB).  Its device address is
+// looked up when a context is created on a device (rxgs_create calls
+// noalloc_scratch_address with that device current); that lookup also loads
+// the module that holds the array, so from the first rxgs_create on a device
+// the array occupies 16 MiB there until the process exits.  Every call
+// shares it: the kernel writes every entry it later reads, so no clearing is
+// needed, but two calls whose work overlaps on the same GPU (for example on
+// two streams) race on it and give wrong results.
 #include <cstdio>
 #include <mutex>
 
 #include "rxgs.h"
+#include "ctx_internal.h"
 #include "render_common.cuh"
 #include "rxgs_internal.h"
 
@@ -30,29 +34,24 @@ constexpr int kNoAllocCols = 64;                    // output columns per CTA
 
 static __device__ __align__(256) float g_noalloc_partial[kNoAllocFloats];
 
-// Per-device address of g_noalloc_partial, taken once with that device
-// current (a host-side reference to the symbol is not a device address).
-static float* noalloc_scratch(int device, cudaError_t* err) {
+// Device address of g_noalloc_partial on `device`, which must be the current
+// device; looked up once per device (a host-side reference to the symbol is
+// not a device address).
+cudaError_t noalloc_scratch_address(int device, float** out) {
   constexpr int kMaxDevices = 64;
   static float* addr[kMaxDevices] = {};
   static std::mutex mu;
-  if (device < 0 || device >= kMaxDevices) {
-    *err = cudaErrorInvalidDevice;
-    return nullptr;
-  }
+  *out = nullptr;
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   if (!addr[device]) {
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(device);
     void* p = nullptr;
-    *err = cudaGetSymbolAddress(&p, g_noalloc_partial);
-    cudaSetDevice(cur);
-    if (*err != cudaSuccess) return nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess) return e;
     addr[device] = static_cast<float*>(p);
   }
-  *err = cudaSuccess;
-  return addr[device];
+  *out = addr[device];
+  return cudaSuccess;
 }
 
 // Same two-phase compositing as the regular forward kernel (phase A: the
@@ -159,33 +158,62 @@ __global__ void __launch_bounds__(kTilePixels, 2)
 
 using namespace rxgs;
 
+namespace {
+// Makes `device` current for the scope and restores the caller's device.
+struct DeviceScope {
+  int prev = -1;
+  cudaError_t e = cudaSuccess;
+  explicit DeviceScope(int device) {
+    e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
 extern "C" rxgs_status rxgs_render_csi_noalloc(rxgs_ctx* ctx, rxgs_views_t views,
                                                const float* radiance, int N, float* csi,
                                                float* rssi, void* stream) {
-  ViewsRef v{};
-  const char* err = nullptr;
-  if (!radiance || (!csi && !rssi) || N <= 0) return RXGS_E_INVALID;
-  if (!lookup_views(ctx, views, &v, &err)) return RXGS_E_INVALID;
-  if (rssi && v.C != 1) return RXGS_E_INVALID;
-  const size_t need = static_cast<size_t>(v.M) * v.g.T * 2 * static_cast<size_t>(N) * v.C;
-  if (need > kNoAllocFloats) {
-    fprintf(stderr,
-            "rxgs_render_csi_noalloc: %zu partial sums (views x tiles x 2NC) exceed the fixed "
-            "scratch of %zu floats\n",
-            need, kNoAllocFloats);
-    return RXGS_E_INVALID;
-  }
-  cudaError_t e = cudaSetDevice(v.device);
-  if (e != cudaSuccess) return RXGS_E_CUDA;
-  float* partial = noalloc_scratch(v.device, &e);
-  if (!partial) return RXGS_E_CUDA;
+  if (!ctx) return RXGS_E_INVALID;
+  if (!radiance || (!csi && !rssi) || N <= 0)
+    return fail(ctx, RXGS_E_INVALID, "render_csi_noalloc: null radiance, no output, or N <= 0");
+  // the views stay locked from the lookup through both launches, so a
+  // concurrent rxgs_release_views cannot free them in between
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->views.find(views);
+  if (it == ctx->views.end()) return fail(ctx, RXGS_E_INVALID, "render_csi_noalloc: unknown views");
+  const ViewsState* v = it->second;
+  const int C = ctx->scenes.at(v->scene)->C;
+  if (rssi && C != 1)
+    return fail(ctx, RXGS_E_INVALID, "render_csi_noalloc: RSSI needs one channel (C = %d)", C);
+  const GridConst& g = ctx->g;
+  const size_t need = static_cast<size_t>(v->M) * g.T * 2 * static_cast<size_t>(N) * C;
+  if (need > kNoAllocFloats)
+    return fail(ctx, RXGS_E_INVALID,
+                "render_csi_noalloc: %zu partial sums (views x tiles x 2NC) exceed the fixed "
+                "scratch of %zu floats",
+                need, kNoAllocFloats);
+  const size_t ncols = 2 * static_cast<size_t>(N) * C;
+  const size_t blocks_y = (ncols + kNoAllocCols - 1) / kNoAllocCols;
+  if (blocks_y > 65535 || v->M > 65535)
+    return fail(ctx, RXGS_E_INVALID,
+                "render_csi_noalloc: %zu column blocks x %d views exceed the launch grid", blocks_y,
+                v->M);
+  float* partial = ctx->noalloc_partial;
+  if (!partial) return fail(ctx, RXGS_E_CUDA, "render_csi_noalloc: no scratch address");
+  DeviceScope dev(ctx->device);
+  if (dev.e != cudaSuccess)
+    return fail(ctx, RXGS_E_CUDA, "render_csi_noalloc: %s", cudaGetErrorString(dev.e));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int ncols = 2 * N * v.C;
-  dim3 grid(v.g.T, (ncols + kNoAllocCols - 1) / kNoAllocCols, v.M);
-  render_csi_noalloc_kernel<<<grid, kTilePixels, 0, st>>>(v.g, v.rec, v.vals, v.ranges, radiance,
-                                                          v.K, N, v.C, partial);
+  dim3 grid(g.T, static_cast<unsigned>(blocks_y), v->M);
+  render_csi_noalloc_kernel<<<grid, kTilePixels, 0, st>>>(g, v->rec, v->vals, v->ranges, radiance,
+                                                          v->K, N, C, partial);
   note_launches(1);
-  launch_reduce_tiles(partial, v.M, v.g.T, N, v.C, csi, rssi, st);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? RXGS_OK : RXGS_E_CUDA;
+  launch_reduce_tiles(partial, v->M, g.T, N, C, csi, rssi, st);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(ctx, RXGS_E_CUDA, "render_csi_noalloc: %s", cudaGetErrorString(e));
+  return RXGS_OK;
 }

@@ -449,11 +449,8 @@ class Context:
     def render_csi_noalloc(self, views, radiance, N, csi=None, rssi=None, stream=None):
         """CSI / RSSI of prepared views with no device allocation (the
         library's fixed scratch array holds the partial sums)."""
-        st = self.lib.rxgs_render_csi_noalloc(self.h, U64(views), _f32(radiance), int(N), _f32(csi),
-                                              _f32(rssi), _stream(stream))
-        if st != OK:
-            raise RxgsError(st, "rxgs_render_csi_noalloc failed (bad arguments or sizes beyond "
-                                "its fixed scratch)")
+        self._check(self.lib.rxgs_render_csi_noalloc(self.h, U64(views), _f32(radiance), int(N),
+                                                     _f32(csi), _f32(rssi), _stream(stream)))
 
     def sync(self, stream=None):
         self._check(self.lib.rxgs_sync(self.h, _stream(stream)))

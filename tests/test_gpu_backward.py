@@ -173,19 +173,24 @@ def test_backward_through_mlp(torch, rx, oracle, N, C):
     ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
     assert scaled_err(d_tau.cpu().numpy(), ref_t, abs_t) <= TOL
     ref = oracle.mlp_backward(mlp, rxp, sc.means, base, ref_r)
-    # scale: the same chain applied to the absolute radiance-gradient terms;
-    # that chain is not an upper bound of the terms (ReLU on signed inputs,
-    # complex products), so |ref| is added: the check is at least relative
-    absd = {k: np.abs(v) for k, v in oracle.mlp_backward(
-        {k: np.abs(v) for k, v in mlp.items()}, rxp, sc.means, np.abs(base), abs_r).items()}
     got_mlp = S.unflatten_mlp(d_mlp.cpu().numpy(), C)
-    e = scaled_err(d_base.cpu().numpy(), ref["base"],
-                   absd["base"] + np.abs(ref["base"]) + 1e-3 * np.abs(ref["base"]).max())
+    check_mlp_grads(oracle, mlp, rxp, sc.means, base, abs_r, ref, d_base.cpu().numpy(), got_mlp)
+
+
+def check_mlp_grads(oracle, mlp, rxp, means, base, abs_r, ref, got_base, got_mlp, occ=None):
+    """phi_base and MLP gradients against the oracle relative to the MLP
+    backward's absolute chain (the actual ReLU activity, fed by the render
+    backward's absolute radiance-gradient terms).  A hidden unit whose
+    pre-activation float32 cannot place on one side of zero may be taken
+    either way by the GPU: its whole first-layer term is admitted (scaled
+    by 1 / TOL in the error scale).  Returns the number of such units."""
+    chain, amb = oracle.mlp_backward_chain(mlp, rxp, means, base, abs_r, occ=occ)
+    e = scaled_err(got_base, ref["base"], chain["base"])
     assert e <= TOL, f"phi_base gradient {e}"
     for name in mlp:
-        sc_ = absd[name] + np.abs(ref[name]) + 1e-3 * np.abs(ref[name]).max()
-        e = scaled_err(got_mlp[name], ref[name], sc_)
+        e = scaled_err(got_mlp[name], ref[name], chain[name] + amb[name] / TOL)
         assert e <= TOL, f"{name} gradient {e}"
+    return int(sum((v > 0).sum() for v in amb.values()))
 
 
 def test_autograd_function_matches_abi(torch, rx):

@@ -32,15 +32,35 @@ def make_ctx(rx, g, **kw):
                       tile_w=g.tile_w, eps_T=g.eps_T, q_max=g.q_max, r_near=g.r_near, **kw)
 
 
-def check_views(torch, ctx, oracle, g, scene, tx_np, views):
+def check_views(torch, ctx, oracle, g, scene, tx_np, views, which=None):
+    """Records, tile counts, sorted (key, value) lists and tile ranges of the
+    prepared views against the oracle's float32 shadow, bit for bit.  Keys:
+    the whole array ascends; the low 31 bits of each key are the float32
+    bits of the oracle's depth rho of the Gaussian it carries; the high bits
+    are one value per (view, tile) list, increasing from list to list."""
     M, K = tx_np.shape[0], scene.K
     T = ((g.H + g.tile_h - 1) // g.tile_h) * ((g.W + g.tile_w - 1) // g.tile_w)
     rec, counts, keys, vals, ranges = ctx.views_export(views, M, K, T)
     torch.cuda.synchronize()
     rec, counts = rec.cpu().numpy(), counts.cpu().numpy()
     vals, ranges = vals.cpu().numpy(), ranges.cpu().numpy()
+    keys = keys.cpu().numpy().view(np.uint64)
+    assert np.all(keys[1:] >= keys[:-1]), "keys not sorted"
+    hi_prev = -1
     for v in range(M):
+        for t in range(T):
+            s, e = ranges[v, t]
+            if e > s:
+                hi = keys[s:e] >> np.uint64(31)
+                assert np.all(hi == hi[0]) and int(hi[0]) > hi_prev, f"key tile bits, view {v} tile {t}"
+                hi_prev = int(hi[0])
+    for v in (range(M) if which is None else which):
         _, orec, obox = oracle.project_view32(g, scene, tx_np[v])
+        vr = ranges[v]
+        vs, ve = int(vr[:, 0][vr[:, 1] > vr[:, 0]].min(initial=0)), int(vr[:, 1].max(initial=0))
+        kv = keys[vs:ve] & np.uint64(0x7FFFFFFF)
+        np.testing.assert_array_equal(kv.astype(np.uint32), orec[vals[vs:ve], 6].view(np.uint32),
+                                      err_msg=f"depth bits of the keys, view {v}")
         ocnt, olists, ontiles = oracle.tile_lists(g, scene, tx_np[v])
         vis = orec[:, 7] > 0
         np.testing.assert_array_equal(counts[v] > 0, vis)
@@ -111,6 +131,49 @@ def test_small_scene_views_bitexact(torch, rx, oracle):
     views = ctx.prepare(h, dev(tx, torch))
     n = check_views(torch, ctx, oracle, g, sc, tx, views)
     assert n > 10000
+    ctx.release_views(views)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32)])
+@pytest.mark.parametrize("K", [48, 300])
+def test_seam_pole_full_span_scene(torch, rx, oracle, tile, K):
+    """The oracle's seam / pole / full-width-span scene (Gaussians straddling
+    azimuth 0 = 360 deg and near the zenith, whose footprints cover every
+    column) on the 18x36 grid at 10 deg: records, tile sets, sorted lists
+    and ranges bit-exact; spectra, CSI and RSSI against the oracle."""
+    from tests.test_oracle_pins import tiny_scene
+    sc, tx = tiny_scene(60 + K, K=K)
+    g = S.Grid(H=18, W=36, theta0_deg=-10.0, step_deg=10.0, tile_h=tile[0], tile_w=tile[1],
+               eps_T=0.02)
+    ctx = make_ctx(rx, g)
+    h = upload(ctx, sc, torch)
+    txs = np.stack([tx, tx + S.f32([0.3, -0.2, 0.1])])
+    views = ctx.prepare(h, dev(txs, torch))
+    check_views(torch, ctx, oracle, g, sc, txs, views)
+    _, orec, obox = oracle.project_view32(g, sc, txs[0])
+    vis = orec[:, 7] > 0
+    assert ((obox[vis, 3] + 1) >= g.W).any(), "no full-width span in the scene"
+    assert (obox[vis, 2] + obox[vis, 3] >= g.W).any(), "no footprint across the seam"
+    rad = S.draw_radiance(np.random.default_rng(K), 3, sc.K, 1)
+    out = render_all(torch, ctx, h, txs, rad, rx.OUT_SPECTRA | rx.OUT_RSSI | rx.OUT_CSI, views=views)
+    for v in range(2):
+        compare_view(oracle, g, sc, txs[v], rad, *[o[v] for o in out])
+    ctx.release_views(views)
+
+
+def test_full_size_sorted_lists_bitexact(torch, rx, oracle):
+    """The sort at the benchmark's size (100,000 Gaussians, 32 transmitters,
+    millions of instances, so thousands of radix-sort blocks and more than one
+    pass of the block-offset carry loop): keys and values of two views bit
+    for bit against the oracle's depth-sorted tile lists; sortedness and the
+    list structure of the keys over all 32 views."""
+    w = S.workload_mlp()
+    g, sc = w["grid"], w["scene"]
+    ctx = make_ctx(rx, g)
+    h = upload(ctx, sc, torch)
+    views = ctx.prepare(h, dev(w["tx"], torch))
+    n = check_views(torch, ctx, oracle, g, sc, w["tx"], views, which=[0, 31])
+    assert n > 256 * 2048, n              # past 256 sort blocks of 2,048 items
     ctx.release_views(views)
 
 

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2605_24290_gb300 import synthetic as S
+from tests.test_gpu_backward import check_mlp_grads
 from tests.gpu_helpers import TOL, dev, norm_err, upload
 
 pytestmark = pytest.mark.gpu
@@ -69,15 +70,9 @@ def test_occupancy_forward_and_backward_match_oracle(torch, rx, oracle, C):
         ref_r += gr
         abs_r += ar
     ref = oracle.mlp_backward(mlp, rxp, sc.means, base, ref_r, occ=occ)
-    absd = oracle.mlp_backward({k: np.abs(v) for k, v in mlp.items()}, rxp, sc.means,
-                               np.abs(base), abs_r, occ=occ)
     got = S.unflatten_mlp(d_mlp.cpu().numpy(), C)
-    for name in mlp:
-        sc_ = np.abs(absd[name]) + 1e-3 * np.abs(ref[name]).max()
-        e = float((np.abs(got[name] - ref[name]) / sc_).max())
-        assert e <= TOL, (name, e)
-    sc_b = np.abs(absd["base"]) + 1e-3 * np.abs(ref["base"]).max()
-    assert float((np.abs(d_base.cpu().numpy() - ref["base"]) / sc_b).max()) <= TOL
+    check_mlp_grads(oracle, mlp, rxp, sc.means, base, abs_r, ref, d_base.cpu().numpy(), got,
+                    occ=occ)
     ctx.release_views(views)
 
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2605_24290_gb300 import synthetic as S
-from tests.gpu_helpers import dev, upload
+from tests.gpu_helpers import TOL, dev, norm_err, upload
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +34,7 @@ def make_server(torch, rx, K=3000, C=1, seed=501):
     g = S.Grid()
     ctx = rx.Context(H=g.H, W=g.W, cols_per_cta=64)
     h = upload(ctx, sc, torch, base=base, mlp_flat=S.flatten_mlp(mlp, C), C=C)
-    return ctx, h, g, rng
+    return ctx, h, g, rng, dict(scene=sc, base=base, mlp=mlp)
 
 
 def alone(ctx, rx, torch, h, tx, rxp, kind, C):
@@ -49,9 +49,13 @@ def alone(ctx, rx, torch, h, tx, rxp, kind, C):
 
 
 @pytest.mark.parametrize("C,kind_name", [(1, "OUT_RSSI"), (2, "OUT_CSI")])
-def test_each_result_equals_the_request_alone(torch, rx, C, kind_name):
+def test_each_result_equals_the_request_alone(torch, rx, oracle, C, kind_name):
+    """Every served result against the oracle (MLP radiance, brute-force
+    render of the request's transmitter, coherent sum), element by element
+    relative to the oracle's absolute chain; and against the same request
+    rendered alone on the GPU."""
     kind = getattr(rx, kind_name)
-    ctx, h, g, rng = make_server(torch, rx, C=C)
+    ctx, h, g, rng, inp = make_server(torch, rx, C=C)
     ctx.serve_start(h, kind=kind, max_batch_receivers=512, max_batch_views=8, slots=2)
     reqs = []
     for i in range(36):
@@ -80,10 +84,22 @@ def test_each_result_equals_the_request_alone(torch, rx, C, kind_name):
         ref = alone(ctx, rx, torch, h, tx, rxp, kind, C)
         scale = np.abs(ref).max() + 1e-30
         assert float(np.abs(got - ref).max()) <= 1e-4 * scale
+    # the oracle: radiance of the request's receivers, the transmitter's view
+    # rendered brute force, CSI / RSSI as coherent sums over the grid
+    sc = inp["scene"]
+    for i, ((tx, rxp), got) in enumerate(zip(reqs, results)):
+        rad = oracle.mlp_radiance(inp["mlp"], rxp, sc.means, inp["base"])
+        o = oracle.render_view(g, sc, tx, rad)
+        a_csi = o["absacc"].sum(axis=(1, 2))                     # [n, C]
+        if kind == rx.OUT_RSSI:
+            e = float((np.abs(got - oracle.rssi(o["spectra"])) / (a_csi[:, 0] + 1e-30)).max())
+        else:
+            e = norm_err(got.reshape(-1, C, 2), oracle.csi(o["spectra"]), a_csi)
+        assert e <= TOL, f"request {i} ({rxp.shape[0]} receivers): normalised error {e}"
 
 
 def test_admission_cancel_timeout_and_fault(torch, rx):
-    ctx, h, g, rng = make_server(torch, rx, seed=502)
+    ctx, h, g, rng, _ = make_server(torch, rx, seed=502)
     ctx.serve_start(h, kind=rx.OUT_RSSI, max_batch_receivers=256, max_batch_views=4,
                     mem_budget=64 << 20, slots=1)
     # larger than a batch, and larger than the memory budget

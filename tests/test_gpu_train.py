@@ -157,3 +157,77 @@ def test_fle_stage2_gradient_is_the_render_backward(torch, rx):
         m = float(ref.abs().max())
         assert m > 0.0
         assert float((got - ref).abs().max()) <= 1e-5 * m
+
+
+def test_stage2_step_matches_oracle(torch, rx, oracle):
+    """One Stage2Trainer step (3,000 Gaussians, 2 transmitters x 4 receivers,
+    MLP radiance, 90x360) against the oracle's Stage II step: the L1
+    amplitude loss, the gradients of phi_base and of every MLP parameter
+    (relative to their absolute chains), Adam's first moments and the
+    updated parameters of both optimisers.
+
+    The target is the oracle's starting amplitude scaled by 1 +- (0.3 ... 0.8)
+    per element, so no element's |R| - y sign is within float32 reach of a
+    flip.  Adam's first update is lr * g / (|g| + eps): where the oracle's
+    gradient is larger than twice the admitted gradient error the update must
+    agree to float32 rounding; elsewhere it must not exceed the step size."""
+    from paper_2605_24290_gb300.train import Stage2Trainer
+    from tests.test_gpu_backward import check_mlp_grads, oracle_grads, scaled_err
+    from tests.gpu_helpers import TOL
+    rng = np.random.default_rng(805)
+    K, C, M, N = 3000, 1, 2, 4
+    sc = S.draw_scene(rng, K)
+    g = S.Grid()
+    tx, rxp = S.draw_points(rng, M), S.draw_points(rng, N)
+    base0, mlp0 = S.draw_base(rng, K, C), S.draw_mlp(rng, C, final_scale=0.5)
+    base64 = base0.astype(np.float64)
+    mlp64 = {k: v.astype(np.float64) for k, v in mlp0.items()}
+    rad0 = oracle.mlp_radiance(mlp64, rxp, sc.means, base64)
+    views0 = [oracle.render_view(g, sc, tx[v], rad0) for v in range(M)]
+    amp0 = oracle.amplitude(np.stack([o["spectra"] for o in views0]))
+    sgn = np.where(rng.random(amp0.shape) < 0.5, -1.0, 1.0)
+    target = S.f32(amp0 * (1.0 + sgn * rng.uniform(0.3, 0.8, size=amp0.shape)))
+    lr_b, lr_m = 5e-3, 1e-3
+    ref = oracle.stage2_step(g, sc, tx, rxp, base64, mlp64, target.astype(np.float64),
+                             lr_base=lr_b, lr_mlp=lr_m)
+
+    ctx = rx.Context(H=g.H, W=g.W)
+    flat0 = S.flatten_mlp(mlp0, C)
+    h = upload(ctx, sc, torch, base=base0, mlp_flat=flat0, C=C)
+    tr = Stage2Trainer(ctx, h, dev(sc.opacity, torch), dev(base0, torch), dev(flat0, torch),
+                       lr_base=lr_b, lr_mlp=lr_m)
+    loss = float(tr.step(dev(tx, torch), dev(rxp, torch), dev(target, torch)))
+    a_amp = np.stack([o["absacc"][..., 0] for o in views0])      # bounds |R| and its error
+    assert abs(loss - ref["loss"]) <= TOL * a_amp.mean(), (loss, ref["loss"])
+
+    # gradients: the render backward's absolute terms for the oracle's
+    # cotangent, carried through the MLP backward's absolute chain
+    _, gspec = oracle.l1_amplitude(ref["spectra"], target.astype(np.float64))
+    ref_r, _, abs_r, _ = oracle_grads(oracle, g, sc, tx, rad0, gspec)
+    got_gb = tr.base.grad.detach().cpu().numpy()
+    got_gm = S.unflatten_mlp(tr.mlp.grad.detach().cpu().numpy(), C)
+    check_mlp_grads(oracle, mlp64, rxp, sc.means, base64, abs_r,
+                    dict(ref["grad_mlp"], base=ref["grad_base"]), got_gb, got_gm)
+    chain, amb = oracle.mlp_backward_chain(mlp64, rxp, sc.means, base64, abs_r)
+
+    def check_update(p0, p_got, p_ref, g_ref, dg, lr, m_got, name):
+        p0, p_got, p_ref, g_ref, dg = (np.asarray(x, np.float64).reshape(-1)
+                                       for x in (p0, p_got, p_ref, g_ref, dg))
+        m_got = np.asarray(m_got, np.float64).reshape(-1)
+        assert scaled_err(m_got, 0.1 * g_ref, 0.1 * dg / TOL) <= TOL, f"{name} first moment"
+        sure = np.abs(g_ref) > 2.0 * dg
+        tol = 2e-7 * np.maximum(np.abs(p0), lr)
+        assert np.all(np.abs(p_got - p_ref)[sure] <= tol[sure]), f"{name} update"
+        assert np.all(np.abs(p_got - p0)[~sure] <= lr * (1 + 1e-5) + tol[~sure]), f"{name} step"
+        return int(sure.sum())
+
+    st_b = tr.opt_base.state[tr.base]
+    n_sure = check_update(base0, tr.base.detach().cpu().numpy(), ref["base"], ref["grad_base"],
+                          TOL * chain["base"], lr_b, st_b["exp_avg"].cpu().numpy(), "phi_base")
+    assert n_sure > 0.5 * base0.size
+    st_m = tr.opt_mlp.state[tr.mlp]
+    new_m = S.unflatten_mlp(tr.mlp.detach().cpu().numpy(), C)
+    m1 = S.unflatten_mlp(st_m["exp_avg"].cpu().numpy(), C)
+    for name in mlp0:
+        check_update(mlp0[name], new_m[name], ref["params"][name], ref["grad_mlp"][name],
+                     TOL * (chain[name] + amb[name] / TOL), lr_m, m1[name], name)

@@ -444,6 +444,151 @@ def test_mlp_bf16_rounding_matches_torch(oracle):
     np.testing.assert_array_equal(got, ref)
 
 
+def test_mlp_backward_chain_bounds_the_terms(oracle):
+    """The absolute chain of the MLP backward bounds every gradient entry and,
+    with every input, weight and incoming gradient positive and every complex
+    quantity real (zero imaginary parts and zero weights into the imaginary
+    outputs, so every unit is active and no term cancels), equals the
+    gradient itself."""
+    rng = np.random.default_rng(25)
+    C = 2
+    params = S.draw_mlp(rng, C, final_scale=1.0)
+    rx, means, base = rng.normal(size=(3, 3)) * 3, rng.normal(size=(6, 3)) * 3, rng.normal(size=(6, C, 2))
+    g = rng.normal(size=(3, 6, C, 2))
+    got = oracle.mlp_backward(params, rx, means, base, g)
+    chain, amb = oracle.mlp_backward_chain(params, rx, means, base, np.abs(g))
+    for k in got:
+        assert np.all(np.abs(got[k]) <= chain[k] * (1 + 1e-12) + 1e-300), k
+        assert np.all(amb[k] == 0.0), k          # no unit near zero here
+    pos = {k: np.abs(v) + 0.01 for k, v in params.items()}
+    for k in ("g_w2", "g_b2", "l_w2", "l_b2"):    # outputs (a.re, a.im, b.re, b.im)
+        pos[k][1::2] = 0.0
+    means_p = rng.uniform(0.0, 1.0, size=(6, 3))
+    rx_p = rng.uniform(2.0, 3.0, size=(3, 3))     # v_hat > 0 componentwise
+    base_p, g_p = np.abs(base) + 0.1, np.abs(g) + 0.1
+    base_p[..., 1] = 0.0
+    g_p[..., 1] = 0.0
+    got = oracle.mlp_backward(pos, rx_p, means_p, base_p, g_p)
+    chain, _ = oracle.mlp_backward_chain(pos, rx_p, means_p, base_p, g_p)
+    for k in got:
+        np.testing.assert_allclose(chain[k], got[k], rtol=1e-12, err_msg=k)
+
+
+def test_mlp_backward_chain_marks_units_at_zero(oracle):
+    """A hidden unit whose pre-activation is exactly zero is a decision float32
+    cannot settle: its first-layer terms are returned as ambiguous."""
+    rng = np.random.default_rng(26)
+    C = 1
+    params = S.draw_mlp(rng, C, final_scale=1.0)
+    rx = rng.normal(size=(2, 3)) * 3
+    # unit 5 of the global branch: pre = w . x + b = 0 for receiver 0
+    params["g_b1"][5] = -float(params["g_w1"][5] @ rx[0])
+    means, base = rng.normal(size=(4, 3)), rng.normal(size=(4, C, 2))
+    g = rng.normal(size=(2, 4, C, 2))
+    _, amb = oracle.mlp_backward_chain(params, rx, means, base, np.abs(g))
+    assert amb["g_b1"][5] > 0 and np.all(np.delete(amb["g_b1"], 5) == 0)
+    assert np.all(amb["g_w1"][5] > 0)
+
+
+# ------------------------------------------------------- Stage II step pins
+
+def test_l1_amplitude_matches_torch_autograd(oracle):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(27)
+    spec = rng.normal(size=(2, 3, 5, 7, 1, 2))
+    spec[0, 0, 0, 0] = 0.0                        # an empty pixel: |R| = 1e-4
+    y = np.abs(rng.normal(size=(2, 3, 5, 7, 1)))
+    L, g = oracle.l1_amplitude(spec, y)
+    st = torch.tensor(spec, requires_grad=True)
+    amp = torch.sqrt(st[..., 0] ** 2 + st[..., 1] ** 2 + 1e-8)
+    lt = (amp - torch.tensor(y)).abs().mean()
+    lt.backward()
+    assert L == pytest.approx(float(lt.detach()), rel=1e-14)
+    np.testing.assert_allclose(g, st.grad.numpy(), rtol=1e-13, atol=1e-18)
+
+
+def test_l1_rssi_matches_torch_autograd(oracle):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(28)
+    c = rng.normal(size=(3, 4, 2))
+    y = np.abs(rng.normal(size=(3, 4)))
+    L, g = oracle.l1_rssi(c, y)
+    ct = torch.tensor(c, requires_grad=True)
+    lt = (torch.sqrt(ct[..., 0] ** 2 + ct[..., 1] ** 2) - torch.tensor(y)).abs().mean()
+    lt.backward()
+    assert L == pytest.approx(float(lt.detach()), rel=1e-14)
+    np.testing.assert_allclose(g, ct.grad.numpy(), rtol=1e-13, atol=1e-18)
+
+
+def test_adam_matches_torch_optimizer(oracle):
+    """Three Adam steps on given gradients equal torch.optim.Adam's."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(29)
+    p0 = rng.normal(size=50)
+    grads = [rng.normal(size=50) * 10 ** rng.uniform(-6, 1, size=50) for _ in range(3)]
+    pt = torch.nn.Parameter(torch.tensor(p0))
+    opt = torch.optim.Adam([pt], lr=3e-3)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for t, gr in enumerate(grads, start=1):
+        pt.grad = torch.tensor(gr)
+        opt.step()
+        p, m, v = oracle.adam(p, gr, m, v, t, 3e-3)
+        np.testing.assert_allclose(p, pt.detach().numpy(), rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(m, opt.state[pt]["exp_avg"].numpy(), rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(v, opt.state[pt]["exp_avg_sq"].numpy(), rtol=1e-13, atol=1e-300)
+
+
+@pytest.mark.parametrize("kind", ["spectra", "rssi"])
+def test_stage2_step_gradient_matches_finite_differences(oracle, kind):
+    """The Stage II step's gradients (L1 loss -> render backward -> MLP
+    backward) against central differences of its loss over phi_base and MLP
+    entries on the seam / pole scene; the update is Adam's first step."""
+    rng = np.random.default_rng(30)
+    sc, tx = tiny_scene(31, K=40)
+    g = tiny_grid(eps_T=0.02)
+    txs = np.stack([tx, tx + S.f32([0.4, 0.1, -0.2])])
+    rxp = S.f32(rng.uniform([3, 2, 0], [7, 6, 2], size=(2, 3)))
+    C = 1
+    base = rng.normal(size=(sc.K, C, 2))
+    params = {k: v.astype(np.float64) for k, v in S.draw_mlp(rng, C, final_scale=0.5).items()}
+    r0 = oracle.stage2_step(g, sc, txs, rxp, base, params,
+                            np.zeros((2, 2, g.H, g.W, C)) if kind == "spectra" else np.zeros((2, 2)),
+                            kind=kind)
+    spec0 = r0["spectra"]
+    if kind == "spectra":
+        amp = oracle.amplitude(spec0)
+        target = amp * (1 + np.where(rng.random(amp.shape) < 0.5, -0.5, 0.5))
+    else:
+        c = spec0.sum(axis=(2, 3))[..., 0, :]
+        target = np.sqrt((c ** 2).sum(-1)) * (1 + np.where(rng.random((2, 2)) < 0.5, -0.5, 0.5))
+    res = oracle.stage2_step(g, sc, txs, rxp, base, params, target, kind=kind, lr_base=1e-2,
+                             lr_mlp=2e-3)
+
+    def loss(b, P):
+        return oracle.stage2_step(g, sc, txs, rxp, b, P, target, kind=kind)["loss"]
+
+    h = 1e-6
+    for idx in [(0, 0, 0), (7, 0, 1), (23, 0, 0)]:
+        bp, bm = base.copy(), base.copy()
+        bp[idx] += h
+        bm[idx] -= h
+        fd = (loss(bp, params) - loss(bm, params)) / (2 * h)
+        assert fd == pytest.approx(res["grad_base"][idx], rel=1e-5, abs=1e-12)
+    for name, idx in [("g_w1", (3, 1)), ("g_b2", (2,)), ("l_w1", (10, 3)), ("l_w2", (1, 7)),
+                      ("l_b1", (4,))]:
+        pp, pm = dict(params), dict(params)
+        pp[name] = params[name].copy()
+        pm[name] = params[name].copy()
+        pp[name][idx] += h
+        pm[name][idx] -= h
+        fd = (loss(base, pp) - loss(base, pm)) / (2 * h)
+        assert fd == pytest.approx(res["grad_mlp"][name][idx], rel=1e-5, abs=1e-12), name
+    # Adam's first update: lr * g / (|g| + eps)
+    gb = res["grad_base"]
+    np.testing.assert_allclose(res["base"], base - 1e-2 * gb / (np.abs(gb) + 1e-8), rtol=1e-12)
+    assert res["state"]["t"] == 1
+
+
 # -------------------------------------------------------------- backward
 
 def test_render_backward_matches_finite_differences(oracle):
@@ -499,6 +644,38 @@ def test_render_backward_with_stop_matches_fd_of_fixed_sequence(oracle):
         rp[idx] += 1.0
         d = ((oracle.render_view(g, sc, tx, rp)["spectra"] - base) * gs).sum()
         assert d == pytest.approx(gr[idx], rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("case", ["seam_pole", "workload_small"])
+def test_render_pixels_equals_render_view(oracle, case):
+    """The pixel-list render (the checker of the full-size sampled GPU tests)
+    returns, at every listed pixel and in any pixel order, exactly what the
+    full-view render gives there: values, absolute chains, composited counts
+    and the float32 final transmittance, bit for bit.  Cases: the seam, pole
+    and full-width-span scene on the 18x36 grid (6x6 tiles), and the
+    4,096-Gaussian workload on 90x360 with 8 receivers."""
+    rng = np.random.default_rng(42)
+    if case == "seam_pole":
+        sc, tx = tiny_scene(43, K=48)
+        g = tiny_grid(eps_T=0.6)        # a high threshold so that pixels stop
+        rad = rng.normal(size=(3, sc.K, 2, 2))
+        pix = rng.permutation(g.H * g.W).astype(np.int32)
+    else:
+        w = S.workload_small()
+        g, sc, tx = w["grid"], w["scene"], w["tx"][0]
+        rad = w["radiance"].astype(np.float64)
+        pix = rng.choice(g.H * g.W, size=4000, replace=False).astype(np.int32)
+    o = oracle.render_view(g, sc, tx, rad)
+    val, aab, nc, tf = oracle.render_pixels(g, sc, tx, rad, pix)
+    N, C = rad.shape[0], rad.shape[2]
+    ref_val = o["spectra"].reshape(N, g.H * g.W, C, 2)[:, pix].transpose(1, 0, 2, 3)
+    ref_aab = o["absacc"].reshape(N, g.H * g.W, C)[:, pix].transpose(1, 0, 2)
+    np.testing.assert_array_equal(val.view(np.uint64), ref_val.view(np.uint64))
+    np.testing.assert_array_equal(aab.view(np.uint64), ref_aab.view(np.uint64))
+    np.testing.assert_array_equal(nc, o["ncontrib"].reshape(-1)[pix])
+    np.testing.assert_array_equal(tf.view(np.uint32), o["Tfinal"].reshape(-1)[pix].view(np.uint32))
+    # the case is not vacuous: many pixels composite, and some stop early
+    assert (nc > 0).mean() > 0.3 and (tf < g.eps_T).any()
 
 
 def test_backward_on_pixel_subsets_adds_up(oracle):
