@@ -694,6 +694,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     a.partial = partial;
     a.ncontrib = out->ncontrib;
     a.tfinal = out->tfinal;
+    a.err = ctx->d_err;
     {
       Stage sg(ctx, "render_fwd", st);
       launch_render_fwd(a, pick_cols(ctx, ncols), st);
@@ -918,6 +919,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.stops = stops;
   A.tile_stop = tstop;
   A.n_inst = v->n_inst;
+  A.err = ctx->d_err;
   {
     Stage sg(ctx, "bwd_prepass", st);
     launch_bwd_prepass(A, st);

@@ -464,15 +464,18 @@ void launch_bwd_prepass(const BackwardArgs& A, cudaStream_t s) {
   note_launches(1);
 }
 
+void launch_render_bwd_tc(const BackwardArgs& A, cudaStream_t s);  // render_bwd_tc.cu
+
 void launch_render_bwd(const BackwardArgs& A, cudaStream_t s) {
   const RenderArgs& a = A.f;
   if (a.M <= 0 || a.ncols <= 0) return;
   // radiance rows are padded to a multiple of 128 columns, so every block
-  // of 64 or 128 columns lies inside its row
+  // of 64 or 128 columns lies inside its row; blocks of 128 columns run the
+  // tensor-core sweep (render_bwd_tc.cu)
   if (a.ncols <= 64)
     launch_bwd_nb<64>(A, s);
   else
-    launch_bwd_nb<128>(A, s);
+    launch_render_bwd_tc(A, s);
 }
 
 }  // namespace rxgs

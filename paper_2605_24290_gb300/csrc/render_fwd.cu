@@ -51,12 +51,16 @@ static void launch_fwd_nb(const RenderArgs& a, cudaStream_t s) {
   note_launches(1);
 }
 
+void launch_render_fwd_tc(const RenderArgs& a, cudaStream_t s);  // render_fwd_tc.cu
+
+// Blocks of 16-64 columns composite on the CUDA cores; blocks of 128 columns
+// run their chunk products on the tensor cores (render_fwd_tc.cu).
 void launch_render_fwd(const RenderArgs& a, int cols_per_cta, cudaStream_t s) {
   if (a.M <= 0 || a.ncols <= 0) return;
   switch (cols_per_cta) {
     case 16: launch_fwd_nb<16>(a, s); break;
     case 32: launch_fwd_nb<32>(a, s); break;
-    case 128: launch_fwd_nb<128>(a, s); break;
+    case 128: launch_render_fwd_tc(a, s); break;
     default: launch_fwd_nb<64>(a, s); break;
   }
 }

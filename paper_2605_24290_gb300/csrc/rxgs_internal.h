@@ -28,6 +28,7 @@ enum : unsigned {
   kErrCapacity = 1u,   // an instance list was larger than its buffer
   kErrBounds = 2u,     // an index left its buffer (checked builds)
   kErrArgument = 4u,   // a device-side argument check failed
+  kErrTimeout = 8u,    // a bounded device-side wait (mbarrier) gave up
 };
 
 // ----------------------------------------------------------- geometry (a0-a3)
@@ -116,6 +117,7 @@ struct RenderArgs {
   float* partial;          // [M][T][ncols] per-tile column sums or null
   int32_t* ncontrib;       // [M][H][W] or null
   float* tfinal;           // [M][H][W] or null
+  unsigned* err = nullptr; // device error word (kErrTimeout), or null
 };
 void launch_render_fwd(const RenderArgs& a, int cols_per_cta, cudaStream_t s);
 
@@ -133,6 +135,7 @@ struct BackwardArgs {
   uint32_t* stops;            // scratch [M][H][W]: stop position per pixel
   uint32_t* tile_stop;        // scratch [M][T]: largest stop of each tile
   uint32_t n_inst;
+  unsigned* err;              // device error word (kErrTimeout), or null
 };
 // Walk 1 of the backward (final T and stop per pixel, largest stop per tile)
 void launch_bwd_prepass(const BackwardArgs& a, cudaStream_t s);

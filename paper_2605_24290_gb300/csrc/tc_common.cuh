@@ -1,0 +1,177 @@
+// tc_common.cuh -- Blackwell (sm_103a) tensor-core building blocks written
+// as inline PTX: tensor memory (TMEM) allocation and loads, shared-memory
+// matrix descriptors for operands in the canonical no-swizzle layout,
+// tcgen05.mma (kind::f16 with bf16 operands, float32 accumulation in TMEM),
+// mbarrier completion tracking with bounded waits, and the split of a
+// float32 value into two bf16 terms.
+//
+// Operand layout (no swizzle).  A matrix of 16-bit elements is stored as
+// "core matrices" of 8 rows x 8 elements (16 bytes per row, 128 contiguous
+// bytes per core matrix).  For an operand read K-major (rows = M or N, the
+// 8 elements of a row consecutive in K) the descriptor's stride byte offset
+// (SBO) is the distance between core matrices adjacent in M/N and the
+// leading byte offset (LBO) the distance between core matrices adjacent in
+// K.  The same bytes read MN-major (the 8 consecutive elements of a core row
+// running along M/N, the 8 rows along K) take SBO = distance between core
+// matrices adjacent in M/N and LBO = distance between those adjacent in K.
+// So one blocked buffer of an 8x8-core [R][C] matrix serves both as a
+// K-major operand with K = C and as an MN-major operand with M = C, K = R.
+//
+// Split precision.  x = hi + lo with hi = bf16(x) and lo = bf16(x - hi)
+// represents x to within 2^-17 |x|; a product x*y is formed as
+// hi_x*hi_y + hi_x*lo_y + lo_x*hi_y (three MMAs into one accumulator), which
+// drops lo_x*lo_y (below 2^-16 |x y|): about 1.2e-5 relative per term in
+// all, float32 accumulation.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace rxgs {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------- TMEM
+// Allocates `ncols` (power of two >= 32) TMEM columns for this CTA; the
+// address is written to *dst (shared).  Called by one whole warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+// Frees them again (one whole warp; no MMA or load may still use them).
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane: the warp reads
+// lanes (taddr >> 16) .. +31 (warp w may read lanes 32 (w % 4) .. +31), thread
+// i lane (taddr >> 16) + i.  Completes at tmem_wait_ld.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Orders tcgen05 operations around a thread barrier.
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// Makes this thread's ordinary shared-memory stores visible to the tensor
+// core's (async proxy) reads.
+__device__ __forceinline__ void fence_smem_to_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------- descriptors
+// Shared-memory matrix descriptor, no swizzle: start address, LBO and SBO in
+// bytes (multiples of 16), descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;  // base offset 0, absolute LBO mode, layout 0 = no swizzle
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B, float32 D, M x N,
+// A / B read K-major (0) or MN-major (1).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, int b_mn_major) {
+  return (1u << 4)                                   // D: float32
+         | (1u << 7)                                 // A: bf16
+         | (1u << 10)                                // B: bf16
+         | (static_cast<uint32_t>(a_mn_major) << 15) // A major
+         | (static_cast<uint32_t>(b_mn_major) << 16) // B major
+         | (static_cast<uint32_t>(N >> 3) << 17)     // N / 8
+         | (static_cast<uint32_t>(M >> 4) << 24);    // M / 16
+}
+
+// D[tmem] (+)= A[smem] * B[smem]; issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The mbarrier at `mbar` receives one arrival when every MMA this thread
+// issued before has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
+
+// ------------------------------------------------------------ mbarriers
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// Waits until the phase with the given parity has completed; gives up after
+// `limit` polls and returns false (the caller records the failure).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+  const uint32_t a = smem_u32(mbar);
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------ bf16 split
+// x = hi + lo: hi = bf16(x) (nearest), lo = bf16(x - hi) (x - hi is exact).
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+// Eight floats -> two 16-byte rows of hi and lo terms.
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(x[2 * i], h0, l0);
+    split_bf16(x[2 * i + 1], h1, l1);
+    h[i] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+    l[i] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+}  // namespace tc
+}  // namespace rxgs

@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(256) mlp_weighted_kernel(
       for (int i = 0; i < 6; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
       h[u] = rb(fmaxf(a, 0.0f));
     }
-#pragma unroll
+    // channels unrolled for the narrow spectra only (wide float32 spectra
+    // would unroll 52 x 256 FMAs)
+#pragma unroll(MAXC2 <= 8 ? MAXC2 / 2 : 1)
     for (int c = 0; c < MAXC2 / 2; ++c) {
       if (c >= C) break;
       float ol[4];

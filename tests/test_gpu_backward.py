@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2605_24290_gb300 import synthetic as S
-from tests.gpu_helpers import TOL, dev, upload
+from tests.gpu_helpers import TOL, dev, norm_err, upload
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,48 @@ def test_backward_explicit_radiance(torch, rx, oracle, tile):
     assert e_r <= TOL, f"radiance gradient error {e_r}"
     assert e_t <= TOL, f"opacity gradient error {e_t}"
     assert np.abs(ref_t).max() > 0
+
+
+@pytest.mark.parametrize("N", [64, 40, 100])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32)])
+def test_backward_wide_blocks_tensor_cores(torch, rx, oracle, N, tile):
+    """Column blocks of 128 (2NC > 64) take the tensor-core sweep: 64
+    receivers fill one block exactly (the benchmark's width), 40 leave 48
+    padding columns, 100 need two blocks (the second ragged).  Forward spectra
+    (the tensor-core forward) and both gradients against the oracle."""
+    rng = np.random.default_rng(206 + N)
+    K = 2500
+    sc = S.draw_scene(rng, K)
+    g = S.Grid()
+    g.tile_h, g.tile_w = tile
+    tx = S.draw_points(rng, 2)
+    rad = S.draw_radiance(rng, N, K, 1)
+    M = 2
+    gs = rng.normal(size=(M, N, g.H, g.W, 1, 2)).astype(np.float32)
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch)
+    views = ctx.prepare(h, dev(tx, torch))
+    radd = dev(rad, torch)
+    spec = torch.zeros((M, N, g.H, g.W, 1, 2), device="cuda")
+    csi = torch.zeros((M, N, 1, 2), device="cuda")
+    ctx.render_views(views, None, N, rx.OUT_SPECTRA | rx.OUT_CSI, radiance=radd, spectra=spec,
+                     csi=csi)
+    d_rad = torch.zeros_like(radd)
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, None, N, rx.OUT_SPECTRA, radiance=radd, grad_spectra=dev(gs, torch),
+                        grad_radiance=d_rad, grad_opacity=d_tau)
+    ctx.sync()
+    for v in range(M):
+        o = oracle.render_view(g, sc, tx[v], rad.astype(np.float64))
+        assert norm_err(spec[v].cpu().numpy(), o["spectra"], o["absacc"]) <= TOL
+        a = o["absacc"].sum(axis=(1, 2))
+        assert norm_err(csi[v].cpu().numpy(), oracle.csi(o["spectra"]), a) <= TOL
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
+    e_r = scaled_err(d_rad.cpu().numpy(), ref_r, abs_r)
+    e_t = scaled_err(d_tau.cpu().numpy(), ref_t, abs_t)
+    assert e_r <= TOL, f"radiance gradient error {e_r}"
+    assert e_t <= TOL, f"opacity gradient error {e_t}"
+    assert np.abs(ref_t).max() > 0 and np.abs(ref_r).max() > 0
 
 
 def test_backward_csi_and_rssi_cotangents(torch, rx, oracle):

@@ -95,9 +95,11 @@ def test_batched_mlp_matches_single_batches_and_oracle(torch, rx, oracle):
         off += n
 
 
-def test_autotune_keeps_spectra(torch, rx):
-    """The autotuner only moves work between CTAs: spectra after tuning are
-    bit-identical to those before."""
+def test_autotune_keeps_spectra(torch, rx, oracle):
+    """The autotuner only moves work between CTAs: spectra after tuning equal
+    those before (bit for bit when both runs composite on the CUDA cores;
+    within the parity tolerance of the oracle's absolute chain when one of
+    them takes the 128-column tensor-core product)."""
     rng = np.random.default_rng(403)
     sc = S.draw_scene(rng, 3000)
     g = S.Grid()
@@ -114,5 +116,11 @@ def test_autotune_keeps_spectra(torch, rx):
     after = torch.zeros_like(before)
     ctx.render(h, tx, None, 24, rx.OUT_SPECTRA, radiance=rad, spectra=after)
     ctx.sync()
-    np.testing.assert_array_equal(before.cpu().numpy().view(np.uint32),
-                                  after.cpu().numpy().view(np.uint32))
+    b_np, a_np = before.cpu().numpy(), after.cpu().numpy()
+    if ch["cols"] < 128:
+        np.testing.assert_array_equal(b_np.view(np.uint32), a_np.view(np.uint32))
+    else:
+        rad_np, tx_np = rad.cpu().numpy().astype(np.float64), tx.cpu().numpy()
+        for v in range(2):
+            o = oracle.render_view(g, sc, tx_np[v], rad_np)
+            assert norm_err(a_np[v], b_np[v], o["absacc"]) <= TOL

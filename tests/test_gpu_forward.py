@@ -57,7 +57,10 @@ def check_views(torch, ctx, oracle, g, scene, tx_np, views, which=None):
     for v in (range(M) if which is None else which):
         _, orec, obox = oracle.project_view32(g, scene, tx_np[v])
         vr = ranges[v]
-        vs, ve = int(vr[:, 0][vr[:, 1] > vr[:, 0]].min(initial=0)), int(vr[:, 1].max(initial=0))
+        used = vr[:, 1] > vr[:, 0]
+        vs = int(vr[used, 0].min()) if used.any() else 0
+        ve = int(vr[used, 1].max()) if used.any() else 0
+        assert ve - vs == int((vr[used, 1] - vr[used, 0]).sum()), f"view {v} not contiguous"
         kv = keys[vs:ve] & np.uint64(0x7FFFFFFF)
         np.testing.assert_array_equal(kv.astype(np.uint32), orec[vals[vs:ve], 6].view(np.uint32),
                                       err_msg=f"depth bits of the keys, view {v}")
@@ -193,17 +196,27 @@ def test_small_workload_forward_parity(torch, rx, oracle):
 
 
 @pytest.mark.parametrize("cols", [16, 32, 64, 128])
-def test_column_blocking_is_bit_identical(torch, rx, cols):
+def test_column_blocking(torch, rx, oracle, cols):
+    """Column blocks of 16-64 composite on the CUDA cores in the same order:
+    spectra bit-identical.  Blocks of 128 columns take the tensor-core
+    product (split bf16, float32 accumulation): the same stop positions and
+    final transmittances bit for bit, spectra within the parity tolerance of
+    the oracle's absolute chain of the CUDA-core result."""
     w = S.workload_small()
     g, sc = w["grid"], w["scene"]
-    ref = None
     ctx = make_ctx(rx, g, cols_per_cta=cols)
     h = upload(ctx, sc, torch)
-    spec = render_all(torch, ctx, h, w["tx"], w["radiance"], rx.OUT_SPECTRA)[0]
+    spec, _, _, ncon, tfin = render_all(torch, ctx, h, w["tx"], w["radiance"], rx.OUT_SPECTRA)
     ctx2 = make_ctx(rx, g, cols_per_cta=64)
     h2 = upload(ctx2, sc, torch)
-    ref = render_all(torch, ctx2, h2, w["tx"], w["radiance"], rx.OUT_SPECTRA)[0]
-    np.testing.assert_array_equal(spec.view(np.uint32), ref.view(np.uint32))
+    ref, _, _, ncon2, tfin2 = render_all(torch, ctx2, h2, w["tx"], w["radiance"], rx.OUT_SPECTRA)
+    np.testing.assert_array_equal(ncon, ncon2)
+    np.testing.assert_array_equal(tfin.view(np.uint32), tfin2.view(np.uint32))
+    if cols < 128:
+        np.testing.assert_array_equal(spec.view(np.uint32), ref.view(np.uint32))
+    else:
+        o = oracle.render_view(g, sc, w["tx"][0], w["radiance"].astype(np.float64))
+        assert norm_err(spec[0], ref[0], o["absacc"]) <= TOL
 
 
 def test_ragged_sizes_and_channels(torch, rx, oracle):

@@ -216,7 +216,12 @@ def test_stage2_step_matches_oracle(torch, rx, oracle):
         m_got = np.asarray(m_got, np.float64).reshape(-1)
         assert scaled_err(m_got, 0.1 * g_ref, 0.1 * dg / TOL) <= TOL, f"{name} first moment"
         sure = np.abs(g_ref) > 2.0 * dg
-        tol = 2e-7 * np.maximum(np.abs(p0), lr)
+        # float32 rounding of the parameter and of the step, plus the step's
+        # sensitivity to the admitted gradient error through Adam's eps:
+        # d/dg [g / (|g| + eps)] = eps / (|g| + eps)^2
+        eps = 1e-8
+        tol = 2e-7 * np.maximum(np.abs(p0), lr) + \
+            1.01 * lr * eps * dg / (np.maximum(np.abs(g_ref) - dg, 0.0) + eps) ** 2
         assert np.all(np.abs(p_got - p_ref)[sure] <= tol[sure]), f"{name} update"
         assert np.all(np.abs(p_got - p0)[~sure] <= lr * (1 + 1e-5) + tol[~sure]), f"{name} step"
         return int(sure.sum())
