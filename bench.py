@@ -433,7 +433,7 @@ def gpu_bench(args):
         cov = coverage_bench(torch, rxgs, S)
     fle = None
     if rank == 0 and not args.no_fle:
-        fle = fle_bench(torch, rxgs, S)
+        fle = fle_bench(torch, rxgs, S, K=args.fle_gaussians)
     train = None
     if rank == 0 and not args.no_train:
         train = train_bench(torch, rxgs, S)
@@ -658,13 +658,13 @@ def coverage_bench(torch, rxgs, S, reps=3):
             "workload": "1M Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance [1024,1M,1,2]"}
 
 
-def fle_bench(torch, rxgs, S, reps=3, lmax=9):
+def fle_bench(torch, rxgs, S, reps=3, lmax=9, K=None):
     """FLE radiance (App. E.2) at the bench scene's size: 100,000 Gaussians,
     32 transmitters x 64 receivers, degree 9 (L = 100 components; the
     coefficient tensor [64, 100k, 2, 100] is 5.1 GB), 90x360 grid: forward
     spectra, and forward + backward (spectra cotangent) to the coefficients
     and the opacity.  Views prepared once outside the timing."""
-    w = S.workload_mlp()
+    w = S.workload_mlp() if K is None else S.workload_mlp(K=K)
     g, sc = w["grid"], w["scene"]
     M, N, K = w["tx"].shape[0], w["rx"].shape[0], sc.K
     L = (lmax + 1) ** 2
@@ -734,7 +734,7 @@ def fle_bench(torch, rxgs, S, reps=3, lmax=9):
     ms_f = out["film_forward_backward"]["ms"]
     return {"spectra_per_s_fwd_bwd": round(M * N / (ms / 1e3), 1),
             "film_spectra_per_s_fwd_bwd": round(M * N / (ms_f / 1e3), 1), **out,
-            "workload": "100k Gaussians, 32 tx x 64 rx, FLE degree 9 (L = 100), 90x360, "
+            "workload": f"{K} Gaussians, 32 tx x 64 rx, FLE degree 9 (L = 100), 90x360, "
                         "spectra; backward to coefficients and opacity; film_*: base "
                         "coefficients [100k, 2, 100] conditioned by the global FiLM branch "
                         "(18 frequency vectors, d_c = 16, d = 64), backward to the base, "
@@ -883,6 +883,8 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-occupancy", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--fle-gaussians", type=int, default=None,
+                    help="Gaussians of the FLE section (default: the bench scene's 100,000)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -36,9 +36,15 @@
  *   - A status other than RXGS_OK means nothing was enqueued, except for
  *     RXGS_E_CUDA / RXGS_E_DEVICE, which report an error of the CUDA
  *     context; rxgs_last_error() gives a message.
- *   - Forward outputs are deterministic: the same inputs give bit-identical
- *     results; a receiver's spectrum does not depend on the other receivers
- *     of its batch.
+ *   - Forward outputs are deterministic: the same inputs and options give
+ *     bit-identical results.  A receiver's spectrum does not depend on the
+ *     other receivers of its batch beyond the width of the column block it
+ *     falls in: blocks of 16-64 columns composite on the CUDA cores in list
+ *     order, blocks of 128 columns (2 N C > 64) run the chunk products on
+ *     the tensor cores in split bf16 with float32 accumulation; the two
+ *     agree to about 1e-5 of each value's absolute chain.
+ *   - Backward outputs accumulate over tiles and views with float atomics:
+ *     repeated runs agree to within float32 rounding, not bit for bit.
  */
 #ifndef RXGS_H
 #define RXGS_H
@@ -81,7 +87,10 @@ typedef struct {
                           culled (0.05 m)                                    */
   int cols_per_cta;    /* receiver*channel*2 columns per render CTA:
                           16, 32, 64 or 128; 0 = chosen by the autotuner     */
-  int deterministic;   /* reserved (the forward is always deterministic)     */
+  int deterministic;   /* must be 0: a bit-reproducible backward is not
+                          provided (it would need a fixed-order reduction of
+                          per-instance dL/ds rows, 5 GB at 10M instances x
+                          128 columns); rxgs_create refuses other values     */
   size_t mem_budget;   /* serving admission budget in bytes; 0 = 8 GiB      */
 } rxgs_options;
 
@@ -181,7 +190,17 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream);
  *   film       packed FiLM parameters (rxgs_film_param_count floats, device),
  *              read when fle_base != NULL
  *   film_nfreq, film_embed, film_hidden   the FiLM sizes: frequency vectors
- *              (1..32), embedding width (0..64), hidden width (1..256) */
+ *              (1..32), embedding width (0..64), hidden width (1..256)
+ *   film_local 1: with fle_base, also the local branch (Eq. local): each
+ *              (receiver j, Gaussian k) gets (alpha_jk, beta_jk) from the
+ *              scene's conditioning MLP's local branch (inputs [v_hat, d, T,
+ *              rho_bar], the occlusion probes when the scene has an occupancy
+ *              grid), composed per Eq. combined_local:
+ *              (1 + alpha_jk) ((1 + a_jl) fle_base_kl + b_jl) + beta_jk.
+ *              Needs a scene uploaded with MLP weights (64 hidden units, C ==
+ *              1); its backward adds the local branch's gradient to grad_mlp
+ *              (the global branch's entries stay untouched).  0: no local
+ *              branch. */
 typedef struct {
   int kind;
   const float* radiance;
@@ -193,6 +212,7 @@ typedef struct {
   int film_nfreq;
   int film_embed;
   int film_hidden;
+  int film_local;
 } rxgs_render_desc;
 
 /* The global FiLM branch over FLE components (Eq. rx_enc, film; App. E.4).
@@ -415,6 +435,21 @@ rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset);
  * events). */
 rxgs_status rxgs_render_csi_noalloc(rxgs_ctx* ctx, rxgs_views_t views, const float* radiance,
                                     int N, float* csi, float* rssi, void* stream);
+
+/* The L1 term of the Stage II training loss (App. E.3; Sec. 3.1 Stage II)
+ * and its cotangent, in one pass over device buffers on `stream`:
+ *   kind RXGS_OUT_SPECTRA: values = rendered spectra [n][2] (Re, Im), target
+ *     = amplitudes [n]; with a_i = sqrt(Re^2 + Im^2 + 1e-8) (App. E.2)
+ *     grad[n][2] = sign(a_i - y_i) / n * (Re, Im) / a_i;
+ *   kind RXGS_OUT_RSSI: values = RSSI [n], target [n],
+ *     grad[n] = sign(rssi_i - y_i) / n;
+ *   loss[0] = (1/n) sum_i |a_i - y_i| (a fixed-order sum: the same from run
+ *     to run).
+ * All pointers are caller-owned device memory; grad may be passed as the
+ * cotangent of rxgs_render_backward.  Null pointers or another kind return
+ * RXGS_E_INVALID. */
+rxgs_status rxgs_l1_loss(rxgs_ctx* ctx, int kind, const float* values, const float* target,
+                         size_t n, float* loss, float* grad, void* stream);
 
 /* Waits for `stream` and converts a recorded device error into a status. */
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream);

@@ -8,8 +8,10 @@ The render itself lives in `rxgs_oracle.c` (plain C, float64 values with a
 float32 decision shadow); this module compiles it with gcc, loads it with
 ctypes and adds, in float64 numpy, the conditioning MLP (Sec. 3.3.2), the
 FLE directional basis (App. E.2), the occupancy grid and its probes
-(App. E.5) and the global FiLM branch over FLE components (Eq. rx_enc, film,
-film_apply), each with its backward where the path has one.
+(App. E.5), the global FiLM branch over FLE components (Eq. rx_enc, film,
+film_apply), its composition with the local branch (Eq. combined_local) and
+the Stage II step (App. E.3 L1 term, Adam of App. E.5), each with its
+backward where the path has one.
 """
 from __future__ import annotations
 
@@ -785,4 +787,57 @@ def film_fle_backward(film, base, rx, lmax: int, grad_coeffs):
     ph = np.asarray(rx, np.float64) @ P["omega"].T
     d_ph = d_g[:, 0::2] * np.cos(ph) - d_g[:, 1::2] * np.sin(ph)            # [N, F]
     out["omega"] = d_ph.T @ np.asarray(rx, np.float64)
+    return out
+
+
+# ------------------ Eq. combined_local over the FLE components (Sec. 3.3.2)
+# The local branch (Eq. local) of the conditioning MLP gives one complex pair
+# (alpha_loc, beta_loc) per (receiver j, Gaussian k) from [v_hat, d, T,
+# rho_bar]; Eq. combined_local applies it to every component's coefficient
+# after the global FiLM modulation (Eq. film_apply):
+#   phi_jkl = (1 + alpha_jk) [(1 + a_jl) phi_base,kl + b_jl] + beta_jk.
+
+def local_factors(params, rx, means, occ=None):
+    """(alpha_loc, beta_loc): complex [N, K] each, the local branch's four
+    outputs (alpha.re, alpha.im, beta.re, beta.im) for one channel."""
+    P = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    ol, _ = _mlp(local_features(rx, means, occ), P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"],
+                 False)
+    return ol[..., 0] + 1j * ol[..., 1], ol[..., 2] + 1j * ol[..., 3]
+
+
+def film_local_fle_coeffs(film, params, base, rx, means, lmax: int, occ=None):
+    """Per-receiver FLE coefficients [N,K,2,L] under both branches:
+    (1 + alpha_jk) ((1 + a_jl) phi_kl + b_jl) + beta_jk."""
+    c = film_fle_coeffs(film, base, rx, lmax)
+    c = c[:, :, 0, :] + 1j * c[:, :, 1, :]                                 # [N, K, L]
+    alpha, beta = local_factors(params, rx, means, occ)
+    c2 = (1.0 + alpha)[..., None] * c + beta[..., None]
+    return np.stack([c2.real, c2.imag], axis=2)
+
+
+def film_local_fle_backward(film, params, base, rx, means, lmax: int, grad_coeffs, occ=None):
+    """Gradients of sum(grad_coeffs * coeffs) (coeffs = film_local_fle_coeffs)
+    w.r.t. base, every FiLM parameter (names of `film`) and the local branch
+    (l_w1, l_b1, l_w2, l_b2).  With G' = dL/dRe + i dL/dIm of a coefficient:
+    dL/dalpha_jk = sum_l conj(c_jkl) G'_jkl, dL/dbeta_jk = sum_l G'_jkl and
+    the FiLM-modulated coefficient c gets conj(1 + alpha_jk) G'."""
+    gc = np.asarray(grad_coeffs, np.float64)
+    G2 = gc[:, :, 0, :] + 1j * gc[:, :, 1, :]                              # [N, K, L]
+    c = film_fle_coeffs(film, base, rx, lmax)
+    c = c[:, :, 0, :] + 1j * c[:, :, 1, :]
+    alpha, _ = local_factors(params, rx, means, occ)
+    d_alpha = (np.conj(c) * G2).sum(axis=-1)                               # [N, K]
+    d_beta = G2.sum(axis=-1)
+    G = np.conj(1.0 + alpha)[..., None] * G2
+    out = film_fle_backward(film, base, rx, lmax, np.stack([G.real, G.imag], axis=2))
+    P = {k: np.asarray(v, np.float64) for k, v in params.items()}
+    x = local_features(rx, means, occ)                                     # [N, K, 6]
+    _, h = _mlp(x, P["l_w1"], P["l_b1"], P["l_w2"], P["l_b2"], False)      # h [N, K, H]
+    d_ol = np.stack([d_alpha.real, d_alpha.imag, d_beta.real, d_beta.imag], axis=-1)
+    out["l_w2"] = np.einsum("nko,nkh->oh", d_ol, h)
+    out["l_b2"] = d_ol.sum(axis=(0, 1))
+    d_h = (d_ol @ P["l_w2"]) * (h > 0)
+    out["l_w1"] = np.einsum("nkh,nki->hi", d_h, x)
+    out["l_b1"] = d_h.sum(axis=(0, 1))
     return out

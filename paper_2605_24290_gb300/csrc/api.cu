@@ -47,6 +47,7 @@ bool make_grid(const rxgs_options& o, GridConst* g, std::string* why) {
     return *why = "tile_h * tile_w must be 256", false;
   if (!(o.q_max > 0.0f) || !(o.eps_T >= 0.0f) || !(o.r_near > 0.0f))
     return *why = "q_max, eps_T, r_near out of range", false;
+  if (o.deterministic != 0) return *why = "deterministic backward is not provided", false;
   if (o.cols_per_cta != 0 && o.cols_per_cta != 16 && o.cols_per_cta != 32 &&
       o.cols_per_cta != 64 && o.cols_per_cta != 128)
     return *why = "cols_per_cta must be 0, 16, 32, 64 or 128", false;
@@ -164,7 +165,7 @@ void rxgs_default_options(rxgs_options* o) {
   o->q_max = 9.0f;
   o->r_near = 0.05f;
   o->cols_per_cta = 0;
-  o->deterministic = 1;
+  o->deterministic = 0;
   o->mem_budget = 0;
 }
 
@@ -506,6 +507,8 @@ namespace {
 
 // Checks of the FLE radiance arguments (explicit or FiLM-conditioned).
 rxgs_status check_fle(rxgs_ctx* ctx, const SceneState* s, const rxgs_render_desc* d) {
+  if (d->film_local && !d->fle_base)
+    return fail(ctx, RXGS_E_INVALID, "film_local needs fle_base (the FiLM-conditioned FLE path)");
   if (!d->fle_coeffs && !d->fle_base) return RXGS_OK;
   if (d->fle_coeffs && d->fle_base)
     return fail(ctx, RXGS_E_INVALID, "fle_coeffs and fle_base exclude each other");
@@ -513,6 +516,11 @@ rxgs_status check_fle(rxgs_ctx* ctx, const SceneState* s, const rxgs_render_desc
   if (s->C != 1) return fail(ctx, RXGS_E_INVALID, "FLE radiance needs C == 1");
   if (d->fle_lmax < 0 || d->fle_lmax > 9) return fail(ctx, RXGS_E_INVALID, "fle_lmax must be 0..9");
   if (d->reduce_path == 1) return fail(ctx, RXGS_E_INVALID, "reduce_path 1 does not take FLE radiance");
+  if (d->film_local && !d->fle_base)
+    return fail(ctx, RXGS_E_INVALID, "film_local needs fle_base (the FiLM-conditioned FLE path)");
+  if (d->film_local && (!s->mlp || !local_branch_supported(s->hidden, s->C)))
+    return fail(ctx, RXGS_E_INVALID,
+                "film_local needs a scene with conditioning MLP weights (64 hidden units, C == 1)");
   if (d->fle_base) {
     if (!d->film) return fail(ctx, RXGS_E_INVALID, "fle_base needs the FiLM parameters (film)");
     if (rxgs_film_param_count(d->film_nfreq, d->film_embed, d->film_hidden, d->fle_lmax) <= 0)
@@ -538,16 +546,38 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
     float4* ab = nullptr;
     if (dalloc(&ab, static_cast<size_t>(N) * f.L, st) != cudaSuccess)
       return fail(ctx, RXGS_E_OOM, "FiLM outputs");
+    // the conditioned coefficients [N][K][2][L] (Eq. film_apply; with the
+    // local branch, Eq. combined_local), then the same contraction as for
+    // given coefficients
+    float* coeffs = nullptr;
+    float4* loc = nullptr;
+    float2* feat = nullptr;
+    cudaError_t e = dalloc(&coeffs, static_cast<size_t>(N) * s->K * 2 * f.L, st);
+    if (e == cudaSuccess && d->film_local) e = dalloc(&loc, static_cast<size_t>(N) * s->K, st);
+    if (e == cudaSuccess && d->film_local && s->occ)
+      e = dalloc(&feat, static_cast<size_t>(N) * s->K, st);
+    if (e != cudaSuccess) {
+      dfree(ab, st); dfree(coeffs, st); dfree(loc, st); dfree(feat, st);
+      return fail(ctx, RXGS_E_OOM, "FiLM coefficients");
+    }
     launch_film_global(d->film, f, rx, N, ab, st);
+    if (d->film_local) {
+      if (feat) launch_occ_probes(s->geom, s->K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
+      launch_local_factors(s->mlp, rx, N, s->geom, s->K, feat, loc, st);
+    }
+    launch_film_coeffs(d->fle_base, ab, loc, N, s->K, d->fle_lmax, coeffs, st);
+    dfree(loc, st);
+    dfree(feat, st);
     cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
-    launch_fle_radiance(nullptr, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
-                        static_cast<size_t>(s->K) * stride, rad, st, d->fle_base, ab);
+    launch_fle_radiance_tc(coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+                           static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
     dfree(ab, st);
+    dfree(coeffs, st);
   } else if (d->fle_coeffs) {
     // pad columns of every row stay zero
     cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
-    launch_fle_radiance(d->fle_coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
-                        static_cast<size_t>(s->K) * stride, rad, st);
+    launch_fle_radiance_tc(d->fle_coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+                           static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
   } else if (d->radiance) {
     launch_radiance_transpose(d->radiance, N, s->K, s->C, stride, rad, st);
   } else {
@@ -671,6 +701,7 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     v->key_film_dims[0] = d->fle_base ? d->film_nfreq : 0;
     v->key_film_dims[1] = d->fle_base ? d->film_embed : 0;
     v->key_film_dims[2] = d->fle_base ? d->film_hidden : 0;
+    v->key_film_local = d->fle_base ? d->film_local : 0;
     v->key_lmax = fle ? d->fle_lmax : -1;
     v->key_N = N;
     v->key_stride = stride;
@@ -855,6 +886,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
                       v->key_film_dims[0] == (film ? d->film_nfreq : 0) &&
                       v->key_film_dims[1] == (film ? d->film_embed : 0) &&
                       v->key_film_dims[2] == (film ? d->film_hidden : 0) &&
+                      v->key_film_local == (film ? d->film_local : 0) &&
                       v->key_lmax == (fle ? d->fle_lmax : -1) &&
                       v->key_N == N && v->key_stride == stride && v->key_gen == s->generation;
   auto cleanup = [&]() {
@@ -933,14 +965,26 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     if (gr->grad_radiance) launch_radiance_untranspose_add(d_rad, N, K, C, stride, gr->grad_radiance, st);
   } else if (film) {
     const FilmDims f = desc_film_dims(d);
-    float4 *ab = nullptr, *d_ab = nullptr;
-    float* ftmp = nullptr;
+    float4 *ab = nullptr, *d_ab = nullptr, *loc = nullptr, *d_loc = nullptr;
+    float *ftmp = nullptr, *G = nullptr;
+    float2* feat = nullptr;
     const size_t S = static_cast<size_t>(N) * f.L;
+    const size_t NK = static_cast<size_t>(N) * K;
     e = dalloc(&ab, S, st);
     if (e == cudaSuccess) e = dalloc(&d_ab, S, st);
     if (e == cudaSuccess && gr->grad_film) e = dalloc(&ftmp, film_backward_tmp_floats(f, N), st);
+    // the conditioned coefficients' gradient [N][K][2][L], written (not
+    // accumulated) by the tensor-core contraction, then folded
+    if (e == cudaSuccess) e = dalloc(&G, S * K * 2, st);
+    if (e == cudaSuccess && d->film_local) e = dalloc(&loc, NK, st);
+    if (e == cudaSuccess && d->film_local) e = dalloc(&d_loc, NK, st);
+    if (e == cudaSuccess && d->film_local && s->occ) e = dalloc(&feat, NK, st);
+    auto free_film = [&]() {
+      dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st); dfree(G, st);
+      dfree(loc, st); dfree(d_loc, st); dfree(feat, st);
+    };
     if (e != cudaSuccess) {
-      dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st);
+      free_film();
       cleanup();
       return fail(ctx, RXGS_E_OOM, "backward (FiLM): %s", cudaGetErrorString(e));
     }
@@ -948,20 +992,29 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
       Stage sg(ctx, "fle_film_bwd", st);
       cudaMemsetAsync(d_ab, 0, sizeof(float4) * S, st);
       launch_film_global(d->film, f, rx, N, ab, st);
-      launch_film_fle_backward(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
-                               d->fle_base, ab, gr->grad_fle_base, reinterpret_cast<float*>(d_ab),
-                               st);
+      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view, G,
+                             false, st, ctx->d_err);
+      if (d->film_local) {
+        // the local branch (Eq. combined_local): its gradient, and G becomes
+        // the FiLM-modulated coefficients' gradient
+        if (feat) launch_occ_probes(s->geom, K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
+        launch_local_factors(s->mlp, rx, N, s->geom, K, feat, loc, st);
+        launch_film_local_backward(G, d->fle_base, ab, loc, s->mlp, rx, N, s->geom, K,
+                                   d->fle_lmax, feat, d_loc, gr->grad_mlp, st);
+      }
+      launch_film_fold(G, N, K, d->fle_lmax, d->fle_base, ab, gr->grad_fle_base,
+                       reinterpret_cast<float*>(d_ab), st);
     }
     if (gr->grad_film) {
       Stage sg(ctx, "film_mlp_bwd", st);
       launch_film_backward(d->film, f, rx, N, d_ab, ftmp, gr->grad_film, st);
     }
-    dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st);
+    free_film();
   } else if (fle) {
     Stage sg(ctx, "fle_bwd", st);
     if (gr->grad_fle)
-      launch_fle_backward(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
-                          gr->grad_fle, st);
+      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
+                             gr->grad_fle, true, st, ctx->d_err);
   } else {
     MlpParams m{s->mlp, s->hidden, C, 0};
     g_base = gr->grad_base;
@@ -1060,6 +1113,22 @@ rxgs_status rxgs_profile_read(rxgs_ctx* ctx, char* json, size_t cap, int reset) 
   if (out.size() + 1 > cap) return fail(ctx, RXGS_E_INVALID, "buffer too small (%zu)", out.size() + 1);
   std::memcpy(json, out.c_str(), out.size() + 1);
   return RXGS_OK;
+}
+
+rxgs_status rxgs_l1_loss(rxgs_ctx* ctx, int kind, const float* values, const float* target,
+                         size_t n, float* loss, float* grad, void* stream) {
+  if (!ctx) return RXGS_E_INVALID;
+  if (!values || !target || !loss || !grad) return fail(ctx, RXGS_E_INVALID, "l1_loss: null argument");
+  if (kind != RXGS_OUT_SPECTRA && kind != RXGS_OUT_RSSI)
+    return fail(ctx, RXGS_E_INVALID, "l1_loss: kind must be RXGS_OUT_SPECTRA or RXGS_OUT_RSSI");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nparts = l1_loss_blocks();
+  float* part = nullptr;
+  CK(dalloc(&part, static_cast<size_t>(nparts), st));
+  launch_l1_loss(kind == RXGS_OUT_SPECTRA, values, target, n, loss, grad, part, nparts, st);
+  dfree(part, st);
+  return check_last(ctx, "l1_loss");
 }
 
 rxgs_status rxgs_sync(rxgs_ctx* ctx, void* stream) {

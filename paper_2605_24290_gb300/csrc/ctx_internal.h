@@ -57,6 +57,7 @@ struct ViewsState {
   const float* key_fle = nullptr;   // fle_coeffs, or fle_base with the FiLM below
   const float* key_film = nullptr;
   int key_film_dims[3] = {0, 0, 0};
+  int key_film_local = 0;
   int key_lmax = -1;
   int key_N = 0, key_stride = 0;
   uint64_t key_gen = ~0ull;

@@ -18,18 +18,23 @@
 // per CTA and serves both products: K-major as the A operand of gamma,
 // MN-major as the A operand of dL/ds.
 //
-// 512 threads.  Warps 0-7 own one pixel each (thread = pixel = TMEM lane of
-// its gamma row); warps 8-15 stage the next chunk's radiance, drain the
-// previous chunk's dL/ds accumulator (TMEM lanes = columns) into the
-// gradient with float atomics, sum the dL/dtau of the previous chunk, and
-// thread 256 issues the MMAs.  Per chunk n:
-//   1. all 512 threads evaluate the weights G[b][p] of chunk n (the entries
-//      that meet each warp's 32-pixel strip, shared between the two warps of
-//      a strip);
-//   2. warps 0-7 wait for gamma(n), run the recurrence, write T w (bf16 x 2);
-//      warps 8-15 wait for gamma(n), stage radiance(n+1) (bf16 x 2), drain
-//      dL/ds(n-1) and dL/dtau(n-1);
-//   3. one barrier, then dL/ds(n) and gamma(n+1) are issued.
+// 512 threads, 16 warps; pixel p = t % 256 belongs to warps w and w + 8
+// (w = p / 32), and its TMEM row (gamma) is lane 32 (w % 4) + p % 32 of
+// column block (w % 8) / 4, which both warps may read.  Per chunk n:
+//   1. gamma(n) is issued (its radiance s(n) was staged at the end of the
+//      previous chunk); all threads evaluate the weights G[b][p] of the
+//      entries meeting each 32-pixel strip, the two warps of a strip taking
+//      alternate entries, four at a time;
+//   2. the recurrence runs on two threads per pixel: warps 0-7 take entries
+//      31..16, warps 8-15 entries 15..0 after deriving the transmittance and
+//      Q in the middle of the chunk from entries 31..16 (a product of
+//      (1 - w) and the Q recurrence alone); each writes T w (bf16 x 2) and
+//      its dL/dtau terms in place of the weights; then all warps drain
+//      dL/ds(n-1) from TMEM into the gradient with float atomics (warp w:
+//      lanes 32 (w % 4) = columns, entries 8 (w / 4) .. +7);
+//   3. one barrier, dL/ds(n) is issued; all threads sum the chunk's dL/dtau
+//      terms over the pixels (fixed order, one float atomic per entry) and
+//      stage s(n+1) (prefetched into registers during step 2).
 // Every mbarrier wait is bounded: a wait that gives up sets kErrTimeout in the
 // device error word and the CTA leaves the loop, frees its tensor memory and
 // returns.
@@ -65,8 +70,8 @@ constexpr uint32_t kOffA1 = kOffS2 + kSBytes, kOffA2 = kOffA1 + kABytes;
 constexpr uint32_t kOffW = kOffA2 + kABytes;              // float G[32][256]
 constexpr uint32_t kOffRec = kOffW + kCH * kP * 4;        // float4 [2][32][2]
 constexpr uint32_t kOffIdx = kOffRec + 2 * kCH * 2 * 16;  // u32 [4][32] list indices
-constexpr uint32_t kOffTau = kOffIdx + 4 * kCH * 4;       // float [2][32][8] dL/dtau per warp
-constexpr uint32_t kOffMask = kOffTau + 2 * kCH * 8 * 4;  // u32 [8] strip masks
+constexpr uint32_t kOffTQ = kOffIdx + 4 * kCH * 4;        // float2 [256] T, Q per pixel
+constexpr uint32_t kOffMask = kOffTQ + kP * 8;            // u32 [8] strip masks
 constexpr uint32_t kOffBar = kOffMask + 64;               // u64 [2] mbarriers
 constexpr uint32_t kOffMisc = kOffBar + 16;               // u32 TMEM base, abort, #gamma, #dlds
 constexpr uint32_t kSmem = kOffMisc + 16;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
   float* sW = reinterpret_cast<float*>(sm + kOffW);
   float4* sRec0 = reinterpret_cast<float4*>(sm + kOffRec);
   uint32_t* sIdx = reinterpret_cast<uint32_t*>(sm + kOffIdx);
-  float* sTau = reinterpret_cast<float*>(sm + kOffTau);
+  float2* sTQ = reinterpret_cast<float2*>(sm + kOffTQ);
   uint32_t* sMask = reinterpret_cast<uint32_t*>(sm + kOffMask);
   uint64_t* barG = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* barD = barG + 1;
@@ -109,19 +114,19 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
   const int nchunks = static_cast<int>((tile_stop - rg.x + kCH - 1) / kCH);
   const uint32_t sbase = tc::smem_u32(sm);
 
-  // this thread's pixel (warps 8-15 mirror warps 0-7 in the weight phase)
+  // this thread's pixel; warps w and w + 8 share the pixels of strip w % 8
   const int p = t & (kP - 1);
+  const int wp = warp & 7, half = warp >> 3;
   const int i = tr * g.TH + p / g.TW, jj = tcol * g.TW + p % g.TW;
   const bool valid = i < g.H && jj < g.W;
   const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
-  float T = 1.0f, Q = 0.0f;
+  float T = 1.0f, Q = 0.0f;  // at the back end of the next chunk
   uint32_t stop = rg.x;
   if (valid) {
     const size_t o = static_cast<size_t>(v) * HW + static_cast<size_t>(i) * g.W + jj;
     T = A.tfin[o];
     stop = A.stops[o];
   }
-  const int wp = warp & 7, half = warp >> 3;
   const Strip strip = pixel_strip(g, tr, tcol, 32 * wp, 32);
 
   // chunk n of the sweep covers list positions [chunk_start(n), +chunk_len(n))
@@ -145,91 +150,77 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     cp_async16(&rb[2 * l + 0], &rec[2 * k + 0], ok);
     cp_async16(&rb[2 * l + 1], &rec[2 * k + 1], ok);
   };
-  // warps 8-15: radiance rows of chunk n, 16 columns per thread
-  auto load_rad = [&](int n, float (&x)[16]) {
-    const int h = t - 256, b = h >> 3, cg = h & 7;
+  // all threads: radiance of chunk n, entry t / 16, 8 columns from 8 (t % 16)
+  auto load_rad = [&](int n, float (&x)[8]) {
+    const int b = t >> 4, cg = t & 15;
     const bool ok = b < chunk_len(n);
     const uint32_t k = ok ? sIdx[(n & 3) * kCH + b] : 0u;
     const float4* src =
-        reinterpret_cast<const float4*>(radv + static_cast<size_t>(k) * a.stride + col0 + cg * 16);
+        reinterpret_cast<const float4*>(radv + static_cast<size_t>(k) * a.stride + col0 + cg * 8);
+    const float4 r0 = ok ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 r1 = ok ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    x[0] = r0.x; x[1] = r0.y; x[2] = r0.z; x[3] = r0.w;
+    x[4] = r1.x; x[5] = r1.y; x[6] = r1.z; x[7] = r1.w;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 r = ok ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-      x[4 * q + 0] = r.x;
-      x[4 * q + 1] = r.y;
-      x[4 * q + 2] = r.z;
-      x[4 * q + 3] = r.w;
-    }
-#pragma unroll
-    for (int e = 0; e < 16; ++e)
-      if (col0 + cg * 16 + e >= a.ncols) x[e] = 0.0f;
+    for (int e = 0; e < 8; ++e)
+      if (col0 + cg * 8 + e >= a.ncols) x[e] = 0.0f;
   };
-  auto store_rad = [&](const float (&x)[16]) {
-    const int h = t - 256, b = h >> 3, cg = h & 7;
-    float x0[8], x1[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      x0[e] = x[e];
-      x1[e] = x[8 + e];
-    }
+  auto store_rad = [&](const float (&x)[8]) {
+    const int b = t >> 4, cg = t & 15;
     uint4 hi, lo;
-    const uint32_t row = (b >> 3) * kSboS + (b & 7) * 16;
-    tc::split8(x0, hi, lo);
-    *reinterpret_cast<uint4*>(sm + kOffS1 + row + (2 * cg) * kLboS) = hi;
-    *reinterpret_cast<uint4*>(sm + kOffS2 + row + (2 * cg) * kLboS) = lo;
-    tc::split8(x1, hi, lo);
-    *reinterpret_cast<uint4*>(sm + kOffS1 + row + (2 * cg + 1) * kLboS) = hi;
-    *reinterpret_cast<uint4*>(sm + kOffS2 + row + (2 * cg + 1) * kLboS) = lo;
+    tc::split8(x, hi, lo);
+    const uint32_t off = (b >> 3) * kSboS + cg * kLboS + (b & 7) * 16;
+    *reinterpret_cast<uint4*>(sm + kOffS1 + off) = hi;
+    *reinterpret_cast<uint4*>(sm + kOffS2 + off) = lo;
   };
-  // warps 8-11: dL/ds of chunk n from TMEM (lane = column) into the gradient
-  auto drain_dlds = [&](int n) {
-    float d[32];
-    tc::tmem_ld32(sMisc[0] + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64, d);
+  // all warps: dL/ds of chunk n from TMEM; warp w reads lanes 32 (w % 4)
+  // (columns) and entries 8 (w / 4) .. +7
+  auto drain_dlds = [&](uint32_t tmem, int n) {
+    const int e0 = 8 * (warp >> 2);
+    float d[8];
+    tc::tmem_ld8(tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 + e0, d);
     const int col = col0 + 32 * (warp & 3) + lane;
     const int nb = chunk_len(n);
-    const uint32_t* ks = sIdx + (n & 3) * kCH;
+    const uint32_t* ks = sIdx + (n & 3) * kCH + e0;
     if (col < a.ncols) {
 #pragma unroll
-      for (int b = 0; b < kCH; ++b)
-        if (b < nb && d[b] != 0.0f)
+      for (int b = 0; b < 8; ++b)
+        if (e0 + b < nb && d[b] != 0.0f)
           atomicAdd(&drad[static_cast<size_t>(ks[b]) * a.stride + col], d[b]);
     }
   };
-  // warp 12: dL/dtau of chunk n, the eight pixel warps' sums in order
-  auto drain_tau = [&](int n) {
-    const int b = lane;
-    if (b < chunk_len(n)) {
-      const float* src = sTau + (n & 1) * kCH * 8 + b * 8;
-      float y = 0.0f;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) y += src[w];
-      if (y != 0.0f) atomicAdd(&A.d_tau[sIdx[(n & 3) * kCH + b]], y);
-    }
-  };
-  // thread 256: the MMAs of gamma(n) (g x s) and dL/ds(n) (g^T x a)
+  // thread 256: the MMAs of gamma(n) (g x s) and dL/ds(n) (g^T x a);
+  // descriptors: a base per operand buffer, the start address (bits 0-13,
+  // in 16-byte units) moved by adding the byte offset >> 4
   auto issue_gamma = [&](uint32_t tmem) {
-#pragma unroll 1
+    const uint64_t dg[2] = {tc::smem_desc(sbase + kOffG1, kLboG, kSboG),
+                            tc::smem_desc(sbase + kOffG2, kLboG, kSboG)};
+    const uint64_t ds[2] = {tc::smem_desc(sbase + kOffS1, kLboS, kSboS),
+                            tc::smem_desc(sbase + kOffS2, kLboS, kSboS)};
+#pragma unroll
     for (int m = 0; m < 2; ++m)
-#pragma unroll 1
+#pragma unroll
       for (int k = 0; k < kNB / 16; ++k)
 #pragma unroll
         for (int term = 0; term < 3; ++term) {
-          const uint32_t ga = sbase + (term == 2 ? kOffG2 : kOffG1) + ((16 * m) * 16 + 2 * k) * 128;
-          const uint32_t sb = sbase + (term == 1 ? kOffS2 : kOffS1) + 2 * k * kLboS;
-          tc::mma_bf16(tmem + 32 * m, tc::smem_desc(ga, kLboG, kSboG),
-                       tc::smem_desc(sb, kLboS, kSboS), kIdescGamma, (k | term) != 0);
+          const uint64_t a_d = dg[term == 2] + ((((16 * m) * 16 + 2 * k) * 128) >> 4);
+          const uint64_t b_d = ds[term == 1] + ((2 * k * kLboS) >> 4);
+          tc::mma_bf16(tmem + 32 * m, a_d, b_d, kIdescGamma, (k | term) != 0);
         }
   };
   auto issue_dlds = [&](uint32_t tmem) {
-#pragma unroll 1
+    // g read MN-major: M = columns (core pitch 128 B), K = pixels (core pitch 2048 B)
+    const uint64_t dg[2] = {tc::smem_desc(sbase + kOffG1, kSboG, kLboG),
+                            tc::smem_desc(sbase + kOffG2, kSboG, kLboG)};
+    const uint64_t da[2] = {tc::smem_desc(sbase + kOffA1, kLboA, kSboA),
+                            tc::smem_desc(sbase + kOffA2, kLboA, kSboA)};
+#pragma unroll
     for (int k = 0; k < kP / 16; ++k)
 #pragma unroll
       for (int term = 0; term < 3; ++term) {
-        // g read MN-major: M = columns (core pitch 128 B), K = pixels (core pitch 2048 B)
-        const uint32_t ga = sbase + (term == 2 ? kOffG2 : kOffG1) + k * 2 * kSboG;
-        const uint32_t ab = sbase + (term == 1 ? kOffA2 : kOffA1) + 2 * k * kLboA;
-        tc::mma_bf16(tmem + 64, tc::smem_desc(ga, kSboG, kLboG), tc::smem_desc(ab, kLboA, kSboA),
-                     kIdescDlds, (k | term) != 0);
+        const uint64_t a_d = dg[term == 2] + ((k * 2 * kSboG) >> 4);
+        const uint64_t b_d = da[term == 1] + ((2 * k * kLboA) >> 4);
+        tc::mma_bf16(tmem + 64, a_d, b_d, kIdescDlds, (k | term) != 0);
       }
   };
 
@@ -249,28 +240,45 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     if (nchunks > 1) copy_indices(1);
     cp_async_commit();
   }
-  // cotangent tile -> g (bf16 x 2), 8 columns per store
-#pragma unroll 1
-  for (int r = 0; r < 8; ++r) {
-    const int oc = (t >> 8) + 2 * r;
-    float x[8];
+  // cotangent tile -> g (bf16 x 2): thread t takes pixel p and the 8-column
+  // octets (t >> 8) + 2r; every (re, im) column pair is one 8-byte load, all
+  // 32 of a thread in flight before the split
+  {
+    float2 xv[8][4];
+    const size_t pix = static_cast<size_t>(i) * g.W + jj;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int col = col0 + oc * 8 + e;
-      float val = 0.0f;
-      if (valid && col < a.ncols) {
-        const int j = col / twoC, ec = col - j * twoC;
-        const size_t pix = static_cast<size_t>(i) * g.W + jj;
-        if (A.g_spec) val += A.g_spec[((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + ec];
-        if (A.g_uniform) val += A.g_uniform[static_cast<size_t>(v) * a.ncols + col];
+    for (int r = 0; r < 8; ++r) {
+      const int oc = (t >> 8) + 2 * r;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = col0 + oc * 8 + 2 * e;  // even: (re, im) of one channel
+        float2 val = make_float2(0.0f, 0.0f);
+        if (valid && col < a.ncols) {
+          const int j = col / twoC, ec = col - j * twoC;
+          if (A.g_spec)
+            val = *reinterpret_cast<const float2*>(
+                &A.g_spec[((static_cast<size_t>(v) * a.N + j) * HW + pix) * twoC + ec]);
+          if (A.g_uniform) {
+            const float2 u =
+                *reinterpret_cast<const float2*>(&A.g_uniform[static_cast<size_t>(v) * a.ncols + col]);
+            val.x += u.x;
+            val.y += u.y;
+          }
+        }
+        xv[r][e] = val;
       }
-      x[e] = val;
     }
-    uint4 hi, lo;
-    tc::split8(x, hi, lo);
-    const uint32_t off = g_off(p, oc * 8);
-    *reinterpret_cast<uint4*>(sm + kOffG1 + off) = hi;
-    *reinterpret_cast<uint4*>(sm + kOffG2 + off) = lo;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int oc = (t >> 8) + 2 * r;
+      const float x[8] = {xv[r][0].x, xv[r][0].y, xv[r][1].x, xv[r][1].y,
+                          xv[r][2].x, xv[r][2].y, xv[r][3].x, xv[r][3].y};
+      uint4 hi, lo;
+      tc::split8(x, hi, lo);
+      const uint32_t off = g_off(p, oc * 8);
+      *reinterpret_cast<uint4*>(sm + kOffG1 + off) = hi;
+      *reinterpret_cast<uint4*>(sm + kOffG2 + off) = lo;
+    }
   }
   if (warp == 8 && nchunks > 0) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
   __syncthreads();  // indices of chunk 0, mbarriers, TMEM address
@@ -278,27 +286,26 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     gather_rec(0);
     cp_async_commit();
   }
-  if (warp >= 8 && nchunks > 0) {
-    float x[16];
+  if (nchunks > 0) {
+    float x[8];
     load_rad(0, x);
     store_rad(x);
   }
-  tc::fence_smem_to_async();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
   const uint32_t tmem = sMisc[0];
-  if (t == 256 && nchunks > 0) {
-    issue_gamma(tmem);
-    tc::mma_commit(barG);
-    sMisc[2] = 1;
-  }
 
   // ---- the sweep, back to front
   for (int n = 0; n < nchunks; ++n) {
+    tc::fence_smem_to_async();  // s(n) (and g for n = 0) for the tensor core
+    tc::fence_before_sync();
     cp_async_wait_all();  // records of chunk n, indices of chunk n + 1
     __syncthreads();
+    tc::fence_after_sync();
     if (sMisc[1]) break;
+    if (t == 256) {
+      issue_gamma(tmem);
+      tc::mma_commit(barG);
+      sMisc[2] = n + 1;
+    }
     const uint32_t start = chunk_start(n);
     const int nb = chunk_len(n);
     if (warp == 8) {
@@ -307,79 +314,105 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
       cp_async_commit();
     }
     const float4* sR = sRec0 + (n & 1) * 2 * kCH;
-    // 1. weights G[b][p] of the entries meeting this warp's strip, the two
-    //    warps of a strip taking alternate entries
+    // 1. weights G[b][p] (0: not composited) of the entries meeting this
+    //    warp's strip; the two warps of a strip take alternate entries
     {
       const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
       if (!__any_sync(0xffffffffu, start < stop)) m = 0;  // no pixel reaches this chunk
       if (half == 0 && lane == 0) sMask[wp] = m;
+      unsigned mine = 0;
       int r = 0;
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        if ((r++ & 1) != half) continue;
-        float G = 0.0f;
-        if (valid && start + b < stop) {
-          float w, Gv;
-          if (pixel_weight(g, sR[2 * b], sR[2 * b + 1], i, jj, fi, fj, &w, &Gv)) G = Gv;
+      for (unsigned mm = m; mm; mm &= mm - 1)
+        if ((r++ & 1) == half) mine |= 1u << (__ffs(mm) - 1);
+      while (mine) {
+        int bq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          bq[q] = mine ? __ffs(mine) - 1 : -1;
+          mine &= mine - 1;
         }
-        sW[b * kP + p] = G;  // 0: not composited by this pixel
+        float G[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int b = bq[q] >= 0 ? bq[q] : bq[0];
+          G[q] = pixel_G(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (bq[q] >= 0)
+            sW[bq[q] * kP + p] = (valid && start + bq[q] < stop && G[q] > 0.0f) ? G[q] : 0.0f;
       }
     }
     __syncthreads();
-    if (warp < 8) {
-      // 2a. the recurrence over the chunk, back to front
-      if (!tc::mbar_wait(barG, n & 1, kWaitLimit)) fail();
-      tc::fence_after_sync();
-      float gam[32];
-      tc::tmem_ld32(tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 32 * (warp >> 2), gam);
-      if (n > 0 && !tc::mbar_wait(barD, (n - 1) & 1, kWaitLimit)) fail();  // a is free again
-      const unsigned m = sMask[warp];
-      float* tauw = sTau + (n & 1) * kCH * 8;
+    // 2. the recurrence, two threads per pixel
+    float x[8];
+    const bool more = n + 1 < nchunks;
+    if (more) load_rad(n + 1, x);  // in flight during the recurrence
+    if (!tc::mbar_wait(barG, n & 1, kWaitLimit)) fail();
+    tc::fence_after_sync();
+    float gam[32];
+    tc::tmem_ld32(tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 32 * (wp >> 2), gam);
+    if (n > 0 && !tc::mbar_wait(barD, (n - 1) & 1, kWaitLimit)) fail();  // a is free again
+    tc::fence_after_sync();
+    const unsigned m = sMask[wp];
+    auto step = [&](int b, float& dt) {
+      float Tw = 0.0f;
+      dt = 0.0f;
+      if (m & (1u << b)) {
+        const float G = sW[b * kP + p];
+        if (G != 0.0f) {
+          const float w = __fmul_rn(sR[2 * b + 1].y, G);
+          const float one_m_w = 1.0f - w;
+          T = __fdividef(T, one_m_w);  // transmittance in front of entry b
+          Tw = T * w;
+          dt = T * (gam[b] - Q) * G;
+          Q = fmaf(w, gam[b], one_m_w * Q);
+        }
+      }
+      __nv_bfloat16 hi, lo;
+      tc::split_bf16(Tw, hi, lo);
+      const uint32_t off = (b >> 3) * kSboA + (p >> 3) * kLboA + (b & 7) * 16 + (p & 7) * 2;
+      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = lo;
+    };
+    if (half == 0) {
+      // entries 31..16 from the back end; their dL/dtau terms are written
+      // after the front thread has read these entries' weights
+      float dts[16];
 #pragma unroll
-      for (int b = kCH - 1; b >= 0; --b) {
-        float Tw = 0.0f;
+      for (int b = kCH - 1; b >= 16; --b) step(b, dts[b - 16]);
+      tc::named_barrier(1 + wp, 64);
+#pragma unroll
+      for (int b = 16; b < kCH; ++b) sW[b * kP + p] = dts[b - 16];
+    } else {
+      // T and Q in the middle of the chunk: the transmittance product and
+      // the Q recurrence over entries 31..16
+      float P = 1.0f;
+#pragma unroll
+      for (int b = kCH - 1; b >= 16; --b) {
         if (m & (1u << b)) {
           const float G = sW[b * kP + p];
-          float dt = 0.0f;
           if (G != 0.0f) {
             const float w = __fmul_rn(sR[2 * b + 1].y, G);
             const float one_m_w = 1.0f - w;
-            T = __fdividef(T, one_m_w);  // transmittance in front of entry b
-            Tw = T * w;
-            dt = T * (gam[b] - Q) * G;
+            P *= one_m_w;
             Q = fmaf(w, gam[b], one_m_w * Q);
           }
-          if (__any_sync(0xffffffffu, dt != 0.0f)) {
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
-          }
-          if (lane == 0) tauw[b * 8 + warp] = dt;
-        } else if (lane == 0) {
-          tauw[b * 8 + warp] = 0.0f;
         }
-        __nv_bfloat16 hi, lo;
-        tc::split_bf16(Tw, hi, lo);
-        const uint32_t off = (b >> 3) * kSboA + (p >> 3) * kLboA + (b & 7) * 16 + (p & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = lo;
       }
-    } else {
-      // 2b. next chunk's radiance; previous chunk's dL/ds and dL/dtau
-      float x[16];
-      const bool more = n + 1 < nchunks;
-      if (more) load_rad(n + 1, x);
-      if (!tc::mbar_wait(barG, n & 1, kWaitLimit)) fail();  // gamma(n) has read s
-      if (more) store_rad(x);
-      if (n > 0 && warp < 12) {
-        if (!tc::mbar_wait(barD, (n - 1) & 1, kWaitLimit)) fail();
-        tc::fence_after_sync();
-        drain_dlds(n - 1);
+      T = __fdividef(T, P);
+      tc::named_barrier(1 + wp, 64);
+#pragma unroll
+      for (int b = 15; b >= 0; --b) {
+        float dt;
+        step(b, dt);
+        sW[b * kP + p] = dt;
       }
-      if (n > 0 && warp == 12) drain_tau(n - 1);
+      sTQ[p] = make_float2(T, Q);  // the state at the front end of chunk n
     }
-    // 3. issue dL/ds(n) and gamma(n + 1)
+    if (n > 0) drain_dlds(tmem, n - 1);
+    // 3. issue dL/ds(n); dL/dtau of chunk n; stage s(n + 1)
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -388,27 +421,36 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
       issue_dlds(tmem);
       tc::mma_commit(barD);
       sMisc[3] = n + 1;
-      if (n + 1 < nchunks) {
-        issue_gamma(tmem);
-        tc::mma_commit(barG);
-        sMisc[2] = n + 2;
-      }
+    }
+    {
+      const int b = t >> 4, q = t & 15;
+      float y = 0.0f;
+#pragma unroll
+      for (int r = 0; r < kP / 16; ++r) y += sW[b * kP + q + 16 * r];
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+      if (q == 0 && b < nb && y != 0.0f) atomicAdd(&A.d_tau[sIdx[(n & 3) * kCH + b]], y);
+    }
+    if (more) store_rad(x);  // gamma(n) is complete: s is free
+    if (half == 0) {
+      const float2 tq = sTQ[p];
+      T = tq.x;
+      Q = tq.y;
     }
   }
   cp_async_wait_all();
+  tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
   const bool aborted = sMisc[1] != 0;
   if (!aborted && nchunks > 0) {
     const int nl = nchunks - 1;
-    if (warp >= 8 && warp < 12) {
-      if (tc::mbar_wait(barD, nl & 1, kWaitLimit)) {
-        tc::fence_after_sync();
-        drain_dlds(nl);
-      } else {
-        fail();
-      }
+    if (tc::mbar_wait(barD, nl & 1, kWaitLimit)) {
+      tc::fence_after_sync();
+      drain_dlds(tmem, nl);
+    } else {
+      fail();
     }
-    if (warp == 12) drain_tau(nl);
   }
   if (aborted && t == 256) {
     // let MMAs still in flight finish (bounded) before their memory goes

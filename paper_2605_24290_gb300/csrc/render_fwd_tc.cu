@@ -203,43 +203,46 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
       atomicOr(&sMisc[1], 1u);
       if (a.err) atomicOr(a.err, kErrTimeout);
     }
-    // A[p][b] = T w for the entries of this warp's strip, in depth order
+    // A[p][b] = T w for the entries of this warp's strip, in depth order:
+    // weights four entries at a time (independent, branch-free), then the
+    // transmittance updates in list order
     const float4* sR = sRec0 + (n & 1) * 2 * kCH;
     const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
     const unsigned mask = __any_sync(0xffffffffu, alive) ? __ballot_sync(0xffffffffu, rel) : 0u;
+    auto put_a = [&](int b, float Tw) {
+      __nv_bfloat16 hi, lo;
+      tc::split_bf16(Tw, hi, lo);
+      const uint32_t off = (b >> 3) * kSboA + (t >> 3) * kLboA + (b & 7) * 16 + (t & 7) * 2;
+      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = lo;
+    };
+    for (unsigned z = ~mask; z; z &= z - 1) put_a(__ffs(z) - 1, 0.0f);
+    for (unsigned m = mask; m;) {
+      int bq[4];
 #pragma unroll
-    for (int b0 = 0; b0 < kCH; b0 += 2) {
-      float Tw0 = 0.0f, Tw1 = 0.0f;
-      if (mask & (3u << b0)) {
-        float w0 = 0.0f, w1 = 0.0f, G;
-        bool c0 = false, c1 = false;
-        if (alive) {
-          if (mask & (1u << b0))
-            c0 = pixel_weight(g, sR[2 * b0], sR[2 * b0 + 1], i, jj, fi, fj, &w0, &G);
-          if (mask & (2u << b0))
-            c1 = pixel_weight(g, sR[2 * b0 + 2], sR[2 * b0 + 3], i, jj, fi, fj, &w1, &G);
-        }
-        if (alive && c0) {
-          Tw0 = __fmul_rn(T, w0);
-          T = __fmul_rn(T, __fsub_rn(1.0f, w0));
-          ++ncon;
-          if (T < g.eps_T) alive = false;
-        }
-        if (alive && c1) {
-          Tw1 = __fmul_rn(T, w1);
-          T = __fmul_rn(T, __fsub_rn(1.0f, w1));
-          ++ncon;
-          if (T < g.eps_T) alive = false;
-        }
+      for (int q = 0; q < 4; ++q) {
+        bq[q] = m ? __ffs(m) - 1 : -1;
+        m &= m - 1;
       }
-      __nv_bfloat16 h0, l0, h1, l1;
-      tc::split_bf16(Tw0, h0, l0);
-      tc::split_bf16(Tw1, h1, l1);
-      const uint32_t off = (b0 >> 3) * kSboA + (t >> 3) * kLboA + (b0 & 7) * 16 + (t & 7) * 2;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = h0;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = l0;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off + 16) = h1;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off + 16) = l1;
+      float G[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = bq[q] >= 0 ? bq[q] : bq[0];
+        G[q] = pixel_G(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (bq[q] < 0) break;
+        float Tw = 0.0f;
+        if (alive && G[q] >= 0.0f) {
+          const float w = __fmul_rn(sR[2 * bq[q] + 1].y, G[q]);
+          Tw = __fmul_rn(T, w);
+          T = __fmul_rn(T, __fsub_rn(1.0f, w));
+          ++ncon;
+          if (T < g.eps_T) alive = false;
+        }
+        put_a(bq[q], Tw);
+      }
     }
     if (more) store_rad((n + 1) & 1, x);
     tc::fence_smem_to_async();

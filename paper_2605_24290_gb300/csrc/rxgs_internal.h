@@ -148,6 +148,12 @@ void launch_render_bwd(const BackwardArgs& a, cudaStream_t s);
 void launch_vis_backward(const BackwardArgs& A, const float* rad_rm, const float* gu,
                          float* gamma, float* W, float* grad_radiance, cudaStream_t s);
 
+// ------------------------------------------------ Stage II L1 term (App. E.3)
+// loss[0] = mean |a_i - y_i| over n values (a = |R| of spectra [n][2], or
+// RSSI [n]) and grad = its derivative; part holds nparts block sums.
+int l1_loss_blocks();
+void launch_l1_loss(bool spectra, const float* values, const float* target, size_t n, float* loss,
+                    float* grad, float* part, int nparts, cudaStream_t s);
 // ------------------------------------------ occupancy grid and probes (App. E.5)
 // box[6] = (lo, D) and grid[res^3] from the scene's Gaussians.
 void launch_occ_build(const float4* geom, int K, int res, float* box, float* grid, cudaStream_t s);
@@ -156,23 +162,50 @@ void launch_occ_probes(const float4* geom, int K, const float* rx, int N, int re
                        const float* box, const float* grid, float2* feat, cudaStream_t s);
 
 // ------------------------------------------ FLE directional radiance (App. E.2)
-// rad[v][k][stride] columns 2j, 2j+1 (v < M, rad_view floats per view) from
-// coefficients [N][K][2][(lmax+1)^2] and the transmitters tx[M][3].  With
-// base != NULL the coefficients are not read: receiver j's coefficient l of
-// Gaussian k is (1 + a_jl) base_kl + b_jl (complex, Eq. film_apply), base
-// [K][2][L] and ab[N][L] = (a.re, a.im, b.re, b.im).
-void launch_fle_radiance(const float* coeffs, int N, int K, int lmax, const float4* geom,
-                         const float* tx, int M, int stride, size_t rad_view, float* rad,
-                         cudaStream_t s, const float* base = nullptr,
-                         const float4* ab = nullptr);
-// The backward of the FiLM form above: grad_base[K][2][L] += sum_j conj(1 + a_jl) G_jkl
-// (grad_base may be NULL) and d_ab[N][L] += (conj(base_kl) G_jkl, G_jkl) summed
-// over k with float atomics, where G_jkl = sum_v d_rad[v][k][2j..] conj(Y_v,k,l).
-void launch_film_fle_backward(const float* d_rad, int N, int K, int lmax, const float4* geom,
-                              const float* tx, int M, int stride, size_t rad_view,
-                              const float* base, const float4* ab, float* grad_base,
-                              float* d_ab, cudaStream_t s);
+// N_l|m| by component index l*l + l + m, l <= 9.
+struct FleNorm {
+  float n[100];
+};
+FleNorm fle_norm_table(int lmax);
+// The tensor-core coefficient gradient (fle_bwd_tc.cu): arguments as
+// launch_fle_backward below; err receives kErrTimeout.
+// With accumulate false grad is written, not added to.
+void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax, const float4* geom,
+                            const float* tx, int M, int stride, size_t rad_view, float* grad,
+                            bool accumulate, cudaStream_t s, unsigned* err);
+// The tensor-core contraction of the FLE radiance (fle_tc.cu) for
+// coefficients [N][K][2][L]: rad[v][k][stride] columns 2j, 2j+1 (v < M,
+// rad_view floats per view); err receives kErrTimeout.
+void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax, const float4* geom,
+                            const float* tx, int M, int stride, size_t rad_view, float* rad,
+                            cudaStream_t s, unsigned* err);
+// The global FiLM branch over the FLE coefficients (fle_tc.cu): the
+// conditioned coefficients out[N][K][2][L] = (1 + a_jl) base[K][2][L] + b_jl
+// (Eq. film_apply, ab[N][L] = (a.re, a.im, b.re, b.im)), and the fold of
+// their gradient G[N][K][2][L] into grad_base[K][2][L] += sum_j conj(1 + a) G
+// and d_ab[N][L][4] += sum_k (conj(base) G, G) (either may be NULL).
+// loc[N][K] (or NULL): the local branch's (alpha, beta) per pair (Eq.
+// combined_local), applied as (1 + alpha) c + beta.
+void launch_film_coeffs(const float* base, const float4* ab, const float4* loc, int N, int K,
+                        int lmax, float* out, cudaStream_t s);
+void launch_film_fold(const float* G, int N, int K, int lmax, const float* base,
+                      const float4* ab, float* grad_base, float* d_ab, cudaStream_t s);
 
+// ------------------ local branch composed with the FiLM branch (film_local.cu)
+// The scene MLP's local branch supports the composition for 64 hidden units
+// and one channel.  loc[N][K] = (alpha.re, alpha.im, beta.re, beta.im) of
+// every (receiver, Gaussian) pair (feat = occlusion inputs or NULL).
+bool local_branch_supported(int hidden, int C);
+void launch_local_factors(const float* mlp, const float* rx, int N, const float4* geom, int K,
+                          const float2* feat, float4* loc, cudaStream_t s);
+// From the composed coefficients' gradient G[N][K][2][L] (overwritten in
+// place by conj(1 + alpha) G, the FiLM-modulated coefficients' gradient):
+// d_loc[N][K] (scratch) and grad_mlp's local-branch entries += their
+// gradient (grad_mlp may be NULL).
+void launch_film_local_backward(float* G, const float* base, const float4* ab, const float4* loc,
+                                const float* mlp, const float* rx, int N, const float4* geom,
+                                int K, int lmax, const float2* feat, float4* d_loc,
+                                float* grad_mlp, cudaStream_t s);
 // ------------------------------------------ global FiLM MLP over FLE components
 // Packed parameters (float32): omega[nw][3], embed[L][dc], w1[D][din], b1[D],
 // w2[D][D], b2[D], w3[4][D], b3[4] with din = 2 nw + 2 + dc (Eq. rx_enc, film).
@@ -190,10 +223,7 @@ void launch_film_global(const float* film, const FilmDims& f, const float* rx, i
 size_t film_backward_tmp_floats(const FilmDims& f, int N);
 void launch_film_backward(const float* film, const FilmDims& f, const float* rx, int N,
                           const float4* d_ab, float* tmp, float* grad_film, cudaStream_t s);
-// grad[N][K][2][L] += sum_v d_rad[v][k][2j..] conj(Y_v,k)
-void launch_fle_backward(const float* d_rad, int N, int K, int lmax, const float4* geom,
-                         const float* tx, int M, int stride, size_t rad_view, float* grad,
-                         cudaStream_t s);
+
 
 // ------------------------------------------ visibility weights (Eq. render_reorder)
 // W[M][K] = sum over each view's pixels of T_k w_k (zeroed first).

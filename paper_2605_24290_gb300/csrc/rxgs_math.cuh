@@ -48,6 +48,27 @@ __device__ __forceinline__ float exp32(float x) {
   return __fmul_rn(p, s);
 }
 
+// exp32 without its range checks, for -87 < x <= 88 (the compositing weight
+// exp(-q/2) with q in [0, q_max]): the same operations, so the same result
+// bits there; outside that range the value is meaningless and callers
+// discard it.
+__device__ __forceinline__ float exp32_inrange(float x) {
+  const float t = __fmul_rn(x, kLog2e);
+  const float n = rintf(t);
+  float r = __fmaf_rn(-n, kLn2Hi, x);
+  r = __fmaf_rn(-n, kLn2Lo, r);
+  float p = 1.0f / 5040.0f;
+  p = __fmaf_rn(p, r, 1.0f / 720.0f);
+  p = __fmaf_rn(p, r, 1.0f / 120.0f);
+  p = __fmaf_rn(p, r, 1.0f / 24.0f);
+  p = __fmaf_rn(p, r, 1.0f / 6.0f);
+  p = __fmaf_rn(p, r, 0.5f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  const float s = __int_as_float((static_cast<int>(n) + 127) << 23);
+  return __fmul_rn(p, s);
+}
+
 __device__ __forceinline__ float atan2_32(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
   const float mx = ax > ay ? ax : ay;

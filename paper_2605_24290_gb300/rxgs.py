@@ -47,7 +47,7 @@ class RenderDesc(ctypes.Structure):
                 ("fle_coeffs", ctypes.c_void_p), ("fle_lmax", ctypes.c_int),
                 ("fle_base", ctypes.c_void_p), ("film", ctypes.c_void_p),
                 ("film_nfreq", ctypes.c_int), ("film_embed", ctypes.c_int),
-                ("film_hidden", ctypes.c_int)]
+                ("film_hidden", ctypes.c_int), ("film_local", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):
@@ -108,6 +108,7 @@ SIGNATURES = {
     "rxgs_serve_inject_fault": (I, [P, I]),
     "rxgs_serve_stop": (I, [P]),
     "rxgs_sync": (I, [P, P]),
+    "rxgs_l1_loss": (I, [P, I, P, P, ctypes.c_size_t, P, P, P]),
     "rxgs_film_param_count": (ctypes.c_int64, [I, I, I, I]),
     "rxgs_film_eval": (I, [P, P, I, I, I, I, P, I, P, P]),
 }
@@ -226,7 +227,7 @@ class Context:
     """One rxgs context on one CUDA device (argument marshalling only)."""
 
     def __init__(self, H=90, W=360, theta0_deg=0.0, step_deg=1.0, tile_h=16, tile_w=16,
-                 eps_T=1e-4, q_max=9.0, r_near=0.05, cols_per_cta=0, deterministic=1,
+                 eps_T=1e-4, q_max=9.0, r_near=0.05, cols_per_cta=0, deterministic=0,
                  mem_budget=0, device=None):
         import torch
         if not torch.cuda.is_available():
@@ -293,12 +294,14 @@ class Context:
         self._check(self.lib.rxgs_release_views(self.h, U64(views), _stream(stream)))
 
     @staticmethod
-    def _desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims):
+    def _desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims,
+              film_local=False):
         nf, ne, nh = film_dims if film_dims is not None else (0, 0, 0)
         if film is not None and film_dims is not None:
             check_film_length(film.numel(), int(nf), int(ne), int(nh), int(fle_lmax))
         return RenderDesc(int(kind), _f32(radiance), int(reduce_path), _f32(fle_coeffs),
-                          int(fle_lmax), _f32(fle_base), _f32(film), int(nf), int(ne), int(nh))
+                          int(fle_lmax), _f32(fle_base), _f32(film), int(nf), int(ne), int(nh),
+                          1 if film_local else 0)
 
     def film_eval(self, film, film_dims, lmax, rx, N, ab, stream=None):
         """ab[N, L, 4] = (a.re, a.im, b.re, b.im) of the global FiLM branch."""
@@ -313,16 +316,18 @@ class Context:
 
     def render_views(self, views, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
                      ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0,
-                     fle_base=None, film=None, film_dims=None, stream=None):
-        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims)
+                     fle_base=None, film=None, film_dims=None, film_local=False, stream=None):
+        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims,
+                       film_local)
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render_views(self.h, U64(views), _f32(rx), int(N),
                                                ctypes.byref(d), ctypes.byref(o), _stream(stream)))
 
     def render(self, scene, tx, rx, N, kind, radiance=None, spectra=None, rssi=None, csi=None,
                ncontrib=None, tfinal=None, reduce_path=0, fle_coeffs=None, fle_lmax=0,
-               fle_base=None, film=None, film_dims=None, stream=None):
-        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims)
+               fle_base=None, film=None, film_dims=None, film_local=False, stream=None):
+        d = self._desc(kind, radiance, reduce_path, fle_coeffs, fle_lmax, fle_base, film, film_dims,
+                       film_local)
         o = Outputs(_f32(spectra), _f32(rssi), _f32(csi), _ptr(ncontrib), _f32(tfinal))
         self._check(self.lib.rxgs_render(self.h, U64(scene), _f32(tx), int(tx.shape[0]),
                                          _f32(rx), int(N), ctypes.byref(d), ctypes.byref(o),
@@ -332,8 +337,10 @@ class Context:
                         grad_csi=None, grad_rssi=None, fwd_csi=None,
                         grad_radiance=None, grad_opacity=None, grad_base=None, grad_mlp=None,
                         fle_coeffs=None, fle_lmax=0, grad_fle=None, fle_base=None, film=None,
-                        film_dims=None, grad_fle_base=None, grad_film=None, stream=None):
-        d = self._desc(kind, radiance, 0, fle_coeffs, fle_lmax, fle_base, film, film_dims)
+                        film_dims=None, grad_fle_base=None, grad_film=None, film_local=False,
+                        stream=None):
+        d = self._desc(kind, radiance, 0, fle_coeffs, fle_lmax, fle_base, film, film_dims,
+                       film_local)
         c = Cotangents(_f32(grad_spectra), _f32(grad_csi), _f32(grad_rssi), _f32(fwd_csi))
         g = Grads(_f32(grad_radiance), _f32(grad_opacity), _f32(grad_base), _f32(grad_mlp),
                   _f32(grad_fle), _f32(grad_fle_base), _f32(grad_film))
@@ -451,6 +458,16 @@ class Context:
         library's fixed scratch array holds the partial sums)."""
         self._check(self.lib.rxgs_render_csi_noalloc(self.h, U64(views), _f32(radiance), int(N),
                                                      _f32(csi), _f32(rssi), _stream(stream)))
+
+    def l1_loss(self, kind, values, target, loss, grad, stream=None):
+        """Stage II L1 term and its cotangent in one pass (device tensors):
+        kind OUT_SPECTRA: values = spectra [..., 2], target = amplitudes [...];
+        kind OUT_RSSI: values = RSSI, target the same shape.  Writes the mean
+        absolute difference into loss[0] and its gradient into grad (the
+        shape of values)."""
+        n = int(target.numel())
+        self._check(self.lib.rxgs_l1_loss(self.h, int(kind), _f32(values), _f32(target), n,
+                                          _f32(loss), _f32(grad), _stream(stream)))
 
     def sync(self, stream=None):
         self._check(self.lib.rxgs_sync(self.h, _stream(stream)))

@@ -240,3 +240,84 @@ def test_film_arguments_are_checked(torch, rx):
     ctx.sync()
     assert bool(torch.isfinite(csi).all())
     ctx.release_views(views)
+
+
+@pytest.mark.parametrize("occupancy", [False, True])
+def test_film_local_branch_matches_oracle(torch, rx, oracle, occupancy):
+    """Eq. combined_local over the FLE components: the global FiLM branch and
+    the scene MLP's local branch (with the occlusion probes when the scene
+    has an occupancy grid) composed per (receiver, Gaussian, component).
+    Forward spectra and CSI, and the gradients of the base coefficients, the
+    opacity, every FiLM parameter and the local branch against the oracle."""
+    K, M, N, lmax = 1200, 2, 4, 3
+    rng, sc, tx, r, film, base, g, ctx, views = _render_case(torch, rx, oracle, 820, K, M, N,
+                                                              lmax, F=2, dc=4, D=16)
+    ctx.release_views(views)
+    mlp = S.draw_mlp(rng, 1, final_scale=0.5)
+    flat = S.flatten_mlp(mlp, 1)
+    h = upload(ctx, sc, torch, base=S.draw_base(rng, K, 1), mlp_flat=flat, C=1)
+    occ = None
+    if occupancy:
+        ctx.build_occupancy(h, 64)
+        occ = oracle.occupancy_grid(sc, 64)
+    views = ctx.prepare(h, dev(tx, torch))
+    dims = rx.film_sizes(film)
+    fd = dev(rx.pack_film(film), torch)
+    bd, rd = dev(base, torch), dev(r, torch)
+    spec = torch.zeros((M, N, g.H, g.W, 1, 2), device="cuda")
+    csi = torch.zeros((M, N, 1, 2), device="cuda")
+    kw = dict(fle_lmax=lmax, fle_base=bd, film=fd, film_dims=dims, film_local=True)
+    ctx.render_views(views, rd, N, rx.OUT_SPECTRA | rx.OUT_CSI, spectra=spec, csi=csi, **kw)
+    gs = rng.normal(size=(M, N, g.H, g.W, 1, 2)).astype(np.float32)
+    d_base = torch.zeros_like(bd)
+    d_film = torch.zeros_like(fd)
+    d_mlp = torch.zeros(flat.shape[0], device="cuda")
+    d_tau = torch.zeros(K, device="cuda")
+    ctx.render_backward(views, rd, N, rx.OUT_SPECTRA, grad_spectra=dev(gs, torch),
+                        grad_opacity=d_tau, grad_fle_base=d_base, grad_film=d_film,
+                        grad_mlp=d_mlp, **kw)
+    ctx.sync()
+    mlp64 = {k: v.astype(np.float64) for k, v in mlp.items()}
+    coeffs = oracle.film_local_fle_coeffs(film, mlp64, base, r, sc.means, lmax, occ=occ)
+    ab = oracle.film_global(film, r, lmax)
+    alpha, _ = oracle.local_factors(mlp64, r, sc.means, occ)
+    amod = np.hypot(1.0 + ab[..., 0], ab[..., 1])                       # |1 + a| [N, L]
+    almod = np.abs(1.0 + alpha)                                          # |1 + alpha| [N, K]
+    gc = np.zeros(coeffs.shape)
+    scale_c = np.zeros(coeffs.shape)
+    ref_t, abs_t = np.zeros(K), np.zeros(K)
+    for v in range(M):
+        rad = oracle.fle_radiance(coeffs, sc.means, tx[v], lmax)
+        o = oracle.render_view(g, sc, tx[v], rad)
+        a = o["absacc"]
+        assert norm_err(spec[v].cpu().numpy(), o["spectra"], a) <= TOL
+        assert norm_err(csi[v].cpu().numpy(), oracle.csi(o["spectra"]), a.sum(axis=(1, 2))) <= TOL
+        gr, gt, ar, at = oracle.backward_view(g, sc, tx[v], rad, gs[v].astype(np.float64),
+                                              want_abs=True)
+        gc += oracle.fle_backward(gr, sc.means, tx[v], lmax)
+        Ya = np.abs(oracle.fle_basis(sc.means, tx[v], lmax))
+        scale_c += (ar[:, :, 0, 0] + ar[:, :, 0, 1])[:, :, None, None] * Ya[None, :, None, :]
+        ref_t += gt
+        abs_t += at
+    ref = oracle.film_local_fle_backward(film, mlp64, base, r, sc.means, lmax, gc, occ=occ)
+    # base: dL/dphi = sum_j conj(1 + a) conj(1 + alpha) G', scaled by the |.| chain
+    scale_b = (amod[:, None, None, :] * almod[:, :, None, None] * scale_c).sum(axis=0)
+    e_b = float((np.abs(d_base.cpu().numpy() - ref["base"]) / (scale_b + 1e-30)).max())
+    assert e_b <= TOL, e_b
+    e_t = float((np.abs(d_tau.cpu().numpy() - ref_t) / (abs_t + 1e-30)).max())
+    assert e_t <= TOL, e_t
+    got_film = rx.unpack_film(d_film.cpu().numpy(), *dims, lmax)
+    got_mlp = S.unflatten_mlp(d_mlp.cpu().numpy(), 1)
+    checks = [(got_film[k], ref[k], k) for k in rx.FILM_FIELDS] + \
+             [(got_mlp[k], ref[k], k) for k in ("l_w1", "l_b1", "l_w2", "l_b2")]
+    for got, want, k in checks:
+        m = float(np.abs(want).max())
+        assert m > 0.0, k
+        e = float(np.abs(got - want).max()) / m
+        assert e <= TOL, (k, e)
+    for k in ("g_w1", "g_b1", "g_w2", "g_b2"):            # the global MLP branch is not used
+        assert float(np.abs(got_mlp[k]).max()) == 0.0, k
+    with pytest.raises(rx.RxgsError):                      # film_local needs the FiLM path
+        ctx.render_views(views, rd, N, rx.OUT_SPECTRA, spectra=spec, fle_lmax=lmax,
+                         fle_coeffs=torch.zeros((N, K, 2, 16), device="cuda"), film_local=True)
+    ctx.release_views(views)

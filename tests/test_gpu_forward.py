@@ -305,6 +305,8 @@ def test_invalid_arguments_are_refused(torch, rx):
         ctx.render(h, tx, dev(w["rx"], torch), 8, rx.OUT_RSSI, rssi=torch.zeros(8, device="cuda"))
     with pytest.raises(rx.RxgsError):
         rx.Context(tile_h=10, tile_w=10)
+    with pytest.raises(rx.RxgsError):          # no bit-reproducible backward is offered
+        rx.Context(deterministic=1)
 
 
 def test_mlp_radiance_full_size_sampled(torch, rx, oracle):

@@ -236,3 +236,48 @@ def test_stage2_step_matches_oracle(torch, rx, oracle):
     for name in mlp0:
         check_update(mlp0[name], new_m[name], ref["params"][name], ref["grad_mlp"][name],
                      TOL * (chain[name] + amb[name] / TOL), lr_m, m1[name], name)
+
+
+@pytest.mark.parametrize("kind_name", ["OUT_SPECTRA", "OUT_RSSI"])
+def test_l1_loss_kernel_matches_oracle(torch, rx, oracle, kind_name):
+    """rxgs_l1_loss (one pass: loss and cotangent) against the oracle's L1
+    terms on 1,000,003 values, including exact zeros (an empty pixel has
+    |R| = 1e-4) and ties |R| = y (sign 0)."""
+    rng = np.random.default_rng(806)
+    kind = getattr(rx, kind_name)
+    n = 1_000_003
+    ctx = rx.Context()
+    if kind == rx.OUT_SPECTRA:
+        vals = rng.normal(size=(n, 2)).astype(np.float32)
+        vals[:1000] = 0.0
+        y = np.abs(rng.normal(size=n)).astype(np.float32)
+        y[:500] = np.sqrt(np.float32(1e-8))            # float32 |R| of an empty pixel
+        L_ref, g_ref = oracle.l1_amplitude(vals.astype(np.float64), y.astype(np.float64))
+        shape = (n, 2)
+    else:
+        vals = np.abs(rng.normal(size=n)).astype(np.float32)
+        y = np.abs(rng.normal(size=n)).astype(np.float32)
+        y[:700] = vals[:700]
+        d = vals.astype(np.float64) - y
+        L_ref, g_ref = float(np.abs(d).mean()), np.sign(d) / n
+        shape = (n,)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(shape, device="cuda")
+    ctx.l1_loss(kind, dev(vals, torch), dev(y, torch), loss, grad)
+    ctx.sync()
+    g = grad.cpu().numpy().astype(np.float64)
+    # each |a - y| carries a float32 rounding of a; the mean of n terms in
+    # float32 sums adds at most a few ulps per level of the block tree
+    scale = np.abs(vals).sum(-1).mean() if kind == rx.OUT_SPECTRA else np.abs(vals).mean()
+    assert abs(float(loss.item()) - L_ref) <= 1e-5 * scale + 1e-6 * L_ref
+    if kind == rx.OUT_SPECTRA:
+        # sign(|R| - y) is decided in float32 on the GPU: where |R| is within
+        # float32 reach of y either sign is admitted (the cotangent is bounded)
+        a = oracle.amplitude(vals.astype(np.float64))
+        sure = np.abs(a - y) > 1e-5 * np.maximum(a, 1e-4)
+        np.testing.assert_allclose(g[sure], g_ref[sure], rtol=1e-5, atol=1e-6 / n)
+        assert np.all(np.abs(g[~sure]) <= (1 + 1e-5) / n)
+    else:
+        # float32 differences of float32 values have exact signs
+        np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=0)
+    ctx.close()

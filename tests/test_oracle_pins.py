@@ -994,3 +994,78 @@ def test_film_degree_zero_radiance_closed_form(oracle):
     np.testing.assert_allclose(s[..., 0], ref.real, rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(s[..., 1], ref.imag, rtol=1e-13, atol=1e-15)
 
+
+
+# ------------------- Eq. combined_local over FLE components (Sec. 3.3.2)
+
+def _film_local_case(rng, lmax=2, K=4, N=3, out_scale=1.0):
+    film = {k: v.astype(np.float64) for k, v in
+            S.draw_film(rng, lmax, F=2, dc=3, D=5, out_scale=out_scale).items()}
+    params = {k: v.astype(np.float64) for k, v in S.draw_mlp(rng, 1, final_scale=0.5).items()}
+    base = S.draw_fle_base(rng, K, lmax).astype(np.float64)
+    rx = rng.uniform(-1.0, 1.0, size=(N, 3))
+    means = rng.uniform(-2.0, 2.0, size=(K, 3))
+    return film, params, base, rx, means
+
+
+def test_film_local_zero_final_layer_is_film_only(oracle):
+    """A local branch whose final layer is zero is the identity (Sec. 3.3.2:
+    zero-initialised final layers): the composed coefficients equal the
+    FiLM-modulated ones exactly."""
+    rng = np.random.default_rng(50)
+    lmax = 3
+    film, params, base, rx, means = _film_local_case(rng, lmax=lmax)
+    params["l_w2"][:] = 0.0
+    params["l_b2"][:] = 0.0
+    got = oracle.film_local_fle_coeffs(film, params, base, rx, means, lmax)
+    ref = oracle.film_fle_coeffs(film, base, rx, lmax)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_film_local_complex_affine_hand_value(oracle):
+    """With the local branch's output fixed by its bias (alpha = 0.3 - 0.2i,
+    beta = -0.1 + 0.4i), one coefficient (1 + a) phi + b = 1.5 + 2i becomes
+    (1.3 - 0.2i)(1.5 + 2i) + (-0.1 + 0.4i) = (1.95 + 0.4) + (2.6 - 0.3)i
+    - 0.1 + 0.4i = 2.25 + 2.7i: a complex product, not an elementwise one
+    (which would give 1.85 + 2.0i)."""
+    rng = np.random.default_rng(51)
+    lmax = 0
+    film, params, base, rx, means = _film_local_case(rng, lmax=lmax, K=1, N=1)
+    film["w3"][:] = 0.0
+    film["b3"][:] = 0.0                                  # a = b = 0: c = phi_base
+    base[0, :, 0] = [1.5, 2.0]
+    params["l_w2"][:] = 0.0
+    params["l_b2"][:] = [0.3, -0.2, -0.1, 0.4]           # (alpha.re, alpha.im, beta.re, beta.im)
+    got = oracle.film_local_fle_coeffs(film, params, base, rx, means, lmax)
+    assert got[0, 0, 0, 0] == pytest.approx(2.25, abs=1e-14)
+    assert got[0, 0, 1, 0] == pytest.approx(2.7, abs=1e-14)
+
+
+def test_film_local_backward_matches_finite_differences(oracle):
+    """The local branch's parameters, the base coefficients and FiLM
+    parameters against central differences of film_local_fle_coeffs."""
+    rng = np.random.default_rng(52)
+    lmax, K, N = 2, 4, 3
+    film, params, base, rx, means = _film_local_case(rng, lmax=lmax, K=K, N=N)
+    gc = rng.normal(size=(N, K, 2, oracle.fle_count(lmax)))
+    got = oracle.film_local_fle_backward(film, params, base, rx, means, lmax, gc)
+
+    def loss():
+        return float((gc * oracle.film_local_fle_coeffs(film, params, base, rx, means,
+                                                        lmax)).sum())
+
+    h = 1e-6
+    groups = [("l_w1", params), ("l_b1", params), ("l_w2", params), ("l_b2", params),
+              ("base", None), ("w3", film), ("b1", film), ("omega", film)]
+    for name, owner in groups:
+        src = base if owner is None else owner[name]
+        ref = np.zeros_like(got[name])
+        for idx in np.ndindex(src.shape):
+            keep = src[idx]
+            src[idx] = keep + h
+            lp = loss()
+            src[idx] = keep - h
+            lm = loss()
+            src[idx] = keep
+            ref[idx] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(got[name], ref, rtol=1e-6, atol=1e-7, err_msg=name)
