@@ -460,7 +460,7 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   {
     Stage sg(ctx, "sort", st);
     radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, 31 + v->tile_bits + v->view_bits,
-                     sort_tmp, &in_alt, st);
+                     sort_tmp, &in_alt, st, nullptr, ctx->d_err);
   }
   if (in_alt) {
     std::swap(v->keys, keys_alt);
@@ -568,16 +568,34 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
     launch_film_coeffs(d->fle_base, ab, loc, N, s->K, d->fle_lmax, coeffs, st);
     dfree(loc, st);
     dfree(feat, st);
+    unsigned char* image = nullptr;
+    if (dalloc(&image, fle_basis_image_bytes(s->K, v->M), st) != cudaSuccess) {
+      dfree(ab, st); dfree(coeffs, st);
+      return fail(ctx, RXGS_E_OOM, "FLE basis image");
+    }
+    {
+      Stage sb(ctx, "fle_basis", st);  // within the radiance stage
+      launch_fle_basis_image(s->geom, v->tx, s->K, v->M, d->fle_lmax, image, st);
+    }
     cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
-    launch_fle_radiance_tc(coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+    launch_fle_radiance_tc(coeffs, N, s->K, d->fle_lmax, image, v->M, stride,
                            static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
+    dfree(image, st);
     dfree(ab, st);
     dfree(coeffs, st);
   } else if (d->fle_coeffs) {
+    unsigned char* image = nullptr;
+    if (dalloc(&image, fle_basis_image_bytes(s->K, v->M), st) != cudaSuccess)
+      return fail(ctx, RXGS_E_OOM, "FLE basis image");
+    {
+      Stage sb(ctx, "fle_basis", st);  // within the radiance stage
+      launch_fle_basis_image(s->geom, v->tx, s->K, v->M, d->fle_lmax, image, st);
+    }
     // pad columns of every row stay zero
     cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
-    launch_fle_radiance_tc(d->fle_coeffs, N, s->K, d->fle_lmax, s->geom, v->tx, v->M, stride,
+    launch_fle_radiance_tc(d->fle_coeffs, N, s->K, d->fle_lmax, image, v->M, stride,
                            static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
+    dfree(image, st);
   } else if (d->radiance) {
     launch_radiance_transpose(d->radiance, N, s->K, s->C, stride, rad, st);
   } else {
@@ -967,6 +985,7 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     const FilmDims f = desc_film_dims(d);
     float4 *ab = nullptr, *d_ab = nullptr, *loc = nullptr, *d_loc = nullptr;
     float *ftmp = nullptr, *G = nullptr;
+    unsigned char* image = nullptr;
     float2* feat = nullptr;
     const size_t S = static_cast<size_t>(N) * f.L;
     const size_t NK = static_cast<size_t>(N) * K;
@@ -976,12 +995,13 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     // the conditioned coefficients' gradient [N][K][2][L], written (not
     // accumulated) by the tensor-core contraction, then folded
     if (e == cudaSuccess) e = dalloc(&G, S * K * 2, st);
+    if (e == cudaSuccess) e = dalloc(&image, fle_basis_image_bytes(K, M), st);
     if (e == cudaSuccess && d->film_local) e = dalloc(&loc, NK, st);
     if (e == cudaSuccess && d->film_local) e = dalloc(&d_loc, NK, st);
     if (e == cudaSuccess && d->film_local && s->occ) e = dalloc(&feat, NK, st);
     auto free_film = [&]() {
       dfree(ab, st); dfree(d_ab, st); dfree(ftmp, st); dfree(G, st);
-      dfree(loc, st); dfree(d_loc, st); dfree(feat, st);
+      dfree(loc, st); dfree(d_loc, st); dfree(feat, st); dfree(image, st);
     };
     if (e != cudaSuccess) {
       free_film();
@@ -992,8 +1012,12 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
       Stage sg(ctx, "fle_film_bwd", st);
       cudaMemsetAsync(d_ab, 0, sizeof(float4) * S, st);
       launch_film_global(d->film, f, rx, N, ab, st);
-      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view, G,
-                             false, st, ctx->d_err);
+      {
+        Stage sb(ctx, "fle_basis", st);  // within the backward stage
+        launch_fle_basis_image(s->geom, v->tx, K, M, d->fle_lmax, image, st);
+      }
+      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, image, M, stride, rad_view, G, false, st,
+                             ctx->d_err);
       if (d->film_local) {
         // the local branch (Eq. combined_local): its gradient, and G becomes
         // the FiLM-modulated coefficients' gradient
@@ -1012,9 +1036,20 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
     free_film();
   } else if (fle) {
     Stage sg(ctx, "fle_bwd", st);
-    if (gr->grad_fle)
-      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, s->geom, v->tx, M, stride, rad_view,
-                             gr->grad_fle, true, st, ctx->d_err);
+    if (gr->grad_fle) {
+      unsigned char* image = nullptr;
+      if (dalloc(&image, fle_basis_image_bytes(K, M), st) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, RXGS_E_OOM, "backward (FLE basis image)");
+      }
+      {
+        Stage sb(ctx, "fle_basis", st);  // within the backward stage
+        launch_fle_basis_image(s->geom, v->tx, K, M, d->fle_lmax, image, st);
+      }
+      launch_fle_backward_tc(d_rad, N, K, d->fle_lmax, image, M, stride, rad_view, gr->grad_fle,
+                             true, st, ctx->d_err);
+      dfree(image, st);
+    }
   } else {
     MlpParams m{s->mlp, s->hidden, C, 0};
     g_base = gr->grad_base;

@@ -265,7 +265,7 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   const uint32_t* n_dev = p->offsets + MK;
   bool in_alt = false;
   radix_sort_pairs(p->keys, p->vals, p->keys_alt, p->vals_alt, p->I_cap,
-                   31 + p->tile_bits + p->view_bits, p->sort_tmp, &in_alt, st, n_dev);
+                   31 + p->tile_bits + p->view_bits, p->sort_tmp, &in_alt, st, n_dev, ctx->d_err);
   p->sorted_in_alt = in_alt;
   uint64_t* keys = in_alt ? p->keys_alt : p->keys;
   uint32_t* vals = in_alt ? p->vals_alt : p->vals;

@@ -1,214 +1,94 @@
 // fle_bwd_tc.cu -- the coefficient gradient of the FLE radiance (App. E.2;
 // the backward of Algorithm 1 eval_fle) as a tcgen05 contraction per
-// Gaussian:
-//   dL/d(a + i b)_jk,l = G_jkl = sum_v g[v][k][j] conj(Y_vkl)
-// with g the gradient of the per-view radiance.  Real-ified with the
-// cotangent rows interleaved (row 2j = Re g_j, row 2j + 1 = Im g_j) as the A
-// operand (M = 128 rows of 64 receivers, K = 32 views) and the basis of the
-// views as two B operands (N = 112 components: Re Y, Im Y):
-//   Q1 = g Yr,  Q2 = g Yi   (float32 in TMEM, accumulated over view groups)
-//   Re G_j = Q1[2j] + Q2[2j+1],  Im G_j = Q1[2j+1] - Q2[2j]
-// (lanes 2j and 2j + 1 exchange one value).  Operands split into two bf16
-// terms (three MMAs per product, tc_common.cuh).  The finished tile goes
-// through shared memory so that the gradient rows are read, added to and
-// written back coalesced (or only written, when the caller asks for the
-// gradient itself rather than an accumulation).
+// Gaussian, over the folded components (fle_tc.cuh).  With g the gradient
+// of the per-view radiance s = sum_P Yr c+ + i sum_Q Yi c-:
+//   D+[2j] = sum_v Re g_vj Yr_v,  D+[2j+1] = sum_v Im g_vj Yr_v   (dL/dRe c+, dL/dIm c+)
+//   D-[2j] = sum_v Im g_vj Yi_v,  D-[2j+1] = -sum_v Re g_vj Yi_v  (dL/dRe c-, dL/dIm c-)
+//   dL/dc_{l,+m} = D+ + D-,  dL/dc_{l,-m} = D+ - D-,  dL/dc_{l,0} = D+
+// The A operands (M = 128 rows 2j, 2j + 1, K = 32 views) are the cotangent
+// rows and their swapped copy (row 2j = Im g_j, row 2j + 1 = -Re g_j), split
+// into bf16 terms and stored in tensor memory; the B operand is the step's
+// basis read MN-major (N = components, K = views); D+ and D- accumulate over
+// a job's view groups in tensor memory.
 //
-// One CTA per SM (512 threads) walks jobs (Gaussian, receiver group, view
-// group); a group (Gaussian, receiver group) accumulates over its view
-// groups in one of two TMEM sets (224 columns each), and its tile is written
-// out while the next group's MMAs run.  Operand buffers are double-buffered
-// by job with one mbarrier each; every wait is bounded (kErrTimeout).
+// Warp-specialised like the forward (fle_tc.cu), on the same basis image:
+//   warp 0      one bulk copy of the step's basis block per step;
+//   warps 4-7   load the cotangent of a step (lane = row; the loads of the
+//               next step are in flight while this one is split and stored);
+//   warp 1      one thread issues the MMAs;
+//   warps 8-11  read a job's D+ and D- (tcgen05.ld), unfold them into the
+//               (lmax + 1)^2 components of the lane's half-row, stage the
+//               job's rows in shared memory as one tensor-map box and add it
+//               to (or store it into) the gradient with one TMA reduction.
+// Every wait is bounded (kErrTimeout).  A degree whose half-rows are not
+// whole 16-byte units or an unaligned gradient array is written directly.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 
-#include "fle_basis.cuh"
+#include "fle_tc.cuh"
 #include "rxgs_internal.h"
 #include "tc_common.cuh"
 
 namespace rxgs {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kRx = 64;
-constexpr int kViews = 32;
-constexpr int kLp = 112;
-constexpr int kOct = kLp / 8;
-// A[row][v] read MN-major: core (v/8, row/8) at (v/8) * kAK + (row/8) * kAM,
-// 8 consecutive rows per 16-byte core row (one view)
-constexpr uint32_t kAM = 144, kAK = 16 * kAM;
-constexpr uint32_t kABytes = 4 * kAK;
-// B[v][l] read MN-major: core (v/8, l/8) at (v/8) * kBK + (l/8) * 128
-constexpr uint32_t kBN = 128, kBK = kOct * 128;
-constexpr uint32_t kBBytes = 4 * kBK;
-constexpr uint32_t kSetBytes = 2 * kABytes + 4 * kBBytes;  // A hi, lo; Yr hi, lo; Yi hi, lo
-constexpr int kYPitch = kLp + 1;                           // float2 per basis row
-constexpr uint32_t kOffY = 2 * kSetBytes;                  // float2 Y[32][kYPitch]
-constexpr uint32_t kOutPitch = kLp + 1;                    // floats per staged row
-constexpr uint32_t kOffOut = kOffY + kViews * kYPitch * 8; // float [128][kOutPitch]
-constexpr uint32_t kOffNorm = kOffOut + 128 * kOutPitch * 4;  // float N_l|m|[100]
-constexpr uint32_t kOffBar = kOffNorm + 100 * 4;
-constexpr uint32_t kOffMisc = kOffBar + 16;
-constexpr uint32_t kSmem = kOffMisc + 16;
+using namespace fle;
+
+constexpr int kThreads = 384;
+// the gradient rows of a job as one box [64 receivers][2L floats] (the TMA
+// layout; at degree 9 the 8 lanes of a quarter warp write 8 bank groups),
+// two boxes
+constexpr uint32_t kBox = kRx * 200 * 4;
+constexpr uint32_t kOffOut = 0;
+constexpr uint32_t kOffB = 2 * kBox;
+constexpr uint32_t kOffBar = kOffB + 2 * kBStage;
+constexpr int kNumBars = 11;
+constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
+constexpr uint32_t kSmem = kOffMisc + 48;  // TMEM base, abort, write-out flags [2][4]
 static_assert(kSmem <= 232448, "shared memory");
-static_assert(kOffBar % 8 == 0, "mbarrier alignment");
-constexpr uint32_t kTmemCols = 512;  // 2 sets x (Q1: 112, Q2: 112) at 0 and 256
-constexpr uint32_t kWaitLimit = 1u << 20;
-constexpr uint32_t kIdesc = tc::idesc_bf16(128, kLp, 1, 1);
+static_assert(kOffBar % 8 == 0 && kBox % 1024 == 0, "alignment");
+constexpr uint32_t kTmemCols = 512;
+// tensor memory: D at 128 * (job & 1) (D+: 64 columns, D-: 48 at +64);
+// A operands at 256 + 64 * (step & 1): G+ hi, G+ lo, G- hi, G- lo (16 each)
+constexpr uint32_t kColA = 256;
 
-struct Job {
-  int k, j0, v0, nr, nv, grp, last;
-};
-
-__device__ __forceinline__ Job job_of(int n, int N, int M) {
-  const int njg = (N + kRx - 1) / kRx, nvg = (M + kViews - 1) / kViews;
-  const int per_k = njg * nvg;
-  const int i = n / per_k, r = n % per_k;
-  Job J;
-  J.k = blockIdx.x + i * gridDim.x;
-  J.j0 = (r / nvg) * kRx;
-  J.v0 = (r % nvg) * kViews;
-  J.nr = min(kRx, N - J.j0);
-  J.nv = min(kViews, M - J.v0);
-  J.grp = n / nvg;
-  J.last = (r % nvg) == nvg - 1;
-  return J;
-}
-
+template <bool kBulk>
 __global__ void __launch_bounds__(kThreads, 1)
     fle_backward_tc_kernel(const float* __restrict__ d_rad, int N, int K, int lmax,
-                           const float4* __restrict__ geom, const float* __restrict__ tx, int M,
-                           int stride, size_t rad_view, FleNorm nrm, float* __restrict__ grad,
-                           int accumulate, unsigned* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  float2* sY = reinterpret_cast<float2*>(sm + kOffY);
-  float* sOut = reinterpret_cast<float*>(sm + kOffOut);
-  float* sNorm = reinterpret_cast<float*>(sm + kOffNorm);
+                           const unsigned char* __restrict__ image, int M, int stride,
+                           size_t rad_view, float* __restrict__ grad,
+                           int accumulate, unsigned* __restrict__ err,
+                           const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffBar);
+  uint64_t* afull = bar;        // [2] A operands of a step in TMEM
+  uint64_t* bfull = bar + 2;    // [2] B operand of a step staged
+  uint64_t* sdone = bar + 4;    // [2] MMAs of a step complete
+  uint64_t* dfull = bar + 6;    // [2] MMAs of a job complete
+  uint64_t* dempty = bar + 8;   // [2] a job's D read
+  uint64_t* fin = bar + 10;
   uint32_t* sMisc = reinterpret_cast<uint32_t*>(sm + kOffMisc);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  volatile uint32_t* abort_flag = &sMisc[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = (lmax + 1) * (lmax + 1);
-  const uint32_t sbase = tc::smem_u32(sm);
-  const int njg = (N + kRx - 1) / kRx, nvg = (M + kViews - 1) / kViews;
-  const int nk = blockIdx.x < K ? (K - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int njobs = nk * njg * nvg;
-  auto set_off = [](int n) { return (n & 1) ? kSetBytes : 0u; };
-
-  auto stage = [&](int n) {
-    const Job J = job_of(n, N, M);
-    const uint32_t so = set_off(n);
-    fle_basis_group(geom[3 * J.k], tx, J.v0, J.nv, lmax, sNorm, sY, kYPitch, t, kThreads);
-    // cotangent rows: thread (view v, row octet ro) loads 8 consecutive
-    // columns of the view's radiance row
-    {
-      const int v = t >> 4, ro = t & 15;
-      float x[8];
-      const bool ok = v < J.nv && 8 * ro < 2 * J.nr;
-      if (ok) {
-        const float4* src = reinterpret_cast<const float4*>(
-            d_rad + static_cast<size_t>(J.v0 + v) * rad_view + static_cast<size_t>(J.k) * stride +
-            2 * J.j0 + 8 * ro);
-        const float4 a0 = src[0], a1 = src[1];
-        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
-        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (8 * ro + e >= 2 * J.nr) x[e] = 0.0f;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = 0.0f;
-      }
-      uint4 hi, lo;
-      tc::split8(x, hi, lo);
-      const uint32_t off = (v >> 3) * kAK + ro * kAM + (v & 7) * 16;
-      *reinterpret_cast<uint4*>(sm + so + off) = hi;
-      *reinterpret_cast<uint4*>(sm + so + kABytes + off) = lo;
-    }
-    __syncthreads();  // sY complete
-    for (int e = t; e < kViews * kOct; e += kThreads) {
-      const int v = e / kOct, o = e % kOct;
-      float yr[8], yi[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float2 y = sY[v * kYPitch + 8 * o + q];
-        yr[q] = y.x;
-        yi[q] = y.y;
-      }
-      const uint32_t off = (v >> 3) * kBK + o * kBN + (v & 7) * 16;
-      uint4 hi, lo;
-      tc::split8(yr, hi, lo);
-      *reinterpret_cast<uint4*>(sm + so + 2 * kABytes + off) = hi;
-      *reinterpret_cast<uint4*>(sm + so + 2 * kABytes + kBBytes + off) = lo;
-      tc::split8(yi, hi, lo);
-      *reinterpret_cast<uint4*>(sm + so + 2 * kABytes + 2 * kBBytes + off) = hi;
-      *reinterpret_cast<uint4*>(sm + so + 2 * kABytes + 3 * kBBytes + off) = lo;
-    }
-  };
-  auto issue = [&](uint32_t tmem, int n) {
-    const Job J = job_of(n, N, M);
-    const uint32_t so = sbase + set_off(n);
-    const uint64_t dA[2] = {tc::smem_desc(so, kAK, kAM), tc::smem_desc(so + kABytes, kAK, kAM)};
-    const uint32_t first = J.v0 == 0;
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {  // Q1 (Re Y), Q2 (Im Y)
-      const uint32_t yb = so + 2 * kABytes + 2 * pr * kBBytes;
-      const uint64_t dB[2] = {tc::smem_desc(yb, kBK, kBN), tc::smem_desc(yb + kBBytes, kBK, kBN)};
-      const uint32_t d = tmem + 256 * (J.grp & 1) + kLp * pr;
-#pragma unroll
-      for (int k = 0; k < kViews / 16; ++k)
-#pragma unroll
-        for (int term = 0; term < 3; ++term)
-          tc::mma_bf16(d, dA[term == 2] + ((2 * k * kAK) >> 4), dB[term == 1] + ((2 * k * kBK) >> 4),
-                       kIdesc, !(first && k == 0 && term == 0));
-    }
-    tc::mma_commit(&bar[n & 1]);
-  };
-  // the finished tile of job n's group: TMEM -> shared (warps 0-3), then the
-  // gradient rows += (all threads)
-  auto write_out = [&](uint32_t tmem, int n) {
-    const Job J = job_of(n, N, M);
-    if (warp < 4) {
-      const uint32_t base = tmem + (static_cast<uint32_t>(32 * warp) << 16) + 256 * (J.grp & 1);
-      const int row = 32 * warp + lane;
-      const bool odd = lane & 1;
-#pragma unroll 1
-      for (int c0 = 0; c0 < kLp; c0 += 16) {
-        float q1a[8], q1b[8], q2a[8], q2b[8];
-        tc::tmem_ld8(base + c0, q1a);
-        tc::tmem_ld8(base + c0 + 8, q1b);
-        tc::tmem_ld8(base + kLp + c0, q2a);
-        tc::tmem_ld8(base + kLp + c0 + 8, q2b);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float oa = __shfl_xor_sync(0xffffffffu, q2a[e], 1);
-          const float ob = __shfl_xor_sync(0xffffffffu, q2b[e], 1);
-          sOut[row * kOutPitch + c0 + e] = odd ? q1a[e] - oa : q1a[e] + oa;
-          sOut[row * kOutPitch + c0 + 8 + e] = odd ? q1b[e] - ob : q1b[e] + ob;
-        }
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    // row r = 2j + part -> grad[j0 + j][k][part][l]; 128 threads per row pass
-    for (int e = t; e < 2 * J.nr * 128; e += kThreads) {
-      const int row = e >> 7, l = e & 127;
-      if (l < L) {
-        float* dst = grad + (static_cast<size_t>(J.j0 + (row >> 1)) * K + J.k) * 2 * L +
-                     (row & 1) * L + l;
-        *dst = accumulate ? *dst + sOut[row * kOutPitch + l] : sOut[row * kOutPitch + l];
-      }
-    }
-  };
+  const int njobs = jobs_of_cta(K, N), nvg = (M + kViews - 1) / kViews;
+  const int nsteps = njobs * nvg;
 
   if (warp == 0) tc::tmem_alloc(&sMisc[0], kTmemCols);
-  if (t == 32) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&afull[i], 4);
+      tc::mbar_init(&bfull[i], 1);
+      tc::mbar_init(&sdone[i], 1);
+      tc::mbar_init(&dfull[i], 1);
+      tc::mbar_init(&dempty[i], 4);
+    }
+    tc::mbar_init(fin, 1);
     tc::mbar_fence_init();
     sMisc[1] = 0;
   }
-  for (int l = t; l < 100; l += kThreads) sNorm[l] = nrm.n[l];
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -217,33 +97,233 @@ __global__ void __launch_bounds__(kThreads, 1)
     atomicOr(&sMisc[1], 1u);
     if (err) atomicOr(err, kErrTimeout);
   };
-  for (int n = 0; n < min(2, njobs); ++n) {
-    stage(n);
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (t == 0) {
-      tc::fence_after_sync();
-      issue(tmem, n);
+  auto wait_warp = [&](uint64_t* b, uint32_t parity) -> bool {
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(b, parity, kWaitLimit));
+    if (!ok && lane == 0) fail();
+    return ok;
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    // per step the view group's basis block into one of two B stages
+    if (lane == 0) {
+      int s = 0, issued = 0;
+      bool stop = false;
+      JobIter it(K);
+      for (int n = 0; n < njobs && !stop; ++n, it.next()) {
+        for (int vg = 0; vg < nvg; ++vg, ++s) {
+          if (*abort_flag) { stop = true; break; }
+          if (s >= 2 && !tc::mbar_wait(&sdone[s & 1], ((s >> 1) - 1) & 1, kWaitLimit)) {
+            fail();
+            stop = true;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&bfull[s & 1], kBStage);
+          tc::bulk_g2s(sm + kOffB + (s & 1) * kBStage,
+                       image + (static_cast<size_t>(it.k) * nvg + vg) * kBStage, kBStage,
+                       &bfull[s & 1]);
+          issued = s + 1;
+        }
+      }
+      // copies of a walk cut short land before the CTA exits
+      for (int q = max(0, issued - 2); q < issued; ++q)
+        tc::mbar_wait(&bfull[q & 1], (q >> 1) & 1, kWaitLimit);
     }
-  }
-  for (int n = 1; n <= njobs; ++n) {
-    const int pn = n - 1;
-    if (!tc::mbar_wait(&bar[pn & 1], (pn >> 1) & 1, kWaitLimit)) fail();
-    tc::fence_after_sync();
-    __syncthreads();
-    if (sMisc[1]) break;
-    if (job_of(pn, N, M).last) write_out(tmem, pn);
-    const bool more = n + 1 < njobs;
-    if (more) stage(n + 1);  // into operand set (n + 1) & 1 = pn & 1 (job pn is done)
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (more && t == 0) {
-      tc::fence_after_sync();
-      issue(tmem, n + 1);
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const int kp = kp_of(lmax), kq = kq_of(lmax);
+      const uint32_t idp = tc::idesc_bf16(128, kp, 0, 1);
+      const uint32_t idq = kq > 0 ? tc::idesc_bf16(128, kq, 0, 1) : 0u;
+      const uint32_t sb = tc::smem_u32(sm) + kOffB;
+      int s = 0;
+      bool stop = false;
+      for (int n = 0; n < njobs && !stop; ++n) {
+        for (int vg = 0; vg < nvg; ++vg, ++s) {
+          if (*abort_flag) { stop = true; break; }
+          if (!tc::mbar_wait(&afull[s & 1], (s >> 1) & 1, kWaitLimit)) { fail(); stop = true; break; }
+          if (!tc::mbar_wait(&bfull[s & 1], (s >> 1) & 1, kWaitLimit)) { fail(); stop = true; break; }
+          if (vg == 0 && n >= 2 &&
+              !tc::mbar_wait(&dempty[n & 1], ((n >> 1) - 1) & 1, kWaitLimit)) {
+            fail(); stop = true; break;
+          }
+          tc::fence_after_sync();
+          const uint32_t d = tmem + 128 * (n & 1);
+          const uint32_t a = tmem + kColA + 64 * (s & 1);
+          const uint32_t b = sb + (s & 1) * kBStage;
+#pragma unroll
+          for (int ks = 0; ks < kViews / 16; ++ks) {
+            // B read MN-major: LBO = distance of core matrices 8 views apart,
+            // SBO = distance of those 8 components apart
+            const uint32_t more = vg == 0 && ks == 0 ? 0u : 1u;
+            const uint64_t ph = tc::smem_desc(b + kYrHi + ks * 2 * kSboP, kSboP, 128);
+            const uint64_t pl = tc::smem_desc(b + kYrLo + ks * 2 * kSboP, kSboP, 128);
+            tc::mma_bf16_ts(d, a + ks * 8, ph, idp, more);
+            tc::mma_bf16_ts(d, a + ks * 8, pl, idp, 1);
+            tc::mma_bf16_ts(d, a + 16 + ks * 8, ph, idp, 1);
+            if (kq > 0) {
+              const uint64_t qh = tc::smem_desc(b + kYiHi + ks * 2 * kSboQ, kSboQ, 128);
+              const uint64_t ql = tc::smem_desc(b + kYiLo + ks * 2 * kSboQ, kSboQ, 128);
+              tc::mma_bf16_ts(d + 64, a + 32 + ks * 8, qh, idq, more);
+              tc::mma_bf16_ts(d + 64, a + 32 + ks * 8, ql, idq, 1);
+              tc::mma_bf16_ts(d + 64, a + 48 + ks * 8, qh, idq, 1);
+            }
+          }
+          tc::mma_commit(&sdone[s & 1]);
+          if (vg == nvg - 1) tc::mma_commit(&dfull[n & 1]);
+        }
+      }
+      tc::mma_commit(fin);
+      if (!tc::mbar_wait(fin, 0, kWaitLimit)) fail();
     }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------------------------------------------------------- A operands
+    const int q = warp - 4, row = 32 * q + lane;
+    const bool odd = lane & 1;
+    // (job, view group) of the step being loaded
+    JobIter lit(K);
+    int lvg = 0;
+    auto load = [&](float (&g)[kViews]) {
+      const int v0 = lvg * kViews;
+      const int nv = min(kViews, M - v0);
+      const bool ok = row < 2 * (N - lit.jg * kRx);
+      const float* src = d_rad + static_cast<size_t>(lit.k) * stride + 2 * lit.jg * kRx + row +
+                         static_cast<size_t>(v0) * rad_view;
+#pragma unroll
+      for (int v = 0; v < kViews; ++v)
+        g[v] = (ok && v < nv) ? src[static_cast<size_t>(v) * rad_view] : 0.0f;
+      if (++lvg == nvg) {
+        lvg = 0;
+        lit.next();
+      }
+    };
+    auto put = [&](int s, const float (&g)[kViews]) -> bool {
+      if (*abort_flag) return false;
+      if (s >= 2 && !wait_warp(&sdone[s & 1], ((s >> 1) - 1) & 1)) return false;
+      tc::fence_after_sync();
+      const uint32_t a = tmem + (static_cast<uint32_t>(32 * q) << 16) + kColA + 64 * (s & 1);
+      uint32_t h[16], lo[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) tc::split2(g[2 * e], g[2 * e + 1], h[e], lo[e]);
+      tc::tmem_st16(a, h);
+      tc::tmem_st16(a + 16, lo);
+      float x[kViews];  // row 2j: Im g_j, row 2j + 1: -Re g_j
+#pragma unroll
+      for (int v = 0; v < kViews; ++v) {
+        const float o = __shfl_xor_sync(0xffffffffu, g[v], 1);
+        x[v] = odd ? -o : o;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) tc::split2(x[2 * e], x[2 * e + 1], h[e], lo[e]);
+      tc::tmem_st16(a + 32, h);
+      tc::tmem_st16(a + 48, lo);
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&afull[s & 1]);
+      return true;
+    };
+    // two register sets: the loads of step s + 1 are in flight while step s is stored
+    float ga[kViews], gb[kViews];
+    if (nsteps > 0) load(ga);
+    for (int s = 0; s < nsteps; s += 2) {
+      if (s + 1 < nsteps) load(gb);
+      if (!put(s, ga) || s + 1 >= nsteps) break;
+      if (s + 2 < nsteps) load(ga);
+      if (!put(s + 1, gb)) break;
+    }
+  } else if (warp >= 8) {
+    // ---------------------------------------------------------------- write-out
+    const int q = warp - 8, row = 32 * q + lane, jl = row >> 1, p = row & 1;
+    const bool has_q = kq_of(lmax) > 0;
+    JobIter it(K);
+    // the four warps agree on going on (they meet at named barriers below,
+    // so none may leave the walk alone): flags [n & 1][warp], read after
+    // the barrier of job n and next written for job n + 2
+    volatile uint32_t* go = sMisc + 4;
+    for (int n = 0; n < njobs; ++n, it.next()) {
+      const bool ok = !*abort_flag && wait_warp(&dfull[n & 1], (n >> 1) & 1);
+      if (lane == 0) go[(n & 1) * 4 + q] = ok ? 1u : 0u;
+      tc::named_barrier(1, 128);
+      if (!(go[(n & 1) * 4] & go[(n & 1) * 4 + 1] & go[(n & 1) * 4 + 2] & go[(n & 1) * 4 + 3]))
+        break;
+      tc::fence_after_sync();
+      uint32_t dp[64], dq[48];
+      const uint32_t d = tmem + (static_cast<uint32_t>(32 * q) << 16) + 128 * (n & 1);
+      {
+        uint32_t r[32];
+        tc::tmem_ld32_async(d, r);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) dp[e] = r[e];
+      }
+      {
+        uint32_t r[32];
+        tc::tmem_ld32_async(d + 32, r);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) dp[32 + e] = r[e];
+      }
+      {
+        uint32_t r[32];
+        tc::tmem_ld32_async(d + 64, r);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) dq[e] = r[e];
+      }
+      {
+        uint32_t r[16];
+        tc::tmem_ld16_async(d + 96, r);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) dq[32 + e] = r[e];
+      }
+      tc::tmem_wait_ld();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&dempty[n & 1]);
+      // the lane's half-row in component order l*l + l + m
+      float o[100];
+#pragma unroll
+      for (int l = 0; l < 10; ++l)
+#pragma unroll
+        for (int m = -l; m <= l; ++m) {
+          const int am = m < 0 ? -m : m;
+          const float vp = __uint_as_float(dp[kappa_p(l, am)]);
+          const float vq = (am > 0 && has_q) ? __uint_as_float(dq[kappa_q(l, am)]) : 0.0f;
+          o[l * l + l + m] = m == 0 ? vp : (m > 0 ? vp + vq : vp - vq);
+        }
+      const bool on = jl < N - it.jg * kRx;
+      if (kBulk) {
+        // box n & 1 is free once the copy issued from it two jobs ago has
+        // read it; the four warps fill it, then one thread adds (or stores)
+        // it to the gradient rows (rows past N are not written)
+        if (row == 0) tc::bulk_wait_read<1>();
+        tc::named_barrier(1, 128);
+        unsigned char* box = sm + kOffOut + (n & 1) * kBox;
+        if (on) {
+          float4* srow = reinterpret_cast<float4*>(box + (jl * 2 * L + p * L) * 4);
+#pragma unroll
+          for (int t = 0; t < 25; ++t)
+            if (4 * t < L) srow[t] = make_float4(o[4 * t], o[4 * t + 1], o[4 * t + 2], o[4 * t + 3]);
+        }
+        tc::fence_smem_to_async();
+        tc::named_barrier(1, 128);
+        if (row == 0) {
+          if (accumulate)
+            tc::tma_reduce_add_3d(&tmap, 0, it.k, it.jg * kRx, box);
+          else
+            tc::tma_store_3d(&tmap, 0, it.k, it.jg * kRx, box);
+          tc::bulk_commit();
+        }
+      } else if (on) {
+        float* dst = grad + (static_cast<size_t>(it.jg * kRx + jl) * K + it.k) * 2 * L + p * L;
+#pragma unroll
+        for (int i = 0; i < 100; ++i)
+          if (i < L) dst[i] = accumulate ? dst[i] + o[i] : o[i];
+      }
+    }
+    if (kBulk && row == 0) tc::bulk_wait_all();
   }
+
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -252,25 +332,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-}  // namespace
-
-void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax, const float4* geom,
-                            const float* tx, int M, int stride, size_t rad_view, float* grad,
-                            bool accumulate, cudaStream_t s, unsigned* err) {
-  if (K <= 0 || N <= 0 || M <= 0) return;
+template <bool kBulk>
+void launch_backward(const float* d_rad, int N, int K, int lmax, const unsigned char* image,
+                     int M, int stride, size_t rad_view, float* grad, bool accumulate, int grid,
+                     cudaStream_t s, unsigned* err, const CUtensorMap& tmap) {
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(fle_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(fle_backward_tc_kernel<kBulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kSmem));
     configured = true;
   }
+  fle_backward_tc_kernel<kBulk><<<grid, kThreads, kSmem, s>>>(
+      d_rad, N, K, lmax, image, M, stride, rad_view, grad, accumulate ? 1 : 0, err, tmap);
+}
+
+}  // namespace
+
+void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax,
+                            const unsigned char* image, int M, int stride, size_t rad_view,
+                            float* grad, bool accumulate, cudaStream_t s, unsigned* err) {
+  if (K <= 0 || N <= 0 || M <= 0) return;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(K, nsm));
-  fle_backward_tc_kernel<<<grid, kThreads, kSmem, s>>>(d_rad, N, K, lmax, geom, tx, M, stride,
-                                                       rad_view, fle_norm_table(lmax), grad,
-                                                       accumulate ? 1 : 0, err);
+  const long long jobs = static_cast<long long>(K) * ((N + kRx - 1) / kRx);
+  const int grid = static_cast<int>(std::max(1LL, std::min<long long>(jobs, nsm)));
+  const int L = (lmax + 1) * (lmax + 1);
+  CUtensorMap tmap{};
+  if (encode_fle_rows(&tmap, grad, N, K, L))
+    launch_backward<true>(d_rad, N, K, lmax, image, M, stride, rad_view, grad, accumulate, grid, s,
+                          err, tmap);
+  else
+    launch_backward<false>(d_rad, N, K, lmax, image, M, stride, rad_view, grad, accumulate, grid,
+                           s, err, tmap);
   note_launches(1);
 }
 

@@ -2,258 +2,237 @@
 // as a tcgen05 contraction per Gaussian.
 //
 // For Gaussian k, receivers j (a group of 64) and views v (a group of 32):
-//   s[v][k][j] = sum_l Y_vl (c_jl),   Y_vl = N_l|m| P_l^|m|(cos theta_v) e^{i m phi_v}
-// with c_jl the coefficients (a + i b)_jk,l (given, or formed from the base
-// coefficients by the global FiLM branch, film_coeffs below).  Real-ified, with the
-// coefficient rows interleaved (row 2j = Re c_j, row 2j + 1 = Im c_j) as the
-// A operand (M = 128, K = components padded to a multiple of 16) and the
-// basis of the 32 views as two B operands (N = 32: Re Y and Im Y):
-//   P1 = A Yr^T,  P2 = A Yi^T   (float32 in TMEM)
+//   s[v][k][j] = sum_l Y_vl c_jl = sum_P Yr c+_j + i sum_Q Yi c-_j
+// with the +m / -m components folded (fle_tc.cuh) and c_jl the coefficients
+// (a + i b)_jk,l (given, or formed from the base coefficients by the global
+// FiLM branch, film_coeffs below).  Real-ified, with the coefficient rows
+// interleaved (row 2j = Re, row 2j + 1 = Im) as the A operand (M = 128) and
+// the folded basis of the 32 views as the B operand (N = 32):
+//   P1 = A+ Yr^T (K = P components),  P2 = A- Yi^T (K = Q components)
 //   Re s_j = P1[2j] - P2[2j+1],  Im s_j = P1[2j+1] + P2[2j]
-// so lanes 2j and 2j + 1 of a warp exchange one value (shuffle) and row r of
-// the accumulator is column r of the radiance row the views write.  Operands
-// are split into two bf16 terms (three MMAs per product, tc_common.cuh).
+// (lanes 2j and 2j + 1 exchange one value).  Operands are split into two
+// bf16 terms (three MMAs per product, tc_common.cuh).
 //
-// One CTA per SM (512 threads) walks jobs (Gaussian, receiver group, view
-// group) with two operand buffers and two TMEM accumulator sets: while the
-// MMAs of job n run, the threads write out job n - 1 (warps 0-3 read its
-// accumulators) and stage job n + 1 (basis evaluated in float32 per (view,
-// order m) and split; coefficients split from registers that were loaded a
-// whole iteration earlier, so their memory latency is hidden).  Each buffer
-// set has its own mbarrier, so no wait is ever more than one phase behind;
-// every wait is bounded (kErrTimeout).
+// The basis operand of every (Gaussian, group of 32 views) is computed
+// first (fle_basis_image: fully parallel, one thread per view, written in
+// the staged layout).  Then one CTA per SM walks jobs (Gaussian, receiver
+// group), each with one step per group of 32 views, through warp-specialised
+// stages on mbarriers:
+//   warp 0       per job one TMA copy (a tensor-map box of the job's 64
+//                coefficient rows) into one of three shared-memory stages,
+//                per step one bulk copy of the basis block into one of two
+//                B stages;
+//   warps 4-7,   fold and split the coefficients (lane = accumulator row)
+//   12-15        and store the A operand into tensor memory (tcgen05.st),
+//                double-buffered; the two groups take even and odd jobs;
+//   warp 1       one thread issues the MMAs (A from tensor memory, B from
+//                shared memory) into one of two accumulators;
+//   warps 8-11   read the accumulators (tcgen05.ld), combine and store.
+// Every wait is bounded: on a timeout the CTA records kErrTimeout, stops
+// walking, lets its copies and MMAs in flight complete and frees its tensor
+// memory.  A degree whose half-rows are not whole 16-byte units
+// ((lmax + 1)^2 odd) or an unaligned coefficient array takes the same kernel
+// with the converters reading the coefficients directly.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
-#include "fle_basis.cuh"
+#include "fle_tc.cuh"
 #include "rxgs_internal.h"
 #include "tc_common.cuh"
 
 namespace rxgs {
 
-// N_l|m| = sqrt((2l + 1) / (4 pi) (l - |m|)! / (l + |m|)!) by component index
-// l*l + l + m (the orthonormal basis of App. E.2).
-FleNorm fle_norm_table(int lmax) {
-  FleNorm t{};
-  for (int l = 0; l <= lmax; ++l)
-    for (int m = -l; m <= l; ++m) {
-      const int am = m < 0 ? -m : m;
-      double ratio = 1.0;  // (l - |m|)! / (l + |m|)!
-      for (int q = l - am + 1; q <= l + am; ++q) ratio /= q;
-      t.n[l * l + l + m] = static_cast<float>(std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * ratio));
+// N_lm = sqrt((2l + 1) / (4 pi) (l - m)! / (l + m)!) (the orthonormal basis of
+// App. E.2, m >= 0) and the three-term recurrence of P_l^m in l, both folded
+// into the coefficients of the recurrence of y_lm = N_lm P_l^m (double, then
+// rounded once).
+FleRec fle_rec_table() {
+  auto norm = [](int l, int m) {
+    double ratio = 1.0;  // (l - m)! / (l + m)!
+    for (int q = l - m + 1; q <= l + m; ++q) ratio /= q;
+    return std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * ratio);
+  };
+  FleRec t{};
+  t.r[0][0][0] = static_cast<float>(norm(0, 0));
+  for (int l = 1; l < 10; ++l) {
+    // P_l^l = (2l - 1) st P_{l-1}^{l-1},  P_l^{l-1} = (2l - 1) ct P_{l-1}^{l-1}
+    t.r[l][l][0] = static_cast<float>((2.0 * l - 1.0) * norm(l, l) / norm(l - 1, l - 1));
+    t.r[l][l - 1][0] = static_cast<float>((2.0 * l - 1.0) * norm(l, l - 1) / norm(l - 1, l - 1));
+    // (l - m) P_l^m = (2l - 1) ct P_{l-1}^m - (l + m - 1) P_{l-2}^m
+    for (int m = 0; m + 2 <= l; ++m) {
+      t.r[l][m][0] = static_cast<float>((2.0 * l - 1.0) / (l - m) * norm(l, m) / norm(l - 1, m));
+      t.r[l][m][1] = static_cast<float>((l + m - 1.0) / (l - m) * norm(l, m) / norm(l - 2, m));
     }
+  }
   return t;
 }
 
+namespace fle {
+
+bool encode_fle_rows(CUtensorMap* map, const float* base, int N, int K, int L) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<Encode>(fn);
+  }
+  if (!encode || (L & 3) != 0 || 2 * L > 256 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(2 * L), static_cast<cuuint64_t>(K),
+                              static_cast<cuuint64_t>(N)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(2 * L) * 4,
+                                 static_cast<cuuint64_t>(K) * 2 * L * 4};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(2 * L), 1,
+                             static_cast<cuuint32_t>(N < kRx ? N : kRx)};
+  const cuuint32_t unit[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
+                box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace fle
+
 namespace {
+
+using namespace fle;
 
 constexpr int kThreads = 512;
-constexpr int kRx = 64;      // receivers per job (128 accumulator rows)
-constexpr int kViews = 32;   // views per job (N of the MMA)
-constexpr int kLp = 112;     // components, padded: (lmax + 1)^2 <= 100
-constexpr int kOct = kLp / 8;
-// A[row][l]: core (row/8, l/8) at (row/8) * kSboA + (l/8) * 128 (K-major)
-// B[v][l]  : core (v/8, l/8)   at (v/8) * kSboB + (l/8) * 128 (K-major)
-constexpr uint32_t kLbo = 128;
-constexpr uint32_t kSboA = kOct * 128, kSboB = kOct * 128;
-constexpr uint32_t kABytes = 16 * kSboA;  // 128 rows
-constexpr uint32_t kBBytes = 4 * kSboB;   // 32 views
-// per buffer set: A hi, A lo, Yr hi, Yr lo, Yi hi, Yi lo
-constexpr uint32_t kSetBytes = 2 * kABytes + 4 * kBBytes;
-constexpr uint32_t kOffSet0 = 0, kOffSet1 = kSetBytes;
-constexpr int kYPitch = kLp + 1;                           // float2 per basis row (bank spread)
-constexpr uint32_t kOffY = 2 * kSetBytes;                  // float2 Y[32][kYPitch] (float32 basis)
-constexpr uint32_t kOffNorm = kOffY + kViews * kYPitch * 8; // float N_l|m|[100]
-constexpr uint32_t kOffBar = kOffNorm + 100 * 4;            // u64 [2]
-constexpr uint32_t kOffMisc = kOffBar + 16;                 // TMEM base, abort
+constexpr int kStages = 3;                      // coefficient stages
+// one stage: the job's box [64 receivers][2L floats] as the TMA lays it out
+// (at degree 9 a receiver's Re and Im half-rows are 25 16-byte units apart
+// and receivers 50, so the 8 lanes of a quarter warp read 8 bank groups)
+constexpr uint32_t kCStage = kRx * 200 * 4;
+constexpr uint32_t kOffB = kStages * kCStage;
+constexpr uint32_t kOffBar = kOffB + 2 * kBStage;
+constexpr int kNumBars = 2 * kStages + 11;
+constexpr uint32_t kOffMisc = kOffBar + 8 * kNumBars;
 constexpr uint32_t kSmem = kOffMisc + 16;
 static_assert(kSmem <= 232448, "shared memory");
-constexpr uint32_t kTmemCols = 128;  // 2 sets x (P1: 32, P2: 32)
-constexpr uint32_t kWaitLimit = 1u << 20;
-constexpr uint32_t kIdesc = tc::idesc_bf16(128, kViews, 0, 0);
+static_assert(kOffBar % 8 == 0 && kOffB % 1024 == 0, "alignment");
+constexpr uint32_t kTmemCols = 512;
+// tensor memory: accumulators (P1: 32 columns, P2: 32) at 64 * (step & 1);
+// A operands at 128 + 128 * (job & 1): A+ hi, A+ lo (32 columns each), A- hi,
+// A- lo (24 each)
+constexpr uint32_t kColA = 128, kAPlo = 32, kAQhi = 64, kAQlo = 88;
 
-struct Job {
-  int k, j0, v0, nr, nv;
-};
+// The basis image: thread = (Gaussian, view) pair of a block's two
+// (Gaussian, view group) blocks.
+constexpr int kImgThreads = 64;
 
-__device__ __forceinline__ Job job_of(int n, int K, int N, int M) {
-  const int njg = (N + kRx - 1) / kRx, nvg = (M + kViews - 1) / kViews;
-  const int per_k = njg * nvg;
-  const int i = n / per_k, r = n % per_k;
-  Job J;
-  J.k = blockIdx.x + i * gridDim.x;
-  J.j0 = (r / nvg) * kRx;
-  J.v0 = (r % nvg) * kViews;
-  J.nr = min(kRx, N - J.j0);
-  J.nv = min(kViews, M - J.v0);
-  (void)K;
-  return J;
+__global__ void __launch_bounds__(kImgThreads) fle_basis_image_kernel(
+    const float4* __restrict__ geom, const float* __restrict__ tx, int K, int M, int lmax,
+    FleRec rec, unsigned char* __restrict__ image) {
+  __shared__ float2 sRec[100];
+  __shared__ float scratch[kImgThreads / 32][32 * kBPitch];
+  for (int i = threadIdx.x; i < 100; i += kImgThreads)
+    sRec[i] = make_float2(rec.r[i / 10][i % 10][0], rec.r[i / 10][i % 10][1]);
+  __syncthreads();
+  const int nvg = (M + kViews - 1) / kViews;
+  const long long g = static_cast<long long>(blockIdx.x) * (kImgThreads / 32) + (threadIdx.x >> 5);
+  if (g >= static_cast<long long>(K) * nvg) return;
+  const int k = static_cast<int>(g / nvg), v0 = static_cast<int>(g % nvg) * kViews;
+  basis_rows(image + g * kBStage, scratch[threadIdx.x >> 5], geom[3 * k], tx, v0,
+             min(kViews, M - v0), lmax, sRec, threadIdx.x & 31);
 }
 
-__device__ __forceinline__ void put16(unsigned char* base, uint32_t off, const uint4& x) {
-  *reinterpret_cast<uint4*>(base + off) = x;
+// The coefficients of one job -> the A operand in tensor memory: lane = row
+// 2j + p of the warp's quarter, c its half-row (row past N: zeros).
+// A+ = c_{l,m} + c_{l,-m} (m > 0), c_{l,0}; A- = c_{l,m} - c_{l,-m}; 16
+// components at a time split into hi and lo terms (8 columns each).
+__device__ __forceinline__ void store_a(uint32_t a, const float (&c)[100]) {
+  {
+    float v[16];
+#pragma unroll
+    for (int l = 0; l < 10; ++l)
+#pragma unroll
+      for (int m = 0; m <= l; ++m) {
+        const int kp = kappa_p(l, m);
+        v[kp & 15] = m == 0 ? c[l * l + l] : c[l * l + l + m] + c[l * l + l - m];
+        if ((kp & 15) == 15 || kp == kappa_p(9, 9)) {
+          if (kp == kappa_p(9, 9))
+#pragma unroll
+            for (int e = (kappa_p(9, 9) & 15) + 1; e < 16; ++e) v[e] = 0.0f;
+          uint32_t h[8], lo[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tc::split2(v[2 * e], v[2 * e + 1], h[e], lo[e]);
+          tc::tmem_st8(a + (kp >> 4) * 8, h);
+          tc::tmem_st8(a + kAPlo + (kp >> 4) * 8, lo);
+        }
+      }
+  }
+  {
+    float v[16];
+#pragma unroll
+    for (int l = 1; l < 10; ++l)
+#pragma unroll
+      for (int m = 1; m <= l; ++m) {
+        const int kq = kappa_q(l, m);
+        v[kq & 15] = c[l * l + l + m] - c[l * l + l - m];
+        if ((kq & 15) == 15 || kq == kappa_q(9, 9)) {
+          if (kq == kappa_q(9, 9))
+#pragma unroll
+            for (int e = (kappa_q(9, 9) & 15) + 1; e < 16; ++e) v[e] = 0.0f;
+          uint32_t h[8], lo[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tc::split2(v[2 * e], v[2 * e + 1], h[e], lo[e]);
+          tc::tmem_st8(a + kAQhi + (kq >> 4) * 8, h);
+          tc::tmem_st8(a + kAQlo + (kq >> 4) * 8, lo);
+        }
+      }
+  }
 }
 
-}  // namespace
-
-namespace {
-
-// Coefficient tasks of one job: (receiver j, component octet o), thread t
-// takes tasks t and t + 512; the 16 values of a task (8 real, 8 imaginary
-// parts) are loaded one iteration ahead of their conversion.
-constexpr int kTasks = kRx * kOct;
-constexpr int kTasksPerThread = (kTasks + kThreads - 1) / kThreads;
-struct ARegs {
-  float4 v[kTasksPerThread][4];
-};
-
+template <bool kBulk>
 __global__ void __launch_bounds__(kThreads, 1)
     fle_radiance_tc_kernel(const float* __restrict__ coeffs, int N, int K, int lmax,
-                           const float4* __restrict__ geom, const float* __restrict__ tx, int M,
-                           int stride, size_t rad_view, FleNorm nrm, float* __restrict__ rad,
-                           unsigned* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  float2* sY = reinterpret_cast<float2*>(sm + kOffY);
-  float* sNorm = reinterpret_cast<float*>(sm + kOffNorm);
+                           const unsigned char* __restrict__ image, int M, int stride,
+                           size_t rad_view, float* __restrict__ rad, unsigned* __restrict__ err,
+                           const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffBar);
+  uint64_t* cfull = bar;                 // [kStages] coefficients landed
+  uint64_t* cempty = bar + kStages;      // [kStages] converters done with them
+  uint64_t* afull = bar + 2 * kStages;   // [2] A operand of a job in TMEM
+  uint64_t* adone = afull + 2;           // [2] MMAs of a job complete
+  uint64_t* bfull = afull + 4;           // [2] B operand of a step landed
+  uint64_t* sdone = afull + 6;           // [2] MMAs of a step complete
+  uint64_t* aempty = afull + 8;          // [2] accumulators of a step read
+  uint64_t* fin = afull + 10;            // every MMA complete
   uint32_t* sMisc = reinterpret_cast<uint32_t*>(sm + kOffMisc);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  volatile uint32_t* abort_flag = &sMisc[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = (lmax + 1) * (lmax + 1);
-  const uint32_t sbase = tc::smem_u32(sm);
-  const int njg = (N + kRx - 1) / kRx, nvg = (M + kViews - 1) / kViews;
-  const int nk = static_cast<int>(blockIdx.x) < K ? (K - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
-  const int njobs = nk * njg * nvg;
-  auto set_off = [](int n) { return (n & 1) ? kOffSet1 : kOffSet0; };
+  const int njobs = jobs_of_cta(K, N), nvg = (M + kViews - 1) / kViews;
 
-  // coefficient rows of job n into registers
-  auto load_A = [&](int n, ARegs& R) {
-    const Job J = job_of(n, K, N, M);
-#pragma unroll
-    for (int u = 0; u < kTasksPerThread; ++u) {
-      const int e = t + u * kThreads;
-      const int j = e / kOct, o = e % kOct;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) R.v[u][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e >= kTasks || j >= J.nr || 8 * o >= L) continue;
-      const float* c = coeffs + (static_cast<size_t>(J.j0 + j) * K + J.k) * 2 * L;
-      if (8 * o + 8 <= L && (L & 3) == 0) {
-        const float4* c4 = reinterpret_cast<const float4*>(c + 8 * o);
-        const float4* d4 = reinterpret_cast<const float4*>(c + L + 8 * o);
-        R.v[u][0] = c4[0];
-        R.v[u][1] = c4[1];
-        R.v[u][2] = d4[0];
-        R.v[u][3] = d4[1];
-      } else {
-        float re[8], im[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int l = 8 * o + q;
-          re[q] = l < L ? c[l] : 0.0f;
-          im[q] = l < L ? c[L + l] : 0.0f;
-        }
-        R.v[u][0] = make_float4(re[0], re[1], re[2], re[3]);
-        R.v[u][1] = make_float4(re[4], re[5], re[6], re[7]);
-        R.v[u][2] = make_float4(im[0], im[1], im[2], im[3]);
-        R.v[u][3] = make_float4(im[4], im[5], im[6], im[7]);
-      }
-    }
-  };
-  // ... split into bf16 terms, rows 2j (real) and 2j + 1 (imaginary)
-  auto store_A = [&](int n, const ARegs& R) {
-    const uint32_t so = set_off(n);
-#pragma unroll
-    for (int u = 0; u < kTasksPerThread; ++u) {
-      const int e = t + u * kThreads;
-      if (e >= kTasks) continue;
-      const int j = e / kOct, o = e % kOct;
-      const float re[8] = {R.v[u][0].x, R.v[u][0].y, R.v[u][0].z, R.v[u][0].w,
-                           R.v[u][1].x, R.v[u][1].y, R.v[u][1].z, R.v[u][1].w};
-      const float im[8] = {R.v[u][2].x, R.v[u][2].y, R.v[u][2].z, R.v[u][2].w,
-                           R.v[u][3].x, R.v[u][3].y, R.v[u][3].z, R.v[u][3].w};
-      uint4 hi, lo;
-      const int r0 = 2 * j;
-      const uint32_t off0 = (r0 >> 3) * kSboA + o * kLbo + (r0 & 7) * 16;
-      tc::split8(re, hi, lo);
-      put16(sm, so + off0, hi);
-      put16(sm, so + kABytes + off0, lo);
-      tc::split8(im, hi, lo);
-      put16(sm, so + off0 + 16, hi);  // row 2j + 1 (same core matrix)
-      put16(sm, so + kABytes + off0 + 16, lo);
-    }
-  };
-  // basis of job n's views, split into Re / Im bf16 terms
-  auto stage_B = [&](int n) {
-    const Job J = job_of(n, K, N, M);
-    const uint32_t so = set_off(n);
-    fle_basis_group(geom[3 * J.k], tx, J.v0, J.nv, lmax, sNorm, sY, kYPitch, t, kThreads);
-    __syncthreads();  // sY complete
-    for (int e = t; e < kViews * kOct; e += kThreads) {
-      const int v = e / kOct, o = e % kOct;
-      float yr[8], yi[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float2 y = sY[v * kYPitch + 8 * o + q];
-        yr[q] = y.x;
-        yi[q] = y.y;
-      }
-      const uint32_t off = (v >> 3) * kSboB + o * kLbo + (v & 7) * 16;
-      uint4 hi, lo;
-      tc::split8(yr, hi, lo);
-      put16(sm, so + 2 * kABytes + off, hi);
-      put16(sm, so + 2 * kABytes + kBBytes + off, lo);
-      tc::split8(yi, hi, lo);
-      put16(sm, so + 2 * kABytes + 2 * kBBytes + off, hi);
-      put16(sm, so + 2 * kABytes + 3 * kBBytes + off, lo);
-    }
-  };
-  // ---- MMAs of job n (thread 0)
-  auto issue = [&](uint32_t tmem, int n) {
-    const uint32_t so = sbase + set_off(n);
-    const uint64_t dA[2] = {tc::smem_desc(so, kLbo, kSboA), tc::smem_desc(so + kABytes, kLbo, kSboA)};
-#pragma unroll
-    for (int pr = 0; pr < 2; ++pr) {  // P1 (Re Y), P2 (Im Y)
-      const uint32_t yb = so + 2 * kABytes + 2 * pr * kBBytes;
-      const uint64_t dB[2] = {tc::smem_desc(yb, kLbo, kSboB), tc::smem_desc(yb + kBBytes, kLbo, kSboB)};
-      const uint32_t d = tmem + 64 * (n & 1) + 32 * pr;
-#pragma unroll
-      for (int k = 0; k < kOct / 2; ++k)
-#pragma unroll
-        for (int term = 0; term < 3; ++term)
-          tc::mma_bf16(d, dA[term == 2] + ((2 * k * kLbo) >> 4), dB[term == 1] + ((2 * k * kLbo) >> 4),
-                       kIdesc, (k | term) != 0);
-    }
-    tc::mma_commit(&bar[n & 1]);
-  };
-  // ---- write-out of job n (warps 0-3: accumulator rows = radiance columns)
-  auto write_out = [&](uint32_t tmem, int n) {
-    const Job J = job_of(n, K, N, M);
-    const uint32_t lanes = static_cast<uint32_t>(32 * warp) << 16;
-    float p1[32], p2[32];
-    tc::tmem_ld32(tmem + lanes + 64 * (n & 1), p1);
-    tc::tmem_ld32(tmem + lanes + 64 * (n & 1) + 32, p2);
-    const int row = 32 * warp + lane;  // 2j + part
-    const bool odd = lane & 1;
-    const bool ok = row < 2 * J.nr;
-    float* dst = rad + static_cast<size_t>(J.k) * stride + 2 * J.j0 + row;
-#pragma unroll
-    for (int v = 0; v < kViews; ++v) {
-      const float other = __shfl_xor_sync(0xffffffffu, p2[v], 1);
-      const float val = odd ? p1[v] + other : p1[v] - other;
-      if (ok && v < J.nv) dst[static_cast<size_t>(J.v0 + v) * rad_view] = val;
-    }
-  };
-
-  // ---- set-up
   if (warp == 0) tc::tmem_alloc(&sMisc[0], kTmemCols);
-  if (t == 32) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&cfull[i], 1);
+      tc::mbar_init(&cempty[i], 4);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&afull[i], 4);
+      tc::mbar_init(&adone[i], 1);
+      tc::mbar_init(&bfull[i], 1);
+      tc::mbar_init(&sdone[i], 1);
+      tc::mbar_init(&aempty[i], 4);
+    }
+    tc::mbar_init(fin, 1);
     tc::mbar_fence_init();
     sMisc[1] = 0;
   }
-  for (int l = t; l < 100; l += kThreads) sNorm[l] = nrm.n[l];
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -262,43 +241,172 @@ __global__ void __launch_bounds__(kThreads, 1)
     atomicOr(&sMisc[1], 1u);
     if (err) atomicOr(err, kErrTimeout);
   };
-  ARegs R;
-  // prologue: jobs 0 and 1 staged and issued, job 2's coefficients in flight
-  for (int n = 0; n < min(2, njobs); ++n) {
-    load_A(n, R);
-    stage_B(n);
-    store_A(n, R);
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (t == 0) {
+  // a whole warp waits; any lane that gave up stops the warp
+  auto wait_warp = [&](uint64_t* b, uint32_t parity) -> bool {
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(b, parity, kWaitLimit));
+    if (!ok && lane == 0) fail();
+    return ok;
+  };
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    // per job one box of the coefficient rows (rows j0 .. j0 + 63 of Gaussian
+    // k; rows past N read as zero), per step the view group's basis block
+    if (lane == 0) {
+      const uint32_t box_bytes = static_cast<uint32_t>(min(kRx, N)) * 8u * L;
+      int cissued = 0, s = 0, bissued = 0;
+      bool stop = false;
+      JobIter it(K);
+      for (int n = 0; n < njobs && !stop; ++n, it.next()) {
+        if (*abort_flag) break;
+        const int st = n % kStages;
+        if (kBulk) {
+          if (n >= kStages && !tc::mbar_wait(&cempty[st], ((n / kStages) - 1) & 1, kWaitLimit)) {
+            fail();
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&cfull[st], box_bytes);
+          tc::tma_load_3d(sm + st * kCStage, &tmap, 0, it.k, it.jg * kRx, &cfull[st]);
+          cissued = n + 1;
+        }
+        for (int vg = 0; vg < nvg; ++vg, ++s) {
+          if (s >= 2 && !tc::mbar_wait(&sdone[s & 1], ((s >> 1) - 1) & 1, kWaitLimit)) {
+            fail();
+            stop = true;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&bfull[s & 1], kBStage);
+          tc::bulk_g2s(sm + kOffB + (s & 1) * kBStage,
+                       image + (static_cast<size_t>(it.k) * nvg + vg) * kBStage, kBStage,
+                       &bfull[s & 1]);
+          bissued = s + 1;
+        }
+      }
+      // copies of a walk cut short land before the CTA exits
+      for (int n = max(0, cissued - kStages); n < cissued; ++n)
+        tc::mbar_wait(&cfull[n % kStages], (n / kStages) & 1, kWaitLimit);
+      for (int q = max(0, bissued - 2); q < bissued; ++q)
+        tc::mbar_wait(&bfull[q & 1], (q >> 1) & 1, kWaitLimit);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const int kp16 = kp_of(lmax) / 16, kq16 = kq_of(lmax) / 16;
+      constexpr uint32_t idesc = tc::idesc_bf16(128, kViews, 0, 0);
+      const uint32_t sb = tc::smem_u32(sm) + kOffB;
+      int s = 0;
+      bool stop = false;
+      for (int n = 0; n < njobs && !stop; ++n) {
+        for (int vg = 0; vg < nvg; ++vg, ++s) {
+          if (*abort_flag) { stop = true; break; }
+          if (vg == 0 && !tc::mbar_wait(&afull[n & 1], (n >> 1) & 1, kWaitLimit)) {
+            fail(); stop = true; break;
+          }
+          if (!tc::mbar_wait(&bfull[s & 1], (s >> 1) & 1, kWaitLimit)) { fail(); stop = true; break; }
+          if (s >= 2 && !tc::mbar_wait(&aempty[s & 1], ((s >> 1) - 1) & 1, kWaitLimit)) {
+            fail(); stop = true; break;
+          }
+          tc::fence_after_sync();
+          const uint32_t acc = tmem + 64 * (s & 1);
+          const uint32_t a = tmem + kColA + 128 * (n & 1);
+          const uint32_t b = sb + (s & 1) * kBStage;
+          for (int ks = 0; ks < kp16; ++ks) {  // P1 = A+ Yr^T
+            const uint64_t bh = tc::smem_desc(b + kYrHi + ks * 256, 128, kSboP);
+            const uint64_t bl = tc::smem_desc(b + kYrLo + ks * 256, 128, kSboP);
+            tc::mma_bf16_ts(acc, a + ks * 8, bh, idesc, ks > 0);
+            tc::mma_bf16_ts(acc, a + ks * 8, bl, idesc, 1);
+            tc::mma_bf16_ts(acc, a + kAPlo + ks * 8, bh, idesc, 1);
+          }
+          for (int ks = 0; ks < kq16; ++ks) {  // P2 = A- Yi^T
+            const uint64_t bh = tc::smem_desc(b + kYiHi + ks * 256, 128, kSboQ);
+            const uint64_t bl = tc::smem_desc(b + kYiLo + ks * 256, 128, kSboQ);
+            tc::mma_bf16_ts(acc + 32, a + kAQhi + ks * 8, bh, idesc, ks > 0);
+            tc::mma_bf16_ts(acc + 32, a + kAQhi + ks * 8, bl, idesc, 1);
+            tc::mma_bf16_ts(acc + 32, a + kAQlo + ks * 8, bh, idesc, 1);
+          }
+          tc::mma_commit(&sdone[s & 1]);
+          if (vg == nvg - 1) tc::mma_commit(&adone[n & 1]);
+        }
+      }
+      tc::mma_commit(fin);
+      if (!tc::mbar_wait(fin, 0, kWaitLimit)) fail();
+    }
+    __syncwarp();
+  } else if ((warp >= 4 && warp < 8) || warp >= 12) {
+    // ---------------------------------------------------------------- A operand
+    // two groups of four warps take the even and the odd jobs
+    const int grp = warp >= 12, q = warp & 3, row = 32 * q + lane, jl = row >> 1, p = row & 1;
+    JobIter it(K);
+    if (grp) it.next();
+    for (int n = grp; n < njobs; n += 2, it.next(), it.next()) {
+      if (*abort_flag) break;
+      const int st = n % kStages;
+      if (kBulk && !wait_warp(&cfull[st], (n / kStages) & 1)) break;
+      if (n >= 2 && !wait_warp(&adone[n & 1], ((n >> 1) - 1) & 1)) break;
       tc::fence_after_sync();
-      issue(tmem, n);
+      const bool on = jl < N - it.jg * kRx;
+      float c[100];
+      if (kBulk) {
+        const float4* r4 =
+            reinterpret_cast<const float4*>(sm + st * kCStage + (jl * 2 * L + p * L) * 4);
+#pragma unroll
+        for (int t = 0; t < 25; ++t) {
+          const float4 v = (on && 4 * t < L) ? r4[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+          c[4 * t] = v.x;
+          c[4 * t + 1] = v.y;
+          c[4 * t + 2] = v.z;
+          c[4 * t + 3] = v.w;
+        }
+      } else {
+        const float* g =
+            coeffs + (static_cast<size_t>(it.jg * kRx + jl) * K + it.k) * 2 * L + p * L;
+#pragma unroll
+        for (int i = 0; i < 100; ++i) c[i] = (on && i < L) ? __ldg(g + i) : 0.0f;
+      }
+      store_a(tmem + (static_cast<uint32_t>(32 * q) << 16) + kColA + 128 * (n & 1), c);
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&afull[n & 1]);
+        if (kBulk) tc::mbar_arrive(&cempty[st]);
+      }
+    }
+  } else if (warp >= 8 && warp < 12) {
+    // ---------------------------------------------------------------- write-out
+    const int q = warp - 8, row = 32 * q + lane;
+    const bool odd = lane & 1, has_q = kq_of(lmax) > 0;
+    JobIter it(K);
+    int s = 0;
+    bool stop = false;
+    for (int n = 0; n < njobs && !stop; ++n, it.next()) {
+      const bool ok = row < 2 * (N - it.jg * kRx);
+      float* dst = rad + static_cast<size_t>(it.k) * stride + 2 * it.jg * kRx + row;
+      for (int vg = 0; vg < nvg; ++vg, ++s) {
+        if (*abort_flag || !wait_warp(&sdone[s & 1], (s >> 1) & 1)) { stop = true; break; }
+        tc::fence_after_sync();
+        uint32_t r1[32], r2[32];
+        const uint32_t acc = tmem + (static_cast<uint32_t>(32 * q) << 16) + 64 * (s & 1);
+        tc::tmem_ld32_async(acc, r1);
+        tc::tmem_ld32_async(acc + 32, r2);
+        tc::tmem_wait_ld();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&aempty[s & 1]);
+        const int v0 = vg * kViews, nv = min(kViews, M - v0);
+        float* d = dst + static_cast<size_t>(v0) * rad_view;
+#pragma unroll
+        for (int v = 0; v < kViews; ++v) {
+          const float other =
+              __shfl_xor_sync(0xffffffffu, has_q ? __uint_as_float(r2[v]) : 0.0f, 1);
+          const float p1 = __uint_as_float(r1[v]);
+          if (ok && v < nv) d[static_cast<size_t>(v) * rad_view] = odd ? p1 + other : p1 - other;
+        }
+      }
     }
   }
-  if (njobs > 2) load_A(2, R);
-  // steady state: job n - 1 written out and job n + 1 staged while job n runs
-  for (int n = 1; n <= njobs; ++n) {
-    const int pn = n - 1;  // the job to finish
-    if (!tc::mbar_wait(&bar[pn & 1], (pn >> 1) & 1, kWaitLimit)) fail();
-    tc::fence_after_sync();
-    __syncthreads();
-    if (sMisc[1]) break;
-    if (warp < 4) write_out(tmem, pn);
-    const bool more = n + 1 < njobs;
-    if (more) {
-      stage_B(n + 1);  // into set (n + 1) & 1 = pn & 1, free since job pn is done
-      store_A(n + 1, R);
-      if (n + 2 < njobs) load_A(n + 2, R);  // arrives during the next iteration
-    }
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (more && t == 0) {
-      tc::fence_after_sync();
-      issue(tmem, n + 1);
-    }
-  }
+
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -307,24 +415,53 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-}  // namespace
-
-void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax, const float4* geom,
-                            const float* tx, int M, int stride, size_t rad_view, float* rad,
-                            cudaStream_t s, unsigned* err) {
-  if (K <= 0 || N <= 0 || M <= 0) return;
+template <bool kBulk>
+void launch_radiance(const float* coeffs, int N, int K, int lmax, const unsigned char* image,
+                     int M, int stride, size_t rad_view, float* rad, int grid, cudaStream_t s,
+                     unsigned* err, const CUtensorMap& tmap) {
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(fle_radiance_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(fle_radiance_tc_kernel<kBulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(kSmem));
     configured = true;
   }
+  fle_radiance_tc_kernel<kBulk><<<grid, kThreads, kSmem, s>>>(coeffs, N, K, lmax, image, M,
+                                                              stride, rad_view, rad, err, tmap);
+}
+
+}  // namespace
+
+size_t fle_basis_image_bytes(int K, int M) {
+  return static_cast<size_t>(K) * ((M + kViews - 1) / kViews) * kBStage;
+}
+
+void launch_fle_basis_image(const float4* geom, const float* tx, int K, int M, int lmax,
+                            unsigned char* image, cudaStream_t s) {
+  if (K <= 0 || M <= 0) return;
+  const long long blocks = (static_cast<long long>(K) * ((M + kViews - 1) / kViews) +
+                            kImgThreads / 32 - 1) / (kImgThreads / 32);
+  fle_basis_image_kernel<<<static_cast<unsigned>(blocks), kImgThreads, 0, s>>>(
+      geom, tx, K, M, lmax, fle_rec_table(), image);
+  note_launches(1);
+}
+
+void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax,
+                            const unsigned char* image, int M, int stride, size_t rad_view,
+                            float* rad, cudaStream_t s, unsigned* err) {
+  if (K <= 0 || N <= 0 || M <= 0) return;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(K, nsm));
-  fle_radiance_tc_kernel<<<grid, kThreads, kSmem, s>>>(coeffs, N, K, lmax, geom, tx, M, stride,
-                                                       rad_view, fle_norm_table(lmax), rad, err);
+  const long long jobs = static_cast<long long>(K) * ((N + kRx - 1) / kRx);
+  const int grid = static_cast<int>(std::max(1LL, std::min<long long>(jobs, nsm)));
+  const int L = (lmax + 1) * (lmax + 1);
+  CUtensorMap tmap{};
+  if (encode_fle_rows(&tmap, coeffs, N, K, L))
+    launch_radiance<true>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s, err,
+                          tmap);
+  else
+    launch_radiance<false>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s, err,
+                           tmap);
   note_launches(1);
 }
 
@@ -376,36 +513,34 @@ void launch_film_coeffs(const float* base, const float4* ab, const float4* loc, 
 }
 
 // ---- its backward, from the coefficient gradient G[j][k][.][l]:
-//   dL/dbase_kl = sum_j conj(1 + a_jl) G_jkl      (film_fold_base: a block holds
-//                 the modulation of all receivers in shared memory and takes
-//                 a range of Gaussians, one thread per component)
+//   dL/dbase_kl = sum_j conj(1 + a_jl) G_jkl      (film_fold_base: one thread
+//                 per (Gaussian, component), the receivers summed in order,
+//                 the modulation read through the cache)
 //   dL/da_jl    = sum_k conj(base_kl) G_jkl,  dL/db_jl = sum_k G_jkl
 //                 (film_fold_ab: a block per (receiver, range of Gaussians),
 //                 one thread per component, one float atomic per entry)
-constexpr int kFoldBaseK = 64;   // Gaussians per block
 constexpr int kFoldAbK = 1024;   // Gaussians per block
 
-__global__ void film_fold_base_kernel(const float* __restrict__ G, const float4* __restrict__ ab,
-                                      int N, int K, int L, float* __restrict__ grad_base) {
-  extern __shared__ float4 sAb[];  // [N][L]
-  for (int e = threadIdx.x; e < N * L; e += blockDim.x) sAb[e] = ab[e];
-  __syncthreads();
-  const int l = threadIdx.x;
-  if (l >= L) return;
-  const int k0 = blockIdx.x * kFoldBaseK, k1 = min(K, k0 + kFoldBaseK);
-  for (int k = k0; k < k1; ++k) {
-    float sr = 0.0f, si = 0.0f;
-    for (int j = 0; j < N; ++j) {
-      const float* g = G + (static_cast<size_t>(j) * K + k) * 2 * L;
-      const float gr = g[l], gi = g[L + l];
-      const float4 q = sAb[j * L + l];
-      const float ar = 1.0f + q.x, ai = q.y;  // conj(1 + a) G
-      sr = fmaf(ar, gr, fmaf(ai, gi, sr));
-      si = fmaf(ar, gi, fmaf(-ai, gr, si));
-    }
-    grad_base[static_cast<size_t>(k) * 2 * L + l] += sr;
-    grad_base[static_cast<size_t>(k) * 2 * L + L + l] += si;
+__global__ void __launch_bounds__(256) film_fold_base_kernel(const float* __restrict__ G,
+                                                             const float4* __restrict__ ab, int N,
+                                                             int K, int L,
+                                                             float* __restrict__ grad_base) {
+  const size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;  // (k, l)
+  if (idx >= static_cast<size_t>(K) * L) return;
+  const int k = static_cast<int>(idx / L), l = static_cast<int>(idx % L);
+  const size_t jstride = static_cast<size_t>(K) * 2 * L;
+  const float* g = G + static_cast<size_t>(k) * 2 * L + l;
+  float sr = 0.0f, si = 0.0f;
+#pragma unroll 8
+  for (int j = 0; j < N; ++j) {
+    const float gr = g[j * jstride], gi = g[j * jstride + L];
+    const float4 q = __ldg(&ab[static_cast<size_t>(j) * L + l]);
+    const float ar = 1.0f + q.x, ai = q.y;  // conj(1 + a) G
+    sr = fmaf(ar, gr, fmaf(ai, gi, sr));
+    si = fmaf(ar, gi, fmaf(-ai, gr, si));
   }
+  grad_base[static_cast<size_t>(k) * 2 * L + l] += sr;
+  grad_base[static_cast<size_t>(k) * 2 * L + L + l] += si;
 }
 
 __global__ void film_fold_ab_kernel(const float* __restrict__ G, const float* __restrict__ base,
@@ -414,6 +549,7 @@ __global__ void film_fold_ab_kernel(const float* __restrict__ G, const float* __
   if (l >= L) return;
   const int k0 = blockIdx.x * kFoldAbK, k1 = min(K, k0 + kFoldAbK);
   float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
   for (int k = k0; k < k1; ++k) {
     const float* g = G + (static_cast<size_t>(j) * K + k) * 2 * L;
     const float gr = g[l], gi = g[L + l];
@@ -436,11 +572,9 @@ void launch_film_fold(const float* G, int N, int K, int lmax, const float* base,
   const int L = (lmax + 1) * (lmax + 1);
   if (N <= 0 || K <= 0) return;
   if (grad_base) {
-    const size_t smem = sizeof(float4) * static_cast<size_t>(N) * L;
-    cudaFuncSetAttribute(film_fold_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    film_fold_base_kernel<<<(K + kFoldBaseK - 1) / kFoldBaseK, 128, smem, s>>>(G, ab, N, K, L,
-                                                                              grad_base);
+    const size_t n = static_cast<size_t>(K) * L;
+    film_fold_base_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(G, ab, N, K, L,
+                                                                                grad_base);
     note_launches(1);
   }
   if (d_ab) {

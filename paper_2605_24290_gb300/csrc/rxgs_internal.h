@@ -64,9 +64,10 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
 // buffers.  tmp must hold radix_tmp_words(n) uint32.
 size_t radix_tmp_words(size_t n);
 // n_dev (optional): the actual item count, <= n (launch sizes follow n).
+// err (optional): receives kErrTimeout if a pass's look-back gave up.
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
-                      const uint32_t* n_dev = nullptr);
+                      const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
 
 // ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
 void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
@@ -162,23 +163,32 @@ void launch_occ_probes(const float4* geom, int K, const float* rx, int N, int re
                        const float* box, const float* grid, float2* feat, cudaStream_t s);
 
 // ------------------------------------------ FLE directional radiance (App. E.2)
-// N_l|m| by component index l*l + l + m, l <= 9.
-struct FleNorm {
-  float n[100];
+// The recurrence of the normalised basis y_lm = N_l|m| P_l^m (App. E.2),
+// l, m <= 9: r[l][m] = (a, b) with y_lm = a ct y_{l-1,m} - b y_{l-2,m} for
+// m < l (b = 0 for m = l - 1), y_ll = a st y_{l-1,l-1} for l >= 1 and
+// y_00 = a (ct = cos theta, st = sin theta).
+struct FleRec {
+  float r[10][10][2];
 };
-FleNorm fle_norm_table(int lmax);
-// The tensor-core coefficient gradient (fle_bwd_tc.cu): arguments as
-// launch_fle_backward below; err receives kErrTimeout.
-// With accumulate false grad is written, not added to.
-void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax, const float4* geom,
-                            const float* tx, int M, int stride, size_t rad_view, float* grad,
-                            bool accumulate, cudaStream_t s, unsigned* err);
+FleRec fle_rec_table();
+// The basis operand image (fle_tc.cu): for every (Gaussian, group of 32
+// views) the bf16 hi / lo terms of Yr and Yi in the layout the tensor-core
+// kernels stage (14,336 bytes each), K * ceil(M / 32) blocks.
+size_t fle_basis_image_bytes(int K, int M);
+void launch_fle_basis_image(const float4* geom, const float* tx, int K, int M, int lmax,
+                            unsigned char* image, cudaStream_t s);
+// The tensor-core coefficient gradient (fle_bwd_tc.cu) from the cotangent
+// d_rad (the radiance layout below) and the basis image; err receives
+// kErrTimeout.  With accumulate false grad is written, not added to.
+void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax,
+                            const unsigned char* image, int M, int stride, size_t rad_view,
+                            float* grad, bool accumulate, cudaStream_t s, unsigned* err);
 // The tensor-core contraction of the FLE radiance (fle_tc.cu) for
-// coefficients [N][K][2][L]: rad[v][k][stride] columns 2j, 2j+1 (v < M,
-// rad_view floats per view); err receives kErrTimeout.
-void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax, const float4* geom,
-                            const float* tx, int M, int stride, size_t rad_view, float* rad,
-                            cudaStream_t s, unsigned* err);
+// coefficients [N][K][2][L] and the basis image: rad[v][k][stride] columns
+// 2j, 2j+1 (v < M, rad_view floats per view); err receives kErrTimeout.
+void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax,
+                            const unsigned char* image, int M, int stride, size_t rad_view,
+                            float* rad, cudaStream_t s, unsigned* err);
 // The global FiLM branch over the FLE coefficients (fle_tc.cu): the
 // conditioned coefficients out[N][K][2][L] = (1 + a_jl) base[K][2][L] + b_jl
 // (Eq. film_apply, ab[N][L] = (a.re, a.im, b.re, b.im)), and the fold of

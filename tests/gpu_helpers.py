@@ -39,3 +39,19 @@ def norm_err(x_gpu, x_ref, a_ref):
     if zero.any():
         assert np.all(d[zero] == 0.0), "non-zero output where nothing was composited"
     return float((d / (a + 1e-30)).max()) if d.size else 0.0
+
+
+def fle_abs_radiance(oracle, coeffs, means, centre, lmax):
+    """The absolute chain of the FLE radiance, sum_l (|Re Y_l| + |Im Y_l|)
+    (|Re c_l| + |Im c_l|) as a real radiance [N,K,1,2]: the tensor-core
+    contraction rounds each real product of Y and c (split bf16 terms), so its
+    error scales with this sum, not with |sum_l Y_l c_l|.  Rendered with
+    oracle.render_view, its "absacc" is the error scale of the spectra."""
+    c = np.asarray(coeffs, np.float64)
+    Y = oracle.fle_basis(means, centre, lmax)                       # [K, L]
+    ya = np.abs(Y.real) + np.abs(Y.imag)
+    ca = np.abs(c[:, :, 0, :]) + np.abs(c[:, :, 1, :])              # [N, K, L]
+    chain = (ca * ya[None]).sum(axis=-1)
+    out = np.zeros(c.shape[:2] + (1, 2))
+    out[..., 0, 0] = chain
+    return out
