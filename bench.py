@@ -148,7 +148,7 @@ def whole_job_rate(torch, dist, ms_local, units_per_step, device):
 
 # --------------------------------------------------------------- the step
 class Workload:
-    def __init__(self, torch, rxgs, S, device):
+    def __init__(self, torch, rxgs, S, device, tile=None, cols=0):
         self.torch = torch
         w = S.workload_mlp()
         self.w = w
@@ -156,7 +156,8 @@ class Workload:
         self.g, self.C = g, C
         self.M, self.N, self.K = w["tx"].shape[0], w["rx"].shape[0], sc.K
         d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
-        self.ctx = rxgs.Context(H=g.H, W=g.W)
+        th, tw = tile if tile else (16, 16)
+        self.ctx = rxgs.Context(H=g.H, W=g.W, tile_h=th, tile_w=tw, cols_per_cta=cols)
         self.rxgs = rxgs
         flat = S.flatten_mlp(w["mlp"], C)
         self.nmlp = flat.shape[0]
@@ -239,10 +240,10 @@ def gpu_bench(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    W = Workload(torch, rxgs, S, dev)
+    W = Workload(torch, rxgs, S, dev, tile=args.tile, cols=args.cols)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     tune = None
-    if not args.no_tune:
+    if not args.no_tune and not args.tile:
         # the project's autotuner picks tile shape and columns per CTA on
         # this workload (forward pass); the choice stays in the context
         tune = W.ctx.autotune(W.scene, W.tx, W.rx, W.N, W.kind, iters=2)
@@ -289,9 +290,10 @@ def gpu_bench(args):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = fp32_alu_peak_tflops(sm_mhz, sms)
-    tile = tune["chosen"]["tile"] if tune else [16, 16]
+    tile = tune["chosen"]["tile"] if tune else (list(args.tile) if args.tile else [16, 16])
     # column block of the forward (the backward always takes 128 for 128 columns)
-    cols = tune["chosen"]["cols"] if tune else (128 if 2 * W.N * W.C > 64 else 64)
+    cols = tune["chosen"]["cols"] if tune else (
+        args.cols if args.cols else (128 if 2 * W.N * W.C > 64 else 64))
 
     def roofline(kernel, flops_per_pair, what):
         if kernel not in stages:
@@ -451,7 +453,8 @@ def gpu_bench(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; indoor-room scene recipe)",
-            "config": dict(bench_config(world), tile_autotuned=tune["chosen"] if tune else None),
+            "config": dict(bench_config(world), tile_autotuned=tune["chosen"] if tune else None,
+                           tile=tile, cols=cols),
             "wall_s": round(wall, 3),
             "stages_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in stages.items()},
             "dominant_stage": dom,
@@ -877,6 +880,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tile", type=int, nargs=2, default=None, metavar=("H", "W"),
+                    help="fixed tile shape instead of the autotuner's choice")
+    ap.add_argument("--cols", type=int, default=0, help="columns per CTA with --tile (0: auto)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-coverage", action="store_true")
     ap.add_argument("--no-fle", action="store_true")

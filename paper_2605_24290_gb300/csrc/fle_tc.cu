@@ -127,24 +127,85 @@ constexpr uint32_t kTmemCols = 512;
 // A- lo (24 each)
 constexpr uint32_t kColA = 128, kAPlo = 32, kAQhi = 64, kAQlo = 88;
 
-// The basis image: thread = (Gaussian, view) pair of a block's two
-// (Gaussian, view group) blocks.
-constexpr int kImgThreads = 64;
+// The basis image: thread = (Gaussian, view), warp = (Gaussian, view
+// group).  Fully unrolled (degree and order known at compile time, the
+// recurrence table in the constant bank, components past lmax zero): each
+// component is written as soon as its core-matrix row of 8 is complete.
+constexpr int kImgThreads = 128;
 
 __global__ void __launch_bounds__(kImgThreads) fle_basis_image_kernel(
     const float4* __restrict__ geom, const float* __restrict__ tx, int K, int M, int lmax,
     FleRec rec, unsigned char* __restrict__ image) {
-  __shared__ float2 sRec[100];
-  __shared__ float scratch[kImgThreads / 32][32 * kBPitch];
-  for (int i = threadIdx.x; i < 100; i += kImgThreads)
-    sRec[i] = make_float2(rec.r[i / 10][i % 10][0], rec.r[i / 10][i % 10][1]);
-  __syncthreads();
-  const int nvg = (M + kViews - 1) / kViews;
+  const int nvg = (M + kViews - 1) / kViews, lane = threadIdx.x & 31;
   const long long g = static_cast<long long>(blockIdx.x) * (kImgThreads / 32) + (threadIdx.x >> 5);
   if (g >= static_cast<long long>(K) * nvg) return;
   const int k = static_cast<int>(g / nvg), v0 = static_cast<int>(g % nvg) * kViews;
-  basis_rows(image + g * kBStage, scratch[threadIdx.x >> 5], geom[3 * k], tx, v0,
-             min(kViews, M - v0), lmax, sRec, threadIdx.x & 31);
+  const bool on = lane < M - v0;
+  const float4 p = geom[3 * k];
+  float ct = 1.0f, st = 0.0f, cp = 1.0f, sp = 0.0f;
+  if (on) {
+    const float ux = p.x - tx[3 * (v0 + lane)], uy = p.y - tx[3 * (v0 + lane) + 1],
+                uz = p.z - tx[3 * (v0 + lane) + 2];
+    const float hh2 = ux * ux + uy * uy;
+    const float rho2 = hh2 + uz * uz;
+    // a centre on the transmitter itself (culled by the projection anyway)
+    // takes the +z direction
+    const float irho = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;
+    const float ihh = hh2 > 0.0f ? rsqrtf(hh2) : 0.0f;
+    ct = rho2 > 0.0f ? uz * irho : 1.0f;
+    st = hh2 * ihh * irho;
+    cp = hh2 > 0.0f ? ux * ihh : 1.0f;
+    sp = uy * ihh;
+  }
+  float cm[10], sn[10];
+  cm[0] = on ? 1.0f : 0.0f;  // rows past the views are zero
+  sn[0] = 0.0f;
+#pragma unroll
+  for (int m = 1; m < 10; ++m) {
+    cm[m] = cm[m - 1] * cp - sn[m - 1] * sp;
+    sn[m] = cm[m - 1] * sp + sn[m - 1] * cp;
+  }
+  unsigned char* blk = image + g * kBStage;
+  const uint32_t sub = (lane & 7) * 16;
+  const uint32_t offP = (lane >> 3) * kSboP + sub, offQ = (lane >> 3) * kSboQ + sub;
+  float bp[8], bq[8];
+  float p1[10], p2[10];  // y_{l-1,m}, y_{l-2,m}
+#pragma unroll
+  for (int l = 0; l < 10; ++l) {
+    const float keep = l <= lmax ? 1.0f : 0.0f;
+    float y[10];
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      const float a = rec.r[l][m][0], b = rec.r[l][m][1];
+      if (m == l)
+        y[m] = l == 0 ? a : a * st * p1[m - 1 >= 0 ? m - 1 : 0];
+      else if (m == l - 1)
+        y[m] = a * ct * p1[m];
+      else
+        y[m] = a * ct * p1[m] - b * p2[m];
+      const int kp = kappa_p(l, m);
+      bp[kp & 7] = keep * y[m] * cm[m];
+      if ((kp & 7) == 7) put_octet(blk + kYrHi, blk + kYrLo, offP + (kp >> 3) * 128, bp);
+      if (m > 0) {
+        const int kq = kappa_q(l, m);
+        bq[kq & 7] = keep * y[m] * sn[m];
+        if ((kq & 7) == 7) put_octet(blk + kYiHi, blk + kYiLo, offQ + (kq >> 3) * 128, bq);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m <= l; ++m) {
+      p2[m] = p1[m];
+      p1[m] = y[m];
+    }
+  }
+  // tails: P components 55..63 and Q components 45..47 are zero
+  bp[7] = 0.0f;
+  put_octet(blk + kYrHi, blk + kYrLo, offP + 6 * 128, bp);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) bp[e] = 0.0f;
+  put_octet(blk + kYrHi, blk + kYrLo, offP + 7 * 128, bp);
+  bq[5] = bq[6] = bq[7] = 0.0f;
+  put_octet(blk + kYiHi, blk + kYiLo, offQ + 5 * 128, bq);
 }
 
 // The coefficients of one job -> the A operand in tensor memory: lane = row
