@@ -432,7 +432,7 @@ def gpu_bench(args):
         bcsi = batched_csi_bench(torch, rxgs, S)
     cov = None
     if rank == 0 and not args.no_coverage:
-        cov = coverage_bench(torch, rxgs, S)
+        cov = coverage_bench(torch, rxgs, S, K=args.coverage_gaussians)
     fle = None
     if rank == 0 and not args.no_fle:
         fle = fle_bench(torch, rxgs, S, K=args.fle_gaussians)
@@ -589,7 +589,7 @@ def batched_csi_bench(torch, rxgs, S, reps=3):
             "workload": "300k Gaussians, 256 rx in U{1..64} batches, C=52, bf16 MLP, CSI"}
 
 
-def coverage_bench(torch, rxgs, S, reps=3):
+def coverage_bench(torch, rxgs, S, reps=3, K=None):
     """Coverage map: 1,000,000 Gaussians, 16 transmitters x 1,024 receivers,
     180x360 grid, explicit radiance [1024, 1M, 1, 2] (8.2 GB, resident).
     One step = the transmitter-side preparation of the 16 views (projection,
@@ -599,7 +599,8 @@ def coverage_bench(torch, rxgs, S, reps=3):
     Roofline: HBM, for the weighted sum (the radiance read once for all 16
     views) and the visibility backward (the radiance read once more, the
     gradient read and written once)."""
-    w = S.workload_coverage(with_radiance=False)
+    w = (S.workload_coverage(with_radiance=False) if K is None
+         else S.workload_coverage(K=K, with_radiance=False))
     g, sc = w["grid"], w["scene"]
     M, N, K = w["tx"].shape[0], w["rx"].shape[0], sc.K
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -653,12 +654,13 @@ def coverage_bench(torch, rxgs, S, reps=3):
 
     return {"pairs": M * N, "ms_per_step": round(ms, 3), "rssi_per_s": round(M * N / (ms / 1e3), 1),
             "stages_ms_per_step": stages,
-            "roofline": [hbm("weighted_sum", rad_bytes, "radiance [1024, 1M, 1, 2] read once"),
+            "roofline": [hbm("weighted_sum", rad_bytes, f"radiance [1024, {K:,}, 1, 2] read once"),
                          hbm("vis_bwd", 3 * rad_bytes,
                              "radiance read once, radiance gradient read and written once")],
             "step": "prepare (16 views) + RSSI forward (visibility path) + RSSI backward to "
                     "radiance and opacity",
-            "workload": "1M Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance [1024,1M,1,2]"}
+            "workload": f"{K:,} Gaussians, 16 tx x 1,024 rx, 180x360, explicit radiance "
+                        f"[1024,{K},1,2]"}
 
 
 def fle_bench(torch, rxgs, S, reps=3, lmax=9, K=None):
@@ -889,6 +891,8 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-occupancy", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--coverage-gaussians", type=int, default=None,
+                    help="Gaussians of the coverage section (default: 1,000,000; smaller for profiling)")
     ap.add_argument("--fle-gaussians", type=int, default=None,
                     help="Gaussians of the FLE section (default: the bench scene's 100,000)")
     args = ap.parse_args()

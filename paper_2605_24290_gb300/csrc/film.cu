@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(256) film_wgrad_kernel(FilmDims f, int S, int 
 }
 
 // grad_film += the chunk partials in chunk order (weights and biases), and
-// the embedding and frequency gradients summed over the samples in order.
+// the embedding gradients summed over the samples in order (the frequency
+// vectors: film_freq_grad_kernel).
 __global__ void __launch_bounds__(256) film_grad_finish_kernel(const float* __restrict__ film,
                                                                FilmDims f,
                                                                const float* __restrict__ rx, int N,
@@ -264,22 +265,46 @@ __global__ void __launch_bounds__(256) film_grad_finish_kernel(const float* __re
     for (int j = 0; j < N; ++j)
       acc += sc.DX[(static_cast<size_t>(j) * f.L + l) * f.din + 2 * f.nw + 2 + e];
   } else {
-    // dL/dw_f[d] = sum_j r_j[d] sum_l (DX_sin cos(w_f.r_j) - DX_cos sin(w_f.r_j))
-    const int fq = static_cast<int>(idx / 3), d = static_cast<int>(idx % 3);
-    const float* w = film + f.o_omega + 3 * fq;
-    for (int j = 0; j < N; ++j) {
-      const float* r = rx + 3 * j;
-      const float ph = fmaf(w[2], r[2], fmaf(w[1], r[1], w[0] * r[0]));
-      const float cs = cosf(ph), sn = sinf(ph);
-      float sj = 0.0f;
-      for (int l = 0; l < f.L; ++l) {
-        const float* dx = sc.DX + (static_cast<size_t>(j) * f.L + l) * f.din + 2 * fq;
-        sj += fmaf(dx[0], cs, -dx[1] * sn);
-      }
-      acc = fmaf(sj, r[d], acc);
-    }
+    return;  // the frequency vectors: film_freq_grad_kernel
   }
   grad[idx] += acc;
+}
+
+// dL/dw_f[d] = sum_j r_j[d] sum_l (DX_sin cos(w_f.r_j) - DX_cos sin(w_f.r_j)):
+// block f, warp w takes receivers w, w + 8, ... (lanes over components, a
+// shuffle sum), then the warps' sums in warp order.
+__global__ void __launch_bounds__(256) film_freq_grad_kernel(const float* __restrict__ film,
+                                                             FilmDims f,
+                                                             const float* __restrict__ rx, int N,
+                                                             FilmScratch sc,
+                                                             float* __restrict__ grad) {
+  __shared__ float part[8][3];
+  const int fq = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* w = film + f.o_omega + 3 * fq;
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+  for (int j = warp; j < N; j += 8) {
+    const float* r = rx + 3 * j;
+    const float ph = fmaf(w[2], r[2], fmaf(w[1], r[1], w[0] * r[0]));
+    const float cs = cosf(ph), sn = sinf(ph);
+    float sj = 0.0f;
+    for (int l = lane; l < f.L; l += 32) {
+      const float* dx = sc.DX + (static_cast<size_t>(j) * f.L + l) * f.din + 2 * fq;
+      sj += fmaf(dx[0], cs, -dx[1] * sn);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) acc[d] = fmaf(sj, r[d], acc[d]);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) part[warp][d] = acc[d];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += part[q][threadIdx.x];
+    grad[f.o_omega + 3 * fq + threadIdx.x] += t;
+  }
 }
 
 void launch_film_global(const float* film, const FilmDims& f, const float* rx, int N, float4* ab,
@@ -303,7 +328,8 @@ void launch_film_backward(const float* film, const FilmDims& f, const float* rx,
   film_wgrad_kernel<<<grid, 256, 0, s>>>(f, S, film_chunk_len(S), sc);
   film_grad_finish_kernel<<<static_cast<unsigned>((f.total + 255) / 256), 256, 0, s>>>(
       film, f, rx, N, nchunk, sc, grad_film);
-  note_launches(3);
+  if (f.nw > 0) film_freq_grad_kernel<<<f.nw, 256, 0, s>>>(film, f, rx, N, sc, grad_film);
+  note_launches(f.nw > 0 ? 4 : 3);
 }
 
 }  // namespace rxgs

@@ -536,40 +536,45 @@ namespace rxgs {
 // above then reduces against the basis.  With the local branch (loc[j][k] =
 // (alpha.re, alpha.im, beta.re, beta.im), Eq. combined_local) they become
 // (1 + alpha_jk) c_jkl + beta_jk.
-__global__ void film_coeffs_kernel(const float* __restrict__ base, const float4* __restrict__ ab,
-                                   const float4* __restrict__ loc, int N, int K, int L,
-                                   float* __restrict__ out) {
-  const size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;  // (j, k, l)
-  const size_t total = static_cast<size_t>(N) * K * L;
-  if (idx >= total) return;
-  const int l = static_cast<int>(idx % L);
-  const size_t jk = idx / L;
-  const int k = static_cast<int>(jk % K), j = static_cast<int>(jk / K);
+// block (range of kFilmK Gaussians, receiver j), thread = component l: the
+// modulation (a_jl, b_jl) loaded once, then the Gaussians in turn (both
+// half-rows written coalesced).
+constexpr int kFilmK = 16;
+
+__global__ void __launch_bounds__(128) film_coeffs_kernel(const float* __restrict__ base,
+                                                          const float4* __restrict__ ab,
+                                                          const float4* __restrict__ loc, int K,
+                                                          int L, float* __restrict__ out) {
+  const int l = threadIdx.x, j = blockIdx.y;
+  if (l >= L) return;
   const float4 q = ab[static_cast<size_t>(j) * L + l];
-  const float pr = base[static_cast<size_t>(k) * 2 * L + l];
-  const float pi = base[static_cast<size_t>(k) * 2 * L + L + l];
   const float ar = 1.0f + q.x;
-  float cr = fmaf(ar, pr, fmaf(-q.y, pi, q.z));
-  float ci = fmaf(ar, pi, fmaf(q.y, pr, q.w));
-  if (loc) {
-    const float4 lf = loc[jk];
-    const float alr = 1.0f + lf.x;
-    const float r = fmaf(alr, cr, fmaf(-lf.y, ci, lf.z));
-    ci = fmaf(alr, ci, fmaf(lf.y, cr, lf.w));
-    cr = r;
+  const int k0 = blockIdx.x * kFilmK, k1 = min(K, k0 + kFilmK);
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const float pr = base[static_cast<size_t>(k) * 2 * L + l];
+    const float pi = base[static_cast<size_t>(k) * 2 * L + L + l];
+    float cr = fmaf(ar, pr, fmaf(-q.y, pi, q.z));
+    float ci = fmaf(ar, pi, fmaf(q.y, pr, q.w));
+    const size_t jk = static_cast<size_t>(j) * K + k;
+    if (loc) {
+      const float4 lf = loc[jk];
+      const float alr = 1.0f + lf.x;
+      const float r = fmaf(alr, cr, fmaf(-lf.y, ci, lf.z));
+      ci = fmaf(alr, ci, fmaf(lf.y, cr, lf.w));
+      cr = r;
+    }
+    float* o = out + jk * 2 * L;
+    o[l] = cr;
+    o[L + l] = ci;
   }
-  float* o = out + jk * 2 * L;
-  o[l] = cr;
-  o[L + l] = ci;
 }
 
 void launch_film_coeffs(const float* base, const float4* ab, const float4* loc, int N, int K,
                         int lmax, float* out, cudaStream_t s) {
   const int L = (lmax + 1) * (lmax + 1);
-  const size_t total = static_cast<size_t>(N) * K * L;
-  if (total == 0) return;
-  film_coeffs_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(base, ab, loc, N,
-                                                                               K, L, out);
+  if (N <= 0 || K <= 0) return;
+  film_coeffs_kernel<<<dim3((K + kFilmK - 1) / kFilmK, N), 128, 0, s>>>(base, ab, loc, K, L, out);
   note_launches(1);
 }
 

@@ -1,6 +1,6 @@
 // fle_tc.cuh -- pieces shared by the tensor-core FLE kernels (fle_tc.cu,
-// fle_bwd_tc.cu): the folded component order, the job/step walk and the
-// basis operand of one group of views.
+// fle_bwd_tc.cu): the folded component order, the layout of the basis
+// operand of one group of views, the job walk and the coefficient tensor map.
 //
 // Folding +m and -m (App. E.2).  With Y_{l,m} = N_l|m| P_l^|m|(cos theta)
 // e^{i m phi} the basis of -m is the conjugate of that of +m, so writing
@@ -14,9 +14,10 @@
 // The gradient unfolds the same way: dL/dc_{l,+-m} = dL/dc+ +- dL/dc-.
 //
 // Operand layouts (fixed at the lmax = 9 extents, a smaller degree runs
-// fewer K steps): the basis of one step (32 views, lane = view) as K-major
-// core matrices of 8 views x 8 components, Yr over kP = 64 and Yi over
-// kQ = 48 components, each as hi and lo bf16 terms (14,336 bytes).
+// fewer K steps): the basis of one step (32 views) as K-major core matrices
+// of 8 views x 8 components, Yr over kP = 64 and Yi over kQ = 48 components,
+// each as hi and lo bf16 terms (14,336 bytes).  The basis image holds one
+// such block per (Gaussian, view group) in HBM; the kernels copy it whole.
 #pragma once
 #include <cuda.h>
 
@@ -85,106 +86,6 @@ __device__ __forceinline__ void put_octet(unsigned char* hi, unsigned char* lo, 
   tc::split2(x[6], x[7], h.w, l.w);
   *reinterpret_cast<uint4*>(hi + off) = h;
   *reinterpret_cast<uint4*>(lo + off) = l;
-}
-
-// Scratch row pitch of the float32 basis (odd: the lanes' rows fall in
-// different banks).
-constexpr int kBPitch = kP + kQ + 1;
-constexpr uint32_t kBScratch = 32 * kBPitch * 4;  // bytes per basis warp
-
-// The basis operands of one step: lane = view v0 + lane (zero rows past nv),
-// direction u = p - t_v (polar angle from +z, azimuth atan2(u_y, u_x)),
-// y_lm = N_lm P_l^m(cos theta) by the recurrence in l of `rec` (shared, see
-// FleRec; no Condon-Shortley phase), e^{i m phi} by repeated complex
-// products.  Each degree l updates the ten orders at once (independent
-// chains), m from high to low so that the diagonal reads y_{l-1,l-1} before
-// it is replaced.  The values go to the lane's float32 scratch row (P
-// components, then Q), then 8 at a time into hi and lo core rows.  Ends with
-// the proxy fence that makes the rows visible to the tensor core.
-__device__ __forceinline__ void basis_rows(unsigned char* stage, float* scratch, const float4 p,
-                                           const float* __restrict__ tx, int v0, int nv, int lmax,
-                                           const float2* rec, int lane) {
-  const bool on = lane < nv;
-  float ct = 1.0f, st = 0.0f, cp = 1.0f, sp = 0.0f;
-  if (on) {
-    const float ux = p.x - tx[3 * (v0 + lane)], uy = p.y - tx[3 * (v0 + lane) + 1],
-                uz = p.z - tx[3 * (v0 + lane) + 2];
-    const float hh2 = ux * ux + uy * uy;
-    const float rho2 = hh2 + uz * uz;
-    // a centre on the transmitter itself (culled by the projection anyway)
-    // takes the +z direction
-    const float irho = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;
-    const float ihh = hh2 > 0.0f ? rsqrtf(hh2) : 0.0f;
-    ct = rho2 > 0.0f ? uz * irho : 1.0f;
-    st = hh2 * ihh * irho;
-    cp = hh2 > 0.0f ? ux * ihh : 1.0f;
-    sp = uy * ihh;
-  }
-  const float zero = on ? 1.0f : 0.0f;  // rows past nv are zero
-  float cm[10], sn[10];
-  cm[0] = zero;
-  sn[0] = 0.0f;
-#pragma unroll
-  for (int m = 1; m < 10; ++m) {
-    cm[m] = cm[m - 1] * cp - sn[m - 1] * sp;
-    sn[m] = cm[m - 1] * sp + sn[m - 1] * cp;
-  }
-  float* row = scratch + lane * kBPitch;
-  const int np = (lmax + 1) * (lmax + 2) / 2, nq = lmax * (lmax + 1) / 2;
-  for (int e = np; e < kP; ++e) row[e] = 0.0f;
-  for (int e = nq; e < kQ; ++e) row[kP + e] = 0.0f;
-  float p1[10], p2[10];  // y_{l-1,m}, y_{l-2,m}
-#pragma unroll
-  for (int m = 0; m < 10; ++m) p1[m] = p2[m] = 0.0f;
-#pragma unroll 1
-  for (int l = 0; l <= lmax; ++l) {
-    const float2* rl = rec + 10 * l;
-    float* rp = row + l * (l + 1) / 2;
-    float* rq = row + kP + l * (l - 1) / 2 - 1;
-    // the degree's table row first (no scratch store may come between: the
-    // compiler cannot tell the scratch and the table apart), then the ten
-    // orders branch-free (orders past l computed and dropped)
-    float2 cr[10];
-#pragma unroll
-    for (int m = 0; m < 10; ++m) cr[m] = rl[m];
-#pragma unroll
-    for (int m = 9; m >= 0; --m) {
-      const float2 c = cr[m];
-      const float off = c.x * ct * p1[m] - c.y * p2[m];
-      const float diag = m == 0 ? c.x : c.x * st * p1[m > 0 ? m - 1 : 0];
-      const bool live = m <= l;
-      const float y = m == l ? diag : off;
-      if (live) {
-        rp[m] = y * cm[m];
-        if (m > 0) rq[m] = y * sn[m];
-      }
-      p2[m] = live ? p1[m] : p2[m];
-      p1[m] = live ? y : p1[m];
-    }
-  }
-  __syncwarp();
-  const uint32_t sub = (lane & 7) * 16;  // the view's row within a core matrix
-  const uint32_t offP = (lane >> 3) * kSboP + sub, offQ = (lane >> 3) * kSboQ + sub;
-  // all of a row's reads before its stores (same aliasing reason), P then Q
-  {
-    float x[kP];
-#pragma unroll
-    for (int e = 0; e < kP; ++e) x[e] = row[e];
-#pragma unroll
-    for (int o = 0; o < kP / 8; ++o)
-      put_octet(stage + kYrHi, stage + kYrLo, offP + o * 128,
-                *reinterpret_cast<const float(*)[8]>(&x[8 * o]));
-  }
-  {
-    float x[kQ];
-#pragma unroll
-    for (int e = 0; e < kQ; ++e) x[e] = row[kP + e];
-#pragma unroll
-    for (int o = 0; o < kQ / 8; ++o)
-      put_octet(stage + kYiHi, stage + kYiLo, offQ + o * 128,
-                *reinterpret_cast<const float(*)[8]>(&x[8 * o]));
-  }
-  tc::fence_smem_to_async();
 }
 
 }  // namespace fle

@@ -92,15 +92,19 @@ constexpr int kWsChunk = 1024;   // Gaussians per block
 constexpr int kWsSub = 256;      // Gaussians per shared-memory stage
 constexpr int kWsMaxViews = 16;  // views handled per pass
 
-// Block (chunk of 1024 Gaussians, 256 complex columns q = (j, c)): thread t
-// accumulates sum_k W[v][k] s[j][k][c] for its column and up to 16 views in
-// registers, four Gaussians per step, with the next step's radiance already
-// loading while the current one is multiplied (register double buffer: the
-// kernel is bound by the bytes in flight).  The chunk's visibility weights
-// are staged 256 Gaussians at a time in shared memory as [view][k] and read
-// as 16-byte broadcasts.  With C = 1 (K even) a column's four Gaussians are
-// 32 contiguous bytes, read as two 16-byte loads, so each warp load uses
-// whole sectors.
+// Block (chunk of 1024 Gaussians, 32 complex columns q = (j, c)), eight
+// threads per column: sub-lane u takes the column's Gaussians
+// k0 + 4u + 32i, four at a time, so one warp load covers four rows x 256
+// contiguous bytes (few pages per instruction: the rows of a 1M-Gaussian
+// radiance are 8 MB apart).  The chunk's visibility weights are staged 256
+// Gaussians at a time in shared memory as [view][k] (16-byte reads, eight
+// distinct per quarter warp); all eight loads of a stage are issued before
+// its products, and the eight sub-lanes' sums are added by shuffles at the
+// end (fixed order).  With C = 1 (K even) four Gaussians are 32 contiguous
+// bytes (two 16-byte loads).
+constexpr int kWsCols = 32;      // complex columns per block
+constexpr int kWsPer = kWsSub / 32;  // four-Gaussian groups per sub-lane and stage
+
 template <bool kVec>
 __device__ __forceinline__ void ws_load4(const float2* col, int k, int kk, int kn, int C,
                                          bool act, float2 (&sv)[4]) {
@@ -119,15 +123,15 @@ __device__ __forceinline__ void ws_load4(const float2* col, int k, int kk, int k
 }
 
 template <bool kVec>
-__global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restrict__ rad, int N,
+__global__ void __launch_bounds__(256, 2) weighted_sum_kernel(const float* __restrict__ rad, int N,
                                                            int K, int C,
                                                            const float* __restrict__ W, int M,
                                                            int v0, int nv,
                                                            float* __restrict__ part) {
   __shared__ __align__(16) float sW[kWsMaxViews][kWsSub];
-  const int chunk = blockIdx.x, t = threadIdx.x;
+  const int chunk = blockIdx.x, t = threadIdx.x, u = t & 7;
   const int ncq = N * C;
-  const int qcol = blockIdx.y * 256 + t;
+  const int qcol = blockIdx.y * kWsCols + (t >> 3);
   const bool act = qcol < ncq;
   const int jq = act ? qcol / C : 0, cq = act ? qcol - jq * C : 0;
   const float2* col = reinterpret_cast<const float2*>(rad) + static_cast<size_t>(jq) * K * C + cq;
@@ -137,37 +141,46 @@ __global__ void __launch_bounds__(256) weighted_sum_kernel(const float* __restri
   for (int v = 0; v < kWsMaxViews; ++v) acc[v][0] = acc[v][1] = 0.0f;
   for (int ks = k0; ks < k1; ks += kWsSub) {
     const int kn = min(kWsSub, k1 - ks);
+    // this stage's radiance first (in flight while the weights are staged)
+    float2 sv[kWsPer][4];
+#pragma unroll
+    for (int i = 0; i < kWsPer; ++i) {
+      const int kk = 32 * i + 4 * u;
+      ws_load4<kVec>(col, ks + kk, kk, kn, C, act, sv[i]);
+    }
     __syncthreads();  // the previous stage is consumed
 #pragma unroll
     for (int v = 0; v < kWsMaxViews; ++v)
       sW[v][t] = (v < nv && t < kn) ? W[static_cast<size_t>(v0 + v) * K + ks + t] : 0.0f;
     __syncthreads();
-    // four Gaussians per step; sW is zero past kn, and the loads of
-    // Gaussians past kn are skipped
-    float2 cur[4], nxt[4];
-    ws_load4<kVec>(col, ks, 0, kn, C, act, cur);
-    for (int kk = 0; kk < kn; kk += 4) {
-      if (kk + 4 < kn) ws_load4<kVec>(col, ks + kk + 4, kk + 4, kn, C, act, nxt);
+#pragma unroll
+    for (int i = 0; i < kWsPer; ++i) {
+      const int kk = 32 * i + 4 * u;
 #pragma unroll
       for (int v = 0; v < kWsMaxViews; ++v) {
         const float4 w4 = *reinterpret_cast<const float4*>(&sW[v][kk]);
         float re = acc[v][0], im = acc[v][1];
-        re = fmaf(w4.x, cur[0].x, re);
-        im = fmaf(w4.x, cur[0].y, im);
-        re = fmaf(w4.y, cur[1].x, re);
-        im = fmaf(w4.y, cur[1].y, im);
-        re = fmaf(w4.z, cur[2].x, re);
-        im = fmaf(w4.z, cur[2].y, im);
-        re = fmaf(w4.w, cur[3].x, re);
-        im = fmaf(w4.w, cur[3].y, im);
+        re = fmaf(w4.x, sv[i][0].x, re);
+        im = fmaf(w4.x, sv[i][0].y, im);
+        re = fmaf(w4.y, sv[i][1].x, re);
+        im = fmaf(w4.y, sv[i][1].y, im);
+        re = fmaf(w4.z, sv[i][2].x, re);
+        im = fmaf(w4.z, sv[i][2].y, im);
+        re = fmaf(w4.w, sv[i][3].x, re);
+        im = fmaf(w4.w, sv[i][3].y, im);
         acc[v][0] = re;
         acc[v][1] = im;
       }
-#pragma unroll
-      for (int x = 0; x < 4; ++x) cur[x] = nxt[x];
     }
   }
-  if (!act) return;
+  // the eight sub-lanes of a column (lanes 8a .. 8a + 7 of the warp)
+#pragma unroll
+  for (int v = 0; v < kWsMaxViews; ++v)
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) acc[v][e] += __shfl_xor_sync(0xffffffffu, acc[v][e], o);
+  if (!act || u != 0) return;
   const int twoC = 2 * C;
 #pragma unroll
   for (int v = 0; v < kWsMaxViews; ++v) {
@@ -208,7 +221,7 @@ bool weighted_sum_supported(int C) { return C >= 1; }
 void launch_weighted_sum(const float* rad, int N, int K, int C, const float* W, int M, float* tmp,
                          float* csi, float* rssi, cudaStream_t s) {
   const int nchunks = (K + kWsChunk - 1) / kWsChunk;
-  const unsigned colblocks = static_cast<unsigned>((N * C + 255) / 256);
+  const unsigned colblocks = static_cast<unsigned>((N * C + kWsCols - 1) / kWsCols);
   // 16-byte loads need each receiver row of a single channel to start on 16 B
   const bool vec = C == 1 && K % 2 == 0 && (reinterpret_cast<uintptr_t>(rad) & 15) == 0;
   for (int v0 = 0; v0 < M; v0 += kWsMaxViews) {

@@ -58,10 +58,12 @@ __global__ void __launch_bounds__(256) gamma_kernel(const float* __restrict__ ra
     }
     __syncthreads();
     if (k0 < K) {
-      for (int qq = 0; qq < nq; ++qq) {
+      // the column's four Gaussians; a ring of four register buffers keeps
+      // three columns' loads in flight (unrolled by four: no buffer copy,
+      // which would wait for its load)
+      auto load = [&](int qq, float2 (&sv)[4]) {
         const int q = q0 + qq, j = q / C, c = q - j * C;
         const float2* cp = r2 + (static_cast<size_t>(j) * K + k0) * C + c;
-        float2 sv[4];
         if (kVec && full) {
           const float4 a4 = *reinterpret_cast<const float4*>(cp);
           const float4 b4 = *reinterpret_cast<const float4*>(cp + 2);
@@ -74,6 +76,8 @@ __global__ void __launch_bounds__(256) gamma_kernel(const float* __restrict__ ra
           for (int x = 0; x < 4; ++x)
             sv[x] = k0 + x < K ? cp[static_cast<size_t>(x) * C] : make_float2(0.f, 0.f);
         }
+      };
+      auto step = [&](int qq, const float2 (&sv)[4]) {
 #pragma unroll
         for (int v2 = 0; v2 < kVbViews / 2; ++v2) {
           const float4 g4 = *reinterpret_cast<const float4*>(&sg[qq][2 * v2][0]);
@@ -82,6 +86,19 @@ __global__ void __launch_bounds__(256) gamma_kernel(const float* __restrict__ ra
             acc[2 * v2][x] = fmaf(g4.x, sv[x].x, fmaf(g4.y, sv[x].y, acc[2 * v2][x]));
             acc[2 * v2 + 1][x] = fmaf(g4.z, sv[x].x, fmaf(g4.w, sv[x].y, acc[2 * v2 + 1][x]));
           }
+        }
+      };
+      float2 rb[4][4];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        if (b < nq) load(b, rb[b]);
+      for (int qb = 0; qb < nq; qb += 4) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int qq = qb + b;
+          if (qq >= nq) break;
+          if (qq + 3 < nq) load(qq + 3, rb[(b + 3) & 3]);
+          step(qq, rb[b]);
         }
       }
     }
@@ -251,41 +268,60 @@ __global__ void __launch_bounds__(256) outer_kernel(const float* __restrict__ W,
 #pragma unroll
     for (int x = 0; x < 4; ++x)
       w[v][x] = (v < nv && k0 + x < K) ? W[static_cast<size_t>(v0 + v) * K + k0 + x] : 0.0f;
-  for (int qq = 0; qq < nq; ++qq) {
+  // per column: the four gradient entries read, the update added, written
+  // back; a ring of four register buffers keeps three columns' reads in
+  // flight (unrolled by four: no buffer copy)
+  const bool vec = kVec && k0 + 4 <= K;
+  auto dst_of = [&](int qq) {
     const int q = q0 + qq, j = q / C, c = q - j * C;
-    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    return reinterpret_cast<float2*>(grad) + (static_cast<size_t>(j) * K + k0) * C + c;
+  };
+  auto load = [&](int qq, float2 (&o)[4]) {
+    const float2* d = dst_of(qq);
+    if (vec) {
+      const float4 a4 = reinterpret_cast<const float4*>(d)[0];
+      const float4 b4 = reinterpret_cast<const float4*>(d)[1];
+      o[0] = make_float2(a4.x, a4.y);
+      o[1] = make_float2(a4.z, a4.w);
+      o[2] = make_float2(b4.x, b4.y);
+      o[3] = make_float2(b4.z, b4.w);
+    } else {
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+        o[x] = k0 + x < K ? d[static_cast<size_t>(x) * C] : make_float2(0.f, 0.f);
+    }
+  };
+  auto step = [&](int qq, float2 (&o)[4]) {
 #pragma unroll
     for (int v2 = 0; v2 < kVbViews / 2; ++v2) {
       const float4 g4 = *reinterpret_cast<const float4*>(&sg[qq][2 * v2][0]);
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
-        re[x] = fmaf(w[2 * v2][x], g4.x, fmaf(w[2 * v2 + 1][x], g4.z, re[x]));
-        im[x] = fmaf(w[2 * v2][x], g4.y, fmaf(w[2 * v2 + 1][x], g4.w, im[x]));
+        o[x].x = fmaf(w[2 * v2][x], g4.x, fmaf(w[2 * v2 + 1][x], g4.z, o[x].x));
+        o[x].y = fmaf(w[2 * v2][x], g4.y, fmaf(w[2 * v2 + 1][x], g4.w, o[x].y));
       }
     }
-    float2* dst = reinterpret_cast<float2*>(grad) + (static_cast<size_t>(j) * K + k0) * C + c;
-    if (kVec && k0 + 4 <= K) {
-      float4* d4 = reinterpret_cast<float4*>(dst);
-      float4 a4 = d4[0], b4 = d4[1];
-      a4.x += re[0];
-      a4.y += im[0];
-      a4.z += re[1];
-      a4.w += im[1];
-      b4.x += re[2];
-      b4.y += im[2];
-      b4.z += re[3];
-      b4.w += im[3];
-      d4[0] = a4;
-      d4[1] = b4;
+    float2* d = dst_of(qq);
+    if (vec) {
+      reinterpret_cast<float4*>(d)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+      reinterpret_cast<float4*>(d)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
     } else {
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        if (k0 + x >= K) break;
-        float2 o = dst[static_cast<size_t>(x) * C];
-        o.x += re[x];
-        o.y += im[x];
-        dst[static_cast<size_t>(x) * C] = o;
-      }
+      for (int x = 0; x < 4; ++x)
+        if (k0 + x < K) d[static_cast<size_t>(x) * C] = o[x];
+    }
+  };
+  float2 rb[4][4];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    if (b < nq) load(b, rb[b]);
+  for (int qb = 0; qb < nq; qb += 4) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int qq = qb + b;
+      if (qq >= nq) break;
+      if (qq + 3 < nq) load(qq + 3, rb[(b + 3) & 3]);
+      step(qq, rb[b]);
     }
   }
 }
