@@ -350,7 +350,11 @@ rxgs_status rxgs_serve_stop(rxgs_ctx* ctx);
  * rxgs_render_views computed on `views` is reused when rx, N, radiance (or
  * fle_coeffs, or fle_base with film and its sizes) and the scene
  * (rxgs_update_scene) are unchanged, compared by pointer; otherwise it is
- * recomputed.
+ * recomputed.  A forward that ran with 128-column blocks (the tensor-core
+ * kernel) also leaves on `views` each pixel's stop position and final
+ * transmittance (they depend on the views alone); the backward then skips
+ * the re-walk.  Both reuses assume the backward is ordered after that
+ * forward (same stream, or synchronised).
  * Gradients are accumulated with float atomics (their rounding order is not
  * fixed).
  * Outputs (accumulated: caller zero-fills):

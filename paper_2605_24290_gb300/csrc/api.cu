@@ -495,6 +495,7 @@ rxgs_status rxgs_release_views(rxgs_ctx* ctx, rxgs_views_t views, void* stream) 
   dfree(v->tx, st); dfree(v->rec, st); dfree(v->depth, st); dfree(v->counts, st);
   dfree(v->offsets, st); dfree(v->keys, st); dfree(v->vals, st); dfree(v->ranges, st);
   dfree(v->rad, st); dfree(v->glob, st);
+  dfree(v->tfin, st); dfree(v->stops, st); dfree(v->tile_stop, st);
   delete v;
   ctx->views.erase(it);
   return RXGS_OK;
@@ -744,10 +745,26 @@ rxgs_status rxgs_render_views(rxgs_ctx* ctx, rxgs_views_t views, const float* rx
     a.ncontrib = out->ncontrib;
     a.tfinal = out->tfinal;
     a.err = ctx->d_err;
+    const int cols = pick_cols(ctx, ncols);
+    // the tensor-core forward also leaves the backward's per-pixel state on
+    // the views (kept for their lifetime; without the buffers it is skipped)
+    if (render_fwd_keeps_stops(cols) && !v->stops_valid) {
+      const size_t MHW = static_cast<size_t>(v->M) * g.H * g.W;
+      if (!v->tfin && dalloc(&v->tfin, MHW, st) != cudaSuccess) v->tfin = nullptr;
+      if (!v->stops && dalloc(&v->stops, MHW, st) != cudaSuccess) v->stops = nullptr;
+      if (!v->tile_stop && dalloc(&v->tile_stop, static_cast<size_t>(v->M) * g.T, st) != cudaSuccess)
+        v->tile_stop = nullptr;
+      if (v->tfin && v->stops && v->tile_stop) {
+        a.keep_tfin = v->tfin;
+        a.keep_stops = v->stops;
+        a.keep_tile_stop = v->tile_stop;
+      }
+    }
     {
       Stage sg(ctx, "render_fwd", st);
-      launch_render_fwd(a, pick_cols(ctx, ncols), st);
+      launch_render_fwd(a, cols, st);
     }
+    if (a.keep_tfin) v->stops_valid = true;
     if (reduce) {
       Stage sg(ctx, "reduce", st);
       launch_reduce_tiles(partial, v->M, g.T, N, s->C, (kind & RXGS_OUT_CSI) ? out->csi : nullptr,
@@ -824,9 +841,9 @@ static rxgs_status backward_visibility(rxgs_ctx* ctx, const SceneState* s, const
   if (e == cudaSuccess) e = dalloc(&gamma, MK, st);
   if (e == cudaSuccess && gr->grad_radiance) e = dalloc(&W, MK, st);
   if (e == cudaSuccess && W) e = cudaMemsetAsync(W, 0, sizeof(float) * MK, st);
-  if (e == cudaSuccess) e = dalloc(&tfin, MHW, st);
-  if (e == cudaSuccess) e = dalloc(&stops, MHW, st);
-  if (e == cudaSuccess) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&tfin, MHW, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&stops, MHW, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
   d_tau = gr->grad_opacity;
   if (e == cudaSuccess && !d_tau) e = dalloc(&d_tau, static_cast<size_t>(K), st);
   if (e != cudaSuccess) {
@@ -845,11 +862,16 @@ static rxgs_status backward_visibility(rxgs_ctx* ctx, const SceneState* s, const
   A.f.C = C;
   A.f.ncols = 2 * N * C;
   A.d_tau = d_tau;
-  A.tfin = tfin;
-  A.stops = stops;
-  A.tile_stop = tstop;
   A.n_inst = v->n_inst;
-  {
+  if (v->stops_valid) {
+    // kept by the tensor-core forward on these views
+    A.tfin = v->tfin;
+    A.stops = v->stops;
+    A.tile_stop = v->tile_stop;
+  } else {
+    A.tfin = tfin;
+    A.stops = stops;
+    A.tile_stop = tstop;
     Stage sg(ctx, "bwd_prepass", st);
     launch_bwd_prepass(A, st);
   }
@@ -930,9 +952,9 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   if (e == cudaSuccess) e = dalloc(&d_rad, nrad, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_rad, 0, sizeof(float) * nrad, st);
   const size_t MHW = static_cast<size_t>(M) * g.H * g.W;
-  if (e == cudaSuccess) e = dalloc(&tfin, MHW, st);
-  if (e == cudaSuccess) e = dalloc(&stops, MHW, st);
-  if (e == cudaSuccess) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&tfin, MHW, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&stops, MHW, st);
+  if (e == cudaSuccess && !v->stops_valid) e = dalloc(&tstop, static_cast<size_t>(M) * g.T, st);
   if (e == cudaSuccess && (cot->grad_csi || cot->grad_rssi))
     e = dalloc(&g_uni, static_cast<size_t>(M) * ncols, st);
   d_tau = gr->grad_opacity;
@@ -965,12 +987,17 @@ rxgs_status rxgs_render_backward(rxgs_ctx* ctx, rxgs_views_t views, const float*
   A.g_uniform = g_uni;
   A.d_rad = d_rad;
   A.d_tau = d_tau;
-  A.tfin = tfin;
-  A.stops = stops;
-  A.tile_stop = tstop;
   A.n_inst = v->n_inst;
   A.err = ctx->d_err;
-  {
+  if (v->stops_valid) {
+    // kept by the tensor-core forward on these views
+    A.tfin = v->tfin;
+    A.stops = v->stops;
+    A.tile_stop = v->tile_stop;
+  } else {
+    A.tfin = tfin;
+    A.stops = stops;
+    A.tile_stop = tstop;
     Stage sg(ctx, "bwd_prepass", st);
     launch_bwd_prepass(A, st);
   }

@@ -61,6 +61,13 @@ struct ViewsState {
   int key_lmax = -1;
   int key_N = 0, key_stride = 0;
   uint64_t key_gen = ~0ull;
+  // per-pixel final T and stop position and per-tile largest stop, written
+  // by a tensor-core forward on these views (they depend on the views only),
+  // so that the backward can skip its pre-pass
+  float* tfin = nullptr;
+  uint32_t* stops = nullptr;
+  uint32_t* tile_stop = nullptr;
+  bool stops_valid = false;
 };
 
 struct BatchPlan;    // batch.cu

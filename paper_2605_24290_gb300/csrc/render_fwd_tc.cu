@@ -51,8 +51,8 @@ constexpr uint32_t kOffRec = kOffA2 + kABytes;              // float4 [2][32][2]
 constexpr uint32_t kOffIdx = kOffRec + 2 * kCH * 2 * 16;    // u32 [3][32]
 constexpr uint32_t kOffMask = kOffIdx + 3 * kCH * 4;        // u32 [8]
 constexpr uint32_t kOffBar = kOffMask + 32;                 // u64
-constexpr uint32_t kOffMisc = kOffBar + 8;                  // u32 TMEM base, abort
-constexpr uint32_t kSmemUsed = kOffMisc + 8;
+constexpr uint32_t kOffMisc = kOffBar + 8;                  // u32 TMEM base, abort, tile stop
+constexpr uint32_t kSmemUsed = kOffMisc + 12;
 // requested: more than a third of an SM's shared memory, so at most two CTAs
 // (2 x 256 TMEM columns, all of it) share an SM and an allocation never waits
 constexpr uint32_t kSmem = 80 * 1024;
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
   float T = 1.0f;
   bool alive = valid;
   int ncon = 0, issued = 0;
+  uint32_t stop = valid ? rg.y : rg.x;  // list position after the stopping entry
   for (int n = 0; n < nchunks; ++n) {
     cp_async_wait_all();  // records of chunk n, indices of chunk n + 1
     __syncthreads();
@@ -239,7 +240,10 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
           Tw = __fmul_rn(T, w);
           T = __fmul_rn(T, __fsub_rn(1.0f, w));
           ++ncon;
-          if (T < g.eps_T) alive = false;
+          if (T < g.eps_T) {
+            alive = false;
+            stop = rg.x + static_cast<uint32_t>(n * kCH + bq[q] + 1);
+          }
         }
         put_a(bq[q], Tw);
       }
@@ -313,6 +317,19 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
     const size_t o = static_cast<size_t>(v) * HW + po;
     if (a.ncontrib) a.ncontrib[o] = ncon;
     if (a.tfinal) a.tfinal[o] = T;
+    if (a.keep_tfin) {
+      a.keep_tfin[o] = T;
+      a.keep_stops[o] = stop;
+    }
+  }
+  // the tile's largest stop (reuses the abort word's neighbour: the MMAs and
+  // every wait are over)
+  if (col0 == 0 && a.keep_tile_stop) {
+    if (t == 0) sMisc[2] = rg.x;
+    __syncthreads();
+    atomicMax(&sMisc[2], stop);
+    __syncthreads();
+    if (t == 0) a.keep_tile_stop[static_cast<size_t>(v) * g.T + tile] = sMisc[2];
   }
   tc::fence_before_sync();
   __syncthreads();

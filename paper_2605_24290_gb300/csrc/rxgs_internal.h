@@ -119,7 +119,15 @@ struct RenderArgs {
   int32_t* ncontrib;       // [M][H][W] or null
   float* tfinal;           // [M][H][W] or null
   unsigned* err = nullptr; // device error word (kErrTimeout), or null
+  // the backward's per-pixel state, written by the tensor-core forward when
+  // set (column block 0): final T and stop position per pixel, largest stop
+  // per tile, as the backward pre-pass computes them (render_bwd.cu)
+  float* keep_tfin = nullptr;          // [M][H][W]
+  uint32_t* keep_stops = nullptr;      // [M][H][W]
+  uint32_t* keep_tile_stop = nullptr;  // [M][T]
 };
+// Whether launch_render_fwd writes keep_* for these columns per CTA.
+inline bool render_fwd_keeps_stops(int cols_per_cta) { return cols_per_cta == 128; }
 void launch_render_fwd(const RenderArgs& a, int cols_per_cta, cudaStream_t s);
 
 // Sums partial[M][T][ncols] over tiles -> csi[M][N][C][2], rssi[M][N].

@@ -121,6 +121,46 @@ def test_backward_wide_blocks_tensor_cores(torch, rx, oracle, N, tile):
     assert np.abs(ref_t).max() > 0 and np.abs(ref_r).max() > 0
 
 
+def test_backward_reuses_the_forward_stops(torch, rx, oracle):
+    """A 128-column forward leaves each pixel's stop and final transmittance
+    on the views; the backward then skips its re-walk.  The gradients with
+    that state equal, within float-atomic reordering, those of a backward on
+    freshly prepared views that never saw a forward, and both match the
+    oracle (two views, 64 receivers, 8x32 tiles, an early-stopping eps)."""
+    rng = np.random.default_rng(231)
+    K, N, M = 3000, 64, 2
+    sc = S.draw_scene(rng, K)
+    g = S.Grid()
+    g.tile_h, g.tile_w = 8, 32
+    g.eps_T = 0.05
+    tx = S.draw_points(rng, M)
+    rad = S.draw_radiance(rng, N, K, 1)
+    gs = rng.normal(size=(M, N, g.H, g.W, 1, 2)).astype(np.float32)
+    ctx = ctx_for(rx, g)
+    h = upload(ctx, sc, torch)
+    radd, gsd = dev(rad, torch), dev(gs, torch)
+    grads = []
+    for with_forward in (True, False):
+        views = ctx.prepare(h, dev(tx, torch))
+        if with_forward:
+            spec = torch.zeros((M, N, g.H, g.W, 1, 2), device="cuda")
+            ctx.render_views(views, None, N, rx.OUT_SPECTRA, radiance=radd, spectra=spec)
+        d_rad = torch.zeros_like(radd)
+        d_tau = torch.zeros(K, device="cuda")
+        ctx.render_backward(views, None, N, rx.OUT_SPECTRA, radiance=radd, grad_spectra=gsd,
+                            grad_radiance=d_rad, grad_opacity=d_tau)
+        ctx.sync()
+        grads.append((d_rad.cpu().numpy(), d_tau.cpu().numpy()))
+        ctx.release_views(views)
+    ref_r, ref_t, abs_r, abs_t = oracle_grads(oracle, g, sc, tx, rad, gs.astype(np.float64))
+    for d_r, d_t in grads:
+        assert scaled_err(d_r, ref_r, abs_r) <= TOL
+        assert scaled_err(d_t, ref_t, abs_t) <= TOL
+    # the same stops: only the atomics' order differs
+    assert scaled_err(grads[0][0], grads[1][0], abs_r) <= 1e-6
+    assert scaled_err(grads[0][1], grads[1][1], abs_t) <= 1e-6
+
+
 def test_backward_csi_and_rssi_cotangents(torch, rx, oracle):
     """dL/dCSI and dL/dRSSI act as pixel-uniform cotangents on the spectra."""
     rng = np.random.default_rng(202)
