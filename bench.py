@@ -176,13 +176,15 @@ class Workload:
         self.d_mlp = torch.zeros(self.nmlp, device=device)
         self.kind = rxgs.OUT_SPECTRA | rxgs.OUT_CSI | rxgs.OUT_RSSI
 
-    def step(self, tx=None, rx=None, gspec=None, before_backward=None):
+    def step(self, tx=None, rx=None, gspec=None, before_backward=None, spec=None, rssi=None):
         c, rx_ = self.ctx, self.rxgs
         tx = self.tx if tx is None else tx
         rx = self.rx if rx is None else rx
         gspec = self.gspec if gspec is None else gspec
+        spec = self.spec if spec is None else spec
+        rssi = self.rssi if rssi is None else rssi
         views = c.prepare(self.scene, tx)
-        c.render_views(views, rx, self.N, self.kind, spectra=self.spec, csi=self.csi, rssi=self.rssi)
+        c.render_views(views, rx, self.N, self.kind, spectra=spec, csi=self.csi, rssi=rssi)
         if before_backward is not None:
             before_backward()
         self.d_tau.zero_()
@@ -375,45 +377,76 @@ def gpu_bench(args):
         d2h = (o_tau.numel() + o_base.numel() + o_mlp.numel() + o_rssi.numel() +
                o_spec.numel()) * 4
 
-        # the cotangent (531 MB) is only needed by the backward: its copy runs
-        # on a side stream, overlapped with prepare + forward
-        copy_stream = torch.cuda.Stream()
+        # Every step copies its own inputs in and its results out, through
+        # two copy streams (copies in one direction share a copy engine in
+        # issue order, so nothing small is queued behind a large copy): step
+        # k + 1's tx, rx and then its cotangent (531 MB, needed only by the
+        # backward) go up while step k computes, into the other of two device
+        # buffers; step k's spectra come down while its backward and the
+        # next forward run (with its RSSI), and its gradients after its
+        # backward.
+        copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
+        d_txs = [d_tx, torch.empty_like(W.tx)]
+        d_rxs = [d_rx, torch.empty_like(W.rx)]
+        d_gs = [d_g, torch.empty_like(W.gspec)]
+        specs = [W.spec, torch.empty_like(W.spec)]
+        rssis = [W.rssi, torch.empty_like(W.rssi)]
+        ev = lambda: [torch.cuda.Event(), torch.cuda.Event()]
+        ev_in, ev_g, ev_bwd, ev_out, ev_small = ev(), ev(), ev(), ev(), ev()
 
-        def e2e_step():
-            d_tx.copy_(h_tx, non_blocking=True)
-            d_rx.copy_(h_rx, non_blocking=True)
-            with torch.cuda.stream(copy_stream):
-                d_g.copy_(h_g, non_blocking=True)
-                g_ready = torch.cuda.Event()
-                g_ready.record(copy_stream)
-            # the spectra (531 MB) go back to the host on the side stream while
-            # the backward runs
+        def upload(k):
+            b = k % 2
+            if k >= 2:
+                copy_in.wait_event(ev_bwd[b])  # step k - 2 is done with buffers b
+            with torch.cuda.stream(copy_in):
+                d_txs[b].copy_(h_tx, non_blocking=True)
+                d_rxs[b].copy_(h_rx, non_blocking=True)
+                ev_in[b].record(copy_in)
+                d_gs[b].copy_(h_g, non_blocking=True)
+                ev_g[b].record(copy_in)
+
+        def e2e_step(k, last):
+            cur = torch.cuda.current_stream()
+            b = k % 2
+            if k >= 2:
+                cur.wait_event(ev_out[b])  # the spectra of step k - 2 are down
+            cur.wait_event(ev_in[b])
+            if not last:
+                upload(k + 1)
+
             def before_backward():
-                cur = torch.cuda.current_stream()
-                cur.wait_event(g_ready)
                 f_done = torch.cuda.Event()
                 f_done.record(cur)
-                copy_stream.wait_event(f_done)
-                with torch.cuda.stream(copy_stream):
-                    o_spec.copy_(W.spec, non_blocking=True)
-                    s_done.record(copy_stream)
+                copy_out.wait_event(f_done)
+                with torch.cuda.stream(copy_out):
+                    o_spec.copy_(specs[b], non_blocking=True)
+                    o_rssi.copy_(rssis[b], non_blocking=True)
+                    ev_out[b].record(copy_out)
+                cur.wait_event(ev_g[b])
+                if k >= 1:
+                    cur.wait_event(ev_small[1 - b])  # step k - 1's gradients are down
 
-            s_done = torch.cuda.Event()
-            W.step(d_tx, d_rx, d_g, before_backward=before_backward)
-            torch.cuda.current_stream().wait_event(s_done)
-            o_tau.copy_(W.d_tau, non_blocking=True)
-            o_base.copy_(W.d_base, non_blocking=True)
-            o_mlp.copy_(W.d_mlp, non_blocking=True)
-            o_rssi.copy_(W.rssi, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            W.step(d_txs[b], d_rxs[b], d_gs[b], before_backward=before_backward, spec=specs[b],
+                   rssi=rssis[b])
+            ev_bwd[b].record(cur)
+            copy_out.wait_event(ev_bwd[b])
+            with torch.cuda.stream(copy_out):
+                o_tau.copy_(W.d_tau, non_blocking=True)
+                o_base.copy_(W.d_base, non_blocking=True)
+                o_mlp.copy_(W.d_mlp, non_blocking=True)
+                ev_small[b].record(copy_out)
 
-        for _ in range(2):
-            e2e_step()
-        n_e = max(3, args.steps // 2)
+        def e2e_run(n):
+            upload(0)
+            for k in range(n):
+                e2e_step(k, k == n - 1)
+            torch.cuda.synchronize()
+
+        e2e_run(2)
+        n_e = max(5, args.steps)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(n_e):
-            e2e_step()
+        e2e_run(n_e)
         barrier()
         e_ms = (time.perf_counter() - t0) * 1e3 / n_e
         e_ms, e_val = whole_job_rate(torch, dist if world > 1 else None, e_ms, spectra_per_step,
@@ -422,7 +455,9 @@ def gpu_bench(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e_ms, 4),
                "copies": "H2D tx, rx and the spectra cotangent; D2H the spectra, RSSI and the "
-                         "opacity, phi_base and MLP gradients (pinned host buffers)"}
+                         "opacity, phi_base and MLP gradients (pinned host buffers); the next "
+                         "step's cotangent goes up and this step's spectra come down on two copy "
+                         "streams while the GPU computes"}
 
     serve = None
     if rank == 0 and not args.no_serve:

@@ -19,9 +19,10 @@
 // group), each with one step per group of 32 views, through warp-specialised
 // stages on mbarriers:
 //   warp 0       per job one TMA copy (a tensor-map box of the job's 64
-//                coefficient rows) into one of three shared-memory stages,
-//                per step one bulk copy of the basis block into one of two
-//                B stages;
+//                coefficient rows) into one of three shared-memory stages;
+//   warp 2       per step one bulk copy of the basis block into one of two
+//                B stages (a producer of its own, so that neither copy
+//                stream waits behind the other);
 //   warps 4-7,   fold and split the coefficients (lane = accumulator row)
 //   12-15        and store the A operand into tensor memory (tcgen05.st),
 //                double-buffered; the two groups take even and odd jobs;
@@ -310,27 +311,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
 
   if (warp == 0) {
-    // ---------------------------------------------------------------- producer
+    // ------------------------------------------------- coefficient producer
     // per job one box of the coefficient rows (rows j0 .. j0 + 63 of Gaussian
-    // k; rows past N read as zero), per step the view group's basis block
-    if (lane == 0) {
+    // k; rows past N read as zero)
+    if (kBulk && lane == 0) {
       const uint32_t box_bytes = static_cast<uint32_t>(min(kRx, N)) * 8u * L;
-      int cissued = 0, s = 0, bissued = 0;
+      int issued = 0;
+      JobIter it(K);
+      for (int n = 0; n < njobs; ++n, it.next()) {
+        if (*abort_flag) break;
+        const int st = n % kStages;
+        if (n >= kStages && !tc::mbar_wait(&cempty[st], ((n / kStages) - 1) & 1, kWaitLimit)) {
+          fail();
+          break;
+        }
+        tc::mbar_arrive_expect_tx(&cfull[st], box_bytes);
+        tc::tma_load_3d(sm + st * kCStage, &tmap, 0, it.k, it.jg * kRx, &cfull[st]);
+        issued = n + 1;
+      }
+      // copies of a walk cut short land before the CTA exits
+      for (int n = max(0, issued - kStages); n < issued; ++n)
+        tc::mbar_wait(&cfull[n % kStages], (n / kStages) & 1, kWaitLimit);
+    }
+    __syncwarp();
+  } else if (warp == 2) {
+    // ------------------------------------------------------- basis producer
+    // per step the view group's basis block into one of two B stages
+    if (lane == 0) {
+      int s = 0, issued = 0;
       bool stop = false;
       JobIter it(K);
       for (int n = 0; n < njobs && !stop; ++n, it.next()) {
-        if (*abort_flag) break;
-        const int st = n % kStages;
-        if (kBulk) {
-          if (n >= kStages && !tc::mbar_wait(&cempty[st], ((n / kStages) - 1) & 1, kWaitLimit)) {
-            fail();
-            break;
-          }
-          tc::mbar_arrive_expect_tx(&cfull[st], box_bytes);
-          tc::tma_load_3d(sm + st * kCStage, &tmap, 0, it.k, it.jg * kRx, &cfull[st]);
-          cissued = n + 1;
-        }
         for (int vg = 0; vg < nvg; ++vg, ++s) {
+          if (*abort_flag) { stop = true; break; }
           if (s >= 2 && !tc::mbar_wait(&sdone[s & 1], ((s >> 1) - 1) & 1, kWaitLimit)) {
             fail();
             stop = true;
@@ -340,13 +353,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::bulk_g2s(sm + kOffB + (s & 1) * kBStage,
                        image + (static_cast<size_t>(it.k) * nvg + vg) * kBStage, kBStage,
                        &bfull[s & 1]);
-          bissued = s + 1;
+          issued = s + 1;
         }
       }
-      // copies of a walk cut short land before the CTA exits
-      for (int n = max(0, cissued - kStages); n < cissued; ++n)
-        tc::mbar_wait(&cfull[n % kStages], (n / kStages) & 1, kWaitLimit);
-      for (int q = max(0, bissued - 2); q < bissued; ++q)
+      for (int q = max(0, issued - 2); q < issued; ++q)
         tc::mbar_wait(&bfull[q & 1], (q >> 1) & 1, kWaitLimit);
     }
     __syncwarp();
