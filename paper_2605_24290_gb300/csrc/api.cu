@@ -535,6 +535,14 @@ FilmDims desc_film_dims(const rxgs_render_desc* d) {
   return film_dims(d->film_nfreq, d->film_embed, d->film_hidden, d->fle_lmax);
 }
 
+// The FLE contraction writes columns [0, used) of every row; the pad columns
+// [used, stride) are read by the compositing as zero radiance.
+void clear_pad_columns(float* rad, size_t rows, int stride, int used, cudaStream_t st) {
+  if (stride > used)
+    cudaMemset2DAsync(rad + used, sizeof(float) * stride, 0, sizeof(float) * (stride - used), rows,
+                      st);
+}
+
 // Produces the Gaussian-major radiance [K][stride] for receivers rx[N]; with
 // FLE coefficients, one such array per view of v ([M][K][stride]).
 rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* v,
@@ -578,7 +586,7 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
       Stage sb(ctx, "fle_basis", st);  // within the radiance stage
       launch_fle_basis_image(s->geom, v->tx, s->K, v->M, d->fle_lmax, image, st);
     }
-    cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
+    clear_pad_columns(rad, static_cast<size_t>(v->M) * s->K, stride, 2 * N, st);
     launch_fle_radiance_tc(coeffs, N, s->K, d->fle_lmax, image, v->M, stride,
                            static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
     dfree(image, st);
@@ -592,8 +600,7 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
       Stage sb(ctx, "fle_basis", st);  // within the radiance stage
       launch_fle_basis_image(s->geom, v->tx, s->K, v->M, d->fle_lmax, image, st);
     }
-    // pad columns of every row stay zero
-    cudaMemsetAsync(rad, 0, sizeof(float) * static_cast<size_t>(v->M) * s->K * stride, st);
+    clear_pad_columns(rad, static_cast<size_t>(v->M) * s->K, stride, 2 * N, st);
     launch_fle_radiance_tc(d->fle_coeffs, N, s->K, d->fle_lmax, image, v->M, stride,
                            static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
     dfree(image, st);
