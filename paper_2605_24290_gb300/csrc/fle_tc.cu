@@ -71,9 +71,10 @@ FleRec fle_rec_table() {
   return t;
 }
 
-namespace fle {
+namespace tc {
 
-bool encode_fle_rows(CUtensorMap* map, const float* base, int N, int K, int L) {
+bool encode_f32_tiled(CUtensorMap* map, const float* base, int rank, const uint64_t* dims,
+                      const uint64_t* strides, const uint32_t* box) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -89,18 +90,40 @@ bool encode_fle_rows(CUtensorMap* map, const float* base, int N, int K, int L) {
         q == cudaDriverEntryPointSuccess)
       encode = reinterpret_cast<Encode>(fn);
   }
-  if (!encode || (L & 3) != 0 || 2 * L > 256 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+  if (!encode || rank < 1 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
     return false;
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(2 * L), static_cast<cuuint64_t>(K),
-                              static_cast<cuuint64_t>(N)};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(2 * L) * 4,
-                                 static_cast<cuuint64_t>(K) * 2 * L * 4};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(2 * L), 1,
-                             static_cast<cuuint32_t>(N < kRx ? N : kRx)};
-  const cuuint32_t unit[3] = {1, 1, 1};
-  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides,
-                box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], unit[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    unit[i] = 1;
+    if (box[i] < 1 || box[i] > 256) return false;
+    if (i + 1 < rank) {
+      st[i] = strides[i];
+      if ((strides[i] & 15) != 0) return false;
+    }
+  }
+  if ((box[0] * 4u) % 16u != 0) return false;
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, static_cast<cuuint32_t>(rank),
+                const_cast<float*>(base), d, st, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+namespace fle {
+
+bool encode_fle_rows(CUtensorMap* map, const float* base, int N, int K, int L) {
+  if ((L & 3) != 0 || 2 * L > 256) return false;
+  const uint64_t dims[3] = {static_cast<uint64_t>(2 * L), static_cast<uint64_t>(K),
+                            static_cast<uint64_t>(N)};
+  const uint64_t strides[2] = {static_cast<uint64_t>(2 * L) * 4,
+                               static_cast<uint64_t>(K) * 2 * L * 4};
+  const uint32_t box[3] = {static_cast<uint32_t>(2 * L), 1,
+                           static_cast<uint32_t>(N < kRx ? N : kRx)};
+  return tc::encode_f32_tiled(map, base, 3, dims, strides, box);
 }
 
 }  // namespace fle

@@ -55,15 +55,17 @@ constexpr int kThreads = 512;
 // Operand buffers, 8x8 bf16 core matrices (128 bytes each):
 //   g[p][c]: core (p/8, c/8) at (p/8 * 16 + c/8) * 128
 //   s[b][c]: core (b/8, c/8) at (b/8) * kSboS + (c/8) * kLboS
-//   a[b][p]: core (b/8, p/8) at (b/8) * kSboA + (p/8) * kLboA
-// (s and a are written every chunk; their 144-byte core pitch along K spreads
-// a warp's stores over all banks).
+//   a[b][p]: MN-major (8 entries of one pixel are one 16-byte core row):
+//            core (p/8, b/8) at (p/8) * kKsA + (b/8) * kMnA
+// (s is written every chunk; its 144-byte core pitch along K spreads a warp's
+// stores over all banks; a is written 8 entries per 16-byte store, 8 lanes
+// of a quarter warp on one 128-byte span).
 constexpr uint32_t kLboG = 128, kSboG = 16 * 128;
 constexpr uint32_t kLboS = 144, kSboS = 16 * kLboS;
-constexpr uint32_t kLboA = 144, kSboA = 32 * kLboA;
+constexpr uint32_t kMnA = 128, kKsA = 4 * kMnA;
 constexpr uint32_t kGBytes = kP * kNB * 2;
 constexpr uint32_t kSBytes = 4 * kSboS;
-constexpr uint32_t kABytes = 4 * kSboA;
+constexpr uint32_t kABytes = (kP / 8) * kKsA;
 constexpr uint32_t kOffG1 = 0, kOffG2 = kGBytes;
 constexpr uint32_t kOffS1 = 2 * kGBytes, kOffS2 = kOffS1 + kSBytes;
 constexpr uint32_t kOffA1 = kOffS2 + kSBytes, kOffA2 = kOffA1 + kABytes;
@@ -72,22 +74,25 @@ constexpr uint32_t kOffRec = kOffW + kCH * kP * 4;        // float4 [2][32][2]
 constexpr uint32_t kOffIdx = kOffRec + 2 * kCH * 2 * 16;  // u32 [4][32] list indices
 constexpr uint32_t kOffTQ = kOffIdx + 4 * kCH * 4;        // float2 [256] T, Q per pixel
 constexpr uint32_t kOffMask = kOffTQ + kP * 8;            // u32 [8] strip masks
-constexpr uint32_t kOffBar = kOffMask + 64;               // u64 [2] mbarriers
-constexpr uint32_t kOffMisc = kOffBar + 16;               // u32 TMEM base, abort, #gamma, #dlds
+constexpr uint32_t kOffBar = kOffMask + 64;               // u64 [3] mbarriers
+constexpr uint32_t kOffMisc = kOffBar + 24;               // u32 TMEM base, abort, #gamma, #dlds
 constexpr uint32_t kSmem = kOffMisc + 16;
 static_assert(kSmem <= 232448, "shared memory");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+static_assert(kOffW % 16 == 0 && kOffA1 % 16 == 0 && kOffA2 % 16 == 0, "16-byte operand rows");
 
 constexpr uint32_t kTmemCols = 128;  // gamma: columns 0-63 (two M tiles), dL/ds: 64-95
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdescGamma = tc::idesc_bf16(128, 32, 0, 0);
-constexpr uint32_t kIdescDlds = tc::idesc_bf16(128, 32, 1, 0);
+constexpr uint32_t kIdescDlds = tc::idesc_bf16(128, 32, 1, 1);
 
 __device__ __forceinline__ uint32_t g_off(int p, int c) {
   return ((p >> 3) * 16 + (c >> 3)) * 128 + (p & 7) * 16 + (c & 7) * 2;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const BackwardArgs A) {
+__global__ void __launch_bounds__(kThreads, 1)
+    render_bwd_tc_kernel(const BackwardArgs A, int next_stride, int g_tma,
+                         const __grid_constant__ CUtensorMap gmap) {
   extern __shared__ __align__(128) unsigned char sm[];
   float* sW = reinterpret_cast<float*>(sm + kOffW);
   float4* sRec0 = reinterpret_cast<float4*>(sm + kOffRec);
@@ -96,6 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
   uint32_t* sMask = reinterpret_cast<uint32_t*>(sm + kOffMask);
   uint64_t* barG = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* barD = barG + 1;
+  uint64_t* barT = barG + 2;  // the cotangent tile's TMA copy
   uint32_t* sMisc = reinterpret_cast<uint32_t*>(sm + kOffMisc);
 
   const RenderArgs& a = A.f;
@@ -150,23 +156,26 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     cp_async16(&rb[2 * l + 0], &rec[2 * k + 0], ok);
     cp_async16(&rb[2 * l + 1], &rec[2 * k + 1], ok);
   };
-  // all threads: radiance of chunk n, entry t / 16, 8 columns from 8 (t % 16)
-  auto load_rad = [&](int n, float (&x)[8]) {
+  // all threads: radiance of chunk n, entry t / 16, 8 columns from 8 (t % 16);
+  // past the chunk the loads read entry 0's row (always in the array) and
+  // store_rad writes zeros, so nothing waits for the loads before the
+  // recurrence has run
+  auto load_rad = [&](int n, float (&x)[8]) -> bool {
     const int b = t >> 4, cg = t & 15;
     const bool ok = b < chunk_len(n);
     const uint32_t k = ok ? sIdx[(n & 3) * kCH + b] : 0u;
     const float4* src =
         reinterpret_cast<const float4*>(radv + static_cast<size_t>(k) * a.stride + col0 + cg * 8);
-    const float4 r0 = ok ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 r1 = ok ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 r0 = src[0], r1 = src[1];
     x[0] = r0.x; x[1] = r0.y; x[2] = r0.z; x[3] = r0.w;
     x[4] = r1.x; x[5] = r1.y; x[6] = r1.z; x[7] = r1.w;
+    return ok;
+  };
+  auto store_rad = [&](float (&x)[8], bool ok) {
+    const int b = t >> 4, cg = t & 15;
 #pragma unroll
     for (int e = 0; e < 8; ++e)
-      if (col0 + cg * 8 + e >= a.ncols) x[e] = 0.0f;
-  };
-  auto store_rad = [&](const float (&x)[8]) {
-    const int b = t >> 4, cg = t & 15;
+      if (!ok || col0 + cg * 8 + e >= a.ncols) x[e] = 0.0f;
     uint4 hi, lo;
     tc::split8(x, hi, lo);
     const uint32_t off = (b >> 3) * kSboS + cg * kLboS + (b & 7) * 16;
@@ -212,14 +221,15 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     // g read MN-major: M = columns (core pitch 128 B), K = pixels (core pitch 2048 B)
     const uint64_t dg[2] = {tc::smem_desc(sbase + kOffG1, kSboG, kLboG),
                             tc::smem_desc(sbase + kOffG2, kSboG, kLboG)};
-    const uint64_t da[2] = {tc::smem_desc(sbase + kOffA1, kLboA, kSboA),
-                            tc::smem_desc(sbase + kOffA2, kLboA, kSboA)};
+    // a read MN-major: N = entries (core pitch 128 B), K = pixels (512 B)
+    const uint64_t da[2] = {tc::smem_desc(sbase + kOffA1, kKsA, kMnA),
+                            tc::smem_desc(sbase + kOffA2, kKsA, kMnA)};
 #pragma unroll
     for (int k = 0; k < kP / 16; ++k)
 #pragma unroll
       for (int term = 0; term < 3; ++term) {
         const uint64_t a_d = dg[term == 2] + ((k * 2 * kSboG) >> 4);
-        const uint64_t b_d = da[term == 1] + ((2 * k * kLboA) >> 4);
+        const uint64_t b_d = da[term == 1] + ((2 * k * kKsA) >> 4);
         tc::mma_bf16(tmem + 64, a_d, b_d, kIdescDlds, (k | term) != 0);
       }
   };
@@ -229,10 +239,19 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
   if (t == 256) {
     tc::mbar_init(barG, 1);
     tc::mbar_init(barD, 1);
+    tc::mbar_init(barT, 1);
     tc::mbar_fence_init();
     sMisc[1] = 0;
     sMisc[2] = 0;
     sMisc[3] = 0;
+    if (g_tma) {
+      // the tile's cotangent as float32 [kNB / 2C receivers][TH rows][TW
+      // pixels x 2C] into the g buffers (one box; out-of-range rows,
+      // pixels and receivers read as zero), split in place below; it needs
+      // nothing loaded first, so it overlaps the list-index chain
+      tc::mbar_arrive_expect_tx(barT, 2 * kGBytes);
+      tc::tma_load_4d(sm + kOffG1, &gmap, tcol * g.TW * twoC, tr * g.TH, col0 / twoC, v, barT);
+    }
   }
   if (warp == 8 && nchunks > 0) {
     copy_indices(0);
@@ -242,8 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
   }
   // cotangent tile -> g (bf16 x 2): thread t takes pixel p and the 8-column
   // octets (t >> 8) + 2r; every (re, im) column pair is one 8-byte load, all
-  // 32 of a thread in flight before the split
-  {
+  // 32 of a thread in flight before the split (without the TMA copy)
+  if (!g_tma) {
     float2 xv[8][4];
     const size_t pix = static_cast<size_t>(i) * g.W + jj;
 #pragma unroll
@@ -286,12 +305,77 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     gather_rec(0);
     cp_async_commit();
   }
-  if (nchunks > 0) {
+  {
     float x[8];
-    load_rad(0, x);
-    store_rad(x);
+    const bool ok = nchunks > 0 && load_rad(0, x);
+    if (g_tma) {
+      // the copied tile: thread t reads pixel p's (re, im) pairs of octets
+      // (t >> 8) + 2r, then (every read done) writes them split in place
+      if (!tc::mbar_wait(barT, 0, kWaitLimit)) fail();
+      const float* stg = reinterpret_cast<const float*>(sm + kOffG1);
+      const int y = p / g.TW, px = p % g.TW, rowf = g.TW * twoC;
+      float2 xv[8][4];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int oc = (t >> 8) + 2 * r;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c = oc * 8 + 2 * e, z = c / twoC, ec = c - z * twoC;
+          float2 val = *reinterpret_cast<const float2*>(&stg[(z * g.TH + y) * rowf + px * twoC + ec]);
+          if (A.g_uniform && valid && col0 + c < a.ncols) {
+            const float2 u = *reinterpret_cast<const float2*>(
+                &A.g_uniform[static_cast<size_t>(v) * a.ncols + col0 + c]);
+            val.x += u.x;
+            val.y += u.y;
+          }
+          xv[r][e] = val;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int oc = (t >> 8) + 2 * r;
+        const float xs[8] = {xv[r][0].x, xv[r][0].y, xv[r][1].x, xv[r][1].y,
+                             xv[r][2].x, xv[r][2].y, xv[r][3].x, xv[r][3].y};
+        uint4 hi, lo;
+        tc::split8(xs, hi, lo);
+        const uint32_t off = g_off(p, oc * 8);
+        *reinterpret_cast<uint4*>(sm + kOffG1 + off) = hi;
+        *reinterpret_cast<uint4*>(sm + kOffG2 + off) = lo;
+      }
+    }
+    if (nchunks > 0) store_rad(x, ok);
   }
   const uint32_t tmem = sMisc[0];
+
+  // The cotangent tile of the CTA likely to start next on this SM (linear
+  // index + the CTAs resident at once) into L2, so that its prologue reads
+  // hit L2 instead of waiting on HBM: one thread per (receiver, tile row)
+  // segment, one prefetch per 128-byte line.
+  if (A.g_spec && next_stride > 0) {
+    const long long total = static_cast<long long>(gridDim.x) * gridDim.y * gridDim.z;
+    const long long nxt =
+        blockIdx.x + static_cast<long long>(gridDim.x) * (blockIdx.y + static_cast<long long>(gridDim.y) * blockIdx.z) +
+        next_stride;
+    if (nxt < total) {
+      const int tile2 = static_cast<int>(nxt % gridDim.x);
+      const long long r2 = nxt / gridDim.x;
+      const int v2 = static_cast<int>(r2 / gridDim.y);
+      const int c0 = static_cast<int>(r2 % gridDim.y) * kNB, c1 = min(a.ncols, c0 + kNB) - 1;
+      const int j0 = c0 / twoC, nj = c1 / twoC - j0 + 1;
+      const int i0 = (tile2 / g.tiles_w) * g.TH, jj0 = (tile2 % g.tiles_w) * g.TW;
+      const int rows = min(g.TH, g.H - i0), ncol = min(g.TW, g.W - jj0);
+      for (int q = t; q < nj * rows; q += kThreads) {
+        const int j = j0 + q / rows, i = i0 + q % rows;
+        const float* row = A.g_spec + ((static_cast<size_t>(v2) * a.N + j) * HW +
+                                       static_cast<size_t>(i) * g.W + jj0) * twoC;
+        const uintptr_t e = reinterpret_cast<uintptr_t>(row + static_cast<size_t>(ncol) * twoC);
+        for (uintptr_t ln = reinterpret_cast<uintptr_t>(row) & ~static_cast<uintptr_t>(127); ln < e;
+             ln += 128)
+          asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ln));
+      }
+    }
+  }
 
   // ---- the sweep, back to front
   for (int n = 0; n < nchunks; ++n) {
@@ -336,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int b = bq[q] >= 0 ? bq[q] : bq[0];
-          G[q] = pixel_G(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
+          G[q] = pixel_G_grad(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -348,7 +432,8 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     // 2. the recurrence, two threads per pixel
     float x[8];
     const bool more = n + 1 < nchunks;
-    if (more) load_rad(n + 1, x);  // in flight during the recurrence
+    bool x_ok = false;
+    if (more) x_ok = load_rad(n + 1, x);  // in flight during the recurrence
     if (!tc::mbar_wait(barG, n & 1, kWaitLimit)) fail();
     tc::fence_after_sync();
     float gam[32];
@@ -356,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     if (n > 0 && !tc::mbar_wait(barD, (n - 1) & 1, kWaitLimit)) fail();  // a is free again
     tc::fence_after_sync();
     const unsigned m = sMask[wp];
-    auto step = [&](int b, float& dt) {
+    auto step = [&](int b, float& dt) -> float {
       float Tw = 0.0f;
       dt = 0.0f;
       if (m & (1u << b)) {
@@ -370,21 +455,29 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
           Q = fmaf(w, gam[b], one_m_w * Q);
         }
       }
-      __nv_bfloat16 hi, lo;
-      tc::split_bf16(Tw, hi, lo);
-      const uint32_t off = (b >> 3) * kSboA + (p >> 3) * kLboA + (b & 7) * 16 + (p & 7) * 2;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = hi;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = lo;
+      return Tw;
+    };
+    // T w of entries 8e .. 8e + 7 of this pixel: one 16-byte core row per term
+    auto put_a = [&](int e, const float (&tw)[8]) {
+      uint4 hi, lo;
+      tc::split8(tw, hi, lo);
+      const uint32_t off = (p >> 3) * kKsA + e * kMnA + (p & 7) * 16;
+      *reinterpret_cast<uint4*>(sm + kOffA1 + off) = hi;
+      *reinterpret_cast<uint4*>(sm + kOffA2 + off) = lo;
     };
     if (half == 0) {
       // entries 31..16 from the back end; their dL/dtau terms are written
       // after the front thread has read these entries' weights
-      float dts[16];
+      float dts[16], tw0[8], tw1[8];
 #pragma unroll
-      for (int b = kCH - 1; b >= 16; --b) step(b, dts[b - 16]);
+      for (int b = kCH - 1; b >= 24; --b) tw1[b - 24] = step(b, dts[b - 16]);
+#pragma unroll
+      for (int b = 23; b >= 16; --b) tw0[b - 16] = step(b, dts[b - 16]);
       tc::named_barrier(1 + wp, 64);
 #pragma unroll
       for (int b = 16; b < kCH; ++b) sW[b * kP + p] = dts[b - 16];
+      put_a(2, tw0);
+      put_a(3, tw1);
     } else {
       // T and Q in the middle of the chunk: the transmittance product and
       // the Q recurrence over entries 31..16
@@ -403,12 +496,21 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
       }
       T = __fdividef(T, P);
       tc::named_barrier(1 + wp, 64);
+      float tw0[8], tw1[8];
 #pragma unroll
-      for (int b = 15; b >= 0; --b) {
+      for (int b = 15; b >= 8; --b) {
         float dt;
-        step(b, dt);
+        tw1[b - 8] = step(b, dt);
         sW[b * kP + p] = dt;
       }
+#pragma unroll
+      for (int b = 7; b >= 0; --b) {
+        float dt;
+        tw0[b] = step(b, dt);
+        sW[b * kP + p] = dt;
+      }
+      put_a(0, tw0);
+      put_a(1, tw1);
       sTQ[p] = make_float2(T, Q);  // the state at the front end of chunk n
     }
     if (n > 0) drain_dlds(tmem, n - 1);
@@ -423,15 +525,21 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
       sMisc[3] = n + 1;
     }
     {
+      // entry b = t / 16: 16 lanes sum its 256 pixels, 16-byte loads (a
+      // quarter warp on 128 contiguous bytes), then a shuffle tree
       const int b = t >> 4, q = t & 15;
+      const float4* w4 = reinterpret_cast<const float4*>(sW + b * kP);
       float y = 0.0f;
 #pragma unroll
-      for (int r = 0; r < kP / 16; ++r) y += sW[b * kP + q + 16 * r];
+      for (int r = 0; r < kP / 64; ++r) {
+        const float4 u = w4[q + 16 * r];
+        y += (u.x + u.y) + (u.z + u.w);
+      }
 #pragma unroll
       for (int o = 8; o >= 1; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
       if (q == 0 && b < nb && y != 0.0f) atomicAdd(&A.d_tau[sIdx[(n & 3) * kCH + b]], y);
     }
-    if (more) store_rad(x);  // gamma(n) is complete: s is free
+    if (more) store_rad(x, x_ok);  // gamma(n) is complete: s is free
     if (half == 0) {
       const float2 tq = sTQ[p];
       T = tq.x;
@@ -453,7 +561,9 @@ __global__ void __launch_bounds__(kThreads, 1) render_bwd_tc_kernel(const Backwa
     }
   }
   if (aborted && t == 256) {
-    // let MMAs still in flight finish (bounded) before their memory goes
+    // let copies and MMAs still in flight finish (bounded) before their
+    // memory goes
+    if (g_tma) tc::mbar_wait(barT, 0, kWaitLimit);
     const uint32_t ng = sMisc[2], nd = sMisc[3];
     if (ng > 0) tc::mbar_wait(barG, (ng - 1) & 1, kWaitLimit);
     if (nd > 0) tc::mbar_wait(barD, (nd - 1) & 1, kWaitLimit);
@@ -476,8 +586,28 @@ void launch_render_bwd_tc(const BackwardArgs& A, cudaStream_t s) {
                          static_cast<int>(kSmem));
     configured = true;
   }
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  // the cotangent tile by TMA when a box covers it: 2C divides the block's
+  // columns and a tile row of pixels x 2C fits one box extent
+  CUtensorMap gmap{};
+  const int twoC = 2 * a.C, rowf = a.g.TW * twoC;
+  bool tma = A.g_spec && kNB % twoC == 0 && rowf <= 256 && rowf % 4 == 0;
+  if (tma) {
+    const uint64_t W2 = static_cast<uint64_t>(a.g.W) * twoC;
+    const uint64_t dims[4] = {W2, static_cast<uint64_t>(a.g.H), static_cast<uint64_t>(a.N),
+                              static_cast<uint64_t>(a.M)};
+    const uint64_t strides[3] = {W2 * 4, W2 * a.g.H * 4, W2 * a.g.H * a.N * 4};
+    const uint32_t box[4] = {static_cast<uint32_t>(rowf), static_cast<uint32_t>(a.g.TH),
+                             static_cast<uint32_t>(kNB / twoC), 1};
+    tma = tc::encode_f32_tiled(&gmap, A.g_spec, 4, dims, strides, box);
+  }
   dim3 grid(a.g.T, (a.ncols + kNB - 1) / kNB, a.M);
-  render_bwd_tc_kernel<<<grid, kThreads, kSmem, s>>>(A);
+  render_bwd_tc_kernel<<<grid, kThreads, kSmem, s>>>(A, nsm, tma ? 1 : 0, gmap);
   note_launches(1);
 }
 

@@ -78,6 +78,31 @@ __device__ __forceinline__ float pixel_G(const GridConst& g, const float4 r0, co
   return (inside && q <= g.q_max) ? G : -1.0f;
 }
 
+// The backward's weight: the same decision as pixel_G (footprint, q in the
+// specification's operation order, q <= q_max, so the same entries count as
+// composited) with the value exp(-q/2) from the hardware exponential
+// (__expf: a few ulp, well inside the gradients' tolerance).  The forward
+// keeps pixel_G, whose exact value decides the transmittance cut-off.
+__device__ __forceinline__ float pixel_G_grad(const GridConst& g, const float4 r0,
+                                              const float4 r1, int i, float fi, int jj,
+                                              float fj) {
+  const int rows = __float_as_int(r1.z), cols = __float_as_int(r1.w);
+  int dj = jj - (cols & 0xffff);
+  dj += dj < 0 ? g.W : 0;
+  const bool inside = i >= (rows & 0xffff) && i <= (rows >> 16) && dj <= (cols >> 16);
+  const float dt = __fsub_rn(fi, r0.x);
+  float dp = __fsub_rn(fj, r0.y);
+  dp = dp >= g.halfW ? __fsub_rn(dp, g.Wf) : (dp < -g.halfW ? __fadd_rn(dp, g.Wf) : dp);
+  const float t1 = __fmul_rn(r0.w, dp);
+  const float t2 = __fmaf_rn(r0.z, dt, t1);
+  const float t3 = __fmul_rn(r1.x, dp);
+  const float t4 = __fmul_rn(t3, dp);
+  const float q = __fmaf_rn(dt, t2, t4);
+  const float x = __fmul_rn(-0.5f, q);
+  const float G = x > -87.0f ? __expf(x) : 0.0f;
+  return (inside && q <= g.q_max) ? G : -1.0f;
+}
+
 // The pixels of warp `w` of a tile (threads 32w .. 32w+31, row-major over the
 // TH x TW tile) lie in grid rows [r0, r1] and columns [c0, c1].
 struct Strip {

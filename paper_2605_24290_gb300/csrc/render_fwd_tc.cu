@@ -102,8 +102,10 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
     cp_async16(&rb[2 * lane + 0], &rec[2 * k + 0], ok);
     cp_async16(&rb[2 * lane + 1], &rec[2 * k + 1], ok);
   };
-  // radiance of chunk n: thread t takes entry t / 8 and 16 columns
-  auto load_rad = [&](int n, float (&x)[16]) {
+  // radiance of chunk n: thread t takes entry t / 8 and 16 columns; past the
+  // chunk the loads read entry 0's row (always in the array) and store_rad
+  // writes zeros, so nothing waits for the loads before the weights have run
+  auto load_rad = [&](int n, float (&x)[16]) -> bool {
     const int b = t >> 3, cg = t & 7;
     const bool ok = b < chunk_len(n);
     const uint32_t k = ok ? sIdx[(n % 3) * kCH + b] : 0u;
@@ -111,18 +113,19 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
         reinterpret_cast<const float4*>(radv + static_cast<size_t>(k) * a.stride + col0 + cg * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 r = ok ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 r = src[q];
       x[4 * q + 0] = r.x;
       x[4 * q + 1] = r.y;
       x[4 * q + 2] = r.z;
       x[4 * q + 3] = r.w;
     }
+    return ok;
+  };
+  auto store_rad = [&](int buf, float (&x)[16], bool ok) {
+    const int b = t >> 3, cg = t & 7;
 #pragma unroll
     for (int e = 0; e < 16; ++e)
-      if (col0 + cg * 16 + e >= a.ncols) x[e] = 0.0f;
-  };
-  auto store_rad = [&](int buf, const float (&x)[16]) {
-    const int b = t >> 3, cg = t & 7;
+      if (!ok || col0 + cg * 16 + e >= a.ncols) x[e] = 0.0f;
     float x0[8], x1[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -178,8 +181,8 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
   }
   if (nchunks > 0) {
     float x[16];
-    load_rad(0, x);
-    store_rad(0, x);
+    const bool ok = load_rad(0, x);
+    store_rad(0, x, ok);
   }
 
   float T = 1.0f;
@@ -198,7 +201,8 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
     }
     float x[16];
     const bool more = n + 1 < nchunks;
-    if (more) load_rad(n + 1, x);
+    bool x_ok = false;
+    if (more) x_ok = load_rad(n + 1, x);
     // the MMA of chunk n - 1 has read A and radiance buffer (n + 1) & 1
     if (n > 0 && !tc::mbar_wait(bar, (n - 1) & 1, kWaitLimit)) {
       atomicOr(&sMisc[1], 1u);
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
         put_a(bq[q], Tw);
       }
     }
-    if (more) store_rad((n + 1) & 1, x);
+    if (more) store_rad((n + 1) & 1, x, x_ok);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     const int n_alive = __syncthreads_count(alive);

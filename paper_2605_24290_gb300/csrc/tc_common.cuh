@@ -23,11 +23,21 @@
 // drops lo_x*lo_y (below 2^-16 |x y|): about 1.2e-5 relative per term in
 // all, float32 accumulation.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstdint>
 
 namespace rxgs {
 namespace tc {
+
+// Host: a TMA tensor map over a float32 array of `rank` dimensions (dims[0]
+// innermost; strides[i] = bytes between consecutive indices of dimension
+// i + 1) copied in boxes of box[0] x ... elements, out-of-range elements
+// read as zero.  False when the driver's encoder is unavailable or refuses
+// the layout (16-byte aligned base and strides, box extents 1..256, inner
+// box extent a multiple of 16 bytes); the caller then takes another path.
+bool encode_f32_tiled(CUtensorMap* map, const float* base, int rank, const uint64_t* dims,
+                      const uint64_t* strides, const uint32_t* box);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -281,6 +291,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0,
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
       "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
       "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            int c3, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(mbar))
       : "memory");
 }
 // shared -> global (plain store, or element-wise float add) in this
