@@ -24,7 +24,7 @@
 //   1. gamma(n) is issued (its radiance s(n) was staged at the end of the
 //      previous chunk); all threads evaluate the weights G[b][p] of the
 //      entries meeting each 32-pixel strip, the two warps of a strip taking
-//      alternate entries, four at a time;
+//      its even and its odd entries, eight at a time;
 //   2. the recurrence runs on two threads per pixel: warps 0-7 take entries
 //      31..16, warps 8-15 entries 15..0 after deriving the transmittance and
 //      Q in the middle of the chunk from entries 31..16 (a product of
@@ -81,6 +81,7 @@ static_assert(kSmem <= 232448, "shared memory");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(kOffW % 16 == 0 && kOffA1 % 16 == 0 && kOffA2 % 16 == 0, "16-byte operand rows");
 
+constexpr int kWq = 8;  // weights evaluated at once per thread (independent chains)
 constexpr uint32_t kTmemCols = 128;  // gamma: columns 0-63 (two M tiles), dL/ds: 64-95
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdescGamma = tc::idesc_bf16(128, 32, 0, 0);
@@ -126,11 +127,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int i = tr * g.TH + p / g.TW, jj = tcol * g.TW + p % g.TW;
   const bool valid = i < g.H && jj < g.W;
   const float fi = static_cast<float>(i), fj = static_cast<float>(jj);
-  float T = 1.0f, Q = 0.0f;  // at the back end of the next chunk
+  // 1 / T and Q at the back end of the next chunk: the recovery
+  // T_m = T_{m+1} / (1 - w_m) runs on the reciprocal, iT_m = iT_{m+1} (1 - w_m),
+  // a multiply on the serial chain (the reciprocal T_m is off it)
+  float iT = 1.0f, Q = 0.0f;
   uint32_t stop = rg.x;
   if (valid) {
     const size_t o = static_cast<size_t>(v) * HW + static_cast<size_t>(i) * g.W + jj;
-    T = A.tfin[o];
+    iT = A.tfin[o];  // T here; inverted before the sweep
     stop = A.stops[o];
   }
   const Strip strip = pixel_strip(g, tr, tcol, 32 * wp, 32);
@@ -377,6 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
 
+  iT = 1.0f / iT;
   // ---- the sweep, back to front
   for (int n = 0; n < nchunks; ++n) {
     tc::fence_smem_to_async();  // s(n) (and g for n = 0) for the tensor core
@@ -399,31 +404,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const float4* sR = sRec0 + (n & 1) * 2 * kCH;
     // 1. weights G[b][p] (0: not composited) of the entries meeting this
-    //    warp's strip; the two warps of a strip take alternate entries
+    //    warp's strip; the two warps of a strip take its even and odd entries
     {
       const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
       if (!__any_sync(0xffffffffu, start < stop)) m = 0;  // no pixel reaches this chunk
       if (half == 0 && lane == 0) sMask[wp] = m;
-      unsigned mine = 0;
-      int r = 0;
-      for (unsigned mm = m; mm; mm &= mm - 1)
-        if ((r++ & 1) == half) mine |= 1u << (__ffs(mm) - 1);
+      unsigned mine = m & (half ? 0xaaaaaaaau : 0x55555555u);  // odd / even entries
       while (mine) {
-        int bq[4];
+        int bq[kWq];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kWq; ++q) {
           bq[q] = mine ? __ffs(mine) - 1 : -1;
           mine &= mine - 1;
         }
-        float G[4];
+        float G[kWq];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kWq; ++q) {
           const int b = bq[q] >= 0 ? bq[q] : bq[0];
           G[q] = pixel_G_grad(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < kWq; ++q)
           if (bq[q] >= 0)
             sW[bq[q] * kP + p] = (valid && start + bq[q] < stop && G[q] > 0.0f) ? G[q] : 0.0f;
       }
@@ -449,7 +451,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (G != 0.0f) {
           const float w = __fmul_rn(sR[2 * b + 1].y, G);
           const float one_m_w = 1.0f - w;
-          T = __fdividef(T, one_m_w);  // transmittance in front of entry b
+          iT *= one_m_w;
+          const float T = __fdividef(1.0f, iT);  // transmittance in front of entry b
           Tw = T * w;
           dt = T * (gam[b] - Q) * G;
           Q = fmaf(w, gam[b], one_m_w * Q);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      T = __fdividef(T, P);
+      iT *= P;
       tc::named_barrier(1 + wp, 64);
       float tw0[8], tw1[8];
 #pragma unroll
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       put_a(0, tw0);
       put_a(1, tw1);
-      sTQ[p] = make_float2(T, Q);  // the state at the front end of chunk n
+      sTQ[p] = make_float2(iT, Q);  // the state at the front end of chunk n
     }
     if (n > 0) drain_dlds(tmem, n - 1);
     // 3. issue dL/ds(n); dL/dtau of chunk n; stage s(n + 1)
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (more) store_rad(x, x_ok);  // gamma(n) is complete: s is free
     if (half == 0) {
       const float2 tq = sTQ[p];
-      T = tq.x;
+      iT = tq.x;
       Q = tq.y;
     }
   }

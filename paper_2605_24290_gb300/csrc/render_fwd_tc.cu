@@ -62,6 +62,7 @@ static_assert(8 * kNB * 4 <= 2 * kABytes, "partial sums fit in A");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(2 * kSmem <= 232448, "two CTAs per SM");
 
+constexpr int kWq = 4;  // weights evaluated at once per thread (independent chains)
 constexpr uint32_t kTmemCols = 256;  // two M tiles x 128 float32 columns
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 128, 1, 1);
@@ -223,20 +224,20 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
     };
     for (unsigned z = ~mask; z; z &= z - 1) put_a(__ffs(z) - 1, 0.0f);
     for (unsigned m = mask; m;) {
-      int bq[4];
+      int bq[kWq];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kWq; ++q) {
         bq[q] = m ? __ffs(m) - 1 : -1;
         m &= m - 1;
       }
-      float G[4];
+      float G[kWq];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kWq; ++q) {
         const int b = bq[q] >= 0 ? bq[q] : bq[0];
         G[q] = pixel_G(g, sR[2 * b], sR[2 * b + 1], i, fi, jj, fj);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < kWq; ++q) {
         if (bq[q] < 0) break;
         float Tw = 0.0f;
         if (alive && G[q] >= 0.0f) {
