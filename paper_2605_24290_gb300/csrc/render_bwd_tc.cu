@@ -322,10 +322,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int oc = (t >> 8) + 2 * r;
+        // column c = 2C z + ec of the block's receiver z (one division per octet)
+        int z = (oc * 8) / twoC, ec = oc * 8 - z * twoC;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int c = oc * 8 + 2 * e, z = c / twoC, ec = c - z * twoC;
+          const int c = oc * 8 + 2 * e;
           float2 val = *reinterpret_cast<const float2*>(&stg[(z * g.TH + y) * rowf + px * twoC + ec]);
+          ec += 2;
+          if (ec == twoC) {
+            ec = 0;
+            ++z;
+          }
           if (A.g_uniform && valid && col0 + c < a.ncols) {
             const float2 u = *reinterpret_cast<const float2*>(
                 &A.g_uniform[static_cast<size_t>(v) * a.ncols + col0 + c]);

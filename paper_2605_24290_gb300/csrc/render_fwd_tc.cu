@@ -57,8 +57,12 @@ constexpr uint32_t kSmemUsed = kOffMisc + 12;
 // (2 x 256 TMEM columns, all of it) share an SM and an allocation never waits
 constexpr uint32_t kSmem = 80 * 1024;
 static_assert(kSmemUsed <= kSmem, "shared memory");
-// the epilogue's column sums reuse the A buffer: float [8 warps][128]
-static_assert(8 * kNB * 4 <= 2 * kABytes, "partial sums fit in A");
+// the epilogue reuses the operand buffers (the MMAs are done): two staging
+// buffers of 32 spectra columns for the TMA stores, then the column sums
+// float [8 warps][128]
+constexpr uint32_t kStage = kP * 32 * 4;
+constexpr uint32_t kOffPart = 2 * kStage;
+static_assert(kOffPart + 8 * kNB * 4 <= kOffRec, "staging and partial sums fit in the operands");
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(2 * kSmem <= 232448, "two CTAs per SM");
 
@@ -67,7 +71,8 @@ constexpr uint32_t kTmemCols = 256;  // two M tiles x 128 float32 columns
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 128, 1, 1);
 
-__global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const RenderArgs a) {
+__global__ void __launch_bounds__(kThreads, 2)
+    render_fwd_tc_kernel(const RenderArgs a, int s_tma, const __grid_constant__ CUtensorMap smap) {
   extern __shared__ __align__(128) unsigned char sm[];
   float4* sRec0 = reinterpret_cast<float4*>(sm + kOffRec);
   uint32_t* sIdx = reinterpret_cast<uint32_t*>(sm + kOffIdx);
@@ -281,7 +286,8 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
   const size_t HW = static_cast<size_t>(g.H) * g.W;
   const int twoC = 2 * a.C;
   const size_t po = static_cast<size_t>(i) * g.W + jj;
-  float* sPart = reinterpret_cast<float*>(sm + kOffA1);  // [8][128]; the MMAs are done
+  float* sPart = reinterpret_cast<float*>(sm + kOffPart);  // [8][128]; the MMAs are done
+  const int y = t / g.TW, px = t % g.TW, rowf = g.TW * twoC;
 #pragma unroll 1
   for (int q = 0; q < kNB / 32; ++q) {
     float d[32];
@@ -292,14 +298,48 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
 #pragma unroll
       for (int e = 0; e < 32; ++e) d[e] = 0.0f;
     }
-    if (a.spectra && valid) {
+    if (s_tma) {
+      // 32 columns as one box [32 / 2C receivers][TH rows][TW pixels x 2C]
+      // staged in shared memory and stored by TMA (out-of-range pixels and
+      // receivers are not written); two staging buffers
+      float* stg = reinterpret_cast<float*>(sm + (q & 1) * kStage);
+      if (q >= 2) {
+        if (t == 0) tc::bulk_wait_read<1>();  // the store of q - 2 has read its buffer
+        __syncthreads();
+      }
+      int z = 0, ec = 0;
 #pragma unroll
       for (int e = 0; e < 32; e += 2) {
-        const int col = col0 + 32 * q + e;
-        if (col < a.ncols) {
-          const int j = col / twoC, ec = col - j * twoC;
-          const size_t off = ((static_cast<size_t>(v) * a.N + j) * HW + po) * twoC + ec;
-          *reinterpret_cast<float2*>(&a.spectra[off]) = make_float2(d[e], d[e + 1]);
+        *reinterpret_cast<float2*>(&stg[(z * g.TH + y) * rowf + px * twoC + ec]) =
+            make_float2(d[e], d[e + 1]);
+        ec += 2;
+        if (ec == twoC) {
+          ec = 0;
+          ++z;
+        }
+      }
+      tc::fence_smem_to_async();
+      __syncthreads();
+      if (t == 0) {
+        tc::tma_store_4d(&smap, tcol * g.TW * twoC, tr * g.TH, (col0 + 32 * q) / twoC, v, stg);
+        tc::bulk_commit();
+      }
+    } else if (a.spectra && valid) {
+      // column c = 2C j + ec of receiver j: the (re, im) pairs of this
+      // pixel advance by 2 within a receiver and by H W 2C floats to the
+      // next one (one division per 32 columns)
+      const int c0 = col0 + 32 * q;
+      int ec = c0 % twoC;
+      float* dst = a.spectra + ((static_cast<size_t>(v) * a.N + c0 / twoC) * HW + po) * twoC + ec;
+      const size_t jstep = HW * twoC - twoC;
+#pragma unroll
+      for (int e = 0; e < 32; e += 2) {
+        if (c0 + e < a.ncols) *reinterpret_cast<float2*>(dst) = make_float2(d[e], d[e + 1]);
+        ec += 2;
+        dst += 2;
+        if (ec == twoC) {
+          ec = 0;
+          dst += jstep;
         }
       }
     }
@@ -344,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 2) render_fwd_tc_kernel(const Render
     for (int w = 0; w < 8; ++w) y += sPart[w * kNB + t];
     a.partial[(static_cast<size_t>(v) * g.T + tile) * a.ncols + col0 + t] = y;
   }
+  if (s_tma && t == 0) tc::bulk_wait_read<0>();  // staging read before the CTA leaves
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kTmemCols);
@@ -359,8 +400,22 @@ void launch_render_fwd_tc(const RenderArgs& a, cudaStream_t s) {
                          static_cast<int>(kSmem));
     configured = true;
   }
+  // spectra by TMA stores when a box of 32 columns covers whole receivers
+  // and a tile row of pixels x 2C fits one box extent
+  CUtensorMap smap{};
+  const int twoC = 2 * a.C, rowf = a.g.TW * twoC;
+  bool tma = a.spectra && 32 % twoC == 0 && rowf <= 256 && rowf % 4 == 0;
+  if (tma) {
+    const uint64_t W2 = static_cast<uint64_t>(a.g.W) * twoC;
+    const uint64_t dims[4] = {W2, static_cast<uint64_t>(a.g.H), static_cast<uint64_t>(a.N),
+                              static_cast<uint64_t>(a.M)};
+    const uint64_t strides[3] = {W2 * 4, W2 * a.g.H * 4, W2 * a.g.H * a.N * 4};
+    const uint32_t box[4] = {static_cast<uint32_t>(rowf), static_cast<uint32_t>(a.g.TH),
+                             static_cast<uint32_t>(32 / twoC), 1};
+    tma = tc::encode_f32_tiled(&smap, a.spectra, 4, dims, strides, box);
+  }
   dim3 grid(a.g.T, (a.ncols + kNB - 1) / kNB, a.M);
-  render_fwd_tc_kernel<<<grid, kThreads, kSmem, s>>>(a);
+  render_fwd_tc_kernel<<<grid, kThreads, kSmem, s>>>(a, tma ? 1 : 0, smap);
   note_launches(1);
 }
 
