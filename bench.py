@@ -56,12 +56,12 @@ def peaks():
 # measured by one ncu capture of that kernel on this workload; valid only
 # while the kernel sources hash to the value recorded at capture time.
 NCU_TRAFFIC = {
-    "render_fwd": {"bytes": 27_203_328 + 475_968_256, "tile": [16, 16], "cols": 128,
-                   "files": ['render_fwd.cu', 'render_tile.cuh', 'render_common.cuh', 'rxgs_math.cuh'],
-                   "sha1": "14661ac63bf56f4d"},
-    "render_bwd": {"bytes": 567_486_720 + 8_035_072, "tile": [16, 16], "cols": 128,
-                   "files": ['render_bwd.cu', 'render_common.cuh', 'rxgs_math.cuh'],
-                   "sha1": "50d0a45e3f3c9562"},
+    "render_fwd": {"bytes": 19_816_448 + 483_368_960, "tile": [8, 32], "cols": 128,
+                   "files": ['render_fwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
+                   "sha1": "81cf6bb6ea56c668"},
+    "render_bwd": {"bytes": 560_865_024 + 8_279_040, "tile": [8, 32], "cols": 128,
+                   "files": ['render_bwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
+                   "sha1": "445f21d5d4d93274"},
 }
 
 

@@ -64,7 +64,7 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
 // buffers.  tmp must hold radix_tmp_words(n) uint32.
 size_t radix_tmp_words(size_t n);
 // n_dev (optional): the actual item count, <= n (launch sizes follow n).
-// err (optional): receives kErrTimeout if a pass's look-back gave up.
+// err (optional): unused (no kernel of the sort waits on another).
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
