@@ -443,7 +443,7 @@ def gpu_bench(args):
             torch.cuda.synchronize()
 
         e2e_run(2)
-        n_e = max(5, args.steps)
+        n_e = max(20, args.steps)
         barrier()
         t0 = time.perf_counter()
         e2e_run(n_e)

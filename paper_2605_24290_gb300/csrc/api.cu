@@ -188,6 +188,8 @@ rxgs_status rxgs_create(const rxgs_options* opts, int device, rxgs_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_pinned),
+                                                     ctx->h_pinned, 0);
   if (e == cudaSuccess) {
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -407,7 +409,20 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     delete v;
   };
   cudaError_t e = dalloc(&v->tx, 3ull * M, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v->tx, tx, sizeof(float) * 3 * M, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) {
+    // transmitters already on the device are copied by a kernel, so the
+    // step does not wait behind copies the caller queued on the copy engines
+    cudaPointerAttributes pa{};
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, tx);
+    if (pe != cudaSuccess) cudaGetLastError();  // not a device pointer: clear and copy
+    const bool on_device =
+        pe == cudaSuccess && (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    if (on_device)
+      launch_copy_words(reinterpret_cast<const uint32_t*>(tx), reinterpret_cast<uint32_t*>(v->tx),
+                        3ull * M, st);
+    else
+      e = cudaMemcpyAsync(v->tx, tx, sizeof(float) * 3 * M, cudaMemcpyDefault, st);
+  }
   if (e == cudaSuccess) e = dalloc(&v->rec, 2 * MK, st);
   if (e == cudaSuccess) e = dalloc(&v->depth, MK, st);
   if (e == cudaSuccess) e = dalloc(&v->counts, MK, st);
@@ -426,7 +441,10 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     Stage sg(ctx, "scan", st);
     launch_exclusive_scan(v->counts, v->offsets, MK, scan_tmp, st);
   }
-  e = cudaMemcpyAsync(ctx->h_pinned, v->offsets + MK, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  // the instance count, written into the pinned readback slot by a kernel
+  // (a copy-engine transfer would queue behind the caller's large copies)
+  launch_copy_words(v->offsets + MK, ctx->d_pinned, 1, st);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(scan_tmp, st);
   if (e != cudaSuccess) {

@@ -273,6 +273,24 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
   note_launches(1);
 }
 
+// ------------------------------------------------------------ small copies
+// n 32-bit words from src to dst by the SMs (device memory, or pinned host
+// memory mapped into the device's address space): small transfers that
+// must not wait behind large copies queued on the copy engines.
+__global__ void copy_words_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                                  size_t n) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    dst[i] = src[i];
+}
+
+void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_t s) {
+  if (n == 0) return;
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 64);
+  copy_words_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(src, dst, n);
+  note_launches(1);
+}
+
 // -------------------------------------------------------------- tile ranges
 __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, size_t n, int tile_bits,
                                    int T, uint2* __restrict__ ranges,

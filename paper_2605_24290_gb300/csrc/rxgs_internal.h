@@ -69,6 +69,11 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
 
+// dst[i] = src[i] for n 32-bit words, copied by a kernel (device memory or
+// mapped pinned host memory on either side): for small transfers that must
+// not queue behind large copies on the copy engines.
+void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_t s);
+
 // ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
 void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
                         int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
