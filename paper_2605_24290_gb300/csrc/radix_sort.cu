@@ -5,15 +5,16 @@
 //
 // Digits of up to 9 bits (ceil(bits / 9) passes; 44-bit keys take 5).  One
 // pass = three kernels over tiles of 2,048 items:
-//   sort_count    each tile's digit counts (shared-memory histogram) and the
-//                 digit totals;
+//   sort_count    each tile's digit counts (shared-memory histogram);
 //   sort_offsets  one block per digit: where each tile's run of that digit
-//                 starts in the output (exclusive scan over the tiles plus
-//                 the digit's base);
-//   sort_scatter  ranks the tile's items stably (warp match-any, per-warp
-//                 digit counters in shared memory), reorders the tile by
-//                 digit in shared memory and writes each digit's run to its
-//                 place, consecutive threads on consecutive addresses.
+//                 starts within the digit (exclusive scan over the tiles),
+//                 and the digit's total;
+//   sort_scatter  adds the digit bases (an exclusive scan of the totals in
+//                 each block; no global atomics anywhere in the pass), ranks
+//                 the tile's items stably (warp match-any, per-warp digit
+//                 counters in shared memory), reorders the tile by digit in
+//                 shared memory and writes each digit's run to its place,
+//                 consecutive threads on consecutive addresses.
 // Every tile's loads are issued before any of its ranks is computed.
 #include <algorithm>
 #include <utility>
@@ -44,14 +45,12 @@ Plan plan_of(int bits) {
 
 size_t tiles_of(size_t n) { return (n + kTile - 1) / kTile; }
 
-// hist[d * nt + tile] = count of digit d in the tile; totals[d] += it
+// hist[d * nt + tile] = count of digit d in the tile
 __global__ void __launch_bounds__(kThreads) sort_count_kernel(const uint64_t* __restrict__ keys,
                                                               size_t n,
                                                               const uint32_t* __restrict__ n_dev,
                                                               int shift, int width,
-                                                              uint32_t* __restrict__ hist,
-                                                              uint32_t* __restrict__ totals,
-                                                              int nt) {
+                                                              uint32_t* __restrict__ hist, int nt) {
   if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t h[kBins];
   for (int d = threadIdx.x; d < kBins; d += kThreads) h[d] = 0;
@@ -70,31 +69,19 @@ __global__ void __launch_bounds__(kThreads) sort_count_kernel(const uint64_t* __
     if (i < n) atomicAdd(&h[(k[r] >> shift) & mask], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kBins; d += kThreads) {
-    const uint32_t c = h[d];
-    hist[static_cast<size_t>(d) * nt + blockIdx.x] = c;
-    if (c) atomicAdd(&totals[d], c);
-  }
+  for (int d = threadIdx.x; d < kBins; d += kThreads)
+    hist[static_cast<size_t>(d) * nt + blockIdx.x] = h[d];
 }
 
-// Block d: hist[d][b] <- base(d) + sum_{b' < b} hist[d][b'], base(d) =
-// sum_{d' < d} totals[d'].
+// Block d: hist[d][b] <- sum_{b' < b} hist[d][b'] (the run's start within
+// the digit) and totals[d] = the digit's count; the digit bases (exclusive
+// sums of the totals) are added by the scatter.
 __global__ void __launch_bounds__(kThreads) sort_offsets_kernel(uint32_t* __restrict__ hist,
-                                                                const uint32_t* __restrict__ totals,
+                                                                uint32_t* __restrict__ totals,
                                                                 int nt) {
   __shared__ uint32_t wsum[kWarps];
   const int d = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // digit base: the totals of the digits below d
-  uint32_t b = 0;
-  for (int e = threadIdx.x; e < d; e += kThreads) b += totals[e];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-  if (lane == 0) wsum[wid] = b;
-  __syncthreads();
   uint32_t carry = 0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) carry += wsum[w];
-  __syncthreads();
   uint32_t* row = hist + static_cast<size_t>(d) * nt;
   for (int base = 0; base < nt; base += kThreads) {
     const int i = base + threadIdx.x;
@@ -118,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) sort_offsets_kernel(uint32_t* __rest
     carry += total;
     __syncthreads();
   }
+  if (threadIdx.x == 0) totals[d] = carry;
 }
 
 struct ScatterSmem {
@@ -132,7 +120,7 @@ struct ScatterSmem {
 __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, const uint32_t* __restrict__ n_dev, int shift, int width,
-    const uint32_t* __restrict__ offsets, int nt) {
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals, int nt) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smraw);
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -151,8 +139,32 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     v[r] = i < n ? vin[i] : 0;
   }
   for (int e = t; e < kWarps * kBins; e += kThreads) (&S.wcnt[0][0])[e] = 0;
-  for (int d = t; d < kBins; d += kThreads)
-    S.gpos[d] = offsets[static_cast<size_t>(d) * nt + blockIdx.x];
+  {
+    // where each digit's run of this tile starts in the output: the digit's
+    // base (exclusive sum of the digit totals) plus the tile's offset in it
+    uint32_t tv[kBinsPerThread], ts = 0;
+#pragma unroll
+    for (int q = 0; q < kBinsPerThread; ++q) {
+      tv[q] = totals[t * kBinsPerThread + q];
+      ts += tv[q];
+    }
+    uint32_t x = ts;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) S.part[wid] = x;
+    __syncthreads();
+    uint32_t b = x - ts;
+    for (int w = 0; w < wid; ++w) b += S.part[w];
+#pragma unroll
+    for (int q = 0; q < kBinsPerThread; ++q) {
+      const int d = t * kBinsPerThread + q;
+      S.gpos[d] = offsets[static_cast<size_t>(d) * nt + blockIdx.x] + b;
+      b += tv[q];
+    }
+  }
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const size_t i = base + static_cast<size_t>(wid) * (32 * kItems) + r * 32 + lane;
@@ -262,17 +274,15 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32
                          static_cast<int>(sizeof(ScatterSmem)));
     configured = true;
   }
-  cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kMaxPasses * kBins, s);
   uint64_t *kin = keys, *kout = keys_alt;
   uint32_t *vin = vals, *vout = vals_alt;
   bool alt = false;
   for (int p = 0; p < P.passes; ++p) {
     const int shift = p * P.width;
-    sort_count_kernel<<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, hist,
-                                              totals + p * kBins, nt);
+    sort_count_kernel<<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, hist, nt);
     sort_offsets_kernel<<<kBins, kThreads, 0, s>>>(hist, totals + p * kBins, nt);
-    sort_scatter_kernel<<<nt, kThreads, sizeof(ScatterSmem), s>>>(kin, vin, kout, vout, n, n_dev,
-                                                                 shift, P.width, hist, nt);
+    sort_scatter_kernel<<<nt, kThreads, sizeof(ScatterSmem), s>>>(
+        kin, vin, kout, vout, n, n_dev, shift, P.width, hist, totals + p * kBins, nt);
     note_launches(3);
     std::swap(kin, kout);
     std::swap(vin, vout);
