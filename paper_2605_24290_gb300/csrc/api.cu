@@ -573,43 +573,37 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
     float4* ab = nullptr;
     if (dalloc(&ab, static_cast<size_t>(N) * f.L, st) != cudaSuccess)
       return fail(ctx, RXGS_E_OOM, "FiLM outputs");
-    // the conditioned coefficients [N][K][2][L] (Eq. film_apply; with the
-    // local branch, Eq. combined_local), then the same contraction as for
-    // given coefficients
-    float* coeffs = nullptr;
+    // the conditioned coefficients (Eq. film_apply; with the local branch,
+    // Eq. combined_local) are formed inside the contraction from the base
+    // coefficients, the modulations ab and the local factors loc
     float4* loc = nullptr;
     float2* feat = nullptr;
-    cudaError_t e = dalloc(&coeffs, static_cast<size_t>(N) * s->K * 2 * f.L, st);
-    if (e == cudaSuccess && d->film_local) e = dalloc(&loc, static_cast<size_t>(N) * s->K, st);
+    cudaError_t e = cudaSuccess;
+    if (d->film_local) e = dalloc(&loc, static_cast<size_t>(N) * s->K, st);
     if (e == cudaSuccess && d->film_local && s->occ)
       e = dalloc(&feat, static_cast<size_t>(N) * s->K, st);
+    unsigned char* image = nullptr;
+    if (e == cudaSuccess) e = dalloc(&image, fle_basis_image_bytes(s->K, v->M), st);
     if (e != cudaSuccess) {
-      dfree(ab, st); dfree(coeffs, st); dfree(loc, st); dfree(feat, st);
-      return fail(ctx, RXGS_E_OOM, "FiLM coefficients");
+      dfree(ab, st); dfree(loc, st); dfree(feat, st); dfree(image, st);
+      return fail(ctx, RXGS_E_OOM, "FiLM radiance");
     }
     launch_film_global(d->film, f, rx, N, ab, st);
     if (d->film_local) {
       if (feat) launch_occ_probes(s->geom, s->K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
       launch_local_factors(s->mlp, rx, N, s->geom, s->K, feat, loc, st);
     }
-    launch_film_coeffs(d->fle_base, ab, loc, N, s->K, d->fle_lmax, coeffs, st);
-    dfree(loc, st);
-    dfree(feat, st);
-    unsigned char* image = nullptr;
-    if (dalloc(&image, fle_basis_image_bytes(s->K, v->M), st) != cudaSuccess) {
-      dfree(ab, st); dfree(coeffs, st);
-      return fail(ctx, RXGS_E_OOM, "FLE basis image");
-    }
     {
       Stage sb(ctx, "fle_basis", st);  // within the radiance stage
       launch_fle_basis_image(s->geom, v->tx, s->K, v->M, d->fle_lmax, image, st);
     }
     clear_pad_columns(rad, static_cast<size_t>(v->M) * s->K, stride, 2 * N, st);
-    launch_fle_radiance_tc(coeffs, N, s->K, d->fle_lmax, image, v->M, stride,
-                           static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
+    launch_fle_radiance_film_tc(d->fle_base, ab, loc, N, s->K, d->fle_lmax, image, v->M, stride,
+                                static_cast<size_t>(s->K) * stride, rad, st, ctx->d_err);
     dfree(image, st);
     dfree(ab, st);
-    dfree(coeffs, st);
+    dfree(loc, st);
+    dfree(feat, st);
   } else if (d->fle_coeffs) {
     unsigned char* image = nullptr;
     if (dalloc(&image, fle_basis_image_bytes(s->K, v->M), st) != cudaSuccess)

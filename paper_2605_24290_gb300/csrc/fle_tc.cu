@@ -5,7 +5,7 @@
 //   s[v][k][j] = sum_l Y_vl c_jl = sum_P Yr c+_j + i sum_Q Yi c-_j
 // with the +m / -m components folded (fle_tc.cuh) and c_jl the coefficients
 // (a + i b)_jk,l (given, or formed from the base coefficients by the global
-// FiLM branch, film_coeffs below).  Real-ified, with the coefficient rows
+// FiLM branch inside the converters, kFilm).  Real-ified, with the coefficient rows
 // interleaved (row 2j = Re, row 2j + 1 = Im) as the A operand (M = 128) and
 // the folded basis of the 32 views as the B operand (N = 32):
 //   P1 = A+ Yr^T (K = P components),  P2 = A- Yi^T (K = Q components)
@@ -279,12 +279,18 @@ __device__ __forceinline__ void store_a(uint32_t a, const float (&c)[100]) {
   }
 }
 
-template <bool kBulk>
+// kFilm: the coefficients are formed in the converters from the base
+// coefficients and the modulations (Eq. film_apply; with loc, Eq.
+// combined_local), never written to memory: the CTA keeps its receiver
+// group's (a, b) table [component][receiver] in shared memory (loaded once)
+// and warp 0 stages each job's base coefficients phi_k (2L floats).
+template <bool kBulk, bool kFilm>
 __global__ void __launch_bounds__(kThreads, 1)
     fle_radiance_tc_kernel(const float* __restrict__ coeffs, int N, int K, int lmax,
                            const unsigned char* __restrict__ image, int M, int stride,
                            size_t rad_view, float* __restrict__ rad, unsigned* __restrict__ err,
-                           const __grid_constant__ CUtensorMap tmap) {
+                           const __grid_constant__ CUtensorMap tmap, const float* __restrict__ base,
+                           const float4* __restrict__ ab, const float4* __restrict__ loc) {
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kOffBar);
   uint64_t* cfull = bar;                 // [kStages] coefficients landed
@@ -299,12 +305,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile uint32_t* abort_flag = &sMisc[1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int L = (lmax + 1) * (lmax + 1);
-  const int njobs = jobs_of_cta(K, N), nvg = (M + kViews - 1) / kViews;
+  const int G = kFilm ? (N + kRx - 1) / kRx : 0;
+  const int njobs = jobs_of_cta(K, N, G), nvg = (M + kViews - 1) / kViews;
+  // kFilm: the (a, b) table float4 [L][kRx] and kStages stages of phi (2L floats)
+  float4* sTab = reinterpret_cast<float4*>(sm);
+  float* sPhi = reinterpret_cast<float*>(sm + kRx * 100 * 16);
+  if constexpr (kFilm) {
+    const int jg = static_cast<int>(blockIdx.x) % G, j0 = jg * kRx;
+    for (int e = threadIdx.x; e < kRx * L; e += kThreads) {
+      const int l = e / kRx, jl = e - l * kRx;
+      sTab[e] = j0 + jl < N ? ab[static_cast<size_t>(j0 + jl) * L + l]
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
 
   if (warp == 0) tc::tmem_alloc(&sMisc[0], kTmemCols);
   if (threadIdx.x == 32) {
     for (int i = 0; i < kStages; ++i) {
-      tc::mbar_init(&cfull[i], 1);
+      tc::mbar_init(&cfull[i], kFilm ? 32 : 1);
       tc::mbar_init(&cempty[i], 4);
     }
     for (int i = 0; i < 2; ++i) {
@@ -333,14 +351,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     return ok;
   };
 
-  if (warp == 0) {
+  if (warp == 0 && kFilm) {
+    // ------------------------------------------------- base coefficients
+    // per job phi_k (2L floats) into one of kStages stages, all lanes
+    JobIter it(K, G);
+    for (int n = 0; n < njobs; ++n, it.next()) {
+      if (*abort_flag) break;
+      const int st = n % kStages;
+      if (n >= kStages && !wait_warp(&cempty[st], ((n / kStages) - 1) & 1)) break;
+      const float* src = base + static_cast<size_t>(it.k) * 2 * L;
+      float* dst = sPhi + st * 200;
+      for (int e = lane; e < 2 * L; e += 32) dst[e] = __ldg(src + e);
+      tc::mbar_arrive(&cfull[st]);  // release: each lane's stores before its arrival
+    }
+  } else if (warp == 0) {
     // ------------------------------------------------- coefficient producer
     // per job one box of the coefficient rows (rows j0 .. j0 + 63 of Gaussian
     // k; rows past N read as zero)
     if (kBulk && lane == 0) {
       const uint32_t box_bytes = static_cast<uint32_t>(min(kRx, N)) * 8u * L;
       int issued = 0;
-      JobIter it(K);
+      JobIter it(K, G);
       for (int n = 0; n < njobs; ++n, it.next()) {
         if (*abort_flag) break;
         const int st = n % kStages;
@@ -363,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int s = 0, issued = 0;
       bool stop = false;
-      JobIter it(K);
+      JobIter it(K, G);
       for (int n = 0; n < njobs && !stop; ++n, it.next()) {
         for (int vg = 0; vg < nvg; ++vg, ++s) {
           if (*abort_flag) { stop = true; break; }
@@ -431,17 +462,51 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------------------------------------------------------- A operand
     // two groups of four warps take the even and the odd jobs
     const int grp = warp >= 12, q = warp & 3, row = 32 * q + lane, jl = row >> 1, p = row & 1;
-    JobIter it(K);
+    JobIter it(K, G);
     if (grp) it.next();
     for (int n = grp; n < njobs; n += 2, it.next(), it.next()) {
       if (*abort_flag) break;
       const int st = n % kStages;
-      if (kBulk && !wait_warp(&cfull[st], (n / kStages) & 1)) break;
+      if ((kBulk || kFilm) && !wait_warp(&cfull[st], (n / kStages) & 1)) break;
       if (n >= 2 && !wait_warp(&adone[n & 1], ((n >> 1) - 1) & 1)) break;
       tc::fence_after_sync();
       const bool on = jl < N - it.jg * kRx;
       float c[100];
-      if (kBulk) {
+      if (kFilm) {
+        // c = (1 + a) phi + b (complex, per component), then (1 + alpha) c +
+        // beta with the local factors; this lane keeps the Re (p = 0) or Im
+        // (p = 1) part
+        // Re: (1 + a.re) phi.re - a.im phi.im + b.re; Im: (1 + a.re) phi.im +
+        // a.im phi.re + b.im -- with x, y = this part's and the other part of
+        // phi and sg = -1 / +1, both are fma(1 + a.re, x, fma(sg a.im, y, b))
+        const float* ph = sPhi + st * 200;
+        const float* px = ph + p * L;
+        const float* py = ph + (1 - p) * L;
+        const float sg = p ? 1.0f : -1.0f;
+        const float4 lf = (loc && on) ? loc[static_cast<size_t>(it.jg * kRx + jl) * K + it.k]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float alr = 1.0f + lf.x, sal = sg * lf.y, bl = p ? lf.w : lf.z;
+#pragma unroll
+        for (int l = 0; l < 100; ++l) {
+          float v = 0.0f;
+          if (l < L) {
+            const float4 q4 = sTab[l * kRx + jl];
+            v = fmaf(1.0f + q4.x, px[l], fmaf(sg * q4.y, py[l], p ? q4.w : q4.z));
+          }
+          c[l] = v;
+        }
+        if (loc) {
+          // (1 + alpha) c + beta: the other part from the partner lane
+#pragma unroll
+          for (int l = 0; l < 100; ++l) {
+            const float o = __shfl_xor_sync(0xffffffffu, c[l], 1);
+            if (l < L) c[l] = fmaf(alr, c[l], fmaf(sal, o, bl));
+          }
+        }
+        if (!on)
+#pragma unroll
+          for (int l = 0; l < 100; ++l) c[l] = 0.0f;
+      } else if (kBulk) {
         const float4* r4 =
             reinterpret_cast<const float4*>(sm + st * kCStage + (jl * 2 * L + p * L) * 4);
 #pragma unroll
@@ -464,14 +529,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) {
         tc::mbar_arrive(&afull[n & 1]);
-        if (kBulk) tc::mbar_arrive(&cempty[st]);
+        if (kBulk || kFilm) tc::mbar_arrive(&cempty[st]);
       }
     }
   } else if (warp >= 8 && warp < 12) {
     // ---------------------------------------------------------------- write-out
     const int q = warp - 8, row = 32 * q + lane;
     const bool odd = lane & 1, has_q = kq_of(lmax) > 0;
-    JobIter it(K);
+    JobIter it(K, G);
     int s = 0;
     bool stop = false;
     for (int n = 0; n < njobs && !stop; ++n, it.next()) {
@@ -509,18 +574,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <bool kBulk>
+template <bool kBulk, bool kFilm>
 void launch_radiance(const float* coeffs, int N, int K, int lmax, const unsigned char* image,
                      int M, int stride, size_t rad_view, float* rad, int grid, cudaStream_t s,
-                     unsigned* err, const CUtensorMap& tmap) {
+                     unsigned* err, const CUtensorMap& tmap, const float* base = nullptr,
+                     const float4* ab = nullptr, const float4* loc = nullptr) {
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(fle_radiance_tc_kernel<kBulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(kSmem));
+    cudaFuncSetAttribute(fle_radiance_tc_kernel<kBulk, kFilm>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmem));
     configured = true;
   }
-  fle_radiance_tc_kernel<kBulk><<<grid, kThreads, kSmem, s>>>(coeffs, N, K, lmax, image, M,
-                                                              stride, rad_view, rad, err, tmap);
+  fle_radiance_tc_kernel<kBulk, kFilm><<<grid, kThreads, kSmem, s>>>(
+      coeffs, N, K, lmax, image, M, stride, rad_view, rad, err, tmap, base, ab, loc);
 }
 
 }  // namespace
@@ -551,11 +617,27 @@ void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax,
   const int L = (lmax + 1) * (lmax + 1);
   CUtensorMap tmap{};
   if (encode_fle_rows(&tmap, coeffs, N, K, L))
-    launch_radiance<true>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s, err,
-                          tmap);
+    launch_radiance<true, false>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s,
+                                 err, tmap);
   else
-    launch_radiance<false>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s, err,
-                           tmap);
+    launch_radiance<false, false>(coeffs, N, K, lmax, image, M, stride, rad_view, rad, grid, s,
+                                  err, tmap);
+  note_launches(1);
+}
+
+void launch_fle_radiance_film_tc(const float* base, const float4* ab, const float4* loc, int N,
+                                 int K, int lmax, const unsigned char* image, int M, int stride,
+                                 size_t rad_view, float* rad, cudaStream_t s, unsigned* err) {
+  if (K <= 0 || N <= 0 || M <= 0) return;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // G receiver groups, P CTAs per group (each keeps its group's modulation)
+  const int G = (N + kRx - 1) / kRx;
+  const int P = std::max(1, std::min(K, nsm / G));
+  CUtensorMap tmap{};
+  launch_radiance<false, true>(nullptr, N, K, lmax, image, M, stride, rad_view, rad, G * P, s,
+                               err, tmap, base, ab, loc);
   note_launches(1);
 }
 
@@ -563,53 +645,6 @@ void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax,
 
 namespace rxgs {
 
-// ---- the global FiLM branch over the FLE coefficients (Eq. film_apply)
-// c[j][k][.][l] = (1 + a_jl) base[k][.][l] + b_jl (complex), ab[j][l] =
-// (a.re, a.im, b.re, b.im): the coefficients that the tensor-core contraction
-// above then reduces against the basis.  With the local branch (loc[j][k] =
-// (alpha.re, alpha.im, beta.re, beta.im), Eq. combined_local) they become
-// (1 + alpha_jk) c_jkl + beta_jk.
-// block (range of kFilmK Gaussians, receiver j), thread = component l: the
-// modulation (a_jl, b_jl) loaded once, then the Gaussians in turn (both
-// half-rows written coalesced).
-constexpr int kFilmK = 16;
-
-__global__ void __launch_bounds__(128) film_coeffs_kernel(const float* __restrict__ base,
-                                                          const float4* __restrict__ ab,
-                                                          const float4* __restrict__ loc, int K,
-                                                          int L, float* __restrict__ out) {
-  const int l = threadIdx.x, j = blockIdx.y;
-  if (l >= L) return;
-  const float4 q = ab[static_cast<size_t>(j) * L + l];
-  const float ar = 1.0f + q.x;
-  const int k0 = blockIdx.x * kFilmK, k1 = min(K, k0 + kFilmK);
-#pragma unroll 4
-  for (int k = k0; k < k1; ++k) {
-    const float pr = base[static_cast<size_t>(k) * 2 * L + l];
-    const float pi = base[static_cast<size_t>(k) * 2 * L + L + l];
-    float cr = fmaf(ar, pr, fmaf(-q.y, pi, q.z));
-    float ci = fmaf(ar, pi, fmaf(q.y, pr, q.w));
-    const size_t jk = static_cast<size_t>(j) * K + k;
-    if (loc) {
-      const float4 lf = loc[jk];
-      const float alr = 1.0f + lf.x;
-      const float r = fmaf(alr, cr, fmaf(-lf.y, ci, lf.z));
-      ci = fmaf(alr, ci, fmaf(lf.y, cr, lf.w));
-      cr = r;
-    }
-    float* o = out + jk * 2 * L;
-    o[l] = cr;
-    o[L + l] = ci;
-  }
-}
-
-void launch_film_coeffs(const float* base, const float4* ab, const float4* loc, int N, int K,
-                        int lmax, float* out, cudaStream_t s) {
-  const int L = (lmax + 1) * (lmax + 1);
-  if (N <= 0 || K <= 0) return;
-  film_coeffs_kernel<<<dim3((K + kFilmK - 1) / kFilmK, N), 128, 0, s>>>(base, ab, loc, K, L, out);
-  note_launches(1);
-}
 
 // ---- its backward, from the coefficient gradient G[j][k][.][l]:
 //   dL/dbase_kl = sum_j conj(1 + a_jl) G_jkl      (film_fold_base: one thread

@@ -53,21 +53,39 @@ __host__ __device__ inline int kq_of(int lmax) { return (lmax * (lmax + 1) / 2 +
 // The CTA's jobs are (Gaussian k, receiver group jg) for global index
 // g = blockIdx.x + n * gridDim.x (n = 0, 1, ...), k = g % K, jg = g / K; each
 // job has one step per group of 32 views.  The iterator advances (k, jg)
-// without divisions.
-__device__ __forceinline__ int jobs_of_cta(int K, int N) {
+// without divisions.  With G > 0 (the FiLM-conditioned contraction, whose
+// CTAs keep one receiver group's modulation in shared memory) the grid is
+// G x P CTAs: CTA b keeps group jg = b % G and takes k = b / G, b / G + P, ...
+__device__ __forceinline__ int jobs_of_cta(int K, int N, int G = 0) {
+  if (G > 0) {
+    const int kb = static_cast<int>(blockIdx.x) / G, P = static_cast<int>(gridDim.x) / G;
+    return kb < K ? (K - 1 - kb) / P + 1 : 0;
+  }
   const long long total = static_cast<long long>(K) * ((N + kRx - 1) / kRx);
   const long long b = blockIdx.x;
   return b < total ? static_cast<int>((total - 1 - b) / gridDim.x + 1) : 0;
 }
 struct JobIter {
-  int K, k, jg;
-  __device__ explicit JobIter(int K_) : K(K_), k(static_cast<int>(blockIdx.x)), jg(0) {
+  int K, k, jg, step;
+  bool fixed;
+  __device__ explicit JobIter(int K_, int G = 0) : K(K_), k(0), jg(0), step(0), fixed(G > 0) {
+    if (fixed) {
+      jg = static_cast<int>(blockIdx.x) % G;
+      k = static_cast<int>(blockIdx.x) / G;
+      step = static_cast<int>(gridDim.x) / G;
+      return;
+    }
+    k = static_cast<int>(blockIdx.x);
     while (k >= K) {
       k -= K;
       ++jg;
     }
   }
   __device__ void next() {
+    if (fixed) {
+      k += step;
+      return;
+    }
     k += static_cast<int>(gridDim.x);
     while (k >= K) {
       k -= K;

@@ -202,15 +202,19 @@ void launch_fle_backward_tc(const float* d_rad, int N, int K, int lmax,
 void launch_fle_radiance_tc(const float* coeffs, int N, int K, int lmax,
                             const unsigned char* image, int M, int stride, size_t rad_view,
                             float* rad, cudaStream_t s, unsigned* err);
-// The global FiLM branch over the FLE coefficients (fle_tc.cu): the
-// conditioned coefficients out[N][K][2][L] = (1 + a_jl) base[K][2][L] + b_jl
-// (Eq. film_apply, ab[N][L] = (a.re, a.im, b.re, b.im)), and the fold of
-// their gradient G[N][K][2][L] into grad_base[K][2][L] += sum_j conj(1 + a) G
-// and d_ab[N][L][4] += sum_k (conj(base) G, G) (either may be NULL).
-// loc[N][K] (or NULL): the local branch's (alpha, beta) per pair (Eq.
-// combined_local), applied as (1 + alpha) c + beta.
-void launch_film_coeffs(const float* base, const float4* ab, const float4* loc, int N, int K,
-                        int lmax, float* out, cudaStream_t s);
+// The same contraction with the coefficients formed inside it (the global
+// FiLM branch, Eq. film_apply): c[j][k][.][l] = (1 + a_jl) base[k][.][l] +
+// b_jl (complex) from the base coefficients base[K][2][L] and the
+// modulations ab[N][L] = (a.re, a.im, b.re, b.im); when loc is not null,
+// the local factors loc[N][K] = (alpha.re, alpha.im, beta.re, beta.im) make
+// it (1 + alpha) c + beta (Eq. combined_local).  c is never written to
+// memory.
+void launch_fle_radiance_film_tc(const float* base, const float4* ab, const float4* loc, int N,
+                                 int K, int lmax, const unsigned char* image, int M, int stride,
+                                 size_t rad_view, float* rad, cudaStream_t s, unsigned* err);
+// The fold of the conditioned coefficients' gradient G[N][K][2][L] (fle_tc.cu)
+// into grad_base[K][2][L] += sum_j conj(1 + a) G and d_ab[N][L][4] +=
+// sum_k (conj(base) G, G) (either may be NULL).
 void launch_film_fold(const float* G, int N, int K, int lmax, const float* base,
                       const float4* ab, float* grad_base, float* d_ab, cudaStream_t s);
 
