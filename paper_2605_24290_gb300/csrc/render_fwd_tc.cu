@@ -66,7 +66,7 @@ static_assert(kOffPart + 8 * kNB * 4 <= kOffRec, "staging and partial sums fit i
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(2 * kSmem <= 232448, "two CTAs per SM");
 
-constexpr int kWq = 4;  // weights evaluated at once per thread (independent chains)
+constexpr int kWq = 3;  // weights evaluated at once per thread (independent chains)
 constexpr uint32_t kTmemCols = 256;  // two M tiles x 128 float32 columns
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr uint32_t kIdesc = tc::idesc_bf16(128, 128, 1, 1);
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (a.err) atomicOr(a.err, kErrTimeout);
     }
     // A[p][b] = T w for the entries of this warp's strip, in depth order:
-    // weights four entries at a time (independent, branch-free), then the
+    // weights three entries at a time (independent, branch-free), then the
     // transmittance updates in list order
     const float4* sR = sRec0 + (n & 1) * 2 * kCH;
     const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
@@ -227,7 +227,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       *reinterpret_cast<__nv_bfloat16*>(sm + kOffA1 + off) = hi;
       *reinterpret_cast<__nv_bfloat16*>(sm + kOffA2 + off) = lo;
     };
-    for (unsigned z = ~mask; z; z &= z - 1) put_a(__ffs(z) - 1, 0.0f);
+    // entries that meet no pixel of the strip: A = 0 (both terms, no split)
+    for (unsigned z = ~mask; z; z &= z - 1) {
+      const int b = __ffs(z) - 1;
+      const uint32_t off = (b >> 3) * kSboA + (t >> 3) * kLboA + (b & 7) * 16 + (t & 7) * 2;
+      *reinterpret_cast<uint16_t*>(sm + kOffA1 + off) = 0;
+      *reinterpret_cast<uint16_t*>(sm + kOffA2 + off) = 0;
+    }
     for (unsigned m = mask; m;) {
       int bq[kWq];
 #pragma unroll
