@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   iT = 1.0f / iT;
+  const uint32_t strip_stop = __reduce_max_sync(0xffffffffu, stop);  // the warp's 32 pixels
   // ---- the sweep, back to front
   for (int n = 0; n < nchunks; ++n) {
     tc::fence_smem_to_async();  // s(n) (and g for n = 0) for the tensor core
@@ -415,7 +416,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     {
       const bool rel = lane < nb && touches_strip(g, sR[2 * lane + 1], strip);
       unsigned m = __ballot_sync(0xffffffffu, rel);
-      if (!__any_sync(0xffffffffu, start < stop)) m = 0;  // no pixel reaches this chunk
+      // entries at or past the strip's last stop position are composited by
+      // none of its pixels
+      if (strip_stop <= start)
+        m = 0;
+      else if (strip_stop - start < 32u)
+        m &= (1u << (strip_stop - start)) - 1u;
       if (half == 0 && lane == 0) sMask[wp] = m;
       unsigned mine = m & (half ? 0xaaaaaaaau : 0x55555555u);  // odd / even entries
       while (mine) {
