@@ -149,11 +149,22 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
     const float* __restrict__ glob, float* __restrict__ out, const int* __restrict__ n_dev,
     const int* __restrict__ col_of, const float2* __restrict__ feat) {
   constexpr int n4 = 4 * CC;
-  __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
+  // per hidden unit u, as 16-byte broadcasts: (w1[0..3]), (w1[4], w1[5], b1, 0)
+  // and the unit's output weights (W2[4c..4c+3][u]) per channel c
+  __shared__ float4 W1a[kHidden], W1b[kHidden], W2t[kHidden * CC];
+  __shared__ float B2[n4];
   const MlpOffsets o = mlp_offsets(kHidden, CC);
-  for (int e = threadIdx.x; e < kHidden * 6; e += blockDim.x) W1[e] = rb(P[o.l_w1 + e], bf16);
-  for (int e = threadIdx.x; e < kHidden; e += blockDim.x) B1[e] = P[o.l_b1 + e];
-  for (int e = threadIdx.x; e < n4 * kHidden; e += blockDim.x) W2[e] = rb(P[o.l_w2 + e], bf16);
+  for (int u = threadIdx.x; u < kHidden; u += blockDim.x) {
+    const float* w = P + o.l_w1 + u * 6;
+    W1a[u] = make_float4(rb(w[0], bf16), rb(w[1], bf16), rb(w[2], bf16), rb(w[3], bf16));
+    W1b[u] = make_float4(rb(w[4], bf16), rb(w[5], bf16), P[o.l_b1 + u], 0.0f);
+#pragma unroll
+    for (int c = 0; c < CC; ++c)
+      W2t[u * CC + c] = make_float4(rb(P[o.l_w2 + (4 * c + 0) * kHidden + u], bf16),
+                                    rb(P[o.l_w2 + (4 * c + 1) * kHidden + u], bf16),
+                                    rb(P[o.l_w2 + (4 * c + 2) * kHidden + u], bf16),
+                                    rb(P[o.l_w2 + (4 * c + 3) * kHidden + u], bf16));
+  }
   for (int e = threadIdx.x; e < n4; e += blockDim.x) B2[e] = P[o.l_b2 + e];
   __syncthreads();
   const size_t npairs = static_cast<size_t>(N) * K;
@@ -197,11 +208,15 @@ __global__ void __launch_bounds__(256) mlp_local_narrow_kernel(
 #pragma unroll 4
   for (int u = 0; u < kHidden; ++u) {
     float w1[6], w2[n4];
+    const float4 a4 = W1a[u], b4 = W1b[u];
+    w1[0] = a4.x; w1[1] = a4.y; w1[2] = a4.z; w1[3] = a4.w;
+    w1[4] = b4.x; w1[5] = b4.y;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) w1[i] = W1[u * 6 + i];
-#pragma unroll
-    for (int q = 0; q < n4; ++q) w2[q] = W2[q * kHidden + u];
-    const float b1 = B1[u];
+    for (int c = 0; c < CC; ++c) {
+      const float4 t4 = W2t[u * CC + c];
+      w2[4 * c] = t4.x; w2[4 * c + 1] = t4.y; w2[4 * c + 2] = t4.z; w2[4 * c + 3] = t4.w;
+    }
+    const float b1 = b4.z;
 #pragma unroll
     for (int r = 0; r < PP; ++r) {
       // inputs 4 and 5 are the constants 1 and 0: the same fmaf chain as the
