@@ -396,16 +396,30 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   v->K = s->K;
   v->tile_bits = bits_for(static_cast<uint64_t>(g.T));
   v->view_bits = bits_for(static_cast<uint64_t>(M));
-  if (31 + v->tile_bits + v->view_bits > 64) {
+  if (v->tile_bits + v->view_bits > 32) {
     delete v;
-    return fail(ctx, RXGS_E_INVALID, "too many views x tiles for a 64-bit key");
+    return fail(ctx, RXGS_E_INVALID, "too many views x tiles for a 32-bit (view, tile) key");
   }
   const size_t MK = static_cast<size_t>(M) * s->K;
+  if (MK >= 0xffffffffull) {
+    delete v;
+    return fail(ctx, RXGS_E_INVALID, "views x Gaussians must stay below 2^32");
+  }
   uint32_t* scan_tmp = nullptr;
+  // the depth order of every view's Gaussians: key and index buffers of
+  // the segmented sort, the counts in that order
+  uint32_t *dkeys = nullptr, *dkeys_alt = nullptr, *ord_a = nullptr, *ord_b = nullptr;
+  uint32_t *dsort_tmp = nullptr, *scounts = nullptr;
+  const uint32_t* ord = nullptr;
+  auto free_order = [&]() {
+    dfree(dkeys, st); dfree(dkeys_alt, st); dfree(ord_a, st); dfree(ord_b, st);
+    dfree(dsort_tmp, st); dfree(scounts, st);
+  };
   auto cleanup = [&]() {
     dfree(v->tx, st); dfree(v->rec, st); dfree(v->depth, st); dfree(v->counts, st);
     dfree(v->offsets, st); dfree(v->keys, st); dfree(v->vals, st); dfree(v->ranges, st);
     dfree(scan_tmp, st);
+    free_order();
     delete v;
   };
   cudaError_t e = dalloc(&v->tx, 3ull * M, st);
@@ -429,6 +443,12 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   if (e == cudaSuccess) e = dalloc(&v->offsets, MK + 1, st);
   if (e == cudaSuccess) e = dalloc(&scan_tmp, scan_tmp_words(MK), st);
   if (e == cudaSuccess) e = dalloc(&v->ranges, static_cast<size_t>(M) * g.T, st);
+  if (e == cudaSuccess) e = dalloc(&dkeys, MK, st);
+  if (e == cudaSuccess) e = dalloc(&dkeys_alt, MK, st);
+  if (e == cudaSuccess) e = dalloc(&ord_a, MK, st);
+  if (e == cudaSuccess) e = dalloc(&ord_b, MK, st);
+  if (e == cudaSuccess) e = dalloc(&dsort_tmp, radix_segments_tmp_words(s->K, M), st);
+  if (e == cudaSuccess) e = dalloc(&scounts, MK, st);
   if (e != cudaSuccess) {
     cleanup();
     return fail(ctx, RXGS_E_OOM, "prepare: %s", cudaGetErrorString(e));
@@ -438,8 +458,16 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st);
   }
   {
+    // every view's Gaussians by depth (ties: ascending Gaussian index), and
+    // their tile counts in that order
+    Stage sg(ctx, "depth_sort", st);
+    ord = radix_sort_segments(v->depth, s->K, M, 31, dkeys, dkeys_alt, ord_a, ord_b, dsort_tmp,
+                              st);
+    launch_gather_words(v->counts, ord, MK, scounts, st);
+  }
+  {
     Stage sg(ctx, "scan", st);
-    launch_exclusive_scan(v->counts, v->offsets, MK, scan_tmp, st);
+    launch_exclusive_scan(scounts, v->offsets, MK, scan_tmp, st);
   }
   // the instance count, written into the pinned readback slot by a kernel
   // (a copy-engine transfer would queue behind the caller's large copies)
@@ -457,7 +485,7 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
     return fail(ctx, RXGS_E_INVALID, "instance count overflow");
   }
   v->n_inst = I;
-  uint64_t* keys_alt = nullptr;
+  uint32_t* keys_alt = nullptr;
   uint32_t* vals_alt = nullptr;
   uint32_t* sort_tmp = nullptr;
   e = dalloc(&v->keys, I, st);
@@ -472,12 +500,14 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   }
   {
     Stage sg(ctx, "emit", st);
-    launch_emit(g, v->rec, v->depth, v->offsets, s->K, M, v->tile_bits, v->keys, v->vals, st);
+    launch_emit_sorted(g, v->rec, ord, v->offsets, MK, s->K, v->tile_bits, v->keys, v->vals, st);
   }
+  free_order();
   bool in_alt = false;
   {
+    // stable: each (view, tile) keeps the depth order of the emission
     Stage sg(ctx, "sort", st);
-    radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, 31 + v->tile_bits + v->view_bits,
+    radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, v->tile_bits + v->view_bits,
                      sort_tmp, &in_alt, st, nullptr, ctx->d_err);
   }
   if (in_alt) {
@@ -830,7 +860,10 @@ rxgs_status rxgs_views_export(rxgs_ctx* ctx, rxgs_views_t views, float* rec, uin
   const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
   if (rec) CK(cudaMemcpyAsync(rec, v->rec, sizeof(float4) * 2 * MK, dd, st));
   if (counts) CK(cudaMemcpyAsync(counts, v->counts, sizeof(uint32_t) * MK, dd, st));
-  if (keys && v->n_inst) CK(cudaMemcpyAsync(keys, v->keys, sizeof(uint64_t) * v->n_inst, dd, st));
+  if (keys && v->n_inst) {
+    launch_expand_keys(v->keys, v->vals, v->n_inst, v->depth, v->K, v->tile_bits, keys, st);
+    CK(cudaGetLastError());
+  }
   if (vals && v->n_inst) CK(cudaMemcpyAsync(vals, v->vals, sizeof(uint32_t) * v->n_inst, dd, st));
   if (ranges)
     CK(cudaMemcpyAsync(ranges, v->ranges, sizeof(uint2) * static_cast<size_t>(v->M) * ctx->g.T, dd,

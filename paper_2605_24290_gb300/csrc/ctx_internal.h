@@ -40,9 +40,9 @@ struct ViewsState {
   float* tx = nullptr;        // [M][3]
   float4* rec = nullptr;      // [M][K][2]
   uint32_t* depth = nullptr;  // [M][K]
-  uint32_t* counts = nullptr; // [M*K]
-  uint32_t* offsets = nullptr;// [M*K+1]
-  uint64_t* keys = nullptr;   // [I]
+  uint32_t* counts = nullptr; // [M*K] tile counts, view-major
+  uint32_t* offsets = nullptr;// [M*K+1] scan of the counts in (view, depth) order
+  uint32_t* keys = nullptr;   // [I] (view << tile_bits | tile), sorted
   uint32_t* vals = nullptr;   // [I]
   uint2* ranges = nullptr;    // [M][T]
   uint32_t n_inst = 0;

@@ -304,6 +304,116 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
   note_launches(1);
 }
 
+// ---------------------------------------------- instances in depth order
+// The per-tile lists (Algorithm 1, Stage 1) in two sorts instead of one over
+// 64-bit (view | tile | depth) instance keys: every view's Gaussians by
+// depth (a segmented sort of the depth keys, one segment per view, values
+// the view-major pair index; the stable sort keeps equal depths in
+// ascending Gaussian index), then the instances, emitted in that order, by
+// (view, tile) with 32-bit keys (the stable sort keeps each tile's
+// instances in depth order).  The result is the order of the single sort:
+// by (view, tile, depth, Gaussian index).
+__global__ void gather_words_kernel(const uint32_t* __restrict__ src,
+                                    const uint32_t* __restrict__ idx, size_t n,
+                                    uint32_t* __restrict__ dst) {
+  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+void launch_gather_words(const uint32_t* src, const uint32_t* idx, size_t n, uint32_t* dst,
+                         cudaStream_t s) {
+  if (n == 0) return;
+  gather_words_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(src, idx, n, dst);
+  note_launches(1);
+}
+
+// Instances of the depth-ordered pairs: pair i (view-major index ord[i])
+// writes its tiles at offsets[i] .. offsets[i + 1] - 1 with key
+// view << tile_bits | tile and value the Gaussian index.  A warp takes 32
+// consecutive pairs; their instances form one contiguous range, lane l
+// writes positions start + l, start + l + 32, ... (coalesced), the owner
+// found by binary search over the warp's offsets as in emit_kernel.
+__global__ void __launch_bounds__(256) emit_sorted_kernel(
+    GridConst g, const float4* __restrict__ rec, const uint32_t* __restrict__ ord,
+    const uint32_t* __restrict__ offsets, size_t MK, int K, int tile_bits,
+    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  __shared__ uint32_t sO[8][33];  // per warp: first position of each lane's pair, end
+  __shared__ int4 sD[8][32];      // (tr0, ncols, n0 | c0a << 16, c1a)
+  __shared__ uint2 sB[8][32];     // (view << tile_bits, Gaussian index)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  uint32_t o, end;
+  int4 d = make_int4(0, 1, 0, 0);
+  uint2 b = make_uint2(0u, 0u);
+  if (i < MK) {
+    o = offsets[i];
+    end = offsets[i + 1];
+    if (end > o) {
+      const uint32_t idx = ord[i];
+      const uint32_t m = idx / static_cast<uint32_t>(K);
+      const float4 r1 = rec[2 * static_cast<size_t>(idx) + 1];
+      const int rows = __float_as_int(r1.z), cols = __float_as_int(r1.w);
+      const int i_lo = rows & 0xffff, j_lo = cols & 0xffff, span = cols >> 16;
+      const TileCols tc = tile_cols(g, j_lo, span);
+      const int n0 = tc.c0b - tc.c0a + 1, n1 = tc.c1b >= tc.c1a ? tc.c1b - tc.c1a + 1 : 0;
+      d = make_int4(i_lo / g.TH, n0 + n1, n0 | (tc.c0a << 16), tc.c1a);
+      b = make_uint2(m << tile_bits, idx - m * static_cast<uint32_t>(K));
+    }
+  } else {
+    o = end = offsets[MK];  // past the last pair
+  }
+  sO[w][lane] = o;
+  if (lane == 31) sO[w][32] = end;
+  sD[w][lane] = d;
+  sB[w][lane] = b;
+  __syncwarp();
+  const uint32_t start = sO[w][0], stop = sO[w][32];
+  for (uint32_t q = start + lane; q < stop; q += 32) {
+    // the owner: the last lane whose first position is <= q (a lane with
+    // no instances shares its first position with the next lane)
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+      if (sO[w][lo + step] <= q) lo += step;
+    const int4 dd = sD[w][lo];
+    const uint2 bb = sB[w][lo];
+    const int j = static_cast<int>(q - sO[w][lo]);
+    const int row = j / dd.y, ci = j - row * dd.y;
+    const int n0 = dd.z & 0xffff;
+    const int c = ci < n0 ? (dd.z >> 16) + ci : dd.w + (ci - n0);
+    keys[q] = bb.x | static_cast<uint32_t>((dd.x + row) * g.tiles_w + c);
+    vals[q] = bb.y;
+  }
+}
+
+void launch_emit_sorted(const GridConst& g, const float4* rec, const uint32_t* ord,
+                        const uint32_t* offsets, size_t MK, int K, int tile_bits, uint32_t* keys,
+                        uint32_t* vals, cudaStream_t s) {
+  if (MK == 0) return;
+  emit_sorted_kernel<<<static_cast<unsigned>((MK + 255) / 256), 256, 0, s>>>(
+      g, rec, ord, offsets, MK, K, tile_bits, keys, vals);
+  note_launches(1);
+}
+
+// (view | tile) keys and Gaussian indices -> (view | tile | depth) keys
+__global__ void expand_keys_kernel(const uint32_t* __restrict__ vt, const uint32_t* __restrict__ vals,
+                                   size_t n, const uint32_t* __restrict__ depth, int K,
+                                   int tile_bits, uint64_t* __restrict__ out) {
+  const size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint32_t key = vt[q];
+  const size_t m = key >> tile_bits;
+  out[q] = (static_cast<uint64_t>(key) << 31) | depth[m * K + vals[q]];
+}
+
+void launch_expand_keys(const uint32_t* vt, const uint32_t* vals, size_t n, const uint32_t* depth,
+                        int K, int tile_bits, uint64_t* out, cudaStream_t s) {
+  if (n == 0) return;
+  expand_keys_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(vt, vals, n, depth, K,
+                                                                            tile_bits, out);
+  note_launches(1);
+}
+
 // ------------------------------------------------------------ small copies
 // n 32-bit words from src to dst by the SMs (device memory, or pinned host
 // memory mapped into the device's address space): small transfers that
@@ -323,14 +433,16 @@ void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_
 }
 
 // -------------------------------------------------------------- tile ranges
-__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, size_t n, int tile_bits,
+// Keys (view | tile | depth) (64 bits) or (view | tile) (32 bits).
+template <typename Key>
+__global__ void tile_ranges_kernel(const Key* __restrict__ keys, size_t n, int tile_bits,
                                    int T, uint2* __restrict__ ranges,
                                    const uint32_t* __restrict__ n_dev) {
   if (n_dev && *n_dev < n) n = *n_dev;
   const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  auto slot = [&](uint64_t key) {
-    const uint64_t vt = key >> 31;
+  auto slot = [&](Key key) {
+    const uint64_t vt = sizeof(Key) == 8 ? static_cast<uint64_t>(key) >> 31 : key;
     const uint64_t v = vt >> tile_bits, t = vt & ((1ull << tile_bits) - 1);
     return v * T + t;
   };
@@ -339,13 +451,24 @@ __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, size_t n, 
   if (i + 1 == n || slot(keys[i + 1]) != cur) ranges[cur].y = static_cast<unsigned>(i + 1);
 }
 
-void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
-                        int M, cudaStream_t s, const uint32_t* n_dev) {
+template <typename Key>
+static void tile_ranges(const Key* keys, size_t n, int tile_bits, int T, uint2* ranges, int M,
+                        cudaStream_t s, const uint32_t* n_dev) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(M) * T, s);
   if (n == 0) return;
-  tile_ranges_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(keys, n, tile_bits,
-                                                                            T, ranges, n_dev);
+  tile_ranges_kernel<Key><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      keys, n, tile_bits, T, ranges, n_dev);
   note_launches(1);
+}
+
+void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
+                        int M, cudaStream_t s, const uint32_t* n_dev) {
+  tile_ranges<uint64_t>(keys, n, tile_bits, T, ranges, M, s, n_dev);
+}
+
+void launch_tile_ranges(const uint32_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
+                        int M, cudaStream_t s, const uint32_t* n_dev) {
+  tile_ranges<uint32_t>(keys, n, tile_bits, T, ranges, M, s, n_dev);
 }
 
 // -------------------------------------------------------------------- scan

@@ -1,21 +1,28 @@
-// radix_sort.cu -- stable LSD radix sort of (uint64 key, uint32 value) pairs,
-// used to order every view's instances by (view, tile, depth) (Algorithm 1,
-// Stage 1: per-tile depth-sorted lists).  Stability keeps equal keys in
-// emission order, which is ascending Gaussian index.
+// radix_sort.cu -- stable LSD radix sort of (uint64 or uint32 key, uint32
+// value) pairs, used for the per-tile depth-sorted lists (Algorithm 1,
+// Stage 1): every view's Gaussians by depth (one segment per view, 31-bit
+// keys), then the instances by (view, tile) (32-bit keys), or the single
+// sort of (view | tile | depth) keys of the batched path; stability keeps
+// equal keys in input order.
 //
-// Digits of up to 9 bits (ceil(bits / 9) passes; 44-bit keys take 5).  One
-// pass = three kernels over tiles of 2,048 items:
+// Segments: nseg runs of `len` consecutive items, each sorted in place on
+// its own (nseg = 1: a plain sort).  Digits of up to 9 bits (ceil(bits / 9)
+// passes).  One pass = three kernels over tiles of 2,048 items, no tile
+// crossing a segment boundary:
 //   sort_count    each tile's digit counts (shared-memory histogram);
-//   sort_offsets  one block per digit: where each tile's run of that digit
-//                 starts within the digit (exclusive scan over the tiles),
-//                 and the digit's total;
-//   sort_scatter  adds the digit bases (an exclusive scan of the totals in
-//                 each block; no global atomics anywhere in the pass), ranks
-//                 the tile's items stably (warp match-any, per-warp digit
-//                 counters in shared memory), reorders the tile by digit in
-//                 shared memory and writes each digit's run to its place,
-//                 consecutive threads on consecutive addresses.
-// Every tile's loads are issued before any of its ranks is computed.
+//   sort_offsets  per (segment, digit): where each tile's run of that digit
+//                 starts within the digit (exclusive scan over the
+//                 segment's tiles), and the digit's total;
+//   sort_scatter  adds the digit bases (an exclusive scan of the segment's
+//                 totals in each block; no global atomics anywhere in the
+//                 pass), ranks the tile's items stably (warp match-any,
+//                 per-warp digit counters in shared memory), reorders the
+//                 tile by digit in shared memory and writes each digit's
+//                 run to its place, consecutive threads on consecutive
+//                 addresses.
+// Every tile's loads are issued before any of its ranks is computed.  The
+// first pass may read a key array it does not own and no values (each
+// item's value is then its index).
 #include <algorithm>
 #include <utility>
 
@@ -31,7 +38,7 @@ constexpr int kTile = kThreads * kItems;    // 2,048 items per tile
 constexpr int kMaxWidth = 9;
 constexpr int kBins = 1 << kMaxWidth;       // 512
 constexpr int kBinsPerThread = kBins / kThreads;
-constexpr int kMaxPasses = 8;
+constexpr int kWarpRowMax = 256;            // tiles per segment scanned by one warp
 
 struct Plan {
   int passes, width;
@@ -45,37 +52,61 @@ Plan plan_of(int bits) {
 
 size_t tiles_of(size_t n) { return (n + kTile - 1) / kTile; }
 
-// hist[d * nt + tile] = count of digit d in the tile
-__global__ void __launch_bounds__(kThreads) sort_count_kernel(const uint64_t* __restrict__ keys,
+// The segments of one sort: tile b is tile b % tps of segment b / tps.
+struct Segs {
+  size_t len;  // items per segment
+  int nseg;    // segments
+  int tps;     // tiles per segment
+};
+
+// Items [lo, hi) of tile b (hi <= lo: none); n: the items in all.
+struct TileSpan {
+  size_t lo, hi;
+  int seg, tt;
+};
+__device__ __forceinline__ TileSpan tile_span(const Segs& S, size_t n) {
+  TileSpan t;
+  t.seg = static_cast<int>(blockIdx.x / S.tps);
+  t.tt = static_cast<int>(blockIdx.x % S.tps);
+  const size_t s0 = static_cast<size_t>(t.seg) * S.len;
+  t.lo = s0 + static_cast<size_t>(t.tt) * kTile;
+  t.hi = min(min(t.lo + kTile, s0 + S.len), n);
+  return t;
+}
+
+// hist[(seg * kBins + d) * tps + tt] = count of digit d in tile tt of seg
+template <typename Key>
+__global__ void __launch_bounds__(kThreads) sort_count_kernel(const Key* __restrict__ keys,
                                                               size_t n,
                                                               const uint32_t* __restrict__ n_dev,
                                                               int shift, int width,
-                                                              uint32_t* __restrict__ hist, int nt) {
+                                                              uint32_t* __restrict__ hist, Segs S) {
   if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t h[kBins];
   for (int d = threadIdx.x; d < kBins; d += kThreads) h[d] = 0;
-  const size_t base = static_cast<size_t>(blockIdx.x) * kTile;
-  uint64_t k[kItems];
+  const TileSpan ts = tile_span(S, n);
+  Key k[kItems];
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const size_t i = base + static_cast<size_t>(r) * kThreads + threadIdx.x;
-    k[r] = i < n ? keys[i] : 0;
+    const size_t i = ts.lo + static_cast<size_t>(r) * kThreads + threadIdx.x;
+    k[r] = i < ts.hi ? keys[i] : 0;
   }
   __syncthreads();
-  const uint64_t mask = (1ull << width) - 1;
+  const Key mask = (Key(1) << width) - 1;
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
-    const size_t i = base + static_cast<size_t>(r) * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(k[r] >> shift) & mask], 1u);
+    const size_t i = ts.lo + static_cast<size_t>(r) * kThreads + threadIdx.x;
+    if (i < ts.hi) atomicAdd(&h[(k[r] >> shift) & mask], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kBins; d += kThreads)
-    hist[static_cast<size_t>(d) * nt + blockIdx.x] = h[d];
+  uint32_t* row = hist + static_cast<size_t>(ts.seg) * kBins * S.tps + ts.tt;
+  for (int d = threadIdx.x; d < kBins; d += kThreads) row[static_cast<size_t>(d) * S.tps] = h[d];
 }
 
-// Block d: hist[d][b] <- sum_{b' < b} hist[d][b'] (the run's start within
-// the digit) and totals[d] = the digit's count; the digit bases (exclusive
-// sums of the totals) are added by the scatter.
+// Row r = (seg, digit) of hist (tps entries): each entry <- the exclusive
+// sum of the entries before it (the tile's run start within the digit),
+// totals[r] = the row's sum; the digit bases (exclusive sums of a segment's
+// totals) are added by the scatter.  One block per row ...
 __global__ void __launch_bounds__(kThreads) sort_offsets_kernel(uint32_t* __restrict__ hist,
                                                                 uint32_t* __restrict__ totals,
                                                                 int nt) {
@@ -108,8 +139,44 @@ __global__ void __launch_bounds__(kThreads) sort_offsets_kernel(uint32_t* __rest
   if (threadIdx.x == 0) totals[d] = carry;
 }
 
+// ... or one warp per row when rows are short (nt <= kWarpRowMax): lane l
+// takes entries [l per, (l + 1) per), all loads in flight at once.
+__global__ void __launch_bounds__(kThreads) sort_offsets_warp_kernel(uint32_t* __restrict__ hist,
+                                                                     uint32_t* __restrict__ totals,
+                                                                     int nt, int rows) {
+  constexpr int kPer = kWarpRowMax / 32;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (r >= rows) return;  // whole warps leave together
+  uint32_t* row = hist + static_cast<size_t>(r) * nt;
+  const int per = (nt + 31) / 32;
+  uint32_t v[kPer];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = lane * per + q;
+    v[q] = (q < per && i < nt) ? row[i] : 0u;
+    sum += v[q];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  uint32_t run = x - sum;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = lane * per + q;
+    if (q < per && i < nt) row[i] = run;
+    run += v[q];
+  }
+  if (lane == 31) totals[r] = x;
+}
+
+template <typename Key>
 struct ScatterSmem {
-  uint64_t key[kTile];
+  Key key[kTile];
   uint32_t val[kTile];
   uint32_t wcnt[kWarps][kBins];  // per-warp digit counts, then their exclusive prefix
   uint32_t toff[kBins];          // the tile's digit runs: start in the reordered tile
@@ -117,38 +184,42 @@ struct ScatterSmem {
   uint32_t part[kWarps];
 };
 
+template <typename Key>
 __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    const Key* __restrict__ kin, const uint32_t* __restrict__ vin, Key* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, const uint32_t* __restrict__ n_dev, int shift, int width,
-    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals, int nt) {
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals, Segs G) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smraw);
+  ScatterSmem<Key>& S = *reinterpret_cast<ScatterSmem<Key>*>(smraw);
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   if (n_dev && *n_dev < n) n = *n_dev;
-  const size_t base = static_cast<size_t>(blockIdx.x) * kTile;
+  const TileSpan ts = tile_span(G, n);
+  const size_t base = ts.lo;
   const uint32_t mask = (1u << width) - 1;
   // warp w takes items [base + 256 w, base + 256 (w + 1)), 32 per round;
   // every load in flight before the first rank
-  uint64_t k[kItems];
+  Key k[kItems];
   uint32_t v[kItems], rd[kItems];  // rank in the warp's run << 10 | digit (kBins = none)
   unsigned peers[kItems];
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const size_t i = base + static_cast<size_t>(wid) * (32 * kItems) + r * 32 + lane;
-    k[r] = i < n ? kin[i] : 0;
-    v[r] = i < n ? vin[i] : 0;
+    k[r] = i < ts.hi ? kin[i] : 0;
+    v[r] = i < ts.hi ? (vin ? vin[i] : static_cast<uint32_t>(i)) : 0;
   }
   for (int e = t; e < kWarps * kBins; e += kThreads) (&S.wcnt[0][0])[e] = 0;
   {
-    // where each digit's run of this tile starts in the output: the digit's
-    // base (exclusive sum of the digit totals) plus the tile's offset in it
-    uint32_t tv[kBinsPerThread], ts = 0;
+    // where each digit's run of this tile starts in the output: the
+    // segment's start, the digit's base in it (exclusive sum of the
+    // segment's digit totals) and the tile's offset in the digit
+    const uint32_t* segtot = totals + static_cast<size_t>(ts.seg) * kBins;
+    uint32_t tv[kBinsPerThread], tsum = 0;
 #pragma unroll
     for (int q = 0; q < kBinsPerThread; ++q) {
-      tv[q] = totals[t * kBinsPerThread + q];
-      ts += tv[q];
+      tv[q] = segtot[t * kBinsPerThread + q];
+      tsum += tv[q];
     }
-    uint32_t x = ts;
+    uint32_t x = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -156,19 +227,20 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     }
     if (lane == 31) S.part[wid] = x;
     __syncthreads();
-    uint32_t b = x - ts;
+    uint32_t b = x - tsum + static_cast<uint32_t>(static_cast<size_t>(ts.seg) * G.len);
     for (int w = 0; w < wid; ++w) b += S.part[w];
+    const uint32_t* tofs = offsets + static_cast<size_t>(ts.seg) * kBins * G.tps + ts.tt;
 #pragma unroll
     for (int q = 0; q < kBinsPerThread; ++q) {
       const int d = t * kBinsPerThread + q;
-      S.gpos[d] = offsets[static_cast<size_t>(d) * nt + blockIdx.x] + b;
+      S.gpos[d] = tofs[static_cast<size_t>(d) * G.tps] + b;
       b += tv[q];
     }
   }
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const size_t i = base + static_cast<size_t>(wid) * (32 * kItems) + r * 32 + lane;
-    const int d = i < n ? static_cast<int>((k[r] >> shift) & mask) : kBins;
+    const int d = i < ts.hi ? static_cast<int>((k[r] >> shift) & mask) : kBins;
     rd[r] = static_cast<uint32_t>(d);
     peers[r] = __match_any_sync(0xffffffffu, d);
   }
@@ -239,10 +311,10 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     }
   __syncthreads();
   // each digit's run to its place
-  const int nin = base < n ? static_cast<int>(min(static_cast<size_t>(kTile), n - base)) : 0;
+  const int nin = ts.hi > ts.lo ? static_cast<int>(ts.hi - ts.lo) : 0;
 #pragma unroll 4
   for (int i = t; i < nin; i += kThreads) {
-    const uint64_t key = S.key[i];
+    const Key key = S.key[i];
     const int d = static_cast<int>((key >> shift) & mask);
     const uint32_t p = S.gpos[d] + static_cast<uint32_t>(i) - S.toff[d];
     kout[p] = key;
@@ -250,45 +322,111 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
   }
 }
 
+
+size_t tmp_words(const Segs& G) {
+  return static_cast<size_t>(G.nseg) * kBins * (1 + static_cast<size_t>(G.tps));
+}
+
+// The passes: pass 0 reads (k0, v0) (v0 null: values = indices), pass p
+// writes buffer p % 2.  Returns the buffer holding the result, -1 if no
+// pass ran.  tmp: the digit totals [nseg][512], then the tile counts
+// [nseg][512][tps].
+template <typename Key>
+int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t* const (&vb)[2],
+               size_t n, const Segs& G, int bits, uint32_t* tmp, cudaStream_t s,
+               const uint32_t* n_dev) {
+  if (n == 0 || bits <= 0) return -1;
+  const Plan P = plan_of(bits);
+  const int nt = G.nseg * G.tps;
+  const int rows = G.nseg * kBins;
+  uint32_t* totals = tmp;
+  uint32_t* hist = tmp + rows;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(sort_scatter_kernel<Key>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(ScatterSmem<Key>)));
+    configured = true;
+  }
+  const Key* kin = k0;
+  const uint32_t* vin = v0;
+  int out = 0;
+  for (int p = 0; p < P.passes; ++p) {
+    out = p & 1;
+    const int shift = p * P.width;
+    sort_count_kernel<Key><<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, hist, G);
+    if (G.tps <= kWarpRowMax)
+      sort_offsets_warp_kernel<<<(rows + kWarps - 1) / kWarps, kThreads, 0, s>>>(hist, totals,
+                                                                                G.tps, rows);
+    else
+      sort_offsets_kernel<<<rows, kThreads, 0, s>>>(hist, totals, G.tps);
+    sort_scatter_kernel<Key><<<nt, kThreads, sizeof(ScatterSmem<Key>), s>>>(
+        kin, vin, kb[out], vb[out], n, n_dev, shift, P.width, hist, totals, G);
+    note_launches(3);
+    kin = kb[out];
+    vin = vb[out];
+  }
+  return out;
+}
+
+Segs whole(size_t n) {
+  Segs G;
+  G.len = n < 1 ? 1 : n;
+  G.nseg = 1;
+  G.tps = static_cast<int>(tiles_of(G.len));
+  return G;
+}
+
+Segs segments(size_t len, int nseg) {
+  Segs G;
+  G.len = len < 1 ? 1 : len;
+  G.nseg = nseg < 1 ? 1 : nseg;
+  G.tps = static_cast<int>(tiles_of(G.len));
+  return G;
+}
+
+template <typename Key>
+void sort_pairs(Key* keys, uint32_t* vals, Key* keys_alt, uint32_t* vals_alt, size_t n, int bits,
+                uint32_t* tmp, bool* result_in_alt, cudaStream_t s, const uint32_t* n_dev) {
+  *result_in_alt = false;
+  if (n <= 1) return;
+  Key* const kb[2] = {keys_alt, keys};
+  uint32_t* const vb[2] = {vals_alt, vals};
+  const int out = run_passes<Key>(keys, vals, kb, vb, n, whole(n), bits, tmp, s, n_dev);
+  *result_in_alt = out == 0;
+}
+
 }  // namespace
 
-// totals [8][512], then the tile counts [512][tiles] of one pass
-size_t radix_tmp_words(size_t n) {
-  return static_cast<size_t>(kMaxPasses) * kBins +
-         static_cast<size_t>(kBins) * tiles_of(n < 1 ? 1 : n);
-}
+size_t radix_tmp_words(size_t n) { return tmp_words(whole(n)); }
+
+size_t radix_segments_tmp_words(size_t len, int nseg) { return tmp_words(segments(len, nseg)); }
 
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev, unsigned* err) {
   (void)err;  // no kernel of this sort waits on another
-  *result_in_alt = false;
-  if (n <= 1 || bits <= 0) return;
-  const Plan P = plan_of(bits);
-  const int nt = static_cast<int>(tiles_of(n));
-  uint32_t* totals = tmp;
-  uint32_t* hist = tmp + kMaxPasses * kBins;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(sort_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(sizeof(ScatterSmem)));
-    configured = true;
-  }
-  uint64_t *kin = keys, *kout = keys_alt;
-  uint32_t *vin = vals, *vout = vals_alt;
-  bool alt = false;
-  for (int p = 0; p < P.passes; ++p) {
-    const int shift = p * P.width;
-    sort_count_kernel<<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, hist, nt);
-    sort_offsets_kernel<<<kBins, kThreads, 0, s>>>(hist, totals + p * kBins, nt);
-    sort_scatter_kernel<<<nt, kThreads, sizeof(ScatterSmem), s>>>(
-        kin, vin, kout, vout, n, n_dev, shift, P.width, hist, totals + p * kBins, nt);
-    note_launches(3);
-    std::swap(kin, kout);
-    std::swap(vin, vout);
-    alt = !alt;
-  }
-  *result_in_alt = alt;
+  sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, tmp, result_in_alt, s, n_dev);
+}
+
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
+                      const uint32_t* n_dev, unsigned* err) {
+  (void)err;
+  if (bits > 32) bits = 32;
+  sort_pairs<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, tmp, result_in_alt, s, n_dev);
+}
+
+const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
+                                    uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
+                                    uint32_t* idx_b, uint32_t* tmp, cudaStream_t s) {
+  if (bits > 32) bits = 32;
+  if (bits < 1) bits = 1;  // at least one pass: the indices are written
+  const Segs G = segments(len, nseg);
+  uint32_t* const kb[2] = {keys_a, keys_b};
+  uint32_t* const vb[2] = {idx_a, idx_b};
+  const int out = run_passes<uint32_t>(keys, nullptr, kb, vb, len * static_cast<size_t>(nseg), G,
+                                       bits, tmp, s, nullptr);
+  return out < 0 ? nullptr : vb[out];
 }
 
 }  // namespace rxgs

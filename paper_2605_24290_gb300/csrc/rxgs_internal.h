@@ -59,6 +59,22 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
                  uint32_t* vals, cudaStream_t s, uint32_t cap = 0xffffffffu,
                  unsigned* err = nullptr);
 
+// The two-sort order of the instances (view, tile, depth, Gaussian index):
+// every view's Gaussians sorted by depth (radix_sort_segments over the
+// depth keys, one segment per view), then dst[i] = src[idx[i]] (the tile
+// counts in that order, then scanned) ...
+void launch_gather_words(const uint32_t* src, const uint32_t* idx, size_t n, uint32_t* dst,
+                         cudaStream_t s);
+// ... the instances of the ordered pairs (ord: view-major pair indices,
+// offsets: the scan of their counts) with (view << tile_bits | tile) keys
+// and Gaussian-index values, then stably sorted by those keys.
+void launch_emit_sorted(const GridConst& g, const float4* rec, const uint32_t* ord,
+                        const uint32_t* offsets, size_t MK, int K, int tile_bits, uint32_t* keys,
+                        uint32_t* vals, cudaStream_t s);
+// (view | tile) keys and values -> (view | tile | depth) keys (export only).
+void launch_expand_keys(const uint32_t* vt, const uint32_t* vals, size_t n, const uint32_t* depth,
+                        int K, int tile_bits, uint64_t* out, cudaStream_t s);
+
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
 // Returns, through *result_in_alt, whether the sorted data ended in the alt
 // buffers.  tmp must hold radix_tmp_words(n) uint32.
@@ -68,6 +84,18 @@ size_t radix_tmp_words(size_t n);
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
+                      const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
+// Each of nseg segments of len consecutive keys (read only) sorted stably
+// on its own by the low `bits` bits; returns the sorted item indices (of
+// the whole array) in idx_a or idx_b; keys_a / keys_b are scratch, all
+// four of len * nseg words.  tmp must hold radix_segments_tmp_words(len,
+// nseg) uint32.  Null if nothing was sorted (len * nseg == 0).
+size_t radix_segments_tmp_words(size_t len, int nseg);
+const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
+                                    uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
+                                    uint32_t* idx_b, uint32_t* tmp, cudaStream_t s);
 
 // dst[i] = src[i] for n 32-bit words, copied by a kernel (device memory or
 // mapped pinned host memory on either side): for small transfers that must
@@ -76,6 +104,9 @@ void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_
 
 // ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
 void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
+                        int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
+// ... from (view | tile) keys
+void launch_tile_ranges(const uint32_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
                         int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
 
 // ------------------------------------------------------------- radiance (a4)
