@@ -448,42 +448,50 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   if (e == cudaSuccess) e = dalloc(&ord_a, MK, st);
   if (e == cudaSuccess) e = dalloc(&ord_b, MK, st);
   if (e == cudaSuccess) e = dalloc(&dsort_tmp, radix_segments_tmp_words(s->K, M), st);
-  if (e == cudaSuccess) e = dalloc(&scounts, MK, st);
+  if (e == cudaSuccess) e = dalloc(&scounts, std::max<size_t>(MK, 4ull * M), st);  // also the stats
   if (e != cudaSuccess) {
     cleanup();
     return fail(ctx, RXGS_E_OOM, "prepare: %s", cudaGetErrorString(e));
   }
   {
+    // stats: the instance count and the visible pairs' depth-key range
     Stage sg(ctx, "preprocess", st);
-    launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st);
+    cudaMemsetAsync(scounts, 0, 4 * sizeof(uint32_t) * M, st);
+    launch_preprocess(g, s->geom, s->K, v->tx, M, v->rec, v->depth, v->counts, st, nullptr,
+                      scounts);
   }
+  // read back by a kernel into the pinned slot (a copy-engine transfer
+  // would queue behind the caller's large copies)
+  launch_combine_stats(scounts, M, ctx->d_pinned, st);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, RXGS_E_CUDA, "prepare: %s", cudaGetErrorString(e));
+  }
+  const uint64_t I64 = static_cast<uint64_t>(ctx->h_pinned[0]) |
+                       (static_cast<uint64_t>(ctx->h_pinned[1]) << 32);
+  if (I64 > 0x7fffffffu) {
+    cleanup();
+    return fail(ctx, RXGS_E_INVALID, "instance count overflow");
+  }
+  const uint32_t I = static_cast<uint32_t>(I64);
+  // visible depth keys lie in [dmin, dmax]: the sort needs the bits of
+  // dmax - dmin only (culled pairs emit nothing; their order is immaterial)
+  const uint32_t dmin = I ? ~ctx->h_pinned[2] : 0u, dmax = I ? ctx->h_pinned[3] : 0u;
+  const int dbits = bits_for(static_cast<uint64_t>(dmax - dmin) + 1);
   {
     // every view's Gaussians by depth (ties: ascending Gaussian index), and
     // their tile counts in that order
     Stage sg(ctx, "depth_sort", st);
-    ord = radix_sort_segments(v->depth, s->K, M, 31, dkeys, dkeys_alt, ord_a, ord_b, dsort_tmp,
-                              st);
-    launch_gather_words(v->counts, ord, MK, scounts, st);
+    ord = radix_sort_segments(v->depth, s->K, M, dbits, dmin, dkeys, dkeys_alt, ord_a, ord_b,
+                              dsort_tmp, v->counts, scounts, st);
   }
   {
     Stage sg(ctx, "scan", st);
     launch_exclusive_scan(scounts, v->offsets, MK, scan_tmp, st);
   }
-  // the instance count, written into the pinned readback slot by a kernel
-  // (a copy-engine transfer would queue behind the caller's large copies)
-  launch_copy_words(v->offsets + MK, ctx->d_pinned, 1, st);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(scan_tmp, st);
-  if (e != cudaSuccess) {
-    cleanup();
-    return fail(ctx, RXGS_E_CUDA, "prepare: %s", cudaGetErrorString(e));
-  }
-  const uint32_t I = ctx->h_pinned[0];
-  if (I > 0x7fffffffu) {
-    cleanup();
-    return fail(ctx, RXGS_E_INVALID, "instance count overflow");
-  }
   v->n_inst = I;
   uint32_t* keys_alt = nullptr;
   uint32_t* vals_alt = nullptr;
@@ -492,7 +500,10 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   if (e == cudaSuccess) e = dalloc(&v->vals, I, st);
   if (e == cudaSuccess) e = dalloc(&keys_alt, I, st);
   if (e == cudaSuccess) e = dalloc(&vals_alt, I, st);
-  if (e == cudaSuccess) e = dalloc(&sort_tmp, radix_tmp_words(I), st);
+  // one pass by tile within each view's run when the tile fits one digit
+  const bool one_pass = v->tile_bits <= 9;
+  if (e == cudaSuccess)
+    e = dalloc(&sort_tmp, one_pass ? radix_views_tmp_words(I, M) : radix_tmp_words(I), st);
   if (e != cudaSuccess) {
     dfree(keys_alt, st); dfree(vals_alt, st); dfree(sort_tmp, st);
     cleanup();
@@ -504,11 +515,21 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   }
   free_order();
   bool in_alt = false;
-  {
-    // stable: each (view, tile) keeps the depth order of the emission
+  if (one_pass) {
+    // stable: each (view, tile) keeps the depth order of the emission; the
+    // pass writes the ranges as well
     Stage sg(ctx, "sort", st);
-    radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, v->tile_bits + v->view_bits,
-                     sort_tmp, &in_alt, st, nullptr, ctx->d_err);
+    radix_sort_views(v->keys, v->vals, keys_alt, vals_alt, I, v->offsets, s->K, M, v->tile_bits,
+                     v->ranges, g.T, sort_tmp, st);
+    in_alt = true;
+  } else {
+    {
+      Stage sg(ctx, "sort", st);
+      radix_sort_pairs(v->keys, v->vals, keys_alt, vals_alt, I, v->tile_bits + v->view_bits,
+                       sort_tmp, &in_alt, st, nullptr, ctx->d_err);
+    }
+    Stage sg(ctx, "ranges", st);
+    launch_tile_ranges(in_alt ? keys_alt : v->keys, I, v->tile_bits, g.T, v->ranges, M, st);
   }
   if (in_alt) {
     std::swap(v->keys, keys_alt);
@@ -517,10 +538,6 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   dfree(keys_alt, st);
   dfree(vals_alt, st);
   dfree(sort_tmp, st);
-  {
-    Stage sg(ctx, "ranges", st);
-    launch_tile_ranges(v->keys, I, v->tile_bits, g.T, v->ranges, M, st);
-  }
   rxgs_status rs = check_last(ctx, "prepare kernels");
   if (rs != RXGS_OK) {
     cleanup();

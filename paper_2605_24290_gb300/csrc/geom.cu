@@ -184,13 +184,15 @@ __device__ __forceinline__ TileCols tile_cols(const GridConst& g, int j_lo, int 
   return t;
 }
 
-__global__ void preprocess_kernel(GridConst g, const float4* __restrict__ geom, int K,
-                                  const float* __restrict__ tx, float4* __restrict__ rec,
-                                  uint32_t* __restrict__ depth, uint32_t* __restrict__ count,
-                                  const int* __restrict__ nviews_dev) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
-  if (k >= K) return;
+// One (view, Gaussian) pair of the projection; returns its tile count and
+// its depth key.
+__device__ __forceinline__ uint32_t preprocess_one(GridConst g, const float4* __restrict__ geom,
+                                                   int K, const float* __restrict__ tx,
+                                                   float4* __restrict__ rec,
+                                                   uint32_t* __restrict__ depth,
+                                                   uint32_t* __restrict__ count,
+                                                   const int* __restrict__ nviews_dev, int k,
+                                                   int v, uint32_t& dkey) {
   const float4 g0 = geom[3 * k + 0], g1 = geom[3 * k + 1], g2 = geom[3 * k + 2];
   Footprint f;
   if (nviews_dev && v >= *nviews_dev) {
@@ -213,16 +215,99 @@ __global__ void preprocess_kernel(GridConst g, const float4* __restrict__ geom, 
     rec[2 * idx + 0] = make_float4(0.f, 0.f, 0.f, 0.f);
     rec[2 * idx + 1] = make_float4(0.f, 0.f, __int_as_float(1), __int_as_float(0));  // empty rows
   }
-  depth[idx] = __float_as_uint(f.rho);
+  dkey = __float_as_uint(f.rho);
+  depth[idx] = dkey;
   count[idx] = n;
+  return n;
+}
+
+// stats (optional, [M][4] zeroed before the launch), per view: [0..1] the
+// total tile count (uint64), [2] the largest ~depth key and [3] the largest
+// depth key of the visible pairs (their smallest key is ~stats[2]); one
+// atomic per block and quantity, into the view's own slot.
+__global__ void preprocess_kernel(GridConst g, const float4* __restrict__ geom, int K,
+                                  const float* __restrict__ tx, float4* __restrict__ rec,
+                                  uint32_t* __restrict__ depth, uint32_t* __restrict__ count,
+                                  const int* __restrict__ nviews_dev, uint32_t* __restrict__ stats) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  uint32_t n = 0, dkey = 0;
+  if (k < K) {
+    n = preprocess_one(g, geom, K, tx, rec, depth, count, nviews_dev, k, v, dkey);
+  }
+  if (stats) {
+    // all lanes reach this point: warp reductions, then the block's
+    __shared__ uint32_t red[3][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t tot = __reduce_add_sync(0xffffffffu, n);
+    uint32_t nmin = __reduce_max_sync(0xffffffffu, n ? ~dkey : 0u);
+    uint32_t dmax = __reduce_max_sync(0xffffffffu, n ? dkey : 0u);
+    if (lane == 0) {
+      red[0][w] = tot;
+      red[1][w] = nmin;
+      red[2][w] = dmax;
+    }
+    __syncthreads();
+    if (w == 0) {
+      const bool in = lane < static_cast<int>(blockDim.x >> 5);
+      tot = __reduce_add_sync(0xffffffffu, in ? red[0][lane] : 0u);
+      nmin = __reduce_max_sync(0xffffffffu, in ? red[1][lane] : 0u);
+      dmax = __reduce_max_sync(0xffffffffu, in ? red[2][lane] : 0u);
+      if (lane == 0 && tot) {
+        uint32_t* st = stats + 4 * static_cast<size_t>(v);
+        atomicAdd(reinterpret_cast<unsigned long long*>(st), static_cast<unsigned long long>(tot));
+        atomicMax(&st[2], nmin);
+        atomicMax(&st[3], dmax);
+      }
+    }
+  }
+}
+
+// The per-view stats [M][4] of preprocess_kernel combined into dst[4] (one
+// block; dst may be mapped pinned host memory).
+__global__ void combine_stats_kernel(const uint32_t* __restrict__ stats, int M,
+                                     uint32_t* __restrict__ dst) {
+  __shared__ unsigned long long s_tot[256];
+  __shared__ uint32_t s_min[256], s_max[256];
+  unsigned long long tot = 0;
+  uint32_t nmin = 0, dmax = 0;
+  for (int v = threadIdx.x; v < M; v += blockDim.x) {
+    const uint32_t* st = stats + 4 * static_cast<size_t>(v);
+    tot += static_cast<unsigned long long>(st[0]) | (static_cast<unsigned long long>(st[1]) << 32);
+    nmin = max(nmin, st[2]);
+    dmax = max(dmax, st[3]);
+  }
+  s_tot[threadIdx.x] = tot;
+  s_min[threadIdx.x] = nmin;
+  s_max[threadIdx.x] = dmax;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (static_cast<int>(threadIdx.x) < h) {
+      s_tot[threadIdx.x] += s_tot[threadIdx.x + h];
+      s_min[threadIdx.x] = max(s_min[threadIdx.x], s_min[threadIdx.x + h]);
+      s_max[threadIdx.x] = max(s_max[threadIdx.x], s_max[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    dst[0] = static_cast<uint32_t>(s_tot[0]);
+    dst[1] = static_cast<uint32_t>(s_tot[0] >> 32);
+    dst[2] = s_min[0];
+    dst[3] = s_max[0];
+  }
+}
+
+void launch_combine_stats(const uint32_t* stats, int M, uint32_t* dst, cudaStream_t s) {
+  combine_stats_kernel<<<1, 256, 0, s>>>(stats, M, dst);
+  note_launches(1);
 }
 
 void launch_preprocess(const GridConst& g, const float4* geom, int K, const float* tx, int M,
                        float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s,
-                       const int* nviews_dev) {
+                       const int* nviews_dev, uint32_t* stats) {
   if (K <= 0 || M <= 0) return;
   dim3 grid((K + 255) / 256, M);
-  preprocess_kernel<<<grid, 256, 0, s>>>(g, geom, K, tx, rec, depth, count, nviews_dev);
+  preprocess_kernel<<<grid, 256, 0, s>>>(g, geom, K, tx, rec, depth, count, nviews_dev, stats);
   note_launches(1);
 }
 

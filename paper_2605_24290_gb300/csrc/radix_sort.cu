@@ -74,17 +74,50 @@ __device__ __forceinline__ TileSpan tile_span(const Segs& S, size_t n) {
   return t;
 }
 
+// Variable segments (the instances of each view, one pass by tile):
+// segment m holds items [start[m], start[m + 1]) in tiles [tile0[m],
+// tile0[m + 1]); tile b belongs to segment tile_seg[b] (nseg: none, no
+// items).  Tile counts are laid out [digit][nt]; each segment's first tile
+// writes the segment's per-digit [start, end) into ranges[m][T].
+struct VarSegs {
+  const uint32_t* start;     // [nseg + 1]
+  const uint32_t* tile0;     // [nseg + 1]
+  const uint32_t* tile_seg;  // [nt]
+  int nseg, nt, T;
+  uint2* ranges;
+};
+
+__device__ __forceinline__ TileSpan var_span(const VarSegs& V) {
+  TileSpan t;
+  const uint32_t m = V.tile_seg[blockIdx.x];
+  t.seg = static_cast<int>(m);
+  t.tt = 0;
+  t.lo = t.hi = 0;
+  if (m < static_cast<uint32_t>(V.nseg)) {
+    t.tt = static_cast<int>(blockIdx.x - V.tile0[m]);
+    t.lo = V.start[m] + static_cast<size_t>(t.tt) * kTile;
+    t.hi = min(t.lo + kTile, static_cast<size_t>(V.start[m + 1]));
+  }
+  return t;
+}
+
 // hist[(seg * kBins + d) * tps + tt] = count of digit d in tile tt of seg
-template <typename Key>
+// (kVar: hist[d * nt + tile])
+template <typename Key, bool kVar>
 __global__ void __launch_bounds__(kThreads) sort_count_kernel(const Key* __restrict__ keys,
                                                               size_t n,
                                                               const uint32_t* __restrict__ n_dev,
-                                                              int shift, int width,
-                                                              uint32_t* __restrict__ hist, Segs S) {
+                                                              int shift, int width, Key bias,
+                                                              uint32_t* __restrict__ hist, Segs S,
+                                                              VarSegs V) {
   if (n_dev && *n_dev < n) n = *n_dev;
   __shared__ uint32_t h[kBins];
   for (int d = threadIdx.x; d < kBins; d += kThreads) h[d] = 0;
-  const TileSpan ts = tile_span(S, n);
+  TileSpan ts;
+  if constexpr (kVar)
+    ts = var_span(V);
+  else
+    ts = tile_span(S, n);
   Key k[kItems];
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
@@ -96,11 +129,16 @@ __global__ void __launch_bounds__(kThreads) sort_count_kernel(const Key* __restr
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const size_t i = ts.lo + static_cast<size_t>(r) * kThreads + threadIdx.x;
-    if (i < ts.hi) atomicAdd(&h[(k[r] >> shift) & mask], 1u);
+    if (i < ts.hi) atomicAdd(&h[((k[r] - bias) >> shift) & mask], 1u);
   }
   __syncthreads();
-  uint32_t* row = hist + static_cast<size_t>(ts.seg) * kBins * S.tps + ts.tt;
-  for (int d = threadIdx.x; d < kBins; d += kThreads) row[static_cast<size_t>(d) * S.tps] = h[d];
+  if constexpr (kVar) {
+    for (int d = threadIdx.x; d < kBins; d += kThreads)
+      hist[static_cast<size_t>(d) * V.nt + blockIdx.x] = h[d];
+  } else {
+    uint32_t* row = hist + static_cast<size_t>(ts.seg) * kBins * S.tps + ts.tt;
+    for (int d = threadIdx.x; d < kBins; d += kThreads) row[static_cast<size_t>(d) * S.tps] = h[d];
+  }
 }
 
 // Row r = (seg, digit) of hist (tps entries): each entry <- the exclusive
@@ -178,22 +216,30 @@ template <typename Key>
 struct ScatterSmem {
   Key key[kTile];
   uint32_t val[kTile];
-  uint32_t wcnt[kWarps][kBins];  // per-warp digit counts, then their exclusive prefix
-  uint32_t toff[kBins];          // the tile's digit runs: start in the reordered tile
-  uint32_t gpos[kBins];          // ... and in the output
+  uint32_t wcnt[kWarps][kBins];  // per-warp digit counts, then where each warp's
+                                 // items of the digit start in the reordered tile
+  uint32_t gpos[kBins];          // the digit run's output position, then that
+                                 // minus the run's start in the reordered tile
   uint32_t part[kWarps];
 };
 
-template <typename Key>
+template <typename Key, bool kVar>
 __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     const Key* __restrict__ kin, const uint32_t* __restrict__ vin, Key* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, const uint32_t* __restrict__ n_dev, int shift, int width,
-    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals, Segs G) {
+    Key bias, const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals, Segs G,
+    const uint32_t* __restrict__ gsrc, uint32_t* __restrict__ gdst, VarSegs V) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ScatterSmem<Key>& S = *reinterpret_cast<ScatterSmem<Key>*>(smraw);
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   if (n_dev && *n_dev < n) n = *n_dev;
-  const TileSpan ts = tile_span(G, n);
+  TileSpan ts;
+  if constexpr (kVar) {
+    ts = var_span(V);
+    if (ts.seg >= V.nseg) return;  // a tile past the last segment: no items
+  } else {
+    ts = tile_span(G, n);
+  }
   const size_t base = ts.lo;
   const uint32_t mask = (1u << width) - 1;
   // warp w takes items [base + 256 w, base + 256 (w + 1)), 32 per round;
@@ -212,12 +258,34 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     // where each digit's run of this tile starts in the output: the
     // segment's start, the digit's base in it (exclusive sum of the
     // segment's digit totals) and the tile's offset in the digit
-    const uint32_t* segtot = totals + static_cast<size_t>(ts.seg) * kBins;
-    uint32_t tv[kBinsPerThread], tsum = 0;
+    uint32_t tv[kBinsPerThread], tofs[kBinsPerThread], tsum = 0, seg0;
+    if constexpr (kVar) {
+      // E(d, x): the exclusive sum of digit d's counts over tiles < x
+      auto E = [&](int d, uint32_t x) {
+        return x < static_cast<uint32_t>(V.nt) ? offsets[static_cast<size_t>(d) * V.nt + x]
+                                               : totals[d];
+      };
+      const uint32_t p0 = V.tile0[ts.seg], p1 = V.tile0[ts.seg + 1];
 #pragma unroll
-    for (int q = 0; q < kBinsPerThread; ++q) {
-      tv[q] = segtot[t * kBinsPerThread + q];
-      tsum += tv[q];
+      for (int q = 0; q < kBinsPerThread; ++q) {
+        const int d = t * kBinsPerThread + q;
+        const uint32_t a = E(d, p0);
+        tv[q] = E(d, p1) - a;
+        tofs[q] = E(d, blockIdx.x) - a;
+        tsum += tv[q];
+      }
+      seg0 = V.start[ts.seg];
+    } else {
+      const uint32_t* segtot = totals + static_cast<size_t>(ts.seg) * kBins;
+      const uint32_t* tofsp = offsets + static_cast<size_t>(ts.seg) * kBins * G.tps + ts.tt;
+#pragma unroll
+      for (int q = 0; q < kBinsPerThread; ++q) {
+        const int d = t * kBinsPerThread + q;
+        tv[q] = segtot[d];
+        tofs[q] = tofsp[static_cast<size_t>(d) * G.tps];
+        tsum += tv[q];
+      }
+      seg0 = static_cast<uint32_t>(static_cast<size_t>(ts.seg) * G.len);
     }
     uint32_t x = tsum;
 #pragma unroll
@@ -227,20 +295,24 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     }
     if (lane == 31) S.part[wid] = x;
     __syncthreads();
-    uint32_t b = x - tsum + static_cast<uint32_t>(static_cast<size_t>(ts.seg) * G.len);
+    uint32_t b = x - tsum + seg0;
     for (int w = 0; w < wid; ++w) b += S.part[w];
-    const uint32_t* tofs = offsets + static_cast<size_t>(ts.seg) * kBins * G.tps + ts.tt;
 #pragma unroll
     for (int q = 0; q < kBinsPerThread; ++q) {
       const int d = t * kBinsPerThread + q;
-      S.gpos[d] = tofs[static_cast<size_t>(d) * G.tps] + b;
+      S.gpos[d] = tofs[q] + b;
+      if constexpr (kVar) {
+        // the segment's first tile: each digit's [start, end) in the output
+        if (ts.tt == 0 && d < V.T && tv[q] > 0)
+          V.ranges[static_cast<size_t>(ts.seg) * V.T + d] = make_uint2(b, b + tv[q]);
+      }
       b += tv[q];
     }
   }
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const size_t i = base + static_cast<size_t>(wid) * (32 * kItems) + r * 32 + lane;
-    const int d = i < ts.hi ? static_cast<int>((k[r] >> shift) & mask) : kBins;
+    const int d = i < ts.hi ? static_cast<int>(((k[r] - bias) >> shift) & mask) : kBins;
     rd[r] = static_cast<uint32_t>(d);
     peers[r] = __match_any_sync(0xffffffffu, d);
   }
@@ -287,10 +359,13 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
     __syncthreads();
     uint32_t before = 0;
     for (int w = 0; w < wid; ++w) before += S.part[w];
-    uint32_t off = before + x - s;
+    uint32_t off = before + x - s;  // the run's start in the reordered tile
 #pragma unroll
     for (int q = 0; q < kBinsPerThread; ++q) {
-      S.toff[t * kBinsPerThread + q] = off;
+      const int d = t * kBinsPerThread + q;
+      S.gpos[d] -= off;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) S.wcnt[w][d] += off;
       off += cnt[q];
     }
   }
@@ -301,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int d = static_cast<int>(rd[r] & 1023u);
-    pos[r] = d < kBins ? S.toff[d] + S.wcnt[wid][d] + (rd[r] >> 10) : kTile;
+    pos[r] = d < kBins ? S.wcnt[wid][d] + (rd[r] >> 10) : kTile;
   }
 #pragma unroll
   for (int r = 0; r < kItems; ++r)
@@ -315,13 +390,75 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
 #pragma unroll 4
   for (int i = t; i < nin; i += kThreads) {
     const Key key = S.key[i];
-    const int d = static_cast<int>((key >> shift) & mask);
-    const uint32_t p = S.gpos[d] + static_cast<uint32_t>(i) - S.toff[d];
-    kout[p] = key;
-    vout[p] = S.val[i];
+    const int d = static_cast<int>(((key - bias) >> shift) & mask);
+    const uint32_t p = S.gpos[d] + static_cast<uint32_t>(i);
+    const uint32_t val = S.val[i];
+    if (kout) kout[p] = key;  // null: the keys are not needed after this pass
+    vout[p] = val;
+    if (gdst) gdst[p] = gsrc[val];
   }
 }
 
+
+// The view segments of the emitted instances: start[m] = offsets[m K]
+// (the emission is view-major), tile0 = exclusive scan of the segments'
+// tile counts, tile_seg[b] for b < nt.  One block.
+__global__ void __launch_bounds__(1024) var_segs_kernel(const uint32_t* __restrict__ offsets, int K,
+                                                       int M, int nt, uint32_t* __restrict__ start,
+                                                       uint32_t* __restrict__ tile0,
+                                                       uint32_t* __restrict__ tile_seg) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 <= M; c0 += 1024) {
+    const int m = c0 + t;
+    uint32_t cnt = 0;
+    if (m <= M) {
+      const uint32_t s0 = offsets[static_cast<size_t>(m) * K];
+      start[m] = s0;
+      if (m < M) {
+        const uint32_t s1 = offsets[static_cast<size_t>(m + 1) * K];
+        cnt = (s1 - s0 + kTile - 1) / kTile;
+      }
+    }
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    uint32_t before = carry;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    if (m <= M) tile0[m] = before + x - cnt;
+    __syncthreads();
+    if (t == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < 32; ++w) tot += wsum[w];
+      carry += tot;
+    }
+    __syncthreads();
+  }
+  // tile b -> the last segment m with tile0[m] <= b (tiles of empty
+  // segments are skipped by the search); M past the end
+  const uint32_t used = __ldcg(&tile0[M]);  // written by this block (L2)
+  for (int b = t; b < nt; b += 1024) {
+    uint32_t m = static_cast<uint32_t>(M);
+    if (static_cast<uint32_t>(b) < used) {
+      int lo = 0, hi = M - 1;  // tile0[lo] <= b < tile0[hi + 1]
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldcg(&tile0[mid]) <= static_cast<uint32_t>(b)) lo = mid;
+        else hi = mid - 1;
+      }
+      m = static_cast<uint32_t>(lo);
+    }
+    tile_seg[b] = m;
+  }
+}
 
 size_t tmp_words(const Segs& G) {
   return static_cast<size_t>(G.nseg) * kBins * (1 + static_cast<size_t>(G.tps));
@@ -334,7 +471,8 @@ size_t tmp_words(const Segs& G) {
 template <typename Key>
 int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t* const (&vb)[2],
                size_t n, const Segs& G, int bits, uint32_t* tmp, cudaStream_t s,
-               const uint32_t* n_dev) {
+               const uint32_t* n_dev, Key bias = 0, const uint32_t* gsrc = nullptr,
+               uint32_t* gdst = nullptr) {
   if (n == 0 || bits <= 0) return -1;
   const Plan P = plan_of(bits);
   const int nt = G.nseg * G.tps;
@@ -343,8 +481,11 @@ int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t*
   uint32_t* hist = tmp + rows;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(sort_scatter_kernel<Key>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(sort_scatter_kernel<Key, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(sizeof(ScatterSmem<Key>)));
+    cudaFuncSetAttribute(sort_scatter_kernel<Key, false>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     configured = true;
   }
   const Key* kin = k0;
@@ -353,14 +494,17 @@ int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t*
   for (int p = 0; p < P.passes; ++p) {
     out = p & 1;
     const int shift = p * P.width;
-    sort_count_kernel<Key><<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, hist, G);
+    sort_count_kernel<Key, false><<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, bias,
+                                                          hist, G, VarSegs{});
     if (G.tps <= kWarpRowMax)
       sort_offsets_warp_kernel<<<(rows + kWarps - 1) / kWarps, kThreads, 0, s>>>(hist, totals,
                                                                                 G.tps, rows);
     else
       sort_offsets_kernel<<<rows, kThreads, 0, s>>>(hist, totals, G.tps);
-    sort_scatter_kernel<Key><<<nt, kThreads, sizeof(ScatterSmem<Key>), s>>>(
-        kin, vin, kb[out], vb[out], n, n_dev, shift, P.width, hist, totals, G);
+    const bool last = p + 1 == P.passes;
+    sort_scatter_kernel<Key, false><<<nt, kThreads, sizeof(ScatterSmem<Key>), s>>>(
+        kin, vin, last && gdst ? nullptr : kb[out], vb[out], n, n_dev, shift, P.width, bias, hist,
+        totals, G, last ? gsrc : nullptr, last ? gdst : nullptr, VarSegs{});
     note_launches(3);
     kin = kb[out];
     vin = vb[out];
@@ -417,16 +561,68 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
 }
 
 const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
-                                    uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
-                                    uint32_t* idx_b, uint32_t* tmp, cudaStream_t s) {
+                                    uint32_t bias, uint32_t* keys_a, uint32_t* keys_b,
+                                    uint32_t* idx_a, uint32_t* idx_b, uint32_t* tmp,
+                                    const uint32_t* gather_src, uint32_t* gather_dst,
+                                    cudaStream_t s) {
   if (bits > 32) bits = 32;
   if (bits < 1) bits = 1;  // at least one pass: the indices are written
   const Segs G = segments(len, nseg);
   uint32_t* const kb[2] = {keys_a, keys_b};
   uint32_t* const vb[2] = {idx_a, idx_b};
+  const bool gather = gather_src && gather_dst;
   const int out = run_passes<uint32_t>(keys, nullptr, kb, vb, len * static_cast<size_t>(nseg), G,
-                                       bits, tmp, s, nullptr);
+                                       bits, tmp, s, nullptr, bias, gather ? gather_src : nullptr,
+                                       gather ? gather_dst : nullptr);
   return out < 0 ? nullptr : vb[out];
+}
+
+size_t radix_views_tmp_words(size_t n, int M) {
+  const size_t nt = tiles_of(n) + static_cast<size_t>(M);
+  return static_cast<size_t>(kBins) * (1 + nt) + 2 * (static_cast<size_t>(M) + 1) + nt;
+}
+
+void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
+                      uint32_t* vals_out, size_t n, const uint32_t* offsets, int K, int M,
+                      int tile_bits, uint2* ranges, int T, uint32_t* tmp, cudaStream_t s) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(M) * T, s);
+  if (n == 0 || M <= 0) return;
+  const int nt = static_cast<int>(tiles_of(n) + static_cast<size_t>(M));
+  uint32_t* totals = tmp;
+  uint32_t* hist = totals + kBins;
+  uint32_t* start = hist + static_cast<size_t>(kBins) * nt;
+  uint32_t* tile0 = start + (M + 1);
+  uint32_t* tile_seg = tile0 + (M + 1);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(sort_scatter_kernel<uint32_t, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(ScatterSmem<uint32_t>)));
+    cudaFuncSetAttribute(sort_scatter_kernel<uint32_t, true>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    configured = true;
+  }
+  VarSegs V;
+  V.start = start;
+  V.tile0 = tile0;
+  V.tile_seg = tile_seg;
+  V.nseg = M;
+  V.nt = nt;
+  V.T = T;
+  V.ranges = ranges;
+  var_segs_kernel<<<1, 1024, 0, s>>>(offsets, K, M, nt, start, tile0, tile_seg);
+  const Segs G = whole(n);
+  sort_count_kernel<uint32_t, true><<<nt, kThreads, 0, s>>>(keys, n, nullptr, 0, tile_bits, 0u,
+                                                            hist, G, V);
+  if (nt <= kWarpRowMax)
+    sort_offsets_warp_kernel<<<(kBins + kWarps - 1) / kWarps, kThreads, 0, s>>>(hist, totals, nt,
+                                                                               kBins);
+  else
+    sort_offsets_kernel<<<kBins, kThreads, 0, s>>>(hist, totals, nt);
+  sort_scatter_kernel<uint32_t, true><<<nt, kThreads, sizeof(ScatterSmem<uint32_t>), s>>>(
+      keys, vals, keys_out, vals_out, n, nullptr, 0, tile_bits, 0u, hist, totals, G, nullptr,
+      nullptr, V);
+  note_launches(4);
 }
 
 }  // namespace rxgs

@@ -41,9 +41,14 @@ void launch_set_opacity(const float* opacity, int K, float4* geom, cudaStream_t 
 // Projection of K Gaussians for M views.  rec[M][K][2] float4, depth[M][K]
 // (float bits of rho), count[M*K] tile counts (0 = culled).
 // nviews_dev (optional): number of view slots in use; later slots are culled.
+// stats (optional, [M][4] words zeroed before the call), per view: the
+// total tile count (uint64 in words 0-1), ~(smallest) and largest depth key
+// of the visible pairs (words 2 and 3); launch_combine_stats folds the
+// views into dst[4] (device or mapped pinned memory).
 void launch_preprocess(const GridConst& g, const float4* geom, int K, const float* tx, int M,
                        float4* rec, uint32_t* depth, uint32_t* count, cudaStream_t s,
-                       const int* nviews_dev = nullptr);
+                       const int* nviews_dev = nullptr, uint32_t* stats = nullptr);
+void launch_combine_stats(const uint32_t* stats, int M, uint32_t* dst, cudaStream_t s);
 
 // Exclusive scan of n uint32 values; out has n+1 entries (out[n] = total).
 // tmp must hold scan_tmp_words(n) uint32.
@@ -88,14 +93,28 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
 // Each of nseg segments of len consecutive keys (read only) sorted stably
-// on its own by the low `bits` bits; returns the sorted item indices (of
-// the whole array) in idx_a or idx_b; keys_a / keys_b are scratch, all
-// four of len * nseg words.  tmp must hold radix_segments_tmp_words(len,
-// nseg) uint32.  Null if nothing was sorted (len * nseg == 0).
+// on its own by the low `bits` bits of key - bias (uint32 arithmetic);
+// returns the sorted item indices (of the whole array) in idx_a or idx_b;
+// keys_a / keys_b are scratch, all four of len * nseg words.  gather_src
+// (optional): gather_dst[i] = gather_src[index i] is written as well.  tmp
+// must hold radix_segments_tmp_words(len, nseg) uint32.  Null if nothing
+// was sorted (len * nseg == 0).
 size_t radix_segments_tmp_words(size_t len, int nseg);
+// The instances of launch_emit_sorted (keys view << tile_bits | tile,
+// tile_bits <= 9) in one stable pass by tile within each view's contiguous
+// run (offsets: the emission scan, view m's run starts at offsets[m K]);
+// writes the sorted keys and values to keys_out / vals_out and ranges[M][T]
+// ([start, end) of each (view, tile); zero when empty).  tmp must hold
+// radix_views_tmp_words(n, M) uint32.
+size_t radix_views_tmp_words(size_t n, int M);
+void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
+                      uint32_t* vals_out, size_t n, const uint32_t* offsets, int K, int M,
+                      int tile_bits, uint2* ranges, int T, uint32_t* tmp, cudaStream_t s);
 const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
-                                    uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
-                                    uint32_t* idx_b, uint32_t* tmp, cudaStream_t s);
+                                    uint32_t bias, uint32_t* keys_a, uint32_t* keys_b,
+                                    uint32_t* idx_a, uint32_t* idx_b, uint32_t* tmp,
+                                    const uint32_t* gather_src, uint32_t* gather_dst,
+                                    cudaStream_t s);
 
 // dst[i] = src[i] for n 32-bit words, copied by a kernel (device memory or
 // mapped pinned host memory on either side): for small transfers that must
