@@ -190,6 +190,7 @@ rxgs_status rxgs_create(const rxgs_options* opts, int device, rxgs_ctx** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_pinned),
                                                      ctx->h_pinned, 0);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_stats, cudaEventDisableTiming);
   if (e == cudaSuccess) {
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -230,6 +231,7 @@ rxgs_status rxgs_destroy(rxgs_ctx* ctx) {
   for (BatchPlan* p : ctx->plans) destroy_plan(p);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_pinned);
+  if (ctx->ev_stats) cudaEventDestroy(ctx->ev_stats);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -461,10 +463,17 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
                       scounts);
   }
   // read back by a kernel into the pinned slot (a copy-engine transfer
-  // would queue behind the caller's large copies)
+  // would queue behind the caller's large copies); the depth sort's first
+  // pass (the low 9 bits, independent of the depth range) is queued behind
+  // it and runs while the host waits for the slot
   launch_combine_stats(scounts, M, ctx->d_pinned, st);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  e = cudaEventRecord(ctx->ev_stats, st);
+  {
+    Stage sg(ctx, "depth_sort", st);
+    radix_sort_segments_first(v->depth, s->K, M, dkeys, ord_a, dsort_tmp, st);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev_stats);
   if (e != cudaSuccess) {
     cleanup();
     return fail(ctx, RXGS_E_CUDA, "prepare: %s", cudaGetErrorString(e));
@@ -477,15 +486,17 @@ rxgs_status rxgs_prepare(rxgs_ctx* ctx, rxgs_scene_t scene, const float* tx, int
   }
   const uint32_t I = static_cast<uint32_t>(I64);
   // visible depth keys lie in [dmin, dmax]: the sort needs the bits of
-  // dmax - dmin only (culled pairs emit nothing; their order is immaterial)
+  // dmax - bias only, bias = dmin rounded down to a multiple of 512 (culled
+  // pairs emit nothing; their order is immaterial)
   const uint32_t dmin = I ? ~ctx->h_pinned[2] : 0u, dmax = I ? ctx->h_pinned[3] : 0u;
-  const int dbits = bits_for(static_cast<uint64_t>(dmax - dmin) + 1);
+  const uint32_t dbias = dmin & ~511u;
+  const int dbits = bits_for(static_cast<uint64_t>(dmax - dbias) + 1);
   {
     // every view's Gaussians by depth (ties: ascending Gaussian index), and
     // their tile counts in that order
     Stage sg(ctx, "depth_sort", st);
-    ord = radix_sort_segments(v->depth, s->K, M, dbits, dmin, dkeys, dkeys_alt, ord_a, ord_b,
-                              dsort_tmp, v->counts, scounts, st);
+    ord = radix_sort_segments_rest(s->K, M, dbits, dbias, dkeys, dkeys_alt, ord_a, ord_b, dsort_tmp,
+                                   v->counts, scounts, st);
   }
   {
     Stage sg(ctx, "scan", st);

@@ -91,6 +91,7 @@ struct rxgs_ctx {
   rxgs::ServeState* serve = nullptr;
   unsigned* d_err = nullptr;      // device error word
   uint32_t* h_pinned = nullptr;   // pinned readback slot
+  cudaEvent_t ev_stats = nullptr;  // prepare: the readback slot is written
   uint32_t* d_pinned = nullptr;   // ... its device-side address (kernels write it)
   // stage profiler: CUDA events recorded on the call's stream around each
   // stage while enabled, folded into per-stage totals by rxgs_profile_read

@@ -470,11 +470,10 @@ size_t tmp_words(const Segs& G) {
 // [nseg][512][tps].
 template <typename Key>
 int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t* const (&vb)[2],
-               size_t n, const Segs& G, int bits, uint32_t* tmp, cudaStream_t s,
-               const uint32_t* n_dev, Key bias = 0, const uint32_t* gsrc = nullptr,
-               uint32_t* gdst = nullptr) {
-  if (n == 0 || bits <= 0) return -1;
-  const Plan P = plan_of(bits);
+               size_t n, const Segs& G, int pfirst, int pend, int width, uint32_t* tmp,
+               cudaStream_t s, const uint32_t* n_dev, Key bias = 0,
+               const uint32_t* gsrc = nullptr, uint32_t* gdst = nullptr) {
+  if (n == 0 || pend <= pfirst) return -1;
   const int nt = G.nseg * G.tps;
   const int rows = G.nseg * kBins;
   uint32_t* totals = tmp;
@@ -491,19 +490,19 @@ int run_passes(const Key* k0, const uint32_t* v0, Key* const (&kb)[2], uint32_t*
   const Key* kin = k0;
   const uint32_t* vin = v0;
   int out = 0;
-  for (int p = 0; p < P.passes; ++p) {
+  for (int p = pfirst; p < pend; ++p) {
     out = p & 1;
-    const int shift = p * P.width;
-    sort_count_kernel<Key, false><<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, P.width, bias,
+    const int shift = p * width;
+    sort_count_kernel<Key, false><<<nt, kThreads, 0, s>>>(kin, n, n_dev, shift, width, bias,
                                                           hist, G, VarSegs{});
     if (G.tps <= kWarpRowMax)
       sort_offsets_warp_kernel<<<(rows + kWarps - 1) / kWarps, kThreads, 0, s>>>(hist, totals,
                                                                                 G.tps, rows);
     else
       sort_offsets_kernel<<<rows, kThreads, 0, s>>>(hist, totals, G.tps);
-    const bool last = p + 1 == P.passes;
+    const bool last = p + 1 == pend;
     sort_scatter_kernel<Key, false><<<nt, kThreads, sizeof(ScatterSmem<Key>), s>>>(
-        kin, vin, last && gdst ? nullptr : kb[out], vb[out], n, n_dev, shift, P.width, bias, hist,
+        kin, vin, last && gdst ? nullptr : kb[out], vb[out], n, n_dev, shift, width, bias, hist,
         totals, G, last ? gsrc : nullptr, last ? gdst : nullptr, VarSegs{});
     note_launches(3);
     kin = kb[out];
@@ -535,7 +534,10 @@ void sort_pairs(Key* keys, uint32_t* vals, Key* keys_alt, uint32_t* vals_alt, si
   if (n <= 1) return;
   Key* const kb[2] = {keys_alt, keys};
   uint32_t* const vb[2] = {vals_alt, vals};
-  const int out = run_passes<Key>(keys, vals, kb, vb, n, whole(n), bits, tmp, s, n_dev);
+  if (bits <= 0) return;
+  const Plan P = plan_of(bits);
+  const int out = run_passes<Key>(keys, vals, kb, vb, n, whole(n), 0, P.passes, P.width, tmp, s,
+                                  n_dev);
   *result_in_alt = out == 0;
 }
 
@@ -560,21 +562,38 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
   sort_pairs<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, tmp, result_in_alt, s, n_dev);
 }
 
-const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
-                                    uint32_t bias, uint32_t* keys_a, uint32_t* keys_b,
-                                    uint32_t* idx_a, uint32_t* idx_b, uint32_t* tmp,
-                                    const uint32_t* gather_src, uint32_t* gather_dst,
-                                    cudaStream_t s) {
-  if (bits > 32) bits = 32;
-  if (bits < 1) bits = 1;  // at least one pass: the indices are written
+void radix_sort_segments_first(const uint32_t* keys, size_t len, int nseg, uint32_t* keys_a,
+                               uint32_t* idx_a, uint32_t* tmp, cudaStream_t s) {
   const Segs G = segments(len, nseg);
+  uint32_t* const kb[2] = {keys_a, keys_a};
+  uint32_t* const vb[2] = {idx_a, idx_a};
+  run_passes<uint32_t>(keys, nullptr, kb, vb, len * static_cast<size_t>(nseg), G, 0, 1, kMaxWidth,
+                       tmp, s, nullptr);
+}
+
+const uint32_t* radix_sort_segments_rest(size_t len, int nseg, int bits, uint32_t bias,
+                                         uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
+                                         uint32_t* idx_b, uint32_t* tmp,
+                                         const uint32_t* gather_src, uint32_t* gather_dst,
+                                         cudaStream_t s) {
+  const size_t n = len * static_cast<size_t>(nseg);
+  if (n == 0) return nullptr;
+  if (bits > 32) bits = 32;
+  const int passes = bits > kMaxWidth ? (bits + kMaxWidth - 1) / kMaxWidth : 1;
+  const bool gather = gather_src && gather_dst;
+  if (passes == 1) {  // pass 0 was the whole sort
+    if (gather) launch_gather_words(gather_src, idx_a, n, gather_dst, s);
+    return idx_a;
+  }
+  const Segs G = segments(len, nseg);
+  // pass p writes buffer p % 2: pass 0 wrote keys_a / idx_a, pass 1 reads
+  // them and writes keys_b / idx_b, ...
   uint32_t* const kb[2] = {keys_a, keys_b};
   uint32_t* const vb[2] = {idx_a, idx_b};
-  const bool gather = gather_src && gather_dst;
-  const int out = run_passes<uint32_t>(keys, nullptr, kb, vb, len * static_cast<size_t>(nseg), G,
-                                       bits, tmp, s, nullptr, bias, gather ? gather_src : nullptr,
+  const int out = run_passes<uint32_t>(keys_a, idx_a, kb, vb, n, G, 1, passes, kMaxWidth, tmp, s,
+                                       nullptr, bias, gather ? gather_src : nullptr,
                                        gather ? gather_dst : nullptr);
-  return out < 0 ? nullptr : vb[out];
+  return vb[out];
 }
 
 size_t radix_views_tmp_words(size_t n, int M) {

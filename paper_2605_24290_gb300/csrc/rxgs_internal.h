@@ -65,8 +65,8 @@ void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
                  unsigned* err = nullptr);
 
 // The two-sort order of the instances (view, tile, depth, Gaussian index):
-// every view's Gaussians sorted by depth (radix_sort_segments over the
-// depth keys, one segment per view), then dst[i] = src[idx[i]] (the tile
+// every view's Gaussians sorted by depth (radix_sort_segments_first / _rest
+// over the depth keys, one segment per view), then dst[i] = src[idx[i]] (the tile
 // counts in that order, then scanned) ...
 void launch_gather_words(const uint32_t* src, const uint32_t* idx, size_t n, uint32_t* dst,
                          cudaStream_t s);
@@ -93,13 +93,23 @@ void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
 // Each of nseg segments of len consecutive keys (read only) sorted stably
-// on its own by the low `bits` bits of key - bias (uint32 arithmetic);
-// returns the sorted item indices (of the whole array) in idx_a or idx_b;
-// keys_a / keys_b are scratch, all four of len * nseg words.  gather_src
-// (optional): gather_dst[i] = gather_src[index i] is written as well.  tmp
-// must hold radix_segments_tmp_words(len, nseg) uint32.  Null if nothing
-// was sorted (len * nseg == 0).
+// on its own, in 9-bit digits of key - bias (uint32 arithmetic, bias a
+// multiple of 512 so that the first digit does not depend on it): the
+// first pass (radix_sort_segments_first, into keys_a / idx_a, values the
+// items' indices in the whole array) can run before the bias is known; the
+// rest (radix_sort_segments_rest, `bits` of key - bias in all) returns the
+// sorted indices (idx_a or idx_b).  keys_a / keys_b / idx_a / idx_b hold
+// len * nseg words.  gather_src (optional): gather_dst[i] = gather_src[index
+// i] is written as well.  tmp must hold radix_segments_tmp_words(len, nseg)
+// uint32.  Null if nothing was sorted (len * nseg == 0).
 size_t radix_segments_tmp_words(size_t len, int nseg);
+void radix_sort_segments_first(const uint32_t* keys, size_t len, int nseg, uint32_t* keys_a,
+                               uint32_t* idx_a, uint32_t* tmp, cudaStream_t s);
+const uint32_t* radix_sort_segments_rest(size_t len, int nseg, int bits, uint32_t bias,
+                                         uint32_t* keys_a, uint32_t* keys_b, uint32_t* idx_a,
+                                         uint32_t* idx_b, uint32_t* tmp,
+                                         const uint32_t* gather_src, uint32_t* gather_dst,
+                                         cudaStream_t s);
 // The instances of launch_emit_sorted (keys view << tile_bits | tile,
 // tile_bits <= 9) in one stable pass by tile within each view's contiguous
 // run (offsets: the emission scan, view m's run starts at offsets[m K]);
@@ -110,11 +120,6 @@ size_t radix_views_tmp_words(size_t n, int M);
 void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                       uint32_t* vals_out, size_t n, const uint32_t* offsets, int K, int M,
                       int tile_bits, uint2* ranges, int T, uint32_t* tmp, cudaStream_t s);
-const uint32_t* radix_sort_segments(const uint32_t* keys, size_t len, int nseg, int bits,
-                                    uint32_t bias, uint32_t* keys_a, uint32_t* keys_b,
-                                    uint32_t* idx_a, uint32_t* idx_b, uint32_t* tmp,
-                                    const uint32_t* gather_src, uint32_t* gather_dst,
-                                    cudaStream_t s);
 
 // dst[i] = src[i] for n 32-bit words, copied by a kernel (device memory or
 // mapped pinned host memory on either side): for small transfers that must
