@@ -56,12 +56,12 @@ def peaks():
 # measured by one ncu capture of that kernel on this workload; valid only
 # while the kernel sources hash to the value recorded at capture time.
 NCU_TRAFFIC = {
-    "render_fwd": {"bytes": 19_816_448 + 483_368_960, "tile": [8, 32], "cols": 128,
+    "render_fwd": {"bytes": 19_888_896 + 483_264_000, "tile": [8, 32], "cols": 128,
                    "files": ['render_fwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
-                   "sha1": "81cf6bb6ea56c668"},
-    "render_bwd": {"bytes": 560_865_024 + 8_279_040, "tile": [8, 32], "cols": 128,
+                   "sha1": "822d37bb986e6847"},
+    "render_bwd": {"bytes": 560_782_080 + 8_101_632, "tile": [8, 32], "cols": 128,
                    "files": ['render_bwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
-                   "sha1": "445f21d5d4d93274"},
+                   "sha1": "9554e1739008fd4b"},
 }
 
 
@@ -451,9 +451,33 @@ def gpu_bench(args):
         e_ms = (time.perf_counter() - t0) * 1e3 / n_e
         e_ms, e_val = whole_job_rate(torch, dist if world > 1 else None, e_ms, spectra_per_step,
                                      dev)
+        # this machine's host links with the same pinned buffers and streams:
+        # the cotangent up alone, the spectra down alone, both at once (best
+        # of three each); (up + down bytes) / both-at-once is the copy bound
+        # of one e2e step
+        def link_ms(up, down):
+            best = float("inf")
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                if up:
+                    with torch.cuda.stream(copy_in):
+                        d_gs[1].copy_(h_g, non_blocking=True)
+                if down:
+                    with torch.cuda.stream(copy_out):
+                        o_spec.copy_(specs[1], non_blocking=True)
+                torch.cuda.synchronize()
+                best = min(best, (time.perf_counter() - t1) * 1e3)
+            return best
+
+        up_b, down_b = h_g.numel() * 4, o_spec.numel() * 4
+        t_up, t_down, t_both = link_ms(True, False), link_ms(False, True), link_ms(True, True)
+        link = {"h2d_gbs": round(up_b / t_up / 1e6, 1), "d2h_gbs": round(down_b / t_down / 1e6, 1),
+                "both_gbs": round((up_b + down_b) / t_both / 1e6, 1),
+                "copy_bound_ms": round((h2d + d2h) / ((up_b + down_b) / t_both) , 4)}
         e2e = {"value": round(e_val, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": round(e_ms, 4),
+               "ms_per_step": round(e_ms, 4), "host_links": link,
                "copies": "H2D tx, rx and the spectra cotangent; D2H the spectra, RSSI and the "
                          "opacity, phi_base and MLP gradients (pinned host buffers); the next "
                          "step's cotangent goes up and this step's spectra come down on two copy "
