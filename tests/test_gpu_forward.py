@@ -180,6 +180,61 @@ def test_full_size_sorted_lists_bitexact(torch, rx, oracle):
     ctx.release_views(views)
 
 
+def test_lists_many_tiles_two_pass_path(torch, rx, oracle):
+    """More than 512 tiles (a 360x720 grid at 0.5 deg: 1,035 tiles of 16x16)
+    takes the two-pass (view | tile) instance sort and the ranges kernel in
+    place of the one-pass sort per view: records, tile sets, sorted lists and
+    ranges bit-exact for both views."""
+    rng = np.random.default_rng(307)
+    sc = S.draw_scene(rng, 1500)
+    g = S.Grid(H=360, W=720, theta0_deg=-90.0, step_deg=0.5, tile_h=16, tile_w=16)
+    ctx = make_ctx(rx, g)
+    h = upload(ctx, sc, torch)
+    tx = S.draw_points(np.random.default_rng(308), 2)
+    views = ctx.prepare(h, dev(tx, torch))
+    n = check_views(torch, ctx, oracle, g, sc, tx, views)
+    assert n > 0
+    ctx.release_views(views)
+
+
+def test_lists_narrow_depths_ties_empty_view(torch, rx, oracle):
+    """Gaussians on a thin shell around the first transmitter (all depths
+    within 0.3 % of each other, so the depth sort needs two 9-bit passes),
+    fifty of them duplicated at other indices (equal depths and footprints:
+    ties decided by the Gaussian index), and a middle view that sees nothing
+    (an empty run between two non-empty ones in the per-view instance pass):
+    lists and ranges bit-exact; spectra, CSI and RSSI of the first view
+    against the oracle."""
+    rng = np.random.default_rng(311)
+    K = 600
+    d = rng.normal(size=(K, 3))
+    d[:, 2] = np.abs(d[:, 2]) + 0.2          # above the horizon
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tx0 = np.array([5.0, 4.0, 1.0])
+    r = 3.0 + rng.uniform(-0.004, 0.004, K)
+    means = tx0 + d * r[:, None]
+    means[K - 50:] = means[:50]
+    sc = S.Scene(S.f32(means), S.f32(rng.normal(-2.3, 0.3, size=(K, 3))),
+                 S.f32(rng.normal(size=(K, 4))), S.f32(rng.uniform(0.2, 0.9, size=K)))
+    g = S.Grid()
+    ctx = make_ctx(rx, g)
+    h = upload(ctx, sc, torch)
+    tx = S.f32([tx0, [5.0, 4.0, 50.0], tx0 + np.array([0.01, -0.01, 0.0])])
+    views = ctx.prepare(h, dev(tx, torch))
+    check_views(torch, ctx, oracle, g, sc, tx, views)
+    _, orec, _ = oracle.project_view32(g, sc, tx[1])
+    assert not (orec[:, 7] > 0).any(), "the middle view should see nothing"
+    _, orec0, _ = oracle.project_view32(g, sc, tx[0])
+    vis = orec0[:, 7] > 0
+    assert vis[:50].any() and (vis[:50] == vis[K - 50:]).all()
+    rad = S.draw_radiance(np.random.default_rng(312), 2, K, 1)
+    out = render_all(torch, ctx, h, tx, rad, rx.OUT_SPECTRA | rx.OUT_RSSI | rx.OUT_CSI,
+                     views=views)
+    compare_view(oracle, g, sc, tx[0], rad, *[o[0] for o in out])
+    assert np.all(out[0][1] == 0)
+    ctx.release_views(views)
+
+
 def test_small_workload_forward_parity(torch, rx, oracle):
     """4,096 Gaussians, 1 transmitter, 8 receivers, 90x360, 16x16 tiles."""
     w = S.workload_small()
