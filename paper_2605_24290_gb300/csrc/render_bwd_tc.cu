@@ -443,7 +443,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             sW[bq[q] * kP + p] = (valid && start + bq[q] < stop && G[q] > 0.0f) ? G[q] : 0.0f;
       }
     }
-    __syncthreads();
+    // the weights and mask of a strip are read only by its two warps: their
+    // barrier, not the CTA's (everything else the recurrence reads was
+    // ordered by the chunk's first barrier or arrives through mbarriers)
+    tc::named_barrier(1 + wp, 64);
     // 2. the recurrence, two threads per pixel
     float x[8];
     const bool more = n + 1 < nchunks;
