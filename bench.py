@@ -59,9 +59,9 @@ NCU_TRAFFIC = {
     "render_fwd": {"bytes": 19_888_896 + 483_264_000, "tile": [8, 32], "cols": 128,
                    "files": ['render_fwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
                    "sha1": "822d37bb986e6847"},
-    "render_bwd": {"bytes": 560_782_080 + 8_101_632, "tile": [8, 32], "cols": 128,
+    "render_bwd": {"bytes": 561_249_024 + 8_143_360, "tile": [8, 32], "cols": 128,
                    "files": ['render_bwd_tc.cu', 'render_common.cuh', 'rxgs_math.cuh', 'tc_common.cuh'],
-                   "sha1": "9554e1739008fd4b"},
+                   "sha1": "5fc5890331f1f8c7"},
 }
 
 
