@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   constexpr int nloc = kHidden * 6 + kHidden + n4 * kHidden + n4;
   constexpr int kWarps = kBwdThreads / 32;
   __shared__ float W1[kHidden * 6], B1[kHidden], W2[n4 * kHidden], B2[n4];
+  __shared__ float B1x[kHidden];                // B1 + W1[., 4]: the start of a without occlusion
   __shared__ float4 sX[kBwdThreads];            // features of each thread's pair
   __shared__ float2 sO[kBwdThreads];            // its occlusion inputs (T, rho_bar)
   __shared__ float4 sD[kBwdThreads * CC];       // dol of each thread's pair
@@ -371,6 +372,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
   for (int e = t; e < kHidden; e += kBwdThreads) B1[e] = P[o.l_b1 + e];
   for (int e = t; e < n4 * kHidden; e += kBwdThreads) W2[e] = P[o.l_w2 + 4 * c0 * kHidden + e];
   for (int e = t; e < n4; e += kBwdThreads) B2[e] = P[o.l_b2 + 4 * c0 + e];
+  for (int e = t; e < kHidden; e += kBwdThreads) B1x[e] = P[o.l_b1 + e] + P[o.l_w1 + e * 6 + 4];
   __syncthreads();
 
   // phase-2 operands of this lane's hidden units u = lane, lane + 32
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
     for (int q = 0; q < n4; ++q) w2u[hf][q] = W2[q * kHidden + u];
   }
   float b1u[2] = {B1[lane], B1[32 + lane]};
+  const float b1x[2] = {B1x[lane], B1x[32 + lane]};
 
   constexpr int NI = OCC ? 6 : 4;  // inputs with a weight gradient of their own
   float aw2[n4][2], aw1[NI][2], ab1[2], ab2[n4], aog[n4];
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
           a = fmaf(W1[u * 6 + 4], oc.x, a);
           a = fmaf(W1[u * 6 + 5], oc.y, a);
         } else {
-          a = B1[u] + W1[u * 6 + 4];  // input 4 is T = 1, input 5 is rho = 0
+          a = B1x[u];  // input 4 is T = 1, input 5 is rho = 0
 #pragma unroll
           for (int i = 0; i < 4; ++i) a = fmaf(W1[u * 6 + i], x[i], a);
         }
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(kBwdThreads) mlp_local_bwd_kernel(
           a = fmaf(w1u[hf][4], op.x, a);
           a = fmaf(w1u[hf][5], op.y, a);
         } else {
-          a = b1u[hf] + w1u[hf][4];
+          a = b1x[hf];
           a = fmaf(w1u[hf][0], xp.x, a);
           a = fmaf(w1u[hf][1], xp.y, a);
           a = fmaf(w1u[hf][2], xp.z, a);
