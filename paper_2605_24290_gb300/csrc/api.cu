@@ -686,7 +686,11 @@ rxgs_status make_radiance(rxgs_ctx* ctx, const SceneState* s, const ViewsState* 
       launch_occ_probes(s->geom, s->K, rx, N, s->occ_res, s->occ_box, s->occ, feat, st);
       m.feat = feat;
     }
-    launch_mlp_radiance(m, rx, N, s->geom, s->base, s->K, stride, rad, glob, st);
+    // every (Gaussian, receiver) column is written: only the pad columns
+    // past 2 N C are cleared
+    clear_pad_columns(rad, s->K, stride, 2 * N * s->C, st);
+    launch_mlp_radiance(m, rx, N, s->geom, s->base, s->K, stride, rad, glob, st, nullptr,
+                        nullptr, false);
     dfree(feat, st);
   }
   return check_last(ctx, "radiance");
