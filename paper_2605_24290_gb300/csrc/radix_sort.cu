@@ -1,14 +1,17 @@
 // radix_sort.cu -- stable LSD radix sort of (uint64 or uint32 key, uint32
 // value) pairs, used for the per-tile depth-sorted lists (Algorithm 1,
-// Stage 1): every view's Gaussians by depth (one segment per view, 31-bit
-// keys), then the instances by (view, tile) (32-bit keys), or the single
-// sort of (view | tile | depth) keys of the batched path; stability keeps
-// equal keys in input order.
+// Stage 1): every view's Gaussians by depth (one segment of K per view, the
+// 31-bit depth keys less a bias, 9-bit digits), then the instances emitted
+// in that order, in one pass by tile within each view's contiguous run
+// (variable segments; the pass also writes each (view, tile) range); with
+// more than 512 tiles the instances take the plain sort of (view | tile)
+// keys, and the batched path the plain sort of (view | tile | depth) keys.
+// Stability keeps equal keys in input order.
 //
-// Segments: nseg runs of `len` consecutive items, each sorted in place on
-// its own (nseg = 1: a plain sort).  Digits of up to 9 bits (ceil(bits / 9)
-// passes).  One pass = three kernels over tiles of 2,048 items, no tile
-// crossing a segment boundary:
+// Segments: nseg runs of `len` consecutive items (or variable runs), each
+// sorted in place on its own (nseg = 1: a plain sort).  Digits of up to 9
+// bits (ceil(bits / 9) passes).  One pass = three kernels over tiles of
+// 2,048 items, no tile crossing a segment boundary:
 //   sort_count    each tile's digit counts (shared-memory histogram);
 //   sort_offsets  per (segment, digit): where each tile's run of that digit
 //                 starts within the digit (exclusive scan over the
