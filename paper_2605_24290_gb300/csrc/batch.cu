@@ -55,7 +55,11 @@ struct BatchPlan {
   int* desc = nullptr;
   float4* rec = nullptr;
   uint32_t *depth = nullptr, *counts = nullptr, *offsets = nullptr, *scan_tmp = nullptr;
-  uint64_t *keys = nullptr, *keys_alt = nullptr;
+  // the depth order of every view slot's Gaussians: key and index buffers,
+  // sort scratch, the tile counts in that order
+  uint32_t *dkeys = nullptr, *dkeys_alt = nullptr, *ord_a = nullptr, *ord_b = nullptr;
+  uint32_t *dsort_tmp = nullptr, *scounts = nullptr;
+  uint32_t *keys = nullptr, *keys_alt = nullptr;  // (view << tile_bits | tile)
   uint32_t *vals = nullptr, *vals_alt = nullptr, *sort_tmp = nullptr;
   uint2* ranges = nullptr;
   float *partial = nullptr, *spectra = nullptr, *csi = nullptr, *rssi = nullptr;
@@ -75,7 +79,8 @@ void destroy_plan(BatchPlan* p) {
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->desc_done) cudaEventDestroy(p->desc_done);
   void* bufs[] = {p->tx, p->rx, p->rad_in, p->rad, p->glob, p->desc, p->rec, p->depth,
-                  p->counts, p->offsets, p->scan_tmp, p->keys, p->keys_alt, p->vals,
+                  p->counts, p->offsets, p->scan_tmp, p->dkeys, p->dkeys_alt, p->ord_a,
+                  p->ord_b, p->dsort_tmp, p->scounts, p->keys, p->keys_alt, p->vals,
                   p->vals_alt, p->sort_tmp, p->ranges, p->partial, p->spectra, p->csi,
                   p->rssi, p->counter, p->W, p->wtmp};
   for (void* b : bufs)
@@ -190,7 +195,8 @@ static size_t plan_bytes(const BatchPlan& p, int K) {
   const size_t MK = static_cast<size_t>(p.B_max) * K;
   size_t b = 0;
   b += sizeof(float4) * 2 * MK + 3 * sizeof(uint32_t) * MK;
-  b += (sizeof(uint64_t) + sizeof(uint32_t)) * 2ull * p.I_cap;
+  b += 5 * sizeof(uint32_t) * MK;  // depth-order keys and indices (x2), counts in that order
+  b += 2 * sizeof(uint32_t) * 2ull * p.I_cap;
   b += sizeof(float) * static_cast<size_t>(K) * p.stride;
   b += sizeof(float) * static_cast<size_t>(p.g.T) * p.cols_cap;
   if (p.kind & RXGS_OUT_SPECTRA)
@@ -209,8 +215,8 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   p->stride = round_up(p->cols_cap, 128) + 128;
   p->tile_bits = bits_for(static_cast<uint64_t>(g.T));
   p->view_bits = bits_for(static_cast<uint64_t>(p->B_max));
-  if (31 + p->tile_bits + p->view_bits > 64)
-    return fail(ctx, RXGS_E_INVALID, "too many views x tiles for a 64-bit key");
+  if (p->tile_bits + p->view_bits > 32)
+    return fail(ctx, RXGS_E_INVALID, "too many views x tiles for a 32-bit (view, tile) key");
   p->bytes = plan_bytes(*p, K);
   cudaError_t e = cudaSuccess;
   auto A = [&](auto** ptr, size_t n) {
@@ -224,11 +230,18 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   A(&p->counts, MK);
   A(&p->offsets, MK + 1);
   A(&p->scan_tmp, scan_tmp_words(MK));
+  A(&p->dkeys, MK);
+  A(&p->dkeys_alt, MK);
+  A(&p->ord_a, MK);
+  A(&p->ord_b, MK);
+  A(&p->dsort_tmp, radix_segments_tmp_words(K, p->B_max));
+  A(&p->scounts, MK);
   A(&p->keys, p->I_cap);
   A(&p->keys_alt, p->I_cap);
   A(&p->vals, p->I_cap);
   A(&p->vals_alt, p->I_cap);
-  A(&p->sort_tmp, radix_tmp_words(p->I_cap));
+  A(&p->sort_tmp, p->tile_bits <= 9 ? radix_views_tmp_words(p->I_cap, p->B_max)
+                                    : radix_tmp_words(p->I_cap));
   A(&p->ranges, static_cast<size_t>(p->B_max) * g.T);
   if (p->vis) {
     A(&p->W, static_cast<size_t>(p->B_max) * K);
@@ -259,17 +272,30 @@ static rxgs_status build_plan(rxgs_ctx* ctx, const SceneState* s, BatchPlan* p) 
   if (e != cudaSuccess) return fail(ctx, RXGS_E_CUDA, "capture: %s", cudaGetErrorString(e));
   const int* nviews_dev = p->desc;
   launch_preprocess(g, s->geom, K, p->tx, p->B_max, p->rec, p->depth, p->counts, st, nviews_dev);
-  launch_exclusive_scan(p->counts, p->offsets, MK, p->scan_tmp, st);
-  launch_emit(g, p->rec, p->depth, p->offsets, K, p->B_max, p->tile_bits, p->keys, p->vals, st,
-              p->I_cap, ctx->d_err);
+  // the per-tile lists as in prepare: every view slot's Gaussians by depth
+  // (all 31 bits: nothing is read back inside the graph), the instances
+  // emitted in that order (none past the capacity), then one stable pass by
+  // tile within each view's run, which writes the ranges
+  radix_sort_segments_first(p->depth, K, p->B_max, p->dkeys, p->ord_a, p->dsort_tmp, st);
+  const uint32_t* ord = radix_sort_segments_rest(K, p->B_max, 31, 0u, p->dkeys, p->dkeys_alt,
+                                                 p->ord_a, p->ord_b, p->dsort_tmp, p->counts,
+                                                 p->scounts, st);
+  launch_exclusive_scan(p->scounts, p->offsets, MK, p->scan_tmp, st);
+  launch_emit_sorted(g, p->rec, ord, p->offsets, MK, K, p->tile_bits, p->keys, p->vals, st,
+                     p->I_cap, ctx->d_err);
   const uint32_t* n_dev = p->offsets + MK;
-  bool in_alt = false;
-  radix_sort_pairs(p->keys, p->vals, p->keys_alt, p->vals_alt, p->I_cap,
-                   31 + p->tile_bits + p->view_bits, p->sort_tmp, &in_alt, st, n_dev, ctx->d_err);
+  bool in_alt = true;
+  if (p->tile_bits <= 9) {
+    radix_sort_views(p->keys, p->vals, p->keys_alt, p->vals_alt, p->I_cap, p->offsets, K,
+                     p->B_max, p->tile_bits, p->ranges, g.T, p->sort_tmp, st);
+  } else {
+    radix_sort_pairs(p->keys, p->vals, p->keys_alt, p->vals_alt, p->I_cap,
+                     p->tile_bits + p->view_bits, p->sort_tmp, &in_alt, st, n_dev, ctx->d_err);
+    launch_tile_ranges(in_alt ? p->keys_alt : p->keys, p->I_cap, p->tile_bits, g.T, p->ranges,
+                       p->B_max, st, n_dev);
+  }
   p->sorted_in_alt = in_alt;
-  uint64_t* keys = in_alt ? p->keys_alt : p->keys;
   uint32_t* vals = in_alt ? p->vals_alt : p->vals;
-  launch_tile_ranges(keys, p->I_cap, p->tile_bits, g.T, p->ranges, p->B_max, st, n_dev);
   if (p->vis) {
     // CSI / RSSI = sum_k W[v(j)][k] s(j, k): one receiver-independent pass
     // per view, then the MLP evaluated only where the weight is non-zero

@@ -421,7 +421,8 @@ void launch_gather_words(const uint32_t* src, const uint32_t* idx, size_t n, uin
 __global__ void __launch_bounds__(256) emit_sorted_kernel(
     GridConst g, const float4* __restrict__ rec, const uint32_t* __restrict__ ord,
     const uint32_t* __restrict__ offsets, size_t MK, int K, int tile_bits,
-    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t cap,
+    unsigned* __restrict__ err) {
   __shared__ uint32_t sO[8][33];  // per warp: first position of each lane's pair, end
   __shared__ int4 sD[8][32];      // (tr0, ncols, n0 | c0a << 16, c1a)
   __shared__ uint2 sB[8][32];     // (view << tile_bits, Gaussian index)
@@ -433,6 +434,7 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(
   if (i < MK) {
     o = offsets[i];
     end = offsets[i + 1];
+    if (end > cap && err) atomicOr(err, kErrCapacity);  // nothing past cap is written
     if (end > o) {
       const uint32_t idx = ord[i];
       const uint32_t m = idx / static_cast<uint32_t>(K);
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(
   sD[w][lane] = d;
   sB[w][lane] = b;
   __syncwarp();
-  const uint32_t start = sO[w][0], stop = sO[w][32];
+  const uint32_t start = sO[w][0], stop = min(sO[w][32], cap);
   for (uint32_t q = start + lane; q < stop; q += 32) {
     // the owner: the last lane whose first position is <= q (a lane with
     // no instances shares its first position with the next lane)
@@ -473,10 +475,10 @@ __global__ void __launch_bounds__(256) emit_sorted_kernel(
 
 void launch_emit_sorted(const GridConst& g, const float4* rec, const uint32_t* ord,
                         const uint32_t* offsets, size_t MK, int K, int tile_bits, uint32_t* keys,
-                        uint32_t* vals, cudaStream_t s) {
+                        uint32_t* vals, cudaStream_t s, uint32_t cap, unsigned* err) {
   if (MK == 0) return;
   emit_sorted_kernel<<<static_cast<unsigned>((MK + 255) / 256), 256, 0, s>>>(
-      g, rec, ord, offsets, MK, K, tile_bits, keys, vals);
+      g, rec, ord, offsets, MK, K, tile_bits, keys, vals, cap, err);
   note_launches(1);
 }
 

@@ -404,10 +404,12 @@ __global__ void __launch_bounds__(kThreads) sort_scatter_kernel(
 
 
 // The view segments of the emitted instances: start[m] = offsets[m K]
-// (the emission is view-major), tile0 = exclusive scan of the segments'
-// tile counts, tile_seg[b] for b < nt.  One block.
+// (the emission is view-major) clamped to n (a capacity the emission did not
+// write past), tile0 = exclusive scan of the segments' tile counts,
+// tile_seg[b] for b < nt.  One block.
 __global__ void __launch_bounds__(1024) var_segs_kernel(const uint32_t* __restrict__ offsets, int K,
-                                                       int M, int nt, uint32_t* __restrict__ start,
+                                                       int M, int nt, uint32_t n,
+                                                       uint32_t* __restrict__ start,
                                                        uint32_t* __restrict__ tile0,
                                                        uint32_t* __restrict__ tile_seg) {
   __shared__ uint32_t wsum[32];
@@ -419,10 +421,10 @@ __global__ void __launch_bounds__(1024) var_segs_kernel(const uint32_t* __restri
     const int m = c0 + t;
     uint32_t cnt = 0;
     if (m <= M) {
-      const uint32_t s0 = offsets[static_cast<size_t>(m) * K];
+      const uint32_t s0 = min(offsets[static_cast<size_t>(m) * K], n);
       start[m] = s0;
       if (m < M) {
-        const uint32_t s1 = offsets[static_cast<size_t>(m + 1) * K];
+        const uint32_t s1 = min(offsets[static_cast<size_t>(m + 1) * K], n);
         cnt = (s1 - s0 + kTile - 1) / kTile;
       }
     }
@@ -632,7 +634,8 @@ void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys
   V.nt = nt;
   V.T = T;
   V.ranges = ranges;
-  var_segs_kernel<<<1, 1024, 0, s>>>(offsets, K, M, nt, start, tile0, tile_seg);
+  var_segs_kernel<<<1, 1024, 0, s>>>(offsets, K, M, nt, static_cast<uint32_t>(n), start, tile0,
+                                     tile_seg);
   const Segs G = whole(n);
   sort_count_kernel<uint32_t, true><<<nt, kThreads, 0, s>>>(keys, n, nullptr, 0, tile_bits, 0u,
                                                             hist, G, V);

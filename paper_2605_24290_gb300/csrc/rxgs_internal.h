@@ -73,9 +73,12 @@ void launch_gather_words(const uint32_t* src, const uint32_t* idx, size_t n, uin
 // ... the instances of the ordered pairs (ord: view-major pair indices,
 // offsets: the scan of their counts) with (view << tile_bits | tile) keys
 // and Gaussian-index values, then stably sorted by those keys.
+// Positions at or past `cap` are not written; a pair whose instances would
+// end past it sets kErrCapacity in *err.
 void launch_emit_sorted(const GridConst& g, const float4* rec, const uint32_t* ord,
                         const uint32_t* offsets, size_t MK, int K, int tile_bits, uint32_t* keys,
-                        uint32_t* vals, cudaStream_t s);
+                        uint32_t* vals, cudaStream_t s, uint32_t cap = 0xffffffffu,
+                        unsigned* err = nullptr);
 // (view | tile) keys and values -> (view | tile | depth) keys (export only).
 void launch_expand_keys(const uint32_t* vt, const uint32_t* vals, size_t n, const uint32_t* depth,
                         int K, int tile_bits, uint64_t* out, cudaStream_t s);
@@ -114,8 +117,9 @@ const uint32_t* radix_sort_segments_rest(size_t len, int nseg, int bits, uint32_
 // tile_bits <= 9) in one stable pass by tile within each view's contiguous
 // run (offsets: the emission scan, view m's run starts at offsets[m K]);
 // writes the sorted keys and values to keys_out / vals_out and ranges[M][T]
-// ([start, end) of each (view, tile); zero when empty).  tmp must hold
-// radix_views_tmp_words(n, M) uint32.
+// ([start, end) of each (view, tile); zero when empty).  n: the instances,
+// or a capacity they do not exceed (the view runs are clamped to it).  tmp
+// must hold radix_views_tmp_words(n, M) uint32.
 size_t radix_views_tmp_words(size_t n, int M);
 void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out,
                       uint32_t* vals_out, size_t n, const uint32_t* offsets, int K, int M,
