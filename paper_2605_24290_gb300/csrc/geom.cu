@@ -311,84 +311,6 @@ void launch_preprocess(const GridConst& g, const float4* geom, int K, const floa
   note_launches(1);
 }
 
-// ---------------------------------------------------------------- emission
-// Key = view << (31 + tile_bits) | tile << 31 | float bits of rho (rho > 0,
-// so its sign bit is clear and the 31 low bits order like the value).
-// A warp takes 32 consecutive Gaussians of one view; their instances occupy
-// one contiguous range of the output (the offsets are an exclusive scan),
-// and lane l writes positions start + l, start + l + 32, ... (coalesced
-// stores): it finds the Gaussian owning a position by a binary search over
-// the warp's offsets and the tile by the position within that Gaussian's
-// row-major tile rectangle.
-__global__ void __launch_bounds__(256) emit_kernel(GridConst g, const float4* __restrict__ rec,
-                                                   const uint32_t* __restrict__ depth,
-                                                   const uint32_t* __restrict__ offsets, int K,
-                                                   int tile_bits, uint64_t* __restrict__ keys,
-                                                   uint32_t* __restrict__ vals, uint32_t cap,
-                                                   unsigned* __restrict__ err) {
-  __shared__ uint32_t sO[8][33];   // per warp: first position of each lane's Gaussian, end
-  __shared__ int4 sD[8][32];       // (tr0, ncols, n0 | c0a << 16, c1a)
-  __shared__ uint64_t sB[8][32];   // base key (view and depth), or ~0: nothing to write
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
-  const size_t idx = static_cast<size_t>(v) * K + k;
-  uint32_t o = 0, end = 0;
-  if (k < K) {
-    o = offsets[idx];
-    end = offsets[idx + 1];
-  } else {
-    o = end = offsets[static_cast<size_t>(v) * K + K];  // past the view's last Gaussian
-  }
-  int4 d = make_int4(0, 1, 0, 0);
-  uint64_t base = ~0ull;
-  if (k < K && end > o) {
-    if (end > cap) {  // more instances than the buffers hold: record, write nothing
-      if (err) atomicOr(err, kErrCapacity);
-    } else {
-      const float4 r1 = rec[2 * idx + 1];
-      const int rows = __float_as_int(r1.z), cols = __float_as_int(r1.w);
-      const int i_lo = rows & 0xffff, j_lo = cols & 0xffff, span = cols >> 16;
-      const TileCols tc = tile_cols(g, j_lo, span);
-      const int n0 = tc.c0b - tc.c0a + 1, n1 = tc.c1b >= tc.c1a ? tc.c1b - tc.c1a + 1 : 0;
-      d = make_int4(i_lo / g.TH, n0 + n1, n0 | (tc.c0a << 16), tc.c1a);
-      base = (static_cast<uint64_t>(v) << (31 + tile_bits)) | depth[idx];
-    }
-  }
-  sO[w][lane] = o;
-  if (lane == 31) sO[w][32] = end;
-  sD[w][lane] = d;
-  sB[w][lane] = base;
-  __syncwarp();
-  const uint32_t start = sO[w][0], stop = sO[w][32];
-  const int kw = (blockIdx.x * blockDim.x + (w << 5));
-  for (uint32_t q = start + lane; q < stop; q += 32) {
-    // the owner: the last lane whose first position is <= q
-    int lo = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1)
-      if (sO[w][lo + step] <= q) lo += step;
-    const uint64_t b = sB[w][lo];
-    if (b == ~0ull) continue;
-    const int4 dd = sD[w][lo];
-    const int j = static_cast<int>(q - sO[w][lo]);
-    const int row = j / dd.y, ci = j - row * dd.y;
-    const int n0 = dd.z & 0xffff;
-    const int c = ci < n0 ? (dd.z >> 16) + ci : dd.w + (ci - n0);
-    keys[q] = b | (static_cast<uint64_t>((dd.x + row) * g.tiles_w + c) << 31);
-    vals[q] = static_cast<uint32_t>(kw + lo);
-  }
-}
-
-void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
-                 const uint32_t* offsets, int K, int M, int tile_bits, uint64_t* keys,
-                 uint32_t* vals, cudaStream_t s, uint32_t cap, unsigned* err) {
-  if (K <= 0 || M <= 0) return;
-  dim3 grid((K + 255) / 256, M);
-  emit_kernel<<<grid, 256, 0, s>>>(g, rec, depth, offsets, K, tile_bits, keys, vals, cap, err);
-  note_launches(1);
-}
-
 // ---------------------------------------------- instances in depth order
 // The per-tile lists (Algorithm 1, Stage 1) in two sorts instead of one over
 // 64-bit (view | tile | depth) instance keys: every view's Gaussians by
@@ -520,7 +442,8 @@ void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_
 }
 
 // -------------------------------------------------------------- tile ranges
-// Keys (view | tile | depth) (64 bits) or (view | tile) (32 bits).
+// Keys (view | tile): 32 bits (64-bit keys would carry the depth in their
+// low 31 bits).
 template <typename Key>
 __global__ void tile_ranges_kernel(const Key* __restrict__ keys, size_t n, int tile_bits,
                                    int T, uint2* __restrict__ ranges,
@@ -546,11 +469,6 @@ static void tile_ranges(const Key* keys, size_t n, int tile_bits, int T, uint2* 
   tile_ranges_kernel<Key><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
       keys, n, tile_bits, T, ranges, n_dev);
   note_launches(1);
-}
-
-void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
-                        int M, cudaStream_t s, const uint32_t* n_dev) {
-  tile_ranges<uint64_t>(keys, n, tile_bits, T, ranges, M, s, n_dev);
 }
 
 void launch_tile_ranges(const uint32_t* keys, size_t n, int tile_bits, int T, uint2* ranges,

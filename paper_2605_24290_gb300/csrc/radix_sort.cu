@@ -5,8 +5,7 @@
 // in that order, in one pass by tile within each view's contiguous run
 // (variable segments; the pass also writes each (view, tile) range); with
 // more than 512 tiles the instances take the plain sort of (view | tile)
-// keys, and the batched path the plain sort of (view | tile | depth) keys.
-// Stability keeps equal keys in input order.
+// keys.  Stability keeps equal keys in input order.
 //
 // Segments: nseg runs of `len` consecutive items (or variable runs), each
 // sorted in place on its own (nseg = 1: a plain sort).  Digits of up to 9
@@ -552,17 +551,10 @@ size_t radix_tmp_words(size_t n) { return tmp_words(whole(n)); }
 
 size_t radix_segments_tmp_words(size_t len, int nseg) { return tmp_words(segments(len, nseg)); }
 
-void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
-                      const uint32_t* n_dev, unsigned* err) {
-  (void)err;  // no kernel of this sort waits on another
-  sort_pairs<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, tmp, result_in_alt, s, n_dev);
-}
-
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev, unsigned* err) {
-  (void)err;
+  (void)err;  // no kernel of this sort waits on another
   if (bits > 32) bits = 32;
   sort_pairs<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, tmp, result_in_alt, s, n_dev);
 }

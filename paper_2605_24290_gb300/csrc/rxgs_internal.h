@@ -56,14 +56,6 @@ size_t scan_tmp_words(size_t n);
 void launch_exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp,
                            cudaStream_t s);
 
-// Writes the (view | tile | depth) keys and Gaussian-index values.
-// A Gaussian whose instances would end beyond `cap` writes nothing and sets
-// kErrCapacity in *err.
-void launch_emit(const GridConst& g, const float4* rec, const uint32_t* depth,
-                 const uint32_t* offsets, int K, int M, int tile_bits, uint64_t* keys,
-                 uint32_t* vals, cudaStream_t s, uint32_t cap = 0xffffffffu,
-                 unsigned* err = nullptr);
-
 // The two-sort order of the instances (view, tile, depth, Gaussian index):
 // every view's Gaussians sorted by depth (radix_sort_segments_first / _rest
 // over the depth keys, one segment per view), then dst[i] = src[idx[i]] (the tile
@@ -89,9 +81,6 @@ void launch_expand_keys(const uint32_t* vt, const uint32_t* vals, size_t n, cons
 size_t radix_tmp_words(size_t n);
 // n_dev (optional): the actual item count, <= n (launch sizes follow n).
 // err (optional): unused (no kernel of the sort waits on another).
-void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                      size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
-                      const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
 void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                       size_t n, int bits, uint32_t* tmp, bool* result_in_alt, cudaStream_t s,
                       const uint32_t* n_dev = nullptr, unsigned* err = nullptr);
@@ -131,8 +120,6 @@ void radix_sort_views(const uint32_t* keys, const uint32_t* vals, uint32_t* keys
 void launch_copy_words(const uint32_t* src, uint32_t* dst, size_t n, cudaStream_t s);
 
 // ranges[M*T] = [start, end) of each (view, tile) in the sorted keys.
-void launch_tile_ranges(const uint64_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
-                        int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
 // ... from (view | tile) keys
 void launch_tile_ranges(const uint32_t* keys, size_t n, int tile_bits, int T, uint2* ranges,
                         int M, cudaStream_t s, const uint32_t* n_dev = nullptr);
